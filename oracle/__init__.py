@@ -1,0 +1,223 @@
+"""Plain FP64 CPU oracle for the ASCI determinant search (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg
+may import this package.  It shares no code with the GPU path; the C source
+``asci_oracle.c`` is compiled with gcc into ``liboracle.so`` beside it.
+
+Functions follow arXiv:2303.05688: Eq. 1 (the ASCI score), Algorithm 2 (the
+search: core selection, single/double enumeration, sort-and-accumulate) and the
+duplicate-aware top-N selection of Sec. 2.2.  ``fock`` holds an independent
+brute-force second-quantised Hamiltonian that pins the oracle's Slater-Condon
+evaluator.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "asci_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, -O2, no target-specific flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ct.CDLL(_LIB)
+            u64p = ct.POINTER(ct.c_uint64)
+            f64p = ct.POINTER(ct.c_double)
+            szp = ct.POINTER(ct.c_size_t)
+            lib.oracle_search.restype = ct.c_void_p
+            lib.oracle_search.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p, f64p,
+                                          ct.c_size_t, ct.c_double, ct.c_size_t, ct.c_double,
+                                          ct.c_uint64, ct.c_uint64]
+            lib.oracle_free.argtypes = [ct.c_void_p]
+            lib.oracle_result_count.restype = ct.c_size_t
+            lib.oracle_result_count.argtypes = [ct.c_void_p]
+            lib.oracle_result_stats.argtypes = [ct.c_void_p, szp]
+            lib.oracle_result_copy.argtypes = [ct.c_void_p, u64p, u64p, f64p, f64p, f64p, f64p]
+            lib.oracle_topn.restype = ct.c_size_t
+            lib.oracle_topn.argtypes = [u64p, u64p, f64p, ct.c_size_t, ct.c_size_t, szp]
+            lib.oracle_core_select.restype = ct.c_size_t
+            lib.oracle_core_select.argtypes = [u64p, u64p, f64p, ct.c_size_t, ct.c_size_t, szp]
+            lib.oracle_hij.restype = ct.c_double
+            lib.oracle_hij.argtypes = [ct.c_int, f64p, f64p, ct.c_double, ct.c_uint64, ct.c_uint64,
+                                       ct.c_uint64, ct.c_uint64]
+            lib.oracle_diag.restype = ct.c_double
+            lib.oracle_diag.argtypes = [ct.c_int, f64p, f64p, ct.c_double, ct.c_uint64, ct.c_uint64]
+            lib.oracle_dense_h.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p,
+                                           ct.c_size_t, f64p]
+            lib.oracle_pairs.restype = ct.c_size_t
+            lib.oracle_pairs.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p, f64p,
+                                         ct.c_size_t, ct.c_size_t, u64p, u64p, f64p]
+            lib.oracle_numerator.restype = ct.c_double
+            lib.oracle_numerator.argtypes = [ct.c_int, f64p, f64p, ct.c_double, ct.c_uint64,
+                                             ct.c_uint64, u64p, u64p, f64p, ct.c_size_t, f64p]
+            lib.oracle_bucket_of.restype = ct.c_uint64
+            lib.oracle_bucket_of.argtypes = [ct.c_uint64, ct.c_uint64, ct.c_uint64]
+            _lib = lib
+    return _lib
+
+
+def _f64(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _u64(x):
+    return np.ascontiguousarray(x, dtype=np.uint64)
+
+
+def _p(a, t):
+    return a.ctypes.data_as(ct.POINTER(t))
+
+
+class Ints:
+    """Integrals in the oracle's layout: h1[n, n], eri[n, n, n, n] = (pq|rs)."""
+
+    def __init__(self, h1, eri, ecore=0.0):
+        self.h1 = _f64(h1)
+        self.eri = _f64(eri)
+        self.n = int(self.h1.shape[0])
+        self.ecore = float(ecore)
+
+    def args(self):
+        return (self.n, _p(self.h1, ct.c_double), _p(self.eri, ct.c_double), self.ecore)
+
+
+def hij(ints: Ints, bra, ket) -> float:
+    """<bra|H|ket> by the Slater-Condon rules (determinants as (alpha, beta))."""
+    return _load().oracle_hij(*ints.args(), int(bra[0]), int(bra[1]), int(ket[0]), int(ket[1]))
+
+
+def diag(ints: Ints, det) -> float:
+    """<D|H|D>."""
+    return _load().oracle_diag(*ints.args(), int(det[0]), int(det[1]))
+
+
+def dense_h(ints: Ints, A, B) -> np.ndarray:
+    """H[i, j] = <D_i|H|D_j> for the determinant list (A, B)."""
+    A, B = _u64(A), _u64(B)
+    out = np.empty((len(A), len(A)))
+    _load().oracle_dense_h(*ints.args(), _p(A, ct.c_uint64), _p(B, ct.c_uint64), len(A),
+                           _p(out, ct.c_double))
+    return out
+
+
+def core_select(A, B, c, C) -> np.ndarray:
+    """Indices of the C largest |c| (ties: key ascending), in that order."""
+    A, B, c = _u64(A), _u64(B), _f64(c)
+    out = np.empty(max(len(A), 1), dtype=np.uintp)
+    m = _load().oracle_core_select(_p(A, ct.c_uint64), _p(B, ct.c_uint64), _p(c, ct.c_double),
+                                   len(A), int(C), _p(out, ct.c_size_t))
+    return out[:m].astype(np.int64)
+
+
+def pairs(ints: Ints, CA, CB, CC):
+    """Pre-sort (target, H_ij c_j) pairs of Alg. 2 for the given core dets."""
+    CA, CB, CC = _u64(CA), _u64(CB), _f64(CC)
+    lib = _load()
+    args = ints.args() + (_p(CA, ct.c_uint64), _p(CB, ct.c_uint64), _p(CC, ct.c_double), len(CA))
+    n = lib.oracle_pairs(*args, 0, None, None, None)
+    a = np.empty(n, dtype=np.uint64)
+    b = np.empty(n, dtype=np.uint64)
+    v = np.empty(n)
+    lib.oracle_pairs(*args, n, _p(a, ct.c_uint64), _p(b, ct.c_uint64), _p(v, ct.c_double))
+    return a, b, v
+
+
+def numerator(ints: Ints, target, CA, CB, CC):
+    """(sum_j <target|H|D_j> c_j, sum_j |...|) over a core list, by brute force."""
+    CA, CB, CC = _u64(CA), _u64(CB), _f64(CC)
+    s = ct.c_double(0.0)
+    v = _load().oracle_numerator(*ints.args(), int(target[0]), int(target[1]),
+                                 _p(CA, ct.c_uint64), _p(CB, ct.c_uint64), _p(CC, ct.c_double),
+                                 len(CA), ct.byref(s))
+    return v, s.value
+
+
+def bucket_of(a: int, b: int, nbuckets: int) -> int:
+    return int(_load().oracle_bucket_of(int(a), int(b), int(nbuckets)))
+
+
+class SearchResult:
+    """Every unique candidate outside psi (Alg. 2 before the final selection)."""
+
+    def __init__(self, a, b, num, abssum, haa, score, stats):
+        self.a, self.b = a, b
+        self.num, self.abssum, self.haa, self.score = num, abssum, haa, score
+        (self.generated, self.surviving, self.unique, self.excluded, self.ncore) = stats
+
+    @property
+    def keys(self) -> np.ndarray:
+        return np.stack([self.a, self.b], axis=1)
+
+    def topn(self, N: int) -> np.ndarray:
+        """Indices of the selected candidates (|S| desc, key asc)."""
+        return topn(self.a, self.b, self.score, N)
+
+
+def search(ints: Ints, A, B, c, E0: float, C: int, eps: float = 0.0,
+           nbuckets: int = 1, bucket: int = 0) -> SearchResult:
+    """Algorithm 2 + Eq. 1: all unique candidates with numerator, H_ii and score."""
+    A, B, c = _u64(A), _u64(B), _f64(c)
+    lib = _load()
+    h = lib.oracle_search(*ints.args(), _p(A, ct.c_uint64), _p(B, ct.c_uint64),
+                          _p(c, ct.c_double), len(A), float(E0), int(C), float(eps),
+                          int(nbuckets), int(bucket))
+    if not h:
+        raise MemoryError("oracle_search failed")
+    try:
+        k = lib.oracle_result_count(h)
+        st = np.zeros(5, dtype=np.uintp)
+        lib.oracle_result_stats(h, _p(st, ct.c_size_t))
+        a = np.empty(k, dtype=np.uint64)
+        b = np.empty(k, dtype=np.uint64)
+        num, abss, haa, sc = (np.empty(k) for _ in range(4))
+        lib.oracle_result_copy(h, _p(a, ct.c_uint64), _p(b, ct.c_uint64), _p(num, ct.c_double),
+                               _p(abss, ct.c_double), _p(haa, ct.c_double), _p(sc, ct.c_double))
+    finally:
+        lib.oracle_free(h)
+    return SearchResult(a, b, num, abss, haa, sc, tuple(int(x) for x in st))
+
+
+def topn(a, b, score, N: int) -> np.ndarray:
+    """Top-N indices by |score| descending, ties by key ascending."""
+    a, b, score = _u64(a), _u64(b), _f64(score)
+    out = np.empty(max(len(a), 1), dtype=np.uintp)
+    m = _load().oracle_topn(_p(a, ct.c_uint64), _p(b, ct.c_uint64), _p(score, ct.c_double),
+                            len(a), int(N), _p(out, ct.c_size_t))
+    return out[:m].astype(np.int64)
+
+
+def variational_energy(ints: Ints, A, B, c) -> float:
+    """<psi|H|psi> / <psi|psi> on the given determinants (dense, small lists)."""
+    H = dense_h(ints, A, B)
+    c = _f64(c)
+    return float(c @ H @ c / (c @ c))
+
+
+def ground_state(ints: Ints, A, B):
+    """Lowest eigenpair of H restricted to the determinant list (dense)."""
+    H = dense_h(ints, A, B)
+    w, V = np.linalg.eigh(H)
+    v = V[:, 0].copy()
+    if v[np.argmax(np.abs(v))] < 0:
+        v = -v
+    return float(w[0]), v

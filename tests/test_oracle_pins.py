@@ -1,0 +1,313 @@
+"""Pins of the CPU oracle against things other than itself (CPU only).
+
+* The brute-force second-quantised Hamiltonian (oracle/fock.py) is pinned by
+  closed forms: the Hubbard ring at U = 0 and t = 0, and the Hubbard dimer.
+* The oracle's Slater-Condon evaluator is pinned element by element against
+  that brute-force Hamiltonian on complete tiny sectors with random integrals.
+* The oracle's search (Alg. 2 with Eq. 1) is pinned by brute force: numerators
+  equal the dense product H[:, core] @ c_core, the candidate set equals the
+  structural set of dets within two excitations of the core and outside psi,
+  counts follow the closed form, and the single-determinant case reduces to
+  Epstein-Nesbet coefficients.
+* The ASCI loop with N = infinity converges to full CI on the Hubbard ring.
+* Mutation tests plant plausible mistakes in a copy of the oracle and check
+  that a pin catches each one.
+"""
+import json
+import math
+import os
+import subprocess
+import ctypes as ct
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fock
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")
+
+
+def _gold():
+    with open(GOLD) as f:
+        return json.load(f)
+
+
+def _lowest(H):
+    """Lowest eigenvalue of a dense symmetric matrix (LAPACK, robust to degeneracy)."""
+    import scipy.linalg as sl
+    return float(sl.eigh(H, subset_by_index=[0, 0], eigvals_only=True)[0])
+
+
+# --------------------------------------------------------------------------
+# brute force pinned by closed forms
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", _gold()["hubbard"]["cases"], ids=lambda c: f"n{c['norb']}_t{c['t']}_U{c['U']}")
+def test_bruteforce_hubbard_closed_forms(case):
+    n, na, nb = case["norb"], case["na"], case["nb"]
+    h1, eri, ec = W.hubbard_ring(n, case["t"], case["U"])
+    A, B = fock.sector(n, na, nb)
+    H = fock.hamiltonian(n, h1, eri, ec, A, B)
+    assert np.allclose(H, H.T, atol=1e-14)
+    assert abs(_lowest(H) - case["E"]) < 1e-9
+
+
+def test_bruteforce_particle_and_spin_conservation():
+    # H never couples sectors: the brute-force action on one sector lands in it
+    n = 4
+    h1, eri, ec = W.random_molecular(n, 5)
+    A, B = fock.sector(n, 2, 1)
+    A2, B2 = fock.sector(n, 1, 2)
+    H = fock.hamiltonian(n, h1, eri, ec, np.concatenate([A, A2]), np.concatenate([B, B2]))
+    m = len(A)
+    assert np.all(H[:m, m:] == 0.0) and np.all(H[m:, :m] == 0.0)
+
+
+# --------------------------------------------------------------------------
+# Slater-Condon (oracle) pinned by brute force
+# --------------------------------------------------------------------------
+
+SECTORS = [(4, 1, 1, 0.0), (6, 2, 2, 0.37), (6, 3, 3, 0.0), (5, 3, 1, -1.25), (5, 2, 0, 0.0)]
+
+
+@pytest.mark.parametrize("n,na,nb,ecore", SECTORS)
+def test_slater_condon_matches_bruteforce(oracle_mod, n, na, nb, ecore):
+    h1, eri, _ = W.random_molecular(n, 100 + n + na)
+    A, B = fock.sector(n, na, nb)
+    Hb = fock.hamiltonian(n, h1, eri, ecore, A, B)
+    Ho = oracle_mod.dense_h(oracle_mod.Ints(h1, eri, ecore), A, B)
+    assert np.max(np.abs(Ho - Hb)) < 1e-13
+
+
+def test_slater_condon_hubbard_matches_bruteforce(oracle_mod):
+    n = 6
+    h1, eri, ec = W.hubbard_ring(n, 1.0, 3.0)
+    A, B = fock.sector(n, 3, 3)
+    Hb = fock.hamiltonian(n, h1, eri, ec, A, B)
+    Ho = oracle_mod.dense_h(oracle_mod.Ints(h1, eri, ec), A, B)
+    assert np.max(np.abs(Ho - Hb)) < 1e-13
+
+
+def test_hermiticity(oracle_mod):
+    n = 8
+    h1, eri, _ = W.random_molecular(n, 9)
+    ints = oracle_mod.Ints(h1, eri)
+    A, B = fock.sector(n, 3, 3)
+    rng = np.random.default_rng(0)
+    idx = rng.choice(len(A), 150, replace=False)
+    H = oracle_mod.dense_h(ints, A[idx], B[idx])
+    assert np.max(np.abs(H - H.T)) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# the search pinned by brute force
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,na,nb,npsi,C", [(6, 2, 2, 20, 12), (6, 3, 3, 40, 40), (5, 3, 1, 8, 5),
+                                             (7, 3, 2, 30, 17)])
+def test_search_numerators_equal_dense_product(oracle_mod, n, na, nb, npsi, C):
+    h1, eri, _ = W.random_molecular(n, 7 * n + na)
+    ecore = 0.5
+    ints = oracle_mod.Ints(h1, eri, ecore)
+    A, B = fock.sector(n, na, nb)
+    Hb = fock.hamiltonian(n, h1, eri, ecore, A, B)
+    rng = np.random.default_rng(n + npsi)
+    psi = rng.choice(len(A), npsi, replace=False)
+    c = rng.normal(size=npsi)
+    E0 = float(np.min(np.diag(Hb))) - 0.3
+    res = oracle_mod.search(ints, A[psi], B[psi], c, E0, C)
+    core = psi[np.argsort(-np.abs(c), kind="stable")][:C]   # |c| distinct a.s.
+    core_c = c[np.argsort(-np.abs(c), kind="stable")][:C]
+    # structural candidate set: within two excitations of a core det, not in psi
+    exc = lambda i, j: (bin(int(A[i]) ^ int(A[j])).count("1") + bin(int(B[i]) ^ int(B[j])).count("1")) // 2
+    expect = sorted(i for i in range(len(A)) if i not in set(psi.tolist())
+                    and any(1 <= exc(i, j) <= 2 for j in core))
+    key_of = {(int(A[i]), int(B[i])): i for i in range(len(A))}
+    got = sorted(key_of[(int(a), int(b))] for a, b in zip(res.a, res.b))
+    assert got == expect
+    num_dense = Hb[:, core] @ core_c
+    for k, (a, b) in enumerate(zip(res.a, res.b)):
+        i = key_of[(int(a), int(b))]
+        assert abs(res.num[k] - num_dense[i]) <= 1e-13 * max(1.0, res.abssum[k])
+        assert abs(res.haa[k] - Hb[i, i]) <= 1e-13 * max(1.0, abs(Hb[i, i]))
+        assert abs(res.score[k] - num_dense[i] / (E0 - Hb[i, i])) <= 1e-12 * abs(res.score[k]) + 1e-15
+    assert res.generated == len(core) * W.n_excitations(n, na, nb)
+
+
+def test_search_single_det_is_epstein_nesbet(oracle_mod):
+    n, na, nb = 6, 3, 3
+    h1, eri, _ = W.random_molecular(n, 77)
+    ints = oracle_mod.Ints(h1, eri)
+    A, B = fock.sector(n, na, nb)
+    Hb = fock.hamiltonian(n, h1, eri, 0.0, A, B)
+    hf = (W.aufbau(na), W.aufbau(nb))
+    key_of = {(int(A[i]), int(B[i])): i for i in range(len(A))}
+    i0 = key_of[hf]
+    E0 = Hb[i0, i0]
+    res = oracle_mod.search(ints, [hf[0]], [hf[1]], [1.0], E0, 1)
+    assert res.generated == W.n_excitations(n, na, nb) == len(res.a)
+    for k, (a, b) in enumerate(zip(res.a, res.b)):
+        i = key_of[(int(a), int(b))]
+        en = Hb[i, i0] / (E0 - Hb[i, i])
+        assert abs(res.score[k] - en) <= 1e-12 * abs(en) + 1e-15
+
+
+@pytest.mark.parametrize("case", _gold()["excitation_counts"]["cases"], ids=lambda c: f"n{c['norb']}")
+def test_excitation_counts_closed_form(oracle_mod, case):
+    n, na, nb = case["norb"], case["na"], case["nb"]
+    assert W.n_excitations(n, na, nb) == case["n_exc"]
+    h1 = np.zeros((n, n))
+    eri = np.zeros((n,) * 4)
+    ints = oracle_mod.Ints(h1, eri)
+    # a non-aufbau parent so holes and particles interleave
+    rng = np.random.default_rng(n)
+    pa = sum(1 << int(x) for x in rng.choice(n, na, replace=False))
+    pb = sum(1 << int(x) for x in rng.choice(n, nb, replace=False))
+    a, b, v = oracle_mod.pairs(ints, [pa], [pb], [1.0])
+    assert len(a) == case["n_exc"]
+    keys = set(zip(a.tolist(), b.tolist()))
+    assert len(keys) == case["n_exc"]               # every excitation is a distinct det
+    for x, y in zip(a.tolist(), b.tolist()):
+        assert bin(x).count("1") == na and bin(y).count("1") == nb
+        lvl = (bin(x ^ pa).count("1") + bin(y ^ pb).count("1")) // 2
+        assert 1 <= lvl <= 2
+
+
+# --------------------------------------------------------------------------
+# invariants of the search
+# --------------------------------------------------------------------------
+
+def _small_random_case():
+    w = W.WORKLOADS["random_10e14o"]
+    h1, eri, ec = w.integrals()
+    A, B, c = w.psi()
+    return w, h1, eri, ec, A, B, c
+
+
+def test_invariants_permutation_sign_and_buckets(oracle_mod):
+    w, h1, eri, ec, A, B, c = _small_random_case()
+    ints = oracle_mod.Ints(h1, eri, ec)
+    E0 = -20.0
+    C = 60
+    r0 = oracle_mod.search(ints, A, B, c, E0, C)
+    perm = np.random.default_rng(1).permutation(len(A))
+    r1 = oracle_mod.search(ints, A[perm], B[perm], c[perm], E0, C)
+    assert np.array_equal(r0.a, r1.a) and np.array_equal(r0.b, r1.b)
+    assert np.array_equal(r0.score, r1.score)
+    r2 = oracle_mod.search(ints, A, B, -c, E0, C)
+    assert np.array_equal(r0.a, r2.a) and np.array_equal(r0.score, -r2.score)
+    parts = [oracle_mod.search(ints, A, B, c, E0, C, nbuckets=3, bucket=k) for k in range(3)]
+    ka = np.concatenate([p.a for p in parts])
+    kb = np.concatenate([p.b for p in parts])
+    sc = np.concatenate([p.score for p in parts])
+    o = np.lexsort((ka, kb))
+    assert np.array_equal(ka[o], r0.a) and np.array_equal(kb[o], r0.b)
+    assert np.array_equal(sc[o], r0.score)
+    assert sum(p.generated for p in parts) == 3 * r0.generated
+
+
+def test_invariant_alpha_beta_swap(oracle_mod):
+    w, h1, eri, ec, A, B, c = _small_random_case()
+    ints = oracle_mod.Ints(h1, eri, ec)
+    E0, C = -20.0, 60
+    r0 = oracle_mod.search(ints, A, B, c, E0, C)
+    r1 = oracle_mod.search(ints, B, A, c, E0, C)
+    o0 = np.lexsort((r0.a, r0.b))
+    o1 = np.lexsort((r1.b, r1.a))  # swapped keys
+    assert np.array_equal(r0.a[o0], r1.b[o1]) and np.array_equal(r0.b[o0], r1.a[o1])
+    # the reordering phase (-1)^(na nb) is global, so |S| is unchanged
+    s0, s1 = np.abs(r0.score[o0]), np.abs(r1.score[o1])
+    assert np.all(np.abs(s0 - s1) <= 1e-12 * s0 + 1e-300)
+
+
+def test_topn_is_duplicate_aware_selection(oracle_mod):
+    # |{a > a_k}| < k <= |{a >= a_k}| (Sec. 2.2), ties broken by key ascending
+    rng = np.random.default_rng(3)
+    n = 500
+    a = rng.integers(0, 1 << 20, n).astype(np.uint64)
+    b = rng.integers(0, 1 << 20, n).astype(np.uint64)
+    s = rng.choice([-3.0, -1.0, 0.5, 1.0, 2.0, 3.0], n)
+    for N in (1, 7, 100, 250, 499, 500, 800):
+        idx = oracle_mod.topn(a, b, s, N)
+        assert len(idx) == min(N, n)
+        k = len(idx)
+        ak = np.abs(s[idx[-1]])
+        assert np.sum(np.abs(s) > ak) < k <= np.sum(np.abs(s) >= ak)
+        sel = set(idx.tolist())
+        ties = [i for i in range(n) if np.abs(s[i]) == ak]
+        tie_sel = sorted((int(b[i]), int(a[i])) for i in ties if i in sel)
+        tie_all = sorted((int(b[i]), int(a[i])) for i in ties)
+        assert tie_sel == tie_all[:len(tie_sel)]
+
+
+# --------------------------------------------------------------------------
+# full CI through the ASCI loop (Alg. 1 with N = infinity)
+# --------------------------------------------------------------------------
+
+def test_asci_loop_reaches_full_ci_on_hubbard_ring(oracle_mod):
+    n, na, nb = 8, 4, 4
+    h1, eri, ec = W.hubbard_ring(n, 1.0, 4.0)
+    ints = oracle_mod.Ints(h1, eri, ec)
+    A, B = fock.sector(n, na, nb)
+    E_fci = _lowest(fock.hamiltonian(n, h1, eri, ec, A, B))
+    from tests.golden.make_golden import hubbard_start
+    pa, pb, c, E0 = hubbard_start(oracle_mod)
+    for _ in range(10):
+        res = oracle_mod.search(ints, pa, pb, c, E0, len(pa))
+        if len(res.a) == 0:
+            break
+        pa = np.concatenate([pa, res.a])
+        pb = np.concatenate([pb, res.b])
+        import scipy.linalg as sl
+        H = oracle_mod.dense_h(ints, pa, pb)
+        w, V = sl.eigh(H, subset_by_index=[0, 0])
+        E0, c = float(w[0]), V[:, 0]
+    assert len(pa) == len(A) == 4900
+    assert abs(E0 - E_fci) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# planted mistakes: each must be caught by a pin
+# --------------------------------------------------------------------------
+
+MUTATIONS = {
+    "drop_single_exchange": ("ERI(I, i, a, k, k) - ERI(I, i, k, k, a)", "ERI(I, i, a, k, k)"),
+    "flip_double_sign": ("return sg * (ERI(I, i, a, j, b) - ERI(I, i, b, j, a));",
+                         "return -sg * (ERI(I, i, a, j, b) - ERI(I, i, b, j, a));"),
+    "transpose_double_operand": ("ERI(I, i, a, j, b) - ERI(I, i, b, j, a)",
+                                 "ERI(I, i, j, a, b) - ERI(I, i, b, j, a)"),
+    "drop_cross_coulomb": ("if (occupied(a, p) && occupied(b, q)) nsum_add(&acc, ERI(I, p, p, q, q));", ""),
+    "wrong_phase_range": ("for (k = lo + 1; k < hi; k++)", "for (k = lo; k < hi; k++)"),
+    "opposite_spin_sign": ("int s = single_sign(ket_a, ha[0], pa[0]) * single_sign(ket_b, hb[0], pb[0]);",
+                           "int s = single_sign(ket_a, ha[0], pa[0]);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistakes(tmp_path, name):
+    src = open(os.path.join(os.path.dirname(os.path.dirname(__file__)), "oracle", "asci_oracle.c")).read()
+    old, new = MUTATIONS[name]
+    assert old in src, f"mutation site for {name} not found"
+    path = tmp_path / "mut.c"
+    path.write_text(src.replace(old, new, 1))
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c99", "-fPIC", "-shared", "-o", str(so), str(path), "-lm"])
+    lib = ct.CDLL(str(so))
+    f64p = ct.POINTER(ct.c_double)
+    u64p = ct.POINTER(ct.c_uint64)
+    lib.oracle_dense_h.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p, ct.c_size_t, f64p]
+    caught = False
+    for (n, na, nb, ecore) in SECTORS:
+        h1, eri, _ = W.random_molecular(n, 100 + n + na)
+        A, B = fock.sector(n, na, nb)
+        Hb = fock.hamiltonian(n, h1, eri, ecore, A, B)
+        h1c, eric = np.ascontiguousarray(h1), np.ascontiguousarray(eri)
+        A, B = np.ascontiguousarray(A), np.ascontiguousarray(B)
+        out = np.empty((len(A), len(A)))
+        lib.oracle_dense_h(n, h1c.ctypes.data_as(f64p), eric.ctypes.data_as(f64p), ecore,
+                           A.ctypes.data_as(u64p), B.ctypes.data_as(u64p), len(A), out.ctypes.data_as(f64p))
+        if np.max(np.abs(out - Hb)) >= 1e-13:
+            caught = True
+            break
+    assert caught, f"planted mistake {name} went unnoticed"
