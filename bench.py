@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 ASCI search: scored excitations/s at (24e,30o).
+
+One step is one full search (Algorithm 2 with Eq. 1, constraint batched) over
+the synthetic Cr2-shaped workload: 30 orbitals, 12 alpha + 12 beta electrons,
+|psi| = 1e6, C = 1e5 core determinants, N = 1e6 selected; C * n_exc =
+6.73e9 scored excitations per step.  Inputs are device-resident when the timed
+region starts; L2 is flushed (a 512 MB write) before every timed step, outside
+the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl asci|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank runs an independent
+replica (the search shards by constraint class with no data-path exchange);
+timing is the max over ranks and `value` counts all ranks' excitations.
+`--impl reference` times the plain CPU oracle on bounded samples of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ASCI search scored excitations/s at (24e,30o)"
+UNIT = "excitations/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="asci", choices=["asci", "reference"])
+    p.add_argument("--workload", default="random_24e30o")
+    p.add_argument("--eps", type=float, default=0.0)
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32_fp64acc", "fp32_comp"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-core", type=int, default=0,
+                   help="core dets in each oracle sample (0: sized to ~10 s)")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- clocks ---
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- workload ---
+
+def load_workload(name):
+    import numpy as np
+    import workloads as W
+    w = W.WORKLOADS[name]
+    h1, eri, ec = w.integrals()
+    A, B, c = w.psi()
+    return w, h1, eri, ec, A, B, c, W.stored_e0(name), np
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# -------------------------------------------------------------- reference ---
+
+def cpu_sample(w, h1, eri, ec, A, B, c, E0, core, np):
+    """Time the oracle (as it stands) on the top `core` core dets of the workload."""
+    import oracle
+    ints = oracle.Ints(h1, eri, ec)
+    t0 = time.perf_counter()
+    r = oracle.search(ints, A, B, c, E0, core)
+    dt = time.perf_counter() - t0
+    return r.generated, dt
+
+
+def size_cpu_sample(w, args):
+    if args.cpu_sample_core:
+        return args.cpu_sample_core
+    # about 10 s of oracle work on this host class (measured ~1e6 pairs/s)
+    from math import ceil
+    import workloads as W
+    nexc = W.n_excitations(w.norb, w.na, w.nb)
+    return max(1, min(w.C, int(ceil(1.0e7 / nexc))))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w, h1, eri, ec, A, B, c, E0, np = load_workload(args.workload)
+    import oracle
+    oracle.build()
+    core = size_cpu_sample(w, args)
+    for _ in range(args.warmup):
+        cpu_sample(w, h1, eri, ec, A, B, c, E0, max(1, core // 10), np)
+    tot_pairs, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        p, dt = cpu_sample(w, h1, eri, ec, A, B, c, E0, core, np)
+        tot_pairs += p
+        tot_t += dt
+    value = tot_pairs / tot_t
+    sample = (f"oracle on the top {core} of {w.C} core dets of {w.name} per step "
+              f"({tot_pairs // args.steps} excitations/step), full psi for exclusion")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "norb": w.norb, "nelec": [w.na, w.nb], "ndets": w.ndets,
+                   "C": w.C, "N": w.N, "eps": args.eps},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- main ---
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2303_05688_gb300 as asci
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    prec = {"fp64": asci.FP64, "fp32_fp64acc": asci.FP32_INT_FP64_ACC,
+            "fp32_comp": asci.FP32_INT_COMP_ACC}[args.precision]
+    w, h1, eri, ec, A, B, c, E0, np = load_workload(args.workload)
+    dev = torch.device("cuda", local)
+    dets = torch.tensor(np.stack([A, B], 1).astype(np.int64), device=dev)
+    cf = torch.tensor(c, device=dev)
+    h1d = torch.tensor(h1, device=dev)
+    erid = torch.tensor(eri, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    asci.load()
+
+    def one(d=dets, cc=cf, hh=h1d, ee=erid):
+        return asci.search(d, cc, E0, hh, ee, ec, w.C, w.N, eps=args.eps, precision=prec)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        one()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = asci.launch_count()
+    times, stats = [], None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, stats = one()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier()
+    launches = asci.launch_count() - l0
+    clk = clocks.stop()
+    t_total = sum(times) / 1e3
+    if world > 1:
+        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    pairs = stats.generated
+    value = world * pairs * args.steps / t_total
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hd = torch.tensor(np.stack([A, B], 1).astype(np.int64)).pin_memory()
+        hc = torch.tensor(c).pin_memory()
+        hh = torch.tensor(h1).pin_memory()
+        he = torch.tensor(eri).pin_memory()
+        one(hd, hc, hh, he)
+        torch.cuda.synchronize()
+        barrier()
+        te = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            od, osc, _ = one(hd, hc, hh, he)
+            te.append(time.perf_counter() - t0)
+        t_e2e = sum(te)
+        if world > 1:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        h2d = hd.numel() * 8 + hc.numel() * 8 + hh.numel() * 8 + he.numel() * 8
+        d2h = len(od) * 16 + len(osc) * 8
+        e2e = {"value": world * pairs * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline: algorithmic bytes of the search, B_alg = 32 P + 24 C + 16 |psi| + 32 U + 16 N
+    peak, peak_kind = peaks()
+    ts = stats.t_stage_ms
+    b_alg = (32 * stats.surviving + 24 * stats.ncore + 16 * w.ndets + 32 * stats.unique
+             + 16 * stats.selected)
+    t_search = statistics.mean(times) / 1e3
+    achieved = b_alg / t_search / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "whole search (all stages)", "peak_kind": peak_kind,
+                "alg_bytes_per_step": b_alg, "stage_ms": {k: round(v, 3) for k, v in ts.items()}}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        core = size_cpu_sample(w, args)
+        p, dt = cpu_sample(w, h1, eri, ec, A, B, c, E0, core, np)
+        cpu = {"value": p / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle on the top {core} of {w.C} core dets of {w.name} "
+                         f"({p} excitations, {dt:.1f} s), full psi for exclusion"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == asci.FP64 else "f32+f64", "data": "synthetic",
+        "config": {"workload": w.name, "norb": w.norb, "nelec": [w.na, w.nb], "ndets": w.ndets,
+                   "C": w.C, "N": w.N, "eps": args.eps, "precision": args.precision,
+                   "excitations_per_step": pairs, "unique_per_step": stats.unique,
+                   "batches": stats.batches, "l2": "flushed (512 MB write) before each step",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+        "roofline": roofline, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

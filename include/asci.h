@@ -1,0 +1,192 @@
+/*
+ * libasci: GB300 (sm_103a) ASCI determinant search, C ABI.
+ *
+ * The library implements the search step of the Adaptive Sampling
+ * Configuration Interaction method (arXiv:2303.05688, Sec. 2.2, Algorithm 2,
+ * Eq. 1): from the core determinants of a wavefunction it enumerates every
+ * single and double excitation, evaluates H_ij by the Slater-Condon rules,
+ * accumulates the numerator sum_j H_ij c_j per unique target
+ * (sort-and-accumulate), scores each target outside psi as
+ * num / (E0 - H_ii) and keeps the N targets of largest |score|.
+ *
+ * Conventions shared by every entry point:
+ *  - A determinant is a pair of occupation words; bit p of `alpha` (`beta`) is
+ *    spatial orbital p of that spin.  The GPU path packs a determinant into one
+ *    64-bit key, so it accepts norb <= 32.
+ *  - The Hamiltonian is H = ecore + sum h_pq a+_ps a_qs
+ *    + 1/2 sum (pq|rs) a+_ps a+_rt a_st a_qs with real integrals, h1 symmetric
+ *    (row-major norb x norb) and eri in chemists' order, 8-fold symmetric,
+ *    eri[((p*norb+q)*norb+r)*norb+s] = (pq|rs).
+ *  - |D> = prod_{p in alpha asc} a+_{p,alpha} prod_{q in beta asc} a+_{q,beta}|0>;
+ *    a single p->q on one spin carries (-1)^(occupied orbitals of that spin
+ *    strictly between p and q); a same-spin double i<j -> a<b is i->a then j->b.
+ *  - 128-bit key order: beta word high, alpha word low.
+ *  - Pointers may be host or device memory (detected per pointer) unless an
+ *    entry point says "device".  The caller owns every buffer; the library
+ *    allocates its scratch on `cuda_stream` (stream-ordered) and frees it
+ *    before returning.  `cuda_stream` may be NULL (the legacy default stream).
+ *  - Every entry point returns ASCI_OK or a negative error code; no exception
+ *    crosses the boundary.  On error the outputs are unspecified and any
+ *    `*out_n` is set to 0.  Calls are synchronous with respect to the host:
+ *    they return after their results are in the output buffers.
+ */
+#ifndef ASCI_H
+#define ASCI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ASCI_OK 0
+#define ASCI_EINVAL (-1)   /* invalid argument or input data */
+#define ASCI_ENOMEM (-2)   /* device memory exhausted or a batch cannot fit */
+#define ASCI_ECUDA (-3)    /* a CUDA runtime call failed */
+#define ASCI_ETIMEOUT (-4) /* a bounded device-side wait gave up */
+
+/* One determinant: occupation words of the alpha and beta spin strings. */
+typedef struct {
+  uint64_t alpha;
+  uint64_t beta;
+} asci_det;
+
+/* One- and two-electron integrals (see conventions above). */
+typedef struct {
+  int32_t norb;      /* 1..32 */
+  double ecore;      /* constant added to every diagonal element */
+  const double *h1;  /* norb*norb */
+  const double *eri; /* norb^4 */
+} asci_ints;
+
+/* Arithmetic of the per-pair values and numerator sums (the diagonal, E0 and
+ * the denominator E0 - H_ii are FP64 in every mode). */
+enum {
+  ASCI_FP64 = 0,              /* FP64 integrals, FP64 products and sums */
+  ASCI_FP32_INT_FP64_ACC = 1, /* FP32-stored integrals, FP64 accumulation */
+  ASCI_FP32_INT_COMP_ACC = 2  /* FP32-stored integrals, compensated FP32 sums */
+};
+
+typedef struct {
+  /* Alg. 2 screen: keep the pair (target, core) only if |H_ij c_j / (E0 - H_ii)|
+   * > eps_search.  0 keeps every generated pair (the default; the paper's runs
+   * use 1e-10, Sec. 3). */
+  double eps_search;
+  /* Deepest constraint level (number of fixed highest occupied alpha orbitals,
+   * Sec. 2.2) the batch planner may refine to; 0 means no limit (n_alpha). */
+  int32_t max_constraint_level;
+  int32_t precision;         /* ASCI_FP64 | ASCI_FP32_INT_FP64_ACC | ASCI_FP32_INT_COMP_ACC */
+  uint64_t max_batch_pairs;  /* pairs per constraint batch; 0 = sized from free memory */
+  int32_t sort_output;       /* 1: outputs sorted by key ascending; 0: unspecified order */
+  int32_t reserved;
+} asci_opts;
+
+/* Counters and per-stage device times (milliseconds) of one search. */
+typedef struct {
+  uint64_t generated;  /* C * n_exc pairs enumerated */
+  uint64_t surviving;  /* pairs kept by the eps screen */
+  uint64_t unique;     /* unique targets after sort-and-accumulate */
+  uint64_t excluded;   /* unique targets dropped because they are in psi */
+  uint64_t selected;   /* *out_n */
+  uint64_t batches;    /* constraint batches run */
+  uint64_t max_batch;  /* pairs in the largest batch */
+  uint64_t ncore;      /* core determinants used (min(C, ndets)) */
+  uint64_t max_level;  /* deepest constraint level the planner used */
+  uint64_t reserved[3];
+  double t_stage[8];   /* prepare, plan, generate, sort, accumulate, score, select, total */
+} asci_stats;
+
+/* Fill `opts` with the defaults (eps 0, no level cap, FP64, auto batch, unsorted). */
+void asci_default_opts(asci_opts *opts);
+
+/* Library version string and the compute capability it was built for. */
+const char *asci_version(void);
+
+/* Human-readable text of an error code. */
+const char *asci_strerror(int code);
+
+/* Detail of the last error raised on the calling thread ("" if none). */
+const char *asci_last_error(void);
+
+/* Number of kernels this library has launched in the process so far. */
+unsigned long long asci_launch_count(void);
+
+/* Scratch memory is cached per device between calls (a stream-ordered pool);
+ * this returns the cached memory of the current device to the system. */
+void asci_trim_cache(void);
+
+/*
+ * The ASCI search (Algorithm 2 with Eq. 1; constraint batching of Sec. 2.2).
+ *
+ *  dets[ndets], coeffs[ndets]  the wavefunction psi (distinct determinants, all
+ *                              with the same alpha and beta electron counts).
+ *  E0                          the energy in the score's denominator E0 - H_ii.
+ *  ints                        integrals (the struct itself is host memory; its
+ *                              arrays may be host or device memory).
+ *  C                           core size: the C determinants of largest |c|
+ *                              (ties by key ascending); C > ndets is clamped.
+ *  N                           number of targets to return.
+ *  opts                        NULL for defaults.
+ *  out_dets[N], out_scores[N]  the selected targets and their signed scores
+ *                              S = num / (E0 - H_ii); *out_n = min(N, U) where
+ *                              U is the number of unique targets outside psi.
+ *                              Among equal |S| at the cutoff, smaller keys win.
+ *  stats                       may be NULL.
+ *
+ * Errors: ASCI_EINVAL for norb outside 1..32, ndets == 0, C == 0, NULL
+ * pointers, a determinant with bits at or above norb, mixed electron counts,
+ * duplicate determinants, or non-finite E0 / coefficients / integrals;
+ * ASCI_ENOMEM when scratch cannot be allocated; ASCI_ECUDA on CUDA failure.
+ */
+int asci_search(const asci_det *dets, const double *coeffs, size_t ndets, double E0,
+                const asci_ints *ints, size_t C, size_t N, const asci_opts *opts,
+                asci_det *out_dets, double *out_scores, size_t *out_n, asci_stats *stats,
+                void *cuda_stream);
+
+/*
+ * Generation stage of Algorithm 2 (the inner loops: "single and double
+ * connections from D_j" and the partial quantity H_ij C_j), for testing the
+ * excitation kernel in isolation.  For each core determinant, in input order,
+ * writes its n_exc targets and values v = H_ij * c_j in the library's fixed
+ * per-determinant order: alpha singles, beta singles, alpha-alpha doubles,
+ * beta-beta doubles, alpha-beta doubles (holes and particles ascending).
+ * All pointers are device memory; out_* hold capacity elements and
+ * *out_n = ncore * n_exc (ASCI_EINVAL if that exceeds capacity).
+ */
+int asci_excitations(const asci_ints *ints, const asci_det *core, const double *coeffs,
+                     size_t ncore, asci_det *out_targets, double *out_values, size_t capacity,
+                     size_t *out_n, void *cuda_stream);
+
+/*
+ * Diagonal elements H_ii = <D_i|H|D_i> (the denominator of Eq. 1).  Device
+ * pointers; dets[n] in, out_haa[n] out.
+ */
+int asci_diagonal(const asci_ints *ints, const asci_det *dets, size_t n, double *out_haa,
+                  void *cuda_stream);
+
+/*
+ * Sort-and-accumulate (Sec. 2.2): sorts the (key, value) pairs on the key and
+ * sums the values of each unique key.  Device pointers; out_keys / out_sums
+ * hold n elements; *out_n receives the number of unique keys, written in key
+ * order.  Equal keys are summed in input order.
+ */
+int asci_sort_accumulate(const asci_det *keys, const double *values, size_t n,
+                         asci_det *out_keys, double *out_sums, size_t *out_n,
+                         void *cuda_stream);
+
+/*
+ * Top-N selection by |score| (Sec. 2.2, the duplicate-aware selection that
+ * replaces a full sort): returns the min(N, n) entries of largest |score|,
+ * breaking ties at the cutoff by key ascending.  Keys must be distinct.
+ * Device pointers; output order unspecified.
+ */
+int asci_select_topn(const asci_det *keys, const double *scores, size_t n, size_t N,
+                     asci_det *out_keys, double *out_scores, size_t *out_n,
+                     void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASCI_H */

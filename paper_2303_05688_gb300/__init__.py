@@ -1,0 +1,322 @@
+"""Python binding of libasci, the GB300 ASCI determinant search (arXiv:2303.05688).
+
+Argument marshalling only: every step of the search runs in the CUDA kernels
+of ``lib/libasci.so`` behind the C ABI declared in ``include/asci.h``.  There is
+no CPU fallback; importing works without a GPU, but every call needs the built
+library and a CUDA device, and raises otherwise.
+
+Arrays may be numpy arrays (host memory; the library copies them in) or torch
+tensors on the CUDA device (used in place).  Determinants are uint64 pairs
+(alpha word, beta word); torch tensors may hold them as int64 bit patterns.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = ["load", "lib_path", "launch_count", "search", "excitations", "diagonal", "sort_accumulate",
+           "select_topn", "SearchStats", "AsciError", "FP64", "FP32_INT_FP64_ACC",
+           "FP32_INT_COMP_ACC"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "lib", "libasci.so")
+
+FP64, FP32_INT_FP64_ACC, FP32_INT_COMP_ACC = 0, 1, 2
+_ERRORS = {-1: "ASCI_EINVAL", -2: "ASCI_ENOMEM", -3: "ASCI_ECUDA", -4: "ASCI_ETIMEOUT"}
+
+
+class AsciError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {_ERRORS.get(code, code)}" + (f" ({detail})" if detail else ""))
+
+
+class _Det(ct.Structure):
+    _fields_ = [("alpha", ct.c_uint64), ("beta", ct.c_uint64)]
+
+
+class _Ints(ct.Structure):
+    _fields_ = [("norb", ct.c_int32), ("ecore", ct.c_double), ("h1", ct.c_void_p),
+                ("eri", ct.c_void_p)]
+
+
+class _Opts(ct.Structure):
+    _fields_ = [("eps_search", ct.c_double), ("max_constraint_level", ct.c_int32),
+                ("precision", ct.c_int32), ("max_batch_pairs", ct.c_uint64),
+                ("sort_output", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class _Stats(ct.Structure):
+    _fields_ = [("generated", ct.c_uint64), ("surviving", ct.c_uint64), ("unique", ct.c_uint64),
+                ("excluded", ct.c_uint64), ("selected", ct.c_uint64), ("batches", ct.c_uint64),
+                ("max_batch", ct.c_uint64), ("ncore", ct.c_uint64), ("max_level", ct.c_uint64),
+                ("reserved", ct.c_uint64 * 3), ("t_stage", ct.c_double * 8)]
+
+
+@dataclass
+class SearchStats:
+    generated: int
+    surviving: int
+    unique: int
+    excluded: int
+    selected: int
+    batches: int
+    max_batch: int
+    ncore: int
+    max_level: int
+    t_stage_ms: dict
+
+    @classmethod
+    def _from(cls, s: _Stats):
+        names = ["prepare", "plan", "generate", "sort_accumulate", "unused", "score", "select",
+                 "total"]
+        return cls(s.generated, s.surviving, s.unique, s.excluded, s.selected, s.batches,
+                   s.max_batch, s.ncore, s.max_level, {k: s.t_stage[i] for i, k in enumerate(names)})
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libasci.so (built by paper_2303_05688_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"libasci.so is not built ({_LIB_PATH}); run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ct.CDLL(_LIB_PATH)
+    vp, sz, szp = ct.c_void_p, ct.c_size_t, ct.POINTER(ct.c_size_t)
+    lib.asci_search.restype = ct.c_int
+    lib.asci_search.argtypes = [vp, vp, sz, ct.c_double, ct.POINTER(_Ints), sz, sz,
+                                ct.POINTER(_Opts), vp, vp, szp, ct.POINTER(_Stats), vp]
+    lib.asci_excitations.restype = ct.c_int
+    lib.asci_excitations.argtypes = [ct.POINTER(_Ints), vp, vp, sz, vp, vp, sz, szp, vp]
+    lib.asci_diagonal.restype = ct.c_int
+    lib.asci_diagonal.argtypes = [ct.POINTER(_Ints), vp, sz, vp, vp]
+    lib.asci_sort_accumulate.restype = ct.c_int
+    lib.asci_sort_accumulate.argtypes = [vp, vp, sz, vp, vp, szp, vp]
+    lib.asci_select_topn.restype = ct.c_int
+    lib.asci_select_topn.argtypes = [vp, vp, sz, sz, vp, vp, szp, vp]
+    lib.asci_default_opts.argtypes = [ct.POINTER(_Opts)]
+    lib.asci_version.restype = ct.c_char_p
+    lib.asci_strerror.restype = ct.c_char_p
+    lib.asci_strerror.argtypes = [ct.c_int]
+    lib.asci_last_error.restype = ct.c_char_p
+    lib.asci_launch_count.restype = ct.c_ulonglong
+    lib.asci_trim_cache.restype = None
+    _lib = lib
+    return lib
+
+
+def launch_count() -> int:
+    """Kernels launched by libasci in this process so far."""
+    return int(load().asci_launch_count())
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        detail = (load().asci_last_error() or b"").decode(errors="replace")
+        raise AsciError(code, where, detail)
+
+
+# ------------------------------- marshalling -------------------------------
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class _Buf:
+    """A contiguous buffer (host numpy or device torch) and its raw pointer."""
+
+    def __init__(self, obj, ptr, device: bool):
+        self.obj, self.ptr, self.device = obj, ptr, device
+
+
+def _as_buf(x, np_dtype, torch_dtype_name):
+    if _is_torch(x):
+        torch = _torch()
+        t = x.contiguous()
+        want = getattr(torch, torch_dtype_name)
+        if t.dtype != want:
+            if torch_dtype_name == "int64" and t.dtype == getattr(torch, "uint64", None):
+                t = t.view(torch.int64)
+            else:
+                t = t.to(want)
+        if not t.is_cuda:
+            t = t.cpu()
+            return _Buf(t, t.data_ptr(), False)
+        return _Buf(t, t.data_ptr(), True)
+    a = np.ascontiguousarray(x, dtype=np_dtype)
+    return _Buf(a, a.ctypes.data, False)
+
+
+def _dets_buf(dets):
+    """(n, 2) uint64 (alpha, beta) determinants, or a pair (alpha[n], beta[n])."""
+    if isinstance(dets, tuple) and len(dets) == 2:
+        a, b = dets
+        if _is_torch(a):
+            torch = _torch()
+            d = torch.stack([a.view(torch.int64) if a.dtype != torch.int64 else a,
+                             b.view(torch.int64) if b.dtype != torch.int64 else b], dim=1)
+            return _as_buf(d, np.uint64, "int64")
+        d = np.stack([np.asarray(a, dtype=np.uint64), np.asarray(b, dtype=np.uint64)], axis=1)
+        return _as_buf(d, np.uint64, "int64")
+    return _as_buf(dets, np.uint64, "int64")
+
+
+def _stream_ptr(stream, device: bool):
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    if device:
+        return int(_torch().cuda.current_stream().cuda_stream)
+    return None
+
+
+def _ints(h1, eri, ecore, keep):
+    hb = _as_buf(h1, np.float64, "float64")
+    eb = _as_buf(eri, np.float64, "float64")
+    keep += [hb, eb]
+    n = int(round(np.sqrt(np.prod(hb.obj.shape))))
+    return _Ints(n, float(ecore), hb.ptr, eb.ptr), hb.device
+
+
+def _out(n, dtype_np, device, cols=None):
+    shape = (n, cols) if cols else (n,)
+    if device:
+        torch = _torch()
+        tdt = {np.float64: torch.float64, np.uint64: torch.int64}[dtype_np]
+        t = torch.empty(shape, dtype=tdt, device="cuda")
+        return t, t.data_ptr()
+    a = np.empty(shape, dtype=dtype_np)
+    return a, a.ctypes.data
+
+
+# --------------------------------- calls -----------------------------------
+
+def search(dets, coeffs, E0: float, h1, eri, ecore: float, C: int, N: int, *,
+           eps: float = 0.0, precision: int = FP64, max_batch_pairs: int = 0,
+           max_constraint_level: int = 0, sort_output: bool = False, stream=None,
+           return_stats: bool = True):
+    """The ASCI search (Alg. 2 with Eq. 1).  Returns (dets[(m, 2)], scores[m], stats).
+
+    Outputs live where ``dets`` lives (device torch tensors in, device tensors out).
+    """
+    lib = load()
+    keep = []
+    db = _dets_buf(dets)
+    cb = _as_buf(coeffs, np.float64, "float64")
+    keep += [db, cb]
+    ints, _ = _ints(h1, eri, ecore, keep)
+    nd = int(db.obj.shape[0])
+    device = db.device
+    od, odp = _out(max(N, 1), np.uint64, device, 2)
+    os_, osp = _out(max(N, 1), np.float64, device)
+    opts = _Opts()
+    lib.asci_default_opts(ct.byref(opts))
+    opts.eps_search = float(eps)
+    opts.precision = int(precision)
+    opts.max_batch_pairs = int(max_batch_pairs)
+    opts.max_constraint_level = int(max_constraint_level)
+    opts.sort_output = 1 if sort_output else 0
+    st = _Stats()
+    n_out = ct.c_size_t(0)
+    code = lib.asci_search(db.ptr, cb.ptr, nd, float(E0), ct.byref(ints), int(C), int(N),
+                           ct.byref(opts), odp, osp, ct.byref(n_out), ct.byref(st),
+                           _stream_ptr(stream, device))
+    _check(code, "asci_search")
+    m = n_out.value
+    return od[:m], os_[:m], (SearchStats._from(st) if return_stats else None)
+
+
+def excitations(h1, eri, ecore, core_dets, core_coeffs, stream=None):
+    """Every single and double excitation of each core det with H_ij * c_j (device)."""
+    torch = _torch()
+    lib = load()
+    keep = []
+    db = _dets_buf(core_dets)
+    cb = _as_buf(core_coeffs, np.float64, "float64")
+    if not (db.device and cb.device):
+        raise ValueError("excitations() takes CUDA tensors")
+    keep += [db, cb]
+    ints, _ = _ints(h1, eri, ecore, keep)
+    n = ints.norb
+    a0 = int(db.obj[0, 0].item()) & ((1 << 64) - 1)
+    b0 = int(db.obj[0, 1].item()) & ((1 << 64) - 1)
+    na, nb = bin(a0).count("1"), bin(b0).count("1")
+    from math import comb
+    va, vb = n - na, n - nb
+    nexc = na * va + nb * vb + comb(na, 2) * comb(va, 2) + comb(nb, 2) * comb(vb, 2) + na * va * nb * vb
+    total = nexc * int(db.obj.shape[0])
+    ot = torch.empty((max(total, 1), 2), dtype=torch.int64, device="cuda")
+    ov = torch.empty(max(total, 1), dtype=torch.float64, device="cuda")
+    n_out = ct.c_size_t(0)
+    code = lib.asci_excitations(ct.byref(ints), db.ptr, cb.ptr, int(db.obj.shape[0]),
+                                ot.data_ptr(), ov.data_ptr(), total, ct.byref(n_out),
+                                _stream_ptr(stream, True))
+    _check(code, "asci_excitations")
+    return ot[:n_out.value], ov[:n_out.value]
+
+
+def diagonal(h1, eri, ecore, dets, stream=None):
+    """H_ii of each determinant (device)."""
+    torch = _torch()
+    lib = load()
+    keep = []
+    db = _dets_buf(dets)
+    if not db.device:
+        raise ValueError("diagonal() takes CUDA tensors")
+    keep.append(db)
+    ints, _ = _ints(h1, eri, ecore, keep)
+    out = torch.empty(int(db.obj.shape[0]), dtype=torch.float64, device="cuda")
+    _check(lib.asci_diagonal(ct.byref(ints), db.ptr, int(db.obj.shape[0]), out.data_ptr(),
+                             _stream_ptr(stream, True)), "asci_diagonal")
+    return out
+
+
+def sort_accumulate(keys, values, stream=None):
+    """Sort (det, value) pairs on the det and sum per unique det (device)."""
+    torch = _torch()
+    lib = load()
+    kb = _dets_buf(keys)
+    vb = _as_buf(values, np.float64, "float64")
+    if not (kb.device and vb.device):
+        raise ValueError("sort_accumulate() takes CUDA tensors")
+    n = int(kb.obj.shape[0])
+    ok = torch.empty((max(n, 1), 2), dtype=torch.int64, device="cuda")
+    os_ = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    n_out = ct.c_size_t(0)
+    _check(lib.asci_sort_accumulate(kb.ptr, vb.ptr, n, ok.data_ptr(), os_.data_ptr(),
+                                    ct.byref(n_out), _stream_ptr(stream, True)),
+           "asci_sort_accumulate")
+    return ok[:n_out.value], os_[:n_out.value]
+
+
+def select_topn(keys, scores, N: int, stream=None):
+    """Top-N by |score|, ties by key ascending (device)."""
+    torch = _torch()
+    lib = load()
+    kb = _dets_buf(keys)
+    sb = _as_buf(scores, np.float64, "float64")
+    if not (kb.device and sb.device):
+        raise ValueError("select_topn() takes CUDA tensors")
+    n = int(kb.obj.shape[0])
+    m = max(min(n, N), 1)
+    ok = torch.empty((m, 2), dtype=torch.int64, device="cuda")
+    os_ = torch.empty(m, dtype=torch.float64, device="cuda")
+    n_out = ct.c_size_t(0)
+    _check(lib.asci_select_topn(kb.ptr, sb.ptr, n, int(N), ok.data_ptr(), os_.data_ptr(),
+                                ct.byref(n_out), _stream_ptr(stream, True)), "asci_select_topn")
+    return ok[:n_out.value], os_[:n_out.value]

@@ -1,0 +1,206 @@
+// Internal declarations of libasci (GPU path).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <vector>
+
+#include "asci.h"
+
+namespace asci {
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+
+void record_error(const char *what, const char *file, int line);
+
+// Library-owned stream-ordered memory pool of a device (kept cached between calls).
+int device_pool(int dev, cudaMemPool_t *pool);
+
+#define ASCI_TRY_CUDA(expr)                                 \
+  do {                                                      \
+    cudaError_t e__ = (expr);                               \
+    if (e__ != cudaSuccess) {                               \
+      ::asci::record_error(cudaGetErrorString(e__), __FILE__, __LINE__); \
+      return (e__ == cudaErrorMemoryAllocation) ? ASCI_ENOMEM : ASCI_ECUDA; \
+    }                                                       \
+  } while (0)
+
+#define ASCI_TRY(expr)              \
+  do {                              \
+    int r__ = (expr);               \
+    if (r__ != ASCI_OK) return r__; \
+  } while (0)
+
+// Every kernel launch is followed by ASCI_CHECK_LAUNCH, which also counts it
+// (asci_launch_count() reports the total, for launch accounting by callers).
+void count_launch();
+#define ASCI_CHECK_LAUNCH()  \
+  do {                       \
+    ::asci::count_launch();  \
+    ASCI_TRY_CUDA(cudaGetLastError()); \
+  } while (0)
+
+// Stream-ordered scratch arena: every allocation is released when the arena
+// goes out of scope (cudaFreeAsync on the same stream).
+class Arena {
+ public:
+  explicit Arena(cudaStream_t s) : stream_(s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && device_pool(dev, &pool_) != ASCI_OK) pool_ = nullptr;
+  }
+  ~Arena() { release(); }
+  Arena(const Arena &) = delete;
+  Arena &operator=(const Arena &) = delete;
+  template <typename T>
+  int alloc(T **p, size_t count) {
+    void *q = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = pool_ ? cudaMallocFromPoolAsync(&q, bytes, pool_, stream_)
+                          : cudaMallocAsync(&q, bytes, stream_);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      record_error(cudaGetErrorString(e), __FILE__, __LINE__);
+      *p = nullptr;
+      return ASCI_ENOMEM;
+    }
+    ptrs_.push_back(q);
+    *p = static_cast<T *>(q);
+    return ASCI_OK;
+  }
+  void release() {
+    for (void *q : ptrs_) cudaFreeAsync(q, stream_);
+    ptrs_.clear();
+  }
+  cudaStream_t stream() const { return stream_; }
+
+ private:
+  cudaStream_t stream_;
+  cudaMemPool_t pool_ = nullptr;
+  std::vector<void *> ptrs_;
+};
+
+// ---------------------------------------------------------------------------
+// determinants and keys
+// ---------------------------------------------------------------------------
+
+// Packed 64-bit key of a determinant (norb <= 32): beta word high, alpha word
+// low, so that unsigned order equals the 128-bit key order.
+__host__ __device__ inline uint64_t pack_key(uint32_t a, uint32_t b) {
+  return ((uint64_t)b << 32) | (uint64_t)a;
+}
+__host__ __device__ inline uint32_t key_alpha(uint64_t k) { return (uint32_t)k; }
+__host__ __device__ inline uint32_t key_beta(uint64_t k) { return (uint32_t)(k >> 32); }
+
+// Sign of the single p -> q on string s: (-1)^popc(s & bits strictly between).
+__device__ __forceinline__ int single_parity(uint32_t s, int p, int q) {
+  int lo = p < q ? p : q, hi = p < q ? q : p;
+  uint32_t between = ((hi >= 32) ? 0xffffffffu : ((1u << hi) - 1u)) & ~((2u << lo) - 1u);
+  return __popc(s & between) & 1;
+}
+
+// Position of the k-th (0-based) set bit of w; w must hold more than k bits.
+__device__ __forceinline__ int nth_set_bit(uint32_t w, int k) {
+  int pos = 0, c;
+  c = __popc(w & 0xffffu);
+  if (k >= c) { k -= c; w >>= 16; pos += 16; }
+  c = __popc(w & 0xffu);
+  if (k >= c) { k -= c; w >>= 8; pos += 8; }
+  c = __popc(w & 0xfu);
+  if (k >= c) { k -= c; w >>= 4; pos += 4; }
+  c = __popc(w & 0x3u);
+  if (k >= c) { k -= c; w >>= 2; pos += 2; }
+  c = (int)(w & 1u);
+  if (k >= c) pos += 1;
+  return pos;
+}
+
+// Colex unranking of a pair x < y: r = y(y-1)/2 + x.
+__device__ __forceinline__ void unrank_pair(uint32_t r, int *x, int *y) {
+  int yy = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)r)) * 0.5f);
+  while ((uint32_t)(yy * (yy - 1) / 2) > r) --yy;
+  while ((uint32_t)((yy + 1) * yy / 2) <= r) ++yy;
+  *y = yy;
+  *x = (int)(r - (uint32_t)(yy * (yy - 1) / 2));
+}
+
+// ---------------------------------------------------------------------------
+// integral tables resident on the device for one search
+// ---------------------------------------------------------------------------
+
+struct DevInts {
+  int n, na, nb;
+  double ecore;
+  const double *h1;     // n*n
+  const double *eri;    // n^4, (pq|rs)
+  const double *asym;   // n^4, [((i*n+a)*n+j)*n+b] = (ia|jb) - (ib|ja)
+  const double *s_same; // n^3, [(i*n+a)*n+k] = (ia|kk) - (ik|ka)
+  const double *s_opp;  // n^3, [(i*n+a)*n+k] = (ia|kk)
+  const double *jk;     // n*n, (pp|qq) - (pq|qp)
+  const double *jj;     // n*n, (pp|qq)
+  const float *eri32;   // n^4 FP32 copy (precision variants)
+  const float *asym32;  // n^4 FP32 copy
+};
+
+// Counts of one determinant's excitations (Sec. 2.1: singles and doubles).
+struct ExcCounts {
+  uint32_t na, nb, va, vb;
+  uint32_t sa, sb;      // singles per spin: n v
+  uint32_t pa_h, pa_p;  // C(na,2), C(va,2)
+  uint32_t pb_h, pb_p;  // C(nb,2), C(vb,2)
+  uint64_t daa, dbb, dab, total;
+};
+
+ExcCounts exc_counts(int n, int na, int nb);
+
+// Host-side build of the derived integral tables from h1 / eri already on the device.
+int build_tables(const double *h1_dev, const double *eri_dev, int n, int na, int nb, double ecore,
+                 bool want_fp32, Arena &arena, DevInts *out);
+
+// ---------------------------------------------------------------------------
+// primitives (sort.cu)
+// ---------------------------------------------------------------------------
+
+// Exclusive prefix sum, device-wide; in and out may alias.
+int scan_exclusive_u32(const uint32_t *in, uint32_t *out, size_t n, Arena &arena);
+int scan_exclusive_u64(const uint64_t *in, uint64_t *out, size_t n, Arena &arena);
+
+// Stable LSD radix sort of 64-bit keys on bits [begin_bit, end_bit), with an
+// optional payload.  The sorted data ends in *keys / *vals (the two buffers of
+// each pair are swapped as passes proceed).  n < 2^32.
+int radix_sort_u64(uint64_t **keys, uint64_t **keys_alt, size_t n, int begin_bit, int end_bit,
+                   Arena &arena);
+int radix_sort_u64_u32(uint64_t **keys, uint64_t **keys_alt, uint32_t **vals, uint32_t **vals_alt,
+                       size_t n, int begin_bit, int end_bit, Arena &arena);
+int radix_sort_u64_f64(uint64_t **keys, uint64_t **keys_alt, double **vals, double **vals_alt,
+                       size_t n, int begin_bit, int end_bit, Arena &arena);
+
+// Bits in which the keys differ (OR of key ^ keys[0]); result on the host.
+int varying_bits_u64(const uint64_t *keys, size_t n, uint64_t *host_mask, Arena &arena);
+
+// ---------------------------------------------------------------------------
+// stages
+// ---------------------------------------------------------------------------
+
+// Sort-and-accumulate of packed (key, value) pairs: sorts in place (buffers
+// may be swapped) and writes unique keys and sums.  Returns U on the host.
+int sort_accumulate(uint64_t **keys, uint64_t **keys_alt, double **vals, double **vals_alt,
+                    size_t n, uint64_t *ukeys, double *usums, size_t *host_u, Arena &arena);
+
+// H_ii of packed keys.
+int diagonal_packed(const DevInts &I, const uint64_t *keys, size_t n, double *out, Arena &arena);
+
+// Top-N by |score| with key tie-break; compacts into out arrays (may not alias
+// the inputs).  Returns the count on the host.
+int select_topn_packed(const uint64_t *keys, const double *scores, size_t n, size_t N,
+                       uint64_t *out_keys, double *out_scores, size_t *host_out_n, Arena &arena);
+
+// Excitation emission in the fixed per-determinant order (component entry).
+int emit_fixed_order(const DevInts &I, const uint64_t *core_keys, const double *core_c,
+                     size_t ncore, uint64_t *out_keys, double *out_vals, Arena &arena);
+
+}  // namespace asci

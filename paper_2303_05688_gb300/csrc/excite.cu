@@ -1,0 +1,450 @@
+// Excitation generation (Algorithm 2's inner loops) and the derived integral
+// tables it reads.
+//
+// Every single and double excitation of a core determinant D_j is addressed by
+// an index, decoded with popcount arithmetic (k-th set bit, colex pair
+// unranking), and evaluated by the Slater-Condon rules with fermionic phases:
+//   single i->a (spin s, other spin o):
+//       sign * [h_ia + sum_{k in s} ((ia|kk) - (ik|ka)) + sum_{k in o} (ia|kk)]
+//   same-spin double i<j -> a<b:  sign * [(ia|jb) - (ib|ja)], sign = i->a then j->b
+//   opposite-spin double:         sign_alpha * sign_beta * (ia|jb)
+// The partial quantity written per pair is v = H_ij * c_j (Alg. 2 with Eq. 1's
+// numerator).
+#include "asci_internal.cuh"
+
+namespace asci {
+
+ExcCounts exc_counts(int n, int na, int nb) {
+  ExcCounts x;
+  x.na = na;
+  x.nb = nb;
+  x.va = n - na;
+  x.vb = n - nb;
+  x.sa = x.na * x.va;
+  x.sb = x.nb * x.vb;
+  x.pa_h = x.na * (x.na - (x.na ? 1 : 0)) / 2;
+  x.pa_p = x.va * (x.va - (x.va ? 1 : 0)) / 2;
+  x.pb_h = x.nb * (x.nb - (x.nb ? 1 : 0)) / 2;
+  x.pb_p = x.vb * (x.vb - (x.vb ? 1 : 0)) / 2;
+  x.daa = (uint64_t)x.pa_h * x.pa_p;
+  x.dbb = (uint64_t)x.pb_h * x.pb_p;
+  x.dab = (uint64_t)x.sa * x.sb;
+  x.total = (uint64_t)x.sa + x.sb + x.daa + x.dbb + x.dab;
+  return x;
+}
+
+namespace {
+
+// ------------------------------ tables -------------------------------------
+
+__global__ void k_tables_n4(const double *eri, int n, double *asym, float *eri32, float *asym32) {
+  size_t n4 = (size_t)n * n * n * n;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4;
+       t += (size_t)gridDim.x * blockDim.x) {
+    int b = (int)(t % n), j = (int)((t / n) % n), a = (int)((t / n / n) % n), i = (int)(t / n / n / n);
+    double v = eri[t] - eri[(((size_t)i * n + b) * n + j) * n + a];
+    asym[t] = v;
+    if (eri32) eri32[t] = (float)eri[t];
+    if (asym32) asym32[t] = (float)v;
+  }
+}
+
+__global__ void k_tables_n3(const double *eri, int n, double *s_same, double *s_opp) {
+  size_t n3 = (size_t)n * n * n;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n3;
+       t += (size_t)gridDim.x * blockDim.x) {
+    int k = (int)(t % n), a = (int)((t / n) % n), i = (int)(t / n / n);
+    double iakk = eri[(((size_t)i * n + a) * n + k) * n + k];
+    double ikka = eri[(((size_t)i * n + k) * n + k) * n + a];
+    s_same[t] = iakk - ikka;
+    s_opp[t] = iakk;
+  }
+}
+
+__global__ void k_tables_n2(const double *eri, int n, double *jk, double *jj) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  int p = t / n, q = t % n;
+  double J = eri[(((size_t)p * n + p) * n + q) * n + q];
+  double K = eri[(((size_t)p * n + q) * n + q) * n + p];
+  jj[t] = J;
+  jk[t] = J - K;
+}
+
+// ------------------------------ evaluation ---------------------------------
+
+__device__ __forceinline__ double single_value(const DevInts &I, uint32_t s, uint32_t o, int i,
+                                               int a) {
+  const int n = I.n;
+  const double *ss = I.s_same + ((size_t)i * n + a) * n;
+  const double *so = I.s_opp + ((size_t)i * n + a) * n;
+  double v = I.h1[i * n + a];
+  for (uint32_t m = s; m; m &= m - 1) v += ss[__ffs(m) - 1];
+  for (uint32_t m = o; m; m &= m - 1) v += so[__ffs(m) - 1];
+  return v;
+}
+
+__device__ __forceinline__ double eri4(const double *t, int n, int i, int a, int j, int b) {
+  return t[(((size_t)i * n + a) * n + j) * n + b];
+}
+
+__device__ __forceinline__ void decode_single(uint32_t s, uint32_t virt, uint32_t idx, uint32_t nv,
+                                              int *i, int *a) {
+  *i = nth_set_bit(s, (int)(idx / nv));
+  *a = nth_set_bit(virt, (int)(idx % nv));
+}
+
+__device__ __forceinline__ void decode_double(uint32_t s, uint32_t virt, uint32_t idx,
+                                              uint32_t npp, int *i, int *j, int *a, int *b) {
+  int h1, h2, p1, p2;
+  unrank_pair(idx / npp, &h1, &h2);
+  unrank_pair(idx % npp, &p1, &p2);
+  *i = nth_set_bit(s, h1);
+  *j = nth_set_bit(s, h2);
+  *a = nth_set_bit(virt, p1);
+  *b = nth_set_bit(virt, p2);
+}
+
+__device__ __forceinline__ int double_parity(uint32_t s, int i, int j, int a, int b) {
+  int p1 = single_parity(s, i, a);
+  uint32_t s1 = s ^ (1u << i) ^ (1u << a);
+  return p1 ^ single_parity(s1, j, b);
+}
+
+__device__ __forceinline__ uint32_t full_mask(int n) {
+  return n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+}
+
+// Excitation e (fixed order) of determinant (A, B): target and H_ij.
+__device__ void fixed_order_pair(const DevInts &I, const ExcCounts &X, uint32_t A, uint32_t B,
+                                 uint64_t e, uint32_t *ta, uint32_t *tb, double *h) {
+  const uint32_t full = full_mask(I.n);
+  const uint32_t va = ~A & full, vb = ~B & full;
+  int i, j, a, b;
+  if (e < X.sa) {
+    decode_single(A, va, (uint32_t)e, X.va, &i, &a);
+    *ta = A ^ (1u << i) ^ (1u << a);
+    *tb = B;
+    double v = single_value(I, A, B, i, a);
+    *h = single_parity(A, i, a) ? -v : v;
+    return;
+  }
+  e -= X.sa;
+  if (e < X.sb) {
+    decode_single(B, vb, (uint32_t)e, X.vb, &i, &a);
+    *ta = A;
+    *tb = B ^ (1u << i) ^ (1u << a);
+    double v = single_value(I, B, A, i, a);
+    *h = single_parity(B, i, a) ? -v : v;
+    return;
+  }
+  e -= X.sb;
+  if (e < X.daa) {
+    decode_double(A, va, (uint32_t)e, X.pa_p, &i, &j, &a, &b);
+    *ta = A ^ (1u << i) ^ (1u << j) ^ (1u << a) ^ (1u << b);
+    *tb = B;
+    double v = eri4(I.asym, I.n, i, a, j, b);
+    *h = double_parity(A, i, j, a, b) ? -v : v;
+    return;
+  }
+  e -= X.daa;
+  if (e < X.dbb) {
+    decode_double(B, vb, (uint32_t)e, X.pb_p, &i, &j, &a, &b);
+    *ta = A;
+    *tb = B ^ (1u << i) ^ (1u << j) ^ (1u << a) ^ (1u << b);
+    double v = eri4(I.asym, I.n, i, a, j, b);
+    *h = double_parity(B, i, j, a, b) ? -v : v;
+    return;
+  }
+  e -= X.dbb;
+  {
+    decode_single(A, va, (uint32_t)(e / X.sb), X.va, &i, &a);
+    decode_single(B, vb, (uint32_t)(e % X.sb), X.vb, &j, &b);
+    *ta = A ^ (1u << i) ^ (1u << a);
+    *tb = B ^ (1u << j) ^ (1u << b);
+    double v = eri4(I.eri, I.n, i, a, j, b);
+    *h = (single_parity(A, i, a) ^ single_parity(B, j, b)) ? -v : v;
+  }
+}
+
+__global__ void k_emit_fixed(DevInts I, ExcCounts X, const uint64_t *core_keys,
+                             const double *core_c, size_t ncore, uint64_t *out_keys,
+                             double *out_vals) {
+  const uint64_t total = (uint64_t)ncore * X.total;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t m = p / X.total, e = p - m * X.total;
+    uint64_t k = core_keys[m];
+    uint32_t ta, tb;
+    double h;
+    fixed_order_pair(I, X, key_alpha(k), key_beta(k), e, &ta, &tb, &h);
+    out_keys[p] = pack_key(ta, tb);
+    out_vals[p] = h * core_c[m];
+  }
+}
+
+}  // namespace
+
+int build_tables(const double *h1_dev, const double *eri_dev, int n, int na, int nb, double ecore,
+                 bool want_fp32, Arena &arena, DevInts *out) {
+  DevInts I;
+  I.n = n;
+  I.na = na;
+  I.nb = nb;
+  I.ecore = ecore;
+  I.h1 = h1_dev;
+  I.eri = eri_dev;
+  size_t n2 = (size_t)n * n, n3 = n2 * n, n4 = n3 * n;
+  double *asym, *s_same, *s_opp, *jk, *jj;
+  float *eri32 = nullptr, *asym32 = nullptr;
+  ASCI_TRY(arena.alloc(&asym, n4));
+  ASCI_TRY(arena.alloc(&s_same, n3));
+  ASCI_TRY(arena.alloc(&s_opp, n3));
+  ASCI_TRY(arena.alloc(&jk, n2));
+  ASCI_TRY(arena.alloc(&jj, n2));
+  if (want_fp32) {
+    ASCI_TRY(arena.alloc(&eri32, n4));
+    ASCI_TRY(arena.alloc(&asym32, n4));
+  }
+  cudaStream_t s = arena.stream();
+  k_tables_n4<<<(unsigned)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096), 256, 0, s>>>(
+      eri_dev, n, asym, eri32, asym32);
+  ASCI_CHECK_LAUNCH();
+  k_tables_n3<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(eri_dev, n, s_same, s_opp);
+  ASCI_CHECK_LAUNCH();
+  k_tables_n2<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(eri_dev, n, jk, jj);
+  ASCI_CHECK_LAUNCH();
+  I.asym = asym;
+  I.s_same = s_same;
+  I.s_opp = s_opp;
+  I.jk = jk;
+  I.jj = jj;
+  I.eri32 = eri32;
+  I.asym32 = asym32;
+  *out = I;
+  return ASCI_OK;
+}
+
+int emit_fixed_order(const DevInts &I, const uint64_t *core_keys, const double *core_c,
+                     size_t ncore, uint64_t *out_keys, double *out_vals, Arena &arena) {
+  ExcCounts X = exc_counts(I.n, I.na, I.nb);
+  uint64_t total = (uint64_t)ncore * X.total;
+  if (total == 0) return ASCI_OK;
+  uint64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_emit_fixed<<<(unsigned)blocks, 256, 0, arena.stream()>>>(I, X, core_keys, core_c, ncore,
+                                                             out_keys, out_vals);
+  ASCI_CHECK_LAUNCH();
+  return ASCI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// constraint-batched generation
+// ---------------------------------------------------------------------------
+//
+// The core determinants are grouped by alpha string (group k holds the core
+// dets with alpha string A_k).  An "item" is (group k, alpha operation o): no
+// alpha change (o = 0), an alpha single (1 <= o <= sa) or an alpha-alpha double.
+// It fixes the target's alpha string A' and therefore its constraint class:
+// the class of a determinant at level L is the set of its L highest occupied
+// alpha orbitals (Sec. 2.2, triplet constraints and their refinements), and
+// classes are contiguous ranges once items are sorted by A'.  Each item emits
+// its pairs for every core det of its group:
+//   o = 0:      beta singles and beta-beta doubles      (sb + dbb per det)
+//   single:     the alpha single itself and the alpha-beta doubles (1 + sb)
+//   double:     the alpha-alpha double                  (1)
+
+namespace {
+
+__global__ void k_make_items(ExcCounts X, int n, const uint32_t *grp_alpha, uint32_t ngroups,
+                             uint32_t o_begin, uint32_t nops, int opbits, uint64_t *items) {
+  const uint32_t per = nops - o_begin;
+  const uint64_t total = (uint64_t)ngroups * per;
+  const uint32_t full = full_mask(n);
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t k = (uint32_t)(t / per), o = o_begin + (uint32_t)(t % per);
+    uint32_t A = grp_alpha[k], va = ~A & full, At = A;
+    int i, j, a, b;
+    if (o == 0) {
+      At = A;
+    } else if (o <= X.sa) {
+      decode_single(A, va, o - 1, X.va, &i, &a);
+      At = A ^ (1u << i) ^ (1u << a);
+    } else {
+      decode_double(A, va, o - 1 - X.sa, X.pa_p, &i, &j, &a, &b);
+      At = A ^ (1u << i) ^ (1u << j) ^ (1u << a) ^ (1u << b);
+    }
+    items[t] = ((uint64_t)At << 32) | ((uint64_t)k << opbits) | o;
+  }
+}
+
+__global__ void k_item_weights(const uint64_t *items, uint64_t nitems, int opbits,
+                               const uint32_t *grp_count, ExcCounts X, uint64_t *w) {
+  const uint32_t omask = (1u << opbits) - 1u;
+  const uint64_t npd0 = (uint64_t)X.sb + X.dbb, npd1 = 1ull + X.sb;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nitems;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t lo = (uint32_t)items[t];
+    uint32_t k = lo >> opbits, o = lo & omask;
+    uint64_t npd = (o == 0) ? npd0 : (o <= X.sa ? npd1 : 1ull);
+    w[t] = npd * grp_count[k];
+  }
+}
+
+constexpr int kEmitThreads = 256;
+constexpr int kEmitPer = 4;
+constexpr int kEmitTile = kEmitThreads * kEmitPer;
+
+// One CTA per tile of kEmitTile consecutive pair indices of the batch.  The
+// items overlapping the tile (at most kEmitTile, every item having >= 1 pair)
+// and their starting pair offsets are staged in shared memory; each pair finds
+// its item by binary search there, then decodes (core det, excitation).
+__global__ void __launch_bounds__(kEmitThreads)
+    k_emit_batch(DevInts I, ExcCounts X, const uint64_t *items, const uint64_t *Wexcl,
+                 uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1, int opbits,
+                 const uint32_t *grp_alpha, const uint32_t *grp_start, const uint32_t *core_beta,
+                 const double *core_c, uint64_t *out_keys, double *out_vals) {
+  __shared__ uint64_t sW[kEmitTile];
+  __shared__ uint64_t sIt[kEmitTile];
+  __shared__ uint64_t s_ta, s_nspan;
+  const uint64_t pb = P0 + (uint64_t)blockIdx.x * kEmitTile;
+  const uint64_t pe = (pb + kEmitTile < P1) ? pb + kEmitTile : P1;
+  if (threadIdx.x == 0) {
+    // last item whose start offset is <= pb, then last item starting <= pe-1
+    uint64_t lo = t0, hi = t1 - 1;
+    while (lo < hi) {
+      uint64_t mid = (lo + hi + 1) >> 1;
+      if (Wexcl[mid] <= pb) lo = mid; else hi = mid - 1;
+    }
+    uint64_t ta = lo;
+    hi = t1 - 1;
+    while (lo < hi) {
+      uint64_t mid = (lo + hi + 1) >> 1;
+      if (Wexcl[mid] <= pe - 1) lo = mid; else hi = mid - 1;
+    }
+    s_ta = ta;
+    s_nspan = lo - ta + 1;
+  }
+  __syncthreads();
+  const uint64_t ta = s_ta;
+  const int nspan = (int)s_nspan;
+  for (int i = threadIdx.x; i < nspan; i += kEmitThreads) {
+    sIt[i] = items[ta + i];
+    sW[i] = Wexcl[ta + i];
+  }
+  __syncthreads();
+  const uint32_t full = full_mask(I.n);
+  const uint32_t omask = (1u << opbits) - 1u;
+  const uint32_t npd0 = X.sb + (uint32_t)X.dbb, npd1 = 1u + X.sb;
+#pragma unroll 1
+  for (int r = 0; r < kEmitPer; ++r) {
+    const uint64_t p = pb + (uint64_t)r * kEmitThreads + threadIdx.x;
+    if (p >= pe) continue;
+    int lo = 0, hi = nspan - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (sW[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    const uint64_t it = sIt[lo];
+    const uint32_t q = (uint32_t)(p - sW[lo]);
+    const uint32_t At = (uint32_t)(it >> 32);
+    const uint32_t k = (uint32_t)it >> opbits, o = (uint32_t)it & omask;
+    const uint32_t A = grp_alpha[k], va = ~A & full;
+    uint32_t ta = At, tb;
+    double h;
+    if (o == 0) {
+      // beta singles, then beta-beta doubles of core det m
+      const uint32_t m = q / npd0, e = q - m * npd0;
+      const uint32_t jdx = grp_start[k] + m;
+      const uint32_t B = core_beta[jdx], vb = ~B & full;
+      int i, j, a, b;
+      if (e < X.sb) {
+        decode_single(B, vb, e, X.vb, &i, &a);
+        tb = B ^ (1u << i) ^ (1u << a);
+        double v = single_value(I, B, A, i, a);
+        h = single_parity(B, i, a) ? -v : v;
+      } else {
+        decode_double(B, vb, e - X.sb, X.pb_p, &i, &j, &a, &b);
+        tb = B ^ (1u << i) ^ (1u << j) ^ (1u << a) ^ (1u << b);
+        double v = eri4(I.asym, I.n, i, a, j, b);
+        h = double_parity(B, i, j, a, b) ? -v : v;
+      }
+      out_keys[p - P0] = pack_key(ta, tb);
+      out_vals[p - P0] = h * core_c[jdx];
+    } else if (o <= X.sa) {
+      // the alpha single itself (e == 0) or alpha single x beta single
+      const uint32_t m = q / npd1, e = q - m * npd1;
+      const uint32_t jdx = grp_start[k] + m;
+      const uint32_t B = core_beta[jdx];
+      int i, a;
+      decode_single(A, va, o - 1, X.va, &i, &a);
+      const int pa = single_parity(A, i, a);
+      if (e == 0) {
+        tb = B;
+        double v = single_value(I, A, B, i, a);
+        h = pa ? -v : v;
+      } else {
+        const uint32_t vb = ~B & full;
+        int j, b;
+        decode_single(B, vb, e - 1, X.vb, &j, &b);
+        tb = B ^ (1u << j) ^ (1u << b);
+        double v = eri4(I.eri, I.n, i, a, j, b);
+        h = (pa ^ single_parity(B, j, b)) ? -v : v;
+      }
+      out_keys[p - P0] = pack_key(ta, tb);
+      out_vals[p - P0] = h * core_c[jdx];
+    } else {
+      // alpha-alpha double, one pair per core det
+      const uint32_t jdx = grp_start[k] + q;
+      int i, j, a, b;
+      decode_double(A, va, o - 1 - X.sa, X.pa_p, &i, &j, &a, &b);
+      double v = eri4(I.asym, I.n, i, a, j, b);
+      h = double_parity(A, i, j, a, b) ? -v : v;
+      tb = core_beta[jdx];
+      out_keys[p - P0] = pack_key(ta, tb);
+      out_vals[p - P0] = h * core_c[jdx];
+    }
+  }
+}
+
+}  // namespace
+
+int make_items(const ExcCounts &X, int n, const uint32_t *grp_alpha, uint32_t ngroups,
+               uint32_t o_begin, uint32_t nops, int opbits, uint64_t *items, Arena &arena) {
+  uint64_t total = (uint64_t)ngroups * (nops - o_begin);
+  if (!total) return ASCI_OK;
+  uint64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_make_items<<<(unsigned)blocks, 256, 0, arena.stream()>>>(X, n, grp_alpha, ngroups, o_begin,
+                                                             nops, opbits, items);
+  ASCI_CHECK_LAUNCH();
+  return ASCI_OK;
+}
+
+int item_weights(const uint64_t *items, uint64_t nitems, int opbits, const uint32_t *grp_count,
+                 const ExcCounts &X, uint64_t *w, Arena &arena) {
+  if (!nitems) return ASCI_OK;
+  uint64_t blocks = (nitems + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_item_weights<<<(unsigned)blocks, 256, 0, arena.stream()>>>(items, nitems, opbits, grp_count,
+                                                               X, w);
+  ASCI_CHECK_LAUNCH();
+  return ASCI_OK;
+}
+
+int emit_batch(const DevInts &I, const ExcCounts &X, const uint64_t *items, const uint64_t *Wexcl,
+               uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1, int opbits,
+               const uint32_t *grp_alpha, const uint32_t *grp_start, const uint32_t *core_beta,
+               const double *core_c, uint64_t *out_keys, double *out_vals, Arena &arena) {
+  if (P1 <= P0) return ASCI_OK;
+  uint64_t tiles = (P1 - P0 + kEmitTile - 1) / kEmitTile;
+  if (tiles >= (1ull << 31)) return ASCI_EINVAL;
+  k_emit_batch<<<(unsigned)tiles, kEmitThreads, 0, arena.stream()>>>(
+      I, X, items, Wexcl, t0, t1, P0, P1, opbits, grp_alpha, grp_start, core_beta, core_c,
+      out_keys, out_vals);
+  ASCI_CHECK_LAUNCH();
+  return ASCI_OK;
+}
+
+}  // namespace asci

@@ -1,0 +1,995 @@
+// Host orchestration of the ASCI search and the C ABI (include/asci.h).
+//
+// Pipeline of one search (Algorithm 2, batched by constraints of Sec. 2.2):
+//   prepare   stage inputs, validate, sort psi's keys, select the core
+//             (largest |c|, ties by key), group the core by alpha string
+//   plan      build the items (group, alpha operation) with their target alpha
+//             strings, sort them by that string, weigh them (pairs per item),
+//             and cut the item list into batches at constraint-class
+//             boundaries, refining heavy classes level by level (triplets,
+//             quadruplets, ... up to single alpha strings)
+//   per batch generate pairs -> sort -> accumulate -> exclude psi, H_ii, score
+//             -> merge into a running candidate pool (pruned to the top N)
+//   select    top N of the pool (radix select on |S|, key tie-break)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "asci_internal.cuh"
+
+namespace asci {
+
+int make_items(const ExcCounts &X, int n, const uint32_t *grp_alpha, uint32_t ngroups,
+               uint32_t o_begin, uint32_t nops, int opbits, uint64_t *items, Arena &arena);
+int item_weights(const uint64_t *items, uint64_t nitems, int opbits, const uint32_t *grp_count,
+                 const ExcCounts &X, uint64_t *w, Arena &arena);
+int emit_batch(const DevInts &I, const ExcCounts &X, const uint64_t *items, const uint64_t *Wexcl,
+               uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1, int opbits,
+               const uint32_t *grp_alpha, const uint32_t *grp_start, const uint32_t *core_beta,
+               const double *core_c, uint64_t *out_keys, double *out_vals, Arena &arena);
+int compact_u64(const uint64_t *in, const uint32_t *keep, const uint32_t *pos, size_t n,
+                uint64_t *out, Arena &arena);
+int compact_f64(const double *in, const uint32_t *keep, const uint32_t *pos, size_t n, double *out,
+                Arena &arena);
+int kept_count(const uint32_t *keep, const uint32_t *pos, size_t n, size_t *host_count,
+               Arena &arena);
+int score_unique(const DevInts &I, const uint64_t *ukeys, const double *usums, size_t u,
+                 const uint64_t *psi_sorted, size_t npsi, double E0, uint32_t *keep,
+                 double *score, Arena &arena);
+
+static thread_local char g_last_error[512] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void record_error(const char *what, const char *file, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s (%s:%d)", what, file, line);
+}
+
+namespace {
+
+constexpr uint64_t kSentinel = ~0ull;  // key of a screened-out pair (never a real key)
+
+inline unsigned grid_for(size_t n, unsigned cap = 152 * 16) {
+  size_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  return (unsigned)(b < cap ? b : cap);
+}
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Copy `count` elements to a device buffer (alloc + copy when host memory).
+template <typename T>
+int to_device(const T *src, size_t count, const T **dst, Arena &arena) {
+  if (is_device_ptr(src)) {
+    *dst = src;
+    return ASCI_OK;
+  }
+  T *d = nullptr;
+  ASCI_TRY(arena.alloc(&d, count));
+  if (count)
+    ASCI_TRY_CUDA(cudaMemcpyAsync(d, src, count * sizeof(T), cudaMemcpyDefault,
+                                  arena.stream()));
+  *dst = d;
+  return ASCI_OK;
+}
+
+// ------------------------------ kernels ------------------------------------
+
+enum : uint32_t {
+  kBadRange = 1u,     // bits at or above norb
+  kBadCount = 2u,     // electron counts differ from the first determinant
+  kBadValue = 4u,     // non-finite coefficient or integral
+  kDuplicate = 8u,    // repeated determinant
+};
+
+__global__ void k_prepare_psi(const asci_det *dets, const double *c, size_t nd, int norb, int na,
+                              int nb, uint64_t *keys, uint32_t *idx, unsigned *err) {
+  const uint64_t hi = ~((1ull << norb) - 1ull);  // norb <= 32
+  unsigned e = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd;
+       i += (size_t)gridDim.x * blockDim.x) {
+    asci_det d = dets[i];
+    if ((d.alpha & hi) || (d.beta & hi)) e |= kBadRange;
+    if (na >= 0 && (__popcll(d.alpha) != na || __popcll(d.beta) != nb)) e |= kBadCount;
+    if (!isfinite(c[i])) e |= kBadValue;
+    keys[i] = pack_key((uint32_t)d.alpha, (uint32_t)d.beta);
+    idx[i] = (uint32_t)i;
+  }
+  if (e) atomicOr(err, e);
+}
+
+__global__ void k_check_finite(const double *x, size_t n, unsigned *err) {
+  unsigned e = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) e = kBadValue;
+  if (e) atomicOr(err, e);
+}
+
+__global__ void k_check_dups(const uint64_t *sorted, size_t n, unsigned *err) {
+  unsigned e = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    if (sorted[i] == sorted[i - 1]) e = kDuplicate;
+  if (e) atomicOr(err, e);
+}
+
+// key for the core order: ~bits(|c|) ascending = |c| descending
+__global__ void k_abs_keys(const uint32_t *idx, const double *c, size_t n, uint64_t *out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = ~(uint64_t)__double_as_longlong(fabs(c[idx[i]]));
+}
+
+// gather the core: alpha as the sort key (low word), payload = core position
+__global__ void k_gather_core(const uint32_t *core_idx, const uint64_t *psi_keys_by_input,
+                              const double *c, size_t m, uint64_t *alpha_keys, uint32_t *pos,
+                              uint64_t *core_keys, double *core_c) {
+  for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+       j += (size_t)gridDim.x * blockDim.x) {
+    uint32_t i = core_idx[j];
+    uint64_t k = psi_keys_by_input[i];
+    core_keys[j] = k;
+    core_c[j] = c[i];
+    alpha_keys[j] = (uint64_t)key_alpha(k);
+    pos[j] = (uint32_t)j;
+  }
+}
+
+__global__ void k_input_keys(const asci_det *dets, size_t nd, uint64_t *keys) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd;
+       i += (size_t)gridDim.x * blockDim.x)
+    keys[i] = pack_key((uint32_t)dets[i].alpha, (uint32_t)dets[i].beta);
+}
+
+// core sorted by alpha: group heads, per-det beta and coefficient in that order
+__global__ void k_group_heads(const uint64_t *alpha_sorted, const uint32_t *pos,
+                              const uint64_t *core_keys, const double *core_c, size_t m,
+                              uint32_t *head, uint32_t *beta_sorted, double *c_sorted) {
+  for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+       j += (size_t)gridDim.x * blockDim.x) {
+    head[j] = (j == 0 || alpha_sorted[j] != alpha_sorted[j - 1]) ? 1u : 0u;
+    uint32_t p = pos[j];
+    beta_sorted[j] = key_beta(core_keys[p]);
+    c_sorted[j] = core_c[p];
+  }
+}
+
+__global__ void k_group_table(const uint32_t *head, const uint32_t *gid, const uint64_t *alpha_sorted,
+                              size_t m, uint32_t *grp_alpha, uint32_t *grp_start) {
+  for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+       j += (size_t)gridDim.x * blockDim.x)
+    if (head[j]) {
+      grp_alpha[gid[j]] = (uint32_t)alpha_sorted[j];
+      grp_start[gid[j]] = (uint32_t)j;
+    }
+}
+
+__global__ void k_group_count(const uint32_t *grp_start, uint32_t ngroups, uint32_t m,
+                              uint32_t *grp_count) {
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
+       g += gridDim.x * blockDim.x)
+    grp_count[g] = ((g + 1 < ngroups) ? grp_start[g + 1] : m) - grp_start[g];
+}
+
+__device__ __forceinline__ uint32_t top_bits(uint32_t x, int L) {
+  for (int drop = __popc(x) - L; drop > 0; --drop) x &= x - 1u;
+  return x;
+}
+
+// class starts at level L inside items [s, e)
+__global__ void k_class_heads(const uint64_t *items, uint64_t s, uint64_t e, int L,
+                              uint32_t *head) {
+  for (uint64_t t = s + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < e;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t cur = top_bits((uint32_t)(items[t] >> 32), L);
+    uint32_t prv = (t == s) ? ~cur : top_bits((uint32_t)(items[t - 1] >> 32), L);
+    head[t - s] = (t == s || cur != prv) ? 1u : 0u;
+  }
+}
+
+__global__ void k_class_list(const uint32_t *head, const uint32_t *pos, uint64_t s, uint64_t cnt,
+                             const uint64_t *Wexcl, uint64_t *starts, uint64_t *wstarts) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    if (head[i]) {
+      starts[pos[i]] = s + i;
+      wstarts[pos[i]] = Wexcl[s + i];
+    }
+}
+
+// eps screen of Alg. 2: drop (target, core) pairs with |v / (E0 - H_ii)| <= eps
+__device__ double diag_direct(const DevInts &I, uint32_t A, uint32_t B) {
+  const int n = I.n;
+  double s = I.ecore;
+  for (uint32_t m = A; m; m &= m - 1) {
+    const int p = __ffs(m) - 1;
+    s += I.h1[p * n + p];
+    for (uint32_t r = m & (m - 1); r; r &= r - 1) s += I.jk[p * n + __ffs(r) - 1];
+    for (uint32_t r = B; r; r &= r - 1) s += I.jj[p * n + __ffs(r) - 1];
+  }
+  for (uint32_t m = B; m; m &= m - 1) {
+    const int p = __ffs(m) - 1;
+    s += I.h1[p * n + p];
+    for (uint32_t r = m & (m - 1); r; r &= r - 1) s += I.jk[p * n + __ffs(r) - 1];
+  }
+  return s;
+}
+
+__global__ void k_screen(DevInts I, uint64_t *keys, const double *vals, size_t n, double E0,
+                         double eps, unsigned long long *survivors) {
+  unsigned long long kept = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    uint64_t k = keys[i];
+    double hii = diag_direct(I, key_alpha(k), key_beta(k));
+    if (fabs(vals[i] / (E0 - hii)) > eps)
+      ++kept;
+    else
+      keys[i] = kSentinel;
+  }
+  for (int d = 16; d; d >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, d);
+  if ((threadIdx.x & 31) == 0 && kept) atomicAdd(survivors, kept);
+}
+
+__global__ void k_unpack(const uint64_t *keys, size_t n, asci_det *out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    asci_det d;
+    d.alpha = key_alpha(keys[i]);
+    d.beta = key_beta(keys[i]);
+    out[i] = d;
+  }
+}
+
+// ------------------------------- timing ------------------------------------
+
+struct StageTimer {
+  cudaStream_t s;
+  cudaEvent_t ev[2];
+  bool ok = false;
+  explicit StageTimer(cudaStream_t st) : s(st) {
+    ok = cudaEventCreate(&ev[0]) == cudaSuccess && cudaEventCreate(&ev[1]) == cudaSuccess;
+  }
+  ~StageTimer() {
+    if (ok) {
+      cudaEventDestroy(ev[0]);
+      cudaEventDestroy(ev[1]);
+    }
+  }
+  void start() {
+    if (ok) cudaEventRecord(ev[0], s);
+  }
+  void stop(double *acc) {
+    if (!ok) return;
+    cudaEventRecord(ev[1], s);
+    cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    *acc += ms;
+  }
+};
+
+int bits_for(uint32_t v) {
+  int b = 0;
+  while ((1ull << b) < (uint64_t)v) ++b;
+  return b < 1 ? 1 : b;
+}
+
+struct Batch {
+  uint64_t t0, t1, P0, P1;
+};
+
+// Cut items [0, T) into batches of at most bmax pairs at class boundaries
+// (Sec. 2.2 constraints; Alg. 3's work counts h are the class weights).
+class Planner {
+ public:
+  Planner(const uint64_t *items, const uint64_t *Wexcl, uint64_t bmax, int lmax, Arena &arena)
+      : items_(items), W_(Wexcl), bmax_(bmax), lmax_(lmax), arena_(arena) {}
+
+  int run(uint64_t T, uint64_t P, int L0, std::vector<Batch> *out, int *max_level) {
+    batches_.clear();
+    cur_open_ = false;
+    max_level_ = L0;
+    ASCI_TRY(visit(0, T, 0, P, L0));
+    flush();
+    *out = batches_;
+    *max_level = max_level_;
+    return ASCI_OK;
+  }
+
+ private:
+  int query(uint64_t s, uint64_t e, int L, std::vector<uint64_t> *starts,
+            std::vector<uint64_t> *wst) {
+    uint64_t cnt = e - s;
+    Arena qa(arena_.stream());  // released when the query returns
+    uint32_t *head, *pos;
+    ASCI_TRY(qa.alloc(&head, cnt));
+    ASCI_TRY(qa.alloc(&pos, cnt));
+    cudaStream_t st = qa.stream();
+    k_class_heads<<<grid_for(cnt), 256, 0, st>>>(items_, s, e, L, head);
+    ASCI_CHECK_LAUNCH();
+    ASCI_TRY(scan_exclusive_u32(head, pos, cnt, qa));
+    size_t nc = 0;
+    ASCI_TRY(kept_count(head, pos, cnt, &nc, qa));
+    uint64_t *ds, *dw;
+    ASCI_TRY(qa.alloc(&ds, nc));
+    ASCI_TRY(qa.alloc(&dw, nc));
+    k_class_list<<<grid_for(cnt), 256, 0, st>>>(head, pos, s, cnt, W_, ds, dw);
+    ASCI_CHECK_LAUNCH();
+    starts->resize(nc);
+    wst->resize(nc);
+    ASCI_TRY_CUDA(cudaMemcpyAsync(starts->data(), ds, nc * 8, cudaMemcpyDefault, st));
+    ASCI_TRY_CUDA(cudaMemcpyAsync(wst->data(), dw, nc * 8, cudaMemcpyDefault, st));
+    ASCI_TRY_CUDA(cudaStreamSynchronize(st));
+    return ASCI_OK;
+  }
+
+  void flush() {
+    if (cur_open_ && cur_.P1 > cur_.P0) batches_.push_back(cur_);
+    cur_open_ = false;
+  }
+
+  void add(uint64_t cs, uint64_t ce, uint64_t ws, uint64_t we) {
+    if (cur_open_ && (we - cur_.P0) > bmax_) flush();
+    if (!cur_open_) {
+      cur_ = Batch{cs, ce, ws, we};
+      cur_open_ = true;
+    } else {
+      cur_.t1 = ce;
+      cur_.P1 = we;
+    }
+  }
+
+  int visit(uint64_t s, uint64_t e, uint64_t ws, uint64_t we, int L) {
+    if (L > max_level_) max_level_ = L;
+    std::vector<uint64_t> starts, wst;
+    ASCI_TRY(query(s, e, L, &starts, &wst));
+    for (size_t c = 0; c < starts.size(); ++c) {
+      uint64_t cs = starts[c], ce = (c + 1 < starts.size()) ? starts[c + 1] : e;
+      uint64_t w0 = wst[c], w1 = (c + 1 < starts.size()) ? wst[c + 1] : we;
+      if (w1 - w0 > bmax_ && L < lmax_ && ce - cs > 1) {
+        flush();
+        ASCI_TRY(visit(cs, ce, w0, w1, L + 1));
+      } else {
+        add(cs, ce, w0, w1);
+      }
+    }
+    return ASCI_OK;
+  }
+
+  const uint64_t *items_;
+  const uint64_t *W_;
+  uint64_t bmax_;
+  int lmax_;
+  Arena &arena_;
+  std::vector<Batch> batches_;
+  Batch cur_{};
+  bool cur_open_ = false;
+  int max_level_ = 0;
+};
+
+}  // namespace
+
+// Per-device memory pool that keeps the search scratch cached between calls.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {};
+
+int device_pool(int dev, cudaMemPool_t *pool) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (dev < 0 || dev >= 64) return ASCI_ECUDA;
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    ASCI_TRY_CUDA(cudaMemPoolCreate(&g_pools[dev], &props));
+    uint64_t thr = ~0ull;
+    ASCI_TRY_CUDA(cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &thr));
+  }
+  *pool = g_pools[dev];
+  return ASCI_OK;
+}
+
+// The search proper.  All pointers resolved; `arena` owns the scratch.
+static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t nd, double E0,
+                       const asci_ints *ints, size_t C, size_t N, const asci_opts &o,
+                       asci_det *out_dets, double *out_scores, size_t *out_n, asci_stats *st,
+                       cudaStream_t stream) {
+  Arena arena(stream);
+  double tl[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per-stage device milliseconds
+  StageTimer tm(stream), total_tm(stream);
+  total_tm.start();
+  tm.start();
+  const int n = ints->norb;
+  const asci_det *dets;
+  const double *coeffs, *h1, *eri;
+  ASCI_TRY(to_device(dets_in, nd, &dets, arena));
+  ASCI_TRY(to_device(coeffs_in, nd, &coeffs, arena));
+  ASCI_TRY(to_device(ints->h1, (size_t)n * n, &h1, arena));
+  ASCI_TRY(to_device(ints->eri, (size_t)n * n * n * n, &eri, arena));
+
+  // electron counts from the first determinant
+  asci_det d0;
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&d0, dets, sizeof(d0), cudaMemcpyDefault, stream));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+  const int na = __builtin_popcountll(d0.alpha), nb = __builtin_popcountll(d0.beta);
+  if (na > n || nb > n) return ASCI_EINVAL;
+
+  unsigned *derr;
+  ASCI_TRY(arena.alloc(&derr, 1));
+  ASCI_TRY_CUDA(cudaMemsetAsync(derr, 0, sizeof(unsigned), stream));
+  uint64_t *pkeys, *pkeys_alt, *absk, *absk_alt;
+  uint32_t *pidx, *pidx_alt;
+  ASCI_TRY(arena.alloc(&pkeys, nd));
+  ASCI_TRY(arena.alloc(&pkeys_alt, nd));
+  ASCI_TRY(arena.alloc(&pidx, nd));
+  ASCI_TRY(arena.alloc(&pidx_alt, nd));
+  k_prepare_psi<<<grid_for(nd), 256, 0, stream>>>(dets, coeffs, nd, n, na, nb, pkeys, pidx, derr);
+  ASCI_CHECK_LAUNCH();
+  k_check_finite<<<grid_for((size_t)n * n * n * n), 256, 0, stream>>>(eri, (size_t)n * n * n * n,
+                                                                       derr);
+  ASCI_CHECK_LAUNCH();
+  k_check_finite<<<grid_for((size_t)n * n), 256, 0, stream>>>(h1, (size_t)n * n, derr);
+  ASCI_CHECK_LAUNCH();
+  // psi keys sorted (exclusion table) with input positions
+  ASCI_TRY(radix_sort_u64_u32(&pkeys, &pkeys_alt, &pidx, &pidx_alt, nd, 0, 64, arena));
+  k_check_dups<<<grid_for(nd), 256, 0, stream>>>(pkeys, nd, derr);
+  ASCI_CHECK_LAUNCH();
+  unsigned herr = 0;
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(herr), cudaMemcpyDefault, stream));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+  if (herr) {
+    record_error(herr & kDuplicate   ? "duplicate determinants in psi"
+                 : herr & kBadCount  ? "determinants with different electron counts"
+                 : herr & kBadRange  ? "determinant bits at or above norb"
+                                     : "non-finite coefficient or integral",
+                 __FILE__, __LINE__);
+    return ASCI_EINVAL;
+  }
+  const uint64_t *psi_sorted = pkeys;
+  // the psi key buffer stays live; reuse the alternates for the core order
+  ASCI_TRY(arena.alloc(&absk, nd));
+  ASCI_TRY(arena.alloc(&absk_alt, nd));
+  k_abs_keys<<<grid_for(nd), 256, 0, stream>>>(pidx, coeffs, nd, absk);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(radix_sort_u64_u32(&absk, &absk_alt, &pidx, &pidx_alt, nd, 0, 64, arena));
+  const size_t m = std::min(C, nd);
+  // keys of psi by input position (for gathering the core)
+  uint64_t *in_keys;
+  ASCI_TRY(arena.alloc(&in_keys, nd));
+  k_input_keys<<<grid_for(nd), 256, 0, stream>>>(dets, nd, in_keys);
+  ASCI_CHECK_LAUNCH();
+  uint64_t *core_keys, *alpha_k, *alpha_k_alt;
+  double *core_c;
+  uint32_t *cpos, *cpos_alt;
+  ASCI_TRY(arena.alloc(&core_keys, m));
+  ASCI_TRY(arena.alloc(&core_c, m));
+  ASCI_TRY(arena.alloc(&alpha_k, m));
+  ASCI_TRY(arena.alloc(&alpha_k_alt, m));
+  ASCI_TRY(arena.alloc(&cpos, m));
+  ASCI_TRY(arena.alloc(&cpos_alt, m));
+  k_gather_core<<<grid_for(m), 256, 0, stream>>>(pidx, in_keys, coeffs, m, alpha_k, cpos, core_keys,
+                                                 core_c);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(radix_sort_u64_u32(&alpha_k, &alpha_k_alt, &cpos, &cpos_alt, m, 0, 32, arena));
+  uint32_t *ghead, *gid, *core_beta;
+  double *core_c_sorted;
+  ASCI_TRY(arena.alloc(&ghead, m));
+  ASCI_TRY(arena.alloc(&gid, m));
+  ASCI_TRY(arena.alloc(&core_beta, m));
+  ASCI_TRY(arena.alloc(&core_c_sorted, m));
+  k_group_heads<<<grid_for(m), 256, 0, stream>>>(alpha_k, cpos, core_keys, core_c, m, ghead,
+                                                 core_beta, core_c_sorted);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(scan_exclusive_u32(ghead, gid, m, arena));
+  size_t ngroups = 0;
+  ASCI_TRY(kept_count(ghead, gid, m, &ngroups, arena));
+  uint32_t *grp_alpha, *grp_start, *grp_count;
+  ASCI_TRY(arena.alloc(&grp_alpha, ngroups));
+  ASCI_TRY(arena.alloc(&grp_start, ngroups));
+  ASCI_TRY(arena.alloc(&grp_count, ngroups));
+  k_group_table<<<grid_for(m), 256, 0, stream>>>(ghead, gid, alpha_k, m, grp_alpha, grp_start);
+  ASCI_CHECK_LAUNCH();
+  k_group_count<<<grid_for(ngroups), 256, 0, stream>>>(grp_start, (uint32_t)ngroups, (uint32_t)m,
+                                                       grp_count);
+  ASCI_CHECK_LAUNCH();
+
+  DevInts I;
+  ASCI_TRY(build_tables(h1, eri, n, na, nb, ints->ecore, o.precision != ASCI_FP64, arena, &I));
+  const ExcCounts X = exc_counts(n, na, nb);
+  if (st) {
+    st->ncore = m;
+    st->generated = (uint64_t)m * X.total;
+  }
+  tm.stop(&tl[0]);
+
+  // ------------------------------- plan ------------------------------------
+  tm.start();
+  const uint64_t npd0 = (uint64_t)X.sb + X.dbb;
+  const uint32_t nops = 1u + X.sa + (uint32_t)X.daa;
+  const uint32_t o_begin = npd0 > 0 ? 0u : 1u;
+  const int opbits = bits_for(nops);
+  if (opbits >= 32 || (uint64_t)ngroups >= (1ull << (32 - opbits))) {
+    record_error("too many distinct core alpha strings for the item format", __FILE__, __LINE__);
+    return ASCI_EINVAL;
+  }
+  // pairs of one item must index in 32 bits
+  {
+    uint32_t maxc = 0;
+    // conservative bound: the whole core in one group
+    maxc = (uint32_t)m;
+    if ((uint64_t)maxc * std::max<uint64_t>(npd0, 1ull + X.sb) >= (1ull << 32)) {
+      record_error("core too large for one alpha group", __FILE__, __LINE__);
+      return ASCI_EINVAL;
+    }
+  }
+  const uint64_t T = (uint64_t)ngroups * (nops - o_begin);
+  std::vector<Batch> batches;
+  int max_level = 0;
+  uint64_t *items = nullptr, *items_alt = nullptr, *w = nullptr, *Wexcl = nullptr;
+  uint64_t P = 0;
+  if (T > 0) {
+    ASCI_TRY(arena.alloc(&items, T));
+    ASCI_TRY(arena.alloc(&items_alt, T));
+    ASCI_TRY(make_items(X, n, grp_alpha, (uint32_t)ngroups, o_begin, nops, opbits, items, arena));
+    ASCI_TRY(radix_sort_u64(&items, &items_alt, T, 32, 32 + n, arena));
+    ASCI_TRY(arena.alloc(&w, T));
+    ASCI_TRY(arena.alloc(&Wexcl, T));
+    ASCI_TRY(item_weights(items, T, opbits, grp_count, X, w, arena));
+    ASCI_TRY(scan_exclusive_u64(w, Wexcl, T, arena));
+    uint64_t last[2];
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&last[0], Wexcl + T - 1, 8, cudaMemcpyDefault, stream));
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&last[1], w + T - 1, 8, cudaMemcpyDefault, stream));
+    ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+    P = last[0] + last[1];
+    if (P != (uint64_t)m * X.total) {
+      record_error("pair count does not match the closed form", __FILE__, __LINE__);
+      return ASCI_ECUDA;
+    }
+    uint64_t bmax = o.max_batch_pairs;
+    if (bmax == 0) {
+      size_t fr = 0, tot = 0;
+      ASCI_TRY_CUDA(cudaMemGetInfo(&fr, &tot));
+      bmax = (uint64_t)(fr / 2) / 96;
+      bmax = std::max<uint64_t>(bmax, 1ull << 20);
+      bmax = std::min<uint64_t>(bmax, 1ull << 30);
+    }
+    const int lmax = (o.max_constraint_level > 0) ? std::min(o.max_constraint_level, na) : na;
+    const int L0 = std::min(3, lmax);
+    Planner planner(items, Wexcl, bmax, lmax, arena);
+    ASCI_TRY(planner.run(T, P, L0, &batches, &max_level));
+  }
+  uint64_t bcap = 0;
+  for (auto &b : batches) bcap = std::max(bcap, b.P1 - b.P0);
+  if (st) {
+    st->batches = batches.size();
+    st->max_batch = bcap;
+    st->max_level = (uint64_t)max_level;
+  }
+  if (bcap >= (1ull << 32) - 1) {
+    record_error("a constraint batch exceeds 2^32 pairs", __FILE__, __LINE__);
+    return ASCI_ENOMEM;
+  }
+  tm.stop(&tl[1]);
+
+  // --------------------------- batches -------------------------------------
+  uint64_t *bk = nullptr, *bk_alt = nullptr, *ukeys = nullptr;
+  double *bv = nullptr, *bv_alt = nullptr, *usums = nullptr, *uscore = nullptr;
+  uint32_t *keep = nullptr, *kpos = nullptr;
+  uint64_t *pool_k[2] = {nullptr, nullptr};
+  double *pool_s[2] = {nullptr, nullptr};
+  unsigned long long *dsurv = nullptr;
+  const size_t pool_cap = N + bcap;
+  if (bcap) {
+    ASCI_TRY(arena.alloc(&bk, bcap));
+    ASCI_TRY(arena.alloc(&bk_alt, bcap));
+    ASCI_TRY(arena.alloc(&bv, bcap));
+    ASCI_TRY(arena.alloc(&bv_alt, bcap));
+    ASCI_TRY(arena.alloc(&ukeys, bcap));
+    ASCI_TRY(arena.alloc(&usums, bcap));
+    ASCI_TRY(arena.alloc(&uscore, bcap));
+    ASCI_TRY(arena.alloc(&keep, bcap));
+    ASCI_TRY(arena.alloc(&kpos, bcap));
+    ASCI_TRY(arena.alloc(&dsurv, 1));
+    for (int i = 0; i < 2; ++i) {
+      ASCI_TRY(arena.alloc(&pool_k[i], pool_cap));
+      ASCI_TRY(arena.alloc(&pool_s[i], pool_cap));
+    }
+  }
+  size_t pool_n = 0;
+  int pcur = 0;
+  uint64_t surviving = 0, unique = 0, excluded = 0;
+  for (const Batch &b : batches) {
+    Arena ba(stream);  // scratch of this batch, released when the batch ends
+    const size_t nb_pairs = b.P1 - b.P0;
+    uint64_t *k0 = bk, *k1 = bk_alt;
+    double *v0 = bv, *v1 = bv_alt;
+    tm.start();
+    ASCI_TRY(emit_batch(I, X, items, Wexcl, b.t0, b.t1, b.P0, b.P1, opbits, grp_alpha, grp_start,
+                        core_beta, core_c_sorted, k0, v0, ba));
+    size_t surv = nb_pairs;
+    if (o.eps_search > 0.0) {
+      ASCI_TRY_CUDA(cudaMemsetAsync(dsurv, 0, sizeof(unsigned long long), stream));
+      k_screen<<<grid_for(nb_pairs), 256, 0, stream>>>(I, k0, v0, nb_pairs, E0, o.eps_search,
+                                                       dsurv);
+      ASCI_CHECK_LAUNCH();
+      unsigned long long hs = 0;
+      ASCI_TRY_CUDA(cudaMemcpyAsync(&hs, dsurv, sizeof(hs), cudaMemcpyDefault, stream));
+      ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+      surv = (size_t)hs;
+    }
+    surviving += surv;
+    tm.stop(&tl[2]);
+    tm.start();
+    size_t u = 0;
+    ASCI_TRY(sort_accumulate(&k0, &k1, &v0, &v1, nb_pairs, ukeys, usums, &u, ba));
+    tm.stop(&tl[3]);
+    tm.start();
+    ASCI_TRY(score_unique(I, ukeys, usums, u, psi_sorted, nd, E0, keep, uscore, ba));
+    ASCI_TRY(scan_exclusive_u32(keep, kpos, u, ba));
+    size_t kept = 0;
+    ASCI_TRY(kept_count(keep, kpos, u, &kept, ba));
+    const size_t u_real = (surv < nb_pairs) ? u - 1 : u;  // the sentinel run is not a target
+    unique += u_real;
+    excluded += u_real - kept;
+    ASCI_TRY(compact_u64(ukeys, keep, kpos, u, pool_k[pcur] + pool_n, ba));
+    ASCI_TRY(compact_f64(uscore, keep, kpos, u, pool_s[pcur] + pool_n, ba));
+    pool_n += kept;
+    tm.stop(&tl[5]);
+    if (pool_n > N && pool_n + bcap > pool_cap) {
+      tm.start();
+      size_t m2 = 0;
+      ASCI_TRY(select_topn_packed(pool_k[pcur], pool_s[pcur], pool_n, N, pool_k[pcur ^ 1],
+                                  pool_s[pcur ^ 1], &m2, ba));
+      pcur ^= 1;
+      pool_n = m2;
+      tm.stop(&tl[6]);
+    }
+  }
+  // ------------------------------ select -----------------------------------
+  tm.start();
+  size_t nsel = 0;
+  uint64_t *sel_k = nullptr;
+  double *sel_s = nullptr;
+  const size_t nout = std::min(N, pool_n);
+  if (nout) {
+    ASCI_TRY(arena.alloc(&sel_k, nout));
+    ASCI_TRY(arena.alloc(&sel_s, nout));
+    ASCI_TRY(select_topn_packed(pool_k[pcur], pool_s[pcur], pool_n, N, sel_k, sel_s, &nsel, arena));
+    if (o.sort_output && nsel > 1) {
+      uint64_t *k2;
+      double *s2;
+      ASCI_TRY(arena.alloc(&k2, nsel));
+      ASCI_TRY(arena.alloc(&s2, nsel));
+      ASCI_TRY(radix_sort_u64_f64(&sel_k, &k2, &sel_s, &s2, nsel, 0, 64, arena));
+    }
+    asci_det *dout = out_dets;
+    double *sout = out_scores;
+    const bool host_out = !is_device_ptr(out_dets);
+    const bool host_sc = !is_device_ptr(out_scores);
+    if (host_out) ASCI_TRY(arena.alloc(&dout, nsel));
+    if (host_sc) sout = sel_s;
+    k_unpack<<<grid_for(nsel), 256, 0, stream>>>(sel_k, nsel, dout);
+    ASCI_CHECK_LAUNCH();
+    if (host_out)
+      ASCI_TRY_CUDA(cudaMemcpyAsync(out_dets, dout, nsel * sizeof(asci_det),
+                                    cudaMemcpyDefault, stream));
+    if (host_sc)
+      ASCI_TRY_CUDA(cudaMemcpyAsync(out_scores, sout, nsel * sizeof(double),
+                                    cudaMemcpyDefault, stream));
+    else
+      ASCI_TRY_CUDA(cudaMemcpyAsync(out_scores, sel_s, nsel * sizeof(double),
+                                    cudaMemcpyDefault, stream));
+  }
+  ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+  tm.stop(&tl[6]);
+  *out_n = nsel;
+  if (st) {
+    st->surviving = surviving;
+    st->unique = unique;
+    st->excluded = excluded;
+    st->selected = nsel;
+  }
+  total_tm.stop(&tl[7]);
+  return ASCI_OK;
+}
+
+}  // namespace asci
+
+using namespace asci;
+
+// Inputs of the component entry points may be host or device memory; outputs
+// are written through a device staging buffer when they are host memory.
+static int stage_ints(const asci_ints *ints, Arena &arena, const double **h1, const double **eri) {
+  const size_t n = (size_t)ints->norb;
+  ASCI_TRY(to_device(ints->h1, n * n, h1, arena));
+  ASCI_TRY(to_device(ints->eri, n * n * n * n, eri, arena));
+  return ASCI_OK;
+}
+
+template <typename T>
+static int out_buffer(T *user, size_t count, T **dev, Arena &arena) {
+  if (is_device_ptr(user)) {
+    *dev = user;
+    return ASCI_OK;
+  }
+  return arena.alloc(dev, count);
+}
+
+template <typename T>
+static int finish_out(T *user, const T *dev, size_t count, cudaStream_t s) {
+  if ((const T *)user != dev && count)
+    ASCI_TRY_CUDA(cudaMemcpyAsync(user, dev, count * sizeof(T), cudaMemcpyDefault, s));
+  return ASCI_OK;
+}
+
+extern "C" {
+
+void asci_default_opts(asci_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->eps_search = 0.0;
+  o->max_constraint_level = 0;
+  o->precision = ASCI_FP64;
+  o->max_batch_pairs = 0;
+  o->sort_output = 0;
+}
+
+const char *asci_version(void) { return "libasci 0.1 (sm_103a)"; }
+
+const char *asci_strerror(int code) {
+  switch (code) {
+    case ASCI_OK: return "ok";
+    case ASCI_EINVAL: return "invalid argument";
+    case ASCI_ENOMEM: return "out of device memory";
+    case ASCI_ECUDA: return "CUDA error";
+    case ASCI_ETIMEOUT: return "device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+const char *asci_last_error(void) { return g_last_error; }
+
+unsigned long long asci_launch_count(void) { return g_launches.load(); }
+
+void asci_trim_cache(void) {
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) == cudaSuccess && device_pool(dev, &pool) == ASCI_OK)
+    cudaMemPoolTrimTo(pool, 0);
+}
+
+static int begin_call(void *cuda_stream, cudaStream_t *s) {
+  g_last_error[0] = 0;
+  *s = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  ASCI_TRY_CUDA(cudaGetDevice(&dev));
+  (void)dev;
+  return ASCI_OK;
+}
+
+int asci_search(const asci_det *dets, const double *coeffs, size_t ndets, double E0,
+                const asci_ints *ints, size_t C, size_t N, const asci_opts *opts,
+                asci_det *out_dets, double *out_scores, size_t *out_n, asci_stats *stats,
+                void *cuda_stream) {
+  if (out_n) *out_n = 0;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (!dets || !coeffs || !ints || !ints->h1 || !ints->eri || !out_n) return ASCI_EINVAL;
+  if ((N > 0) && (!out_dets || !out_scores)) return ASCI_EINVAL;
+  if (ints->norb < 1 || ints->norb > 32 || ndets == 0 || C == 0) return ASCI_EINVAL;
+  if (!std::isfinite(E0) || !std::isfinite(ints->ecore)) return ASCI_EINVAL;
+  if (ndets >= (1ull << 32)) return ASCI_EINVAL;
+  asci_opts o;
+  asci_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.eps_search >= 0.0) || !std::isfinite(o.eps_search)) return ASCI_EINVAL;
+  if (o.precision < ASCI_FP64 || o.precision > ASCI_FP32_INT_COMP_ACC) return ASCI_EINVAL;
+  cudaStream_t s;
+  ASCI_TRY(begin_call(cuda_stream, &s));
+  int r = search_impl(dets, coeffs, ndets, E0, ints, C, N, o, out_dets, out_scores, out_n, stats,
+                      s);
+  if (r != ASCI_OK) *out_n = 0;
+  return r;
+}
+
+int asci_excitations(const asci_ints *ints, const asci_det *core, const double *coeffs,
+                     size_t ncore, asci_det *out_targets, double *out_values, size_t capacity,
+                     size_t *out_n, void *cuda_stream) {
+  if (out_n) *out_n = 0;
+  if (!ints || !ints->h1 || !ints->eri || !core || !coeffs || !out_targets || !out_values || !out_n)
+    return ASCI_EINVAL;
+  if (ints->norb < 1 || ints->norb > 32 || ncore == 0) return ASCI_EINVAL;
+  cudaStream_t s;
+  ASCI_TRY(begin_call(cuda_stream, &s));
+  Arena arena(s);
+  const int n = ints->norb;
+  const asci_det *dcore;
+  const double *dc, *h1, *eri;
+  ASCI_TRY(to_device(core, ncore, &dcore, arena));
+  ASCI_TRY(to_device(coeffs, ncore, &dc, arena));
+  ASCI_TRY(stage_ints(ints, arena, &h1, &eri));
+  asci_det d0;
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&d0, dcore, sizeof(d0), cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  const int na = __builtin_popcountll(d0.alpha), nb = __builtin_popcountll(d0.beta);
+  if (na > n || nb > n || (n < 64 && ((d0.alpha | d0.beta) >> n))) return ASCI_EINVAL;
+  const ExcCounts X = exc_counts(n, na, nb);
+  const uint64_t total = (uint64_t)ncore * X.total;
+  if (total > capacity) return ASCI_EINVAL;
+  // every core det must have the same electron counts and no bits >= norb
+  {
+    unsigned *derr;
+    uint64_t *tk;
+    uint32_t *ti;
+    double *tc;
+    ASCI_TRY(arena.alloc(&derr, 1));
+    ASCI_TRY(arena.alloc(&tk, ncore));
+    ASCI_TRY(arena.alloc(&ti, ncore));
+    ASCI_TRY(arena.alloc(&tc, ncore));
+    ASCI_TRY_CUDA(cudaMemsetAsync(derr, 0, sizeof(unsigned), s));
+    ASCI_TRY_CUDA(cudaMemsetAsync(tc, 0, ncore * sizeof(double), s));
+    k_prepare_psi<<<grid_for(ncore), 256, 0, s>>>(dcore, tc, ncore, n, na, nb, tk, ti, derr);
+    ASCI_CHECK_LAUNCH();
+    unsigned herr = 0;
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(herr), cudaMemcpyDefault, s));
+    ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+    if (herr & (kBadRange | kBadCount)) return ASCI_EINVAL;
+  }
+  DevInts I;
+  ASCI_TRY(build_tables(h1, eri, n, na, nb, ints->ecore, false, arena, &I));
+  uint64_t *ck, *ok;
+  double *ov;
+  asci_det *dt;
+  ASCI_TRY(arena.alloc(&ck, ncore));
+  ASCI_TRY(arena.alloc(&ok, total));
+  ASCI_TRY(out_buffer(out_values, total, &ov, arena));
+  ASCI_TRY(out_buffer(out_targets, total, &dt, arena));
+  k_input_keys<<<grid_for(ncore), 256, 0, s>>>(dcore, ncore, ck);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(emit_fixed_order(I, ck, dc, ncore, ok, ov, arena));
+  k_unpack<<<grid_for(total), 256, 0, s>>>(ok, total, dt);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(finish_out(out_values, ov, total, s));
+  ASCI_TRY(finish_out(out_targets, dt, total, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  *out_n = total;
+  return ASCI_OK;
+}
+
+int asci_diagonal(const asci_ints *ints, const asci_det *dets, size_t n, double *out_haa,
+                  void *cuda_stream) {
+  if (!ints || !ints->h1 || !ints->eri || !dets || !out_haa) return ASCI_EINVAL;
+  if (ints->norb < 1 || ints->norb > 32) return ASCI_EINVAL;
+  if (n == 0) return ASCI_OK;
+  cudaStream_t s;
+  ASCI_TRY(begin_call(cuda_stream, &s));
+  Arena arena(s);
+  const asci_det *dd;
+  const double *h1, *eri;
+  double *dout;
+  ASCI_TRY(to_device(dets, n, &dd, arena));
+  ASCI_TRY(stage_ints(ints, arena, &h1, &eri));
+  ASCI_TRY(out_buffer(out_haa, n, &dout, arena));
+  {
+    // no bits at or above norb (they would index past the integral tables)
+    unsigned *derr;
+    uint64_t *tk;
+    uint32_t *ti;
+    double *tc;
+    ASCI_TRY(arena.alloc(&derr, 1));
+    ASCI_TRY(arena.alloc(&tk, n));
+    ASCI_TRY(arena.alloc(&ti, n));
+    ASCI_TRY(arena.alloc(&tc, n));
+    ASCI_TRY_CUDA(cudaMemsetAsync(derr, 0, sizeof(unsigned), s));
+    ASCI_TRY_CUDA(cudaMemsetAsync(tc, 0, n * sizeof(double), s));
+    k_prepare_psi<<<grid_for(n), 256, 0, s>>>(dd, tc, n, ints->norb, -1, -1, tk, ti, derr);
+    ASCI_CHECK_LAUNCH();
+    unsigned herr = 0;
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(herr), cudaMemcpyDefault, s));
+    ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+    if (herr & kBadRange) return ASCI_EINVAL;
+  }
+  DevInts I;
+  ASCI_TRY(build_tables(h1, eri, ints->norb, 0, 0, ints->ecore, false, arena, &I));
+  uint64_t *k;
+  ASCI_TRY(arena.alloc(&k, n));
+  k_input_keys<<<grid_for(n), 256, 0, s>>>(dd, n, k);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(diagonal_packed(I, k, n, dout, arena));
+  ASCI_TRY(finish_out(out_haa, dout, n, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  return ASCI_OK;
+}
+
+int asci_sort_accumulate(const asci_det *keys, const double *values, size_t n,
+                         asci_det *out_keys, double *out_sums, size_t *out_n,
+                         void *cuda_stream) {
+  if (out_n) *out_n = 0;
+  if (!keys || !values || !out_keys || !out_sums || !out_n) return ASCI_EINVAL;
+  if (n == 0) return ASCI_OK;
+  if (n >= (1ull << 32)) return ASCI_EINVAL;
+  cudaStream_t s;
+  ASCI_TRY(begin_call(cuda_stream, &s));
+  Arena arena(s);
+  const asci_det *dk;
+  const double *dv;
+  ASCI_TRY(to_device(keys, n, &dk, arena));
+  ASCI_TRY(to_device(values, n, &dv, arena));
+  uint64_t *k0, *k1, *uk;
+  double *v0, *v1, *us;
+  asci_det *dok;
+  ASCI_TRY(arena.alloc(&k0, n));
+  ASCI_TRY(arena.alloc(&k1, n));
+  ASCI_TRY(arena.alloc(&uk, n));
+  ASCI_TRY(arena.alloc(&v0, n));
+  ASCI_TRY(arena.alloc(&v1, n));
+  ASCI_TRY(out_buffer(out_sums, n, &us, arena));
+  ASCI_TRY(out_buffer(out_keys, n, &dok, arena));
+  k_input_keys<<<grid_for(n), 256, 0, s>>>(dk, n, k0);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY_CUDA(cudaMemcpyAsync(v0, dv, n * sizeof(double), cudaMemcpyDefault, s));
+  size_t u = 0;
+  ASCI_TRY(sort_accumulate(&k0, &k1, &v0, &v1, n, uk, us, &u, arena));
+  k_unpack<<<grid_for(u), 256, 0, s>>>(uk, u, dok);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(finish_out(out_sums, us, u, s));
+  ASCI_TRY(finish_out(out_keys, dok, u, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  *out_n = u;
+  return ASCI_OK;
+}
+
+int asci_select_topn(const asci_det *keys, const double *scores, size_t n, size_t N,
+                     asci_det *out_keys, double *out_scores, size_t *out_n,
+                     void *cuda_stream) {
+  if (out_n) *out_n = 0;
+  if (!keys || !scores || !out_n || (N && (!out_keys || !out_scores))) return ASCI_EINVAL;
+  if (n == 0 || N == 0) return ASCI_OK;
+  if (n >= (1ull << 32)) return ASCI_EINVAL;
+  cudaStream_t s;
+  ASCI_TRY(begin_call(cuda_stream, &s));
+  Arena arena(s);
+  const asci_det *dk;
+  const double *ds;
+  ASCI_TRY(to_device(keys, n, &dk, arena));
+  ASCI_TRY(to_device(scores, n, &ds, arena));
+  const size_t m0 = std::min(n, N);
+  uint64_t *k, *ok;
+  double *os;
+  asci_det *dok;
+  ASCI_TRY(arena.alloc(&k, n));
+  ASCI_TRY(arena.alloc(&ok, m0));
+  ASCI_TRY(out_buffer(out_scores, m0, &os, arena));
+  ASCI_TRY(out_buffer(out_keys, m0, &dok, arena));
+  k_input_keys<<<grid_for(n), 256, 0, s>>>(dk, n, k);
+  ASCI_CHECK_LAUNCH();
+  size_t m = 0;
+  ASCI_TRY(select_topn_packed(k, ds, n, N, ok, os, &m, arena));
+  k_unpack<<<grid_for(m), 256, 0, s>>>(ok, m, dok);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(finish_out(out_scores, os, m, s));
+  ASCI_TRY(finish_out(out_keys, dok, m, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  *out_n = m;
+  return ASCI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,288 @@
+// Device-wide primitives: exclusive scan and a stable LSD radix sort.
+//
+// The sort is the "sort" of the paper's sort-and-accumulate (Sec. 2.2); it is
+// written for this library: 8-bit digits, one histogram (upsweep) kernel, a
+// device-wide scan of the digit-major histogram, and a scatter (downsweep)
+// kernel that ranks each tile's keys stably with warp ballots.
+#include "asci_internal.cuh"
+
+namespace asci {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <typename T>
+__device__ T block_exclusive_scan(T v, T *total) {
+  __shared__ T warp_sums[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    T w = lane < nw ? warp_sums[lane] : T(0);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    if (lane < nw) warp_sums[lane] = w;
+  }
+  __syncthreads();
+  T warp_prefix = warp ? warp_sums[warp - 1] : T(0);
+  if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return warp_prefix + x - v;
+}
+
+template <typename T>
+__global__ void k_tile_reduce(const T *in, size_t n, T *partial) {
+  size_t base = (size_t)blockIdx.x * kScanTile;
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    size_t idx = base + (size_t)i * kScanThreads + threadIdx.x;
+    if (idx < n) s += in[idx];
+  }
+  T total;
+  block_exclusive_scan<T>(s, &total);
+  if (threadIdx.x == 0) partial[blockIdx.x] = total;
+}
+
+template <typename T>
+__global__ void k_tile_scan(const T *in, T *out, size_t n, const T *partial) {
+  __shared__ T tile[kScanTile];
+  size_t base = (size_t)blockIdx.x * kScanTile;
+  // coalesced load into shared memory
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    size_t idx = base + (size_t)i * kScanThreads + threadIdx.x;
+    tile[i * kScanThreads + threadIdx.x] = idx < n ? in[idx] : T(0);
+  }
+  __syncthreads();
+  T v[kScanItems];
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = tile[threadIdx.x * kScanItems + i];
+    s += v[i];
+  }
+  T pre = block_exclusive_scan<T>(s, nullptr);
+  if (partial) pre += partial[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    tile[threadIdx.x * kScanItems + i] = pre;
+    pre += v[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    size_t idx = base + (size_t)i * kScanThreads + threadIdx.x;
+    if (idx < n) out[idx] = tile[i * kScanThreads + threadIdx.x];
+  }
+}
+
+template <typename T>
+int scan_exclusive(const T *in, T *out, size_t n, Arena &arena) {
+  if (n == 0) return ASCI_OK;
+  size_t nb = (n + kScanTile - 1) / kScanTile;
+  cudaStream_t s = arena.stream();
+  if (nb == 1) {
+    k_tile_scan<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    ASCI_CHECK_LAUNCH();
+    return ASCI_OK;
+  }
+  T *partial = nullptr;
+  ASCI_TRY(arena.alloc(&partial, nb));
+  k_tile_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(scan_exclusive<T>(partial, partial, nb, arena));
+  k_tile_scan<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partial);
+  ASCI_CHECK_LAUNCH();
+  return ASCI_OK;
+}
+
+// ----------------------------- radix sort ---------------------------------
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;  // per thread
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kRadix = 256;
+
+__global__ void k_digit_hist(const uint64_t *keys, size_t n, int shift, uint32_t *hist,
+                             uint32_t ntiles) {
+  __shared__ uint32_t h[kRadix];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  size_t base = (size_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+  for (int i = 0; i < kSortItems; ++i) {
+    size_t idx = base + (size_t)i * kSortThreads + threadIdx.x;
+    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 0xffu], 1u);
+  }
+  __syncthreads();
+  hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// lanes of this warp whose digit equals mine (8 ballots)
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, uint32_t active) {
+  uint32_t peers = active;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+    peers &= ((d >> b) & 1u) ? bal : ~bal;
+  }
+  return peers;
+}
+
+// Stable scatter of one tile.  Warp w owns elements [w*32*kSortItems, ...) of
+// the tile in rounds of 32 consecutive elements, so tile order is preserved.
+template <typename V, bool kHasVals>
+__global__ void __launch_bounds__(kSortThreads)
+    k_digit_scatter(const uint64_t *keys_in, const V *vals_in, uint64_t *keys_out, V *vals_out,
+                    size_t n, int shift, const uint32_t *offsets, uint32_t ntiles) {
+  __shared__ uint32_t warp_base[kSortWarps][kRadix];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads)
+    (&warp_base[0][0])[i] = 0;
+  __syncthreads();
+  const size_t wbase = (size_t)blockIdx.x * kSortTile + (size_t)warp * 32 * kSortItems;
+  uint64_t k[kSortItems];
+  uint32_t d[kSortItems];
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    size_t idx = wbase + (size_t)r * 32 + lane;
+    bool ok = idx < n;
+    k[r] = ok ? keys_in[idx] : 0ull;
+    d[r] = ok ? (uint32_t)((k[r] >> shift) & 0xffu) : 0u;
+    uint32_t active = __ballot_sync(0xffffffffu, ok);
+    uint32_t peers = digit_peers(d[r], active);
+    if (ok && lane == __ffs(peers) - 1) warp_base[warp][d[r]] += __popc(peers);
+  }
+  __syncthreads();
+  // per digit: tile offset + counts of earlier warps
+  {
+    const int dig = threadIdx.x;  // kSortThreads == kRadix
+    uint32_t run = offsets[(size_t)dig * ntiles + blockIdx.x];
+    for (int w = 0; w < kSortWarps; ++w) {
+      uint32_t c = warp_base[w][dig];
+      warp_base[w][dig] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    size_t idx = wbase + (size_t)r * 32 + lane;
+    bool ok = idx < n;
+    uint32_t active = __ballot_sync(0xffffffffu, ok);
+    uint32_t peers = digit_peers(d[r], active);
+    uint32_t pos = 0;
+    if (ok) pos = warp_base[warp][d[r]] + __popc(peers & lt);
+    __syncwarp();
+    if (ok && lane == __ffs(peers) - 1) warp_base[warp][d[r]] += __popc(peers);
+    __syncwarp();
+    if (ok) {
+      keys_out[pos] = k[r];
+      if (kHasVals) vals_out[pos] = vals_in[idx];
+    }
+  }
+}
+
+template <typename V, bool kHasVals>
+int radix_sort_impl(uint64_t **keys, uint64_t **keys_alt, V **vals, V **vals_alt, size_t n,
+                    int begin_bit, int end_bit, Arena &arena) {
+  if (n <= 1 || begin_bit >= end_bit) return ASCI_OK;
+  if (n >= (1ull << 32)) return ASCI_EINVAL;
+  cudaStream_t s = arena.stream();
+  uint32_t ntiles = (uint32_t)((n + kSortTile - 1) / kSortTile);
+  uint32_t *hist = nullptr;
+  ASCI_TRY(arena.alloc(&hist, (size_t)kRadix * ntiles));
+  uint64_t mask = 0;
+  ASCI_TRY(varying_bits_u64(*keys, n, &mask, arena));
+  for (int shift = begin_bit; shift < end_bit; shift += 8) {
+    uint64_t dmask = (0xffull << shift);
+    if (end_bit - shift < 8) dmask &= ((end_bit >= 64) ? ~0ull : ((1ull << end_bit) - 1));
+    if ((mask & dmask) == 0) continue;  // digit constant over the input
+    k_digit_hist<<<ntiles, kSortThreads, 0, s>>>(*keys, n, shift, hist, ntiles);
+    ASCI_CHECK_LAUNCH();
+    ASCI_TRY(scan_exclusive<uint32_t>(hist, hist, (size_t)kRadix * ntiles, arena));
+    k_digit_scatter<V, kHasVals><<<ntiles, kSortThreads, 0, s>>>(
+        *keys, kHasVals ? *vals : nullptr, *keys_alt, kHasVals ? *vals_alt : nullptr, n, shift,
+        hist, ntiles);
+    ASCI_CHECK_LAUNCH();
+    uint64_t *t = *keys;
+    *keys = *keys_alt;
+    *keys_alt = t;
+    if (kHasVals) {
+      V *tv = *vals;
+      *vals = *vals_alt;
+      *vals_alt = tv;
+    }
+  }
+  return ASCI_OK;
+}
+
+__global__ void k_varying(const uint64_t *keys, size_t n, unsigned long long *out) {
+  uint64_t k0 = keys[0], acc = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    acc |= keys[i] ^ k0;
+  for (int d = 16; d; d >>= 1) acc |= __shfl_xor_sync(0xffffffffu, acc, d);
+  if ((threadIdx.x & 31) == 0 && acc) atomicOr(out, (unsigned long long)acc);
+}
+
+}  // namespace
+
+int scan_exclusive_u32(const uint32_t *in, uint32_t *out, size_t n, Arena &arena) {
+  return scan_exclusive<uint32_t>(in, out, n, arena);
+}
+int scan_exclusive_u64(const uint64_t *in, uint64_t *out, size_t n, Arena &arena) {
+  return scan_exclusive<uint64_t>(in, out, n, arena);
+}
+
+int varying_bits_u64(const uint64_t *keys, size_t n, uint64_t *host_mask, Arena &arena) {
+  *host_mask = 0;
+  if (n == 0) return ASCI_OK;
+  unsigned long long *d = nullptr;
+  ASCI_TRY(arena.alloc(&d, 1));
+  cudaStream_t s = arena.stream();
+  ASCI_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long), s));
+  unsigned blocks = (unsigned)((n + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_varying<<<blocks, 256, 0, s>>>(keys, n, d);
+  ASCI_CHECK_LAUNCH();
+  unsigned long long h = 0;
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  *host_mask = h;
+  return ASCI_OK;
+}
+
+int radix_sort_u64(uint64_t **keys, uint64_t **keys_alt, size_t n, int begin_bit, int end_bit,
+                   Arena &arena) {
+  return radix_sort_impl<uint32_t, false>(keys, keys_alt, nullptr, nullptr, n, begin_bit, end_bit,
+                                          arena);
+}
+int radix_sort_u64_u32(uint64_t **keys, uint64_t **keys_alt, uint32_t **vals, uint32_t **vals_alt,
+                       size_t n, int begin_bit, int end_bit, Arena &arena) {
+  return radix_sort_impl<uint32_t, true>(keys, keys_alt, vals, vals_alt, n, begin_bit, end_bit,
+                                         arena);
+}
+int radix_sort_u64_f64(uint64_t **keys, uint64_t **keys_alt, double **vals, double **vals_alt,
+                       size_t n, int begin_bit, int end_bit, Arena &arena) {
+  return radix_sort_impl<double, true>(keys, keys_alt, vals, vals_alt, n, begin_bit, end_bit,
+                                       arena);
+}
+
+}  // namespace asci

@@ -1,0 +1,63 @@
+"""The C ABI library builds for sm_103a and exports what include/asci.h declares (CPU)."""
+import ctypes as ct
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "asci.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(asci_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2303_05688_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_search_boundary():
+    names = _declared()
+    for f in ("asci_search", "asci_excitations", "asci_diagonal", "asci_sort_accumulate",
+              "asci_select_topn", "asci_default_opts", "asci_version", "asci_strerror"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", built_lib], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (asci_\w+)", out))
+    missing = [f for f in _declared() if f not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_host_only_calls_work(built_lib):
+    lib = ct.CDLL(built_lib)
+    lib.asci_version.restype = ct.c_char_p
+    assert b"sm_103a" in lib.asci_version()
+    lib.asci_strerror.restype = ct.c_char_p
+    assert lib.asci_strerror(-1) == b"invalid argument"
+    import paper_2303_05688_gb300 as m
+    o = m._Opts()
+    m.load().asci_default_opts(ct.byref(o))
+    assert o.eps_search == 0.0 and o.precision == 0 and o.max_batch_pairs == 0
+
+
+def test_library_is_built_for_sm_103a(built_lib):
+    from paper_2303_05688_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    import paper_2303_05688_gb300 as m
+    monkeypatch.setattr(m, "_LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(m, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        m.load()

@@ -1,0 +1,281 @@
+"""GPU parity: libasci (through the C ABI) against the CPU oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from tests._parity import compare_candidates, compare_selection, key_order, score_tol, to_u64_pairs
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def asci():
+    import paper_2303_05688_gb300 as m
+    m.load()
+    return m
+
+
+def _hubbard():
+    with open(os.path.join(HERE, "golden", "hubbard_8e8o_psi.json")) as f:
+        d = json.load(f)
+    h1, eri, ec = W.hubbard_ring(8, 1.0, 4.0)
+    A = np.array(d["alpha"], dtype=np.uint64)
+    B = np.array(d["beta"], dtype=np.uint64)
+    return h1, eri, ec, A, B, np.array(d["c"]), d["E0"]
+
+
+def _random(name, ndets=None):
+    w = W.WORKLOADS[name]
+    h1, eri, ec = w.integrals()
+    A, B, c = w.psi()
+    return w, h1, eri, ec, A, B, c, W.stored_e0(name)
+
+
+def _dev(torch, A, B):
+    return torch.tensor(np.stack([A, B], 1).astype(np.int64), device="cuda")
+
+
+# ---------------------------------------------------------------- stages ---
+
+@pytest.mark.parametrize("name", ["hubbard", "random_12e12o", "random_14e20o"])
+def test_excitations_match_oracle_pairs(torch_cuda, asci, oracle_mod, name):
+    torch = torch_cuda
+    if name == "hubbard":
+        h1, eri, ec, A, B, c, E0 = _hubbard()
+    else:
+        _, h1, eri, ec, A, B, c, E0 = _random(name)
+    core = np.arange(min(37, len(A)))
+    ta, tv = asci.excitations(torch.tensor(h1, device="cuda"), torch.tensor(eri, device="cuda"), ec,
+                              _dev(torch, A[core], B[core]), torch.tensor(c[core], device="cuda"))
+    ga, gb = to_u64_pairs(ta)
+    gv = tv.cpu().numpy()
+    ra, rb, rv = oracle_mod.pairs(oracle_mod.Ints(h1, eri, ec), A[core], B[core], c[core])
+    assert len(ga) == len(ra)
+    nexc = len(ra) // len(core)
+    for j in range(len(core)):
+        s = slice(j * nexc, (j + 1) * nexc)
+        o1 = key_order(ga[s], gb[s])
+        o2 = key_order(ra[s], rb[s])
+        assert np.array_equal(ga[s][o1], ra[s][o2]) and np.array_equal(gb[s][o1], rb[s][o2])
+        d = np.abs(gv[s][o1] - rv[s][o2])
+        assert np.all(d <= 1e-13 * np.maximum(np.abs(rv[s][o2]), 1e-3 * abs(c[core[j]]))), float(d.max())
+
+
+def test_diagonal_matches_oracle(torch_cuda, asci, oracle_mod):
+    torch = torch_cuda
+    _, h1, eri, ec, A, B, c, E0 = _random("random_14e20o")
+    ints = oracle_mod.Ints(h1, eri, ec + 0.75)
+    idx = np.arange(0, len(A), 37)
+    got = asci.diagonal(torch.tensor(h1, device="cuda"), torch.tensor(eri, device="cuda"), ec + 0.75,
+                        _dev(torch, A[idx], B[idx])).cpu().numpy()
+    ref = np.array([oracle_mod.diag(ints, (a, b)) for a, b in zip(A[idx], B[idx])])
+    assert np.all(np.abs(got - ref) <= 1e-13 * np.maximum(1.0, np.abs(ref)))
+
+
+def test_sort_accumulate_matches_numpy(torch_cuda, asci):
+    torch = torch_cuda
+    rng = np.random.default_rng(5)
+    for n in (1, 7, 4095, 4096, 4097, 100_003):
+        a = rng.integers(0, 1 << 12, n).astype(np.uint64)
+        b = rng.integers(0, 1 << 9, n).astype(np.uint64) << np.uint64(20)
+        v = rng.normal(size=n)
+        k, s = asci.sort_accumulate(_dev(torch, a, b), torch.tensor(v, device="cuda"))
+        ka, kb = to_u64_pairs(k)
+        key = (b << np.uint64(32)) | a
+        uk, inv = np.unique(key, return_inverse=True)
+        ref = np.zeros(len(uk))
+        np.add.at(ref, inv, v)
+        assert np.array_equal((kb << np.uint64(32)) | ka, uk)
+        assert np.allclose(s.cpu().numpy(), ref, rtol=0, atol=1e-12)
+
+
+def test_select_topn_matches_oracle(torch_cuda, asci, oracle_mod):
+    torch = torch_cuda
+    rng = np.random.default_rng(8)
+    n = 50_000
+    key = np.unique(rng.integers(0, 1 << 40, n).astype(np.uint64))
+    rng.shuffle(key)
+    n = len(key)
+    a, b = key & np.uint64(0xFFFFFFFF), key >> np.uint64(32)
+    s = rng.choice([-2.0, -1.0, 0.25, 1.0, 3.0], n) * rng.choice([1.0, 1.0 + 2 ** -40], n)
+    for N in (1, 10, 999, 12345, n - 1, n, n + 5):
+        k, sc = asci.select_topn(_dev(torch, a, b), torch.tensor(s, device="cuda"), N)
+        ga, gb = to_u64_pairs(k)
+        idx = oracle_mod.topn(a, b, s, N)
+        assert set(zip(ga.tolist(), gb.tolist())) == set(zip(a[idx].tolist(), b[idx].tolist()))
+
+
+# ---------------------------------------------------------------- search ---
+
+def _run(asci, torch, A, B, c, E0, h1, eri, ec, C, N, device=True, **kw):
+    if device:
+        d = _dev(torch, A, B)
+        cf = torch.tensor(c, device="cuda")
+        hh, ee = torch.tensor(h1, device="cuda"), torch.tensor(eri, device="cuda")
+    else:
+        d, cf, hh, ee = np.stack([A, B], 1), c, h1, eri
+    od, osc, st = asci.search(d, cf, E0, hh, ee, ec, C, N, **kw)
+    ga, gb = to_u64_pairs(od)
+    gs = osc.cpu().numpy() if hasattr(osc, "cpu") else np.asarray(osc)
+    return ga, gb, gs, st
+
+
+CASES = [("hubbard", 100), ("random_12e12o", 200), ("random_10e14o", 150), ("random_14e20o", 400)]
+
+
+@pytest.mark.parametrize("name,C", CASES)
+def test_search_all_candidates_match_oracle(torch_cuda, asci, oracle_mod, name, C):
+    torch = torch_cuda
+    if name == "hubbard":
+        h1, eri, ec, A, B, c, E0 = _hubbard()
+    else:
+        _, h1, eri, ec, A, B, c, E0 = _random(name)
+    ref = oracle_mod.search(oracle_mod.Ints(h1, eri, ec), A, B, c, E0, C)
+    ga, gb, gs, st = _run(asci, torch, A, B, c, E0, h1, eri, ec, C, len(ref.a) + 100)
+    compare_candidates(ga, gb, gs, ref, E0)
+    assert st.generated == ref.generated and st.unique == ref.unique
+    assert st.excluded == ref.excluded and st.selected == len(ref.a)
+
+
+@pytest.mark.parametrize("name,C,N", [("hubbard", 100, 1000), ("random_12e12o", 200, 5000),
+                                      ("random_14e20o", 400, 20000), ("random_10e14o", 150, 1)])
+def test_search_top_n_matches_oracle(torch_cuda, asci, oracle_mod, name, C, N):
+    torch = torch_cuda
+    if name == "hubbard":
+        h1, eri, ec, A, B, c, E0 = _hubbard()
+    else:
+        _, h1, eri, ec, A, B, c, E0 = _random(name)
+    ref = oracle_mod.search(oracle_mod.Ints(h1, eri, ec), A, B, c, E0, C)
+    sel = ref.topn(N)
+    ga, gb, gs, st = _run(asci, torch, A, B, c, E0, h1, eri, ec, C, N, device=False)
+    assert len(ga) == min(N, len(ref.a))
+    compare_selection(ga, gb, ref, sel, E0)
+
+
+def test_search_independent_of_batching_and_constraint_level(torch_cuda, asci):
+    torch = torch_cuda
+    _, h1, eri, ec, A, B, c, E0 = _random("random_14e20o")
+    base = _run(asci, torch, A, B, c, E0, h1, eri, ec, 400, 10**7)
+    assert base[3].batches == 1
+    for bmax, lvl in ((200_000, 0), (50_000, 4), (9_000, 0), (3_000, 7)):
+        got = _run(asci, torch, A, B, c, E0, h1, eri, ec, 400, 10**7, max_batch_pairs=bmax,
+                   max_constraint_level=lvl)
+        assert got[3].batches > 1
+        o0, o1 = key_order(base[0], base[1]), key_order(got[0], got[1])
+        assert np.array_equal(base[0][o0], got[0][o1]) and np.array_equal(base[1][o0], got[1][o1])
+        # contributions to one target keep their order under any batching: sums are bit-identical
+        assert np.array_equal(base[2][o0], got[2][o1])
+
+
+def test_search_eps_screen(torch_cuda, asci, oracle_mod):
+    torch = torch_cuda
+    _, h1, eri, ec, A, B, c, E0 = _random("random_12e12o")
+    ints = oracle_mod.Ints(h1, eri, ec)
+    eps = 3e-7
+    ref = oracle_mod.search(ints, A, B, c, E0, 200, eps=eps)
+    ga, gb, gs, st = _run(asci, torch, A, B, c, E0, h1, eri, ec, 200, 10**6, eps=eps)
+    assert 0 < st.surviving < st.generated
+    # pairs within 1e-12 relative of eps may flip; none do in this case
+    assert st.surviving == ref.surviving
+    compare_candidates(ga, gb, gs, ref, E0)
+
+
+def test_search_host_and_device_inputs_agree(torch_cuda, asci):
+    torch = torch_cuda
+    _, h1, eri, ec, A, B, c, E0 = _random("random_10e14o")
+    r1 = _run(asci, torch, A, B, c, E0, h1, eri, ec, 150, 3000, device=True, sort_output=True)
+    r2 = _run(asci, torch, A, B, c, E0, h1, eri, ec, 150, 3000, device=False, sort_output=True)
+    for x, y in zip(r1[:3], r2[:3]):
+        assert np.array_equal(x, y)
+    k = (r1[1] << np.uint64(32)) | r1[0]
+    assert np.all(k[1:] > k[:-1])
+
+
+def test_search_edge_cases(torch_cuda, asci, oracle_mod):
+    torch = torch_cuda
+    _, h1, eri, ec, A, B, c, E0 = _random("random_10e14o")
+    # C larger than psi is clamped; N = 0 returns nothing
+    ga, gb, gs, st = _run(asci, torch, A[:5], B[:5], c[:5], E0, h1, eri, ec, 50, 0)
+    assert len(ga) == 0 and st.ncore == 5
+    ref = oracle_mod.search(oracle_mod.Ints(h1, eri, ec), A[:5], B[:5], c[:5], E0, 50)
+    ga, gb, gs, st = _run(asci, torch, A[:5], B[:5], c[:5], E0, h1, eri, ec, 50, 10**6)
+    compare_candidates(ga, gb, gs, ref, E0)
+    # a single determinant, C = 1
+    ref = oracle_mod.search(oracle_mod.Ints(h1, eri, ec), A[:1], B[:1], c[:1], E0, 1)
+    ga, gb, gs, st = _run(asci, torch, A[:1], B[:1], c[:1], E0, h1, eri, ec, 1, 10**6)
+    compare_candidates(ga, gb, gs, ref, E0)
+    # no beta excitations possible (beta string empty): only alpha-side work
+    n = 6
+    h1s, eris, _ = W.random_molecular(n, 3)
+    Aa = np.array([0b000111, 0b001011, 0b010101], dtype=np.uint64)
+    Bb = np.zeros(3, dtype=np.uint64)
+    cc = np.array([0.9, -0.3, 0.1])
+    ref = oracle_mod.search(oracle_mod.Ints(h1s, eris, 0.0), Aa, Bb, cc, -1.0, 3)
+    ga, gb, gs, st = _run(asci, torch, Aa, Bb, cc, -1.0, h1s, eris, 0.0, 3, 10**6)
+    compare_candidates(ga, gb, gs, ref, -1.0)
+
+
+@pytest.mark.parametrize("bad", ["norb", "dup", "count", "nan", "C0", "range"])
+def test_search_rejects_invalid_input(torch_cuda, asci, bad):
+    _, h1, eri, ec, A, B, c, E0 = _random("random_10e14o")
+    A, B, c = A[:50].copy(), B[:50].copy(), c[:50].copy()
+    C = 10
+    if bad == "norb":
+        h1 = np.zeros((33, 33))
+        eri = np.zeros((33,) * 4)
+    elif bad == "dup":
+        A[7], B[7] = A[3], B[3]
+    elif bad == "count":
+        A[9] = A[9] | np.uint64(1 << 13) if not (int(A[9]) >> 13) & 1 else A[9] ^ np.uint64(1 << 13)
+    elif bad == "nan":
+        c[4] = np.nan
+    elif bad == "C0":
+        C = 0
+    elif bad == "range":
+        A[2] = A[2] | np.uint64(1 << 20)
+    with pytest.raises(asci.AsciError) as e:
+        asci.search(np.stack([A, B], 1), c, E0, h1, eri, ec, C, 100)
+    assert e.value.code == -1
+
+
+def test_search_full_size_16e16o_sampled(torch_cuda, asci, oracle_mod):
+    """Full (16e,16o) workload (C = 1e4, N = 1e5): sampled outputs against the oracle."""
+    torch = torch_cuda
+    w, h1, eri, ec, A, B, c, E0 = _random("random_16e16o")
+    ga, gb, gs, st = _run(asci, torch, A, B, c, E0, h1, eri, ec, w.C, w.N)
+    assert st.generated == w.C * W.n_excitations(16, 8, 8)
+    assert len(ga) == w.N
+    _check_sampled(oracle_mod, h1, eri, ec, A, B, c, E0, w.C, ga, gb, gs, 64, seed=1)
+
+
+def _check_sampled(oracle_mod, h1, eri, ec, A, B, c, E0, C, ga, gb, gs, nsample, seed):
+    ints = oracle_mod.Ints(h1, eri, ec)
+    core = oracle_mod.core_select(A, B, c, C)
+    CA, CB, CC = A[core], B[core], c[core]
+    psi = set(zip(A.tolist(), B.tolist()))
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(len(ga), min(nsample, len(ga)), replace=False)
+    idx = np.concatenate([idx, np.argsort(-np.abs(gs))[:8]])
+    for i in idx:
+        t = (int(ga[i]), int(gb[i]))
+        assert t not in psi
+        num, abss = oracle_mod.numerator(ints, t, CA, CB, CC)
+        haa = oracle_mod.diag(ints, t)
+        S = num / (E0 - haa)
+        assert abs(gs[i] - S) <= score_tol(S, abss, haa, E0), (t, gs[i], S)
+    # every selected |S| is at least the smallest selected one (trivially) and the
+    # set is closed: no key repeats
+    assert len(set(zip(ga.tolist(), gb.tolist()))) == len(ga)
