@@ -35,7 +35,8 @@ def compare_candidates(got_a, got_b, got_s, ref, E0):
     assert np.array_equal(got_b[o1], ref.b[o2]), "beta words differ"
     tol = score_tol(ref.score[o2], ref.abssum[o2], ref.haa[o2], E0)
     err = np.abs(got_s[o1] - ref.score[o2])
-    worst = float(np.max(err / tol)) if len(err) else 0.0
+    ratio = np.divide(err, tol, out=np.zeros_like(err), where=tol > 0)
+    worst = float(np.max(ratio)) if len(err) else 0.0
     assert np.all(err <= tol), f"score error {worst:.3g} x tolerance"
     return worst
 
