@@ -128,6 +128,25 @@ __device__ __forceinline__ void unrank_pair(uint32_t r, int *x, int *y) {
   *x = (int)(r - (uint32_t)(yy * (yy - 1) / 2));
 }
 
+// Division by a loop-invariant divisor with a multiply-high and two shifts
+// (the round-up method of Granlund and Montgomery, 1994); exact for every
+// 32-bit dividend and divisors 1 <= d < 2^31.
+struct FastDiv {
+  uint32_t d, m, s1, s2;
+  __host__ __device__ FastDiv() : d(1), m(1), s1(0), s2(0) {}
+  __host__ explicit FastDiv(uint32_t div) : d(div) {
+    uint32_t l = 0;
+    while ((1ull << l) < (uint64_t)div) ++l;
+    m = (uint32_t)((((1ull << 32) * ((1ull << l) - div)) / div) + 1);
+    s1 = l < 1 ? l : 1;
+    s2 = l > 0 ? l - 1 : 0;
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    uint32_t t = __umulhi(n, m);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // integral tables resident on the device for one search
 // ---------------------------------------------------------------------------

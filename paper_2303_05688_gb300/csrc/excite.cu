@@ -292,122 +292,6 @@ __global__ void k_item_weights(const uint64_t *items, uint64_t nitems, int opbit
   }
 }
 
-constexpr int kEmitThreads = 256;
-constexpr int kEmitPer = 4;
-constexpr int kEmitTile = kEmitThreads * kEmitPer;
-
-// One CTA per tile of kEmitTile consecutive pair indices of the batch.  The
-// items overlapping the tile (at most kEmitTile, every item having >= 1 pair)
-// and their starting pair offsets are staged in shared memory; each pair finds
-// its item by binary search there, then decodes (core det, excitation).
-__global__ void __launch_bounds__(kEmitThreads)
-    k_emit_batch(DevInts I, ExcCounts X, const uint64_t *items, const uint64_t *Wexcl,
-                 uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1, int opbits,
-                 const uint32_t *grp_alpha, const uint32_t *grp_start, const uint32_t *core_beta,
-                 const double *core_c, uint64_t *out_keys, double *out_vals) {
-  __shared__ uint64_t sW[kEmitTile];
-  __shared__ uint64_t sIt[kEmitTile];
-  __shared__ uint64_t s_ta, s_nspan;
-  const uint64_t pb = P0 + (uint64_t)blockIdx.x * kEmitTile;
-  const uint64_t pe = (pb + kEmitTile < P1) ? pb + kEmitTile : P1;
-  if (threadIdx.x == 0) {
-    // last item whose start offset is <= pb, then last item starting <= pe-1
-    uint64_t lo = t0, hi = t1 - 1;
-    while (lo < hi) {
-      uint64_t mid = (lo + hi + 1) >> 1;
-      if (Wexcl[mid] <= pb) lo = mid; else hi = mid - 1;
-    }
-    uint64_t ta = lo;
-    hi = t1 - 1;
-    while (lo < hi) {
-      uint64_t mid = (lo + hi + 1) >> 1;
-      if (Wexcl[mid] <= pe - 1) lo = mid; else hi = mid - 1;
-    }
-    s_ta = ta;
-    s_nspan = lo - ta + 1;
-  }
-  __syncthreads();
-  const uint64_t ta = s_ta;
-  const int nspan = (int)s_nspan;
-  for (int i = threadIdx.x; i < nspan; i += kEmitThreads) {
-    sIt[i] = items[ta + i];
-    sW[i] = Wexcl[ta + i];
-  }
-  __syncthreads();
-  const uint32_t full = full_mask(I.n);
-  const uint32_t omask = (1u << opbits) - 1u;
-  const uint32_t npd0 = X.sb + (uint32_t)X.dbb, npd1 = 1u + X.sb;
-#pragma unroll 1
-  for (int r = 0; r < kEmitPer; ++r) {
-    const uint64_t p = pb + (uint64_t)r * kEmitThreads + threadIdx.x;
-    if (p >= pe) continue;
-    int lo = 0, hi = nspan - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (sW[mid] <= p) lo = mid; else hi = mid - 1;
-    }
-    const uint64_t it = sIt[lo];
-    const uint32_t q = (uint32_t)(p - sW[lo]);
-    const uint32_t At = (uint32_t)(it >> 32);
-    const uint32_t k = (uint32_t)it >> opbits, o = (uint32_t)it & omask;
-    const uint32_t A = grp_alpha[k], va = ~A & full;
-    uint32_t ta = At, tb;
-    double h;
-    if (o == 0) {
-      // beta singles, then beta-beta doubles of core det m
-      const uint32_t m = q / npd0, e = q - m * npd0;
-      const uint32_t jdx = grp_start[k] + m;
-      const uint32_t B = core_beta[jdx], vb = ~B & full;
-      int i, j, a, b;
-      if (e < X.sb) {
-        decode_single(B, vb, e, X.vb, &i, &a);
-        tb = B ^ (1u << i) ^ (1u << a);
-        double v = single_value(I, B, A, i, a);
-        h = single_parity(B, i, a) ? -v : v;
-      } else {
-        decode_double(B, vb, e - X.sb, X.pb_p, &i, &j, &a, &b);
-        tb = B ^ (1u << i) ^ (1u << j) ^ (1u << a) ^ (1u << b);
-        double v = eri4(I.asym, I.n, i, a, j, b);
-        h = double_parity(B, i, j, a, b) ? -v : v;
-      }
-      out_keys[p - P0] = pack_key(ta, tb);
-      out_vals[p - P0] = h * core_c[jdx];
-    } else if (o <= X.sa) {
-      // the alpha single itself (e == 0) or alpha single x beta single
-      const uint32_t m = q / npd1, e = q - m * npd1;
-      const uint32_t jdx = grp_start[k] + m;
-      const uint32_t B = core_beta[jdx];
-      int i, a;
-      decode_single(A, va, o - 1, X.va, &i, &a);
-      const int pa = single_parity(A, i, a);
-      if (e == 0) {
-        tb = B;
-        double v = single_value(I, A, B, i, a);
-        h = pa ? -v : v;
-      } else {
-        const uint32_t vb = ~B & full;
-        int j, b;
-        decode_single(B, vb, e - 1, X.vb, &j, &b);
-        tb = B ^ (1u << j) ^ (1u << b);
-        double v = eri4(I.eri, I.n, i, a, j, b);
-        h = (pa ^ single_parity(B, j, b)) ? -v : v;
-      }
-      out_keys[p - P0] = pack_key(ta, tb);
-      out_vals[p - P0] = h * core_c[jdx];
-    } else {
-      // alpha-alpha double, one pair per core det
-      const uint32_t jdx = grp_start[k] + q;
-      int i, j, a, b;
-      decode_double(A, va, o - 1 - X.sa, X.pa_p, &i, &j, &a, &b);
-      double v = eri4(I.asym, I.n, i, a, j, b);
-      h = double_parity(A, i, j, a, b) ? -v : v;
-      tb = core_beta[jdx];
-      out_keys[p - P0] = pack_key(ta, tb);
-      out_vals[p - P0] = h * core_c[jdx];
-    }
-  }
-}
-
 }  // namespace
 
 int make_items(const ExcCounts &X, int n, const uint32_t *grp_alpha, uint32_t ngroups,
@@ -429,20 +313,6 @@ int item_weights(const uint64_t *items, uint64_t nitems, int opbits, const uint3
   if (blocks > 152 * 64) blocks = 152 * 64;
   k_item_weights<<<(unsigned)blocks, 256, 0, arena.stream()>>>(items, nitems, opbits, grp_count,
                                                                X, w);
-  ASCI_CHECK_LAUNCH();
-  return ASCI_OK;
-}
-
-int emit_batch(const DevInts &I, const ExcCounts &X, const uint64_t *items, const uint64_t *Wexcl,
-               uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1, int opbits,
-               const uint32_t *grp_alpha, const uint32_t *grp_start, const uint32_t *core_beta,
-               const double *core_c, uint64_t *out_keys, double *out_vals, Arena &arena) {
-  if (P1 <= P0) return ASCI_OK;
-  uint64_t tiles = (P1 - P0 + kEmitTile - 1) / kEmitTile;
-  if (tiles >= (1ull << 31)) return ASCI_EINVAL;
-  k_emit_batch<<<(unsigned)tiles, kEmitThreads, 0, arena.stream()>>>(
-      I, X, items, Wexcl, t0, t1, P0, P1, opbits, grp_alpha, grp_start, core_beta, core_c,
-      out_keys, out_vals);
   ASCI_CHECK_LAUNCH();
   return ASCI_OK;
 }

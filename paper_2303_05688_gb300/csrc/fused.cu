@@ -1,0 +1,1161 @@
+// Constraint-tile search: the batched hot loop of Algorithm 2 with on-chip
+// sort-and-accumulate (Sec. 2.2) and the score of Eq. 1.
+//
+// Work is partitioned by target alpha string A' (the finest constraint class:
+// all occupied alpha orbitals fixed).  Items sorted by A' (see excite.cu) make
+// each class a contiguous range; a batch of classes is generated into a
+// staging buffer as records (beta', core index j, v = H_ij c_j, H_ii) and then
+// reduced tile by tile on chip:
+//   small classes (<= kCap/2 pairs)   packed, several per tile, in item order
+//   medium classes (<= kCap pairs)    one tile each, in item order
+//   big classes                       split into hash buckets of beta' (each a
+//                                     tile); all contributions to one target
+//                                     land in the same bucket
+// A tile is sorted in shared memory by a stable LSD radix sort, runs of equal
+// targets are summed, targets in psi are dropped, and targets whose |score|
+// can reach the running top-N threshold are scored exactly and appended.
+//
+// The diagonal H_ii is carried exactly in 64-bit fixed point: the integral
+// terms are rounded once to multiples of 2^-s, and each pair's H_ii is the
+// parent's H_jj plus the excitation's change, computed from the parent's
+// Fock-like diagonals F_s(p) = h_pp + sum_{q in s} (J-K)_pq + sum_{q in s'} J_pq.
+// Integer sums are exact, so every path to a target gives the same H_ii.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "asci_internal.cuh"
+#include "fused.cuh"
+
+namespace asci {
+
+// ----------------------------------------------------------- fixed point ---
+
+
+namespace {
+
+__global__ void k_fx_bound(const double *h1, const double *eri, int n, double *out3) {
+  // out3[0] = max |h_pp|, out3[1] = max_{p!=q} |J-K|, out3[2] = max_{p,q} |J|
+  double a = 0, b = 0, c = 0;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int p = t / n, q = t % n;
+    double J = eri[(((size_t)p * n + p) * n + q) * n + q];
+    double K = eri[(((size_t)p * n + q) * n + q) * n + p];
+    if (p == q) a = fmax(a, fabs(h1[p * n + p]));
+    if (p != q) b = fmax(b, fabs(J - K));
+    c = fmax(c, fabs(J));
+  }
+  __shared__ double sh[3][256];
+  sh[0][threadIdx.x] = a;
+  sh[1][threadIdx.x] = b;
+  sh[2][threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int i = 0; i < blockDim.x; ++i) {
+      s0 = fmax(s0, sh[0][i]);
+      s1 = fmax(s1, sh[1][i]);
+      s2 = fmax(s2, sh[2][i]);
+    }
+    out3[0] = s0;
+    out3[1] = s1;
+    out3[2] = s2;
+  }
+}
+
+__global__ void k_fx_tables(const double *h1, const double *eri, int n, int s, int64_t *hh,
+                            int64_t *jk, int64_t *jj) {
+  const double sc = ldexp(1.0, s);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x) {
+    int p = t / n, q = t % n;
+    double J = eri[(((size_t)p * n + p) * n + q) * n + q];
+    double K = eri[(((size_t)p * n + q) * n + q) * n + p];
+    jk[t] = (p == q) ? 0 : __double2ll_rn((J - K) * sc);
+    jj[t] = __double2ll_rn(J * sc);
+    if (p == q) hh[p] = __double2ll_rn(h1[p * n + p] * sc);
+  }
+}
+
+}  // namespace
+
+__device__ __forceinline__ int64_t fx_diag(const FxInts &X, uint32_t A, uint32_t B) {
+  const int n = X.n;
+  int64_t s = X.ecore_x;
+  for (uint32_t m = A; m; m &= m - 1) {
+    const int p = __ffs(m) - 1;
+    s += X.hh[p];
+    for (uint32_t r = m & (m - 1); r; r &= r - 1) s += X.jk[p * n + __ffs(r) - 1];
+    for (uint32_t r = B; r; r &= r - 1) s += X.jj[p * n + __ffs(r) - 1];
+  }
+  for (uint32_t m = B; m; m &= m - 1) {
+    const int p = __ffs(m) - 1;
+    s += X.hh[p];
+    for (uint32_t r = m & (m - 1); r; r &= r - 1) s += X.jk[p * n + __ffs(r) - 1];
+  }
+  return s;
+}
+
+namespace {
+
+// Parent data of each core det (alpha-sorted order): H_jj and both Fock-like
+// diagonals.
+__global__ void k_core_fock(FxInts X, const uint32_t *core_alpha, const uint32_t *core_beta,
+                            size_t m, int64_t *Dx, int64_t *Fa, int64_t *Fb) {
+  const int n = X.n;
+  for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+       j += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t A = core_alpha[j], B = core_beta[j];
+    Dx[j] = fx_diag(X, A, B);
+    for (int p = 0; p < n; ++p) {
+      int64_t fa = X.hh[p], fb = X.hh[p];
+      for (uint32_t r = A; r; r &= r - 1) {
+        int q = __ffs(r) - 1;
+        fa += X.jk[p * n + q];
+        fb += X.jj[p * n + q];
+      }
+      for (uint32_t r = B; r; r &= r - 1) {
+        int q = __ffs(r) - 1;
+        fb += X.jk[p * n + q];
+        fa += X.jj[p * n + q];
+      }
+      Fa[j * n + p] = fa;
+      Fb[j * n + p] = fb;
+    }
+  }
+}
+
+__global__ void k_fx_check_diag(FxInts X, const uint64_t *keys, size_t n, int64_t *out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = fx_diag(X, key_alpha(keys[i]), key_beta(keys[i]));
+}
+
+// ------------------------------------------------------ groups of items ---
+
+__global__ void k_item_gflags(const uint64_t *items, uint64_t T, uint32_t *flag) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+       t += (uint64_t)gridDim.x * blockDim.x)
+    flag[t] = (t == 0 || (items[t] >> 32) != (items[t - 1] >> 32)) ? 1u : 0u;
+}
+
+__global__ void k_group_tab(const uint64_t *items, const uint32_t *flag, const uint32_t *gid,
+                            const uint64_t *Wexcl, uint64_t T, uint32_t *g_alpha, uint64_t *g_P0,
+                            uint64_t *g_item0) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+       t += (uint64_t)gridDim.x * blockDim.x)
+    if (flag[t]) {
+      uint32_t g = gid[t];
+      g_alpha[g] = (uint32_t)(items[t] >> 32);
+      g_P0[g] = Wexcl[t];
+      g_item0[g] = t;
+    }
+}
+
+// ------------------------------------------------------- tile planning ---
+
+enum : uint32_t { kTilePacked = 0, kTileMedium = 1, kTileBucket = 2 };
+
+constexpr uint32_t kDropped = 0xffffffffu;  // core index of a screened-out record
+
+struct TileDesc {
+  uint32_t start;   // first record in the batch staging buffer
+  uint32_t npairs;  // records in the tile
+  uint32_t g0;      // first group (global id)
+  uint32_t ng;      // groups (packed tiles)
+  uint32_t kind;
+  uint32_t alpha;   // target alpha string (medium / bucket tiles)
+};
+
+}  // namespace
+
+constexpr int kCellThreads = 512;
+constexpr int kCellItems = 16;
+constexpr int kCap = kCellThreads * kCellItems;  // records per tile
+constexpr uint32_t kSmallMax = kCap / 2;           // packable class size
+constexpr uint32_t kBucketTarget = (kCap * 5) / 10;  // expected records per bucket
+constexpr uint32_t kGroupsPerTile = 2048;
+
+namespace {
+
+__global__ void k_group_class(const uint64_t *g_P0, uint32_t gb0, uint32_t gb1, uint64_t Pend,
+                              uint32_t *kind, uint32_t *nb, uint64_t *small_pairs,
+                              uint32_t *small_cnt) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < gb1 - gb0;
+       i += gridDim.x * blockDim.x) {
+    const uint32_t g = gb0 + i;
+    const uint64_t P = ((g + 1 < gb1) ? g_P0[g + 1] : Pend) - g_P0[g];
+    uint32_t k = P <= kSmallMax ? kTilePacked : (P <= kCap ? kTileMedium : kTileBucket);
+    kind[i] = k;
+    nb[i] = k == kTileBucket ? (uint32_t)((P + kBucketTarget - 1) / kBucketTarget) : 0u;
+    small_pairs[i] = k == kTilePacked ? P : 0;
+    small_cnt[i] = k == kTilePacked ? 1u : 0u;
+  }
+}
+
+__device__ __forceinline__ bool packed_start(uint32_t i, const uint32_t *kind,
+                                             const uint64_t *Ws, const uint32_t *Ns) {
+  if (kind[i] != kTilePacked) return false;
+  if (i == 0 || kind[i - 1] != kTilePacked) return true;
+  return (Ws[i] / kSmallMax) != (Ws[i - 1] / kSmallMax) ||
+         (Ns[i] / kGroupsPerTile) != (Ns[i - 1] / kGroupsPerTile);
+}
+
+__global__ void k_tile_count(uint32_t ng, const uint32_t *kind, const uint32_t *nb,
+                             const uint64_t *Ws, const uint32_t *Ns, uint32_t *ntile) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x)
+    ntile[i] = kind[i] == kTilePacked ? (packed_start(i, kind, Ws, Ns) ? 1u : 0u)
+                                      : (kind[i] == kTileMedium ? 1u : nb[i]);
+}
+
+__global__ void k_tile_write(uint32_t gb0, uint32_t ng, uint64_t P0, uint64_t Pend,
+                             const uint64_t *g_P0, const uint32_t *g_alpha,
+                             const uint32_t *kind, const uint32_t *nb, const uint64_t *Ws,
+                             const uint32_t *Ns, const uint32_t *tile_base,
+                             const uint32_t *cellbase, const uint32_t *cnt,
+                             const uint32_t *cnt_scan, TileDesc *tiles, uint32_t *cell_pos0,
+                             unsigned *overflow) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
+    const uint32_t g = gb0 + i;
+    const uint64_t P = ((i + 1 < ng) ? g_P0[g + 1] : Pend) - g_P0[g];
+    const uint32_t start = (uint32_t)(g_P0[g] - P0);
+    const uint32_t k = kind[i];
+    if (k == kTilePacked) {
+      const bool st = packed_start(i, kind, Ws, Ns);
+      const uint32_t t = st ? tile_base[i] : tile_base[i] - 1;
+      if (st) {
+        tiles[t].start = start;
+        tiles[t].g0 = g;
+        tiles[t].kind = kTilePacked;
+        tiles[t].alpha = g_alpha[g];
+      }
+      atomicAdd(&tiles[t].npairs, (uint32_t)P);
+      atomicAdd(&tiles[t].ng, 1u);
+    } else if (k == kTileMedium) {
+      TileDesc d;
+      d.start = start;
+      d.npairs = (uint32_t)P;
+      d.g0 = g;
+      d.ng = 1;
+      d.kind = kTileMedium;
+      d.alpha = g_alpha[g];
+      tiles[tile_base[i]] = d;
+    } else {
+      const uint32_t cb = cellbase[i];
+      for (uint32_t b = 0; b < nb[i]; ++b) {
+        TileDesc d;
+        d.start = start + (cnt_scan[cb + b] - cnt_scan[cb]);
+        d.npairs = cnt[cb + b];
+        d.g0 = g;
+        d.ng = 1;
+        d.kind = kTileBucket;
+        d.alpha = g_alpha[g];
+        if (d.npairs > (uint32_t)kCap) atomicOr(overflow, 1u);
+        tiles[tile_base[i] + b] = d;
+        cell_pos0[cb + b] = d.start;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ emission ---
+
+__device__ __forceinline__ uint32_t bucket_of(uint32_t beta, uint32_t nb) {
+  return (uint32_t)(((uint64_t)(beta * 0x9E3779B1u) * nb) >> 32);
+}
+
+struct EmitArgs {
+  DevInts I;
+  FxInts X;
+  ExcCounts E;
+  FastDiv dv_va, dv_vb, dv_npd0, dv_npd1, dv_pa_p, dv_pb_p;
+  const uint64_t *items, *Wexcl;
+  const uint32_t *item_group;
+  uint64_t t0, t1, P0, P1;
+  int opbits;
+  const uint32_t *grp_alpha, *grp_start, *core_beta;
+  const double *core_c;
+  const int64_t *Dx, *Fa, *Fb;
+  uint32_t gb0;
+  const uint32_t *kind, *nb, *cellbase;
+  uint32_t *cnt;              // count mode
+  const uint32_t *cell_pos0;  // emit mode
+  uint32_t *fill;             // emit mode
+  uint32_t *sb_beta, *sb_j;
+  double *sb_val;
+  int64_t *sb_haa;
+  double eps;                 // Alg. 2 screen; 0 keeps every pair
+  int64_t E0_x;
+  double inv_scale;
+  unsigned long long *survivors;
+};
+
+constexpr int kEmitThreads = 256;
+constexpr int kEmitPer = 4;
+constexpr int kEmitTile = kEmitThreads * kEmitPer;
+
+__device__ __forceinline__ void dec_single(uint32_t s, uint32_t virt, uint32_t idx,
+                                           const FastDiv &dv, int *i, int *a) {
+  uint32_t q = dv.div(idx);
+  *i = nth_set_bit(s, (int)q);
+  *a = nth_set_bit(virt, (int)(idx - q * dv.d));
+}
+
+__device__ __forceinline__ void dec_double(uint32_t s, uint32_t virt, uint32_t idx,
+                                           const FastDiv &dv, int *i, int *j, int *a, int *b) {
+  uint32_t q = dv.div(idx);
+  int h1, h2, p1, p2;
+  unrank_pair(q, &h1, &h2);
+  unrank_pair(idx - q * dv.d, &p1, &p2);
+  *i = nth_set_bit(s, h1);
+  *j = nth_set_bit(s, h2);
+  *a = nth_set_bit(virt, p1);
+  *b = nth_set_bit(virt, p2);
+}
+
+__device__ __forceinline__ int par_double(uint32_t s, int i, int j, int a, int b) {
+  int p1 = single_parity(s, i, a);
+  uint32_t s1 = s ^ (1u << i) ^ (1u << a);
+  return p1 ^ single_parity(s1, j, b);
+}
+
+__device__ __forceinline__ double single_val(const DevInts &I, uint32_t s, uint32_t o, int i,
+                                             int a) {
+  const int n = I.n;
+  const double *ss = I.s_same + ((size_t)i * n + a) * n;
+  const double *so = I.s_opp + ((size_t)i * n + a) * n;
+  double v = I.h1[i * n + a];
+  for (uint32_t m = s; m; m &= m - 1) v += ss[__ffs(m) - 1];
+  for (uint32_t m = o; m; m &= m - 1) v += so[__ffs(m) - 1];
+  return v;
+}
+
+__device__ __forceinline__ double eri_at(const double *t, int n, int i, int a, int j, int b) {
+  return t[(((size_t)i * n + a) * n + j) * n + b];
+}
+
+// change of the diagonal for same-spin double i,j -> a,b with Fock-like F
+__device__ __forceinline__ int64_t dd_same(const int64_t *F, const int64_t *jk, int n, int i,
+                                           int j, int a, int b) {
+  return F[a] + F[b] - F[i] - F[j] + jk[i * n + j] + jk[a * n + b] - jk[a * n + i] -
+         jk[a * n + j] - jk[b * n + i] - jk[b * n + j];
+}
+
+template <int MODE>  // 0: count bucket sizes of big classes; 1: emit records
+__global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
+  extern __shared__ int64_t s_fx[];  // jk[n*n], jj[n*n]
+  __shared__ uint64_t sW[kEmitTile];
+  __shared__ uint64_t sIt[kEmitTile];
+  __shared__ uint32_t sG[kEmitTile];
+  __shared__ uint64_t s_ta, s_nspan;
+  const int n = A.I.n;
+  int64_t *s_jk = s_fx, *s_jj = s_fx + n * n;
+  if (MODE == 1)
+    for (int t = threadIdx.x; t < n * n; t += kEmitThreads) {
+      s_jk[t] = A.X.jk[t];
+      s_jj[t] = A.X.jj[t];
+    }
+  const uint64_t pb = A.P0 + (uint64_t)blockIdx.x * kEmitTile;
+  const uint64_t pe = (pb + kEmitTile < A.P1) ? pb + kEmitTile : A.P1;
+  if (threadIdx.x == 0) {
+    uint64_t lo = A.t0, hi = A.t1 - 1;
+    while (lo < hi) {
+      uint64_t mid = (lo + hi + 1) >> 1;
+      if (A.Wexcl[mid] <= pb) lo = mid; else hi = mid - 1;
+    }
+    const uint64_t ta = lo;
+    hi = A.t1 - 1;
+    while (lo < hi) {
+      uint64_t mid = (lo + hi + 1) >> 1;
+      if (A.Wexcl[mid] <= pe - 1) lo = mid; else hi = mid - 1;
+    }
+    s_ta = ta;
+    s_nspan = lo - ta + 1;
+  }
+  __syncthreads();
+  const uint64_t ta = s_ta;
+  const int nspan = (int)s_nspan;
+  for (int i = threadIdx.x; i < nspan; i += kEmitThreads) {
+    sIt[i] = A.items[ta + i];
+    sW[i] = A.Wexcl[ta + i];
+    sG[i] = A.item_group[ta + i];
+  }
+  __syncthreads();
+  const uint32_t full = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+  const uint32_t omask = (1u << A.opbits) - 1u;
+  const int lane = threadIdx.x & 31;
+#pragma unroll 1
+  for (int r = 0; r < kEmitPer; ++r) {
+    const uint64_t p = pb + (uint64_t)r * kEmitThreads + threadIdx.x;
+    const bool valid = p < pe;
+    uint32_t cell = 0xffffffffu;  // bucket cell of a big class, else none
+    uint32_t tb = 0, jdx = 0;
+    double h = 0.0;
+    int64_t dh = 0;
+    uint32_t At = 0;
+    bool big = false;
+    if (valid) {
+      int lo = 0, hi = nspan - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (sW[mid] <= p) lo = mid; else hi = mid - 1;
+      }
+      const uint64_t it = sIt[lo];
+      const uint32_t q = (uint32_t)(p - sW[lo]);
+      const uint32_t gi = sG[lo] - A.gb0;
+      big = A.kind[gi] == kTileBucket;
+      At = (uint32_t)(it >> 32);
+      const uint32_t k = (uint32_t)it >> A.opbits, o = (uint32_t)it & omask;
+      const uint32_t Ak = A.grp_alpha[k], va = ~Ak & full;
+      if (MODE == 0 && !big) {
+        // nothing to count
+      } else if (o == 0) {
+        const uint32_t m = A.dv_npd0.div(q), e = q - m * A.dv_npd0.d;
+        jdx = A.grp_start[k] + m;
+        const uint32_t B = A.core_beta[jdx], vb = ~B & full;
+        int i, j2, a, b;
+        if (e < A.E.sb) {
+          dec_single(B, vb, e, A.dv_vb, &i, &a);
+          tb = B ^ (1u << i) ^ (1u << a);
+          if (MODE == 1) {
+            const double v = single_val(A.I, B, Ak, i, a);
+            h = single_parity(B, i, a) ? -v : v;
+            const int64_t *F = A.Fb + (size_t)jdx * n;
+            dh = F[a] - F[i] - s_jk[a * n + i];
+          }
+        } else {
+          dec_double(B, vb, e - A.E.sb, A.dv_pb_p, &i, &j2, &a, &b);
+          tb = B ^ (1u << i) ^ (1u << j2) ^ (1u << a) ^ (1u << b);
+          if (MODE == 1) {
+            const double v = eri_at(A.I.asym, n, i, a, j2, b);
+            h = par_double(B, i, j2, a, b) ? -v : v;
+            dh = dd_same(A.Fb + (size_t)jdx * n, s_jk, n, i, j2, a, b);
+          }
+        }
+      } else if (o <= A.E.sa) {
+        const uint32_t m = A.dv_npd1.div(q), e = q - m * A.dv_npd1.d;
+        jdx = A.grp_start[k] + m;
+        const uint32_t B = A.core_beta[jdx];
+        int i, a;
+        dec_single(Ak, va, o - 1, A.dv_va, &i, &a);
+        if (e == 0) {
+          tb = B;
+          if (MODE == 1) {
+            const double v = single_val(A.I, Ak, B, i, a);
+            h = single_parity(Ak, i, a) ? -v : v;
+            const int64_t *F = A.Fa + (size_t)jdx * n;
+            dh = F[a] - F[i] - s_jk[a * n + i];
+          }
+        } else {
+          const uint32_t vb = ~B & full;
+          int j2, b;
+          dec_single(B, vb, e - 1, A.dv_vb, &j2, &b);
+          tb = B ^ (1u << j2) ^ (1u << b);
+          if (MODE == 1) {
+            const double v = eri_at(A.I.eri, n, i, a, j2, b);
+            h = (single_parity(Ak, i, a) ^ single_parity(B, j2, b)) ? -v : v;
+            const int64_t *Fa = A.Fa + (size_t)jdx * n, *Fb = A.Fb + (size_t)jdx * n;
+            dh = Fa[a] - Fa[i] - s_jk[a * n + i] + Fb[b] - Fb[j2] - s_jk[b * n + j2] +
+                 s_jj[a * n + b] - s_jj[a * n + j2] - s_jj[i * n + b] + s_jj[i * n + j2];
+          }
+        }
+      } else {
+        jdx = A.grp_start[k] + q;
+        tb = A.core_beta[jdx];
+        if (MODE == 1) {
+          int i, j2, a, b;
+          dec_double(Ak, va, o - 1 - A.E.sa, A.dv_pa_p, &i, &j2, &a, &b);
+          const double v = eri_at(A.I.asym, n, i, a, j2, b);
+          h = par_double(Ak, i, j2, a, b) ? -v : v;
+          dh = dd_same(A.Fa + (size_t)jdx * n, s_jk, n, i, j2, a, b);
+        }
+      }
+      if (big) cell = A.cellbase[gi] + bucket_of(tb, A.nb[gi]);
+    }
+    // warp-aggregated bucket counters (one atomic per distinct cell per warp)
+    const uint32_t peers = __match_any_sync(0xffffffffu, cell);
+    const int leader = __ffs(peers) - 1;
+    if (MODE == 0) {
+      if (cell != 0xffffffffu && lane == leader) atomicAdd(&A.cnt[cell], (uint32_t)__popc(peers));
+    } else {
+      uint32_t base = 0;
+      if (cell != 0xffffffffu && lane == leader) base = atomicAdd(&A.fill[cell], (uint32_t)__popc(peers));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      uint32_t kept = 0;
+      if (valid) {
+        uint32_t pos;
+        if (cell != 0xffffffffu)
+          pos = A.cell_pos0[cell] + base + __popc(peers & ((1u << lane) - 1u));
+        else
+          pos = (uint32_t)(p - A.P0);
+        (void)At;
+        const double v = h * A.core_c[jdx];
+        const int64_t haa = A.Dx[jdx] + dh;
+        uint32_t jj = jdx;
+        if (A.eps > 0.0) {
+          // |v / (E0 - H_ii)| > eps, without a division
+          const double den = __ll2double_rn(A.E0_x - haa) * A.inv_scale;
+          if (!(fabs(v) > A.eps * fabs(den))) jj = kDropped;
+        }
+        kept = jj != kDropped;
+        A.sb_beta[pos] = tb;
+        A.sb_j[pos] = jj;
+        A.sb_val[pos] = v;
+        A.sb_haa[pos] = haa;
+      }
+      if (A.eps > 0.0) {
+        const uint32_t nk = __popc(__ballot_sync(0xffffffffu, kept));
+        if (lane == 0 && nk) atomicAdd(A.survivors, (unsigned long long)nk);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------- tile kernel ---
+
+struct CellArgs {
+  const TileDesc *tiles;
+  uint32_t ntiles;
+  const uint32_t *sb_beta, *sb_j;
+  const double *sb_val;
+  const int64_t *sb_haa;
+  const uint32_t *g_alpha;
+  const uint64_t *g_P0;
+  uint64_t P0;
+  int64_t E0_x;
+  double inv_scale;  // 2^-s
+  float inv_scale_f;
+  double tau;
+  float tau_f;
+  const uint64_t *psi_ht;
+  uint64_t psi_mask;
+  uint64_t *cand_key;
+  double *cand_score;
+  unsigned long long *cand_count;
+  unsigned long long cand_cap;
+  unsigned long long *n_unique, *n_excluded;
+  unsigned *tile_counter;
+};
+
+__device__ __forceinline__ uint64_t mix_key(uint64_t z) {
+  z ^= z >> 33;
+  z *= 0xff51afd7ed558ccdull;
+  z ^= z >> 33;
+  z *= 0xc4ceb9fe1a85ec53ull;
+  z ^= z >> 33;
+  return z;
+}
+
+__device__ __forceinline__ bool psi_contains(const uint64_t *ht, uint64_t mask, uint64_t key) {
+  uint64_t h = mix_key(key) & mask;
+  for (;;) {
+    uint64_t s = ht[h];
+    if (s == key) return true;
+    if (s == ~0ull) return false;
+    h = (h + 1) & mask;
+  }
+}
+
+struct CellSmem {
+  uint64_t key[kCap];
+  double val[kCap];
+  uint16_t idx[kCap];
+  uint32_t hist[256 * (kCellThreads / 32)];
+  uint32_t gstart[kGroupsPerTile];
+  uint32_t galpha[kGroupsPerTile];
+  uint64_t red[kCellThreads / 32];
+  uint32_t tile;
+  uint32_t cnt[kCellThreads / 32];
+  unsigned long long cbase;
+};
+
+__device__ __forceinline__ uint32_t peers_of(uint32_t d, uint32_t active) {
+  uint32_t pe = active;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+    pe &= ((d >> b) & 1u) ? bal : ~bal;
+  }
+  return pe;
+}
+
+// Stable LSD radix sort of (key, idx) in shared memory over the digits where
+// the keys differ.  Warp w owns records [w*32*kCellItems, ...) in rounds of 32.
+__device__ void block_sort(CellSmem &S, int nrec, uint64_t vary) {
+  constexpr int W = kCellThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int wbeg = warp * 32 * kCellItems;
+  for (int shift = 0; shift < 64; shift += 8) {
+    if (((vary >> shift) & 0xffull) == 0) continue;
+    for (int t = threadIdx.x; t < 256 * W; t += kCellThreads) S.hist[t] = 0;
+    __syncthreads();
+    uint64_t k[kCellItems];
+    uint16_t ix[kCellItems];
+    uint32_t rk[kCellItems];  // rank in round | count << 8 | leader << 16
+#pragma unroll
+    for (int r = 0; r < kCellItems; ++r) {
+      const int e = wbeg + r * 32 + lane;
+      const bool ok = e < nrec;
+      k[r] = ok ? S.key[e] : 0ull;
+      ix[r] = ok ? S.idx[e] : (uint16_t)0;
+      const uint32_t d = (uint32_t)(k[r] >> shift) & 0xffu;
+      const uint32_t active = __ballot_sync(0xffffffffu, ok);
+      const uint32_t pe = peers_of(d, active);
+      const uint32_t c = __popc(pe);
+      const bool lead = ok && lane == __ffs(pe) - 1;
+      rk[r] = __popc(pe & lt) | (c << 8) | ((lead ? 1u : 0u) << 16);
+      if (lead) S.hist[d * W + warp] += c;
+      __syncwarp();
+    }
+    __syncthreads();
+    // exclusive scan of hist in digit-major order (256*W entries)
+    {
+      constexpr int PER = (256 * W) / kCellThreads;
+      uint32_t loc[PER];
+      uint32_t sum = 0;
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        loc[i] = S.hist[threadIdx.x * PER + i];
+        sum += loc[i];
+      }
+      // block exclusive scan of sum
+      uint32_t x = sum;
+#pragma unroll
+      for (int dlt = 1; dlt < 32; dlt <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, dlt);
+        if (lane >= dlt) x += y;
+      }
+      __shared__ uint32_t wsum[kCellThreads / 32];
+      if (lane == 31) wsum[warp] = x;
+      __syncthreads();
+      if (warp == 0) {
+        uint32_t w2 = lane < W ? wsum[lane] : 0u;
+#pragma unroll
+        for (int dlt = 1; dlt < 32; dlt <<= 1) {
+          uint32_t y = __shfl_up_sync(0xffffffffu, w2, dlt);
+          if (lane >= dlt) w2 += y;
+        }
+        if (lane < W) wsum[lane] = w2;
+      }
+      __syncthreads();
+      uint32_t pre = (warp ? wsum[warp - 1] : 0u) + x - sum;
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        S.hist[threadIdx.x * PER + i] = pre;
+        pre += loc[i];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kCellItems; ++r) {
+      const int e = wbeg + r * 32 + lane;
+      const bool ok = e < nrec;
+      const uint32_t d = (uint32_t)(k[r] >> shift) & 0xffu;
+      uint32_t pos = 0;
+      if (ok) pos = S.hist[d * W + warp] + (rk[r] & 0xffu);
+      __syncwarp();
+      if (ok && ((rk[r] >> 16) & 1u)) S.hist[d * W + warp] += (rk[r] >> 8) & 0xffu;
+      __syncwarp();
+      if (ok) {
+        S.key[pos] = k[r];
+        S.idx[pos] = ix[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Result of one unique target: whether it is new (outside psi) and its score.
+struct UniqueOut {
+  bool keep;
+  double score;
+  uint64_t key;
+};
+
+__device__ __forceinline__ uint64_t target_mask(uint32_t kind) {
+  return kind == kTileBucket ? 0xffffffff00000000ull : ~0ull;
+}
+
+__device__ __forceinline__ void unique_target(const CellSmem &S, const TileDesc &d, uint64_t sk,
+                                              uint32_t *a, uint32_t *b) {
+  if (d.kind == kTileBucket) {
+    *a = d.alpha;
+    *b = (uint32_t)(sk >> 32);
+  } else if (d.kind == kTileMedium) {
+    *a = d.alpha;
+    *b = (uint32_t)sk;
+  } else {
+    *a = S.galpha[(uint32_t)(sk >> 32)];
+    *b = (uint32_t)sk;
+  }
+}
+
+__global__ void __launch_bounds__(kCellThreads, 1) k_cells(CellArgs C) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CellSmem &S = *reinterpret_cast<CellSmem *>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long my_unique = 0, my_excl = 0;
+  for (;;) {
+    if (threadIdx.x == 0) S.tile = atomicAdd(C.tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = S.tile;
+    if (tile >= C.ntiles) break;
+    const TileDesc d = C.tiles[tile];
+    const int nrec = (int)d.npairs;
+    if (d.kind == kTilePacked) {
+      for (uint32_t i = threadIdx.x; i < d.ng; i += kCellThreads) {
+        S.gstart[i] = (uint32_t)(C.g_P0[d.g0 + i] - C.P0) - d.start;
+        S.galpha[i] = C.g_alpha[d.g0 + i];
+      }
+      __syncthreads();
+    }
+    // load records and build sort keys
+    uint64_t vary = 0, k0 = 0;
+    for (int e = threadIdx.x; e < nrec; e += kCellThreads) {
+      const uint32_t beta = C.sb_beta[d.start + e];
+      const uint32_t jr = C.sb_j[d.start + e];
+      uint64_t key;
+      if (jr == kDropped) {
+        key = ~0ull;  // screened out: sorts last, never a target
+      } else if (d.kind == kTileBucket) {
+        key = ((uint64_t)beta << 32) | jr;
+      } else if (d.kind == kTileMedium) {
+        key = beta;
+      } else {
+        int lo = 0, hi = (int)d.ng - 1;
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if ((int)S.gstart[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        key = ((uint64_t)lo << 32) | beta;
+      }
+      S.key[e] = key;
+      S.idx[e] = (uint16_t)e;
+      S.val[e] = C.sb_val[d.start + e];
+    }
+    __syncthreads();
+    if (nrec > 0) k0 = S.key[0];
+    for (int e = threadIdx.x; e < nrec; e += kCellThreads) vary |= S.key[e] ^ k0;
+    for (int dl = 16; dl; dl >>= 1) vary |= __shfl_xor_sync(0xffffffffu, vary, dl);
+    if (lane == 0) S.red[warp] = vary;
+    __syncthreads();
+    vary = 0;
+    for (int w = 0; w < kCellThreads / 32; ++w) vary |= S.red[w];
+    __syncthreads();
+    block_sort(S, nrec, vary);
+    // accumulate runs of equal targets (heads owned by the thread of their slot)
+    const uint64_t tm = target_mask(d.kind);
+    const int base = threadIdx.x * kCellItems;
+    uint32_t pass_mask = 0;
+    int npass = 0;
+    for (int r = 0; r < kCellItems; ++r) {
+      const int i = base + r;
+      if (i >= nrec) break;
+      const uint64_t sk = S.key[i];
+      if (sk == ~0ull) break;  // only screened-out records remain
+      if (i > 0 && ((S.key[i - 1] ^ sk) & tm) == 0) continue;
+      double num = 0.0;
+      int e = i;
+      for (; e < nrec && ((S.key[e] ^ sk) & tm) == 0; ++e) num += S.val[S.idx[e]];
+      uint32_t a, b;
+      unique_target(S, d, sk, &a, &b);
+      const uint64_t full = pack_key(a, b);
+      ++my_unique;
+      if (psi_contains(C.psi_ht, C.psi_mask, full)) {
+        ++my_excl;
+        continue;
+      }
+      const int64_t den_x = C.E0_x - C.sb_haa[d.start + S.idx[i]];
+      bool pass = true;
+      if (C.tau > 0.0) {
+        const float nf = fabsf(__double2float_rn(num));
+        const float df = fabsf(__ll2float_rn(den_x) * C.inv_scale_f);
+        pass = nf >= C.tau_f * df * 0.99999f;
+      }
+      if (pass) {
+        const double den = __ll2double_rn(den_x) * C.inv_scale;
+        const double sc = num / den;
+        if (!(fabs(sc) >= C.tau)) pass = false;
+      }
+      if (pass) {
+        pass_mask |= 1u << r;
+        ++npass;
+      }
+    }
+    // block-aggregated append of the passing targets
+    {
+      uint32_t x = npass;
+#pragma unroll
+      for (int dl = 1; dl < 32; dl <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, dl);
+        if (lane >= dl) x += y;
+      }
+      if (lane == 31) S.cnt[warp] = x;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+        for (int w = 0; w < kCellThreads / 32; ++w) {
+          uint32_t c = S.cnt[w];
+          S.cnt[w] = tot;
+          tot += c;
+        }
+        S.cbase = tot ? atomicAdd(C.cand_count, (unsigned long long)tot) : 0ull;
+      }
+      __syncthreads();
+      unsigned long long slot = S.cbase + S.cnt[warp] + (x - npass);
+      for (int r = 0; r < kCellItems && pass_mask; ++r) {
+        if (!((pass_mask >> r) & 1u)) continue;
+        const int i = base + r;
+        const uint64_t sk = S.key[i];
+        double num = 0.0;
+        for (int e = i; e < nrec && ((S.key[e] ^ sk) & tm) == 0; ++e) num += S.val[S.idx[e]];
+        uint32_t a, b;
+        unique_target(S, d, sk, &a, &b);
+        const int64_t den_x = C.E0_x - C.sb_haa[d.start + S.idx[i]];
+        const double sc = num / (__ll2double_rn(den_x) * C.inv_scale);
+        if (slot < C.cand_cap) {
+          C.cand_key[slot] = pack_key(a, b);
+          C.cand_score[slot] = sc;
+        }
+        ++slot;
+      }
+    }
+    __syncthreads();
+  }
+  // per-block counters
+  for (int dl = 16; dl; dl >>= 1) {
+    my_unique += __shfl_xor_sync(0xffffffffu, my_unique, dl);
+    my_excl += __shfl_xor_sync(0xffffffffu, my_excl, dl);
+  }
+  if (lane == 0) {
+    if (my_unique) atomicAdd(C.n_unique, my_unique);
+    if (my_excl) atomicAdd(C.n_excluded, my_excl);
+  }
+}
+
+__global__ void k_psi_insert(const uint64_t *keys, size_t n, uint64_t *ht, uint64_t mask) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    uint64_t h = mix_key(k) & mask;
+    for (;;) {
+      unsigned long long prev =
+          atomicCAS((unsigned long long *)&ht[h], ~0ull, (unsigned long long)k);
+      if (prev == ~0ull || prev == k) break;
+      h = (h + 1) & mask;
+    }
+  }
+}
+
+__global__ void k_abs_min(const double *s, size_t n, unsigned long long *out) {
+  // min |s| as ordered bits (non-negative doubles order like their bit patterns)
+  unsigned long long m = ~0ull;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(fabs(s[i]));
+    m = b < m ? b : m;
+  }
+  for (int dl = 16; dl; dl >>= 1) {
+    unsigned long long o = __shfl_xor_sync(0xffffffffu, m, dl);
+    m = o < m ? o : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMin(out, m);
+}
+
+inline unsigned grid_for(size_t n, unsigned cap = 152 * 16) {
+  size_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  return (unsigned)(b < cap ? b : cap);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host side ---
+
+int kept_count(const uint32_t *keep, const uint32_t *pos, size_t n, size_t *host_count,
+               Arena &arena);
+
+int build_fx(const double *h1, const double *eri, int n, int na, int nb, double ecore, double E0,
+             Arena &arena, FxInts *out, int64_t *E0_x) {
+  cudaStream_t s = arena.stream();
+  double *d3;
+  ASCI_TRY(arena.alloc(&d3, 3));
+  k_fx_bound<<<1, 256, 0, s>>>(h1, eri, n, d3);
+  ASCI_CHECK_LAUNCH();
+  double h3[3];
+  ASCI_TRY_CUDA(cudaMemcpyAsync(h3, d3, sizeof(h3), cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  // B bounds |E0|, every diagonal element and every Fock-like diagonal value:
+  // (na+nb) one-body terms, C(na,2)+C(nb,2) same-spin and na*nb opposite-spin
+  // pair terms.  With s = 58 - log2(B) a sum of up to 32 such values cannot
+  // overflow 64 bits.
+  const double nn = (double)(na + nb), pairs_same = 0.5 * (na * (na - 1) + nb * (nb - 1));
+  const double B = fabs(ecore) + fabs(E0) + nn * h3[0] + (pairs_same + n) * h3[1] +
+                   ((double)na * nb + n) * h3[2] + 1.0;
+  int e = 0;
+  frexp(B, &e);  // B < 2^e
+  int sc = 58 - e;
+  if (sc > 60) sc = 60;
+  if (sc < 8) {
+    record_error("integrals too large for the fixed-point diagonal", __FILE__, __LINE__);
+    return ASCI_EINVAL;
+  }
+  int64_t *hh, *jk, *jj;
+  ASCI_TRY(arena.alloc(&hh, n));
+  ASCI_TRY(arena.alloc(&jk, (size_t)n * n));
+  ASCI_TRY(arena.alloc(&jj, (size_t)n * n));
+  k_fx_tables<<<(n * n + 255) / 256, 256, 0, s>>>(h1, eri, n, sc, hh, jk, jj);
+  ASCI_CHECK_LAUNCH();
+  FxInts X;
+  X.n = n;
+  X.s = sc;
+  X.ecore_x = llrint(ldexp(ecore, sc));
+  X.hh = hh;
+  X.jk = jk;
+  X.jj = jj;
+  *out = X;
+  *E0_x = llrint(ldexp(E0, sc));
+  return ASCI_OK;
+}
+
+int core_fock(const FxInts &X, const uint32_t *core_alpha, const uint32_t *core_beta, size_t m,
+              int64_t *Dx, int64_t *Fa, int64_t *Fb, Arena &arena) {
+  if (!m) return ASCI_OK;
+  k_core_fock<<<grid_for(m), 256, 0, arena.stream()>>>(X, core_alpha, core_beta, m, Dx, Fa, Fb);
+  ASCI_CHECK_LAUNCH();
+  return ASCI_OK;
+}
+
+int fx_diag_keys(const FxInts &X, const uint64_t *keys, size_t n, int64_t *out, Arena &arena) {
+  if (!n) return ASCI_OK;
+  k_fx_check_diag<<<grid_for(n), 256, 0, arena.stream()>>>(X, keys, n, out);
+  ASCI_CHECK_LAUNCH();
+  return ASCI_OK;
+}
+
+// Groups (distinct target alpha strings) of the sorted item list.
+int item_groups(const uint64_t *items, const uint64_t *Wexcl, uint64_t T, uint32_t *item_group,
+                uint32_t **g_alpha, uint64_t **g_P0, uint64_t **g_item0, size_t *G,
+                Arena &arena) {
+  cudaStream_t s = arena.stream();
+  uint32_t *flag;
+  Arena tmp(s);
+  ASCI_TRY(tmp.alloc(&flag, T));
+  k_item_gflags<<<grid_for(T), 256, 0, s>>>(items, T, flag);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(scan_exclusive_u32(flag, item_group, T, tmp));
+  size_t ng = 0;
+  ASCI_TRY(kept_count(flag, item_group, T, &ng, tmp));
+  ASCI_TRY(arena.alloc(g_alpha, ng));
+  ASCI_TRY(arena.alloc(g_P0, ng));
+  ASCI_TRY(arena.alloc(g_item0, ng));
+  k_group_tab<<<grid_for(T), 256, 0, s>>>(items, flag, item_group, Wexcl, T, *g_alpha, *g_P0,
+                                          *g_item0);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  *G = ng;
+  return ASCI_OK;
+}
+
+int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t *mask,
+                   Arena &arena) {
+  uint64_t size = 1024;
+  while (size < 4 * (uint64_t)nd) size <<= 1;
+  ASCI_TRY(arena.alloc(ht, size));
+  cudaStream_t s = arena.stream();
+  ASCI_TRY_CUDA(cudaMemsetAsync(*ht, 0xff, size * sizeof(uint64_t), s));
+  k_psi_insert<<<grid_for(nd), 256, 0, s>>>(psi_keys, nd, *ht, size - 1);
+  ASCI_CHECK_LAUNCH();
+  *mask = size - 1;
+  return ASCI_OK;
+}
+
+
+// Stage one batch (items [t0, t1), pairs [P0, P1), groups [gb0, gb1)): plan
+// its tiles, count the hash buckets of big classes and emit every record into
+// the staging buffer.  The tile table is left in *tiles_out (arena memory).
+int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
+                uint32_t gb0, uint32_t gb1, uint32_t *sb_beta, uint32_t *sb_j, double *sb_val,
+                int64_t *sb_haa, double eps, unsigned long long *survivors, void **tiles_out,
+                size_t *ntiles_out, Arena &arena) {
+  cudaStream_t s = arena.stream();
+  const uint32_t ng = gb1 - gb0;
+  *ntiles_out = 0;
+  if (P1 <= P0 || ng == 0) return ASCI_OK;
+  uint32_t *kind, *nb, *small_cnt, *Ns, *cellbase, *ntile, *tile_base;
+  uint64_t *small_pairs, *Ws;
+  ASCI_TRY(arena.alloc(&kind, ng));
+  ASCI_TRY(arena.alloc(&nb, ng));
+  ASCI_TRY(arena.alloc(&small_cnt, ng));
+  ASCI_TRY(arena.alloc(&Ns, ng));
+  ASCI_TRY(arena.alloc(&cellbase, ng));
+  ASCI_TRY(arena.alloc(&ntile, ng));
+  ASCI_TRY(arena.alloc(&tile_base, ng));
+  ASCI_TRY(arena.alloc(&small_pairs, ng));
+  ASCI_TRY(arena.alloc(&Ws, ng));
+  k_group_class<<<grid_for(ng), 256, 0, s>>>(F.g_P0, gb0, gb1, P1, kind, nb, small_pairs,
+                                             small_cnt);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(scan_exclusive_u64(small_pairs, Ws, ng, arena));
+  ASCI_TRY(scan_exclusive_u32(small_cnt, Ns, ng, arena));
+  ASCI_TRY(scan_exclusive_u32(nb, cellbase, ng, arena));
+  size_t ncells = 0, ntiles = 0;
+  ASCI_TRY(kept_count(nb, cellbase, ng, &ncells, arena));
+  k_tile_count<<<grid_for(ng), 256, 0, s>>>(ng, kind, nb, Ws, Ns, ntile);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(scan_exclusive_u32(ntile, tile_base, ng, arena));
+  ASCI_TRY(kept_count(ntile, tile_base, ng, &ntiles, arena));
+
+  uint32_t *cnt, *cnt_scan, *cell_pos0, *fill;
+  ASCI_TRY(arena.alloc(&cnt, ncells + 1));
+  ASCI_TRY(arena.alloc(&cnt_scan, ncells + 1));
+  ASCI_TRY(arena.alloc(&cell_pos0, ncells + 1));
+  ASCI_TRY(arena.alloc(&fill, ncells + 1));
+  ASCI_TRY_CUDA(cudaMemsetAsync(cnt, 0, (ncells + 1) * sizeof(uint32_t), s));
+  ASCI_TRY_CUDA(cudaMemsetAsync(fill, 0, (ncells + 1) * sizeof(uint32_t), s));
+
+  EmitArgs A;
+  A.I = F.I;
+  A.X = F.X;
+  A.E = F.E;
+  A.dv_va = FastDiv(F.E.va ? F.E.va : 1);
+  A.dv_vb = FastDiv(F.E.vb ? F.E.vb : 1);
+  A.dv_npd0 = FastDiv((uint32_t)(F.E.sb + F.E.dbb) ? (uint32_t)(F.E.sb + F.E.dbb) : 1);
+  A.dv_npd1 = FastDiv(1u + F.E.sb);
+  A.dv_pa_p = FastDiv(F.E.pa_p ? F.E.pa_p : 1);
+  A.dv_pb_p = FastDiv(F.E.pb_p ? F.E.pb_p : 1);
+  A.items = F.items;
+  A.Wexcl = F.Wexcl;
+  A.item_group = F.item_group;
+  A.t0 = t0;
+  A.t1 = t1;
+  A.P0 = P0;
+  A.P1 = P1;
+  A.opbits = F.opbits;
+  A.grp_alpha = F.grp_alpha;
+  A.grp_start = F.grp_start;
+  A.core_beta = F.core_beta;
+  A.core_c = F.core_c;
+  A.Dx = F.Dx;
+  A.Fa = F.Fa;
+  A.Fb = F.Fb;
+  A.gb0 = gb0;
+  A.kind = kind;
+  A.nb = nb;
+  A.cellbase = cellbase;
+  A.cnt = cnt;
+  A.cell_pos0 = cell_pos0;
+  A.fill = fill;
+  A.sb_beta = sb_beta;
+  A.sb_j = sb_j;
+  A.sb_val = sb_val;
+  A.sb_haa = sb_haa;
+  A.eps = eps;
+  A.E0_x = F.E0_x;
+  A.inv_scale = ldexp(1.0, -F.X.s);
+  A.survivors = survivors;
+  const uint64_t etiles = (P1 - P0 + kEmitTile - 1) / kEmitTile;
+  const size_t emit_smem = 2 * (size_t)F.X.n * F.X.n * sizeof(int64_t);
+  if (ncells) {
+    k_emit2<0><<<(unsigned)etiles, kEmitThreads, 0, s>>>(A);
+    ASCI_CHECK_LAUNCH();
+  }
+  ASCI_TRY(scan_exclusive_u32(cnt, cnt_scan, ncells + 1, arena));
+  TileDesc *tiles;
+  unsigned *overflow;
+  ASCI_TRY(arena.alloc(&tiles, ntiles + 1));
+  ASCI_TRY(arena.alloc(&overflow, 1));
+  ASCI_TRY_CUDA(cudaMemsetAsync(tiles, 0, (ntiles + 1) * sizeof(TileDesc), s));
+  ASCI_TRY_CUDA(cudaMemsetAsync(overflow, 0, sizeof(unsigned), s));
+  k_tile_write<<<grid_for(ng), 256, 0, s>>>(gb0, ng, P0, P1, F.g_P0, F.g_alpha, kind, nb, Ws, Ns,
+                                            tile_base, cellbase, cnt, cnt_scan, tiles, cell_pos0,
+                                            overflow);
+  ASCI_CHECK_LAUNCH();
+  k_emit2<1><<<(unsigned)etiles, kEmitThreads, emit_smem, s>>>(A);
+  ASCI_CHECK_LAUNCH();
+  unsigned hov = 0;
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&hov, overflow, sizeof(hov), cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  if (hov) {
+    record_error("a hash bucket of a large constraint class exceeds the tile capacity", __FILE__,
+                 __LINE__);
+    return ASCI_ENOMEM;
+  }
+  *tiles_out = tiles;
+  *ntiles_out = ntiles;
+  return ASCI_OK;
+}
+
+size_t tile_capacity() { return (size_t)kCap; }
+
+// Reduce tiles [tile_begin, tile_end) of a staged batch on chip and append the
+// targets with |S| >= tau to the candidate buffer (at most kCap per tile).
+int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint32_t tile_end,
+                uint64_t P0, const uint32_t *sb_beta, const uint32_t *sb_j, const double *sb_val,
+                const int64_t *sb_haa, double tau, uint64_t *cand_key, double *cand_score,
+                unsigned long long *cand_count, unsigned long long cand_cap,
+                unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *counter,
+                Arena &arena) {
+  if (tile_end <= tile_begin) return ASCI_OK;
+  cudaStream_t s = arena.stream();
+  CellArgs CA;
+  CA.tiles = static_cast<const TileDesc *>(tiles);
+  CA.ntiles = tile_end;
+  CA.sb_beta = sb_beta;
+  CA.sb_j = sb_j;
+  CA.sb_val = sb_val;
+  CA.sb_haa = sb_haa;
+  CA.g_alpha = F.g_alpha;
+  CA.g_P0 = F.g_P0;
+  CA.P0 = P0;
+  CA.E0_x = F.E0_x;
+  CA.inv_scale = ldexp(1.0, -F.X.s);
+  CA.inv_scale_f = ldexpf(1.0f, -F.X.s);
+  CA.tau = tau;
+  CA.tau_f = (float)tau;
+  if ((double)CA.tau_f > tau) CA.tau_f = nextafterf(CA.tau_f, 0.0f);
+  CA.psi_ht = F.psi_ht;
+  CA.psi_mask = F.psi_mask;
+  CA.cand_key = cand_key;
+  CA.cand_score = cand_score;
+  CA.cand_count = cand_count;
+  CA.cand_cap = cand_cap;
+  CA.n_unique = n_unique;
+  CA.n_excluded = n_excluded;
+  CA.tile_counter = counter;
+  ASCI_TRY_CUDA(cudaMemcpyAsync(counter, &tile_begin, sizeof(unsigned), cudaMemcpyDefault, s));
+  const size_t cell_smem = sizeof(CellSmem);
+  static bool attr_set = false;
+  if (!attr_set) {
+    ASCI_TRY_CUDA(cudaFuncSetAttribute(k_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)cell_smem));
+    attr_set = true;
+  }
+  int dev = 0, sms = 152;
+  ASCI_TRY_CUDA(cudaGetDevice(&dev));
+  ASCI_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid = (unsigned)std::min<size_t>((size_t)sms, tile_end - tile_begin);
+  k_cells<<<grid, kCellThreads, cell_smem, s>>>(CA);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));  // `tile_begin` is read from the host stack
+  return ASCI_OK;
+}
+
+// Smallest |score| among n candidates (host result), used as the threshold.
+int abs_min(const double *s, size_t n, double *host_min, Arena &arena) {
+  unsigned long long *d;
+  ASCI_TRY(arena.alloc(&d, 1));
+  cudaStream_t st = arena.stream();
+  ASCI_TRY_CUDA(cudaMemsetAsync(d, 0xff, sizeof(unsigned long long), st));
+  k_abs_min<<<grid_for(n), 256, 0, st>>>(s, n, d);
+  ASCI_CHECK_LAUNCH();
+  unsigned long long h = 0;
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDefault, st));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(st));
+  double v;
+  memcpy(&v, &h, sizeof(v));
+  *host_min = v;
+  return ASCI_OK;
+}
+
+}  // namespace asci

@@ -1,0 +1,37 @@
+// Shared declarations of the constraint-tile search (fused.cu) and its host
+// orchestration (search.cu).
+#pragma once
+
+#include "asci_internal.cuh"
+
+namespace asci {
+
+// Integral terms of the diagonal in 64-bit fixed point (multiples of 2^-s).
+struct FxInts {
+  int n;
+  int s;              // values are multiples of 2^-s
+  int64_t ecore_x;
+  const int64_t *hh;  // n      h_pp
+  const int64_t *jk;  // n*n    (pp|qq) - (pq|qp), zero diagonal
+  const int64_t *jj;  // n*n    (pp|qq)
+};
+
+// Everything the batch kernels read that stays fixed during one search.
+struct FusedCore {
+  DevInts I;
+  FxInts X;
+  ExcCounts E;
+  const uint64_t *items, *Wexcl;
+  const uint32_t *item_group;
+  int opbits;
+  const uint32_t *grp_alpha, *grp_start, *core_beta;
+  const double *core_c;
+  const int64_t *Dx, *Fa, *Fb;
+  const uint32_t *g_alpha;
+  const uint64_t *g_P0;
+  int64_t E0_x;
+  const uint64_t *psi_ht;
+  uint64_t psi_mask;
+};
+
+}  // namespace asci

@@ -64,35 +64,6 @@ __global__ void k_diag(DevInts I, const uint64_t *keys, size_t n, double *out) {
   }
 }
 
-// ------------------------- exclusion and score -----------------------------
-
-__device__ __forceinline__ bool in_sorted(const uint64_t *a, size_t n, uint64_t k) {
-  size_t lo = 0, hi = n;
-  while (lo < hi) {
-    size_t mid = (lo + hi) >> 1;
-    if (a[mid] < k) lo = mid + 1; else hi = mid;
-  }
-  return lo < n && a[lo] == k;
-}
-
-// keep[u] = target outside psi; score[u] = num / (E0 - H_ii) (Eq. 1).
-__global__ void k_score(DevInts I, const uint64_t *ukeys, const double *usums, size_t u,
-                        const uint64_t *psi_sorted, size_t npsi, double E0, uint32_t *keep,
-                        double *score) {
-  for (size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x; s < u;
-       s += (size_t)gridDim.x * blockDim.x) {
-    uint64_t k = ukeys[s];
-    if (k == ~0ull || in_sorted(psi_sorted, npsi, k)) {  // ~0: run of screened-out pairs
-      keep[s] = 0u;
-      score[s] = 0.0;
-    } else {
-      double haa = diag_value(I, key_alpha(k), key_beta(k));
-      keep[s] = 1u;
-      score[s] = usums[s] / (E0 - haa);
-    }
-  }
-}
-
 template <typename T>
 __global__ void k_compact(const T *in, const uint32_t *keep, const uint32_t *pos, size_t n,
                           T *out) {
@@ -207,16 +178,6 @@ int sort_accumulate(uint64_t **keys, uint64_t **keys_alt, double **vals, double 
 int diagonal_packed(const DevInts &I, const uint64_t *keys, size_t n, double *out, Arena &arena) {
   if (!n) return ASCI_OK;
   k_diag<<<grid_for(n), 256, 0, arena.stream()>>>(I, keys, n, out);
-  ASCI_CHECK_LAUNCH();
-  return ASCI_OK;
-}
-
-int score_unique(const DevInts &I, const uint64_t *ukeys, const double *usums, size_t u,
-                 const uint64_t *psi_sorted, size_t npsi, double E0, uint32_t *keep,
-                 double *score, Arena &arena) {
-  if (!u) return ASCI_OK;
-  k_score<<<grid_for(u), 256, 0, arena.stream()>>>(I, ukeys, usums, u, psi_sorted, npsi, E0, keep,
-                                                   score);
   ASCI_CHECK_LAUNCH();
   return ASCI_OK;
 }

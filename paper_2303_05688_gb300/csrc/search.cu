@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "asci_internal.cuh"
+#include "fused.cuh"
 
 namespace asci {
 
@@ -29,19 +30,34 @@ int make_items(const ExcCounts &X, int n, const uint32_t *grp_alpha, uint32_t ng
                uint32_t o_begin, uint32_t nops, int opbits, uint64_t *items, Arena &arena);
 int item_weights(const uint64_t *items, uint64_t nitems, int opbits, const uint32_t *grp_count,
                  const ExcCounts &X, uint64_t *w, Arena &arena);
-int emit_batch(const DevInts &I, const ExcCounts &X, const uint64_t *items, const uint64_t *Wexcl,
-               uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1, int opbits,
-               const uint32_t *grp_alpha, const uint32_t *grp_start, const uint32_t *core_beta,
-               const double *core_c, uint64_t *out_keys, double *out_vals, Arena &arena);
 int compact_u64(const uint64_t *in, const uint32_t *keep, const uint32_t *pos, size_t n,
                 uint64_t *out, Arena &arena);
 int compact_f64(const double *in, const uint32_t *keep, const uint32_t *pos, size_t n, double *out,
                 Arena &arena);
 int kept_count(const uint32_t *keep, const uint32_t *pos, size_t n, size_t *host_count,
                Arena &arena);
-int score_unique(const DevInts &I, const uint64_t *ukeys, const double *usums, size_t u,
-                 const uint64_t *psi_sorted, size_t npsi, double E0, uint32_t *keep,
-                 double *score, Arena &arena);
+
+int build_fx(const double *h1, const double *eri, int n, int na, int nb, double ecore, double E0,
+             Arena &arena, FxInts *out, int64_t *E0_x);
+int core_fock(const FxInts &X, const uint32_t *core_alpha, const uint32_t *core_beta, size_t m,
+              int64_t *Dx, int64_t *Fa, int64_t *Fb, Arena &arena);
+int item_groups(const uint64_t *items, const uint64_t *Wexcl, uint64_t T, uint32_t *item_group,
+                uint32_t **g_alpha, uint64_t **g_P0, uint64_t **g_item0, size_t *G,
+                Arena &arena);
+int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t *mask,
+                   Arena &arena);
+int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
+                uint32_t gb0, uint32_t gb1, uint32_t *sb_beta, uint32_t *sb_j, double *sb_val,
+                int64_t *sb_haa, double eps, unsigned long long *survivors, void **tiles_out,
+                size_t *ntiles_out, Arena &arena);
+int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint32_t tile_end,
+                uint64_t P0, const uint32_t *sb_beta, const uint32_t *sb_j, const double *sb_val,
+                const int64_t *sb_haa, double tau, uint64_t *cand_key, double *cand_score,
+                unsigned long long *cand_count, unsigned long long cand_cap,
+                unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *counter,
+                Arena &arena);
+size_t tile_capacity();
+int abs_min(const double *s, size_t n, double *host_min, Arena &arena);
 
 static thread_local char g_last_error[512] = "";
 static std::atomic<unsigned long long> g_launches{0};
@@ -53,8 +69,6 @@ void record_error(const char *what, const char *file, int line) {
 }
 
 namespace {
-
-constexpr uint64_t kSentinel = ~0ull;  // key of a screened-out pair (never a real key)
 
 inline unsigned grid_for(size_t n, unsigned cap = 152 * 16) {
   size_t b = (n + 255) / 256;
@@ -151,6 +165,12 @@ __global__ void k_gather_core(const uint32_t *core_idx, const uint64_t *psi_keys
   }
 }
 
+__global__ void k_low_words(const uint64_t *in, size_t n, uint32_t *out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (uint32_t)in[i];
+}
+
 __global__ void k_input_keys(const asci_det *dets, size_t nd, uint64_t *keys) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd;
        i += (size_t)gridDim.x * blockDim.x)
@@ -213,40 +233,6 @@ __global__ void k_class_list(const uint32_t *head, const uint32_t *pos, uint64_t
     }
 }
 
-// eps screen of Alg. 2: drop (target, core) pairs with |v / (E0 - H_ii)| <= eps
-__device__ double diag_direct(const DevInts &I, uint32_t A, uint32_t B) {
-  const int n = I.n;
-  double s = I.ecore;
-  for (uint32_t m = A; m; m &= m - 1) {
-    const int p = __ffs(m) - 1;
-    s += I.h1[p * n + p];
-    for (uint32_t r = m & (m - 1); r; r &= r - 1) s += I.jk[p * n + __ffs(r) - 1];
-    for (uint32_t r = B; r; r &= r - 1) s += I.jj[p * n + __ffs(r) - 1];
-  }
-  for (uint32_t m = B; m; m &= m - 1) {
-    const int p = __ffs(m) - 1;
-    s += I.h1[p * n + p];
-    for (uint32_t r = m & (m - 1); r; r &= r - 1) s += I.jk[p * n + __ffs(r) - 1];
-  }
-  return s;
-}
-
-__global__ void k_screen(DevInts I, uint64_t *keys, const double *vals, size_t n, double E0,
-                         double eps, unsigned long long *survivors) {
-  unsigned long long kept = 0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
-    uint64_t k = keys[i];
-    double hii = diag_direct(I, key_alpha(k), key_beta(k));
-    if (fabs(vals[i] / (E0 - hii)) > eps)
-      ++kept;
-    else
-      keys[i] = kSentinel;
-  }
-  for (int d = 16; d; d >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, d);
-  if ((threadIdx.x & 31) == 0 && kept) atomicAdd(survivors, kept);
-}
-
 __global__ void k_unpack(const uint64_t *keys, size_t n, asci_det *out) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -299,8 +285,10 @@ struct Batch {
 // (Sec. 2.2 constraints; Alg. 3's work counts h are the class weights).
 class Planner {
  public:
-  Planner(const uint64_t *items, const uint64_t *Wexcl, uint64_t bmax, int lmax, Arena &arena)
-      : items_(items), W_(Wexcl), bmax_(bmax), lmax_(lmax), arena_(arena) {}
+  Planner(const uint64_t *items, const uint64_t *Wexcl, uint64_t bmax, uint64_t first_cap,
+          int lmax, Arena &arena)
+      : items_(items), W_(Wexcl), bmax_(bmax), first_cap_(first_cap), lmax_(lmax),
+        arena_(arena) {}
 
   int run(uint64_t T, uint64_t P, int L0, std::vector<Batch> *out, int *max_level) {
     batches_.clear();
@@ -346,7 +334,8 @@ class Planner {
   }
 
   void add(uint64_t cs, uint64_t ce, uint64_t ws, uint64_t we) {
-    if (cur_open_ && (we - cur_.P0) > bmax_) flush();
+    const uint64_t cap = batches_.empty() ? first_cap_ : bmax_;
+    if (cur_open_ && (we - cur_.P0) > cap) flush();
     if (!cur_open_) {
       cur_ = Batch{cs, ce, ws, we};
       cur_open_ = true;
@@ -376,6 +365,7 @@ class Planner {
   const uint64_t *items_;
   const uint64_t *W_;
   uint64_t bmax_;
+  uint64_t first_cap_;
   int lmax_;
   Arena &arena_;
   std::vector<Batch> batches_;
@@ -568,13 +558,15 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     if (bmax == 0) {
       size_t fr = 0, tot = 0;
       ASCI_TRY_CUDA(cudaMemGetInfo(&fr, &tot));
-      bmax = (uint64_t)(fr / 2) / 96;
+      bmax = (uint64_t)(fr / 2) / 32;  // staging record: 24 bytes
       bmax = std::max<uint64_t>(bmax, 1ull << 20);
-      bmax = std::min<uint64_t>(bmax, 1ull << 30);
+      bmax = std::min<uint64_t>(bmax, 1ull << 31);
     }
     const int lmax = (o.max_constraint_level > 0) ? std::min(o.max_constraint_level, na) : na;
     const int L0 = std::min(3, lmax);
-    Planner planner(items, Wexcl, bmax, lmax, arena);
+    // a small first batch fixes the selection threshold early
+    const uint64_t first_cap = std::min<uint64_t>(bmax, std::max<uint64_t>(1ull << 22, P / 64));
+    Planner planner(items, Wexcl, bmax, first_cap, lmax, arena);
     ASCI_TRY(planner.run(T, P, L0, &batches, &max_level));
   }
   uint64_t bcap = 0;
@@ -591,78 +583,148 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   tm.stop(&tl[1]);
 
   // --------------------------- batches -------------------------------------
-  uint64_t *bk = nullptr, *bk_alt = nullptr, *ukeys = nullptr;
-  double *bv = nullptr, *bv_alt = nullptr, *usums = nullptr, *uscore = nullptr;
-  uint32_t *keep = nullptr, *kpos = nullptr;
+  // per-search tables of the constraint-tile kernels
+  tm.start();
+  FusedCore F;
+  F.I = I;
+  F.E = X;
+  F.items = items;
+  F.Wexcl = Wexcl;
+  F.opbits = opbits;
+  F.grp_alpha = grp_alpha;
+  F.grp_start = grp_start;
+  F.core_beta = core_beta;
+  F.core_c = core_c_sorted;
+  uint64_t *psi_ht = nullptr;
+  uint64_t psi_mask = 0;
+  ASCI_TRY(psi_hash_build(psi_sorted, nd, &psi_ht, &psi_mask, arena));
+  F.psi_ht = psi_ht;
+  F.psi_mask = psi_mask;
+  ASCI_TRY(build_fx(h1, eri, n, na, nb, ints->ecore, E0, arena, &F.X, &F.E0_x));
+  {
+    uint32_t *core_alpha32;
+    int64_t *Dx, *Fa, *Fb;
+    ASCI_TRY(arena.alloc(&core_alpha32, m));
+    ASCI_TRY(arena.alloc(&Dx, m));
+    ASCI_TRY(arena.alloc(&Fa, m * n));
+    ASCI_TRY(arena.alloc(&Fb, m * n));
+    k_low_words<<<grid_for(m), 256, 0, stream>>>(alpha_k, m, core_alpha32);
+    ASCI_CHECK_LAUNCH();
+    ASCI_TRY(core_fock(F.X, core_alpha32, core_beta, m, Dx, Fa, Fb, arena));
+    F.Dx = Dx;
+    F.Fa = Fa;
+    F.Fb = Fb;
+  }
+  uint32_t *item_group = nullptr;
+  uint32_t *g_alpha = nullptr;
+  uint64_t *g_P0 = nullptr, *g_item0 = nullptr;
+  size_t G = 0;
+  if (T > 0) {
+    ASCI_TRY(arena.alloc(&item_group, T));
+    ASCI_TRY(item_groups(items, Wexcl, T, item_group, &g_alpha, &g_P0, &g_item0, &G, arena));
+  }
+  F.item_group = item_group;
+  F.g_alpha = g_alpha;
+  F.g_P0 = g_P0;
+  tm.stop(&tl[1]);
+
+  int dev = 0, sms = 152;
+  ASCI_TRY_CUDA(cudaGetDevice(&dev));
+  ASCI_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t cap_extra =
+      std::max<size_t>(tile_capacity() * (size_t)sms * 16, std::min<uint64_t>(bcap, 1ull << 28));
+  const size_t pool_cap = N + cap_extra;
+  uint32_t *sb_beta = nullptr, *sb_j = nullptr;
+  double *sb_val = nullptr;
+  int64_t *sb_haa = nullptr;
   uint64_t *pool_k[2] = {nullptr, nullptr};
   double *pool_s[2] = {nullptr, nullptr};
-  unsigned long long *dsurv = nullptr;
-  const size_t pool_cap = N + bcap;
+  unsigned long long *dcount = nullptr;  // [0] candidates, [1] unique, [2] excluded, [3] survivors
+  unsigned *tile_counter = nullptr;
   if (bcap) {
-    ASCI_TRY(arena.alloc(&bk, bcap));
-    ASCI_TRY(arena.alloc(&bk_alt, bcap));
-    ASCI_TRY(arena.alloc(&bv, bcap));
-    ASCI_TRY(arena.alloc(&bv_alt, bcap));
-    ASCI_TRY(arena.alloc(&ukeys, bcap));
-    ASCI_TRY(arena.alloc(&usums, bcap));
-    ASCI_TRY(arena.alloc(&uscore, bcap));
-    ASCI_TRY(arena.alloc(&keep, bcap));
-    ASCI_TRY(arena.alloc(&kpos, bcap));
-    ASCI_TRY(arena.alloc(&dsurv, 1));
+    ASCI_TRY(arena.alloc(&sb_beta, bcap));
+    ASCI_TRY(arena.alloc(&sb_j, bcap));
+    ASCI_TRY(arena.alloc(&sb_val, bcap));
+    ASCI_TRY(arena.alloc(&sb_haa, bcap));
     for (int i = 0; i < 2; ++i) {
       ASCI_TRY(arena.alloc(&pool_k[i], pool_cap));
       ASCI_TRY(arena.alloc(&pool_s[i], pool_cap));
     }
+    ASCI_TRY(arena.alloc(&dcount, 4));
+    ASCI_TRY(arena.alloc(&tile_counter, 1));
+    ASCI_TRY_CUDA(cudaMemsetAsync(dcount, 0, 4 * sizeof(unsigned long long), stream));
   }
   size_t pool_n = 0;
   int pcur = 0;
-  uint64_t surviving = 0, unique = 0, excluded = 0;
+  double tau = 0.0;
+  // Prune the pool to the top N and raise tau to its N-th |S| (a lower bound of
+  // the final cutoff, so nothing that can still be selected is ever dropped).
+  auto prune = [&](Arena &pa) -> int {
+    size_t m2 = 0;
+    ASCI_TRY(select_topn_packed(pool_k[pcur], pool_s[pcur], pool_n, N, pool_k[pcur ^ 1],
+                                pool_s[pcur ^ 1], &m2, pa));
+    pcur ^= 1;
+    pool_n = m2;
+    if (m2 >= N && N > 0) ASCI_TRY(abs_min(pool_s[pcur], pool_n, &tau, pa));
+    unsigned long long c = pool_n;
+    ASCI_TRY_CUDA(cudaMemcpyAsync(dcount, &c, sizeof(c), cudaMemcpyDefault, stream));
+    ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+    return ASCI_OK;
+  };
   for (const Batch &b : batches) {
     Arena ba(stream);  // scratch of this batch, released when the batch ends
-    const size_t nb_pairs = b.P1 - b.P0;
-    uint64_t *k0 = bk, *k1 = bk_alt;
-    double *v0 = bv, *v1 = bv_alt;
+    uint32_t gg[2];
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&gg[0], item_group + b.t0, 4, cudaMemcpyDefault, stream));
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&gg[1], item_group + b.t1 - 1, 4, cudaMemcpyDefault, stream));
+    ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
     tm.start();
-    ASCI_TRY(emit_batch(I, X, items, Wexcl, b.t0, b.t1, b.P0, b.P1, opbits, grp_alpha, grp_start,
-                        core_beta, core_c_sorted, k0, v0, ba));
-    size_t surv = nb_pairs;
-    if (o.eps_search > 0.0) {
-      ASCI_TRY_CUDA(cudaMemsetAsync(dsurv, 0, sizeof(unsigned long long), stream));
-      k_screen<<<grid_for(nb_pairs), 256, 0, stream>>>(I, k0, v0, nb_pairs, E0, o.eps_search,
-                                                       dsurv);
-      ASCI_CHECK_LAUNCH();
-      unsigned long long hs = 0;
-      ASCI_TRY_CUDA(cudaMemcpyAsync(&hs, dsurv, sizeof(hs), cudaMemcpyDefault, stream));
-      ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
-      surv = (size_t)hs;
-    }
-    surviving += surv;
+    void *tiles = nullptr;
+    size_t ntiles = 0;
+    ASCI_TRY(fused_stage(F, b.t0, b.t1, b.P0, b.P1, gg[0], gg[1] + 1, sb_beta, sb_j, sb_val, sb_haa,
+                         o.eps_search, dcount + 3, &tiles, &ntiles, ba));
     tm.stop(&tl[2]);
     tm.start();
-    size_t u = 0;
-    ASCI_TRY(sort_accumulate(&k0, &k1, &v0, &v1, nb_pairs, ukeys, usums, &u, ba));
-    tm.stop(&tl[3]);
-    tm.start();
-    ASCI_TRY(score_unique(I, ukeys, usums, u, psi_sorted, nd, E0, keep, uscore, ba));
-    ASCI_TRY(scan_exclusive_u32(keep, kpos, u, ba));
-    size_t kept = 0;
-    ASCI_TRY(kept_count(keep, kpos, u, &kept, ba));
-    const size_t u_real = (surv < nb_pairs) ? u - 1 : u;  // the sentinel run is not a target
-    unique += u_real;
-    excluded += u_real - kept;
-    ASCI_TRY(compact_u64(ukeys, keep, kpos, u, pool_k[pcur] + pool_n, ba));
-    ASCI_TRY(compact_f64(uscore, keep, kpos, u, pool_s[pcur] + pool_n, ba));
-    pool_n += kept;
-    tm.stop(&tl[5]);
-    if (pool_n > N && pool_n + bcap > pool_cap) {
-      tm.start();
-      size_t m2 = 0;
-      ASCI_TRY(select_topn_packed(pool_k[pcur], pool_s[pcur], pool_n, N, pool_k[pcur ^ 1],
-                                  pool_s[pcur ^ 1], &m2, ba));
-      pcur ^= 1;
-      pool_n = m2;
-      tm.stop(&tl[6]);
+    size_t t = 0;
+    while (t < ntiles) {
+      // tiles that can append at most the free capacity
+      size_t room = (pool_cap - pool_n) / tile_capacity();
+      if (room == 0) {
+        tm.stop(&tl[5]);
+        tm.start();
+        ASCI_TRY(prune(ba));
+        tm.stop(&tl[6]);
+        tm.start();
+        room = (pool_cap - pool_n) / tile_capacity();
+        if (room == 0) return ASCI_ENOMEM;
+      }
+      const size_t t1 = std::min(ntiles, t + room);
+      ASCI_TRY(fused_cells(F, tiles, (uint32_t)t, (uint32_t)t1, b.P0, sb_beta, sb_j, sb_val, sb_haa,
+                           tau, pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1,
+                           dcount + 2, tile_counter, ba));
+      unsigned long long c = 0;
+      ASCI_TRY_CUDA(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDefault, stream));
+      ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+      if (c > pool_cap) return ASCI_ECUDA;  // cannot happen: room bounds the appends
+      pool_n = (size_t)c;
+      t = t1;
+      if (pool_n > N && (pool_cap - pool_n) < pool_cap / 2) {
+        tm.stop(&tl[5]);
+        tm.start();
+        ASCI_TRY(prune(ba));
+        tm.stop(&tl[6]);
+        tm.start();
+      }
     }
+    tm.stop(&tl[5]);
+  }
+  uint64_t unique = 0, excluded = 0, surviving = (uint64_t)m * X.total;
+  if (bcap) {
+    unsigned long long hc[4];
+    ASCI_TRY_CUDA(cudaMemcpyAsync(hc, dcount, sizeof(hc), cudaMemcpyDefault, stream));
+    ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+    unique = hc[1];
+    excluded = hc[2];
+    if (o.eps_search > 0.0) surviving = hc[3];
   }
   // ------------------------------ select -----------------------------------
   tm.start();
@@ -708,6 +770,8 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     st->excluded = excluded;
     st->selected = nsel;
   }
+  (void)g_item0;
+  (void)G;
   total_tm.stop(&tl[7]);
   return ASCI_OK;
 }
