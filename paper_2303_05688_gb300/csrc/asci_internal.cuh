@@ -17,6 +17,17 @@ namespace asci {
 
 void record_error(const char *what, const char *file, int line);
 
+// Stage tracing to stderr, enabled by the environment variable ASCI_TRACE=1.
+bool trace_on();
+#define ASCI_TRACE(...)                                \
+  do {                                                 \
+    if (::asci::trace_on()) {                          \
+      fprintf(stderr, "[asci] " __VA_ARGS__);          \
+      fputc('\n', stderr);                             \
+      fflush(stderr);                                  \
+    }                                                  \
+  } while (0)
+
 // Library-owned stream-ordered memory pool of a device (kept cached between calls).
 int device_pool(int dev, cudaMemPool_t *pool);
 

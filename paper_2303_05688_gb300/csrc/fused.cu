@@ -138,6 +138,13 @@ __global__ void k_item_gflags(const uint64_t *items, uint64_t T, uint32_t *flag)
     flag[t] = (t == 0 || (items[t] >> 32) != (items[t - 1] >> 32)) ? 1u : 0u;
 }
 
+// group of each item = (group starts up to and including it) - 1
+__global__ void k_item_gfix(const uint32_t *flag, uint64_t T, uint32_t *gid) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+       t += (uint64_t)gridDim.x * blockDim.x)
+    gid[t] = gid[t] + flag[t] - 1u;
+}
+
 __global__ void k_group_tab(const uint64_t *items, const uint32_t *flag, const uint32_t *gid,
                             const uint64_t *Wexcl, uint64_t T, uint32_t *g_alpha, uint64_t *g_P0,
                             uint64_t *g_item0) {
@@ -156,6 +163,12 @@ __global__ void k_group_tab(const uint64_t *items, const uint32_t *flag, const u
 enum : uint32_t { kTilePacked = 0, kTileMedium = 1, kTileBucket = 2 };
 
 constexpr uint32_t kDropped = 0xffffffffu;  // core index of a screened-out record
+
+// bits of the device error word of the constraint-tile kernels
+constexpr unsigned kErrProbe = 1u;      // exclusion probe ran past the table
+constexpr unsigned kErrTile = 2u;       // a tile holds more records than fit on chip
+constexpr unsigned kErrStage = 4u;      // a record position outside the staging buffer
+constexpr unsigned kErrCore = 8u;       // a core index outside the core
 
 struct TileDesc {
   uint32_t start;   // first record in the batch staging buffer
@@ -287,6 +300,9 @@ struct EmitArgs {
   int64_t E0_x;
   double inv_scale;
   unsigned long long *survivors;
+  uint64_t stage_cap;  // records the staging buffer holds
+  uint32_t ncore;
+  unsigned *err;
 };
 
 constexpr int kEmitThreads = 256;
@@ -488,6 +504,10 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
         else
           pos = (uint32_t)(p - A.P0);
         (void)At;
+        if (jdx >= A.ncore) {
+          atomicOr(A.err, kErrCore);
+          jdx = 0;
+        }
         const double v = h * A.core_c[jdx];
         const int64_t haa = A.Dx[jdx] + dh;
         uint32_t jj = jdx;
@@ -497,10 +517,14 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
           if (!(fabs(v) > A.eps * fabs(den))) jj = kDropped;
         }
         kept = jj != kDropped;
-        A.sb_beta[pos] = tb;
-        A.sb_j[pos] = jj;
-        A.sb_val[pos] = v;
-        A.sb_haa[pos] = haa;
+        if (pos < A.stage_cap) {
+          A.sb_beta[pos] = tb;
+          A.sb_j[pos] = jj;
+          A.sb_val[pos] = v;
+          A.sb_haa[pos] = haa;
+        } else {
+          atomicOr(A.err, kErrStage);
+        }
       }
       if (A.eps > 0.0) {
         const uint32_t nk = __popc(__ballot_sync(0xffffffffu, kept));
@@ -534,6 +558,8 @@ struct CellArgs {
   unsigned long long cand_cap;
   unsigned long long *n_unique, *n_excluded;
   unsigned *tile_counter;
+  uint64_t stage_cap;
+  unsigned *err;
 };
 
 __device__ __forceinline__ uint64_t mix_key(uint64_t z) {
@@ -545,14 +571,19 @@ __device__ __forceinline__ uint64_t mix_key(uint64_t z) {
   return z;
 }
 
-__device__ __forceinline__ bool psi_contains(const uint64_t *ht, uint64_t mask, uint64_t key) {
+// Open addressing with linear probing; the table is at most 1/4 full, and the
+// probe count is bounded by the table size (exceeding it sets *err).
+__device__ __forceinline__ bool psi_contains(const uint64_t *ht, uint64_t mask, uint64_t key,
+                                             unsigned *err) {
   uint64_t h = mix_key(key) & mask;
-  for (;;) {
+  for (uint64_t probe = 0; probe <= mask; ++probe) {
     uint64_t s = ht[h];
     if (s == key) return true;
     if (s == ~0ull) return false;
     h = (h + 1) & mask;
   }
+  atomicOr(err, kErrProbe);
+  return false;
 }
 
 struct CellSmem {
@@ -701,6 +732,12 @@ __global__ void __launch_bounds__(kCellThreads, 1) k_cells(CellArgs C) {
     const uint32_t tile = S.tile;
     if (tile >= C.ntiles) break;
     const TileDesc d = C.tiles[tile];
+    if (d.npairs > (uint32_t)kCap || (uint64_t)d.start + d.npairs > C.stage_cap ||
+        (d.kind == kTilePacked && d.ng > kGroupsPerTile)) {
+      if (threadIdx.x == 0) atomicOr(C.err, kErrTile);
+      __syncthreads();
+      continue;
+    }
     const int nrec = (int)d.npairs;
     if (d.kind == kTilePacked) {
       for (uint32_t i = threadIdx.x; i < d.ng; i += kCellThreads) {
@@ -761,7 +798,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) k_cells(CellArgs C) {
       unique_target(S, d, sk, &a, &b);
       const uint64_t full = pack_key(a, b);
       ++my_unique;
-      if (psi_contains(C.psi_ht, C.psi_mask, full)) {
+      if (psi_contains(C.psi_ht, C.psi_mask, full, C.err)) {
         ++my_excl;
         continue;
       }
@@ -946,6 +983,8 @@ int item_groups(const uint64_t *items, const uint64_t *Wexcl, uint64_t T, uint32
   ASCI_TRY(scan_exclusive_u32(flag, item_group, T, tmp));
   size_t ng = 0;
   ASCI_TRY(kept_count(flag, item_group, T, &ng, tmp));
+  k_item_gfix<<<grid_for(T), 256, 0, s>>>(flag, T, item_group);
+  ASCI_CHECK_LAUNCH();
   ASCI_TRY(arena.alloc(g_alpha, ng));
   ASCI_TRY(arena.alloc(g_P0, ng));
   ASCI_TRY(arena.alloc(g_item0, ng));
@@ -976,8 +1015,8 @@ int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t 
 // the staging buffer.  The tile table is left in *tiles_out (arena memory).
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
                 uint32_t gb0, uint32_t gb1, uint32_t *sb_beta, uint32_t *sb_j, double *sb_val,
-                int64_t *sb_haa, double eps, unsigned long long *survivors, void **tiles_out,
-                size_t *ntiles_out, Arena &arena) {
+                int64_t *sb_haa, uint64_t stage_cap, double eps, unsigned long long *survivors,
+                unsigned *err, void **tiles_out, size_t *ntiles_out, Arena &arena) {
   cudaStream_t s = arena.stream();
   const uint32_t ng = gb1 - gb0;
   *ntiles_out = 0;
@@ -996,6 +1035,7 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   k_group_class<<<grid_for(ng), 256, 0, s>>>(F.g_P0, gb0, gb1, P1, kind, nb, small_pairs,
                                              small_cnt);
   ASCI_CHECK_LAUNCH();
+  ASCI_TRACE("stage: classified %u groups", ng);
   ASCI_TRY(scan_exclusive_u64(small_pairs, Ws, ng, arena));
   ASCI_TRY(scan_exclusive_u32(small_cnt, Ns, ng, arena));
   ASCI_TRY(scan_exclusive_u32(nb, cellbase, ng, arena));
@@ -1005,6 +1045,11 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   ASCI_CHECK_LAUNCH();
   ASCI_TRY(scan_exclusive_u32(ntile, tile_base, ng, arena));
   ASCI_TRY(kept_count(ntile, tile_base, ng, &ntiles, arena));
+  ASCI_TRACE("stage: cells=%zu tiles=%zu", ncells, ntiles);
+  if (ncells > P1 - P0 || ntiles > P1 - P0) {
+    record_error("inconsistent tile plan", __FILE__, __LINE__);
+    return ASCI_ECUDA;
+  }
 
   uint32_t *cnt, *cnt_scan, *cell_pos0, *fill;
   ASCI_TRY(arena.alloc(&cnt, ncells + 1));
@@ -1054,6 +1099,9 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   A.E0_x = F.E0_x;
   A.inv_scale = ldexp(1.0, -F.X.s);
   A.survivors = survivors;
+  A.stage_cap = stage_cap;
+  A.ncore = F.ncore;
+  A.err = err;
   const uint64_t etiles = (P1 - P0 + kEmitTile - 1) / kEmitTile;
   const size_t emit_smem = 2 * (size_t)F.X.n * F.X.n * sizeof(int64_t);
   if (ncells) {
@@ -1071,8 +1119,10 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
                                             tile_base, cellbase, cnt, cnt_scan, tiles, cell_pos0,
                                             overflow);
   ASCI_CHECK_LAUNCH();
+  ASCI_TRACE("stage: tiles written");
   k_emit2<1><<<(unsigned)etiles, kEmitThreads, emit_smem, s>>>(A);
   ASCI_CHECK_LAUNCH();
+  ASCI_TRACE("stage: emit launched (%llu blocks)", (unsigned long long)etiles);
   unsigned hov = 0;
   ASCI_TRY_CUDA(cudaMemcpyAsync(&hov, overflow, sizeof(hov), cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
@@ -1092,10 +1142,10 @@ size_t tile_capacity() { return (size_t)kCap; }
 // targets with |S| >= tau to the candidate buffer (at most kCap per tile).
 int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint32_t tile_end,
                 uint64_t P0, const uint32_t *sb_beta, const uint32_t *sb_j, const double *sb_val,
-                const int64_t *sb_haa, double tau, uint64_t *cand_key, double *cand_score,
-                unsigned long long *cand_count, unsigned long long cand_cap,
+                const int64_t *sb_haa, uint64_t stage_cap, double tau, uint64_t *cand_key,
+                double *cand_score, unsigned long long *cand_count, unsigned long long cand_cap,
                 unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *counter,
-                Arena &arena) {
+                unsigned *err, Arena &arena) {
   if (tile_end <= tile_begin) return ASCI_OK;
   cudaStream_t s = arena.stream();
   CellArgs CA;
@@ -1123,6 +1173,8 @@ int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint
   CA.n_unique = n_unique;
   CA.n_excluded = n_excluded;
   CA.tile_counter = counter;
+  CA.stage_cap = stage_cap;
+  CA.err = err;
   ASCI_TRY_CUDA(cudaMemcpyAsync(counter, &tile_begin, sizeof(unsigned), cudaMemcpyDefault, s));
   const size_t cell_smem = sizeof(CellSmem);
   static bool attr_set = false;
@@ -1135,6 +1187,7 @@ int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint
   ASCI_TRY_CUDA(cudaGetDevice(&dev));
   ASCI_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const unsigned grid = (unsigned)std::min<size_t>((size_t)sms, tile_end - tile_begin);
+  ASCI_TRACE("cells: launch grid=%u smem=%zu", grid, cell_smem);
   k_cells<<<grid, kCellThreads, cell_smem, s>>>(CA);
   ASCI_CHECK_LAUNCH();
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));  // `tile_begin` is read from the host stack

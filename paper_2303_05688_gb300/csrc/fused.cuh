@@ -32,6 +32,7 @@ struct FusedCore {
   int64_t E0_x;
   const uint64_t *psi_ht;
   uint64_t psi_mask;
+  uint32_t ncore;
 };
 
 }  // namespace asci

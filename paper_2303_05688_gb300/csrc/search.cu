@@ -17,6 +17,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -48,14 +49,14 @@ int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t 
                    Arena &arena);
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
                 uint32_t gb0, uint32_t gb1, uint32_t *sb_beta, uint32_t *sb_j, double *sb_val,
-                int64_t *sb_haa, double eps, unsigned long long *survivors, void **tiles_out,
-                size_t *ntiles_out, Arena &arena);
+                int64_t *sb_haa, uint64_t stage_cap, double eps, unsigned long long *survivors,
+                unsigned *err, void **tiles_out, size_t *ntiles_out, Arena &arena);
 int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint32_t tile_end,
                 uint64_t P0, const uint32_t *sb_beta, const uint32_t *sb_j, const double *sb_val,
-                const int64_t *sb_haa, double tau, uint64_t *cand_key, double *cand_score,
-                unsigned long long *cand_count, unsigned long long cand_cap,
+                const int64_t *sb_haa, uint64_t stage_cap, double tau, uint64_t *cand_key,
+                double *cand_score, unsigned long long *cand_count, unsigned long long cand_cap,
                 unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *counter,
-                Arena &arena);
+                unsigned *err, Arena &arena);
 size_t tile_capacity();
 int abs_min(const double *s, size_t n, double *host_min, Arena &arena);
 
@@ -63,6 +64,14 @@ static thread_local char g_last_error[512] = "";
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+bool trace_on() {
+  static const bool on = [] {
+    const char *v = getenv("ASCI_TRACE");
+    return v && v[0] && v[0] != '0';
+  }();
+  return on;
+}
 
 void record_error(const char *what, const char *file, int line) {
   snprintf(g_last_error, sizeof(g_last_error), "%s (%s:%d)", what, file, line);
@@ -416,6 +425,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   ASCI_TRY(to_device(ints->h1, (size_t)n * n, &h1, arena));
   ASCI_TRY(to_device(ints->eri, (size_t)n * n * n * n, &eri, arena));
 
+  ASCI_TRACE("search: ndets=%zu norb=%d C=%zu N=%zu eps=%g", nd, n, C, N, o.eps_search);
   // electron counts from the first determinant
   asci_det d0;
   ASCI_TRY_CUDA(cudaMemcpyAsync(&d0, dets, sizeof(d0), cudaMemcpyDefault, stream));
@@ -502,6 +512,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
                                                        grp_count);
   ASCI_CHECK_LAUNCH();
 
+  ASCI_TRACE("prepared: core=%zu groups=%zu", m, ngroups);
   DevInts I;
   ASCI_TRY(build_tables(h1, eri, n, na, nb, ints->ecore, o.precision != ASCI_FP64, arena, &I));
   const ExcCounts X = exc_counts(n, na, nb);
@@ -571,6 +582,9 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   }
   uint64_t bcap = 0;
   for (auto &b : batches) bcap = std::max(bcap, b.P1 - b.P0);
+  ASCI_TRACE("planned: items=%llu pairs=%llu batches=%zu max_batch=%llu level=%d",
+             (unsigned long long)T, (unsigned long long)P, batches.size(),
+             (unsigned long long)bcap, max_level);
   if (st) {
     st->batches = batches.size();
     st->max_batch = bcap;
@@ -600,6 +614,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   ASCI_TRY(psi_hash_build(psi_sorted, nd, &psi_ht, &psi_mask, arena));
   F.psi_ht = psi_ht;
   F.psi_mask = psi_mask;
+  F.ncore = (uint32_t)m;
   ASCI_TRY(build_fx(h1, eri, n, na, nb, ints->ecore, E0, arena, &F.X, &F.E0_x));
   {
     uint32_t *core_alpha32;
@@ -627,6 +642,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   F.g_alpha = g_alpha;
   F.g_P0 = g_P0;
   tm.stop(&tl[1]);
+  ASCI_TRACE("tables: fixed-point scale 2^-%d, target groups=%zu", F.X.s, G);
 
   int dev = 0, sms = 152;
   ASCI_TRY_CUDA(cudaGetDevice(&dev));
@@ -640,7 +656,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   uint64_t *pool_k[2] = {nullptr, nullptr};
   double *pool_s[2] = {nullptr, nullptr};
   unsigned long long *dcount = nullptr;  // [0] candidates, [1] unique, [2] excluded, [3] survivors
-  unsigned *tile_counter = nullptr;
+  unsigned *tile_counter = nullptr, *derr2 = nullptr;
   if (bcap) {
     ASCI_TRY(arena.alloc(&sb_beta, bcap));
     ASCI_TRY(arena.alloc(&sb_j, bcap));
@@ -652,7 +668,9 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     }
     ASCI_TRY(arena.alloc(&dcount, 4));
     ASCI_TRY(arena.alloc(&tile_counter, 1));
+    ASCI_TRY(arena.alloc(&derr2, 1));
     ASCI_TRY_CUDA(cudaMemsetAsync(dcount, 0, 4 * sizeof(unsigned long long), stream));
+    ASCI_TRY_CUDA(cudaMemsetAsync(derr2, 0, sizeof(unsigned), stream));
   }
   size_t pool_n = 0;
   int pcur = 0;
@@ -680,8 +698,16 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     tm.start();
     void *tiles = nullptr;
     size_t ntiles = 0;
+    if ((size_t)gg[1] + 1 > G || gg[0] > gg[1]) {
+      record_error("batch group range outside the group table", __FILE__, __LINE__);
+      return ASCI_ECUDA;
+    }
+    ASCI_TRACE("batch: items [%llu,%llu) pairs [%llu,%llu) groups [%u,%u)",
+               (unsigned long long)b.t0, (unsigned long long)b.t1, (unsigned long long)b.P0,
+               (unsigned long long)b.P1, gg[0], gg[1] + 1);
     ASCI_TRY(fused_stage(F, b.t0, b.t1, b.P0, b.P1, gg[0], gg[1] + 1, sb_beta, sb_j, sb_val, sb_haa,
-                         o.eps_search, dcount + 3, &tiles, &ntiles, ba));
+                         bcap, o.eps_search, dcount + 3, derr2, &tiles, &ntiles, ba));
+    ASCI_TRACE("staged: tiles=%zu", ntiles);
     tm.stop(&tl[2]);
     tm.start();
     size_t t = 0;
@@ -698,12 +724,21 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
         if (room == 0) return ASCI_ENOMEM;
       }
       const size_t t1 = std::min(ntiles, t + room);
+      ASCI_TRACE("cells: tiles [%zu,%zu) tau=%.6g pool=%zu", t, t1, tau, pool_n);
       ASCI_TRY(fused_cells(F, tiles, (uint32_t)t, (uint32_t)t1, b.P0, sb_beta, sb_j, sb_val, sb_haa,
-                           tau, pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1,
-                           dcount + 2, tile_counter, ba));
+                           bcap, tau, pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1,
+                           dcount + 2, tile_counter, derr2, ba));
       unsigned long long c = 0;
+      unsigned he = 0;
       ASCI_TRY_CUDA(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDefault, stream));
+      ASCI_TRY_CUDA(cudaMemcpyAsync(&he, derr2, sizeof(he), cudaMemcpyDefault, stream));
       ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+      if (he) {
+        char msg[96];
+        snprintf(msg, sizeof(msg), "constraint-tile kernel check failed (flags 0x%x)", he);
+        record_error(msg, __FILE__, __LINE__);
+        return ASCI_ECUDA;
+      }
       if (c > pool_cap) return ASCI_ECUDA;  // cannot happen: room bounds the appends
       pool_n = (size_t)c;
       t = t1;
@@ -726,6 +761,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     excluded = hc[2];
     if (o.eps_search > 0.0) surviving = hc[3];
   }
+  ASCI_TRACE("select: pool=%zu N=%zu", pool_n, N);
   // ------------------------------ select -----------------------------------
   tm.start();
   size_t nsel = 0;
@@ -773,6 +809,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   (void)g_item0;
   (void)G;
   total_tm.stop(&tl[7]);
+  if (st) memcpy(st->t_stage, tl, sizeof(tl));
   return ASCI_OK;
 }
 
