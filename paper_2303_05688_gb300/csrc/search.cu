@@ -751,6 +751,11 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
       }
     }
     tm.stop(&tl[5]);
+    if (pool_n > N) {  // tighten tau before the next batch
+      tm.start();
+      ASCI_TRY(prune(ba));
+      tm.stop(&tl[6]);
+    }
   }
   uint64_t unique = 0, excluded = 0, surviving = (uint64_t)m * X.total;
   if (bcap) {
