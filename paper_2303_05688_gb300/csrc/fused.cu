@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "asci_internal.cuh"
 #include "fused.cuh"
@@ -170,7 +171,7 @@ constexpr unsigned kErrTile = 2u;       // a tile holds more records than fit on
 constexpr unsigned kErrStage = 4u;      // a record position outside the staging buffer
 constexpr unsigned kErrCore = 8u;       // a core index outside the core
 
-struct TileDesc {
+struct TileDesc {  // 24 bytes; npairs at byte offset 4 (read by the host)
   uint32_t start;   // first record in the batch staging buffer
   uint32_t npairs;  // records in the tile
   uint32_t g0;      // first group (global id)
@@ -178,6 +179,8 @@ struct TileDesc {
   uint32_t kind;
   uint32_t alpha;   // target alpha string (medium / bucket tiles)
 };
+
+static_assert(sizeof(TileDesc) == 24, "tile descriptor layout");
 
 }  // namespace
 
@@ -226,7 +229,7 @@ __global__ void k_tile_write(uint32_t gb0, uint32_t ng, uint64_t P0, uint64_t Pe
                              const uint32_t *Ns, const uint32_t *tile_base,
                              const uint32_t *cellbase, const uint32_t *cnt,
                              const uint32_t *cnt_scan, TileDesc *tiles, uint32_t *cell_pos0,
-                             unsigned *overflow) {
+                             unsigned *n_over, uint32_t *over_list, uint32_t over_cap) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
     const uint32_t g = gb0 + i;
     const uint64_t P = ((i + 1 < ng) ? g_P0[g + 1] : Pend) - g_P0[g];
@@ -262,7 +265,11 @@ __global__ void k_tile_write(uint32_t gb0, uint32_t ng, uint64_t P0, uint64_t Pe
         d.ng = 1;
         d.kind = kTileBucket;
         d.alpha = g_alpha[g];
-        if (d.npairs > (uint32_t)kCap) atomicOr(overflow, 1u);
+        if (d.npairs > (uint32_t)kCap) {
+          // too large for one tile on chip: reduced through the global sort
+          const unsigned slot = atomicAdd(n_over, 1u);
+          if (slot < over_cap) over_list[slot] = tile_base[i] + b;
+        }
         tiles[tile_base[i] + b] = d;
         cell_pos0[cb + b] = d.start;
       }
@@ -734,7 +741,10 @@ __global__ void __launch_bounds__(kCellThreads, 1) k_cells(CellArgs C) {
     const TileDesc d = C.tiles[tile];
     if (d.npairs > (uint32_t)kCap || (uint64_t)d.start + d.npairs > C.stage_cap ||
         (d.kind == kTilePacked && d.ng > kGroupsPerTile)) {
-      if (threadIdx.x == 0) atomicOr(C.err, kErrTile);
+      // oversized hash buckets are reduced by the global path; anything else is a bug
+      if (threadIdx.x == 0 && !(d.kind == kTileBucket && d.npairs > (uint32_t)kCap &&
+                                (uint64_t)d.start + d.npairs <= C.stage_cap))
+        atomicOr(C.err, kErrTile);
       __syncthreads();
       continue;
     }
@@ -865,6 +875,54 @@ __global__ void __launch_bounds__(kCellThreads, 1) k_cells(CellArgs C) {
     my_excl += __shfl_xor_sync(0xffffffffu, my_excl, dl);
   }
   if (lane == 0) {
+    if (my_unique) atomicAdd(C.n_unique, my_unique);
+    if (my_excl) atomicAdd(C.n_excluded, my_excl);
+  }
+}
+
+// ---------------------------------------------- oversized hash buckets ---
+// A bucket holding more records than one tile is sorted in global memory on
+// (beta', core index) and its runs are reduced one target per thread.
+
+__global__ void k_big_keys(const uint32_t *sb_beta, const uint32_t *sb_j, uint32_t start,
+                           uint32_t n, uint64_t *keys, uint32_t *idx) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t j = sb_j[start + i];
+    keys[i] = (j == kDropped) ? ~0ull : (((uint64_t)sb_beta[start + i] << 32) | j);
+    idx[i] = i;
+  }
+}
+
+__global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, uint32_t n, uint32_t start,
+                             uint32_t alpha, CellArgs C) {
+  unsigned long long my_unique = 0, my_excl = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint64_t sk = keys[i];
+    if (sk == ~0ull) continue;
+    if (i > 0 && (keys[i - 1] >> 32) == (sk >> 32)) continue;
+    double num = 0.0;
+    for (uint32_t e = i; e < n && (keys[e] >> 32) == (sk >> 32); ++e) num += C.sb_val[start + idx[e]];
+    const uint64_t full = pack_key(alpha, (uint32_t)(sk >> 32));
+    ++my_unique;
+    if (psi_contains(C.psi_ht, C.psi_mask, full, C.err)) {
+      ++my_excl;
+      continue;
+    }
+    const int64_t den_x = C.E0_x - C.sb_haa[start + idx[i]];
+    const double sc = num / (__ll2double_rn(den_x) * C.inv_scale);
+    if (fabs(sc) >= C.tau) {
+      const unsigned long long slot = atomicAdd(C.cand_count, 1ull);
+      if (slot < C.cand_cap) {
+        C.cand_key[slot] = full;
+        C.cand_score[slot] = sc;
+      }
+    }
+  }
+  for (int dl = 16; dl; dl >>= 1) {
+    my_unique += __shfl_xor_sync(0xffffffffu, my_unique, dl);
+    my_excl += __shfl_xor_sync(0xffffffffu, my_excl, dl);
+  }
+  if ((threadIdx.x & 31) == 0) {
     if (my_unique) atomicAdd(C.n_unique, my_unique);
     if (my_excl) atomicAdd(C.n_excluded, my_excl);
   }
@@ -1016,10 +1074,12 @@ int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t 
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
                 uint32_t gb0, uint32_t gb1, uint32_t *sb_beta, uint32_t *sb_j, double *sb_val,
                 int64_t *sb_haa, uint64_t stage_cap, double eps, unsigned long long *survivors,
-                unsigned *err, void **tiles_out, size_t *ntiles_out, Arena &arena) {
+                unsigned *err, void **tiles_out, size_t *ntiles_out,
+                std::vector<uint32_t> *oversized, Arena &arena) {
   cudaStream_t s = arena.stream();
   const uint32_t ng = gb1 - gb0;
   *ntiles_out = 0;
+  oversized->clear();
   if (P1 <= P0 || ng == 0) return ASCI_OK;
   uint32_t *kind, *nb, *small_cnt, *Ns, *cellbase, *ntile, *tile_base;
   uint64_t *small_pairs, *Ws;
@@ -1110,26 +1170,35 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   }
   ASCI_TRY(scan_exclusive_u32(cnt, cnt_scan, ncells + 1, arena));
   TileDesc *tiles;
-  unsigned *overflow;
+  unsigned *n_over;
+  uint32_t *over_list;
+  const uint32_t over_cap = (uint32_t)std::min<size_t>(ncells + 1, 1u << 20);
   ASCI_TRY(arena.alloc(&tiles, ntiles + 1));
-  ASCI_TRY(arena.alloc(&overflow, 1));
+  ASCI_TRY(arena.alloc(&n_over, 1));
+  ASCI_TRY(arena.alloc(&over_list, over_cap));
   ASCI_TRY_CUDA(cudaMemsetAsync(tiles, 0, (ntiles + 1) * sizeof(TileDesc), s));
-  ASCI_TRY_CUDA(cudaMemsetAsync(overflow, 0, sizeof(unsigned), s));
+  ASCI_TRY_CUDA(cudaMemsetAsync(n_over, 0, sizeof(unsigned), s));
   k_tile_write<<<grid_for(ng), 256, 0, s>>>(gb0, ng, P0, P1, F.g_P0, F.g_alpha, kind, nb, Ws, Ns,
                                             tile_base, cellbase, cnt, cnt_scan, tiles, cell_pos0,
-                                            overflow);
+                                            n_over, over_list, over_cap);
   ASCI_CHECK_LAUNCH();
   ASCI_TRACE("stage: tiles written");
   k_emit2<1><<<(unsigned)etiles, kEmitThreads, emit_smem, s>>>(A);
   ASCI_CHECK_LAUNCH();
   ASCI_TRACE("stage: emit launched (%llu blocks)", (unsigned long long)etiles);
   unsigned hov = 0;
-  ASCI_TRY_CUDA(cudaMemcpyAsync(&hov, overflow, sizeof(hov), cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&hov, n_over, sizeof(hov), cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
-  if (hov) {
-    record_error("a hash bucket of a large constraint class exceeds the tile capacity", __FILE__,
-                 __LINE__);
+  if (hov > over_cap) {
+    record_error("too many oversized hash buckets", __FILE__, __LINE__);
     return ASCI_ENOMEM;
+  }
+  if (hov) {
+    oversized->resize(hov);
+    ASCI_TRY_CUDA(cudaMemcpyAsync(oversized->data(), over_list, hov * sizeof(uint32_t),
+                                  cudaMemcpyDefault, s));
+    ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+    std::sort(oversized->begin(), oversized->end());
   }
   *tiles_out = tiles;
   *ntiles_out = ntiles;
@@ -1191,6 +1260,55 @@ int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint
   k_cells<<<grid, kCellThreads, cell_smem, s>>>(CA);
   ASCI_CHECK_LAUNCH();
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));  // `tile_begin` is read from the host stack
+  return ASCI_OK;
+}
+
+// Reduce one oversized bucket tile through the global radix sort.  Appends at
+// most `npairs` candidates.
+int fused_big_tile(const FusedCore &F, const void *tiles, uint32_t tile, uint64_t P0,
+                   const uint32_t *sb_beta, const uint32_t *sb_j, const double *sb_val,
+                   const int64_t *sb_haa, uint64_t stage_cap, double tau, uint64_t *cand_key,
+                   double *cand_score, unsigned long long *cand_count,
+                   unsigned long long cand_cap, unsigned long long *n_unique,
+                   unsigned long long *n_excluded, unsigned *err, uint32_t *npairs_out,
+                   Arena &arena) {
+  cudaStream_t s = arena.stream();
+  TileDesc d;
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&d, static_cast<const TileDesc *>(tiles) + tile, sizeof(d),
+                                cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  *npairs_out = d.npairs;
+  if ((uint64_t)d.start + d.npairs > stage_cap) return ASCI_ECUDA;
+  Arena ta(s);
+  uint64_t *k0, *k1;
+  uint32_t *i0, *i1;
+  ASCI_TRY(ta.alloc(&k0, d.npairs));
+  ASCI_TRY(ta.alloc(&k1, d.npairs));
+  ASCI_TRY(ta.alloc(&i0, d.npairs));
+  ASCI_TRY(ta.alloc(&i1, d.npairs));
+  k_big_keys<<<grid_for(d.npairs), 256, 0, s>>>(sb_beta, sb_j, d.start, d.npairs, k0, i0);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(radix_sort_u64_u32(&k0, &k1, &i0, &i1, d.npairs, 0, 64, ta));
+  CellArgs CA;
+  memset(&CA, 0, sizeof(CA));
+  CA.sb_val = sb_val;
+  CA.sb_haa = sb_haa;
+  CA.E0_x = F.E0_x;
+  CA.inv_scale = ldexp(1.0, -F.X.s);
+  CA.tau = tau;
+  CA.psi_ht = F.psi_ht;
+  CA.psi_mask = F.psi_mask;
+  CA.cand_key = cand_key;
+  CA.cand_score = cand_score;
+  CA.cand_count = cand_count;
+  CA.cand_cap = cand_cap;
+  CA.n_unique = n_unique;
+  CA.n_excluded = n_excluded;
+  CA.err = err;
+  (void)P0;
+  k_big_reduce<<<grid_for(d.npairs), 256, 0, s>>>(k0, i0, d.npairs, d.start, d.alpha, CA);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
   return ASCI_OK;
 }
 

@@ -50,7 +50,15 @@ int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t 
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
                 uint32_t gb0, uint32_t gb1, uint32_t *sb_beta, uint32_t *sb_j, double *sb_val,
                 int64_t *sb_haa, uint64_t stage_cap, double eps, unsigned long long *survivors,
-                unsigned *err, void **tiles_out, size_t *ntiles_out, Arena &arena);
+                unsigned *err, void **tiles_out, size_t *ntiles_out,
+                std::vector<uint32_t> *oversized, Arena &arena);
+int fused_big_tile(const FusedCore &F, const void *tiles, uint32_t tile, uint64_t P0,
+                   const uint32_t *sb_beta, const uint32_t *sb_j, const double *sb_val,
+                   const int64_t *sb_haa, uint64_t stage_cap, double tau, uint64_t *cand_key,
+                   double *cand_score, unsigned long long *cand_count,
+                   unsigned long long cand_cap, unsigned long long *n_unique,
+                   unsigned long long *n_excluded, unsigned *err, uint32_t *npairs_out,
+                   Arena &arena);
 int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint32_t tile_end,
                 uint64_t P0, const uint32_t *sb_beta, const uint32_t *sb_j, const double *sb_val,
                 const int64_t *sb_haa, uint64_t stage_cap, double tau, uint64_t *cand_key,
@@ -705,9 +713,10 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     ASCI_TRACE("batch: items [%llu,%llu) pairs [%llu,%llu) groups [%u,%u)",
                (unsigned long long)b.t0, (unsigned long long)b.t1, (unsigned long long)b.P0,
                (unsigned long long)b.P1, gg[0], gg[1] + 1);
+    std::vector<uint32_t> oversized;
     ASCI_TRY(fused_stage(F, b.t0, b.t1, b.P0, b.P1, gg[0], gg[1] + 1, sb_beta, sb_j, sb_val, sb_haa,
-                         bcap, o.eps_search, dcount + 3, derr2, &tiles, &ntiles, ba));
-    ASCI_TRACE("staged: tiles=%zu", ntiles);
+                         bcap, o.eps_search, dcount + 3, derr2, &tiles, &ntiles, &oversized, ba));
+    ASCI_TRACE("staged: tiles=%zu oversized=%zu", ntiles, oversized.size());
     tm.stop(&tl[2]);
     tm.start();
     size_t t = 0;
@@ -749,6 +758,31 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
         tm.stop(&tl[6]);
         tm.start();
       }
+    }
+    // buckets too large for one tile: global sort on (beta', core index)
+    for (uint32_t ot : oversized) {
+      unsigned long long c = 0;
+      uint32_t np = 0;
+      ASCI_TRY_CUDA(cudaMemcpyAsync(&np, static_cast<const char *>(tiles) + (size_t)ot * 24 + 4,
+                                    sizeof(np), cudaMemcpyDefault, stream));
+      ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+      // room for every record of the bucket as a candidate
+      if (pool_cap - pool_n < np) {
+        tm.stop(&tl[5]);
+        tm.start();
+        ASCI_TRY(prune(ba));
+        tm.stop(&tl[6]);
+        tm.start();
+        if (pool_cap - pool_n < np) return ASCI_ENOMEM;
+      }
+      ASCI_TRY(fused_big_tile(F, tiles, ot, b.P0, sb_beta, sb_j, sb_val, sb_haa, bcap, tau,
+                              pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1, dcount + 2,
+                              derr2, &np, ba));
+      ASCI_TRY_CUDA(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDefault, stream));
+      ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+      if (c > pool_cap) return ASCI_ECUDA;
+      pool_n = (size_t)c;
+      ASCI_TRACE("oversized tile %u: %u records, pool=%zu", ot, np, pool_n);
     }
     tm.stop(&tl[5]);
     if (pool_n > N) {  // tighten tau before the next batch

@@ -278,3 +278,33 @@ def _check_sampled(oracle_mod, h1, eri, ec, A, B, c, E0, C, ga, gb, gs, nsample,
     # every selected |S| is at least the smallest selected one (trivially) and the
     # set is closed: no key repeats
     assert len(set(zip(ga.tolist(), gb.tolist()))) == len(ga)
+
+
+def test_search_hot_target_beyond_one_tile(torch_cuda, asci, oracle_mod):
+    """A target with more contributions than one on-chip tile holds (oversized bucket path).
+
+    psi = every single and double excitation of one determinant T (20 orbitals,
+    10 alpha + 10 beta), all in the core, T itself outside psi: T collects
+    14,250 contributions, more than a tile's 8192 records.
+    """
+    torch = torch_cuda
+    n, na, nb = 20, 10, 10
+    h1, eri, ec = W.random_molecular(n, 31)
+    T = (0b00000111111111100000 & ((1 << n) - 1), 0b00001111100000111110 & ((1 << n) - 1))
+    assert bin(T[0]).count("1") == na and bin(T[1]).count("1") == nb
+    ints = oracle_mod.Ints(h1, eri, ec)
+    ta, tb, _ = oracle_mod.pairs(ints, [T[0]], [T[1]], [1.0])
+    rng = np.random.default_rng(4)
+    c = rng.normal(size=len(ta)) * 0.01
+    E0 = oracle_mod.diag(ints, T) - 0.5
+    C = len(ta)
+    ga, gb, gs, st = _run(asci, torch, ta, tb, c, E0, h1, eri, ec, C, 200)
+    keys = list(zip(ga.tolist(), gb.tolist()))
+    assert (T[0], T[1]) in keys, "the hot target must rank in the top 200"
+    num, abss = oracle_mod.numerator(ints, T, ta, tb, c)
+    S = num / (E0 - oracle_mod.diag(ints, T))
+    got = gs[keys.index((T[0], T[1]))]
+    assert abs(got - S) <= score_tol(S, abss, oracle_mod.diag(ints, T), E0)
+    assert st.generated == C * W.n_excitations(n, na, nb)
+    # sampled selected outputs against brute-force numerators
+    _check_sampled(oracle_mod, h1, eri, ec, ta, tb, c, E0, C, ga, gb, gs, 24, seed=2)
