@@ -293,9 +293,11 @@ def test_search_hot_target_beyond_one_tile(torch_cuda, asci, oracle_mod):
     T = (0b00000111111111100000 & ((1 << n) - 1), 0b00001111100000111110 & ((1 << n) - 1))
     assert bin(T[0]).count("1") == na and bin(T[1]).count("1") == nb
     ints = oracle_mod.Ints(h1, eri, ec)
-    ta, tb, _ = oracle_mod.pairs(ints, [T[0]], [T[1]], [1.0])
+    ta, tb, hv = oracle_mod.pairs(ints, [T[0]], [T[1]], [1.0])
+    # coefficients aligned with H_{T,j} (= H_{j,T}, hermiticity) so that the
+    # 14,250 contributions to T add up instead of cancelling
     rng = np.random.default_rng(4)
-    c = rng.normal(size=len(ta)) * 0.01
+    c = 0.01 * np.where(hv >= 0, 1.0, -1.0) * (1.0 + 0.1 * rng.random(len(ta)))
     E0 = oracle_mod.diag(ints, T) - 0.5
     C = len(ta)
     ga, gb, gs, st = _run(asci, torch, ta, tb, c, E0, h1, eri, ec, C, 200)
