@@ -1,0 +1,178 @@
+// Exact summation of doubles in a 192-bit two's-complement fixed-point
+// accumulator with 128 fractional bits (three 64-bit limbs).
+//
+// Every finite double x with 2^-128 <= |x| < 2^63 converts exactly (smaller
+// magnitudes round to the nearest multiple of 2^-128, ties to even; larger ones
+// set the overflow flag).  Integer addition is exact and associative, so the
+// sum of a run of values is independent of their order, and fx192_to_double
+// rounds it once, to nearest even.  This is the numerator accumulator of the
+// score (sum_j H_ij c_j): deterministic under any tiling or scheduling, and
+// free of FP64 instructions, which are scarce on this GPU.
+//
+// Host and device compilable (no CUDA intrinsics outside __CUDA_ARCH__).
+#pragma once
+
+#include <stdint.h>
+#include <string.h>
+
+#ifndef __CUDACC__
+#ifndef __host__
+#define __host__
+#endif
+#ifndef __device__
+#define __device__
+#endif
+#ifndef __forceinline__
+#define __forceinline__ inline
+#endif
+#endif
+
+namespace asci {
+
+constexpr int kFxFrac = 128;  // fractional bits of the accumulator
+
+struct Fx192 {
+  uint64_t w0, w1, w2;  // little-endian limbs, two's complement
+};
+
+__host__ __device__ __forceinline__ int fx_clz64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)x);
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+__host__ __device__ __forceinline__ uint64_t fx_dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return (uint64_t)__double_as_longlong(x);
+#else
+  uint64_t b;
+  memcpy(&b, &x, 8);
+  return b;
+#endif
+}
+
+__host__ __device__ __forceinline__ double fx_bits2d(uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  memcpy(&x, &b, 8);
+  return x;
+#endif
+}
+
+__host__ __device__ __forceinline__ void fx_add(Fx192 &a, const Fx192 &b) {
+#ifdef __CUDA_ARCH__
+  asm("add.cc.u64 %0, %0, %3;\n\t"
+      "addc.cc.u64 %1, %1, %4;\n\t"
+      "addc.u64 %2, %2, %5;"
+      : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2)
+      : "l"(b.w0), "l"(b.w1), "l"(b.w2));
+#else
+  uint64_t s0 = a.w0 + b.w0;
+  uint64_t c0 = s0 < a.w0;
+  uint64_t s1 = a.w1 + b.w1;
+  uint64_t c1 = s1 < a.w1;
+  uint64_t s1c = s1 + c0;
+  c1 |= s1c < s1;
+  a.w0 = s0;
+  a.w1 = s1c;
+  a.w2 = a.w2 + b.w2 + c1;
+#endif
+}
+
+__host__ __device__ __forceinline__ void fx_neg(Fx192 &a) {
+  a.w0 = ~a.w0;
+  a.w1 = ~a.w1;
+  a.w2 = ~a.w2;
+  Fx192 one = {1, 0, 0};
+  fx_add(a, one);
+}
+
+// x -> fixed point (round to nearest even below 2^-128); *ovf set when |x| >= 2^63.
+__host__ __device__ __forceinline__ Fx192 fx_from_double(double x, unsigned *ovf) {
+  Fx192 r = {0, 0, 0};
+  const uint64_t b = fx_dbits(x);
+  int eb = (int)((b >> 52) & 0x7ff);
+  uint64_t m = b & ((1ull << 52) - 1);
+  if (eb == 0x7ff) {  // inf or nan
+    *ovf = 1;
+    return r;
+  }
+  if (eb) m |= (1ull << 52); else eb = 1;
+  if (m == 0) return r;
+  // value = m * 2^(eb - 1075); fixed = m * 2^(eb - 1075 + kFxFrac)
+  const int k = eb - 1075 + kFxFrac;
+  if (k >= 0) {
+    if (k >= 191 - 52) {
+      *ovf = 1;
+      return r;
+    }
+    if (k < 64) {
+      r.w0 = m << k;
+      r.w1 = k ? (m >> (64 - k)) : 0;
+    } else if (k < 128) {
+      const int k2 = k - 64;
+      r.w1 = m << k2;
+      r.w2 = k2 ? (m >> (64 - k2)) : 0;
+    } else {
+      r.w2 = m << (k - 128);
+    }
+  } else {
+    const int s = -k;  // right shift with round to nearest even
+    if (s > 54) return r;
+    const uint64_t q = m >> s;
+    const uint64_t rem = m & ((1ull << s) - 1);
+    const uint64_t half = 1ull << (s - 1);
+    r.w0 = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+  }
+  if (b >> 63) fx_neg(r);
+  return r;
+}
+
+// Round the accumulator to the nearest double (ties to even).
+__host__ __device__ __forceinline__ double fx_to_double(Fx192 a) {
+  const bool neg = (a.w2 >> 63) != 0;
+  if (neg) fx_neg(a);
+  if (!(a.w0 | a.w1 | a.w2)) return 0.0;
+  int P;  // index of the highest set bit
+  if (a.w2) P = 128 + 63 - fx_clz64(a.w2);
+  else if (a.w1) P = 64 + 63 - fx_clz64(a.w1);
+  else P = 63 - fx_clz64(a.w0);
+  uint64_t mant;
+  if (P <= 52) {
+    mant = a.w0 << (52 - P);  // exact
+  } else {
+    // mant = bits [P-52, P]; round bit P-53; sticky = bits below (limbs are
+    // selected with conditionals so that nothing is indexed dynamically)
+    const int sh = P - 52;
+    const int limb = sh >> 6, bit = sh & 63;
+    const uint64_t cur = limb == 0 ? a.w0 : (limb == 1 ? a.w1 : a.w2);
+    const uint64_t nxt = limb == 0 ? a.w1 : (limb == 1 ? a.w2 : 0);
+    const uint64_t win = bit ? ((cur >> bit) | (nxt << (64 - bit))) : cur;
+    mant = win & ((1ull << 53) - 1);
+    const int rb = sh - 1;
+    const int rl = rb >> 6, rbb = rb & 63;
+    const uint64_t rw = rl == 0 ? a.w0 : (rl == 1 ? a.w1 : a.w2);
+    const uint64_t rbit = (rw >> rbb) & 1;
+    bool sticky = (rbb ? (rw & ((1ull << rbb) - 1)) : 0) != 0;
+    if (rl >= 1) sticky |= a.w0 != 0;
+    if (rl >= 2) sticky |= a.w1 != 0;
+    if (rbit && (sticky || (mant & 1))) {
+      mant += 1;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        P += 1;
+      }
+    }
+  }
+  // value = mant * 2^(P - 52 - kFxFrac), mant in [2^52, 2^53)
+  const int e = P - kFxFrac;  // unbiased exponent of the result
+  const uint64_t bits = ((uint64_t)(e + 1023) << 52) | (mant & ((1ull << 52) - 1));
+  const double v = fx_bits2d(bits);
+  return neg ? -v : v;
+}
+
+}  // namespace asci

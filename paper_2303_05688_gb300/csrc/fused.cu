@@ -4,16 +4,18 @@
 // Work is partitioned by target alpha string A' (the finest constraint class:
 // all occupied alpha orbitals fixed).  Items sorted by A' (see excite.cu) make
 // each class a contiguous range; a batch of classes is generated into a
-// staging buffer as records (beta', core index j, v = H_ij c_j, H_ii) and then
-// reduced tile by tile on chip:
+// staging buffer as records (beta', v = H_ij c_j, H_ii) and then reduced tile
+// by tile on chip:
 //   small classes (<= kCap/2 pairs)   packed, several per tile, in item order
 //   medium classes (<= kCap pairs)    one tile each, in item order
 //   big classes                       split into hash buckets of beta' (each a
 //                                     tile); all contributions to one target
 //                                     land in the same bucket
-// A tile is sorted in shared memory by a stable LSD radix sort, runs of equal
-// targets are summed, targets in psi are dropped, and targets whose |score|
-// can reach the running top-N threshold are scored exactly and appended.
+// A tile is sorted on beta' in shared memory by a stable LSD radix sort, runs
+// of equal targets are summed exactly (192-bit fixed point, so the sum does
+// not depend on the order of the contributions), targets in psi are dropped,
+// and targets whose |score| can reach the running top-N threshold are scored
+// in FP64 and appended.
 //
 // The diagonal H_ii is carried exactly in 64-bit fixed point: the integral
 // terms are rounded once to multiples of 2^-s, and each pair's H_ii is the
@@ -26,6 +28,7 @@
 #include <vector>
 
 #include "asci_internal.cuh"
+#include "fixed192.cuh"
 #include "fused.cuh"
 
 namespace asci {
@@ -163,13 +166,12 @@ __global__ void k_group_tab(const uint64_t *items, const uint32_t *flag, const u
 
 enum : uint32_t { kTilePacked = 0, kTileMedium = 1, kTileBucket = 2 };
 
-constexpr uint32_t kDropped = 0xffffffffu;  // core index of a screened-out record
-
 // bits of the device error word of the constraint-tile kernels
 constexpr unsigned kErrProbe = 1u;      // exclusion probe ran past the table
-constexpr unsigned kErrTile = 2u;       // a tile holds more records than fit on chip
+constexpr unsigned kErrTile = 2u;       // a tile descriptor outside its limits
 constexpr unsigned kErrStage = 4u;      // a record position outside the staging buffer
 constexpr unsigned kErrCore = 8u;       // a core index outside the core
+constexpr unsigned kErrAccum = 16u;     // a value outside the exact accumulator's range
 
 struct TileDesc {  // 24 bytes; npairs at byte offset 4 (read by the host)
   uint32_t start;   // first record in the batch staging buffer
@@ -182,14 +184,18 @@ struct TileDesc {  // 24 bytes; npairs at byte offset 4 (read by the host)
 
 static_assert(sizeof(TileDesc) == 24, "tile descriptor layout");
 
+// A screened-out record (Alg. 2's eps test) keeps its slot with a NaN value.
+__device__ __forceinline__ bool is_dropped(double v) { return v != v; }
+
 }  // namespace
 
 constexpr int kCellThreads = 512;
-constexpr int kCellItems = 16;
-constexpr int kCap = kCellThreads * kCellItems;  // records per tile
-constexpr uint32_t kSmallMax = kCap / 2;           // packable class size
-constexpr uint32_t kBucketTarget = (kCap * 5) / 10;  // expected records per bucket
-constexpr uint32_t kGroupsPerTile = 2048;
+constexpr int kCellWarps = kCellThreads / 32;
+constexpr int kCellItems = 8;
+constexpr int kCap = kCellThreads * kCellItems;   // records per tile (4096)
+constexpr uint32_t kSmallMax = kCap / 2;            // packable class size
+constexpr uint32_t kBucketTarget = kCap / 2;        // expected records per hash bucket
+constexpr uint32_t kGroupsPerTile = 1024;
 
 namespace {
 
@@ -283,6 +289,10 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t beta, uint32_t nb) {
   return (uint32_t)(((uint64_t)(beta * 0x9E3779B1u) * nb) >> 32);
 }
 
+constexpr int kEmitThreads = 256;
+constexpr int kEmitPer = 4;
+constexpr int kEmitTile = kEmitThreads * kEmitPer;  // pairs per emission CTA
+
 struct EmitArgs {
   DevInts I;
   FxInts X;
@@ -290,6 +300,8 @@ struct EmitArgs {
   FastDiv dv_va, dv_vb, dv_npd0, dv_npd1, dv_pa_p, dv_pb_p;
   const uint64_t *items, *Wexcl;
   const uint32_t *item_group;
+  const uint32_t *tile_item;  // first item of each emission tile (+1 entry)
+  const uint32_t *tile_list;  // count mode: emission tiles overlapping big classes
   uint64_t t0, t1, P0, P1;
   int opbits;
   const uint32_t *grp_alpha, *grp_start, *core_beta;
@@ -300,7 +312,7 @@ struct EmitArgs {
   uint32_t *cnt;              // count mode
   const uint32_t *cell_pos0;  // emit mode
   uint32_t *fill;             // emit mode
-  uint32_t *sb_beta, *sb_j;
+  uint32_t *sb_beta;
   double *sb_val;
   int64_t *sb_haa;
   double eps;                 // Alg. 2 screen; 0 keeps every pair
@@ -312,9 +324,39 @@ struct EmitArgs {
   unsigned *err;
 };
 
-constexpr int kEmitThreads = 256;
-constexpr int kEmitPer = 4;
-constexpr int kEmitTile = kEmitThreads * kEmitPer;
+// First item of each emission tile: the last item whose first pair is at or
+// before the tile's first pair.
+__global__ void k_tile_items(const uint64_t *Wexcl, uint64_t t0, uint64_t t1, uint64_t P0,
+                             uint64_t P1, uint32_t ntiles, uint32_t *tile_item) {
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= ntiles;
+       b += gridDim.x * blockDim.x) {
+    uint64_t p = P0 + (uint64_t)b * kEmitTile;
+    if (p >= P1) p = P1 - 1;
+    uint64_t lo = t0, hi = t1 - 1;
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi + 1) >> 1;
+      if (Wexcl[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    tile_item[b] = (uint32_t)(lo - t0);
+  }
+}
+
+// Emission tiles that hold pairs of big (hash-bucketed) classes.
+__global__ void k_big_tile_flags(uint32_t gb0, uint32_t ng, uint64_t P0, uint64_t Pend,
+                                 const uint64_t *g_P0, const uint32_t *kind, uint32_t *flag) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
+    if (kind[i] != kTileBucket) continue;
+    const uint32_t g = gb0 + i;
+    const uint64_t a = g_P0[g] - P0, e = ((i + 1 < ng) ? g_P0[g + 1] : Pend) - P0;
+    for (uint64_t b = a / kEmitTile; b <= (e - 1) / kEmitTile; ++b) flag[b] = 1u;
+  }
+}
+
+__global__ void k_list_flags(const uint32_t *flag, const uint32_t *pos, uint32_t n,
+                             uint32_t *list) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (flag[i]) list[pos[i]] = i;
+}
 
 __device__ __forceinline__ void dec_single(uint32_t s, uint32_t virt, uint32_t idx,
                                            const FastDiv &dv, int *i, int *a) {
@@ -366,10 +408,9 @@ __device__ __forceinline__ int64_t dd_same(const int64_t *F, const int64_t *jk, 
 template <int MODE>  // 0: count bucket sizes of big classes; 1: emit records
 __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
   extern __shared__ int64_t s_fx[];  // jk[n*n], jj[n*n]
-  __shared__ uint64_t sW[kEmitTile];
-  __shared__ uint64_t sIt[kEmitTile];
-  __shared__ uint32_t sG[kEmitTile];
-  __shared__ uint64_t s_ta, s_nspan;
+  __shared__ uint64_t sW[kEmitTile + 1];
+  __shared__ uint64_t sIt[kEmitTile + 1];
+  __shared__ uint32_t sG[kEmitTile + 1];
   const int n = A.I.n;
   int64_t *s_jk = s_fx, *s_jj = s_fx + n * n;
   if (MODE == 1)
@@ -377,26 +418,13 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
       s_jk[t] = A.X.jk[t];
       s_jj[t] = A.X.jj[t];
     }
-  const uint64_t pb = A.P0 + (uint64_t)blockIdx.x * kEmitTile;
+  const uint32_t tile = MODE == 0 ? A.tile_list[blockIdx.x] : blockIdx.x;
+  const uint64_t pb = A.P0 + (uint64_t)tile * kEmitTile;
   const uint64_t pe = (pb + kEmitTile < A.P1) ? pb + kEmitTile : A.P1;
-  if (threadIdx.x == 0) {
-    uint64_t lo = A.t0, hi = A.t1 - 1;
-    while (lo < hi) {
-      uint64_t mid = (lo + hi + 1) >> 1;
-      if (A.Wexcl[mid] <= pb) lo = mid; else hi = mid - 1;
-    }
-    const uint64_t ta = lo;
-    hi = A.t1 - 1;
-    while (lo < hi) {
-      uint64_t mid = (lo + hi + 1) >> 1;
-      if (A.Wexcl[mid] <= pe - 1) lo = mid; else hi = mid - 1;
-    }
-    s_ta = ta;
-    s_nspan = lo - ta + 1;
-  }
-  __syncthreads();
-  const uint64_t ta = s_ta;
-  const int nspan = (int)s_nspan;
+  const uint64_t ta = A.t0 + A.tile_item[tile];
+  uint64_t tl = A.t0 + A.tile_item[tile + 1];
+  if (tl >= A.t1) tl = A.t1 - 1;
+  const int nspan = (int)(tl - ta + 1);  // <= kEmitTile + 1: every item has >= 1 pair
   for (int i = threadIdx.x; i < nspan; i += kEmitThreads) {
     sIt[i] = A.items[ta + i];
     sW[i] = A.Wexcl[ta + i];
@@ -414,7 +442,6 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
     uint32_t tb = 0, jdx = 0;
     double h = 0.0;
     int64_t dh = 0;
-    uint32_t At = 0;
     bool big = false;
     if (valid) {
       int lo = 0, hi = nspan - 1;
@@ -426,7 +453,6 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
       const uint32_t q = (uint32_t)(p - sW[lo]);
       const uint32_t gi = sG[lo] - A.gb0;
       big = A.kind[gi] == kTileBucket;
-      At = (uint32_t)(it >> 32);
       const uint32_t k = (uint32_t)it >> A.opbits, o = (uint32_t)it & omask;
       const uint32_t Ak = A.grp_alpha[k], va = ~Ak & full;
       if (MODE == 0 && !big) {
@@ -510,23 +536,20 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
           pos = A.cell_pos0[cell] + base + __popc(peers & ((1u << lane) - 1u));
         else
           pos = (uint32_t)(p - A.P0);
-        (void)At;
         if (jdx >= A.ncore) {
           atomicOr(A.err, kErrCore);
           jdx = 0;
         }
-        const double v = h * A.core_c[jdx];
+        double v = h * A.core_c[jdx];
         const int64_t haa = A.Dx[jdx] + dh;
-        uint32_t jj = jdx;
         if (A.eps > 0.0) {
           // |v / (E0 - H_ii)| > eps, without a division
           const double den = __ll2double_rn(A.E0_x - haa) * A.inv_scale;
-          if (!(fabs(v) > A.eps * fabs(den))) jj = kDropped;
+          if (!(fabs(v) > A.eps * fabs(den))) v = __longlong_as_double(0x7ff8000000000000ll);
         }
-        kept = jj != kDropped;
+        kept = !is_dropped(v);
         if (pos < A.stage_cap) {
           A.sb_beta[pos] = tb;
-          A.sb_j[pos] = jj;
           A.sb_val[pos] = v;
           A.sb_haa[pos] = haa;
         } else {
@@ -546,7 +569,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
 struct CellArgs {
   const TileDesc *tiles;
   uint32_t ntiles;
-  const uint32_t *sb_beta, *sb_j;
+  const uint32_t *sb_beta;
   const double *sb_val;
   const int64_t *sb_haa;
   const uint32_t *g_alpha;
@@ -594,15 +617,18 @@ __device__ __forceinline__ bool psi_contains(const uint64_t *ht, uint64_t mask, 
 }
 
 struct CellSmem {
-  uint64_t key[kCap];
-  double val[kCap];
-  uint16_t idx[kCap];
-  uint32_t hist[256 * (kCellThreads / 32)];
+  uint32_t key[kCap];               // beta' of each record, sorted in place
+  uint16_t idx[kCap];               // original position of each sorted record
+  uint16_t grp[kCap];               // local group of each record (original position)
+  double val[kCap];                 // value of each record (original position)
+  uint32_t hist[256 * kCellWarps];  // per-warp digit counts, digit-major
   uint32_t gstart[kGroupsPerTile];
   uint32_t galpha[kGroupsPerTile];
-  uint64_t red[kCellThreads / 32];
+  uint16_t heads[kCap + 1];         // sorted positions where a target's run starts
+  uint32_t wsum[kCellWarps];
+  uint32_t red[kCellWarps];
+  uint32_t nheads;
   uint32_t tile;
-  uint32_t cnt[kCellThreads / 32];
   unsigned long long cbase;
 };
 
@@ -616,67 +642,72 @@ __device__ __forceinline__ uint32_t peers_of(uint32_t d, uint32_t active) {
   return pe;
 }
 
-// Stable LSD radix sort of (key, idx) in shared memory over the digits where
+// Block-wide exclusive scan of one value per thread; *total receives the sum.
+__device__ __forceinline__ uint32_t block_scan(CellSmem &S, uint32_t v, uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) S.wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kCellWarps ? S.wsum[lane] : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    if (lane < kCellWarps) S.wsum[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t pre = (warp ? S.wsum[warp - 1] : 0u) + x - v;
+  *total = S.wsum[kCellWarps - 1];
+  __syncthreads();
+  return pre;
+}
+
+// Stable LSD radix sort of (beta', idx) in shared memory over the digits where
 // the keys differ.  Warp w owns records [w*32*kCellItems, ...) in rounds of 32.
-__device__ void block_sort(CellSmem &S, int nrec, uint64_t vary) {
-  constexpr int W = kCellThreads / 32;
+__device__ void block_sort(CellSmem &S, int nrec, uint32_t vary) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   const int wbeg = warp * 32 * kCellItems;
-  for (int shift = 0; shift < 64; shift += 8) {
-    if (((vary >> shift) & 0xffull) == 0) continue;
-    for (int t = threadIdx.x; t < 256 * W; t += kCellThreads) S.hist[t] = 0;
+  for (int shift = 0; shift < 32; shift += 8) {
+    if (((vary >> shift) & 0xffu) == 0) continue;
+    for (int t = threadIdx.x; t < 256 * kCellWarps; t += kCellThreads) S.hist[t] = 0;
     __syncthreads();
-    uint64_t k[kCellItems];
-    uint16_t ix[kCellItems];
-    uint32_t rk[kCellItems];  // rank in round | count << 8 | leader << 16
+    // per round: key, and one word packing the original index (12 bits), the
+    // rank among equal digits in the round (5), their count (6) and the leader bit
+    uint32_t k[kCellItems], meta[kCellItems];
 #pragma unroll
     for (int r = 0; r < kCellItems; ++r) {
       const int e = wbeg + r * 32 + lane;
       const bool ok = e < nrec;
-      k[r] = ok ? S.key[e] : 0ull;
-      ix[r] = ok ? S.idx[e] : (uint16_t)0;
-      const uint32_t d = (uint32_t)(k[r] >> shift) & 0xffu;
+      k[r] = ok ? S.key[e] : 0u;
+      const uint32_t ix = ok ? S.idx[e] : 0u;
+      const uint32_t d = (k[r] >> shift) & 0xffu;
       const uint32_t active = __ballot_sync(0xffffffffu, ok);
       const uint32_t pe = peers_of(d, active);
       const uint32_t c = __popc(pe);
       const bool lead = ok && lane == __ffs(pe) - 1;
-      rk[r] = __popc(pe & lt) | (c << 8) | ((lead ? 1u : 0u) << 16);
-      if (lead) S.hist[d * W + warp] += c;
+      meta[r] = ix | (__popc(pe & lt) << 12) | (c << 17) | ((lead ? 1u : 0u) << 23);
+      if (lead) S.hist[d * kCellWarps + warp] += c;
       __syncwarp();
     }
     __syncthreads();
-    // exclusive scan of hist in digit-major order (256*W entries)
     {
-      constexpr int PER = (256 * W) / kCellThreads;
-      uint32_t loc[PER];
-      uint32_t sum = 0;
+      constexpr int PER = (256 * kCellWarps) / kCellThreads;
+      uint32_t loc[PER], sum = 0;
 #pragma unroll
       for (int i = 0; i < PER; ++i) {
         loc[i] = S.hist[threadIdx.x * PER + i];
         sum += loc[i];
       }
-      // block exclusive scan of sum
-      uint32_t x = sum;
-#pragma unroll
-      for (int dlt = 1; dlt < 32; dlt <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, dlt);
-        if (lane >= dlt) x += y;
-      }
-      __shared__ uint32_t wsum[kCellThreads / 32];
-      if (lane == 31) wsum[warp] = x;
-      __syncthreads();
-      if (warp == 0) {
-        uint32_t w2 = lane < W ? wsum[lane] : 0u;
-#pragma unroll
-        for (int dlt = 1; dlt < 32; dlt <<= 1) {
-          uint32_t y = __shfl_up_sync(0xffffffffu, w2, dlt);
-          if (lane >= dlt) w2 += y;
-        }
-        if (lane < W) wsum[lane] = w2;
-      }
-      __syncthreads();
-      uint32_t pre = (warp ? wsum[warp - 1] : 0u) + x - sum;
+      uint32_t tot;
+      uint32_t pre = block_scan(S, sum, &tot);
 #pragma unroll
       for (int i = 0; i < PER; ++i) {
         S.hist[threadIdx.x * PER + i] = pre;
@@ -688,50 +719,49 @@ __device__ void block_sort(CellSmem &S, int nrec, uint64_t vary) {
     for (int r = 0; r < kCellItems; ++r) {
       const int e = wbeg + r * 32 + lane;
       const bool ok = e < nrec;
-      const uint32_t d = (uint32_t)(k[r] >> shift) & 0xffu;
+      const uint32_t d = (k[r] >> shift) & 0xffu;
       uint32_t pos = 0;
-      if (ok) pos = S.hist[d * W + warp] + (rk[r] & 0xffu);
+      if (ok) pos = S.hist[d * kCellWarps + warp] + ((meta[r] >> 12) & 31u);
       __syncwarp();
-      if (ok && ((rk[r] >> 16) & 1u)) S.hist[d * W + warp] += (rk[r] >> 8) & 0xffu;
+      if (ok && ((meta[r] >> 23) & 1u)) S.hist[d * kCellWarps + warp] += (meta[r] >> 17) & 63u;
       __syncwarp();
       if (ok) {
         S.key[pos] = k[r];
-        S.idx[pos] = ix[r];
+        S.idx[pos] = (uint16_t)(meta[r] & 0xfffu);
       }
     }
     __syncthreads();
   }
 }
 
-// Result of one unique target: whether it is new (outside psi) and its score.
-struct UniqueOut {
-  bool keep;
-  double score;
-  uint64_t key;
-};
-
-__device__ __forceinline__ uint64_t target_mask(uint32_t kind) {
-  return kind == kTileBucket ? 0xffffffff00000000ull : ~0ull;
-}
-
-__device__ __forceinline__ void unique_target(const CellSmem &S, const TileDesc &d, uint64_t sk,
-                                              uint32_t *a, uint32_t *b) {
-  if (d.kind == kTileBucket) {
-    *a = d.alpha;
-    *b = (uint32_t)(sk >> 32);
-  } else if (d.kind == kTileMedium) {
-    *a = d.alpha;
-    *b = (uint32_t)sk;
-  } else {
-    *a = S.galpha[(uint32_t)(sk >> 32)];
-    *b = (uint32_t)sk;
+// Exact numerator of the run [b, e) of sorted records (screened records are
+// skipped); returns false when every record of the run was screened out.
+__device__ __forceinline__ bool run_numerator(const CellSmem &S, int b, int e, double *num,
+                                              unsigned *err) {
+  if (e - b == 1) {
+    const double v = S.val[S.idx[b]];
+    *num = v;
+    return !is_dropped(v);
   }
+  Fx192 acc = {0, 0, 0};
+  unsigned ovf = 0;
+  int live = 0;
+  for (int i = b; i < e; ++i) {
+    const double v = S.val[S.idx[i]];
+    if (is_dropped(v)) continue;
+    Fx192 x = fx_from_double(v, &ovf);
+    fx_add(acc, x);
+    ++live;
+  }
+  if (ovf) atomicOr(err, kErrAccum);
+  *num = fx_to_double(acc);
+  return live > 0;
 }
 
-__global__ void __launch_bounds__(kCellThreads, 1) k_cells(CellArgs C) {
+__global__ void __launch_bounds__(kCellThreads, 2) k_cells(CellArgs C) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CellSmem &S = *reinterpret_cast<CellSmem *>(smem_raw);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   unsigned long long my_unique = 0, my_excl = 0;
   for (;;) {
     if (threadIdx.x == 0) S.tile = atomicAdd(C.tile_counter, 1u);
@@ -749,70 +779,85 @@ __global__ void __launch_bounds__(kCellThreads, 1) k_cells(CellArgs C) {
       continue;
     }
     const int nrec = (int)d.npairs;
-    if (d.kind == kTilePacked) {
+    const bool packed = d.kind == kTilePacked;
+    if (packed) {
       for (uint32_t i = threadIdx.x; i < d.ng; i += kCellThreads) {
         S.gstart[i] = (uint32_t)(C.g_P0[d.g0 + i] - C.P0) - d.start;
         S.galpha[i] = C.g_alpha[d.g0 + i];
       }
       __syncthreads();
     }
-    // load records and build sort keys
-    uint64_t vary = 0, k0 = 0;
+    // load records; the sort key is beta' alone: records arrive in class
+    // order, so a stable sort keeps each (class, beta') run contiguous
+    uint32_t vary = 0, k0 = nrec > 0 ? C.sb_beta[d.start] : 0u;
     for (int e = threadIdx.x; e < nrec; e += kCellThreads) {
       const uint32_t beta = C.sb_beta[d.start + e];
-      const uint32_t jr = C.sb_j[d.start + e];
-      uint64_t key;
-      if (jr == kDropped) {
-        key = ~0ull;  // screened out: sorts last, never a target
-      } else if (d.kind == kTileBucket) {
-        key = ((uint64_t)beta << 32) | jr;
-      } else if (d.kind == kTileMedium) {
-        key = beta;
-      } else {
+      uint16_t g = 0;
+      if (packed) {
         int lo = 0, hi = (int)d.ng - 1;
         while (lo < hi) {
           int mid = (lo + hi + 1) >> 1;
           if ((int)S.gstart[mid] <= e) lo = mid; else hi = mid - 1;
         }
-        key = ((uint64_t)lo << 32) | beta;
+        g = (uint16_t)lo;
       }
-      S.key[e] = key;
+      S.key[e] = beta;
       S.idx[e] = (uint16_t)e;
+      S.grp[e] = g;
       S.val[e] = C.sb_val[d.start + e];
+      vary |= beta ^ k0;
     }
-    __syncthreads();
-    if (nrec > 0) k0 = S.key[0];
-    for (int e = threadIdx.x; e < nrec; e += kCellThreads) vary |= S.key[e] ^ k0;
     for (int dl = 16; dl; dl >>= 1) vary |= __shfl_xor_sync(0xffffffffu, vary, dl);
-    if (lane == 0) S.red[warp] = vary;
+    if (lane == 0) S.red[threadIdx.x >> 5] = vary;
     __syncthreads();
     vary = 0;
-    for (int w = 0; w < kCellThreads / 32; ++w) vary |= S.red[w];
+    for (int w = 0; w < kCellWarps; ++w) vary |= S.red[w];
     __syncthreads();
     block_sort(S, nrec, vary);
-    // accumulate runs of equal targets (heads owned by the thread of their slot)
-    const uint64_t tm = target_mask(d.kind);
-    const int base = threadIdx.x * kCellItems;
-    uint32_t pass_mask = 0;
-    int npass = 0;
-    for (int r = 0; r < kCellItems; ++r) {
-      const int i = base + r;
-      if (i >= nrec) break;
-      const uint64_t sk = S.key[i];
-      if (sk == ~0ull) break;  // only screened-out records remain
-      if (i > 0 && ((S.key[i - 1] ^ sk) & tm) == 0) continue;
-      double num = 0.0;
-      int e = i;
-      for (; e < nrec && ((S.key[e] ^ sk) & tm) == 0; ++e) num += S.val[S.idx[e]];
-      uint32_t a, b;
-      unique_target(S, d, sk, &a, &b);
-      const uint64_t full = pack_key(a, b);
+    // heads of target runs: (class, beta') changes along the sorted order
+    {
+      const int b0 = threadIdx.x * kCellItems;
+      uint32_t flags = 0, cnt = 0;
+#pragma unroll
+      for (int r = 0; r < kCellItems; ++r) {
+        const int i = b0 + r;
+        if (i < nrec) {
+          const bool h = i == 0 || S.key[i] != S.key[i - 1] ||
+                         (packed && S.grp[S.idx[i]] != S.grp[S.idx[i - 1]]);
+          if (h) {
+            flags |= 1u << r;
+            ++cnt;
+          }
+        }
+      }
+      uint32_t tot;
+      uint32_t pre = block_scan(S, cnt, &tot);
+#pragma unroll
+      for (int r = 0; r < kCellItems; ++r)
+        if ((flags >> r) & 1u) S.heads[pre++] = (uint16_t)(b0 + r);
+      if (threadIdx.x == 0) {
+        S.nheads = tot;
+        S.heads[tot] = (uint16_t)nrec;
+      }
+      __syncthreads();
+    }
+    // one target per thread, strided: exact numerator, exclusion, threshold
+    const int H = (int)S.nheads;
+    uint32_t pass_mask = 0, npass = 0;
+#pragma unroll 1
+    for (int r = 0; r * kCellThreads + (int)threadIdx.x < H; ++r) {
+      const int h = r * kCellThreads + threadIdx.x;
+      const int b = S.heads[h], e = S.heads[h + 1];
+      double num;
+      if (!run_numerator(S, b, e, &num, C.err)) continue;
+      const uint32_t a = packed ? S.galpha[S.grp[S.idx[b]]] : d.alpha;
+      const uint64_t full = pack_key(a, S.key[b]);
       ++my_unique;
       if (psi_contains(C.psi_ht, C.psi_mask, full, C.err)) {
         ++my_excl;
         continue;
       }
-      const int64_t den_x = C.E0_x - C.sb_haa[d.start + S.idx[i]];
+      const int64_t den_x = C.E0_x - C.sb_haa[d.start + S.idx[b]];
       bool pass = true;
       if (C.tau > 0.0) {
         const float nf = fabsf(__double2float_rn(num));
@@ -820,56 +865,38 @@ __global__ void __launch_bounds__(kCellThreads, 1) k_cells(CellArgs C) {
         pass = nf >= C.tau_f * df * 0.99999f;
       }
       if (pass) {
-        const double den = __ll2double_rn(den_x) * C.inv_scale;
-        const double sc = num / den;
-        if (!(fabs(sc) >= C.tau)) pass = false;
+        const double sc = num / (__ll2double_rn(den_x) * C.inv_scale);
+        pass = fabs(sc) >= C.tau;
       }
       if (pass) {
         pass_mask |= 1u << r;
         ++npass;
       }
     }
-    // block-aggregated append of the passing targets
-    {
-      uint32_t x = npass;
-#pragma unroll
-      for (int dl = 1; dl < 32; dl <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, dl);
-        if (lane >= dl) x += y;
+    // block-aggregated append of the targets that reach the threshold
+    uint32_t tot;
+    const uint32_t pre = block_scan(S, npass, &tot);
+    if (threadIdx.x == 0) S.cbase = tot ? atomicAdd(C.cand_count, (unsigned long long)tot) : 0ull;
+    __syncthreads();
+    unsigned long long slot = S.cbase + pre;
+    for (int r = 0; pass_mask; ++r) {
+      if (!((pass_mask >> r) & 1u)) continue;
+      pass_mask &= ~(1u << r);
+      const int h = r * kCellThreads + threadIdx.x;
+      const int b = S.heads[h], e = S.heads[h + 1];
+      double num;
+      run_numerator(S, b, e, &num, C.err);
+      const uint32_t a = packed ? S.galpha[S.grp[S.idx[b]]] : d.alpha;
+      const int64_t den_x = C.E0_x - C.sb_haa[d.start + S.idx[b]];
+      const double sc = num / (__ll2double_rn(den_x) * C.inv_scale);
+      if (slot < C.cand_cap) {
+        C.cand_key[slot] = pack_key(a, S.key[b]);
+        C.cand_score[slot] = sc;
       }
-      if (lane == 31) S.cnt[warp] = x;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        uint32_t tot = 0;
-        for (int w = 0; w < kCellThreads / 32; ++w) {
-          uint32_t c = S.cnt[w];
-          S.cnt[w] = tot;
-          tot += c;
-        }
-        S.cbase = tot ? atomicAdd(C.cand_count, (unsigned long long)tot) : 0ull;
-      }
-      __syncthreads();
-      unsigned long long slot = S.cbase + S.cnt[warp] + (x - npass);
-      for (int r = 0; r < kCellItems && pass_mask; ++r) {
-        if (!((pass_mask >> r) & 1u)) continue;
-        const int i = base + r;
-        const uint64_t sk = S.key[i];
-        double num = 0.0;
-        for (int e = i; e < nrec && ((S.key[e] ^ sk) & tm) == 0; ++e) num += S.val[S.idx[e]];
-        uint32_t a, b;
-        unique_target(S, d, sk, &a, &b);
-        const int64_t den_x = C.E0_x - C.sb_haa[d.start + S.idx[i]];
-        const double sc = num / (__ll2double_rn(den_x) * C.inv_scale);
-        if (slot < C.cand_cap) {
-          C.cand_key[slot] = pack_key(a, b);
-          C.cand_score[slot] = sc;
-        }
-        ++slot;
-      }
+      ++slot;
     }
     __syncthreads();
   }
-  // per-block counters
   for (int dl = 16; dl; dl >>= 1) {
     my_unique += __shfl_xor_sync(0xffffffffu, my_unique, dl);
     my_excl += __shfl_xor_sync(0xffffffffu, my_excl, dl);
@@ -882,13 +909,12 @@ __global__ void __launch_bounds__(kCellThreads, 1) k_cells(CellArgs C) {
 
 // ---------------------------------------------- oversized hash buckets ---
 // A bucket holding more records than one tile is sorted in global memory on
-// (beta', core index) and its runs are reduced one target per thread.
+// beta' and its runs are reduced one target per thread.
 
-__global__ void k_big_keys(const uint32_t *sb_beta, const uint32_t *sb_j, uint32_t start,
-                           uint32_t n, uint64_t *keys, uint32_t *idx) {
+__global__ void k_big_keys(const uint32_t *sb_beta, uint32_t start, uint32_t n, uint64_t *keys,
+                           uint32_t *idx) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t j = sb_j[start + i];
-    keys[i] = (j == kDropped) ? ~0ull : (((uint64_t)sb_beta[start + i] << 32) | j);
+    keys[i] = sb_beta[start + i];
     idx[i] = i;
   }
 }
@@ -898,11 +924,21 @@ __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, uint32_t
   unsigned long long my_unique = 0, my_excl = 0;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint64_t sk = keys[i];
-    if (sk == ~0ull) continue;
-    if (i > 0 && (keys[i - 1] >> 32) == (sk >> 32)) continue;
-    double num = 0.0;
-    for (uint32_t e = i; e < n && (keys[e] >> 32) == (sk >> 32); ++e) num += C.sb_val[start + idx[e]];
-    const uint64_t full = pack_key(alpha, (uint32_t)(sk >> 32));
+    if (i > 0 && keys[i - 1] == sk) continue;
+    Fx192 acc = {0, 0, 0};
+    unsigned ovf = 0;
+    int live = 0;
+    for (uint32_t e = i; e < n && keys[e] == sk; ++e) {
+      const double v = C.sb_val[start + idx[e]];
+      if (is_dropped(v)) continue;
+      Fx192 x = fx_from_double(v, &ovf);
+      fx_add(acc, x);
+      ++live;
+    }
+    if (ovf) atomicOr(C.err, kErrAccum);
+    if (!live) continue;
+    const double num = fx_to_double(acc);
+    const uint64_t full = pack_key(alpha, (uint32_t)sk);
     ++my_unique;
     if (psi_contains(C.psi_ht, C.psi_mask, full, C.err)) {
       ++my_excl;
@@ -964,6 +1000,7 @@ inline unsigned grid_for(size_t n, unsigned cap = 152 * 16) {
 }
 
 }  // namespace
+
 
 // ------------------------------------------------------------ host side ---
 
@@ -1072,10 +1109,10 @@ int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t 
 // its tiles, count the hash buckets of big classes and emit every record into
 // the staging buffer.  The tile table is left in *tiles_out (arena memory).
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
-                uint32_t gb0, uint32_t gb1, uint32_t *sb_beta, uint32_t *sb_j, double *sb_val,
-                int64_t *sb_haa, uint64_t stage_cap, double eps, unsigned long long *survivors,
-                unsigned *err, void **tiles_out, size_t *ntiles_out,
-                std::vector<uint32_t> *oversized, Arena &arena) {
+                uint32_t gb0, uint32_t gb1, uint32_t *sb_beta, double *sb_val, int64_t *sb_haa,
+                uint64_t stage_cap, double eps, unsigned long long *survivors, unsigned *err,
+                void **tiles_out, size_t *ntiles_out, std::vector<uint32_t> *oversized,
+                Arena &arena) {
   cudaStream_t s = arena.stream();
   const uint32_t ng = gb1 - gb0;
   *ntiles_out = 0;
@@ -1111,6 +1148,16 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
     return ASCI_ECUDA;
   }
 
+  // emission tiles and the first item of each
+  const uint64_t etiles64 = (P1 - P0 + kEmitTile - 1) / kEmitTile;
+  if (etiles64 >= (1ull << 31)) return ASCI_EINVAL;
+  const uint32_t etiles = (uint32_t)etiles64;
+  uint32_t *tile_item;
+  ASCI_TRY(arena.alloc(&tile_item, (size_t)etiles + 1));
+  k_tile_items<<<grid_for((size_t)etiles + 1), 256, 0, s>>>(F.Wexcl, t0, t1, P0, P1, etiles,
+                                                            tile_item);
+  ASCI_CHECK_LAUNCH();
+
   uint32_t *cnt, *cnt_scan, *cell_pos0, *fill;
   ASCI_TRY(arena.alloc(&cnt, ncells + 1));
   ASCI_TRY(arena.alloc(&cnt_scan, ncells + 1));
@@ -1132,6 +1179,8 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   A.items = F.items;
   A.Wexcl = F.Wexcl;
   A.item_group = F.item_group;
+  A.tile_item = tile_item;
+  A.tile_list = nullptr;
   A.t0 = t0;
   A.t1 = t1;
   A.P0 = P0;
@@ -1152,7 +1201,6 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   A.cell_pos0 = cell_pos0;
   A.fill = fill;
   A.sb_beta = sb_beta;
-  A.sb_j = sb_j;
   A.sb_val = sb_val;
   A.sb_haa = sb_haa;
   A.eps = eps;
@@ -1162,11 +1210,26 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   A.stage_cap = stage_cap;
   A.ncore = F.ncore;
   A.err = err;
-  const uint64_t etiles = (P1 - P0 + kEmitTile - 1) / kEmitTile;
   const size_t emit_smem = 2 * (size_t)F.X.n * F.X.n * sizeof(int64_t);
   if (ncells) {
-    k_emit2<0><<<(unsigned)etiles, kEmitThreads, 0, s>>>(A);
+    // count the hash buckets, visiting only emission tiles that hold big classes
+    uint32_t *flag, *pos, *list;
+    ASCI_TRY(arena.alloc(&flag, etiles));
+    ASCI_TRY(arena.alloc(&pos, etiles));
+    ASCI_TRY(arena.alloc(&list, etiles));
+    ASCI_TRY_CUDA(cudaMemsetAsync(flag, 0, (size_t)etiles * sizeof(uint32_t), s));
+    k_big_tile_flags<<<grid_for(ng), 256, 0, s>>>(gb0, ng, P0, P1, F.g_P0, kind, flag);
     ASCI_CHECK_LAUNCH();
+    ASCI_TRY(scan_exclusive_u32(flag, pos, etiles, arena));
+    size_t nbig = 0;
+    ASCI_TRY(kept_count(flag, pos, etiles, &nbig, arena));
+    k_list_flags<<<grid_for(etiles), 256, 0, s>>>(flag, pos, etiles, list);
+    ASCI_CHECK_LAUNCH();
+    A.tile_list = list;
+    if (nbig) {
+      k_emit2<0><<<(unsigned)nbig, kEmitThreads, 0, s>>>(A);
+      ASCI_CHECK_LAUNCH();
+    }
   }
   ASCI_TRY(scan_exclusive_u32(cnt, cnt_scan, ncells + 1, arena));
   TileDesc *tiles;
@@ -1183,9 +1246,9 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
                                             n_over, over_list, over_cap);
   ASCI_CHECK_LAUNCH();
   ASCI_TRACE("stage: tiles written");
-  k_emit2<1><<<(unsigned)etiles, kEmitThreads, emit_smem, s>>>(A);
+  k_emit2<1><<<etiles, kEmitThreads, emit_smem, s>>>(A);
   ASCI_CHECK_LAUNCH();
-  ASCI_TRACE("stage: emit launched (%llu blocks)", (unsigned long long)etiles);
+  ASCI_TRACE("stage: emit launched (%u blocks)", etiles);
   unsigned hov = 0;
   ASCI_TRY_CUDA(cudaMemcpyAsync(&hov, n_over, sizeof(hov), cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
@@ -1207,21 +1270,15 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
 
 size_t tile_capacity() { return (size_t)kCap; }
 
-// Reduce tiles [tile_begin, tile_end) of a staged batch on chip and append the
-// targets with |S| >= tau to the candidate buffer (at most kCap per tile).
-int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint32_t tile_end,
-                uint64_t P0, const uint32_t *sb_beta, const uint32_t *sb_j, const double *sb_val,
-                const int64_t *sb_haa, uint64_t stage_cap, double tau, uint64_t *cand_key,
-                double *cand_score, unsigned long long *cand_count, unsigned long long cand_cap,
-                unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *counter,
-                unsigned *err, Arena &arena) {
-  if (tile_end <= tile_begin) return ASCI_OK;
-  cudaStream_t s = arena.stream();
+static CellArgs cell_args(const FusedCore &F, uint64_t P0, const uint32_t *sb_beta,
+                          const double *sb_val, const int64_t *sb_haa, uint64_t stage_cap,
+                          double tau, uint64_t *cand_key, double *cand_score,
+                          unsigned long long *cand_count, unsigned long long cand_cap,
+                          unsigned long long *n_unique, unsigned long long *n_excluded,
+                          unsigned *err) {
   CellArgs CA;
-  CA.tiles = static_cast<const TileDesc *>(tiles);
-  CA.ntiles = tile_end;
+  memset(&CA, 0, sizeof(CA));
   CA.sb_beta = sb_beta;
-  CA.sb_j = sb_j;
   CA.sb_val = sb_val;
   CA.sb_haa = sb_haa;
   CA.g_alpha = F.g_alpha;
@@ -1241,9 +1298,26 @@ int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint
   CA.cand_cap = cand_cap;
   CA.n_unique = n_unique;
   CA.n_excluded = n_excluded;
-  CA.tile_counter = counter;
   CA.stage_cap = stage_cap;
   CA.err = err;
+  return CA;
+}
+
+// Reduce tiles [tile_begin, tile_end) of a staged batch on chip and append the
+// targets with |S| >= tau to the candidate buffer (at most kCap per tile).
+int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint32_t tile_end,
+                uint64_t P0, const uint32_t *sb_beta, const double *sb_val, const int64_t *sb_haa,
+                uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
+                unsigned long long *cand_count, unsigned long long cand_cap,
+                unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *counter,
+                unsigned *err, Arena &arena) {
+  if (tile_end <= tile_begin) return ASCI_OK;
+  cudaStream_t s = arena.stream();
+  CellArgs CA = cell_args(F, P0, sb_beta, sb_val, sb_haa, stage_cap, tau, cand_key, cand_score,
+                          cand_count, cand_cap, n_unique, n_excluded, err);
+  CA.tiles = static_cast<const TileDesc *>(tiles);
+  CA.ntiles = tile_end;
+  CA.tile_counter = counter;
   ASCI_TRY_CUDA(cudaMemcpyAsync(counter, &tile_begin, sizeof(unsigned), cudaMemcpyDefault, s));
   const size_t cell_smem = sizeof(CellSmem);
   static bool attr_set = false;
@@ -1255,7 +1329,7 @@ int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint
   int dev = 0, sms = 152;
   ASCI_TRY_CUDA(cudaGetDevice(&dev));
   ASCI_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned grid = (unsigned)std::min<size_t>((size_t)sms, tile_end - tile_begin);
+  const unsigned grid = (unsigned)std::min<size_t>((size_t)sms * 2, tile_end - tile_begin);
   ASCI_TRACE("cells: launch grid=%u smem=%zu", grid, cell_smem);
   k_cells<<<grid, kCellThreads, cell_smem, s>>>(CA);
   ASCI_CHECK_LAUNCH();
@@ -1266,12 +1340,11 @@ int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint
 // Reduce one oversized bucket tile through the global radix sort.  Appends at
 // most `npairs` candidates.
 int fused_big_tile(const FusedCore &F, const void *tiles, uint32_t tile, uint64_t P0,
-                   const uint32_t *sb_beta, const uint32_t *sb_j, const double *sb_val,
-                   const int64_t *sb_haa, uint64_t stage_cap, double tau, uint64_t *cand_key,
-                   double *cand_score, unsigned long long *cand_count,
-                   unsigned long long cand_cap, unsigned long long *n_unique,
-                   unsigned long long *n_excluded, unsigned *err, uint32_t *npairs_out,
-                   Arena &arena) {
+                   const uint32_t *sb_beta, const double *sb_val, const int64_t *sb_haa,
+                   uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
+                   unsigned long long *cand_count, unsigned long long cand_cap,
+                   unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
+                   uint32_t *npairs_out, Arena &arena) {
   cudaStream_t s = arena.stream();
   TileDesc d;
   ASCI_TRY_CUDA(cudaMemcpyAsync(&d, static_cast<const TileDesc *>(tiles) + tile, sizeof(d),
@@ -1286,26 +1359,11 @@ int fused_big_tile(const FusedCore &F, const void *tiles, uint32_t tile, uint64_
   ASCI_TRY(ta.alloc(&k1, d.npairs));
   ASCI_TRY(ta.alloc(&i0, d.npairs));
   ASCI_TRY(ta.alloc(&i1, d.npairs));
-  k_big_keys<<<grid_for(d.npairs), 256, 0, s>>>(sb_beta, sb_j, d.start, d.npairs, k0, i0);
+  k_big_keys<<<grid_for(d.npairs), 256, 0, s>>>(sb_beta, d.start, d.npairs, k0, i0);
   ASCI_CHECK_LAUNCH();
-  ASCI_TRY(radix_sort_u64_u32(&k0, &k1, &i0, &i1, d.npairs, 0, 64, ta));
-  CellArgs CA;
-  memset(&CA, 0, sizeof(CA));
-  CA.sb_val = sb_val;
-  CA.sb_haa = sb_haa;
-  CA.E0_x = F.E0_x;
-  CA.inv_scale = ldexp(1.0, -F.X.s);
-  CA.tau = tau;
-  CA.psi_ht = F.psi_ht;
-  CA.psi_mask = F.psi_mask;
-  CA.cand_key = cand_key;
-  CA.cand_score = cand_score;
-  CA.cand_count = cand_count;
-  CA.cand_cap = cand_cap;
-  CA.n_unique = n_unique;
-  CA.n_excluded = n_excluded;
-  CA.err = err;
-  (void)P0;
+  ASCI_TRY(radix_sort_u64_u32(&k0, &k1, &i0, &i1, d.npairs, 0, 32, ta));
+  CellArgs CA = cell_args(F, P0, sb_beta, sb_val, sb_haa, stage_cap, tau, cand_key, cand_score,
+                          cand_count, cand_cap, n_unique, n_excluded, err);
   k_big_reduce<<<grid_for(d.npairs), 256, 0, s>>>(k0, i0, d.npairs, d.start, d.alpha, CA);
   ASCI_CHECK_LAUNCH();
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));

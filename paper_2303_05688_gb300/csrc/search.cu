@@ -48,21 +48,20 @@ int item_groups(const uint64_t *items, const uint64_t *Wexcl, uint64_t T, uint32
 int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t *mask,
                    Arena &arena);
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
-                uint32_t gb0, uint32_t gb1, uint32_t *sb_beta, uint32_t *sb_j, double *sb_val,
-                int64_t *sb_haa, uint64_t stage_cap, double eps, unsigned long long *survivors,
-                unsigned *err, void **tiles_out, size_t *ntiles_out,
-                std::vector<uint32_t> *oversized, Arena &arena);
+                uint32_t gb0, uint32_t gb1, uint32_t *sb_beta, double *sb_val, int64_t *sb_haa,
+                uint64_t stage_cap, double eps, unsigned long long *survivors, unsigned *err,
+                void **tiles_out, size_t *ntiles_out, std::vector<uint32_t> *oversized,
+                Arena &arena);
 int fused_big_tile(const FusedCore &F, const void *tiles, uint32_t tile, uint64_t P0,
-                   const uint32_t *sb_beta, const uint32_t *sb_j, const double *sb_val,
-                   const int64_t *sb_haa, uint64_t stage_cap, double tau, uint64_t *cand_key,
-                   double *cand_score, unsigned long long *cand_count,
-                   unsigned long long cand_cap, unsigned long long *n_unique,
-                   unsigned long long *n_excluded, unsigned *err, uint32_t *npairs_out,
-                   Arena &arena);
+                   const uint32_t *sb_beta, const double *sb_val, const int64_t *sb_haa,
+                   uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
+                   unsigned long long *cand_count, unsigned long long cand_cap,
+                   unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
+                   uint32_t *npairs_out, Arena &arena);
 int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint32_t tile_end,
-                uint64_t P0, const uint32_t *sb_beta, const uint32_t *sb_j, const double *sb_val,
-                const int64_t *sb_haa, uint64_t stage_cap, double tau, uint64_t *cand_key,
-                double *cand_score, unsigned long long *cand_count, unsigned long long cand_cap,
+                uint64_t P0, const uint32_t *sb_beta, const double *sb_val, const int64_t *sb_haa,
+                uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
+                unsigned long long *cand_count, unsigned long long cand_cap,
                 unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *counter,
                 unsigned *err, Arena &arena);
 size_t tile_capacity();
@@ -577,7 +576,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     if (bmax == 0) {
       size_t fr = 0, tot = 0;
       ASCI_TRY_CUDA(cudaMemGetInfo(&fr, &tot));
-      bmax = (uint64_t)(fr / 2) / 32;  // staging record: 24 bytes
+      bmax = (uint64_t)(fr / 2) / 28;  // staging record: 20 bytes
       bmax = std::max<uint64_t>(bmax, 1ull << 20);
       bmax = std::min<uint64_t>(bmax, 1ull << 31);
     }
@@ -658,7 +657,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   const size_t cap_extra =
       std::max<size_t>(tile_capacity() * (size_t)sms * 16, std::min<uint64_t>(bcap, 1ull << 28));
   const size_t pool_cap = N + cap_extra;
-  uint32_t *sb_beta = nullptr, *sb_j = nullptr;
+  uint32_t *sb_beta = nullptr;
   double *sb_val = nullptr;
   int64_t *sb_haa = nullptr;
   uint64_t *pool_k[2] = {nullptr, nullptr};
@@ -667,7 +666,6 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   unsigned *tile_counter = nullptr, *derr2 = nullptr;
   if (bcap) {
     ASCI_TRY(arena.alloc(&sb_beta, bcap));
-    ASCI_TRY(arena.alloc(&sb_j, bcap));
     ASCI_TRY(arena.alloc(&sb_val, bcap));
     ASCI_TRY(arena.alloc(&sb_haa, bcap));
     for (int i = 0; i < 2; ++i) {
@@ -714,7 +712,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
                (unsigned long long)b.t0, (unsigned long long)b.t1, (unsigned long long)b.P0,
                (unsigned long long)b.P1, gg[0], gg[1] + 1);
     std::vector<uint32_t> oversized;
-    ASCI_TRY(fused_stage(F, b.t0, b.t1, b.P0, b.P1, gg[0], gg[1] + 1, sb_beta, sb_j, sb_val, sb_haa,
+    ASCI_TRY(fused_stage(F, b.t0, b.t1, b.P0, b.P1, gg[0], gg[1] + 1, sb_beta, sb_val, sb_haa,
                          bcap, o.eps_search, dcount + 3, derr2, &tiles, &ntiles, &oversized, ba));
     ASCI_TRACE("staged: tiles=%zu oversized=%zu", ntiles, oversized.size());
     tm.stop(&tl[2]);
@@ -734,7 +732,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
       }
       const size_t t1 = std::min(ntiles, t + room);
       ASCI_TRACE("cells: tiles [%zu,%zu) tau=%.6g pool=%zu", t, t1, tau, pool_n);
-      ASCI_TRY(fused_cells(F, tiles, (uint32_t)t, (uint32_t)t1, b.P0, sb_beta, sb_j, sb_val, sb_haa,
+      ASCI_TRY(fused_cells(F, tiles, (uint32_t)t, (uint32_t)t1, b.P0, sb_beta, sb_val, sb_haa,
                            bcap, tau, pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1,
                            dcount + 2, tile_counter, derr2, ba));
       unsigned long long c = 0;
@@ -775,7 +773,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
         tm.start();
         if (pool_cap - pool_n < np) return ASCI_ENOMEM;
       }
-      ASCI_TRY(fused_big_tile(F, tiles, ot, b.P0, sb_beta, sb_j, sb_val, sb_haa, bcap, tau,
+      ASCI_TRY(fused_big_tile(F, tiles, ot, b.P0, sb_beta, sb_val, sb_haa, bcap, tau,
                               pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1, dcount + 2,
                               derr2, &np, ba));
       ASCI_TRY_CUDA(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDefault, stream));

@@ -1,0 +1,28 @@
+// Host harness for the GPU path's exact accumulator (fixed192.cuh):
+// reads groups of doubles (count, then values as hex bit patterns) from stdin
+// and prints the rounded exact sum of each group as a hex bit pattern.
+#include <cstdio>
+#include <cstdint>
+#include <cstring>
+#include "../paper_2303_05688_gb300/csrc/fixed192.cuh"
+
+int main() {
+  unsigned long long cnt;
+  while (scanf("%llu", &cnt) == 1) {
+    asci::Fx192 acc = {0, 0, 0};
+    unsigned ovf = 0;
+    for (unsigned long long i = 0; i < cnt; ++i) {
+      unsigned long long b;
+      if (scanf("%llx", &b) != 1) return 1;
+      double x;
+      memcpy(&x, &b, 8);
+      asci::Fx192 v = asci::fx_from_double(x, &ovf);
+      asci::fx_add(acc, v);
+    }
+    double s = asci::fx_to_double(acc);
+    uint64_t sb;
+    memcpy(&sb, &s, 8);
+    printf("%llx %u\n", (unsigned long long)sb, ovf);
+  }
+  return 0;
+}

@@ -1,0 +1,81 @@
+"""The GPU path's exact numerator accumulator (fixed192.cuh), compiled for the
+host, against exact rational arithmetic (CPU)."""
+import os
+import random
+import struct
+import subprocess
+from fractions import Fraction
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    exe = tmp_path_factory.mktemp("fx") / "fx192"
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-o", str(exe),
+                           os.path.join(HERE, "fixed192_harness.cpp")])
+    return str(exe)
+
+
+def _bits(x):
+    return struct.unpack("<Q", struct.pack("<d", x))[0]
+
+
+def _dbl(b):
+    return struct.unpack("<d", struct.pack("<Q", b))[0]
+
+
+def _exact_rounded(vals):
+    """Round each value to a multiple of 2^-128 (ties to even), sum exactly, round to double."""
+    q = Fraction(1, 2 ** 128)
+    tot = Fraction(0)
+    for v in vals:
+        f = Fraction(v) / q
+        n = round(f)  # Python rounds half to even
+        tot += n * q
+    return float(tot)  # correctly rounded (ties to even)
+
+
+def _run(exe, groups):
+    inp = "".join(f"{len(g)} " + " ".join(f"{_bits(x):x}" for x in g) + "\n" for g in groups)
+    out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    res = []
+    for line in out:
+        if line.strip():
+            h, o = line.split()
+            res.append((_dbl(int(h, 16)), int(o)))
+    return res
+
+
+def test_exact_sum_matches_rationals(harness):
+    rng = random.Random(7)
+    groups = []
+    for _ in range(400):
+        k = rng.choice([1, 2, 3, 7, 30, 200])
+        scale = 10.0 ** rng.uniform(-30, 2)
+        g = [rng.choice([-1, 1]) * rng.random() * scale * 10.0 ** rng.uniform(-8, 0) for _ in range(k)]
+        groups.append(g)
+    # cancellation, tiny tails, exact ties and signed zeros
+    groups += [[1.0, -1.0], [1e-300, 1.0, -1.0], [2.0 ** 60, 1.0, -(2.0 ** 60)],
+               [0.1, 0.2, -0.3], [-0.0], [0.0, -0.0], [3.0 * 2.0 ** -130], [2.0 ** -129],
+               [1.5 * 2.0 ** -128], [2.5 * 2.0 ** -128], [1e-40, -1e-40, 1e-200]]
+    res = _run(harness, groups)
+    for g, (got, ovf) in zip(groups, res):
+        assert ovf == 0
+        want = _exact_rounded(g)
+        assert got == want or (got == 0.0 and want == 0.0), (g[:4], got, want)
+
+
+def test_order_independent(harness):
+    rng = random.Random(3)
+    g = [rng.uniform(-1, 1) * 10.0 ** rng.uniform(-15, 1) for _ in range(1000)]
+    perms = [g, list(reversed(g)), sorted(g), sorted(g, key=abs)]
+    res = _run(harness, perms)
+    assert len({r[0] for r in res}) == 1
+
+
+def test_overflow_flagged(harness):
+    res = _run(harness, [[2.0 ** 63], [float("inf")], [2.0 ** 62]])
+    assert res[0][1] == 1 and res[1][1] == 1 and res[2][1] == 0
