@@ -1,13 +1,18 @@
 // Exact summation of doubles in a 192-bit two's-complement fixed-point
-// accumulator with 128 fractional bits (three 64-bit limbs).
+// accumulator (three 64-bit limbs) whose grid is anchored to the run's largest
+// exponent.
 //
-// Every finite double x with 2^-128 <= |x| < 2^63 converts exactly (smaller
-// magnitudes round to the nearest multiple of 2^-128, ties to even; larger ones
-// set the overflow flag).  Integer addition is exact and associative, so the
-// sum of a run of values is independent of their order, and fx192_to_double
-// rounds it once, to nearest even.  This is the numerator accumulator of the
-// score (sum_j H_ij c_j): deterministic under any tiling or scheduling, and
-// free of FP64 instructions, which are scarce on this GPU.
+// For a run whose largest value has biased exponent emax, values are held as
+// multiples of 2^-frac with frac = fx_frac_for(emax): the largest value's
+// leading bit sits at bit 166, which leaves 24 bits of headroom (up to 2^24
+// values sum without overflow).  Every value within 2^-113 of the largest is
+// converted exactly; smaller ones round to the grid (ties to even), an error
+// of at most 2^-167 relative to the largest value.  Integer addition is exact
+// and associative, and emax does not depend on the order, so the sum of a run
+// is independent of the order of its values; fx_to_double rounds it once, to
+// nearest even.  This is the numerator accumulator of the score
+// (sum_j H_ij c_j): deterministic under any tiling or scheduling, and free of
+// FP64 instructions, which are scarce on this GPU.
 //
 // Host and device compilable (no CUDA intrinsics outside __CUDA_ARCH__).
 #pragma once
@@ -29,7 +34,13 @@
 
 namespace asci {
 
-constexpr int kFxFrac = 128;  // fractional bits of the accumulator
+constexpr int kFxLead = 166;  // bit of the largest value's leading one
+
+// Biased exponent of x (subnormals and zero count as 1).
+__host__ __device__ __forceinline__ int fx_exponent(double x);
+
+// Fractional bits of the grid for a run whose largest biased exponent is emax.
+__host__ __device__ __forceinline__ int fx_frac_for(int emax) { return kFxLead - 52 + 1075 - emax; }
 
 struct Fx192 {
   uint64_t w0, w1, w2;  // little-endian limbs, two's complement
@@ -91,8 +102,14 @@ __host__ __device__ __forceinline__ void fx_neg(Fx192 &a) {
   fx_add(a, one);
 }
 
-// x -> fixed point (round to nearest even below 2^-128); *ovf set when |x| >= 2^63.
-__host__ __device__ __forceinline__ Fx192 fx_from_double(double x, unsigned *ovf) {
+__host__ __device__ __forceinline__ int fx_exponent(double x) {
+  const int eb = (int)((fx_dbits(x) >> 52) & 0x7ff);
+  return eb ? eb : 1;
+}
+
+// x -> multiple of 2^-frac (round to nearest even); *ovf set when x is not
+// finite or does not fit below bit 190.
+__host__ __device__ __forceinline__ Fx192 fx_from_double(double x, int frac, unsigned *ovf) {
   Fx192 r = {0, 0, 0};
   const uint64_t b = fx_dbits(x);
   int eb = (int)((b >> 52) & 0x7ff);
@@ -103,8 +120,8 @@ __host__ __device__ __forceinline__ Fx192 fx_from_double(double x, unsigned *ovf
   }
   if (eb) m |= (1ull << 52); else eb = 1;
   if (m == 0) return r;
-  // value = m * 2^(eb - 1075); fixed = m * 2^(eb - 1075 + kFxFrac)
-  const int k = eb - 1075 + kFxFrac;
+  // value = m * 2^(eb - 1075); fixed = m * 2^(eb - 1075 + frac)
+  const int k = eb - 1075 + frac;
   if (k >= 0) {
     if (k >= 191 - 52) {
       *ovf = 1;
@@ -132,8 +149,8 @@ __host__ __device__ __forceinline__ Fx192 fx_from_double(double x, unsigned *ovf
   return r;
 }
 
-// Round the accumulator to the nearest double (ties to even).
-__host__ __device__ __forceinline__ double fx_to_double(Fx192 a) {
+// Round a * 2^-frac to the nearest double (ties to even).
+__host__ __device__ __forceinline__ double fx_to_double(Fx192 a, int frac) {
   const bool neg = (a.w2 >> 63) != 0;
   if (neg) fx_neg(a);
   if (!(a.w0 | a.w1 | a.w2)) return 0.0;
@@ -168,10 +185,18 @@ __host__ __device__ __forceinline__ double fx_to_double(Fx192 a) {
       }
     }
   }
-  // value = mant * 2^(P - 52 - kFxFrac), mant in [2^52, 2^53)
-  const int e = P - kFxFrac;  // unbiased exponent of the result
-  const uint64_t bits = ((uint64_t)(e + 1023) << 52) | (mant & ((1ull << 52) - 1));
-  const double v = fx_bits2d(bits);
+  // value = mant * 2^(P - 52 - frac), mant in [2^52, 2^53)
+  const int e = P - frac;  // unbiased exponent of the result
+  double v;
+  if (e + 1023 >= 1 && e + 1023 <= 2046) {
+    v = fx_bits2d(((uint64_t)(e + 1023) << 52) | (mant & ((1ull << 52) - 1)));
+  } else {
+    // outside the normal range (a run cancelling far below 1e-300): scale in steps
+    v = (double)mant;
+    int sh = e - 52;
+    while (sh > 0) { const int t = sh > 1000 ? 1000 : sh; v *= fx_bits2d((uint64_t)(t + 1023) << 52); sh -= t; }
+    while (sh < 0) { const int t = sh < -1000 ? -1000 : sh; v *= fx_bits2d((uint64_t)(t + 1023) << 52); sh -= t; }
+  }
   return neg ? -v : v;
 }
 

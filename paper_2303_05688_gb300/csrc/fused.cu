@@ -743,18 +743,26 @@ __device__ __forceinline__ bool run_numerator(const CellSmem &S, int b, int e, d
     *num = v;
     return !is_dropped(v);
   }
-  Fx192 acc = {0, 0, 0};
-  unsigned ovf = 0;
-  int live = 0;
+  // grid anchored to the largest exponent of the run (order independent)
+  int emax = 1, live = 0;
   for (int i = b; i < e; ++i) {
     const double v = S.val[S.idx[i]];
     if (is_dropped(v)) continue;
-    Fx192 x = fx_from_double(v, &ovf);
-    fx_add(acc, x);
+    const int ex = fx_exponent(v);
+    emax = ex > emax ? ex : emax;
     ++live;
   }
+  const int frac = fx_frac_for(emax);
+  Fx192 acc = {0, 0, 0};
+  unsigned ovf = 0;
+  for (int i = b; i < e; ++i) {
+    const double v = S.val[S.idx[i]];
+    if (is_dropped(v)) continue;
+    Fx192 x = fx_from_double(v, frac, &ovf);
+    fx_add(acc, x);
+  }
   if (ovf) atomicOr(err, kErrAccum);
-  *num = fx_to_double(acc);
+  *num = fx_to_double(acc, frac);
   return live > 0;
 }
 
@@ -925,19 +933,26 @@ __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, uint32_t
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint64_t sk = keys[i];
     if (i > 0 && keys[i - 1] == sk) continue;
-    Fx192 acc = {0, 0, 0};
-    unsigned ovf = 0;
-    int live = 0;
+    int emax = 1, live = 0;
     for (uint32_t e = i; e < n && keys[e] == sk; ++e) {
       const double v = C.sb_val[start + idx[e]];
       if (is_dropped(v)) continue;
-      Fx192 x = fx_from_double(v, &ovf);
-      fx_add(acc, x);
+      const int ex = fx_exponent(v);
+      emax = ex > emax ? ex : emax;
       ++live;
+    }
+    const int frac = fx_frac_for(emax);
+    Fx192 acc = {0, 0, 0};
+    unsigned ovf = 0;
+    for (uint32_t e = i; e < n && keys[e] == sk; ++e) {
+      const double v = C.sb_val[start + idx[e]];
+      if (is_dropped(v)) continue;
+      Fx192 x = fx_from_double(v, frac, &ovf);
+      fx_add(acc, x);
     }
     if (ovf) atomicOr(C.err, kErrAccum);
     if (!live) continue;
-    const double num = fx_to_double(acc);
+    const double num = fx_to_double(acc, frac);
     const uint64_t full = pack_key(alpha, (uint32_t)sk);
     ++my_unique;
     if (psi_contains(C.psi_ht, C.psi_mask, full, C.err)) {

@@ -1,6 +1,7 @@
 // Host harness for the GPU path's exact accumulator (fixed192.cuh):
 // reads groups of doubles (count, then values as hex bit patterns) from stdin
-// and prints the rounded exact sum of each group as a hex bit pattern.
+// and prints the rounded sum of each group (grid anchored to the group's
+// largest exponent, as on the device) as a hex bit pattern.
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
@@ -9,17 +10,24 @@
 int main() {
   unsigned long long cnt;
   while (scanf("%llu", &cnt) == 1) {
-    asci::Fx192 acc = {0, 0, 0};
-    unsigned ovf = 0;
+    double xs[4096];
+    if (cnt > 4096) return 1;
+    int emax = 1;
     for (unsigned long long i = 0; i < cnt; ++i) {
       unsigned long long b;
       if (scanf("%llx", &b) != 1) return 1;
-      double x;
-      memcpy(&x, &b, 8);
-      asci::Fx192 v = asci::fx_from_double(x, &ovf);
+      memcpy(&xs[i], &b, 8);
+      const int e = asci::fx_exponent(xs[i]);
+      emax = e > emax ? e : emax;
+    }
+    const int frac = asci::fx_frac_for(emax);
+    asci::Fx192 acc = {0, 0, 0};
+    unsigned ovf = 0;
+    for (unsigned long long i = 0; i < cnt; ++i) {
+      asci::Fx192 v = asci::fx_from_double(xs[i], frac, &ovf);
       asci::fx_add(acc, v);
     }
-    double s = asci::fx_to_double(acc);
+    double s = asci::fx_to_double(acc, frac);
     uint64_t sb;
     memcpy(&sb, &s, 8);
     printf("%llx %u\n", (unsigned long long)sb, ovf);

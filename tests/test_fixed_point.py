@@ -28,8 +28,17 @@ def _dbl(b):
 
 
 def _exact_rounded(vals):
-    """Round each value to a multiple of 2^-128 (ties to even), sum exactly, round to double."""
-    q = Fraction(1, 2 ** 128)
+    """Round each value to the run's grid, sum exactly, round to double.
+
+    The grid is 2^(e - 166) where 2^e <= max|x| < 2^(e+1) (e of the run's largest
+    normal exponent; subnormals and zeros count as 2^-1022).
+    """
+    import math
+    e = -1022
+    for v in vals:
+        if v != 0.0:
+            e = max(e, math.frexp(abs(v))[1] - 1)
+    q = Fraction(2) ** (e - 166)
     tot = Fraction(0)
     for v in vals:
         f = Fraction(v) / q
@@ -60,7 +69,9 @@ def test_exact_sum_matches_rationals(harness):
     # cancellation, tiny tails, exact ties and signed zeros
     groups += [[1.0, -1.0], [1e-300, 1.0, -1.0], [2.0 ** 60, 1.0, -(2.0 ** 60)],
                [0.1, 0.2, -0.3], [-0.0], [0.0, -0.0], [3.0 * 2.0 ** -130], [2.0 ** -129],
-               [1.5 * 2.0 ** -128], [2.5 * 2.0 ** -128], [1e-40, -1e-40, 1e-200]]
+               [1e-40, -1e-40, 1e-200], [1e-36, -0.9e-36, 3e-52],
+               [1.0, 1.5 * 2.0 ** -167], [1.0, 2.5 * 2.0 ** -167], [1.0, 2.0 ** -200],
+               [1e-310, 2e-310, -1e-311], [1e300, -1e300, 1e200]]
     res = _run(harness, groups)
     for g, (got, ovf) in zip(groups, res):
         assert ovf == 0
@@ -77,5 +88,6 @@ def test_order_independent(harness):
 
 
 def test_overflow_flagged(harness):
-    res = _run(harness, [[2.0 ** 63], [float("inf")], [2.0 ** 62]])
-    assert res[0][1] == 1 and res[1][1] == 1 and res[2][1] == 0
+    res = _run(harness, [[float("inf")], [2.0 ** 1000, 2.0 ** 1000], [1e308, 1e308]])
+    assert res[0][1] == 1 and res[1][1] == 0 and res[2][1] == 0
+    assert res[1][0] == 2.0 ** 1001
