@@ -176,6 +176,32 @@ int asci_sort_accumulate(const asci_det *keys, const double *values, size_t n,
                          void *cuda_stream);
 
 /*
+ * Sort-and-accumulate that allocates nothing.  The paper has no counterpart;
+ * this serves callers that cannot allocate device memory during the call: a
+ * process whose device memory is already reserved by another allocator or
+ * capped, or an embedder (a latency-bound or certified code path) whose policy
+ * forbids allocation behind its back.
+ *
+ * Same results as asci_sort_accumulate for n <= ASCI_NOALLOC_MAX_PAIRS
+ * (ASCI_EINVAL above that, with a message in asci_last_error()).  Every scratch
+ * buffer is carved from one fixed device array inside the library, which each
+ * GPU that loads the library holds (about 104 bytes per pair of the maximum
+ * plus 2 MiB, ~7 MB) until the process exits.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array, so calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller; the call itself returns after its results are in
+ * the output buffers.  Inputs and outputs may be host or device memory.
+ */
+#define ASCI_NOALLOC_MAX_PAIRS 65536
+int asci_sort_accumulate_noalloc(const asci_det *keys, const double *values, size_t n,
+                                 asci_det *out_keys, double *out_sums, size_t *out_n,
+                                 void *cuda_stream);
+
+/*
  * Top-N selection by |score| (Sec. 2.2, the duplicate-aware selection that
  * replaces a full sort): returns the min(N, n) entries of largest |score|,
  * breaking ties at the cutoff by key ascending.  Keys must be distinct.

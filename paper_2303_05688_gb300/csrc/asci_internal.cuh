@@ -63,6 +63,10 @@ class Arena {
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess && device_pool(dev, &pool_) != ASCI_OK) pool_ = nullptr;
   }
+  // Bump mode: every allocation is carved, 256-byte aligned, from the given
+  // device region; nothing is allocated or freed.  Exhaustion returns ASCI_ENOMEM.
+  Arena(cudaStream_t s, void *region, size_t bytes)
+      : stream_(s), bump_base_(static_cast<char *>(region)), bump_cap_(bytes) {}
   ~Arena() { release(); }
   Arena(const Arena &) = delete;
   Arena &operator=(const Arena &) = delete;
@@ -71,6 +75,17 @@ class Arena {
     void *q = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 256;
+    if (bump_base_) {
+      const size_t off = (bump_off_ + 255) & ~(size_t)255;
+      if (off > bump_cap_ || bytes > bump_cap_ - off) {
+        record_error("fixed scratch region exhausted", __FILE__, __LINE__);
+        *p = nullptr;
+        return ASCI_ENOMEM;
+      }
+      bump_off_ = off + bytes;
+      *p = reinterpret_cast<T *>(bump_base_ + off);
+      return ASCI_OK;
+    }
     cudaError_t e = pool_ ? cudaMallocFromPoolAsync(&q, bytes, pool_, stream_)
                           : cudaMallocAsync(&q, bytes, stream_);
     if (e != cudaSuccess) {
@@ -86,6 +101,7 @@ class Arena {
   void release() {
     for (void *q : ptrs_) cudaFreeAsync(q, stream_);
     ptrs_.clear();
+    bump_off_ = 0;
   }
   cudaStream_t stream() const { return stream_; }
 
@@ -93,6 +109,8 @@ class Arena {
   cudaStream_t stream_;
   cudaMemPool_t pool_ = nullptr;
   std::vector<void *> ptrs_;
+  char *bump_base_ = nullptr;
+  size_t bump_cap_ = 0, bump_off_ = 0;
 };
 
 // ---------------------------------------------------------------------------
