@@ -11,11 +11,12 @@
 //   big classes                       split into hash buckets of beta' (each a
 //                                     tile); all contributions to one target
 //                                     land in the same bucket
-// A tile is sorted on beta' in shared memory by a stable LSD radix sort, runs
-// of equal targets are summed exactly (192-bit fixed point, so the sum does
-// not depend on the order of the contributions), targets in psi are dropped,
-// and targets whose |score| can reach the running top-N threshold are scored
-// in FP64 and appended.
+// A tile groups its records by target in a shared-memory hash table (the
+// records of each target linked into a list), sums each target's values
+// exactly (192-bit fixed point, so the sum does not depend on the order of the
+// contributions and equals the sort-and-accumulate result bit for bit), drops
+// targets in psi, and scores in FP64 and appends the targets whose |score| can
+// reach the running top-N threshold.
 //
 // The diagonal H_ii is carried exactly in 64-bit fixed point: the integral
 // terms are rounded once to multiples of 2^-s, and each pair's H_ii is the
@@ -191,8 +192,8 @@ __device__ __forceinline__ bool is_dropped(double v) { return v != v; }
 
 constexpr int kCellThreads = 512;
 constexpr int kCellWarps = kCellThreads / 32;
-constexpr int kCellItems = 8;
-constexpr int kCap = kCellThreads * kCellItems;   // records per tile (4096)
+constexpr int kCap = 2048;                          // records per tile
+constexpr int kSlots = 2 * kCap;                    // hash slots per tile (load <= 1/2)
 constexpr uint32_t kSmallMax = kCap / 2;            // packable class size
 constexpr uint32_t kBucketTarget = kCap / 2;        // expected records per hash bucket
 constexpr uint32_t kGroupsPerTile = 1024;
@@ -411,6 +412,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
   __shared__ uint64_t sW[kEmitTile + 1];
   __shared__ uint64_t sIt[kEmitTile + 1];
   __shared__ uint32_t sG[kEmitTile + 1];
+  __shared__ uint32_t sOp[kEmitTile + 1];  // decoded alpha operation of each item
   const int n = A.I.n;
   int64_t *s_jk = s_fx, *s_jj = s_fx + n * n;
   if (MODE == 1)
@@ -425,14 +427,31 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
   uint64_t tl = A.t0 + A.tile_item[tile + 1];
   if (tl >= A.t1) tl = A.t1 - 1;
   const int nspan = (int)(tl - ta + 1);  // <= kEmitTile + 1: every item has >= 1 pair
-  for (int i = threadIdx.x; i < nspan; i += kEmitThreads) {
-    sIt[i] = A.items[ta + i];
-    sW[i] = A.Wexcl[ta + i];
-    sG[i] = A.item_group[ta + i];
-  }
-  __syncthreads();
   const uint32_t full = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
   const uint32_t omask = (1u << A.opbits) - 1u;
+  for (int i = threadIdx.x; i < nspan; i += kEmitThreads) {
+    const uint64_t it = A.items[ta + i];
+    sIt[i] = it;
+    sW[i] = A.Wexcl[ta + i];
+    sG[i] = A.item_group[ta + i];
+    // alpha operation of the item, decoded once: orbitals (5 bits each) and parity
+    const uint32_t k = (uint32_t)it >> A.opbits, o = (uint32_t)it & omask;
+    uint32_t op = 0;
+    if (MODE == 1 && o != 0) {
+      const uint32_t Ak = A.grp_alpha[k], va = ~Ak & full;
+      int ia, aa, ja, ba;
+      if (o <= A.E.sa) {
+        dec_single(Ak, va, o - 1, A.dv_va, &ia, &aa);
+        op = (uint32_t)ia | ((uint32_t)aa << 5) | ((uint32_t)single_parity(Ak, ia, aa) << 20);
+      } else {
+        dec_double(Ak, va, o - 1 - A.E.sa, A.dv_pa_p, &ia, &ja, &aa, &ba);
+        op = (uint32_t)ia | ((uint32_t)aa << 5) | ((uint32_t)ja << 10) | ((uint32_t)ba << 15) |
+             ((uint32_t)par_double(Ak, ia, ja, aa, ba) << 20);
+      }
+    }
+    sOp[i] = op;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int r = 0; r < kEmitPer; ++r) {
@@ -443,18 +462,34 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
     double h = 0.0;
     int64_t dh = 0;
     bool big = false;
+    // item of pair p: lane 0 searches the whole span, the other lanes only
+    // the next 32 items (consecutive lanes hold consecutive pairs)
+    int lo0 = 0;
+    {
+      const uint64_t p0 = pb + (uint64_t)r * kEmitThreads + (threadIdx.x & ~31u);
+      if (lane == 0) {
+        int lo = 0, hi = nspan - 1;
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (sW[mid] <= p0) lo = mid; else hi = mid - 1;
+        }
+        lo0 = lo;
+      }
+      lo0 = __shfl_sync(0xffffffffu, lo0, 0);
+    }
     if (valid) {
-      int lo = 0, hi = nspan - 1;
+      int lo = lo0, hi = (lo0 + 32 < nspan - 1) ? lo0 + 32 : nspan - 1;
       while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (sW[mid] <= p) lo = mid; else hi = mid - 1;
       }
       const uint64_t it = sIt[lo];
+      const uint32_t aop = sOp[lo];
       const uint32_t q = (uint32_t)(p - sW[lo]);
       const uint32_t gi = sG[lo] - A.gb0;
       big = A.kind[gi] == kTileBucket;
       const uint32_t k = (uint32_t)it >> A.opbits, o = (uint32_t)it & omask;
-      const uint32_t Ak = A.grp_alpha[k], va = ~Ak & full;
+      const uint32_t Ak = A.grp_alpha[k];
       if (MODE == 0 && !big) {
         // nothing to count
       } else if (o == 0) {
@@ -484,13 +519,17 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
         const uint32_t m = A.dv_npd1.div(q), e = q - m * A.dv_npd1.d;
         jdx = A.grp_start[k] + m;
         const uint32_t B = A.core_beta[jdx];
-        int i, a;
-        dec_single(Ak, va, o - 1, A.dv_va, &i, &a);
+        int i = 0, a = 0;
+        if (MODE == 1) {
+          i = (int)(aop & 31u);
+          a = (int)((aop >> 5) & 31u);
+        }
+        const int pa = (int)((aop >> 20) & 1u);
         if (e == 0) {
           tb = B;
           if (MODE == 1) {
             const double v = single_val(A.I, Ak, B, i, a);
-            h = single_parity(Ak, i, a) ? -v : v;
+            h = pa ? -v : v;
             const int64_t *F = A.Fa + (size_t)jdx * n;
             dh = F[a] - F[i] - s_jk[a * n + i];
           }
@@ -501,7 +540,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
           tb = B ^ (1u << j2) ^ (1u << b);
           if (MODE == 1) {
             const double v = eri_at(A.I.eri, n, i, a, j2, b);
-            h = (single_parity(Ak, i, a) ^ single_parity(B, j2, b)) ? -v : v;
+            h = (pa ^ single_parity(B, j2, b)) ? -v : v;
             const int64_t *Fa = A.Fa + (size_t)jdx * n, *Fb = A.Fb + (size_t)jdx * n;
             dh = Fa[a] - Fa[i] - s_jk[a * n + i] + Fb[b] - Fb[j2] - s_jk[b * n + j2] +
                  s_jj[a * n + b] - s_jj[a * n + j2] - s_jj[i * n + b] + s_jj[i * n + j2];
@@ -511,17 +550,18 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
         jdx = A.grp_start[k] + q;
         tb = A.core_beta[jdx];
         if (MODE == 1) {
-          int i, j2, a, b;
-          dec_double(Ak, va, o - 1 - A.E.sa, A.dv_pa_p, &i, &j2, &a, &b);
+          const int i = (int)(aop & 31u), a = (int)((aop >> 5) & 31u);
+          const int j2 = (int)((aop >> 10) & 31u), b = (int)((aop >> 15) & 31u);
           const double v = eri_at(A.I.asym, n, i, a, j2, b);
-          h = par_double(Ak, i, j2, a, b) ? -v : v;
+          h = ((aop >> 20) & 1u) ? -v : v;
           dh = dd_same(A.Fa + (size_t)jdx * n, s_jk, n, i, j2, a, b);
         }
       }
       if (big) cell = A.cellbase[gi] + bucket_of(tb, A.nb[gi]);
     }
     // warp-aggregated bucket counters (one atomic per distinct cell per warp)
-    const uint32_t peers = __match_any_sync(0xffffffffu, cell);
+    const bool any_big = __any_sync(0xffffffffu, cell != 0xffffffffu);
+    const uint32_t peers = any_big ? __match_any_sync(0xffffffffu, cell) : 0xffffffffu;
     const int leader = __ffs(peers) - 1;
     if (MODE == 0) {
       if (cell != 0xffffffffu && lane == leader) atomicAdd(&A.cnt[cell], (uint32_t)__popc(peers));
@@ -616,31 +656,23 @@ __device__ __forceinline__ bool psi_contains(const uint64_t *ht, uint64_t mask, 
   return false;
 }
 
+// A tile groups its records by target in a shared-memory hash table: each
+// slot holds (target tag, head record) and each record the index of the next
+// record of its target, so every target ends up with the list of its records.
+// The numerator is then summed exactly over that list, so grouping by hashing
+// gives bit for bit the result of sorting the records and summing the runs.
 struct CellSmem {
-  uint32_t key[kCap];               // beta' of each record, sorted in place
-  uint16_t idx[kCap];               // original position of each sorted record
-  uint16_t grp[kCap];               // local group of each record (original position)
-  double val[kCap];                 // value of each record (original position)
-  uint32_t hist[256 * kCellWarps];  // per-warp digit counts, digit-major
-  uint32_t gstart[kGroupsPerTile];
-  uint32_t galpha[kGroupsPerTile];
-  uint16_t heads[kCap + 1];         // sorted positions where a target's run starts
+  unsigned long long slot[kSlots];  // (tag << 12) | head record; 0 = empty
+  double val[kCap];                 // record values
+  int64_t haa[kCap];                // record diagonals (all records of a target agree)
+  uint16_t next[kCap];              // next record of the same target; 0xffff ends the list
+  uint32_t gstart[kGroupsPerTile];  // packed tiles: first record of each class
+  uint32_t galpha[kGroupsPerTile];  // packed tiles: target alpha string of each class
   uint32_t wsum[kCellWarps];
-  uint32_t red[kCellWarps];
-  uint32_t nheads;
   uint32_t tile;
   unsigned long long cbase;
 };
-
-__device__ __forceinline__ uint32_t peers_of(uint32_t d, uint32_t active) {
-  uint32_t pe = active;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-    pe &= ((d >> b) & 1u) ? bal : ~bal;
-  }
-  return pe;
-}
+static_assert(kCap <= 4096, "record index must fit 12 bits of a slot word");
 
 // Block-wide exclusive scan of one value per thread; *total receives the sum.
 __device__ __forceinline__ uint32_t block_scan(CellSmem &S, uint32_t v, uint32_t *total) {
@@ -669,101 +701,54 @@ __device__ __forceinline__ uint32_t block_scan(CellSmem &S, uint32_t v, uint32_t
   return pre;
 }
 
-// Stable LSD radix sort of (beta', idx) in shared memory over the digits where
-// the keys differ.  Warp w owns records [w*32*kCellItems, ...) in rounds of 32.
-__device__ void block_sort(CellSmem &S, int nrec, uint32_t vary) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t lt = (1u << lane) - 1u;
-  const int wbeg = warp * 32 * kCellItems;
-  for (int shift = 0; shift < 32; shift += 8) {
-    if (((vary >> shift) & 0xffu) == 0) continue;
-    for (int t = threadIdx.x; t < 256 * kCellWarps; t += kCellThreads) S.hist[t] = 0;
-    __syncthreads();
-    // per round: key, and one word packing the original index (12 bits), the
-    // rank among equal digits in the round (5), their count (6) and the leader bit
-    uint32_t k[kCellItems], meta[kCellItems];
-#pragma unroll
-    for (int r = 0; r < kCellItems; ++r) {
-      const int e = wbeg + r * 32 + lane;
-      const bool ok = e < nrec;
-      k[r] = ok ? S.key[e] : 0u;
-      const uint32_t ix = ok ? S.idx[e] : 0u;
-      const uint32_t d = (k[r] >> shift) & 0xffu;
-      const uint32_t active = __ballot_sync(0xffffffffu, ok);
-      const uint32_t pe = peers_of(d, active);
-      const uint32_t c = __popc(pe);
-      const bool lead = ok && lane == __ffs(pe) - 1;
-      meta[r] = ix | (__popc(pe & lt) << 12) | (c << 17) | ((lead ? 1u : 0u) << 23);
-      if (lead) S.hist[d * kCellWarps + warp] += c;
-      __syncwarp();
-    }
-    __syncthreads();
-    {
-      constexpr int PER = (256 * kCellWarps) / kCellThreads;
-      uint32_t loc[PER], sum = 0;
-#pragma unroll
-      for (int i = 0; i < PER; ++i) {
-        loc[i] = S.hist[threadIdx.x * PER + i];
-        sum += loc[i];
+// Insert record e under target key (class << 32 | beta').  Returns false if
+// the probe ran over the whole table (cannot happen at load <= 1/2).
+__device__ __forceinline__ bool slot_insert(CellSmem &S, uint64_t key, uint32_t e) {
+  const unsigned long long tag = key + 1ull;  // never 0
+  uint32_t h = (uint32_t)(mix_key(key) & (kSlots - 1));
+  for (int probe = 0; probe < kSlots; ++probe) {
+    unsigned long long cur = S.slot[h];
+    for (;;) {
+      if (cur == 0ull) {
+        const unsigned long long prev = atomicCAS(&S.slot[h], 0ull, (tag << 12) | e);
+        if (prev == 0ull) {
+          S.next[e] = 0xffffu;
+          return true;
+        }
+        cur = prev;
+        continue;
       }
-      uint32_t tot;
-      uint32_t pre = block_scan(S, sum, &tot);
-#pragma unroll
-      for (int i = 0; i < PER; ++i) {
-        S.hist[threadIdx.x * PER + i] = pre;
-        pre += loc[i];
+      if ((cur >> 12) != tag) break;
+      const unsigned long long prev = atomicCAS(&S.slot[h], cur, (tag << 12) | e);
+      if (prev == cur) {
+        S.next[e] = (uint16_t)(cur & 0xfffu);
+        return true;
       }
+      cur = prev;
     }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kCellItems; ++r) {
-      const int e = wbeg + r * 32 + lane;
-      const bool ok = e < nrec;
-      const uint32_t d = (k[r] >> shift) & 0xffu;
-      uint32_t pos = 0;
-      if (ok) pos = S.hist[d * kCellWarps + warp] + ((meta[r] >> 12) & 31u);
-      __syncwarp();
-      if (ok && ((meta[r] >> 23) & 1u)) S.hist[d * kCellWarps + warp] += (meta[r] >> 17) & 63u;
-      __syncwarp();
-      if (ok) {
-        S.key[pos] = k[r];
-        S.idx[pos] = (uint16_t)(meta[r] & 0xfffu);
-      }
-    }
-    __syncthreads();
+    h = (h + 1) & (kSlots - 1);
   }
+  return false;
 }
 
-// Exact numerator of the run [b, e) of sorted records (screened records are
-// skipped); returns false when every record of the run was screened out.
-__device__ __forceinline__ bool run_numerator(const CellSmem &S, int b, int e, double *num,
-                                              unsigned *err) {
-  if (e - b == 1) {
-    const double v = S.val[S.idx[b]];
-    *num = v;
-    return !is_dropped(v);
-  }
-  // grid anchored to the largest exponent of the run (order independent)
-  int emax = 1, live = 0;
-  for (int i = b; i < e; ++i) {
-    const double v = S.val[S.idx[i]];
-    if (is_dropped(v)) continue;
-    const int ex = fx_exponent(v);
+// Exact numerator over the record list starting at e (values of screened-out
+// records are never inserted).
+__device__ __forceinline__ double list_numerator(const CellSmem &S, uint32_t e, unsigned *err) {
+  if (S.next[e] == 0xffffu) return S.val[e];
+  int emax = 1;
+  for (uint32_t i = e; i != 0xffffu; i = S.next[i]) {
+    const int ex = fx_exponent(S.val[i]);
     emax = ex > emax ? ex : emax;
-    ++live;
   }
   const int frac = fx_frac_for(emax);
   Fx192 acc = {0, 0, 0};
   unsigned ovf = 0;
-  for (int i = b; i < e; ++i) {
-    const double v = S.val[S.idx[i]];
-    if (is_dropped(v)) continue;
-    Fx192 x = fx_from_double(v, frac, &ovf);
+  for (uint32_t i = e; i != 0xffffu; i = S.next[i]) {
+    Fx192 x = fx_from_double(S.val[i], frac, &ovf);
     fx_add(acc, x);
   }
   if (ovf) atomicOr(err, kErrAccum);
-  *num = fx_to_double(acc, frac);
-  return live > 0;
+  return fx_to_double(acc, frac);
 }
 
 __global__ void __launch_bounds__(kCellThreads, 2) k_cells(CellArgs C) {
@@ -773,6 +758,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cells(CellArgs C) {
   unsigned long long my_unique = 0, my_excl = 0;
   for (;;) {
     if (threadIdx.x == 0) S.tile = atomicAdd(C.tile_counter, 1u);
+    for (int i = threadIdx.x; i < kSlots; i += kCellThreads) S.slot[i] = 0ull;
     __syncthreads();
     const uint32_t tile = S.tile;
     if (tile >= C.ntiles) break;
@@ -795,77 +781,43 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cells(CellArgs C) {
       }
       __syncthreads();
     }
-    // load records; the sort key is beta' alone: records arrive in class
-    // order, so a stable sort keeps each (class, beta') run contiguous
-    uint32_t vary = 0, k0 = nrec > 0 ? C.sb_beta[d.start] : 0u;
+    // load the records and link each one into its target's list
     for (int e = threadIdx.x; e < nrec; e += kCellThreads) {
       const uint32_t beta = C.sb_beta[d.start + e];
-      uint16_t g = 0;
+      const double v = C.sb_val[d.start + e];
+      S.val[e] = v;
+      S.haa[e] = C.sb_haa[d.start + e];
+      if (is_dropped(v)) continue;
+      uint32_t g = 0;
       if (packed) {
         int lo = 0, hi = (int)d.ng - 1;
         while (lo < hi) {
           int mid = (lo + hi + 1) >> 1;
           if ((int)S.gstart[mid] <= e) lo = mid; else hi = mid - 1;
         }
-        g = (uint16_t)lo;
+        g = (uint32_t)lo;
       }
-      S.key[e] = beta;
-      S.idx[e] = (uint16_t)e;
-      S.grp[e] = g;
-      S.val[e] = C.sb_val[d.start + e];
-      vary |= beta ^ k0;
+      if (!slot_insert(S, ((uint64_t)g << 32) | beta, (uint32_t)e)) atomicOr(C.err, kErrTile);
     }
-    for (int dl = 16; dl; dl >>= 1) vary |= __shfl_xor_sync(0xffffffffu, vary, dl);
-    if (lane == 0) S.red[threadIdx.x >> 5] = vary;
     __syncthreads();
-    vary = 0;
-    for (int w = 0; w < kCellWarps; ++w) vary |= S.red[w];
-    __syncthreads();
-    block_sort(S, nrec, vary);
-    // heads of target runs: (class, beta') changes along the sorted order
-    {
-      const int b0 = threadIdx.x * kCellItems;
-      uint32_t flags = 0, cnt = 0;
-#pragma unroll
-      for (int r = 0; r < kCellItems; ++r) {
-        const int i = b0 + r;
-        if (i < nrec) {
-          const bool h = i == 0 || S.key[i] != S.key[i - 1] ||
-                         (packed && S.grp[S.idx[i]] != S.grp[S.idx[i - 1]]);
-          if (h) {
-            flags |= 1u << r;
-            ++cnt;
-          }
-        }
-      }
-      uint32_t tot;
-      uint32_t pre = block_scan(S, cnt, &tot);
-#pragma unroll
-      for (int r = 0; r < kCellItems; ++r)
-        if ((flags >> r) & 1u) S.heads[pre++] = (uint16_t)(b0 + r);
-      if (threadIdx.x == 0) {
-        S.nheads = tot;
-        S.heads[tot] = (uint16_t)nrec;
-      }
-      __syncthreads();
-    }
-    // one target per thread, strided: exact numerator, exclusion, threshold
-    const int H = (int)S.nheads;
+    // one target per occupied slot: exact numerator, exclusion, threshold
     uint32_t pass_mask = 0, npass = 0;
+    constexpr int kPer = kSlots / kCellThreads;
 #pragma unroll 1
-    for (int r = 0; r * kCellThreads + (int)threadIdx.x < H; ++r) {
-      const int h = r * kCellThreads + threadIdx.x;
-      const int b = S.heads[h], e = S.heads[h + 1];
-      double num;
-      if (!run_numerator(S, b, e, &num, C.err)) continue;
-      const uint32_t a = packed ? S.galpha[S.grp[S.idx[b]]] : d.alpha;
-      const uint64_t full = pack_key(a, S.key[b]);
+    for (int r = 0; r < kPer; ++r) {
+      const unsigned long long w = S.slot[r * kCellThreads + threadIdx.x];
+      if (!w) continue;
+      const uint32_t e = (uint32_t)(w & 0xfffu);
+      const uint64_t key = (w >> 12) - 1ull;
+      const double num = list_numerator(S, e, C.err);
+      const uint32_t a = packed ? S.galpha[(uint32_t)(key >> 32)] : d.alpha;
+      const uint64_t full = pack_key(a, (uint32_t)key);
       ++my_unique;
       if (psi_contains(C.psi_ht, C.psi_mask, full, C.err)) {
         ++my_excl;
         continue;
       }
-      const int64_t den_x = C.E0_x - C.sb_haa[d.start + S.idx[b]];
+      const int64_t den_x = C.E0_x - S.haa[e];
       bool pass = true;
       if (C.tau > 0.0) {
         const float nf = fabsf(__double2float_rn(num));
@@ -886,22 +838,22 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cells(CellArgs C) {
     const uint32_t pre = block_scan(S, npass, &tot);
     if (threadIdx.x == 0) S.cbase = tot ? atomicAdd(C.cand_count, (unsigned long long)tot) : 0ull;
     __syncthreads();
-    unsigned long long slot = S.cbase + pre;
+    unsigned long long slotc = S.cbase + pre;
     for (int r = 0; pass_mask; ++r) {
       if (!((pass_mask >> r) & 1u)) continue;
       pass_mask &= ~(1u << r);
-      const int h = r * kCellThreads + threadIdx.x;
-      const int b = S.heads[h], e = S.heads[h + 1];
-      double num;
-      run_numerator(S, b, e, &num, C.err);
-      const uint32_t a = packed ? S.galpha[S.grp[S.idx[b]]] : d.alpha;
-      const int64_t den_x = C.E0_x - C.sb_haa[d.start + S.idx[b]];
+      const unsigned long long w = S.slot[r * kCellThreads + threadIdx.x];
+      const uint32_t e = (uint32_t)(w & 0xfffu);
+      const uint64_t key = (w >> 12) - 1ull;
+      const double num = list_numerator(S, e, C.err);
+      const uint32_t a = packed ? S.galpha[(uint32_t)(key >> 32)] : d.alpha;
+      const int64_t den_x = C.E0_x - S.haa[e];
       const double sc = num / (__ll2double_rn(den_x) * C.inv_scale);
-      if (slot < C.cand_cap) {
-        C.cand_key[slot] = pack_key(a, S.key[b]);
-        C.cand_score[slot] = sc;
+      if (slotc < C.cand_cap) {
+        C.cand_key[slotc] = pack_key(a, (uint32_t)key);
+        C.cand_score[slotc] = sc;
       }
-      ++slot;
+      ++slotc;
     }
     __syncthreads();
   }
