@@ -668,8 +668,10 @@ struct CellSmem {
   uint16_t next[kCap];              // next record of the same target; 0xffff ends the list
   uint32_t gstart[kGroupsPerTile];  // packed tiles: first record of each class
   uint32_t galpha[kGroupsPerTile];  // packed tiles: target alpha string of each class
+  uint16_t targets[kCap];           // occupied slots, compacted
   uint32_t wsum[kCellWarps];
   uint32_t tile;
+  uint32_t ntargets;
   unsigned long long cbase;
 };
 static_assert(kCap <= 4096, "record index must fit 12 bits of a slot word");
@@ -800,13 +802,30 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cells(CellArgs C) {
       if (!slot_insert(S, ((uint64_t)g << 32) | beta, (uint32_t)e)) atomicOr(C.err, kErrTile);
     }
     __syncthreads();
-    // one target per occupied slot: exact numerator, exclusion, threshold
+    // compact the occupied slots so that every lane works on a target
+    {
+      constexpr int kPer = kSlots / kCellThreads;
+      uint32_t occ = 0, cnt = 0;
+#pragma unroll
+      for (int r = 0; r < kPer; ++r)
+        if (S.slot[threadIdx.x * kPer + r]) {
+          occ |= 1u << r;
+          ++cnt;
+        }
+      uint32_t tot;
+      uint32_t pre = block_scan(S, cnt, &tot);
+#pragma unroll
+      for (int r = 0; r < kPer; ++r)
+        if ((occ >> r) & 1u) S.targets[pre++] = (uint16_t)(threadIdx.x * kPer + r);
+      if (threadIdx.x == 0) S.ntargets = tot;
+      __syncthreads();
+    }
+    // one target per thread, strided: exact numerator, exclusion, threshold
     uint32_t pass_mask = 0, npass = 0;
-    constexpr int kPer = kSlots / kCellThreads;
+    const int ntg = (int)S.ntargets;
 #pragma unroll 1
-    for (int r = 0; r < kPer; ++r) {
-      const unsigned long long w = S.slot[r * kCellThreads + threadIdx.x];
-      if (!w) continue;
+    for (int r = 0; r * kCellThreads + (int)threadIdx.x < ntg; ++r) {
+      const unsigned long long w = S.slot[S.targets[r * kCellThreads + threadIdx.x]];
       const uint32_t e = (uint32_t)(w & 0xfffu);
       const uint64_t key = (w >> 12) - 1ull;
       const double num = list_numerator(S, e, C.err);
@@ -842,7 +861,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cells(CellArgs C) {
     for (int r = 0; pass_mask; ++r) {
       if (!((pass_mask >> r) & 1u)) continue;
       pass_mask &= ~(1u << r);
-      const unsigned long long w = S.slot[r * kCellThreads + threadIdx.x];
+      const unsigned long long w = S.slot[S.targets[r * kCellThreads + threadIdx.x]];
       const uint32_t e = (uint32_t)(w & 0xfffu);
       const uint64_t key = (w >> 12) - 1ull;
       const double num = list_numerator(S, e, C.err);
@@ -871,47 +890,59 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cells(CellArgs C) {
 // A bucket holding more records than one tile is sorted in global memory on
 // beta' and its runs are reduced one target per thread.
 
-__global__ void k_big_keys(const uint32_t *sb_beta, uint32_t start, uint32_t n, uint64_t *keys,
-                           uint32_t *idx) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    keys[i] = sb_beta[start + i];
-    idx[i] = i;
+// Records of every oversized tile, concatenated: key = (tile position << 32 |
+// beta'), payload = position in the concatenation; src = staging index.
+__global__ void k_big_gather(const uint32_t *sb_beta, const uint32_t *start, const uint32_t *off,
+                             uint32_t nt, uint64_t total, uint64_t *keys, uint32_t *idx,
+                             uint32_t *src) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = nt - 1;  // tile holding record i
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t st = start[lo] + (uint32_t)(i - off[lo]);
+    keys[i] = ((uint64_t)lo << 32) | sb_beta[st];
+    idx[i] = (uint32_t)i;
+    src[i] = st;
   }
 }
 
-__global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, uint32_t n, uint32_t start,
-                             uint32_t alpha, CellArgs C) {
+__global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const uint32_t *src,
+                             uint64_t n, const uint32_t *alpha, CellArgs C) {
   unsigned long long my_unique = 0, my_excl = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t sk = keys[i];
     if (i > 0 && keys[i - 1] == sk) continue;
     int emax = 1, live = 0;
-    for (uint32_t e = i; e < n && keys[e] == sk; ++e) {
-      const double v = C.sb_val[start + idx[e]];
+    for (uint64_t e = i; e < n && keys[e] == sk; ++e) {
+      const double v = C.sb_val[src[idx[e]]];
       if (is_dropped(v)) continue;
       const int ex = fx_exponent(v);
       emax = ex > emax ? ex : emax;
       ++live;
     }
+    if (!live) continue;
     const int frac = fx_frac_for(emax);
     Fx192 acc = {0, 0, 0};
     unsigned ovf = 0;
-    for (uint32_t e = i; e < n && keys[e] == sk; ++e) {
-      const double v = C.sb_val[start + idx[e]];
+    for (uint64_t e = i; e < n && keys[e] == sk; ++e) {
+      const double v = C.sb_val[src[idx[e]]];
       if (is_dropped(v)) continue;
       Fx192 x = fx_from_double(v, frac, &ovf);
       fx_add(acc, x);
     }
     if (ovf) atomicOr(C.err, kErrAccum);
-    if (!live) continue;
     const double num = fx_to_double(acc, frac);
-    const uint64_t full = pack_key(alpha, (uint32_t)sk);
+    const uint64_t full = pack_key(alpha[sk >> 32], (uint32_t)sk);
     ++my_unique;
     if (psi_contains(C.psi_ht, C.psi_mask, full, C.err)) {
       ++my_excl;
       continue;
     }
-    const int64_t den_x = C.E0_x - C.sb_haa[start + idx[i]];
+    const int64_t den_x = C.E0_x - C.sb_haa[src[idx[i]]];
     const double sc = num / (__ll2double_rn(den_x) * C.inv_scale);
     if (fabs(sc) >= C.tau) {
       const unsigned long long slot = atomicAdd(C.cand_count, 1ull);
@@ -1304,34 +1335,73 @@ int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint
   return ASCI_OK;
 }
 
-// Reduce one oversized bucket tile through the global radix sort.  Appends at
-// most `npairs` candidates.
-int fused_big_tile(const FusedCore &F, const void *tiles, uint32_t tile, uint64_t P0,
-                   const uint32_t *sb_beta, const double *sb_val, const int64_t *sb_haa,
-                   uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
-                   unsigned long long *cand_count, unsigned long long cand_cap,
-                   unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
-                   uint32_t *npairs_out, Arena &arena) {
-  cudaStream_t s = arena.stream();
-  TileDesc d;
-  ASCI_TRY_CUDA(cudaMemcpyAsync(&d, static_cast<const TileDesc *>(tiles) + tile, sizeof(d),
-                                cudaMemcpyDefault, s));
+// Record counts of the listed tiles (one synchronisation).
+int tile_sizes(const void *tiles, const std::vector<uint32_t> &list, std::vector<uint32_t> *sizes,
+               cudaStream_t s) {
+  std::vector<TileDesc> h(list.size());
+  const TileDesc *dt = static_cast<const TileDesc *>(tiles);
+  for (size_t i = 0; i < list.size(); ++i)
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&h[i], dt + list[i], sizeof(TileDesc), cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
-  *npairs_out = d.npairs;
-  if ((uint64_t)d.start + d.npairs > stage_cap) return ASCI_ECUDA;
+  sizes->resize(list.size());
+  for (size_t i = 0; i < list.size(); ++i) (*sizes)[i] = h[i].npairs;
+  return ASCI_OK;
+}
+
+// Reduce every listed oversized bucket tile at once: their records are
+// gathered under keys (list position << 32 | beta'), radix-sorted in global
+// memory and reduced one target per thread.  Appends at most as many
+// candidates as there are records.
+int fused_big_tiles(const FusedCore &F, const void *tiles, const std::vector<uint32_t> &list,
+                    const uint32_t *sb_beta, const double *sb_val, const int64_t *sb_haa,
+                    uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
+                    unsigned long long *cand_count, unsigned long long cand_cap,
+                    unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
+                    uint64_t *nrec_out, Arena &arena) {
+  cudaStream_t s = arena.stream();
+  *nrec_out = 0;
+  if (list.empty()) return ASCI_OK;
+  const size_t nt = list.size();
+  std::vector<TileDesc> h(nt);
+  const TileDesc *dt = static_cast<const TileDesc *>(tiles);
+  for (size_t i = 0; i < nt; ++i)
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&h[i], dt + list[i], sizeof(TileDesc), cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  std::vector<uint32_t> start(nt), off(nt + 1), alpha(nt);
+  uint64_t total = 0;
+  for (size_t i = 0; i < nt; ++i) {
+    if ((uint64_t)h[i].start + h[i].npairs > stage_cap) return ASCI_ECUDA;
+    start[i] = h[i].start;
+    alpha[i] = h[i].alpha;
+    off[i] = (uint32_t)total;
+    total += h[i].npairs;
+  }
+  if (total >= (1ull << 32)) return ASCI_ENOMEM;
+  off[nt] = (uint32_t)total;
+  *nrec_out = total;
   Arena ta(s);
+  uint32_t *d_start, *d_off, *d_alpha, *i0, *i1, *src;
   uint64_t *k0, *k1;
-  uint32_t *i0, *i1;
-  ASCI_TRY(ta.alloc(&k0, d.npairs));
-  ASCI_TRY(ta.alloc(&k1, d.npairs));
-  ASCI_TRY(ta.alloc(&i0, d.npairs));
-  ASCI_TRY(ta.alloc(&i1, d.npairs));
-  k_big_keys<<<grid_for(d.npairs), 256, 0, s>>>(sb_beta, d.start, d.npairs, k0, i0);
+  ASCI_TRY(ta.alloc(&d_start, nt));
+  ASCI_TRY(ta.alloc(&d_off, nt + 1));
+  ASCI_TRY(ta.alloc(&d_alpha, nt));
+  ASCI_TRY(ta.alloc(&k0, total));
+  ASCI_TRY(ta.alloc(&k1, total));
+  ASCI_TRY(ta.alloc(&i0, total));
+  ASCI_TRY(ta.alloc(&i1, total));
+  ASCI_TRY(ta.alloc(&src, total));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(d_start, start.data(), nt * 4, cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(d_off, off.data(), (nt + 1) * 4, cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(d_alpha, alpha.data(), nt * 4, cudaMemcpyDefault, s));
+  k_big_gather<<<grid_for(total), 256, 0, s>>>(sb_beta, d_start, d_off, (uint32_t)nt, total, k0,
+                                               i0, src);
   ASCI_CHECK_LAUNCH();
-  ASCI_TRY(radix_sort_u64_u32(&k0, &k1, &i0, &i1, d.npairs, 0, 32, ta));
-  CellArgs CA = cell_args(F, P0, sb_beta, sb_val, sb_haa, stage_cap, tau, cand_key, cand_score,
+  int topbit = 0;
+  while ((1ull << topbit) < (uint64_t)nt) ++topbit;
+  ASCI_TRY(radix_sort_u64_u32(&k0, &k1, &i0, &i1, total, 0, 32 + topbit, ta));
+  CellArgs CA = cell_args(F, 0, sb_beta, sb_val, sb_haa, stage_cap, tau, cand_key, cand_score,
                           cand_count, cand_cap, n_unique, n_excluded, err);
-  k_big_reduce<<<grid_for(d.npairs), 256, 0, s>>>(k0, i0, d.npairs, d.start, d.alpha, CA);
+  k_big_reduce<<<grid_for(total), 256, 0, s>>>(k0, i0, src, total, d_alpha, CA);
   ASCI_CHECK_LAUNCH();
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
   return ASCI_OK;

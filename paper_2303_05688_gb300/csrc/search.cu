@@ -52,12 +52,14 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
                 uint64_t stage_cap, double eps, unsigned long long *survivors, unsigned *err,
                 void **tiles_out, size_t *ntiles_out, std::vector<uint32_t> *oversized,
                 Arena &arena);
-int fused_big_tile(const FusedCore &F, const void *tiles, uint32_t tile, uint64_t P0,
-                   const uint32_t *sb_beta, const double *sb_val, const int64_t *sb_haa,
-                   uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
-                   unsigned long long *cand_count, unsigned long long cand_cap,
-                   unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
-                   uint32_t *npairs_out, Arena &arena);
+int tile_sizes(const void *tiles, const std::vector<uint32_t> &list, std::vector<uint32_t> *sizes,
+               cudaStream_t s);
+int fused_big_tiles(const FusedCore &F, const void *tiles, const std::vector<uint32_t> &list,
+                    const uint32_t *sb_beta, const double *sb_val, const int64_t *sb_haa,
+                    uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
+                    unsigned long long *cand_count, unsigned long long cand_cap,
+                    unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
+                    uint64_t *nrec_out, Arena &arena);
 int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint32_t tile_end,
                 uint64_t P0, const uint32_t *sb_beta, const double *sb_val, const int64_t *sb_haa,
                 uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
@@ -757,30 +759,46 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
         tm.start();
       }
     }
-    // buckets too large for one tile: global sort on (beta', core index)
-    for (uint32_t ot : oversized) {
-      unsigned long long c = 0;
-      uint32_t np = 0;
-      ASCI_TRY_CUDA(cudaMemcpyAsync(&np, static_cast<const char *>(tiles) + (size_t)ot * 24 + 4,
-                                    sizeof(np), cudaMemcpyDefault, stream));
-      ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
-      // room for every record of the bucket as a candidate
-      if (pool_cap - pool_n < np) {
-        tm.stop(&tl[5]);
-        tm.start();
-        ASCI_TRY(prune(ba));
-        tm.stop(&tl[6]);
-        tm.start();
-        if (pool_cap - pool_n < np) return ASCI_ENOMEM;
+    // buckets too large for one tile: global sorts over as many of them as
+    // the free candidate capacity allows (every record may become one)
+    if (!oversized.empty()) {
+      std::vector<uint32_t> sizes;
+      ASCI_TRY(tile_sizes(tiles, oversized, &sizes, stream));
+      size_t i = 0;
+      while (i < oversized.size()) {
+        if ((uint64_t)(pool_cap - pool_n) < sizes[i]) {
+          tm.stop(&tl[5]);
+          tm.start();
+          ASCI_TRY(prune(ba));
+          tm.stop(&tl[6]);
+          tm.start();
+          if ((uint64_t)(pool_cap - pool_n) < sizes[i]) return ASCI_ENOMEM;
+        }
+        uint64_t room = pool_cap - pool_n, total = 0;
+        size_t j = i;
+        while (j < oversized.size() && total + sizes[j] <= room) total += sizes[j++];
+        std::vector<uint32_t> chunk(oversized.begin() + i, oversized.begin() + j);
+        uint64_t nrec = 0;
+        ASCI_TRY(fused_big_tiles(F, tiles, chunk, sb_beta, sb_val, sb_haa, bcap, tau,
+                                 pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1,
+                                 dcount + 2, derr2, &nrec, ba));
+        unsigned long long c = 0;
+        unsigned he = 0;
+        ASCI_TRY_CUDA(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDefault, stream));
+        ASCI_TRY_CUDA(cudaMemcpyAsync(&he, derr2, sizeof(he), cudaMemcpyDefault, stream));
+        ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+        if (he) {
+          char msg[96];
+          snprintf(msg, sizeof(msg), "oversized-tile reduction check failed (flags 0x%x)", he);
+          record_error(msg, __FILE__, __LINE__);
+          return ASCI_ECUDA;
+        }
+        if (c > pool_cap) return ASCI_ECUDA;
+        pool_n = (size_t)c;
+        ASCI_TRACE("oversized tiles: [%zu,%zu) %llu records, pool=%zu", i, j,
+                   (unsigned long long)nrec, pool_n);
+        i = j;
       }
-      ASCI_TRY(fused_big_tile(F, tiles, ot, b.P0, sb_beta, sb_val, sb_haa, bcap, tau,
-                              pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1, dcount + 2,
-                              derr2, &np, ba));
-      ASCI_TRY_CUDA(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDefault, stream));
-      ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
-      if (c > pool_cap) return ASCI_ECUDA;
-      pool_n = (size_t)c;
-      ASCI_TRACE("oversized tile %u: %u records, pool=%zu", ot, np, pool_n);
     }
     tm.stop(&tl[5]);
     if (pool_n > N) {  // tighten tau before the next batch
