@@ -186,7 +186,17 @@ struct TileDesc {  // 24 bytes; npairs at byte offset 4 (read by the host)
 static_assert(sizeof(TileDesc) == 24, "tile descriptor layout");
 
 // A screened-out record (Alg. 2's eps test) keeps its slot with a NaN value.
-__device__ __forceinline__ bool is_dropped(double v) { return v != v; }
+// (Tested on the bits: NaN compares cost FP64 instructions, which are scarce.)
+__device__ __forceinline__ bool is_dropped(double v) {
+  return ((uint64_t)__double_as_longlong(v) & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ double drop_marker() {
+  return __longlong_as_double(0x7ff8000000000000ll);
+}
+// x with its sign flipped when flip is 1 (an integer operation on the bits).
+__device__ __forceinline__ double flip_sign(double x, uint32_t flip) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)(flip & 1u) << 63));
+}
 
 }  // namespace
 
@@ -304,6 +314,7 @@ struct EmitArgs {
   const uint32_t *tile_item;  // first item of each emission tile (+1 entry)
   const uint32_t *tile_list;  // count mode: emission tiles overlapping big classes
   uint64_t t0, t1, P0, P1;
+  uint32_t ntl;  // emission tiles to visit (listed tiles in count mode)
   int opbits;
   const uint32_t *grp_alpha, *grp_start, *core_beta;
   const double *core_c;
@@ -406,7 +417,9 @@ __device__ __forceinline__ int64_t dd_same(const int64_t *F, const int64_t *jk, 
          jk[a * n + j] - jk[b * n + i] - jk[b * n + j];
 }
 
-template <int MODE>  // 0: count bucket sizes of big classes; 1: emit records
+// MODE 0 counts the bucket sizes of big classes, MODE 1 emits the records;
+// EPS compiles Alg. 2's screen in (eps > 0).
+template <int MODE, bool EPS>
 __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
   extern __shared__ int64_t s_fx[];  // jk[n*n], jj[n*n]
   __shared__ uint64_t sW[kEmitTile + 1];
@@ -420,15 +433,19 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
       s_jk[t] = A.X.jk[t];
       s_jj[t] = A.X.jj[t];
     }
-  const uint32_t tile = MODE == 0 ? A.tile_list[blockIdx.x] : blockIdx.x;
+  const uint32_t full = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+  const uint32_t omask = (1u << A.opbits) - 1u;
+  const int lane = threadIdx.x & 31;
+  // persistent: the integral tables above are loaded once per CTA
+#pragma unroll 1
+  for (uint32_t ti = blockIdx.x; ti < A.ntl; ti += gridDim.x) {
+  const uint32_t tile = MODE == 0 ? A.tile_list[ti] : ti;
   const uint64_t pb = A.P0 + (uint64_t)tile * kEmitTile;
   const uint64_t pe = (pb + kEmitTile < A.P1) ? pb + kEmitTile : A.P1;
   const uint64_t ta = A.t0 + A.tile_item[tile];
   uint64_t tl = A.t0 + A.tile_item[tile + 1];
   if (tl >= A.t1) tl = A.t1 - 1;
   const int nspan = (int)(tl - ta + 1);  // <= kEmitTile + 1: every item has >= 1 pair
-  const uint32_t full = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
-  const uint32_t omask = (1u << A.opbits) - 1u;
   for (int i = threadIdx.x; i < nspan; i += kEmitThreads) {
     const uint64_t it = A.items[ta + i];
     sIt[i] = it;
@@ -452,7 +469,6 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
     sOp[i] = op;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int r = 0; r < kEmitPer; ++r) {
     const uint64_t p = pb + (uint64_t)r * kEmitThreads + threadIdx.x;
@@ -501,8 +517,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
           dec_single(B, vb, e, A.dv_vb, &i, &a);
           tb = B ^ (1u << i) ^ (1u << a);
           if (MODE == 1) {
-            const double v = single_val(A.I, B, Ak, i, a);
-            h = single_parity(B, i, a) ? -v : v;
+            h = flip_sign(single_val(A.I, B, Ak, i, a), (uint32_t)single_parity(B, i, a));
             const int64_t *F = A.Fb + (size_t)jdx * n;
             dh = F[a] - F[i] - s_jk[a * n + i];
           }
@@ -510,8 +525,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
           dec_double(B, vb, e - A.E.sb, A.dv_pb_p, &i, &j2, &a, &b);
           tb = B ^ (1u << i) ^ (1u << j2) ^ (1u << a) ^ (1u << b);
           if (MODE == 1) {
-            const double v = eri_at(A.I.asym, n, i, a, j2, b);
-            h = par_double(B, i, j2, a, b) ? -v : v;
+            h = flip_sign(eri_at(A.I.asym, n, i, a, j2, b), (uint32_t)par_double(B, i, j2, a, b));
             dh = dd_same(A.Fb + (size_t)jdx * n, s_jk, n, i, j2, a, b);
           }
         }
@@ -528,8 +542,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
         if (e == 0) {
           tb = B;
           if (MODE == 1) {
-            const double v = single_val(A.I, Ak, B, i, a);
-            h = pa ? -v : v;
+            h = flip_sign(single_val(A.I, Ak, B, i, a), (uint32_t)pa);
             const int64_t *F = A.Fa + (size_t)jdx * n;
             dh = F[a] - F[i] - s_jk[a * n + i];
           }
@@ -539,8 +552,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
           dec_single(B, vb, e - 1, A.dv_vb, &j2, &b);
           tb = B ^ (1u << j2) ^ (1u << b);
           if (MODE == 1) {
-            const double v = eri_at(A.I.eri, n, i, a, j2, b);
-            h = (pa ^ single_parity(B, j2, b)) ? -v : v;
+            h = flip_sign(eri_at(A.I.eri, n, i, a, j2, b), (uint32_t)(pa ^ single_parity(B, j2, b)));
             const int64_t *Fa = A.Fa + (size_t)jdx * n, *Fb = A.Fb + (size_t)jdx * n;
             dh = Fa[a] - Fa[i] - s_jk[a * n + i] + Fb[b] - Fb[j2] - s_jk[b * n + j2] +
                  s_jj[a * n + b] - s_jj[a * n + j2] - s_jj[i * n + b] + s_jj[i * n + j2];
@@ -552,8 +564,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
         if (MODE == 1) {
           const int i = (int)(aop & 31u), a = (int)((aop >> 5) & 31u);
           const int j2 = (int)((aop >> 10) & 31u), b = (int)((aop >> 15) & 31u);
-          const double v = eri_at(A.I.asym, n, i, a, j2, b);
-          h = ((aop >> 20) & 1u) ? -v : v;
+          h = flip_sign(eri_at(A.I.asym, n, i, a, j2, b), aop >> 20);
           dh = dd_same(A.Fa + (size_t)jdx * n, s_jk, n, i, j2, a, b);
         }
       }
@@ -582,12 +593,12 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
         }
         double v = h * A.core_c[jdx];
         const int64_t haa = A.Dx[jdx] + dh;
-        if (A.eps > 0.0) {
+        if (EPS) {
           // |v / (E0 - H_ii)| > eps, without a division
           const double den = __ll2double_rn(A.E0_x - haa) * A.inv_scale;
-          if (!(fabs(v) > A.eps * fabs(den))) v = __longlong_as_double(0x7ff8000000000000ll);
+          if (!(fabs(v) > A.eps * fabs(den))) v = drop_marker();
+          kept = !is_dropped(v);
         }
-        kept = !is_dropped(v);
         if (pos < A.stage_cap) {
           A.sb_beta[pos] = tb;
           A.sb_val[pos] = v;
@@ -596,11 +607,13 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
           atomicOr(A.err, kErrStage);
         }
       }
-      if (A.eps > 0.0) {
+      if (EPS) {
         const uint32_t nk = __popc(__ballot_sync(0xffffffffu, kept));
         if (lane == 0 && nk) atomicAdd(A.survivors, (unsigned long long)nk);
       }
     }
+  }
+  __syncthreads();  // the next tile overwrites the item arrays
   }
 }
 
@@ -617,7 +630,7 @@ struct CellArgs {
   uint64_t P0;
   int64_t E0_x;
   double inv_scale;  // 2^-s
-  float inv_scale_f;
+  int s;  // fixed-point scale of the diagonal: 2^-s
   double tau;
   float tau_f;
   const uint64_t *psi_ht;
@@ -672,7 +685,6 @@ struct CellSmem {
   uint32_t wsum[kCellWarps];
   uint32_t tile;
   uint32_t ntargets;
-  unsigned long long cbase;
 };
 static_assert(kCap <= 4096, "record index must fit 12 bits of a slot word");
 
@@ -736,7 +748,10 @@ __device__ __forceinline__ bool slot_insert(CellSmem &S, uint64_t key, uint32_t 
 // Exact numerator over the record list starting at e (values of screened-out
 // records are never inserted).
 __device__ __forceinline__ double list_numerator(const CellSmem &S, uint32_t e, unsigned *err) {
-  if (S.next[e] == 0xffffu) return S.val[e];
+  const uint32_t e2 = S.next[e];
+  if (e2 == 0xffffu) return S.val[e];
+  // two records: IEEE addition rounds their exact sum once, like the accumulator
+  if (S.next[e2] == 0xffffu) return S.val[e] + S.val[e2];
   int emax = 1;
   for (uint32_t i = e; i != 0xffffu; i = S.next[i]) {
     const int ex = fx_exponent(S.val[i]);
@@ -751,6 +766,28 @@ __device__ __forceinline__ double list_numerator(const CellSmem &S, uint32_t e, 
   }
   if (ovf) atomicOr(err, kErrAccum);
   return fx_to_double(acc, frac);
+}
+
+// |x| as a float built from the bits, truncated (relative error below 2^-23);
+// *ok is false when |x| lies outside the normal float range.
+__device__ __forceinline__ float abs_as_float(double x, bool *ok) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  int e = (int)(b >> 52) - 1023 + 127;
+  *ok = e >= 1 && e <= 254;
+  e = e < 1 ? 1 : (e > 254 ? 254 : e);
+  return __uint_as_float(((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
+}
+
+// |z| * 2^-s as a float, truncated; *ok is false for zero or outside the
+// normal float range.
+__device__ __forceinline__ float abs_scaled_as_float(int64_t z, int s, bool *ok) {
+  const uint64_t u = z < 0 ? 0ull - (uint64_t)z : (uint64_t)z;
+  const int lz = __clzll((long long)u);
+  int e = 63 - lz - s + 127;
+  *ok = u != 0 && e >= 1 && e <= 254;
+  e = e < 1 ? 1 : (e > 254 ? 254 : e);
+  const uint32_t mant = u ? (uint32_t)((u << lz) >> 40) & 0x7fffffu : 0u;
+  return __uint_as_float(((uint32_t)e << 23) | mant);
 }
 
 __global__ void __launch_bounds__(kCellThreads, 2) k_cells(CellArgs C) {
@@ -808,7 +845,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cells(CellArgs C) {
       uint32_t occ = 0, cnt = 0;
 #pragma unroll
       for (int r = 0; r < kPer; ++r)
-        if (S.slot[threadIdx.x * kPer + r]) {
+        if (S.slot[r * kCellThreads + threadIdx.x]) {
           occ |= 1u << r;
           ++cnt;
         }
@@ -816,63 +853,59 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cells(CellArgs C) {
       uint32_t pre = block_scan(S, cnt, &tot);
 #pragma unroll
       for (int r = 0; r < kPer; ++r)
-        if ((occ >> r) & 1u) S.targets[pre++] = (uint16_t)(threadIdx.x * kPer + r);
+        if ((occ >> r) & 1u) S.targets[pre++] = (uint16_t)(r * kCellThreads + threadIdx.x);
       if (threadIdx.x == 0) S.ntargets = tot;
       __syncthreads();
     }
-    // one target per thread, strided: exact numerator, exclusion, threshold
-    uint32_t pass_mask = 0, npass = 0;
+    // one target per thread, strided: exact numerator, exclusion, threshold;
+    // the rounds are uniform over each warp, and a warp appends its targets
+    // that reach the threshold with one atomic
     const int ntg = (int)S.ntargets;
+    const int warp_base = (int)(threadIdx.x & ~31u);
 #pragma unroll 1
-    for (int r = 0; r * kCellThreads + (int)threadIdx.x < ntg; ++r) {
-      const unsigned long long w = S.slot[S.targets[r * kCellThreads + threadIdx.x]];
-      const uint32_t e = (uint32_t)(w & 0xfffu);
-      const uint64_t key = (w >> 12) - 1ull;
-      const double num = list_numerator(S, e, C.err);
-      const uint32_t a = packed ? S.galpha[(uint32_t)(key >> 32)] : d.alpha;
-      const uint64_t full = pack_key(a, (uint32_t)key);
-      ++my_unique;
-      if (psi_contains(C.psi_ht, C.psi_mask, full, C.err)) {
-        ++my_excl;
-        continue;
+    for (int base = 0; base + warp_base < ntg; base += kCellThreads) {
+      const int idx = base + (int)threadIdx.x;
+      bool pass = false;
+      double sc = 0.0;
+      uint64_t full = 0;
+      if (idx < ntg) {
+        const unsigned long long w = S.slot[S.targets[idx]];
+        const uint32_t e = (uint32_t)(w & 0xfffu);
+        const uint64_t key = (w >> 12) - 1ull;
+        const double num = list_numerator(S, e, C.err);
+        const uint32_t a = packed ? S.galpha[(uint32_t)(key >> 32)] : d.alpha;
+        full = pack_key(a, (uint32_t)key);
+        ++my_unique;
+        if (psi_contains(C.psi_ht, C.psi_mask, full, C.err)) {
+          ++my_excl;
+        } else {
+          const int64_t den_x = C.E0_x - S.haa[e];
+          pass = true;
+          if (C.tau > 0.0) {
+            bool okn, okd;
+            const float nf = abs_as_float(num, &okn);
+            const float df = abs_scaled_as_float(den_x, C.s, &okd);
+            if (okn && okd) pass = nf >= C.tau_f * df * 0.99999f;  // else the exact test decides
+          }
+          if (pass) {
+            sc = num / (__ll2double_rn(den_x) * C.inv_scale);
+            pass = fabs(sc) >= C.tau;
+          }
+        }
       }
-      const int64_t den_x = C.E0_x - S.haa[e];
-      bool pass = true;
-      if (C.tau > 0.0) {
-        const float nf = fabsf(__double2float_rn(num));
-        const float df = fabsf(__ll2float_rn(den_x) * C.inv_scale_f);
-        pass = nf >= C.tau_f * df * 0.99999f;
+      const unsigned bal = __ballot_sync(0xffffffffu, pass);
+      if (bal) {
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(C.cand_count, (unsigned long long)__popc(bal));
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        if (pass) {
+          const unsigned long long slotc = b0 + __popc(bal & ((1u << lane) - 1u));
+          if (slotc < C.cand_cap) {
+            C.cand_key[slotc] = full;
+            C.cand_score[slotc] = sc;
+          }
+        }
       }
-      if (pass) {
-        const double sc = num / (__ll2double_rn(den_x) * C.inv_scale);
-        pass = fabs(sc) >= C.tau;
-      }
-      if (pass) {
-        pass_mask |= 1u << r;
-        ++npass;
-      }
-    }
-    // block-aggregated append of the targets that reach the threshold
-    uint32_t tot;
-    const uint32_t pre = block_scan(S, npass, &tot);
-    if (threadIdx.x == 0) S.cbase = tot ? atomicAdd(C.cand_count, (unsigned long long)tot) : 0ull;
-    __syncthreads();
-    unsigned long long slotc = S.cbase + pre;
-    for (int r = 0; pass_mask; ++r) {
-      if (!((pass_mask >> r) & 1u)) continue;
-      pass_mask &= ~(1u << r);
-      const unsigned long long w = S.slot[S.targets[r * kCellThreads + threadIdx.x]];
-      const uint32_t e = (uint32_t)(w & 0xfffu);
-      const uint64_t key = (w >> 12) - 1ull;
-      const double num = list_numerator(S, e, C.err);
-      const uint32_t a = packed ? S.galpha[(uint32_t)(key >> 32)] : d.alpha;
-      const int64_t den_x = C.E0_x - S.haa[e];
-      const double sc = num / (__ll2double_rn(den_x) * C.inv_scale);
-      if (slotc < C.cand_cap) {
-        C.cand_key[slotc] = pack_key(a, (uint32_t)key);
-        C.cand_score[slotc] = sc;
-      }
-      ++slotc;
     }
     __syncthreads();
   }
@@ -1106,6 +1139,15 @@ int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t 
 // Stage one batch (items [t0, t1), pairs [P0, P1), groups [gb0, gb1)): plan
 // its tiles, count the hash buckets of big classes and emit every record into
 // the staging buffer.  The tile table is left in *tiles_out (arena memory).
+// Persistent emission grid: a few CTAs per SM, at most one per tile.
+static unsigned emit_grid(size_t ntl) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 152;
+  return (unsigned)std::max<size_t>(1, std::min<size_t>(ntl, (size_t)sms * 8));
+}
+
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
                 uint32_t gb0, uint32_t gb1, uint32_t *sb_beta, double *sb_val, int64_t *sb_haa,
                 uint64_t stage_cap, double eps, unsigned long long *survivors, unsigned *err,
@@ -1225,7 +1267,8 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
     ASCI_CHECK_LAUNCH();
     A.tile_list = list;
     if (nbig) {
-      k_emit2<0><<<(unsigned)nbig, kEmitThreads, 0, s>>>(A);
+      A.ntl = (uint32_t)nbig;
+      k_emit2<0, false><<<emit_grid(nbig), kEmitThreads, 0, s>>>(A);
       ASCI_CHECK_LAUNCH();
     }
   }
@@ -1244,7 +1287,11 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
                                             n_over, over_list, over_cap);
   ASCI_CHECK_LAUNCH();
   ASCI_TRACE("stage: tiles written");
-  k_emit2<1><<<etiles, kEmitThreads, emit_smem, s>>>(A);
+  A.ntl = etiles;
+  if (eps > 0.0)
+    k_emit2<1, true><<<emit_grid(etiles), kEmitThreads, emit_smem, s>>>(A);
+  else
+    k_emit2<1, false><<<emit_grid(etiles), kEmitThreads, emit_smem, s>>>(A);
   ASCI_CHECK_LAUNCH();
   ASCI_TRACE("stage: emit launched (%u blocks)", etiles);
   unsigned hov = 0;
@@ -1284,7 +1331,7 @@ static CellArgs cell_args(const FusedCore &F, uint64_t P0, const uint32_t *sb_be
   CA.P0 = P0;
   CA.E0_x = F.E0_x;
   CA.inv_scale = ldexp(1.0, -F.X.s);
-  CA.inv_scale_f = ldexpf(1.0f, -F.X.s);
+  CA.s = F.X.s;
   CA.tau = tau;
   CA.tau_f = (float)tau;
   if ((double)CA.tau_f > tau) CA.tau_f = nextafterf(CA.tau_f, 0.0f);
