@@ -200,12 +200,11 @@ __device__ __forceinline__ double flip_sign(double x, uint32_t flip) {
 
 }  // namespace
 
-constexpr int kCellThreads = 512;
-constexpr int kCellWarps = kCellThreads / 32;
-constexpr int kCap = 2048;                          // records per tile
+constexpr int kCellThreads = 256;
+constexpr int kCap = 1024;                          // records per tile
 constexpr int kSlots = 2 * kCap;                    // hash slots per tile (load <= 1/2)
 constexpr uint32_t kSmallMax = kCap / 2;            // packable class size
-constexpr uint32_t kBucketTarget = kCap / 2;        // expected records per hash bucket
+constexpr uint32_t kBucketTarget = kCap * 13 / 16;  // expected records per hash bucket
 constexpr uint32_t kGroupsPerTile = 1024;
 
 namespace {
@@ -324,7 +323,8 @@ struct EmitArgs {
   uint32_t *cnt;              // count mode
   const uint32_t *cell_pos0;  // emit mode
   uint32_t *fill;             // emit mode
-  uint32_t *sb_beta;
+  const uint32_t *g_alpha;  // target alpha string of each class
+  uint64_t *sb_key;
   double *sb_val;
   int64_t *sb_haa;
   double eps;                 // Alg. 2 screen; 0 keeps every pair
@@ -426,6 +426,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
   __shared__ uint64_t sIt[kEmitTile + 1];
   __shared__ uint32_t sG[kEmitTile + 1];
   __shared__ uint32_t sOp[kEmitTile + 1];  // decoded alpha operation of each item
+  __shared__ uint32_t sTA[kEmitTile + 1];  // target alpha string of each item
   const int n = A.I.n;
   int64_t *s_jk = s_fx, *s_jj = s_fx + n * n;
   if (MODE == 1)
@@ -451,6 +452,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
     sIt[i] = it;
     sW[i] = A.Wexcl[ta + i];
     sG[i] = A.item_group[ta + i];
+    if (MODE == 1) sTA[i] = A.g_alpha[sG[i]];
     // alpha operation of the item, decoded once: orbitals (5 bits each) and parity
     const uint32_t k = (uint32_t)it >> A.opbits, o = (uint32_t)it & omask;
     uint32_t op = 0;
@@ -474,7 +476,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
     const uint64_t p = pb + (uint64_t)r * kEmitThreads + threadIdx.x;
     const bool valid = p < pe;
     uint32_t cell = 0xffffffffu;  // bucket cell of a big class, else none
-    uint32_t tb = 0, jdx = 0;
+    uint32_t tb = 0, jdx = 0, talpha = 0;
     double h = 0.0;
     int64_t dh = 0;
     bool big = false;
@@ -503,6 +505,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
       const uint32_t aop = sOp[lo];
       const uint32_t q = (uint32_t)(p - sW[lo]);
       const uint32_t gi = sG[lo] - A.gb0;
+      if (MODE == 1) talpha = sTA[lo];
       big = A.kind[gi] == kTileBucket;
       const uint32_t k = (uint32_t)it >> A.opbits, o = (uint32_t)it & omask;
       const uint32_t Ak = A.grp_alpha[k];
@@ -600,7 +603,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
           kept = !is_dropped(v);
         }
         if (pos < A.stage_cap) {
-          A.sb_beta[pos] = tb;
+          A.sb_key[pos] = pack_key(talpha, tb);
           A.sb_val[pos] = v;
           A.sb_haa[pos] = haa;
         } else {
@@ -621,16 +624,14 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
 
 struct CellArgs {
   const TileDesc *tiles;
-  uint32_t ntiles;
-  const uint32_t *sb_beta;
+  uint32_t ntiles;     // tiles [tile0, ntiles) are visited
+  uint32_t tile0;
+  const uint64_t *sb_key;
   const double *sb_val;
   const int64_t *sb_haa;
-  const uint32_t *g_alpha;
-  const uint64_t *g_P0;
-  uint64_t P0;
   int64_t E0_x;
   double inv_scale;  // 2^-s
-  int s;  // fixed-point scale of the diagonal: 2^-s
+  int s;             // fixed-point scale of the diagonal: 2^-s
   double tau;
   float tau_f;
   const uint64_t *psi_ht;
@@ -640,7 +641,6 @@ struct CellArgs {
   unsigned long long *cand_count;
   unsigned long long cand_cap;
   unsigned long long *n_unique, *n_excluded;
-  unsigned *tile_counter;
   uint64_t stage_cap;
   unsigned *err;
 };
@@ -669,99 +669,75 @@ __device__ __forceinline__ bool psi_contains(const uint64_t *ht, uint64_t mask, 
   return false;
 }
 
-// A tile groups its records by target in a shared-memory hash table: each
-// slot holds (target tag, head record) and each record the index of the next
-// record of its target, so every target ends up with the list of its records.
+// A tile groups its records by target in a shared-memory hash table: a slot
+// holds the newest record of its target and each record the index of the
+// previous one, so that every target ends up with the list of its records.
 // The numerator is then summed exactly over that list, so grouping by hashing
 // gives bit for bit the result of sorting the records and summing the runs.
-struct CellSmem {
-  unsigned long long slot[kSlots];  // (tag << 12) | head record; 0 = empty
-  double val[kCap];                 // record values
-  int64_t haa[kCap];                // record diagonals (all records of a target agree)
-  uint16_t next[kCap];              // next record of the same target; 0xffff ends the list
-  uint32_t gstart[kGroupsPerTile];  // packed tiles: first record of each class
-  uint32_t galpha[kGroupsPerTile];  // packed tiles: target alpha string of each class
-  uint16_t targets[kCap];           // occupied slots, compacted
-  uint32_t wsum[kCellWarps];
-  uint32_t tile;
-  uint32_t ntargets;
-};
-static_assert(kCap <= 4096, "record index must fit 12 bits of a slot word");
+// The records of the next tile are copied in asynchronously meanwhile.
+constexpr uint32_t kEmptySlot = 0xffffffffu;
+constexpr uint16_t kEndList = 0xffffu;
 
-// Block-wide exclusive scan of one value per thread; *total receives the sum.
-__device__ __forceinline__ uint32_t block_scan(CellSmem &S, uint32_t v, uint32_t *total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-    if (lane >= d) x += y;
-  }
-  if (lane == 31) S.wsum[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < kCellWarps ? S.wsum[lane] : 0u;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
-      if (lane >= d) w += y;
-    }
-    if (lane < kCellWarps) S.wsum[lane] = w;
-  }
-  __syncthreads();
-  const uint32_t pre = (warp ? S.wsum[warp - 1] : 0u) + x - v;
-  *total = S.wsum[kCellWarps - 1];
-  __syncthreads();
-  return pre;
+struct CellSmem {
+  uint64_t key[2][kCap];   // record target keys (double-buffered by tile)
+  double val[2][kCap];     // record values
+  uint32_t slot[kSlots];   // newest record of the slot's target, or kEmptySlot
+  uint16_t next[kCap];     // previous record of the same target, or kEndList
+  uint16_t targets[kCap];  // occupied slots, in order of claiming
+  uint32_t ntargets[2];    // by tile parity
+};
+static_assert(kCap < 0xffff, "record index must fit 16 bits");
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Insert record e under target key (class << 32 | beta').  Returns false if
-// the probe ran over the whole table (cannot happen at load <= 1/2).
-__device__ __forceinline__ bool slot_insert(CellSmem &S, uint64_t key, uint32_t e) {
-  const unsigned long long tag = key + 1ull;  // never 0
-  uint32_t h = (uint32_t)(mix_key(key) & (kSlots - 1));
-  for (int probe = 0; probe < kSlots; ++probe) {
-    unsigned long long cur = S.slot[h];
-    for (;;) {
-      if (cur == 0ull) {
-        const unsigned long long prev = atomicCAS(&S.slot[h], 0ull, (tag << 12) | e);
-        if (prev == 0ull) {
-          S.next[e] = 0xffffu;
-          return true;
-        }
-        cur = prev;
-        continue;
-      }
-      if ((cur >> 12) != tag) break;
-      const unsigned long long prev = atomicCAS(&S.slot[h], cur, (tag << 12) | e);
-      if (prev == cur) {
-        S.next[e] = (uint16_t)(cur & 0xfffu);
-        return true;
-      }
-      cur = prev;
-    }
-    h = (h + 1) & (kSlots - 1);
+// A tile that the kernel reduces on chip; oversized hash buckets go to the
+// global path, anything else outside the limits is a planning bug.
+__device__ __forceinline__ bool tile_on_chip(const TileDesc &d, uint64_t stage_cap,
+                                             unsigned *err) {
+  const bool fits = d.npairs <= (uint32_t)kCap && (uint64_t)d.start + d.npairs <= stage_cap;
+  if (!fits && threadIdx.x == 0 &&
+      !(d.kind == kTileBucket && (uint64_t)d.start + d.npairs <= stage_cap))
+    atomicOr(err, kErrTile);
+  return fits;
+}
+
+__device__ __forceinline__ void prefetch_tile(CellSmem &S, int buf, const TileDesc &d,
+                                              const CellArgs &C) {
+  for (uint32_t e = threadIdx.x; e < d.npairs; e += kCellThreads) {
+    cp_async8(&S.key[buf][e], C.sb_key + d.start + e);
+    cp_async8(&S.val[buf][e], C.sb_val + d.start + e);
   }
-  return false;
+  cp_async_commit();
 }
 
 // Exact numerator over the record list starting at e (values of screened-out
 // records are never inserted).
-__device__ __forceinline__ double list_numerator(const CellSmem &S, uint32_t e, unsigned *err) {
+__device__ __forceinline__ double list_numerator(const CellSmem &S, int buf, uint32_t e,
+                                                 unsigned *err) {
+  const double *val = S.val[buf];
   const uint32_t e2 = S.next[e];
-  if (e2 == 0xffffu) return S.val[e];
+  if (e2 == kEndList) return val[e];
   // two records: IEEE addition rounds their exact sum once, like the accumulator
-  if (S.next[e2] == 0xffffu) return S.val[e] + S.val[e2];
+  if (S.next[e2] == kEndList) return val[e] + val[e2];
   int emax = 1;
-  for (uint32_t i = e; i != 0xffffu; i = S.next[i]) {
-    const int ex = fx_exponent(S.val[i]);
+  for (uint32_t i = e; i != kEndList; i = S.next[i]) {
+    const int ex = fx_exponent(val[i]);
     emax = ex > emax ? ex : emax;
   }
   const int frac = fx_frac_for(emax);
   Fx192 acc = {0, 0, 0};
   unsigned ovf = 0;
-  for (uint32_t i = e; i != 0xffffu; i = S.next[i]) {
-    Fx192 x = fx_from_double(S.val[i], frac, &ovf);
+  for (uint32_t i = e; i != kEndList; i = S.next[i]) {
+    Fx192 x = fx_from_double(val[i], frac, &ovf);
     fx_add(acc, x);
   }
   if (ovf) atomicOr(err, kErrAccum);
@@ -790,125 +766,134 @@ __device__ __forceinline__ float abs_scaled_as_float(int64_t z, int s, bool *ok)
   return __uint_as_float(((uint32_t)e << 23) | mant);
 }
 
-__global__ void __launch_bounds__(kCellThreads, 2) k_cells(CellArgs C) {
+__global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CellSmem &S = *reinterpret_cast<CellSmem *>(smem_raw);
   const int lane = threadIdx.x & 31;
+  const int warp_base = (int)(threadIdx.x & ~31u);
   unsigned long long my_unique = 0, my_excl = 0;
-  for (;;) {
-    if (threadIdx.x == 0) S.tile = atomicAdd(C.tile_counter, 1u);
-    for (int i = threadIdx.x; i < kSlots; i += kCellThreads) S.slot[i] = 0ull;
-    __syncthreads();
-    const uint32_t tile = S.tile;
-    if (tile >= C.ntiles) break;
-    const TileDesc d = C.tiles[tile];
-    if (d.npairs > (uint32_t)kCap || (uint64_t)d.start + d.npairs > C.stage_cap ||
-        (d.kind == kTilePacked && d.ng > kGroupsPerTile)) {
-      // oversized hash buckets are reduced by the global path; anything else is a bug
-      if (threadIdx.x == 0 && !(d.kind == kTileBucket && d.npairs > (uint32_t)kCap &&
-                                (uint64_t)d.start + d.npairs <= C.stage_cap))
-        atomicOr(C.err, kErrTile);
-      __syncthreads();
-      continue;
-    }
-    const int nrec = (int)d.npairs;
-    const bool packed = d.kind == kTilePacked;
-    if (packed) {
-      for (uint32_t i = threadIdx.x; i < d.ng; i += kCellThreads) {
-        S.gstart[i] = (uint32_t)(C.g_P0[d.g0 + i] - C.P0) - d.start;
-        S.galpha[i] = C.g_alpha[d.g0 + i];
-      }
-      __syncthreads();
-    }
-    // load the records and link each one into its target's list
-    for (int e = threadIdx.x; e < nrec; e += kCellThreads) {
-      const uint32_t beta = C.sb_beta[d.start + e];
-      const double v = C.sb_val[d.start + e];
-      S.val[e] = v;
-      S.haa[e] = C.sb_haa[d.start + e];
-      if (is_dropped(v)) continue;
-      uint32_t g = 0;
-      if (packed) {
-        int lo = 0, hi = (int)d.ng - 1;
-        while (lo < hi) {
-          int mid = (lo + hi + 1) >> 1;
-          if ((int)S.gstart[mid] <= e) lo = mid; else hi = mid - 1;
-        }
-        g = (uint32_t)lo;
-      }
-      if (!slot_insert(S, ((uint64_t)g << 32) | beta, (uint32_t)e)) atomicOr(C.err, kErrTile);
-    }
-    __syncthreads();
-    // compact the occupied slots so that every lane works on a target
-    {
-      constexpr int kPer = kSlots / kCellThreads;
-      uint32_t occ = 0, cnt = 0;
-#pragma unroll
-      for (int r = 0; r < kPer; ++r)
-        if (S.slot[r * kCellThreads + threadIdx.x]) {
-          occ |= 1u << r;
-          ++cnt;
-        }
-      uint32_t tot;
-      uint32_t pre = block_scan(S, cnt, &tot);
-#pragma unroll
-      for (int r = 0; r < kPer; ++r)
-        if ((occ >> r) & 1u) S.targets[pre++] = (uint16_t)(r * kCellThreads + threadIdx.x);
-      if (threadIdx.x == 0) S.ntargets = tot;
-      __syncthreads();
-    }
-    // one target per thread, strided: exact numerator, exclusion, threshold;
-    // the rounds are uniform over each warp, and a warp appends its targets
-    // that reach the threshold with one atomic
-    const int ntg = (int)S.ntargets;
-    const int warp_base = (int)(threadIdx.x & ~31u);
-#pragma unroll 1
-    for (int base = 0; base + warp_base < ntg; base += kCellThreads) {
-      const int idx = base + (int)threadIdx.x;
-      bool pass = false;
-      double sc = 0.0;
-      uint64_t full = 0;
-      if (idx < ntg) {
-        const unsigned long long w = S.slot[S.targets[idx]];
-        const uint32_t e = (uint32_t)(w & 0xfffu);
-        const uint64_t key = (w >> 12) - 1ull;
-        const double num = list_numerator(S, e, C.err);
-        const uint32_t a = packed ? S.galpha[(uint32_t)(key >> 32)] : d.alpha;
-        full = pack_key(a, (uint32_t)key);
-        ++my_unique;
-        if (psi_contains(C.psi_ht, C.psi_mask, full, C.err)) {
-          ++my_excl;
-        } else {
-          const int64_t den_x = C.E0_x - S.haa[e];
-          pass = true;
-          if (C.tau > 0.0) {
-            bool okn, okd;
-            const float nf = abs_as_float(num, &okn);
-            const float df = abs_scaled_as_float(den_x, C.s, &okd);
-            if (okn && okd) pass = nf >= C.tau_f * df * 0.99999f;  // else the exact test decides
-          }
-          if (pass) {
-            sc = num / (__ll2double_rn(den_x) * C.inv_scale);
-            pass = fabs(sc) >= C.tau;
-          }
-        }
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, pass);
-      if (bal) {
-        unsigned long long b0 = 0;
-        if (lane == 0) b0 = atomicAdd(C.cand_count, (unsigned long long)__popc(bal));
-        b0 = __shfl_sync(0xffffffffu, b0, 0);
-        if (pass) {
-          const unsigned long long slotc = b0 + __popc(bal & ((1u << lane) - 1u));
-          if (slotc < C.cand_cap) {
-            C.cand_key[slotc] = full;
-            C.cand_score[slotc] = sc;
-          }
-        }
-      }
-    }
-    __syncthreads();
+  for (int i = threadIdx.x; i < kSlots; i += kCellThreads) S.slot[i] = kEmptySlot;
+  if (threadIdx.x == 0) S.ntargets[0] = S.ntargets[1] = 0;
+  // tiles blockIdx.x + k * gridDim.x; descriptors are read one tile ahead of
+  // the record copies, which run one tile ahead of the reduction
+  uint32_t tile = C.tile0 + blockIdx.x;
+  TileDesc d = {0, 0, 0, 0, 0, 0}, dn = {0, 0, 0, 0, 0, 0};
+  bool on = false, on_n = false;
+  if (tile < C.ntiles) {
+    d = C.tiles[tile];
+    on = tile_on_chip(d, C.stage_cap, C.err);
+    if (on) prefetch_tile(S, 0, d, C);
   }
+  if (tile + gridDim.x < C.ntiles) dn = C.tiles[tile + gridDim.x];
+  int buf = 0;
+#pragma unroll 1
+  for (; tile < C.ntiles; tile += gridDim.x, buf ^= 1) {
+    TileDesc dnn = {0, 0, 0, 0, 0, 0};
+    if (tile + 2 * gridDim.x < C.ntiles) dnn = C.tiles[tile + 2 * gridDim.x];
+    cp_async_wait_all();
+    __syncthreads();  // records of this tile in place; the previous tile is done
+    if (tile + gridDim.x < C.ntiles) {
+      on_n = tile_on_chip(dn, C.stage_cap, C.err);
+      if (on_n) prefetch_tile(S, buf ^ 1, dn, C);
+    } else {
+      on_n = false;
+    }
+    if (on) {
+      // link each record into its target's list; warps append the slots they
+      // claim to the target list with one shared atomic per round
+      const int nrec = (int)d.npairs;
+#pragma unroll 1
+      for (int base = 0; base + warp_base < nrec; base += kCellThreads) {
+        const int e = base + (int)threadIdx.x;
+        int claimed = -1;
+        if (e < nrec && !is_dropped(S.val[buf][e])) {
+          const uint64_t key = S.key[buf][e];
+          uint32_t h = (uint32_t)mix_key(key) & (kSlots - 1);
+          int probe = 0;
+          for (; probe < kSlots; ++probe) {
+            uint32_t cur = S.slot[h];
+            if (cur == kEmptySlot) {
+              cur = atomicCAS(&S.slot[h], kEmptySlot, (uint32_t)e);
+              if (cur == kEmptySlot) {
+                S.next[e] = kEndList;
+                claimed = (int)h;
+                break;
+              }
+            }
+            if (S.key[buf][cur] == key) {
+              S.next[e] = (uint16_t)atomicExch(&S.slot[h], (uint32_t)e);
+              break;
+            }
+            h = (h + 1) & (kSlots - 1);
+          }
+          if (probe == kSlots) atomicOr(C.err, kErrTile);  // cannot happen at load <= 1/2
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, claimed >= 0);
+        if (bal) {
+          uint32_t b0 = 0;
+          if (lane == 0) b0 = atomicAdd(&S.ntargets[buf], (uint32_t)__popc(bal));
+          b0 = __shfl_sync(0xffffffffu, b0, 0);
+          if (claimed >= 0) S.targets[b0 + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)claimed;
+        }
+      }
+    }
+    __syncthreads();  // lists complete
+    if (threadIdx.x == 0) S.ntargets[buf ^ 1] = 0;  // read by no one until the next barrier
+    if (on) {
+      // one target per thread: exact numerator, exclusion, threshold; the
+      // slot is emptied by its owner for the next tile
+      const int ntg = (int)S.ntargets[buf];
+#pragma unroll 1
+      for (int base = 0; base + warp_base < ntg; base += kCellThreads) {
+        const int idx = base + (int)threadIdx.x;
+        bool pass = false;
+        double sc = 0.0;
+        uint64_t key = 0;
+        if (idx < ntg) {
+          const uint32_t h = S.targets[idx];
+          const uint32_t e = S.slot[h];
+          S.slot[h] = kEmptySlot;
+          key = S.key[buf][e];
+          const int64_t haa = C.sb_haa[d.start + e];  // every record of a target agrees
+          const double num = list_numerator(S, buf, e, C.err);
+          ++my_unique;
+          if (psi_contains(C.psi_ht, C.psi_mask, key, C.err)) {
+            ++my_excl;
+          } else {
+            const int64_t den_x = C.E0_x - haa;
+            pass = true;
+            if (C.tau > 0.0) {
+              bool okn, okd;
+              const float nf = abs_as_float(num, &okn);
+              const float df = abs_scaled_as_float(den_x, C.s, &okd);
+              if (okn && okd) pass = nf >= C.tau_f * df * 0.99999f;  // else the exact test decides
+            }
+            if (pass) {
+              sc = num / (__ll2double_rn(den_x) * C.inv_scale);
+              pass = fabs(sc) >= C.tau;
+            }
+          }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, pass);
+        if (bal) {
+          unsigned long long b0 = 0;
+          if (lane == 0) b0 = atomicAdd(C.cand_count, (unsigned long long)__popc(bal));
+          b0 = __shfl_sync(0xffffffffu, b0, 0);
+          if (pass) {
+            const unsigned long long slotc = b0 + __popc(bal & ((1u << lane) - 1u));
+            if (slotc < C.cand_cap) {
+              C.cand_key[slotc] = key;
+              C.cand_score[slotc] = sc;
+            }
+          }
+        }
+      }
+    }
+    d = dn;
+    dn = dnn;
+    on = on_n;
+  }
+  cp_async_wait_all();
   for (int dl = 16; dl; dl >>= 1) {
     my_unique += __shfl_xor_sync(0xffffffffu, my_unique, dl);
     my_excl += __shfl_xor_sync(0xffffffffu, my_excl, dl);
@@ -923,9 +908,19 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_cells(CellArgs C) {
 // A bucket holding more records than one tile is sorted in global memory on
 // beta' and its runs are reduced one target per thread.
 
+__global__ void k_tile_gather(const TileDesc *tiles, const uint32_t *list, uint32_t n,
+                              uint32_t *info) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const TileDesc d = tiles[list[i]];
+    info[3 * i] = d.start;
+    info[3 * i + 1] = d.npairs;
+    info[3 * i + 2] = d.alpha;
+  }
+}
+
 // Records of every oversized tile, concatenated: key = (tile position << 32 |
 // beta'), payload = position in the concatenation; src = staging index.
-__global__ void k_big_gather(const uint32_t *sb_beta, const uint32_t *start, const uint32_t *off,
+__global__ void k_big_gather(const uint64_t *sb_key, const uint32_t *start, const uint32_t *off,
                              uint32_t nt, uint64_t total, uint64_t *keys, uint32_t *idx,
                              uint32_t *src) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -936,7 +931,7 @@ __global__ void k_big_gather(const uint32_t *sb_beta, const uint32_t *start, con
       if (off[mid] <= i) lo = mid; else hi = mid - 1;
     }
     const uint32_t st = start[lo] + (uint32_t)(i - off[lo]);
-    keys[i] = ((uint64_t)lo << 32) | sb_beta[st];
+    keys[i] = ((uint64_t)lo << 32) | (sb_key[st] >> 32);  // beta' is the high word
     idx[i] = (uint32_t)i;
     src[i] = st;
   }
@@ -1149,7 +1144,7 @@ static unsigned emit_grid(size_t ntl) {
 }
 
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
-                uint32_t gb0, uint32_t gb1, uint32_t *sb_beta, double *sb_val, int64_t *sb_haa,
+                uint32_t gb0, uint32_t gb1, uint64_t *sb_key, double *sb_val, int64_t *sb_haa,
                 uint64_t stage_cap, double eps, unsigned long long *survivors, unsigned *err,
                 void **tiles_out, size_t *ntiles_out, std::vector<uint32_t> *oversized,
                 Arena &arena) {
@@ -1240,7 +1235,8 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   A.cnt = cnt;
   A.cell_pos0 = cell_pos0;
   A.fill = fill;
-  A.sb_beta = sb_beta;
+  A.g_alpha = F.g_alpha;
+  A.sb_key = sb_key;
   A.sb_val = sb_val;
   A.sb_haa = sb_haa;
   A.eps = eps;
@@ -1315,7 +1311,7 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
 
 size_t tile_capacity() { return (size_t)kCap; }
 
-static CellArgs cell_args(const FusedCore &F, uint64_t P0, const uint32_t *sb_beta,
+static CellArgs cell_args(const FusedCore &F, const uint64_t *sb_key,
                           const double *sb_val, const int64_t *sb_haa, uint64_t stage_cap,
                           double tau, uint64_t *cand_key, double *cand_score,
                           unsigned long long *cand_count, unsigned long long cand_cap,
@@ -1323,12 +1319,9 @@ static CellArgs cell_args(const FusedCore &F, uint64_t P0, const uint32_t *sb_be
                           unsigned *err) {
   CellArgs CA;
   memset(&CA, 0, sizeof(CA));
-  CA.sb_beta = sb_beta;
+  CA.sb_key = sb_key;
   CA.sb_val = sb_val;
   CA.sb_haa = sb_haa;
-  CA.g_alpha = F.g_alpha;
-  CA.g_P0 = F.g_P0;
-  CA.P0 = P0;
   CA.E0_x = F.E0_x;
   CA.inv_scale = ldexp(1.0, -F.X.s);
   CA.s = F.X.s;
@@ -1351,77 +1344,79 @@ static CellArgs cell_args(const FusedCore &F, uint64_t P0, const uint32_t *sb_be
 // Reduce tiles [tile_begin, tile_end) of a staged batch on chip and append the
 // targets with |S| >= tau to the candidate buffer (at most kCap per tile).
 int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint32_t tile_end,
-                uint64_t P0, const uint32_t *sb_beta, const double *sb_val, const int64_t *sb_haa,
+                const uint64_t *sb_key, const double *sb_val, const int64_t *sb_haa,
                 uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
                 unsigned long long *cand_count, unsigned long long cand_cap,
-                unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *counter,
-                unsigned *err, Arena &arena) {
+                unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
+                Arena &arena) {
   if (tile_end <= tile_begin) return ASCI_OK;
   cudaStream_t s = arena.stream();
-  CellArgs CA = cell_args(F, P0, sb_beta, sb_val, sb_haa, stage_cap, tau, cand_key, cand_score,
+  CellArgs CA = cell_args(F, sb_key, sb_val, sb_haa, stage_cap, tau, cand_key, cand_score,
                           cand_count, cand_cap, n_unique, n_excluded, err);
   CA.tiles = static_cast<const TileDesc *>(tiles);
+  CA.tile0 = tile_begin;
   CA.ntiles = tile_end;
-  CA.tile_counter = counter;
-  ASCI_TRY_CUDA(cudaMemcpyAsync(counter, &tile_begin, sizeof(unsigned), cudaMemcpyDefault, s));
   const size_t cell_smem = sizeof(CellSmem);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static int per_sm = 0;
+  if (!per_sm) {
     ASCI_TRY_CUDA(cudaFuncSetAttribute(k_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)cell_smem));
-    attr_set = true;
+    ASCI_TRY_CUDA(
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cells, kCellThreads, cell_smem));
+    if (per_sm < 1) per_sm = 1;
   }
   int dev = 0, sms = 152;
   ASCI_TRY_CUDA(cudaGetDevice(&dev));
   ASCI_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned grid = (unsigned)std::min<size_t>((size_t)sms * 2, tile_end - tile_begin);
-  ASCI_TRACE("cells: launch grid=%u smem=%zu", grid, cell_smem);
+  const unsigned grid =
+      (unsigned)std::min<size_t>((size_t)sms * per_sm, tile_end - tile_begin);
+  ASCI_TRACE("cells: launch grid=%u smem=%zu per_sm=%d", grid, cell_smem, per_sm);
   k_cells<<<grid, kCellThreads, cell_smem, s>>>(CA);
   ASCI_CHECK_LAUNCH();
-  ASCI_TRY_CUDA(cudaStreamSynchronize(s));  // `tile_begin` is read from the host stack
   return ASCI_OK;
 }
 
-// Record counts of the listed tiles (one synchronisation).
-int tile_sizes(const void *tiles, const std::vector<uint32_t> &list, std::vector<uint32_t> *sizes,
-               cudaStream_t s) {
-  std::vector<TileDesc> h(list.size());
-  const TileDesc *dt = static_cast<const TileDesc *>(tiles);
-  for (size_t i = 0; i < list.size(); ++i)
-    ASCI_TRY_CUDA(cudaMemcpyAsync(&h[i], dt + list[i], sizeof(TileDesc), cudaMemcpyDefault, s));
+// (start, records, target alpha) of each listed tile: one gather kernel and
+// one copy back.
+int tile_info(const void *tiles, const std::vector<uint32_t> &list, std::vector<uint32_t> *info,
+              cudaStream_t s) {
+  const size_t n = list.size();
+  info->assign(3 * n, 0u);
+  if (!n) return ASCI_OK;
+  Arena ta(s);
+  uint32_t *d_list, *d_info;
+  ASCI_TRY(ta.alloc(&d_list, n));
+  ASCI_TRY(ta.alloc(&d_info, 3 * n));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(d_list, list.data(), n * 4, cudaMemcpyDefault, s));
+  k_tile_gather<<<grid_for(n), 256, 0, s>>>(static_cast<const TileDesc *>(tiles), d_list,
+                                            (uint32_t)n, d_info);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY_CUDA(cudaMemcpyAsync(info->data(), d_info, 3 * n * 4, cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
-  sizes->resize(list.size());
-  for (size_t i = 0; i < list.size(); ++i) (*sizes)[i] = h[i].npairs;
   return ASCI_OK;
 }
 
-// Reduce every listed oversized bucket tile at once: their records are
-// gathered under keys (list position << 32 | beta'), radix-sorted in global
-// memory and reduced one target per thread.  Appends at most as many
-// candidates as there are records.
-int fused_big_tiles(const FusedCore &F, const void *tiles, const std::vector<uint32_t> &list,
-                    const uint32_t *sb_beta, const double *sb_val, const int64_t *sb_haa,
-                    uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
-                    unsigned long long *cand_count, unsigned long long cand_cap,
-                    unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
-                    uint64_t *nrec_out, Arena &arena) {
+// Reduce the oversized bucket tiles described by info[3i..3i+2], i in [0, nt),
+// at once: their records are gathered under keys (position << 32 | beta'),
+// radix-sorted in global memory and reduced one target per thread.  Appends at
+// most as many candidates as there are records.
+int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const uint64_t *sb_key,
+                    const double *sb_val, const int64_t *sb_haa, uint64_t stage_cap, double tau,
+                    uint64_t *cand_key, double *cand_score, unsigned long long *cand_count,
+                    unsigned long long cand_cap, unsigned long long *n_unique,
+                    unsigned long long *n_excluded, unsigned *err, uint64_t *nrec_out,
+                    Arena &arena) {
   cudaStream_t s = arena.stream();
   *nrec_out = 0;
-  if (list.empty()) return ASCI_OK;
-  const size_t nt = list.size();
-  std::vector<TileDesc> h(nt);
-  const TileDesc *dt = static_cast<const TileDesc *>(tiles);
-  for (size_t i = 0; i < nt; ++i)
-    ASCI_TRY_CUDA(cudaMemcpyAsync(&h[i], dt + list[i], sizeof(TileDesc), cudaMemcpyDefault, s));
-  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  if (!nt) return ASCI_OK;
   std::vector<uint32_t> start(nt), off(nt + 1), alpha(nt);
   uint64_t total = 0;
   for (size_t i = 0; i < nt; ++i) {
-    if ((uint64_t)h[i].start + h[i].npairs > stage_cap) return ASCI_ECUDA;
-    start[i] = h[i].start;
-    alpha[i] = h[i].alpha;
+    if ((uint64_t)info[3 * i] + info[3 * i + 1] > stage_cap) return ASCI_ECUDA;
+    start[i] = info[3 * i];
+    alpha[i] = info[3 * i + 2];
     off[i] = (uint32_t)total;
-    total += h[i].npairs;
+    total += info[3 * i + 1];
   }
   if (total >= (1ull << 32)) return ASCI_ENOMEM;
   off[nt] = (uint32_t)total;
@@ -1440,17 +1435,17 @@ int fused_big_tiles(const FusedCore &F, const void *tiles, const std::vector<uin
   ASCI_TRY_CUDA(cudaMemcpyAsync(d_start, start.data(), nt * 4, cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaMemcpyAsync(d_off, off.data(), (nt + 1) * 4, cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaMemcpyAsync(d_alpha, alpha.data(), nt * 4, cudaMemcpyDefault, s));
-  k_big_gather<<<grid_for(total), 256, 0, s>>>(sb_beta, d_start, d_off, (uint32_t)nt, total, k0,
+  k_big_gather<<<grid_for(total), 256, 0, s>>>(sb_key, d_start, d_off, (uint32_t)nt, total, k0,
                                                i0, src);
   ASCI_CHECK_LAUNCH();
   int topbit = 0;
   while ((1ull << topbit) < (uint64_t)nt) ++topbit;
   ASCI_TRY(radix_sort_u64_u32(&k0, &k1, &i0, &i1, total, 0, 32 + topbit, ta));
-  CellArgs CA = cell_args(F, 0, sb_beta, sb_val, sb_haa, stage_cap, tau, cand_key, cand_score,
+  CellArgs CA = cell_args(F, sb_key, sb_val, sb_haa, stage_cap, tau, cand_key, cand_score,
                           cand_count, cand_cap, n_unique, n_excluded, err);
   k_big_reduce<<<grid_for(total), 256, 0, s>>>(k0, i0, src, total, d_alpha, CA);
   ASCI_CHECK_LAUNCH();
-  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));  // the host vectors above are read by the copies
   return ASCI_OK;
 }
 

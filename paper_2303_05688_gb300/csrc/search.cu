@@ -48,24 +48,24 @@ int item_groups(const uint64_t *items, const uint64_t *Wexcl, uint64_t T, uint32
 int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t *mask,
                    Arena &arena);
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
-                uint32_t gb0, uint32_t gb1, uint32_t *sb_beta, double *sb_val, int64_t *sb_haa,
+                uint32_t gb0, uint32_t gb1, uint64_t *sb_key, double *sb_val, int64_t *sb_haa,
                 uint64_t stage_cap, double eps, unsigned long long *survivors, unsigned *err,
                 void **tiles_out, size_t *ntiles_out, std::vector<uint32_t> *oversized,
                 Arena &arena);
-int tile_sizes(const void *tiles, const std::vector<uint32_t> &list, std::vector<uint32_t> *sizes,
-               cudaStream_t s);
-int fused_big_tiles(const FusedCore &F, const void *tiles, const std::vector<uint32_t> &list,
-                    const uint32_t *sb_beta, const double *sb_val, const int64_t *sb_haa,
-                    uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
-                    unsigned long long *cand_count, unsigned long long cand_cap,
-                    unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
-                    uint64_t *nrec_out, Arena &arena);
+int tile_info(const void *tiles, const std::vector<uint32_t> &list, std::vector<uint32_t> *info,
+              cudaStream_t s);
+int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const uint64_t *sb_key,
+                    const double *sb_val, const int64_t *sb_haa, uint64_t stage_cap, double tau,
+                    uint64_t *cand_key, double *cand_score, unsigned long long *cand_count,
+                    unsigned long long cand_cap, unsigned long long *n_unique,
+                    unsigned long long *n_excluded, unsigned *err, uint64_t *nrec_out,
+                    Arena &arena);
 int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint32_t tile_end,
-                uint64_t P0, const uint32_t *sb_beta, const double *sb_val, const int64_t *sb_haa,
+                const uint64_t *sb_key, const double *sb_val, const int64_t *sb_haa,
                 uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
                 unsigned long long *cand_count, unsigned long long cand_cap,
-                unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *counter,
-                unsigned *err, Arena &arena);
+                unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
+                Arena &arena);
 size_t tile_capacity();
 int abs_min(const double *s, size_t n, double *host_min, Arena &arena);
 
@@ -578,7 +578,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     if (bmax == 0) {
       size_t fr = 0, tot = 0;
       ASCI_TRY_CUDA(cudaMemGetInfo(&fr, &tot));
-      bmax = (uint64_t)(fr / 2) / 28;  // staging record: 20 bytes
+      bmax = (uint64_t)(fr / 2) / 32;  // staging record: 24 bytes
       bmax = std::max<uint64_t>(bmax, 1ull << 20);
       bmax = std::min<uint64_t>(bmax, 1ull << 31);
     }
@@ -659,15 +659,15 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   const size_t cap_extra =
       std::max<size_t>(tile_capacity() * (size_t)sms * 16, std::min<uint64_t>(bcap, 1ull << 28));
   const size_t pool_cap = N + cap_extra;
-  uint32_t *sb_beta = nullptr;
+  uint64_t *sb_key = nullptr;
   double *sb_val = nullptr;
   int64_t *sb_haa = nullptr;
   uint64_t *pool_k[2] = {nullptr, nullptr};
   double *pool_s[2] = {nullptr, nullptr};
   unsigned long long *dcount = nullptr;  // [0] candidates, [1] unique, [2] excluded, [3] survivors
-  unsigned *tile_counter = nullptr, *derr2 = nullptr;
+  unsigned *derr2 = nullptr;
   if (bcap) {
-    ASCI_TRY(arena.alloc(&sb_beta, bcap));
+    ASCI_TRY(arena.alloc(&sb_key, bcap));
     ASCI_TRY(arena.alloc(&sb_val, bcap));
     ASCI_TRY(arena.alloc(&sb_haa, bcap));
     for (int i = 0; i < 2; ++i) {
@@ -675,7 +675,6 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
       ASCI_TRY(arena.alloc(&pool_s[i], pool_cap));
     }
     ASCI_TRY(arena.alloc(&dcount, 4));
-    ASCI_TRY(arena.alloc(&tile_counter, 1));
     ASCI_TRY(arena.alloc(&derr2, 1));
     ASCI_TRY_CUDA(cudaMemsetAsync(dcount, 0, 4 * sizeof(unsigned long long), stream));
     ASCI_TRY_CUDA(cudaMemsetAsync(derr2, 0, sizeof(unsigned), stream));
@@ -714,7 +713,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
                (unsigned long long)b.t0, (unsigned long long)b.t1, (unsigned long long)b.P0,
                (unsigned long long)b.P1, gg[0], gg[1] + 1);
     std::vector<uint32_t> oversized;
-    ASCI_TRY(fused_stage(F, b.t0, b.t1, b.P0, b.P1, gg[0], gg[1] + 1, sb_beta, sb_val, sb_haa,
+    ASCI_TRY(fused_stage(F, b.t0, b.t1, b.P0, b.P1, gg[0], gg[1] + 1, sb_key, sb_val, sb_haa,
                          bcap, o.eps_search, dcount + 3, derr2, &tiles, &ntiles, &oversized, ba));
     ASCI_TRACE("staged: tiles=%zu oversized=%zu", ntiles, oversized.size());
     tm.stop(&tl[2]);
@@ -734,9 +733,9 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
       }
       const size_t t1 = std::min(ntiles, t + room);
       ASCI_TRACE("cells: tiles [%zu,%zu) tau=%.6g pool=%zu", t, t1, tau, pool_n);
-      ASCI_TRY(fused_cells(F, tiles, (uint32_t)t, (uint32_t)t1, b.P0, sb_beta, sb_val, sb_haa,
-                           bcap, tau, pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1,
-                           dcount + 2, tile_counter, derr2, ba));
+      ASCI_TRY(fused_cells(F, tiles, (uint32_t)t, (uint32_t)t1, sb_key, sb_val, sb_haa, bcap, tau,
+                           pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1, dcount + 2,
+                           derr2, ba));
       unsigned long long c = 0;
       unsigned he = 0;
       ASCI_TRY_CUDA(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDefault, stream));
@@ -762,25 +761,24 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     // buckets too large for one tile: global sorts over as many of them as
     // the free candidate capacity allows (every record may become one)
     if (!oversized.empty()) {
-      std::vector<uint32_t> sizes;
-      ASCI_TRY(tile_sizes(tiles, oversized, &sizes, stream));
+      std::vector<uint32_t> info;  // (start, records, alpha) per oversized tile
+      ASCI_TRY(tile_info(tiles, oversized, &info, stream));
       size_t i = 0;
       while (i < oversized.size()) {
-        if ((uint64_t)(pool_cap - pool_n) < sizes[i]) {
+        if ((uint64_t)(pool_cap - pool_n) < info[3 * i + 1]) {
           tm.stop(&tl[5]);
           tm.start();
           ASCI_TRY(prune(ba));
           tm.stop(&tl[6]);
           tm.start();
-          if ((uint64_t)(pool_cap - pool_n) < sizes[i]) return ASCI_ENOMEM;
+          if ((uint64_t)(pool_cap - pool_n) < info[3 * i + 1]) return ASCI_ENOMEM;
         }
         uint64_t room = pool_cap - pool_n, total = 0;
         size_t j = i;
-        while (j < oversized.size() && total + sizes[j] <= room) total += sizes[j++];
-        std::vector<uint32_t> chunk(oversized.begin() + i, oversized.begin() + j);
+        while (j < oversized.size() && total + info[3 * j + 1] <= room) total += info[3 * j++ + 1];
         uint64_t nrec = 0;
-        ASCI_TRY(fused_big_tiles(F, tiles, chunk, sb_beta, sb_val, sb_haa, bcap, tau,
-                                 pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1,
+        ASCI_TRY(fused_big_tiles(F, info.data() + 3 * i, j - i, sb_key, sb_val, sb_haa, bcap,
+                                 tau, pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1,
                                  dcount + 2, derr2, &nrec, ba));
         unsigned long long c = 0;
         unsigned he = 0;
