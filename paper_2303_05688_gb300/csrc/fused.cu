@@ -81,7 +81,72 @@ __global__ void k_fx_tables(const double *h1, const double *eri, int n, int s, i
   }
 }
 
+// Largest single-excitation magnitude bound over (i, a):
+// |h_ia| + sum_k |(ia|kk) - (ik|ka)| + sum_k |(ia|kk)|.
+__global__ void k_fx_single_bound(const double *h1, const double *eri, int n, double *out) {
+  double m = 0;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, a = t % n;
+    double b = fabs(h1[t]);
+    for (int k = 0; k < n; ++k) {
+      const double iakk = eri[(((size_t)i * n + a) * n + k) * n + k];
+      const double ikka = eri[(((size_t)i * n + k) * n + k) * n + a];
+      b += fabs(iakk - ikka) + fabs(iakk);
+    }
+    m = fmax(m, b);
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0;
+    for (int i = 0; i < blockDim.x; ++i) r = fmax(r, sh[i]);
+    *out = r;
+  }
+}
+
+__global__ void k_fx_single_tables(const double *h1, const double *eri, int n, int s1,
+                                   int64_t *h1x, int64_t *ssx, int64_t *sox) {
+  const double sc = ldexp(1.0, s1);
+  const size_t n3 = (size_t)n * n * n;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n3;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t % n), ia = (int)(t / n), i = ia / n, a = ia % n;
+    const double iakk = eri[(((size_t)i * n + a) * n + k) * n + k];
+    const double ikka = eri[(((size_t)i * n + k) * n + k) * n + a];
+    ssx[t] = __double2ll_rn((iakk - ikka) * sc);
+    sox[t] = __double2ll_rn(iakk * sc);
+    if (k == 0) h1x[ia] = __double2ll_rn(h1[ia] * sc);
+  }
+}
+
 }  // namespace
+
+// x * 2^-s rounded to the nearest double (ties to even), by integer
+// operations only; x * 2^-s must lie in the normal range.
+__device__ __forceinline__ double fx64_to_double(int64_t x, int s) {
+  if (x == 0) return 0.0;
+  const uint64_t sign = x < 0 ? (1ull << 63) : 0ull;
+  const uint64_t u = x < 0 ? 0ull - (uint64_t)x : (uint64_t)x;
+  int P = 63 - __clzll((long long)u);  // leading bit
+  uint64_t mant;
+  if (P <= 52) {
+    mant = u << (52 - P);
+  } else {
+    const int sh = P - 52;
+    mant = u >> sh;
+    const uint64_t rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++P;
+      }
+    }
+  }
+  return __longlong_as_double(
+      (long long)(sign | ((uint64_t)(P - s + 1023) << 52) | (mant & ((1ull << 52) - 1ull))));
+}
 
 __device__ __forceinline__ int64_t fx_diag(const FxInts &X, uint32_t A, uint32_t B) {
   const int n = X.n;
@@ -174,16 +239,18 @@ constexpr unsigned kErrStage = 4u;      // a record position outside the staging
 constexpr unsigned kErrCore = 8u;       // a core index outside the core
 constexpr unsigned kErrAccum = 16u;     // a value outside the exact accumulator's range
 
-struct TileDesc {  // 24 bytes; npairs at byte offset 4 (read by the host)
+struct TileDesc {  // 32 bytes; npairs at byte offset 4 (read by the host)
   uint32_t start;   // first record in the batch staging buffer
   uint32_t npairs;  // records in the tile
   uint32_t g0;      // first group (global id)
   uint32_t ng;      // groups (packed tiles)
   uint32_t kind;
   uint32_t alpha;   // target alpha string (medium / bucket tiles)
+  uint32_t psi_lo;  // psi determinants that fall in the tile: [psi_lo, psi_hi) of
+  uint32_t psi_hi;  // the batch's tile-ordered psi list
 };
 
-static_assert(sizeof(TileDesc) == 24, "tile descriptor layout");
+static_assert(sizeof(TileDesc) == 32, "tile descriptor layout");
 
 // A screened-out record (Alg. 2's eps test) keeps its slot with a NaN value.
 // (Tested on the bits: NaN compares cost FP64 instructions, which are scarce.)
@@ -193,6 +260,29 @@ __device__ __forceinline__ bool is_dropped(double v) {
 __device__ __forceinline__ double drop_marker() {
   return __longlong_as_double(0x7ff8000000000000ll);
 }
+// Sum of four values that depends only on their multiset: they are ordered by
+// magnitude (then sign) with a sorting network on the bits and added from the
+// smallest.  Pad with +0.0 for fewer values.
+__device__ __forceinline__ uint64_t mag_order(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  return (b << 1) | (b >> 63);
+}
+__device__ __forceinline__ void order2(double &x, double &y) {
+  if (mag_order(y) < mag_order(x)) {
+    const double t = x;
+    x = y;
+    y = t;
+  }
+}
+__device__ __forceinline__ double sum4_ordered(double a, double b, double c, double d) {
+  order2(a, b);
+  order2(c, d);
+  order2(a, c);
+  order2(b, d);
+  order2(b, c);
+  return ((a + b) + c) + d;
+}
+
 // x with its sign flipped when flip is 1 (an integer operation on the bits).
 __device__ __forceinline__ double flip_sign(double x, uint32_t flip) {
   return __longlong_as_double(__double_as_longlong(x) ^ ((long long)(flip & 1u) << 63));
@@ -270,6 +360,7 @@ __global__ void k_tile_write(uint32_t gb0, uint32_t ng, uint64_t P0, uint64_t Pe
       d.ng = 1;
       d.kind = kTileMedium;
       d.alpha = g_alpha[g];
+      d.psi_lo = d.psi_hi = 0;
       tiles[tile_base[i]] = d;
     } else {
       const uint32_t cb = cellbase[i];
@@ -281,6 +372,7 @@ __global__ void k_tile_write(uint32_t gb0, uint32_t ng, uint64_t P0, uint64_t Pe
         d.ng = 1;
         d.kind = kTileBucket;
         d.alpha = g_alpha[g];
+        d.psi_lo = d.psi_hi = 0;
         if (d.npairs > (uint32_t)kCap) {
           // too large for one tile on chip: reduced through the global sort
           const unsigned slot = atomicAdd(n_over, 1u);
@@ -299,23 +391,40 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t beta, uint32_t nb) {
   return (uint32_t)(((uint64_t)(beta * 0x9E3779B1u) * nb) >> 32);
 }
 
-constexpr int kEmitThreads = 256;
-constexpr int kEmitPer = 4;
-constexpr int kEmitTile = kEmitThreads * kEmitPer;  // pairs per emission CTA
+// ----------------------------------------------------------- emission ---
+// The pairs of a batch are emitted in two kinds of work units.
+//  * Determinant runs: an item (core alpha group k, alpha operation o) whose
+//    o is the identity or an alpha single, applied to one core determinant of
+//    the group.  For o = 0 the run holds the determinant's beta singles and
+//    beta doubles (sb + dbb pairs); for an alpha single, that single alone
+//    and combined with each beta single (1 + sb pairs).  One warp walks a
+//    run: lane L holds the L-th occupied and the L-th virtual beta orbital of
+//    the determinant and the diagonal terms that depend on them, and each
+//    pair fetches its orbitals and terms with shuffles.
+//  * Alpha doubles: one pair per core determinant of the group.  These items
+//    are laid out flat and each lane takes one pair; the operation, its
+//    matrix element and the determinant-independent part of the diagonal
+//    change are computed once per item.
+// A pair keeps the position p = Wexcl[t] + m * npd + e of the item order
+// (t: item, m: determinant in the group, e: pair in the run), so classes that
+// fit a tile are staged in place and big classes go through bucket counters.
+
+constexpr int kRunThreads = 256;
+constexpr int kPairTab = 496;  // C(32, 2): unranked index pairs
+constexpr int kAdThreads = 256;
+constexpr int kAdTile = 1024;  // alpha-double pairs per CTA step
 
 struct EmitArgs {
   DevInts I;
   FxInts X;
   ExcCounts E;
-  FastDiv dv_va, dv_vb, dv_npd0, dv_npd1, dv_pa_p, dv_pb_p;
+  FastDiv dv_va, dv_vb, dv_pa_p, dv_pb_p;
+  uint32_t npd0, npd1;        // pairs per determinant for o = 0 and for an alpha single
   const uint64_t *items, *Wexcl;
   const uint32_t *item_group;
-  const uint32_t *tile_item;  // first item of each emission tile (+1 entry)
-  const uint32_t *tile_list;  // count mode: emission tiles overlapping big classes
-  uint64_t t0, t1, P0, P1;
-  uint32_t ntl;  // emission tiles to visit (listed tiles in count mode)
+  uint64_t t0, P0;
   int opbits;
-  const uint32_t *grp_alpha, *grp_start, *core_beta;
+  const uint32_t *grp_alpha, *grp_start, *grp_count, *core_beta;
   const double *core_c;
   const int64_t *Dx, *Fa, *Fb;
   uint32_t gb0;
@@ -323,7 +432,14 @@ struct EmitArgs {
   uint32_t *cnt;              // count mode
   const uint32_t *cell_pos0;  // emit mode
   uint32_t *fill;             // emit mode
-  const uint32_t *g_alpha;  // target alpha string of each class
+  const uint64_t *runs;       // (item - t0) << 32 | determinant in the group
+  uint64_t nruns;
+  const uint32_t *adl;        // alpha-double items (item - t0)
+  const uint32_t *ad_off;     // first flat pair of each (exclusive prefix)
+  uint32_t nad, ad_total;
+  const uint32_t *opinfo;     // per batch item: alpha single i | a << 5 | parity << 10
+  const uint32_t *ad_tile_item;  // first alpha-double item of each CTA step
+  uint32_t ad_tiles;
   uint64_t *sb_key;
   double *sb_val;
   int64_t *sb_haa;
@@ -335,40 +451,6 @@ struct EmitArgs {
   uint32_t ncore;
   unsigned *err;
 };
-
-// First item of each emission tile: the last item whose first pair is at or
-// before the tile's first pair.
-__global__ void k_tile_items(const uint64_t *Wexcl, uint64_t t0, uint64_t t1, uint64_t P0,
-                             uint64_t P1, uint32_t ntiles, uint32_t *tile_item) {
-  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= ntiles;
-       b += gridDim.x * blockDim.x) {
-    uint64_t p = P0 + (uint64_t)b * kEmitTile;
-    if (p >= P1) p = P1 - 1;
-    uint64_t lo = t0, hi = t1 - 1;
-    while (lo < hi) {
-      const uint64_t mid = (lo + hi + 1) >> 1;
-      if (Wexcl[mid] <= p) lo = mid; else hi = mid - 1;
-    }
-    tile_item[b] = (uint32_t)(lo - t0);
-  }
-}
-
-// Emission tiles that hold pairs of big (hash-bucketed) classes.
-__global__ void k_big_tile_flags(uint32_t gb0, uint32_t ng, uint64_t P0, uint64_t Pend,
-                                 const uint64_t *g_P0, const uint32_t *kind, uint32_t *flag) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
-    if (kind[i] != kTileBucket) continue;
-    const uint32_t g = gb0 + i;
-    const uint64_t a = g_P0[g] - P0, e = ((i + 1 < ng) ? g_P0[g + 1] : Pend) - P0;
-    for (uint64_t b = a / kEmitTile; b <= (e - 1) / kEmitTile; ++b) flag[b] = 1u;
-  }
-}
-
-__global__ void k_list_flags(const uint32_t *flag, const uint32_t *pos, uint32_t n,
-                             uint32_t *list) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    if (flag[i]) list[pos[i]] = i;
-}
 
 __device__ __forceinline__ void dec_single(uint32_t s, uint32_t virt, uint32_t idx,
                                            const FastDiv &dv, int *i, int *a) {
@@ -395,228 +477,437 @@ __device__ __forceinline__ int par_double(uint32_t s, int i, int j, int a, int b
   return p1 ^ single_parity(s1, j, b);
 }
 
-__device__ __forceinline__ double single_val(const DevInts &I, uint32_t s, uint32_t o, int i,
+// Single excitation i -> a of the string s (the other spin's string o) in
+// fixed point (multiples of 2^-s1): h_ia plus, over the occupied orbitals k,
+// (ia|kk) - (ik|ka) for k of the same spin and (ia|kk) for k of the other.
+__device__ __forceinline__ int64_t fx_single(const FxInts &X, uint32_t s, uint32_t o, int i,
                                              int a) {
-  const int n = I.n;
-  const double *ss = I.s_same + ((size_t)i * n + a) * n;
-  const double *so = I.s_opp + ((size_t)i * n + a) * n;
-  double v = I.h1[i * n + a];
+  const int n = X.n;
+  const int64_t *ss = X.ssx + ((size_t)i * n + a) * n;
+  const int64_t *so = X.sox + ((size_t)i * n + a) * n;
+  int64_t v = X.h1x[i * n + a];
   for (uint32_t m = s; m; m &= m - 1) v += ss[__ffs(m) - 1];
   for (uint32_t m = o; m; m &= m - 1) v += so[__ffs(m) - 1];
   return v;
 }
 
-__device__ __forceinline__ double eri_at(const double *t, int n, int i, int a, int j, int b) {
-  return t[(((size_t)i * n + a) * n + j) * n + b];
+__device__ __forceinline__ int64_t shfl64(int64_t x, int src) {
+  return (int64_t)__shfl_sync(0xffffffffu, (long long)x, src);
 }
 
-// change of the diagonal for same-spin double i,j -> a,b with Fock-like F
-__device__ __forceinline__ int64_t dd_same(const int64_t *F, const int64_t *jk, int n, int i,
-                                           int j, int a, int b) {
-  return F[a] + F[b] - F[i] - F[j] + jk[i * n + j] + jk[a * n + b] - jk[a * n + i] -
-         jk[a * n + j] - jk[b * n + i] - jk[b * n + j];
+// Staging position of one pair: in place for classes that fit a tile, else
+// the next free slot of its hash-bucket cell (warp-aggregated counters).  In
+// count mode only the cell counters advance.  Returns false in count mode or
+// for an idle lane.
+template <int MODE>
+__device__ __forceinline__ bool pair_position(const EmitArgs &A, bool big, bool valid,
+                                              uint32_t cell, uint64_t p, uint32_t *pos) {
+  const int lane = threadIdx.x & 31;
+  if (big) {  // warp-uniform
+    const uint32_t peers = __match_any_sync(0xffffffffu, valid ? cell : 0xffffffffu);
+    const int leader = __ffs(peers) - 1;
+    if (MODE == 0) {
+      if (valid && lane == leader) atomicAdd(&A.cnt[cell], (uint32_t)__popc(peers));
+      return false;
+    }
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&A.fill[cell], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    *pos = A.cell_pos0[cell] + base + __popc(peers & ((1u << lane) - 1u));
+  } else {
+    *pos = (uint32_t)(p - A.P0);
+  }
+  return MODE == 1 && valid;
+}
+
+template <bool EPS>
+__device__ __forceinline__ void write_record(const EmitArgs &A, uint32_t pos, uint64_t key,
+                                             double v, int64_t haa, bool *kept) {
+  if (EPS) {
+    // |v / (E0 - H_ii)| > eps, without a division
+    const double den = __ll2double_rn(A.E0_x - haa) * A.inv_scale;
+    if (!(fabs(v) > A.eps * fabs(den))) v = drop_marker();
+    *kept = !is_dropped(v);
+  }
+  if (pos < A.stage_cap) {
+    A.sb_key[pos] = key;
+    A.sb_val[pos] = v;
+    A.sb_haa[pos] = haa;
+  } else {
+    atomicOr(A.err, kErrStage);
+  }
 }
 
 // MODE 0 counts the bucket sizes of big classes, MODE 1 emits the records;
 // EPS compiles Alg. 2's screen in (eps > 0).
 template <int MODE, bool EPS>
-__global__ void __launch_bounds__(kEmitThreads) k_emit2(EmitArgs A) {
-  extern __shared__ int64_t s_fx[];  // jk[n*n], jj[n*n]
-  __shared__ uint64_t sW[kEmitTile + 1];
-  __shared__ uint64_t sIt[kEmitTile + 1];
-  __shared__ uint32_t sG[kEmitTile + 1];
-  __shared__ uint32_t sOp[kEmitTile + 1];  // decoded alpha operation of each item
-  __shared__ uint32_t sTA[kEmitTile + 1];  // target alpha string of each item
+__global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
+  extern __shared__ int64_t s_fx[];  // emit mode: jk[n*n], jj[n*n]
+  __shared__ uint16_t s_pair[kPairTab];
   const int n = A.I.n;
   int64_t *s_jk = s_fx, *s_jj = s_fx + n * n;
   if (MODE == 1)
-    for (int t = threadIdx.x; t < n * n; t += kEmitThreads) {
+    for (int t = threadIdx.x; t < n * n; t += kRunThreads) {
       s_jk[t] = A.X.jk[t];
       s_jj[t] = A.X.jj[t];
     }
+  for (int r = threadIdx.x; r < kPairTab; r += kRunThreads) {
+    int x, y;
+    unrank_pair((uint32_t)r, &x, &y);
+    s_pair[r] = (uint16_t)(x | (y << 8));
+  }
+  __syncthreads();
   const uint32_t full = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
   const uint32_t omask = (1u << A.opbits) - 1u;
   const int lane = threadIdx.x & 31;
-  // persistent: the integral tables above are loaded once per CTA
+  const uint32_t sb = A.E.sb, vb = A.E.vb;
+  const uint64_t nw = ((uint64_t)gridDim.x * kRunThreads) >> 5;
 #pragma unroll 1
-  for (uint32_t ti = blockIdx.x; ti < A.ntl; ti += gridDim.x) {
-  const uint32_t tile = MODE == 0 ? A.tile_list[ti] : ti;
-  const uint64_t pb = A.P0 + (uint64_t)tile * kEmitTile;
-  const uint64_t pe = (pb + kEmitTile < A.P1) ? pb + kEmitTile : A.P1;
-  const uint64_t ta = A.t0 + A.tile_item[tile];
-  uint64_t tl = A.t0 + A.tile_item[tile + 1];
-  if (tl >= A.t1) tl = A.t1 - 1;
-  const int nspan = (int)(tl - ta + 1);  // <= kEmitTile + 1: every item has >= 1 pair
-  for (int i = threadIdx.x; i < nspan; i += kEmitThreads) {
-    const uint64_t it = A.items[ta + i];
-    sIt[i] = it;
-    sW[i] = A.Wexcl[ta + i];
-    sG[i] = A.item_group[ta + i];
-    if (MODE == 1) sTA[i] = A.g_alpha[sG[i]];
-    // alpha operation of the item, decoded once: orbitals (5 bits each) and parity
+  for (uint64_t r = ((uint64_t)blockIdx.x * kRunThreads + threadIdx.x) >> 5; r < A.nruns;
+       r += nw) {
+    const uint64_t run = A.runs[r];
+    const uint64_t t = A.t0 + (run >> 32);
+    const uint32_t m = (uint32_t)run;
+    const uint64_t it = A.items[t];
     const uint32_t k = (uint32_t)it >> A.opbits, o = (uint32_t)it & omask;
-    uint32_t op = 0;
-    if (MODE == 1 && o != 0) {
-      const uint32_t Ak = A.grp_alpha[k], va = ~Ak & full;
-      int ia, aa, ja, ba;
-      if (o <= A.E.sa) {
-        dec_single(Ak, va, o - 1, A.dv_va, &ia, &aa);
-        op = (uint32_t)ia | ((uint32_t)aa << 5) | ((uint32_t)single_parity(Ak, ia, aa) << 20);
-      } else {
-        dec_double(Ak, va, o - 1 - A.E.sa, A.dv_pa_p, &ia, &ja, &aa, &ba);
-        op = (uint32_t)ia | ((uint32_t)aa << 5) | ((uint32_t)ja << 10) | ((uint32_t)ba << 15) |
-             ((uint32_t)par_double(Ak, ia, ja, aa, ba) << 20);
+    const uint32_t gi = A.item_group[t] - A.gb0;
+    const bool big = A.kind[gi] == kTileBucket;
+    if (MODE == 0 && !big) continue;
+    const uint32_t jdx = A.grp_start[k] + m;
+    if (jdx >= A.ncore) {
+      if (lane == 0) atomicOr(A.err, kErrCore);
+      continue;
+    }
+    const uint32_t talpha = (uint32_t)(it >> 32);
+    const uint32_t Ak = A.grp_alpha[k], B = A.core_beta[jdx];
+    const uint32_t npd = o == 0 ? A.npd0 : A.npd1;
+    const uint64_t p0 = A.Wexcl[t] + (uint64_t)m * npd;
+    const uint32_t cell0 = big ? A.cellbase[gi] : 0u, nbk = big ? A.nb[gi] : 1u;
+    // lane L: the L-th occupied and the L-th virtual beta orbital of B
+    const int occL = lane < (int)A.E.nb ? nth_set_bit(B, lane) : 0;
+    const int virL = lane < (int)vb ? nth_set_bit(~B & full, lane) : 0;
+    // emit mode: coefficient, alpha part of the diagonal change, and per lane
+    // the diagonal terms of removing occL / adding virL (Fock-like diagonal of
+    // B, plus the alpha-beta Coulomb change when o is an alpha single)
+    double c = 0.0;
+    int64_t base_x = 0, Vo = 0, Vv = 0;
+    int ia = 0, aa = 0;
+    uint32_t pa = 0;
+    double h0 = 0.0;  // the alpha single alone
+    const double *erow = A.I.eri;
+    if (MODE == 1) {
+      c = A.core_c[jdx];
+      base_x = A.Dx[jdx];
+      const int64_t *Fb = A.Fb + (size_t)jdx * n;
+      Vo = Fb[occL];
+      Vv = Fb[virL];
+      if (o != 0) {
+        const uint32_t oi = A.opinfo[t - A.t0];
+        ia = (int)(oi & 31u);
+        aa = (int)((oi >> 5) & 31u);
+        pa = (oi >> 10) & 1u;
+        // its matrix element, summed across the warp: lane L adds the terms of
+        // the L-th occupied alpha and beta orbitals
+        const int occA = lane < (int)A.E.na ? nth_set_bit(Ak, lane) : 0;
+        const size_t row = ((size_t)ia * n + aa) * n;
+        int64_t part = (lane < (int)A.E.na ? A.X.ssx[row + occA] : 0) +
+                       (lane < (int)A.E.nb ? A.X.sox[row + occL] : 0);
+#pragma unroll
+        for (int d = 16; d; d >>= 1) part += (int64_t)__shfl_xor_sync(0xffffffffu, (long long)part, d);
+        h0 = flip_sign(fx64_to_double(part + A.X.h1x[ia * n + aa], A.X.s1), pa);
+        const int64_t *Fa = A.Fa + (size_t)jdx * n;
+        base_x += Fa[aa] - Fa[ia] - s_jk[aa * n + ia];
+        Vo += s_jj[aa * n + occL] - s_jj[ia * n + occL];
+        Vv += s_jj[aa * n + virL] - s_jj[ia * n + virL];
+        erow = A.I.eri + ((size_t)ia * n + aa) * n * n;
       }
     }
-    sOp[i] = op;
-  }
-  __syncthreads();
 #pragma unroll 1
-  for (int r = 0; r < kEmitPer; ++r) {
-    const uint64_t p = pb + (uint64_t)r * kEmitThreads + threadIdx.x;
-    const bool valid = p < pe;
-    uint32_t cell = 0xffffffffu;  // bucket cell of a big class, else none
-    uint32_t tb = 0, jdx = 0, talpha = 0;
-    double h = 0.0;
-    int64_t dh = 0;
-    bool big = false;
-    // item of pair p: lane 0 searches the whole span, the other lanes only
-    // the next 32 items (consecutive lanes hold consecutive pairs)
-    int lo0 = 0;
-    {
-      const uint64_t p0 = pb + (uint64_t)r * kEmitThreads + (threadIdx.x & ~31u);
-      if (lane == 0) {
-        int lo = 0, hi = nspan - 1;
-        while (lo < hi) {
-          int mid = (lo + hi + 1) >> 1;
-          if (sW[mid] <= p0) lo = mid; else hi = mid - 1;
-        }
-        lo0 = lo;
-      }
-      lo0 = __shfl_sync(0xffffffffu, lo0, 0);
-    }
-    if (valid) {
-      int lo = lo0, hi = (lo0 + 32 < nspan - 1) ? lo0 + 32 : nspan - 1;
-      while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (sW[mid] <= p) lo = mid; else hi = mid - 1;
-      }
-      const uint64_t it = sIt[lo];
-      const uint32_t aop = sOp[lo];
-      const uint32_t q = (uint32_t)(p - sW[lo]);
-      const uint32_t gi = sG[lo] - A.gb0;
-      if (MODE == 1) talpha = sTA[lo];
-      big = A.kind[gi] == kTileBucket;
-      const uint32_t k = (uint32_t)it >> A.opbits, o = (uint32_t)it & omask;
-      const uint32_t Ak = A.grp_alpha[k];
-      if (MODE == 0 && !big) {
-        // nothing to count
-      } else if (o == 0) {
-        const uint32_t m = A.dv_npd0.div(q), e = q - m * A.dv_npd0.d;
-        jdx = A.grp_start[k] + m;
-        const uint32_t B = A.core_beta[jdx], vb = ~B & full;
-        int i, j2, a, b;
-        if (e < A.E.sb) {
-          dec_single(B, vb, e, A.dv_vb, &i, &a);
-          tb = B ^ (1u << i) ^ (1u << a);
-          if (MODE == 1) {
-            h = flip_sign(single_val(A.I, B, Ak, i, a), (uint32_t)single_parity(B, i, a));
-            const int64_t *F = A.Fb + (size_t)jdx * n;
-            dh = F[a] - F[i] - s_jk[a * n + i];
-          }
-        } else {
-          dec_double(B, vb, e - A.E.sb, A.dv_pb_p, &i, &j2, &a, &b);
-          tb = B ^ (1u << i) ^ (1u << j2) ^ (1u << a) ^ (1u << b);
-          if (MODE == 1) {
-            h = flip_sign(eri_at(A.I.asym, n, i, a, j2, b), (uint32_t)par_double(B, i, j2, a, b));
-            dh = dd_same(A.Fb + (size_t)jdx * n, s_jk, n, i, j2, a, b);
-          }
-        }
-      } else if (o <= A.E.sa) {
-        const uint32_t m = A.dv_npd1.div(q), e = q - m * A.dv_npd1.d;
-        jdx = A.grp_start[k] + m;
-        const uint32_t B = A.core_beta[jdx];
-        int i = 0, a = 0;
-        if (MODE == 1) {
-          i = (int)(aop & 31u);
-          a = (int)((aop >> 5) & 31u);
-        }
-        const int pa = (int)((aop >> 20) & 1u);
-        if (e == 0) {
-          tb = B;
-          if (MODE == 1) {
-            h = flip_sign(single_val(A.I, Ak, B, i, a), (uint32_t)pa);
-            const int64_t *F = A.Fa + (size_t)jdx * n;
-            dh = F[a] - F[i] - s_jk[a * n + i];
-          }
-        } else {
-          const uint32_t vb = ~B & full;
-          int j2, b;
-          dec_single(B, vb, e - 1, A.dv_vb, &j2, &b);
-          tb = B ^ (1u << j2) ^ (1u << b);
-          if (MODE == 1) {
-            h = flip_sign(eri_at(A.I.eri, n, i, a, j2, b), (uint32_t)(pa ^ single_parity(B, j2, b)));
-            const int64_t *Fa = A.Fa + (size_t)jdx * n, *Fb = A.Fb + (size_t)jdx * n;
-            dh = Fa[a] - Fa[i] - s_jk[a * n + i] + Fb[b] - Fb[j2] - s_jk[b * n + j2] +
-                 s_jj[a * n + b] - s_jj[a * n + j2] - s_jj[i * n + b] + s_jj[i * n + j2];
-          }
-        }
-      } else {
-        jdx = A.grp_start[k] + q;
-        tb = A.core_beta[jdx];
-        if (MODE == 1) {
-          const int i = (int)(aop & 31u), a = (int)((aop >> 5) & 31u);
-          const int j2 = (int)((aop >> 10) & 31u), b = (int)((aop >> 15) & 31u);
-          h = flip_sign(eri_at(A.I.asym, n, i, a, j2, b), aop >> 20);
-          dh = dd_same(A.Fa + (size_t)jdx * n, s_jk, n, i, j2, a, b);
-        }
-      }
-      if (big) cell = A.cellbase[gi] + bucket_of(tb, A.nb[gi]);
-    }
-    // warp-aggregated bucket counters (one atomic per distinct cell per warp)
-    const bool any_big = __any_sync(0xffffffffu, cell != 0xffffffffu);
-    const uint32_t peers = any_big ? __match_any_sync(0xffffffffu, cell) : 0xffffffffu;
-    const int leader = __ffs(peers) - 1;
-    if (MODE == 0) {
-      if (cell != 0xffffffffu && lane == leader) atomicAdd(&A.cnt[cell], (uint32_t)__popc(peers));
-    } else {
-      uint32_t base = 0;
-      if (cell != 0xffffffffu && lane == leader) base = atomicAdd(&A.fill[cell], (uint32_t)__popc(peers));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      uint32_t kept = 0;
+    for (uint32_t e0 = 0; e0 < npd; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      const bool valid = e < npd;
+      // the beta operation as positions in the occupied / virtual lists
+      int op = 0;  // 0: none (the alpha single alone), 1: beta single, 2: beta double
+      uint32_t h1 = 0, h2 = 0, p1 = 0, p2 = 0;
       if (valid) {
-        uint32_t pos;
-        if (cell != 0xffffffffu)
-          pos = A.cell_pos0[cell] + base + __popc(peers & ((1u << lane) - 1u));
-        else
-          pos = (uint32_t)(p - A.P0);
-        if (jdx >= A.ncore) {
-          atomicOr(A.err, kErrCore);
-          jdx = 0;
-        }
-        double v = h * A.core_c[jdx];
-        const int64_t haa = A.Dx[jdx] + dh;
-        if (EPS) {
-          // |v / (E0 - H_ii)| > eps, without a division
-          const double den = __ll2double_rn(A.E0_x - haa) * A.inv_scale;
-          if (!(fabs(v) > A.eps * fabs(den))) v = drop_marker();
-          kept = !is_dropped(v);
-        }
-        if (pos < A.stage_cap) {
-          A.sb_key[pos] = pack_key(talpha, tb);
-          A.sb_val[pos] = v;
-          A.sb_haa[pos] = haa;
-        } else {
-          atomicOr(A.err, kErrStage);
+        if (o == 0 && e >= sb) {
+          op = 2;
+          const uint32_t f = e - sb, q = A.dv_pb_p.div(f);
+          const uint32_t hp = s_pair[q], pp = s_pair[f - q * A.dv_pb_p.d];
+          h1 = hp & 0xffu;
+          h2 = hp >> 8;
+          p1 = pp & 0xffu;
+          p2 = pp >> 8;
+        } else if (o == 0 || e > 0) {
+          op = 1;
+          const uint32_t f = o == 0 ? e : e - 1, q = A.dv_vb.div(f);
+          h1 = q;
+          p1 = f - q * vb;
         }
       }
+      const int bi = __shfl_sync(0xffffffffu, occL, (int)h1);
+      const int bj = __shfl_sync(0xffffffffu, occL, (int)h2);
+      const int ba = __shfl_sync(0xffffffffu, virL, (int)p1);
+      const int bb = __shfl_sync(0xffffffffu, virL, (int)p2);
+      uint32_t tb = B;
+      if (op == 1) tb ^= (1u << bi) | (1u << ba);
+      if (op == 2) tb ^= (1u << bi) | (1u << bj) | (1u << ba) | (1u << bb);
+      // the staging slot first, so that its atomic overlaps the integral loads
+      const uint32_t cell = big ? cell0 + bucket_of(tb, nbk) : 0u;
+      uint32_t pos = 0;
+      const bool wr = pair_position<MODE>(A, big, valid, cell, p0 + e, &pos);
+      double h = 0.0;
+      int64_t dh = 0;
+      if (MODE == 1) {
+        const int64_t vo1 = shfl64(Vo, (int)h1), vv1 = shfl64(Vv, (int)p1);
+        int64_t vo2 = 0, vv2 = 0;
+        if (o == 0) {  // warp-uniform
+          vo2 = shfl64(Vo, (int)h2);
+          vv2 = shfl64(Vv, (int)p2);
+        }
+        if (op == 0) {
+          h = h0;
+        } else if (op == 1) {
+          if (o == 0)
+            h = flip_sign(fx64_to_double(fx_single(A.X, B, Ak, bi, ba), A.X.s1),
+                          (uint32_t)single_parity(B, bi, ba));
+          else
+            h = flip_sign(erow[bi * n + ba], pa ^ (uint32_t)single_parity(B, bi, ba));
+          dh = vv1 - vo1 - s_jk[ba * n + bi];
+        } else {
+          h = flip_sign(A.I.asym[(((size_t)bi * n + ba) * n + bj) * n + bb],
+                        (uint32_t)par_double(B, bi, bj, ba, bb));
+          dh = vv1 + vv2 - vo1 - vo2 + s_jk[bi * n + bj] + s_jk[ba * n + bb] - s_jk[ba * n + bi] -
+               s_jk[ba * n + bj] - s_jk[bb * n + bi] - s_jk[bb * n + bj];
+        }
+      }
+      bool kept = false;
+      if (wr) write_record<EPS>(A, pos, pack_key(talpha, tb), h * c, base_x + dh, &kept);
       if (EPS) {
         const uint32_t nk = __popc(__ballot_sync(0xffffffffu, kept));
         if (lane == 0 && nk) atomicAdd(A.survivors, (unsigned long long)nk);
       }
     }
   }
-  __syncthreads();  // the next tile overwrites the item arrays
+}
+
+// Alpha-double pairs, flat: CTA step s covers flat pairs [s * kAdTile, ...).
+template <int MODE, bool EPS>
+__global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
+  __shared__ uint32_t sF[kAdTile + 1];    // first flat pair of each item in the step
+  __shared__ uint64_t sW[kAdTile + 1];    // first pair of the item in the batch order
+  __shared__ uint32_t sG[kAdTile + 1];    // first core determinant of the item's group
+  __shared__ uint32_t sOrb[kAdTile + 1];  // i | a << 5 | j << 10 | b << 15
+  __shared__ uint32_t sTA[kAdTile + 1];   // target alpha string
+  __shared__ uint32_t sCls[kAdTile + 1];  // class (relative to the batch)
+  __shared__ double sH[kAdTile + 1];      // signed matrix element
+  __shared__ int64_t sD[kAdTile + 1];     // determinant-independent diagonal change
+  const int n = A.I.n;
+  const uint32_t full = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+  const uint32_t omask = (1u << A.opbits) - 1u;
+  const int lane = threadIdx.x & 31;
+#pragma unroll 1
+  for (uint32_t step = blockIdx.x; step < A.ad_tiles; step += gridDim.x) {
+    const uint32_t fb = step * kAdTile;
+    const uint32_t fe = fb + kAdTile < A.ad_total ? fb + kAdTile : A.ad_total;
+    const uint32_t ja = A.ad_tile_item[step];
+    uint32_t jl = A.ad_tile_item[step + 1];
+    if (jl >= A.nad) jl = A.nad - 1;
+    const int nspan = (int)(jl - ja + 1);  // <= kAdTile + 1: every item has >= 1 pair
+    for (int i = threadIdx.x; i < nspan; i += kAdThreads) {
+      const uint64_t t = A.t0 + A.adl[ja + i];
+      const uint64_t it = A.items[t];
+      const uint32_t k = (uint32_t)it >> A.opbits, o = (uint32_t)it & omask;
+      sF[i] = A.ad_off[ja + i];
+      sW[i] = A.Wexcl[t];
+      sG[i] = A.grp_start[k];
+      sTA[i] = (uint32_t)(it >> 32);
+      sCls[i] = A.item_group[t] - A.gb0;
+      if (MODE == 1) {
+        const uint32_t Ak = A.grp_alpha[k];
+        int ia, ja2, aa, ba;
+        dec_double(Ak, ~Ak & full, o - 1 - A.E.sa, A.dv_pa_p, &ia, &ja2, &aa, &ba);
+        sOrb[i] = (uint32_t)ia | ((uint32_t)aa << 5) | ((uint32_t)ja2 << 10) | ((uint32_t)ba << 15);
+        sH[i] = flip_sign(A.I.asym[(((size_t)ia * n + aa) * n + ja2) * n + ba],
+                          (uint32_t)par_double(Ak, ia, ja2, aa, ba));
+        const int64_t *jk = A.X.jk;
+        sD[i] = jk[ia * n + ja2] + jk[aa * n + ba] - jk[aa * n + ia] - jk[aa * n + ja2] -
+                jk[ba * n + ia] - jk[ba * n + ja2];
+      }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (uint32_t f0 = fb + (threadIdx.x & ~31u); f0 < fe; f0 += kAdThreads) {
+      const uint32_t f = f0 + lane;
+      const bool valid = f < fe;
+      // item of flat pair f: lane 0 searches the span, the others the next 32 items
+      int lo0 = 0;
+      if (lane == 0) {
+        int lo = 0, hi = nspan - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (sF[mid] <= f0) lo = mid; else hi = mid - 1;
+        }
+        lo0 = lo;
+      }
+      lo0 = __shfl_sync(0xffffffffu, lo0, 0);
+      int lo = lo0;
+      if (valid) {
+        int hi = (lo0 + 32 < nspan - 1) ? lo0 + 32 : nspan - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (sF[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+      }
+      const uint32_t q = valid ? f - sF[lo] : 0u;
+      uint32_t jdx = sG[lo] + q;
+      const uint32_t gi = sCls[lo];
+      const bool bigl = valid && A.kind[gi] == kTileBucket;
+      const bool big = __any_sync(0xffffffffu, bigl);
+      if (MODE == 0 && !big) continue;
+      if (valid && jdx >= A.ncore) {
+        atomicOr(A.err, kErrCore);
+        jdx = 0;
+      }
+      const uint32_t B = valid ? A.core_beta[jdx] : 0u;
+      // lanes of one warp may straddle classes of both kinds: position per lane
+      uint32_t pos = 0;
+      bool emit = false;
+      if (big) {
+        const uint32_t cell = bigl ? A.cellbase[gi] + bucket_of(B, A.nb[gi]) : 0u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, bigl ? cell : 0xffffffffu);
+        const int leader = __ffs(peers) - 1;
+        if (MODE == 0) {
+          if (bigl && lane == leader) atomicAdd(&A.cnt[cell], (uint32_t)__popc(peers));
+          continue;
+        }
+        uint32_t base = 0;
+        if (bigl && lane == leader) base = atomicAdd(&A.fill[cell], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        pos = bigl ? A.cell_pos0[cell] + base + __popc(peers & ((1u << lane) - 1u))
+                   : (uint32_t)(sW[lo] + q - A.P0);
+      } else {
+        pos = (uint32_t)(sW[lo] + q - A.P0);
+      }
+      emit = valid;
+      bool kept = false;
+      if (MODE == 1 && emit) {
+        const uint32_t ob = sOrb[lo];
+        const int64_t *Fa = A.Fa + (size_t)jdx * n;
+        const int64_t dh = sD[lo] + Fa[(ob >> 5) & 31u] + Fa[(ob >> 15) & 31u] - Fa[ob & 31u] -
+                           Fa[(ob >> 10) & 31u];
+        write_record<EPS>(A, pos, pack_key(sTA[lo], B), sH[lo] * A.core_c[jdx], A.Dx[jdx] + dh,
+                          &kept);
+      }
+      if (EPS) {
+        const uint32_t nk = __popc(__ballot_sync(0xffffffffu, kept));
+        if (lane == 0 && nk) atomicAdd(A.survivors, (unsigned long long)nk);
+      }
+    }
+    __syncthreads();  // the next step overwrites the item arrays
+  }
+}
+
+// Per item of the batch: determinant runs (o = 0 or an alpha single) and the
+// alpha-double flag.
+__global__ void k_batch_counts(const uint64_t *items, uint64_t t0, uint64_t nt, int opbits,
+                               uint32_t sa, const uint32_t *grp_count, uint32_t *rcnt,
+                               uint32_t *adf) {
+  const uint32_t omask = (1u << opbits) - 1u;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nt;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t lo = (uint32_t)items[t0 + i];
+    const uint32_t k = lo >> opbits, o = lo & omask;
+    rcnt[i] = o <= sa ? grp_count[k] : 0u;
+    adf[i] = o > sa ? 1u : 0u;
+  }
+}
+
+__global__ void k_batch_lists(const uint64_t *items, uint64_t t0, uint64_t nt, int opbits,
+                              uint32_t sa, const uint32_t *grp_count, const uint32_t *rcnt,
+                              const uint32_t *roff, const uint32_t *adpos, uint64_t *runs,
+                              uint32_t *adl, uint32_t *adw, const uint32_t *grp_alpha, int n,
+                              FastDiv dv_va, uint32_t *opinfo) {
+  const uint32_t omask = (1u << opbits) - 1u;
+  const uint32_t full = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nt;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t lo = (uint32_t)items[t0 + i];
+    const uint32_t k = lo >> opbits, o = lo & omask;
+    if (o <= sa) {
+      for (uint32_t m = 0; m < rcnt[i]; ++m) runs[(uint64_t)roff[i] + m] = (i << 32) | m;
+      uint32_t oi = 0;
+      if (o != 0) {
+        const uint32_t Ak = grp_alpha[k];
+        int ia, aa;
+        dec_single(Ak, ~Ak & full, o - 1, dv_va, &ia, &aa);
+        oi = (uint32_t)ia | ((uint32_t)aa << 5) | ((uint32_t)single_parity(Ak, ia, aa) << 10);
+      }
+      opinfo[i] = oi;
+    } else {
+      adl[adpos[i]] = (uint32_t)i;
+      adw[adpos[i]] = grp_count[k];
+    }
+  }
+}
+
+// Tile of each psi determinant whose alpha string is a class of the batch
+// (classes are in ascending alpha order): key (tile << 32 | psi index), else
+// all ones.
+__global__ void k_psi_route(const uint64_t *psi_keys, size_t npsi, const uint32_t *g_alpha,
+                            uint32_t gb0, uint32_t ng, const uint32_t *kind, const uint32_t *nb,
+                            const uint64_t *Ws, const uint32_t *Ns, const uint32_t *tile_base,
+                            uint64_t *out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npsi;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t key = psi_keys[i];
+    const uint32_t a = key_alpha(key), b = (uint32_t)(key >> 32);
+    uint32_t lo = 0, hi = ng;  // first class with alpha >= a
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (g_alpha[gb0 + mid] < a) lo = mid + 1; else hi = mid;
+    }
+    uint64_t r = ~0ull;
+    if (lo < ng && g_alpha[gb0 + lo] == a) {
+      const uint32_t k = kind[lo];
+      uint32_t t;
+      if (k == kTilePacked) t = packed_start(lo, kind, Ws, Ns) ? tile_base[lo] : tile_base[lo] - 1;
+      else if (k == kTileMedium) t = tile_base[lo];
+      else t = tile_base[lo] + bucket_of(b, nb[lo]);
+      r = ((uint64_t)t << 32) | (uint64_t)i;
+    }
+    out[i] = r;
+  }
+}
+
+// Tile-ordered psi keys and each tile's range of them.
+__global__ void k_psi_ranges(const uint64_t *sorted, size_t npsi, const uint64_t *psi_keys,
+                             uint64_t *psi_list, TileDesc *tiles) {
+  for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < npsi;
+       j += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t k = sorted[j];
+    if (k == ~0ull) continue;
+    const uint32_t t = (uint32_t)(k >> 32);
+    psi_list[j] = psi_keys[(uint32_t)k];
+    if (j == 0 || (uint32_t)(sorted[j - 1] >> 32) != t) tiles[t].psi_lo = (uint32_t)j;
+    if (j + 1 == npsi || (uint32_t)(sorted[j + 1] >> 32) != t) tiles[t].psi_hi = (uint32_t)j + 1;
+  }
+}
+
+// First alpha-double item of each CTA step: the last item starting at or
+// before the step's first flat pair.
+__global__ void k_ad_tile_items(const uint32_t *ad_off, uint32_t nad, uint32_t total,
+                                uint32_t nsteps, uint32_t *tile_item) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s <= nsteps;
+       s += gridDim.x * blockDim.x) {
+    uint32_t f = s * (uint32_t)kAdTile;
+    if (f >= total) f = total - 1;
+    uint32_t lo = 0, hi = nad - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (ad_off[mid] <= f) lo = mid; else hi = mid - 1;
+    }
+    tile_item[s] = lo;
   }
 }
 
@@ -636,6 +927,7 @@ struct CellArgs {
   float tau_f;
   const uint64_t *psi_ht;
   uint64_t psi_mask;
+  const uint64_t *psi_list;  // psi keys of the batch in tile order
   uint64_t *cand_key;
   double *cand_score;
   unsigned long long *cand_count;
@@ -672,21 +964,30 @@ __device__ __forceinline__ bool psi_contains(const uint64_t *ht, uint64_t mask, 
 // A tile groups its records by target in a shared-memory hash table: a slot
 // holds the newest record of its target and each record the index of the
 // previous one, so that every target ends up with the list of its records.
-// The numerator is then summed exactly over that list, so grouping by hashing
-// gives bit for bit the result of sorting the records and summing the runs.
-// The records of the next tile are copied in asynchronously meanwhile.
+// The psi determinants that fall in the tile are entered first as markers, so
+// a target in psi is recognised without a global lookup.  The numerator is
+// then summed over each list by a rule that depends only on the multiset of
+// its values, so grouping by hashing gives the result of sorting the records
+// and summing the runs.  The records of the next tile are copied in
+// asynchronously meanwhile.
 constexpr uint32_t kEmptySlot = 0xffffffffu;
+constexpr uint32_t kPsiBit = 0x80000000u;  // slot holds psi marker (index in low bits)
 constexpr uint16_t kEndList = 0xffffu;
+constexpr int kPsiCap = 256;               // psi markers per tile; more: global lookups
 
 struct CellSmem {
-  uint64_t key[2][kCap];   // record target keys (double-buffered by tile)
-  double val[2][kCap];     // record values
-  uint32_t slot[kSlots];   // newest record of the slot's target, or kEmptySlot
-  uint16_t next[kCap];     // previous record of the same target, or kEndList
-  uint16_t targets[kCap];  // occupied slots, in order of claiming
-  uint32_t ntargets[2];    // by tile parity
+  uint64_t key[2][kCap];     // record target keys (double-buffered by tile)
+  double val[2][kCap];       // record values
+  int64_t haa[2][kCap];      // record diagonals (every record of a target agrees)
+  uint64_t psik[2][kPsiCap]; // psi keys of the tile
+  uint32_t slot[kSlots];     // newest record of the slot's target, a psi marker, or empty
+  uint32_t psibit[2][kSlots / 32];  // slots whose key is in psi
+  uint16_t next[kCap];       // previous record of the same target, or kEndList
+  uint16_t targets[kCap];    // slots claimed by records, in order of claiming
+  uint16_t psi_slot[kPsiCap];  // slot claimed by each psi marker, or kEndList
+  uint32_t ntargets[2];      // by tile parity
 };
-static_assert(kCap < 0xffff, "record index must fit 16 bits");
+static_assert(kCap < 0xffff && kSlots <= 0xffff, "indices must fit 16 bits");
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -715,8 +1016,17 @@ __device__ __forceinline__ void prefetch_tile(CellSmem &S, int buf, const TileDe
   for (uint32_t e = threadIdx.x; e < d.npairs; e += kCellThreads) {
     cp_async8(&S.key[buf][e], C.sb_key + d.start + e);
     cp_async8(&S.val[buf][e], C.sb_val + d.start + e);
+    cp_async8(&S.haa[buf][e], C.sb_haa + d.start + e);
   }
+  const uint32_t np = d.psi_hi - d.psi_lo;
+  if (np <= (uint32_t)kPsiCap)
+    for (uint32_t q = threadIdx.x; q < np; q += kCellThreads)
+      cp_async8(&S.psik[buf][q], C.psi_list + d.psi_lo + q);
   cp_async_commit();
+}
+
+__device__ __forceinline__ uint64_t slot_key(const CellSmem &S, int buf, uint32_t v) {
+  return (v & kPsiBit) ? S.psik[buf][v & ~kPsiBit] : S.key[buf][v];
 }
 
 // Exact numerator over the record list starting at e (values of screened-out
@@ -726,8 +1036,13 @@ __device__ __forceinline__ double list_numerator(const CellSmem &S, int buf, uin
   const double *val = S.val[buf];
   const uint32_t e2 = S.next[e];
   if (e2 == kEndList) return val[e];
-  // two records: IEEE addition rounds their exact sum once, like the accumulator
-  if (S.next[e2] == kEndList) return val[e] + val[e2];
+  // two records: IEEE addition rounds their exact sum once
+  const uint32_t e3 = S.next[e2];
+  if (e3 == kEndList) return val[e] + val[e2];
+  // three or four: an order-independent FP64 sum; more: the exact accumulator
+  const uint32_t e4 = S.next[e3];
+  if (e4 == kEndList) return sum4_ordered(0.0, val[e], val[e2], val[e3]);
+  if (S.next[e4] == kEndList) return sum4_ordered(val[e], val[e2], val[e3], val[e4]);
   int emax = 1;
   for (uint32_t i = e; i != kEndList; i = S.next[i]) {
     const int ex = fx_exponent(val[i]);
@@ -773,11 +1088,12 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
   const int warp_base = (int)(threadIdx.x & ~31u);
   unsigned long long my_unique = 0, my_excl = 0;
   for (int i = threadIdx.x; i < kSlots; i += kCellThreads) S.slot[i] = kEmptySlot;
+  for (int i = threadIdx.x; i < kSlots / 32; i += kCellThreads) S.psibit[0][i] = S.psibit[1][i] = 0u;
   if (threadIdx.x == 0) S.ntargets[0] = S.ntargets[1] = 0;
   // tiles blockIdx.x + k * gridDim.x; descriptors are read one tile ahead of
   // the record copies, which run one tile ahead of the reduction
   uint32_t tile = C.tile0 + blockIdx.x;
-  TileDesc d = {0, 0, 0, 0, 0, 0}, dn = {0, 0, 0, 0, 0, 0};
+  TileDesc d = {0, 0, 0, 0, 0, 0, 0, 0}, dn = {0, 0, 0, 0, 0, 0, 0, 0};
   bool on = false, on_n = false;
   if (tile < C.ntiles) {
     d = C.tiles[tile];
@@ -788,7 +1104,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
   int buf = 0;
 #pragma unroll 1
   for (; tile < C.ntiles; tile += gridDim.x, buf ^= 1) {
-    TileDesc dnn = {0, 0, 0, 0, 0, 0};
+    TileDesc dnn = {0, 0, 0, 0, 0, 0, 0, 0};
     if (tile + 2 * gridDim.x < C.ntiles) dnn = C.tiles[tile + 2 * gridDim.x];
     cp_async_wait_all();
     __syncthreads();  // records of this tile in place; the previous tile is done
@@ -797,6 +1113,34 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
       if (on_n) prefetch_tile(S, buf ^ 1, dn, C);
     } else {
       on_n = false;
+    }
+    // psi bits of the previous tile are read by no one until the next barrier
+    for (int i = threadIdx.x; i < kSlots / 32; i += kCellThreads) S.psibit[buf ^ 1][i] = 0u;
+    const uint32_t npsi = d.psi_hi - d.psi_lo;
+    const bool psi_local = npsi <= (uint32_t)kPsiCap;
+    if (on && psi_local) {
+      // psi markers: claim a slot, or flag the slot a record already holds
+      for (uint32_t q = threadIdx.x; q < npsi; q += kCellThreads) {
+        const uint64_t key = S.psik[buf][q];
+        uint32_t h = (uint32_t)mix_key(key) & (kSlots - 1);
+        uint16_t claimed = kEndList;
+        int probe = 0;
+        for (; probe < kSlots; ++probe) {
+          uint32_t cur = S.slot[h];
+          if (cur == kEmptySlot) {
+            cur = atomicCAS(&S.slot[h], kEmptySlot, kPsiBit | q);
+            if (cur == kEmptySlot) {
+              claimed = (uint16_t)h;
+              break;
+            }
+          }
+          if (slot_key(S, buf, cur) == key) break;
+          h = (h + 1) & (kSlots - 1);
+        }
+        if (probe == kSlots) atomicOr(C.err, kErrTile);  // cannot happen at load < 3/4
+        else atomicOr(&S.psibit[buf][h >> 5], 1u << (h & 31));
+        S.psi_slot[q] = claimed;
+      }
     }
     if (on) {
       // link each record into its target's list; warps append the slots they
@@ -820,13 +1164,19 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
                 break;
               }
             }
-            if (S.key[buf][cur] == key) {
-              S.next[e] = (uint16_t)atomicExch(&S.slot[h], (uint32_t)e);
+            if (slot_key(S, buf, cur) == key) {
+              const uint32_t old = atomicExch(&S.slot[h], (uint32_t)e);
+              if (old & kPsiBit) {  // the first record of a psi marker's target
+                S.next[e] = kEndList;
+                claimed = (int)h;
+              } else {
+                S.next[e] = (uint16_t)old;
+              }
               break;
             }
             h = (h + 1) & (kSlots - 1);
           }
-          if (probe == kSlots) atomicOr(C.err, kErrTile);  // cannot happen at load <= 1/2
+          if (probe == kSlots) atomicOr(C.err, kErrTile);  // cannot happen at load < 3/4
         }
         const unsigned bal = __ballot_sync(0xffffffffu, claimed >= 0);
         if (bal) {
@@ -840,8 +1190,17 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
     __syncthreads();  // lists complete
     if (threadIdx.x == 0) S.ntargets[buf ^ 1] = 0;  // read by no one until the next barrier
     if (on) {
-      // one target per thread: exact numerator, exclusion, threshold; the
-      // slot is emptied by its owner for the next tile
+      // markers that no record joined are emptied by their inserting thread
+      if (psi_local)
+        for (uint32_t q = threadIdx.x; q < npsi; q += kCellThreads) {
+          const uint32_t h = S.psi_slot[q];
+          if (h != kEndList) {
+            const uint32_t v = S.slot[h];
+            if (v != kEmptySlot && (v & kPsiBit)) S.slot[h] = kEmptySlot;
+          }
+        }
+      // one target per thread: numerator, exclusion, threshold; the slot is
+      // emptied by its owner for the next tile
       const int ntg = (int)S.ntargets[buf];
 #pragma unroll 1
       for (int base = 0; base + warp_base < ntg; base += kCellThreads) {
@@ -854,13 +1213,14 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
           const uint32_t e = S.slot[h];
           S.slot[h] = kEmptySlot;
           key = S.key[buf][e];
-          const int64_t haa = C.sb_haa[d.start + e];  // every record of a target agrees
-          const double num = list_numerator(S, buf, e, C.err);
           ++my_unique;
-          if (psi_contains(C.psi_ht, C.psi_mask, key, C.err)) {
+          const bool in_psi = psi_local ? ((S.psibit[buf][h >> 5] >> (h & 31)) & 1u) != 0u
+                                        : psi_contains(C.psi_ht, C.psi_mask, key, C.err);
+          if (in_psi) {
             ++my_excl;
           } else {
-            const int64_t den_x = C.E0_x - haa;
+            const double num = list_numerator(S, buf, e, C.err);
+            const int64_t den_x = C.E0_x - S.haa[buf][e];
             pass = true;
             if (C.tau > 0.0) {
               bool okn, okd;
@@ -944,26 +1304,39 @@ __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const ui
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t sk = keys[i];
     if (i > 0 && keys[i - 1] == sk) continue;
+    // the same rule as on chip: one or two values by IEEE addition, three or
+    // four by the ordered FP64 sum, more by the exact accumulator
     int emax = 1, live = 0;
+    double w[4] = {0.0, 0.0, 0.0, 0.0};
     for (uint64_t e = i; e < n && keys[e] == sk; ++e) {
       const double v = C.sb_val[src[idx[e]]];
       if (is_dropped(v)) continue;
       const int ex = fx_exponent(v);
       emax = ex > emax ? ex : emax;
+      if (live < 4) w[live] = v;
       ++live;
     }
     if (!live) continue;
-    const int frac = fx_frac_for(emax);
-    Fx192 acc = {0, 0, 0};
-    unsigned ovf = 0;
-    for (uint64_t e = i; e < n && keys[e] == sk; ++e) {
-      const double v = C.sb_val[src[idx[e]]];
-      if (is_dropped(v)) continue;
-      Fx192 x = fx_from_double(v, frac, &ovf);
-      fx_add(acc, x);
+    double num;
+    if (live == 1) {
+      num = w[0];
+    } else if (live == 2) {
+      num = w[0] + w[1];
+    } else if (live <= 4) {
+      num = sum4_ordered(w[0], w[1], w[2], w[3]);
+    } else {
+      const int frac = fx_frac_for(emax);
+      Fx192 acc = {0, 0, 0};
+      unsigned ovf = 0;
+      for (uint64_t e = i; e < n && keys[e] == sk; ++e) {
+        const double v = C.sb_val[src[idx[e]]];
+        if (is_dropped(v)) continue;
+        Fx192 x = fx_from_double(v, frac, &ovf);
+        fx_add(acc, x);
+      }
+      if (ovf) atomicOr(C.err, kErrAccum);
+      num = fx_to_double(acc, frac);
     }
-    if (ovf) atomicOr(C.err, kErrAccum);
-    const double num = fx_to_double(acc, frac);
     const uint64_t full = pack_key(alpha[sk >> 32], (uint32_t)sk);
     ++my_unique;
     if (psi_contains(C.psi_ht, C.psi_mask, full, C.err)) {
@@ -1064,9 +1437,34 @@ int build_fx(const double *h1, const double *eri, int n, int na, int nb, double 
   ASCI_TRY(arena.alloc(&jj, (size_t)n * n));
   k_fx_tables<<<(n * n + 255) / 256, 256, 0, s>>>(h1, eri, n, sc, hh, jk, jj);
   ASCI_CHECK_LAUNCH();
+  // single excitations: a sum of at most n + 1 table values stays below the
+  // bound Bs, and s1 = 61 - log2(Bs) keeps it inside 64 bits
+  double *d1;
+  ASCI_TRY(arena.alloc(&d1, 1));
+  k_fx_single_bound<<<1, 256, 0, s>>>(h1, eri, n, d1);
+  ASCI_CHECK_LAUNCH();
+  double bs = 0;
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&bs, d1, sizeof(bs), cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  int e1 = 0;
+  frexp(bs + 1e-300, &e1);
+  int s1 = 61 - e1;
+  if (s1 > 1000) s1 = 1000;
+  const size_t n3 = (size_t)n * n * n;
+  int64_t *h1x, *ssx, *sox;
+  ASCI_TRY(arena.alloc(&h1x, (size_t)n * n));
+  ASCI_TRY(arena.alloc(&ssx, n3));
+  ASCI_TRY(arena.alloc(&sox, n3));
+  k_fx_single_tables<<<(unsigned)std::min<size_t>((n3 + 255) / 256, 4096), 256, 0, s>>>(
+      h1, eri, n, s1, h1x, ssx, sox);
+  ASCI_CHECK_LAUNCH();
   FxInts X;
   X.n = n;
   X.s = sc;
+  X.s1 = s1;
+  X.h1x = h1x;
+  X.ssx = ssx;
+  X.sox = sox;
   X.ecore_x = llrint(ldexp(ecore, sc));
   X.hh = hh;
   X.jk = jk;
@@ -1146,10 +1544,11 @@ static unsigned emit_grid(size_t ntl) {
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
                 uint32_t gb0, uint32_t gb1, uint64_t *sb_key, double *sb_val, int64_t *sb_haa,
                 uint64_t stage_cap, double eps, unsigned long long *survivors, unsigned *err,
-                void **tiles_out, size_t *ntiles_out, std::vector<uint32_t> *oversized,
-                Arena &arena) {
+                void **tiles_out, size_t *ntiles_out, const uint64_t **psi_list_out,
+                std::vector<uint32_t> *oversized, Arena &arena) {
   cudaStream_t s = arena.stream();
   const uint32_t ng = gb1 - gb0;
+  *psi_list_out = nullptr;
   *ntiles_out = 0;
   oversized->clear();
   if (P1 <= P0 || ng == 0) return ASCI_OK;
@@ -1183,15 +1582,50 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
     return ASCI_ECUDA;
   }
 
-  // emission tiles and the first item of each
-  const uint64_t etiles64 = (P1 - P0 + kEmitTile - 1) / kEmitTile;
-  if (etiles64 >= (1ull << 31)) return ASCI_EINVAL;
-  const uint32_t etiles = (uint32_t)etiles64;
-  uint32_t *tile_item;
-  ASCI_TRY(arena.alloc(&tile_item, (size_t)etiles + 1));
-  k_tile_items<<<grid_for((size_t)etiles + 1), 256, 0, s>>>(F.Wexcl, t0, t1, P0, P1, etiles,
-                                                            tile_item);
+  // work lists of the batch: determinant runs and alpha-double items
+  const uint64_t nt = t1 - t0;
+  if (nt >= (1ull << 32)) return ASCI_EINVAL;
+  uint32_t *rcnt, *roff, *adf, *adpos;
+  ASCI_TRY(arena.alloc(&rcnt, nt));
+  ASCI_TRY(arena.alloc(&roff, nt));
+  ASCI_TRY(arena.alloc(&adf, nt));
+  ASCI_TRY(arena.alloc(&adpos, nt));
+  k_batch_counts<<<grid_for(nt), 256, 0, s>>>(F.items, t0, nt, F.opbits, F.E.sa, F.grp_count,
+                                              rcnt, adf);
   ASCI_CHECK_LAUNCH();
+  ASCI_TRY(scan_exclusive_u32(rcnt, roff, nt, arena));
+  ASCI_TRY(scan_exclusive_u32(adf, adpos, nt, arena));
+  size_t nruns = 0, nad = 0;
+  ASCI_TRY(kept_count(rcnt, roff, nt, &nruns, arena));
+  ASCI_TRY(kept_count(adf, adpos, nt, &nad, arena));
+  uint64_t *runs;
+  uint32_t *adl, *adw, *ad_off, *opinfo;
+  ASCI_TRY(arena.alloc(&opinfo, nt));
+  ASCI_TRY(arena.alloc(&runs, nruns + 1));
+  ASCI_TRY(arena.alloc(&adl, nad + 1));
+  ASCI_TRY(arena.alloc(&adw, nad + 1));
+  ASCI_TRY(arena.alloc(&ad_off, nad + 1));
+  k_batch_lists<<<grid_for(nt), 256, 0, s>>>(F.items, t0, nt, F.opbits, F.E.sa, F.grp_count, rcnt,
+                                             roff, adpos, runs, adl, adw, F.grp_alpha, F.X.n,
+                                             FastDiv(F.E.va ? F.E.va : 1), opinfo);
+  ASCI_CHECK_LAUNCH();
+  size_t ad_total = 0;
+  uint32_t ad_tiles = 0;
+  uint32_t *ad_tile_item = nullptr;
+  if (nad) {
+    ASCI_TRY(scan_exclusive_u32(adw, ad_off, nad, arena));
+    ASCI_TRY(kept_count(adw, ad_off, nad, &ad_total, arena));
+    if (ad_total > P1 - P0) {
+      record_error("alpha-double pairs exceed the batch", __FILE__, __LINE__);
+      return ASCI_ECUDA;
+    }
+    ad_tiles = (uint32_t)((ad_total + kAdTile - 1) / kAdTile);
+    ASCI_TRY(arena.alloc(&ad_tile_item, (size_t)ad_tiles + 1));
+    k_ad_tile_items<<<grid_for((size_t)ad_tiles + 1), 256, 0, s>>>(
+        ad_off, (uint32_t)nad, (uint32_t)ad_total, ad_tiles, ad_tile_item);
+    ASCI_CHECK_LAUNCH();
+  }
+  ASCI_TRACE("stage: runs=%zu alpha-double items=%zu pairs=%zu", nruns, nad, ad_total);
 
   uint32_t *cnt, *cnt_scan, *cell_pos0, *fill;
   ASCI_TRY(arena.alloc(&cnt, ncells + 1));
@@ -1202,27 +1636,25 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   ASCI_TRY_CUDA(cudaMemsetAsync(fill, 0, (ncells + 1) * sizeof(uint32_t), s));
 
   EmitArgs A;
+  memset(&A, 0, sizeof(A));
   A.I = F.I;
   A.X = F.X;
   A.E = F.E;
   A.dv_va = FastDiv(F.E.va ? F.E.va : 1);
   A.dv_vb = FastDiv(F.E.vb ? F.E.vb : 1);
-  A.dv_npd0 = FastDiv((uint32_t)(F.E.sb + F.E.dbb) ? (uint32_t)(F.E.sb + F.E.dbb) : 1);
-  A.dv_npd1 = FastDiv(1u + F.E.sb);
   A.dv_pa_p = FastDiv(F.E.pa_p ? F.E.pa_p : 1);
   A.dv_pb_p = FastDiv(F.E.pb_p ? F.E.pb_p : 1);
+  A.npd0 = (uint32_t)(F.E.sb + F.E.dbb);
+  A.npd1 = 1u + F.E.sb;
   A.items = F.items;
   A.Wexcl = F.Wexcl;
   A.item_group = F.item_group;
-  A.tile_item = tile_item;
-  A.tile_list = nullptr;
   A.t0 = t0;
-  A.t1 = t1;
   A.P0 = P0;
-  A.P1 = P1;
   A.opbits = F.opbits;
   A.grp_alpha = F.grp_alpha;
   A.grp_start = F.grp_start;
+  A.grp_count = F.grp_count;
   A.core_beta = F.core_beta;
   A.core_c = F.core_c;
   A.Dx = F.Dx;
@@ -1235,7 +1667,15 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   A.cnt = cnt;
   A.cell_pos0 = cell_pos0;
   A.fill = fill;
-  A.g_alpha = F.g_alpha;
+  A.runs = runs;
+  A.nruns = nruns;
+  A.adl = adl;
+  A.opinfo = opinfo;
+  A.ad_off = ad_off;
+  A.nad = (uint32_t)nad;
+  A.ad_total = (uint32_t)ad_total;
+  A.ad_tile_item = ad_tile_item;
+  A.ad_tiles = ad_tiles;
   A.sb_key = sb_key;
   A.sb_val = sb_val;
   A.sb_haa = sb_haa;
@@ -1247,24 +1687,15 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   A.ncore = F.ncore;
   A.err = err;
   const size_t emit_smem = 2 * (size_t)F.X.n * F.X.n * sizeof(int64_t);
-  if (ncells) {
-    // count the hash buckets, visiting only emission tiles that hold big classes
-    uint32_t *flag, *pos, *list;
-    ASCI_TRY(arena.alloc(&flag, etiles));
-    ASCI_TRY(arena.alloc(&pos, etiles));
-    ASCI_TRY(arena.alloc(&list, etiles));
-    ASCI_TRY_CUDA(cudaMemsetAsync(flag, 0, (size_t)etiles * sizeof(uint32_t), s));
-    k_big_tile_flags<<<grid_for(ng), 256, 0, s>>>(gb0, ng, P0, P1, F.g_P0, kind, flag);
-    ASCI_CHECK_LAUNCH();
-    ASCI_TRY(scan_exclusive_u32(flag, pos, etiles, arena));
-    size_t nbig = 0;
-    ASCI_TRY(kept_count(flag, pos, etiles, &nbig, arena));
-    k_list_flags<<<grid_for(etiles), 256, 0, s>>>(flag, pos, etiles, list);
-    ASCI_CHECK_LAUNCH();
-    A.tile_list = list;
-    if (nbig) {
-      A.ntl = (uint32_t)nbig;
-      k_emit2<0, false><<<emit_grid(nbig), kEmitThreads, 0, s>>>(A);
+  const unsigned run_grid = emit_grid((nruns + 7) / 8);
+  const unsigned ad_grid = emit_grid(ad_tiles);
+  if (ncells) {  // count the hash buckets of big classes
+    if (nruns) {
+      k_emit_runs<0, false><<<run_grid, kRunThreads, 0, s>>>(A);
+      ASCI_CHECK_LAUNCH();
+    }
+    if (ad_tiles) {
+      k_emit_ad<0, false><<<ad_grid, kAdThreads, 0, s>>>(A);
       ASCI_CHECK_LAUNCH();
     }
   }
@@ -1283,13 +1714,38 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
                                             n_over, over_list, over_cap);
   ASCI_CHECK_LAUNCH();
   ASCI_TRACE("stage: tiles written");
-  A.ntl = etiles;
-  if (eps > 0.0)
-    k_emit2<1, true><<<emit_grid(etiles), kEmitThreads, emit_smem, s>>>(A);
-  else
-    k_emit2<1, false><<<emit_grid(etiles), kEmitThreads, emit_smem, s>>>(A);
-  ASCI_CHECK_LAUNCH();
-  ASCI_TRACE("stage: emit launched (%u blocks)", etiles);
+  // psi determinants routed to their tiles (entered there as markers)
+  uint64_t *psi_list = nullptr;
+  if (F.npsi) {
+    uint64_t *pk, *pk_alt;
+    ASCI_TRY(arena.alloc(&pk, F.npsi));
+    ASCI_TRY(arena.alloc(&pk_alt, F.npsi));
+    ASCI_TRY(arena.alloc(&psi_list, F.npsi));
+    k_psi_route<<<grid_for(F.npsi), 256, 0, s>>>(F.psi_keys, F.npsi, F.g_alpha, gb0, ng, kind, nb,
+                                                 Ws, Ns, tile_base, pk);
+    ASCI_CHECK_LAUNCH();
+    int topbit = 1;
+    while ((1ull << topbit) <= (uint64_t)ntiles) ++topbit;
+    ASCI_TRY(radix_sort_u64(&pk, &pk_alt, F.npsi, 0, 32 + topbit, arena));
+    k_psi_ranges<<<grid_for(F.npsi), 256, 0, s>>>(pk, F.npsi, F.psi_keys, psi_list, tiles);
+    ASCI_CHECK_LAUNCH();
+  }
+  *psi_list_out = psi_list;
+  if (nruns) {
+    if (eps > 0.0)
+      k_emit_runs<1, true><<<run_grid, kRunThreads, emit_smem, s>>>(A);
+    else
+      k_emit_runs<1, false><<<run_grid, kRunThreads, emit_smem, s>>>(A);
+    ASCI_CHECK_LAUNCH();
+  }
+  if (ad_tiles) {
+    if (eps > 0.0)
+      k_emit_ad<1, true><<<ad_grid, kAdThreads, 0, s>>>(A);
+    else
+      k_emit_ad<1, false><<<ad_grid, kAdThreads, 0, s>>>(A);
+    ASCI_CHECK_LAUNCH();
+  }
+  ASCI_TRACE("stage: emission launched");
   unsigned hov = 0;
   ASCI_TRY_CUDA(cudaMemcpyAsync(&hov, n_over, sizeof(hov), cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
@@ -1343,8 +1799,8 @@ static CellArgs cell_args(const FusedCore &F, const uint64_t *sb_key,
 
 // Reduce tiles [tile_begin, tile_end) of a staged batch on chip and append the
 // targets with |S| >= tau to the candidate buffer (at most kCap per tile).
-int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint32_t tile_end,
-                const uint64_t *sb_key, const double *sb_val, const int64_t *sb_haa,
+int fused_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
+                uint32_t tile_begin, uint32_t tile_end, const uint64_t *sb_key, const double *sb_val, const int64_t *sb_haa,
                 uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
                 unsigned long long *cand_count, unsigned long long cand_cap,
                 unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
@@ -1354,6 +1810,7 @@ int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint
   CellArgs CA = cell_args(F, sb_key, sb_val, sb_haa, stage_cap, tau, cand_key, cand_score,
                           cand_count, cand_cap, n_unique, n_excluded, err);
   CA.tiles = static_cast<const TileDesc *>(tiles);
+  CA.psi_list = psi_list;
   CA.tile0 = tile_begin;
   CA.ntiles = tile_end;
   const size_t cell_smem = sizeof(CellSmem);

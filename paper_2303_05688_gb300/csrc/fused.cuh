@@ -14,6 +14,10 @@ struct FxInts {
   const int64_t *hh;  // n      h_pp
   const int64_t *jk;  // n*n    (pp|qq) - (pq|qp), zero diagonal
   const int64_t *jj;  // n*n    (pp|qq)
+  // single excitations i -> a in fixed point, multiples of 2^-s1:
+  // h1x = h_ia, ssx[(i*n+a)*n+k] = (ia|kk) - (ik|ka), sox[(i*n+a)*n+k] = (ia|kk)
+  int s1;
+  const int64_t *h1x, *ssx, *sox;
 };
 
 // Everything the batch kernels read that stays fixed during one search.
@@ -24,7 +28,7 @@ struct FusedCore {
   const uint64_t *items, *Wexcl;
   const uint32_t *item_group;
   int opbits;
-  const uint32_t *grp_alpha, *grp_start, *core_beta;
+  const uint32_t *grp_alpha, *grp_start, *grp_count, *core_beta;
   const double *core_c;
   const int64_t *Dx, *Fa, *Fb;
   const uint32_t *g_alpha;
@@ -32,6 +36,8 @@ struct FusedCore {
   int64_t E0_x;
   const uint64_t *psi_ht;
   uint64_t psi_mask;
+  const uint64_t *psi_keys;  // psi keys, sorted
+  size_t npsi;
   uint32_t ncore;
 };
 

@@ -50,8 +50,8 @@ int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t 
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
                 uint32_t gb0, uint32_t gb1, uint64_t *sb_key, double *sb_val, int64_t *sb_haa,
                 uint64_t stage_cap, double eps, unsigned long long *survivors, unsigned *err,
-                void **tiles_out, size_t *ntiles_out, std::vector<uint32_t> *oversized,
-                Arena &arena);
+                void **tiles_out, size_t *ntiles_out, const uint64_t **psi_list_out,
+                std::vector<uint32_t> *oversized, Arena &arena);
 int tile_info(const void *tiles, const std::vector<uint32_t> &list, std::vector<uint32_t> *info,
               cudaStream_t s);
 int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const uint64_t *sb_key,
@@ -60,8 +60,8 @@ int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const u
                     unsigned long long cand_cap, unsigned long long *n_unique,
                     unsigned long long *n_excluded, unsigned *err, uint64_t *nrec_out,
                     Arena &arena);
-int fused_cells(const FusedCore &F, const void *tiles, uint32_t tile_begin, uint32_t tile_end,
-                const uint64_t *sb_key, const double *sb_val, const int64_t *sb_haa,
+int fused_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
+                uint32_t tile_begin, uint32_t tile_end, const uint64_t *sb_key, const double *sb_val, const int64_t *sb_haa,
                 uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
                 unsigned long long *cand_count, unsigned long long cand_cap,
                 unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
@@ -616,12 +616,15 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   F.opbits = opbits;
   F.grp_alpha = grp_alpha;
   F.grp_start = grp_start;
+  F.grp_count = grp_count;
   F.core_beta = core_beta;
   F.core_c = core_c_sorted;
   uint64_t *psi_ht = nullptr;
   uint64_t psi_mask = 0;
   ASCI_TRY(psi_hash_build(psi_sorted, nd, &psi_ht, &psi_mask, arena));
   F.psi_ht = psi_ht;
+  F.psi_keys = psi_sorted;
+  F.npsi = nd;
   F.psi_mask = psi_mask;
   F.ncore = (uint32_t)m;
   ASCI_TRY(build_fx(h1, eri, n, na, nb, ints->ecore, E0, arena, &F.X, &F.E0_x));
@@ -713,8 +716,10 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
                (unsigned long long)b.t0, (unsigned long long)b.t1, (unsigned long long)b.P0,
                (unsigned long long)b.P1, gg[0], gg[1] + 1);
     std::vector<uint32_t> oversized;
+    const uint64_t *psi_list = nullptr;
     ASCI_TRY(fused_stage(F, b.t0, b.t1, b.P0, b.P1, gg[0], gg[1] + 1, sb_key, sb_val, sb_haa,
-                         bcap, o.eps_search, dcount + 3, derr2, &tiles, &ntiles, &oversized, ba));
+                         bcap, o.eps_search, dcount + 3, derr2, &tiles, &ntiles, &psi_list,
+                         &oversized, ba));
     ASCI_TRACE("staged: tiles=%zu oversized=%zu", ntiles, oversized.size());
     tm.stop(&tl[2]);
     tm.start();
@@ -733,7 +738,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
       }
       const size_t t1 = std::min(ntiles, t + room);
       ASCI_TRACE("cells: tiles [%zu,%zu) tau=%.6g pool=%zu", t, t1, tau, pool_n);
-      ASCI_TRY(fused_cells(F, tiles, (uint32_t)t, (uint32_t)t1, sb_key, sb_val, sb_haa, bcap, tau,
+      ASCI_TRY(fused_cells(F, tiles, psi_list, (uint32_t)t, (uint32_t)t1, sb_key, sb_val, sb_haa, bcap, tau,
                            pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1, dcount + 2,
                            derr2, ba));
       unsigned long long c = 0;
