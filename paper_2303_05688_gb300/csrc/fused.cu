@@ -440,14 +440,11 @@ struct EmitArgs {
   const uint32_t *opinfo;     // per batch item: alpha single i | a << 5 | parity << 10
   const uint32_t *ad_tile_item;  // first alpha-double item of each CTA step
   uint32_t ad_tiles;
-  uint64_t *sb_key;
-  double *sb_val;
-  int64_t *sb_haa;
+  Stage st;
   double eps;                 // Alg. 2 screen; 0 keeps every pair
   int64_t E0_x;
   double inv_scale;
   unsigned long long *survivors;
-  uint64_t stage_cap;  // records the staging buffer holds
   uint32_t ncore;
   unsigned *err;
 };
@@ -520,19 +517,34 @@ __device__ __forceinline__ bool pair_position(const EmitArgs &A, bool big, bool 
   return MODE == 1 && valid;
 }
 
+// z * 2^-s as a float built from the bits (truncated, relative error below
+// 2^-23); 0 when z is zero or the value lies outside the normal float range.
+__device__ __forceinline__ float scaled_as_float(int64_t z, int s) {
+  if (!z) return 0.0f;
+  const uint64_t u = z < 0 ? 0ull - (uint64_t)z : (uint64_t)z;
+  const int lz = __clzll((long long)u);
+  const int e = 63 - lz - s + 127;
+  if (e < 1 || e > 254) return 0.0f;
+  const uint32_t mant = (uint32_t)((u << lz) >> 40) & 0x7fffffu;
+  return __uint_as_float((z < 0 ? 0x80000000u : 0u) | ((uint32_t)e << 23) | mant);
+}
+
 template <bool EPS>
-__device__ __forceinline__ void write_record(const EmitArgs &A, uint32_t pos, uint64_t key,
-                                             double v, int64_t haa, bool *kept) {
+__device__ __forceinline__ void write_record(const EmitArgs &A, uint32_t pos, uint32_t talpha,
+                                             uint32_t tb, bool packed, double v, int64_t haa,
+                                             bool *kept) {
   if (EPS) {
     // |v / (E0 - H_ii)| > eps, without a division
     const double den = __ll2double_rn(A.E0_x - haa) * A.inv_scale;
     if (!(fabs(v) > A.eps * fabs(den))) v = drop_marker();
     *kept = !is_dropped(v);
   }
-  if (pos < A.stage_cap) {
-    A.sb_key[pos] = key;
-    A.sb_val[pos] = v;
-    A.sb_haa[pos] = haa;
+  if (pos < A.st.cap) {
+    const uint64_t vb = (uint64_t)__double_as_longlong(v);
+    reinterpret_cast<uint4 *>(A.st.rec)[pos] =
+        make_uint4((uint32_t)vb, (uint32_t)(vb >> 32), tb,
+                   __float_as_uint(scaled_as_float(A.E0_x - haa, A.X.s)));
+    if (packed) A.st.alpha[pos] = talpha;
   } else {
     atomicOr(A.err, kErrStage);
   }
@@ -571,7 +583,8 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
     const uint64_t it = A.items[t];
     const uint32_t k = (uint32_t)it >> A.opbits, o = (uint32_t)it & omask;
     const uint32_t gi = A.item_group[t] - A.gb0;
-    const bool big = A.kind[gi] == kTileBucket;
+    const uint32_t kd = A.kind[gi];
+    const bool big = kd == kTileBucket, packed = kd == kTilePacked;
     if (MODE == 0 && !big) continue;
     const uint32_t jdx = A.grp_start[k] + m;
     if (jdx >= A.ncore) {
@@ -622,52 +635,67 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
         erow = A.I.eri + ((size_t)ia * n + aa) * n * n;
       }
     }
-#pragma unroll 1
-    for (uint32_t e0 = 0; e0 < npd; e0 += 32) {
+    // one chunk of 32 pairs: the beta operation as positions in the occupied /
+    // virtual lists (op 0: none, the alpha single alone; 1: beta single;
+    // 2: beta double), its orbitals and the target beta string
+    struct Chunk {
+      uint32_t h1, h2, p1, p2;
+      int op, bi, bj, ba, bb;
+      uint32_t tb, pos;
+      bool valid, wr;
+    };
+    auto decode = [&](uint32_t e0, Chunk &q) {
       const uint32_t e = e0 + lane;
-      const bool valid = e < npd;
-      // the beta operation as positions in the occupied / virtual lists
-      int op = 0;  // 0: none (the alpha single alone), 1: beta single, 2: beta double
-      uint32_t h1 = 0, h2 = 0, p1 = 0, p2 = 0;
-      if (valid) {
+      q.valid = e < npd;
+      q.op = 0;
+      q.h1 = q.h2 = q.p1 = q.p2 = 0;
+      if (q.valid) {
         if (o == 0 && e >= sb) {
-          op = 2;
-          const uint32_t f = e - sb, q = A.dv_pb_p.div(f);
-          const uint32_t hp = s_pair[q], pp = s_pair[f - q * A.dv_pb_p.d];
-          h1 = hp & 0xffu;
-          h2 = hp >> 8;
-          p1 = pp & 0xffu;
-          p2 = pp >> 8;
+          q.op = 2;
+          const uint32_t f = e - sb, qq = A.dv_pb_p.div(f);
+          const uint32_t hp = s_pair[qq], pp = s_pair[f - qq * A.dv_pb_p.d];
+          q.h1 = hp & 0xffu;
+          q.h2 = hp >> 8;
+          q.p1 = pp & 0xffu;
+          q.p2 = pp >> 8;
         } else if (o == 0 || e > 0) {
-          op = 1;
-          const uint32_t f = o == 0 ? e : e - 1, q = A.dv_vb.div(f);
-          h1 = q;
-          p1 = f - q * vb;
+          q.op = 1;
+          const uint32_t f = o == 0 ? e : e - 1, qq = A.dv_vb.div(f);
+          q.h1 = qq;
+          q.p1 = f - qq * vb;
         }
       }
-      const int bi = __shfl_sync(0xffffffffu, occL, (int)h1);
-      const int bj = __shfl_sync(0xffffffffu, occL, (int)h2);
-      const int ba = __shfl_sync(0xffffffffu, virL, (int)p1);
-      const int bb = __shfl_sync(0xffffffffu, virL, (int)p2);
-      uint32_t tb = B;
-      if (op == 1) tb ^= (1u << bi) | (1u << ba);
-      if (op == 2) tb ^= (1u << bi) | (1u << bj) | (1u << ba) | (1u << bb);
-      // the staging slot first, so that its atomic overlaps the integral loads
-      const uint32_t cell = big ? cell0 + bucket_of(tb, nbk) : 0u;
-      uint32_t pos = 0;
-      const bool wr = pair_position<MODE>(A, big, valid, cell, p0 + e, &pos);
+      q.bi = __shfl_sync(0xffffffffu, occL, (int)q.h1);
+      q.bj = __shfl_sync(0xffffffffu, occL, (int)q.h2);
+      q.ba = __shfl_sync(0xffffffffu, virL, (int)q.p1);
+      q.bb = __shfl_sync(0xffffffffu, virL, (int)q.p2);
+      q.tb = B;
+      if (q.op == 1) q.tb ^= (1u << q.bi) | (1u << q.ba);
+      if (q.op == 2) q.tb ^= (1u << q.bi) | (1u << q.bj) | (1u << q.ba) | (1u << q.bb);
+      const uint32_t cell = big ? cell0 + bucket_of(q.tb, nbk) : 0u;
+      q.pos = 0;
+      q.wr = pair_position<MODE>(A, big, q.valid, cell, p0 + e, &q.pos);
+    };
+    // software-pipelined: the next chunk's staging slots (an atomic for big
+    // classes) are claimed before this chunk's matrix elements are formed
+    Chunk cur, nxt;
+    decode(0, cur);
+#pragma unroll 1
+    for (uint32_t e0 = 0; e0 < npd; e0 += 32) {
+      if (e0 + 32 < npd) decode(e0 + 32, nxt);  // warp-uniform
       double h = 0.0;
       int64_t dh = 0;
       if (MODE == 1) {
-        const int64_t vo1 = shfl64(Vo, (int)h1), vv1 = shfl64(Vv, (int)p1);
+        const int64_t vo1 = shfl64(Vo, (int)cur.h1), vv1 = shfl64(Vv, (int)cur.p1);
         int64_t vo2 = 0, vv2 = 0;
         if (o == 0) {  // warp-uniform
-          vo2 = shfl64(Vo, (int)h2);
-          vv2 = shfl64(Vv, (int)p2);
+          vo2 = shfl64(Vo, (int)cur.h2);
+          vv2 = shfl64(Vv, (int)cur.p2);
         }
-        if (op == 0) {
+        const int bi = cur.bi, bj = cur.bj, ba = cur.ba, bb = cur.bb;
+        if (cur.op == 0) {
           h = h0;
-        } else if (op == 1) {
+        } else if (cur.op == 1) {
           if (o == 0)
             h = flip_sign(fx64_to_double(fx_single(A.X, B, Ak, bi, ba), A.X.s1),
                           (uint32_t)single_parity(B, bi, ba));
@@ -682,11 +710,12 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
         }
       }
       bool kept = false;
-      if (wr) write_record<EPS>(A, pos, pack_key(talpha, tb), h * c, base_x + dh, &kept);
+      if (cur.wr) write_record<EPS>(A, cur.pos, talpha, cur.tb, packed, h * c, base_x + dh, &kept);
       if (EPS) {
         const uint32_t nk = __popc(__ballot_sync(0xffffffffu, kept));
         if (lane == 0 && nk) atomicAdd(A.survivors, (unsigned long long)nk);
       }
+      cur = nxt;
     }
   }
 }
@@ -796,8 +825,8 @@ __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
         const int64_t *Fa = A.Fa + (size_t)jdx * n;
         const int64_t dh = sD[lo] + Fa[(ob >> 5) & 31u] + Fa[(ob >> 15) & 31u] - Fa[ob & 31u] -
                            Fa[(ob >> 10) & 31u];
-        write_record<EPS>(A, pos, pack_key(sTA[lo], B), sH[lo] * A.core_c[jdx], A.Dx[jdx] + dh,
-                          &kept);
+        write_record<EPS>(A, pos, sTA[lo], B, A.kind[gi] == kTilePacked, sH[lo] * A.core_c[jdx],
+                          A.Dx[jdx] + dh, &kept);
       }
       if (EPS) {
         const uint32_t nk = __popc(__ballot_sync(0xffffffffu, kept));
@@ -917,9 +946,8 @@ struct CellArgs {
   const TileDesc *tiles;
   uint32_t ntiles;     // tiles [tile0, ntiles) are visited
   uint32_t tile0;
-  const uint64_t *sb_key;
-  const double *sb_val;
-  const int64_t *sb_haa;
+  Stage st;
+  FxInts X;          // exact diagonal of the targets that pass the screen
   int64_t E0_x;
   double inv_scale;  // 2^-s
   int s;             // fixed-point scale of the diagonal: 2^-s
@@ -933,7 +961,6 @@ struct CellArgs {
   unsigned long long *cand_count;
   unsigned long long cand_cap;
   unsigned long long *n_unique, *n_excluded;
-  uint64_t stage_cap;
   unsigned *err;
 };
 
@@ -973,12 +1000,11 @@ __device__ __forceinline__ bool psi_contains(const uint64_t *ht, uint64_t mask, 
 constexpr uint32_t kEmptySlot = 0xffffffffu;
 constexpr uint32_t kPsiBit = 0x80000000u;  // slot holds psi marker (index in low bits)
 constexpr uint16_t kEndList = 0xffffu;
-constexpr int kPsiCap = 256;               // psi markers per tile; more: global lookups
+constexpr int kPsiCap = 64;                // psi markers per tile; more: global lookups
 
 struct CellSmem {
-  uint64_t key[2][kCap];     // record target keys (double-buffered by tile)
-  double val[2][kCap];       // record values
-  int64_t haa[2][kCap];      // record diagonals (every record of a target agrees)
+  StageRec rec[2][kCap];     // records (double-buffered by tile)
+  uint32_t alpha[2][kCap];   // record target alpha strings (packed tiles)
   uint64_t psik[2][kPsiCap]; // psi keys of the tile
   uint32_t slot[kSlots];     // newest record of the slot's target, a psi marker, or empty
   uint32_t psibit[2][kSlots / 32];  // slots whose key is in psi
@@ -992,6 +1018,14 @@ static_assert(kCap < 0xffff && kSlots <= 0xffff, "indices must fit 16 bits");
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -1014,9 +1048,8 @@ __device__ __forceinline__ bool tile_on_chip(const TileDesc &d, uint64_t stage_c
 __device__ __forceinline__ void prefetch_tile(CellSmem &S, int buf, const TileDesc &d,
                                               const CellArgs &C) {
   for (uint32_t e = threadIdx.x; e < d.npairs; e += kCellThreads) {
-    cp_async8(&S.key[buf][e], C.sb_key + d.start + e);
-    cp_async8(&S.val[buf][e], C.sb_val + d.start + e);
-    cp_async8(&S.haa[buf][e], C.sb_haa + d.start + e);
+    cp_async16(&S.rec[buf][e], C.st.rec + d.start + e);
+    if (d.kind == kTilePacked) cp_async4(&S.alpha[buf][e], C.st.alpha + d.start + e);
   }
   const uint32_t np = d.psi_hi - d.psi_lo;
   if (np <= (uint32_t)kPsiCap)
@@ -1025,34 +1058,40 @@ __device__ __forceinline__ void prefetch_tile(CellSmem &S, int buf, const TileDe
   cp_async_commit();
 }
 
-__device__ __forceinline__ uint64_t slot_key(const CellSmem &S, int buf, uint32_t v) {
-  return (v & kPsiBit) ? S.psik[buf][v & ~kPsiBit] : S.key[buf][v];
+// Target key of record e (bucket and medium tiles share one alpha string).
+__device__ __forceinline__ uint64_t rec_key(const CellSmem &S, int buf, uint32_t e, bool packed,
+                                            uint32_t alpha) {
+  return pack_key(packed ? S.alpha[buf][e] : alpha, S.rec[buf][e].beta);
+}
+__device__ __forceinline__ uint64_t slot_key(const CellSmem &S, int buf, uint32_t v, bool packed,
+                                             uint32_t alpha) {
+  return (v & kPsiBit) ? S.psik[buf][v & ~kPsiBit] : rec_key(S, buf, v, packed, alpha);
 }
 
 // Exact numerator over the record list starting at e (values of screened-out
 // records are never inserted).
 __device__ __forceinline__ double list_numerator(const CellSmem &S, int buf, uint32_t e,
                                                  unsigned *err) {
-  const double *val = S.val[buf];
+  const StageRec *r = S.rec[buf];
   const uint32_t e2 = S.next[e];
-  if (e2 == kEndList) return val[e];
+  if (e2 == kEndList) return r[e].v;
   // two records: IEEE addition rounds their exact sum once
   const uint32_t e3 = S.next[e2];
-  if (e3 == kEndList) return val[e] + val[e2];
+  if (e3 == kEndList) return r[e].v + r[e2].v;
   // three or four: an order-independent FP64 sum; more: the exact accumulator
   const uint32_t e4 = S.next[e3];
-  if (e4 == kEndList) return sum4_ordered(0.0, val[e], val[e2], val[e3]);
-  if (S.next[e4] == kEndList) return sum4_ordered(val[e], val[e2], val[e3], val[e4]);
+  if (e4 == kEndList) return sum4_ordered(0.0, r[e].v, r[e2].v, r[e3].v);
+  if (S.next[e4] == kEndList) return sum4_ordered(r[e].v, r[e2].v, r[e3].v, r[e4].v);
   int emax = 1;
   for (uint32_t i = e; i != kEndList; i = S.next[i]) {
-    const int ex = fx_exponent(val[i]);
+    const int ex = fx_exponent(r[i].v);
     emax = ex > emax ? ex : emax;
   }
   const int frac = fx_frac_for(emax);
   Fx192 acc = {0, 0, 0};
   unsigned ovf = 0;
   for (uint32_t i = e; i != kEndList; i = S.next[i]) {
-    Fx192 x = fx_from_double(val[i], frac, &ovf);
+    Fx192 x = fx_from_double(r[i].v, frac, &ovf);
     fx_add(acc, x);
   }
   if (ovf) atomicOr(err, kErrAccum);
@@ -1067,18 +1106,6 @@ __device__ __forceinline__ float abs_as_float(double x, bool *ok) {
   *ok = e >= 1 && e <= 254;
   e = e < 1 ? 1 : (e > 254 ? 254 : e);
   return __uint_as_float(((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
-}
-
-// |z| * 2^-s as a float, truncated; *ok is false for zero or outside the
-// normal float range.
-__device__ __forceinline__ float abs_scaled_as_float(int64_t z, int s, bool *ok) {
-  const uint64_t u = z < 0 ? 0ull - (uint64_t)z : (uint64_t)z;
-  const int lz = __clzll((long long)u);
-  int e = 63 - lz - s + 127;
-  *ok = u != 0 && e >= 1 && e <= 254;
-  e = e < 1 ? 1 : (e > 254 ? 254 : e);
-  const uint32_t mant = u ? (uint32_t)((u << lz) >> 40) & 0x7fffffu : 0u;
-  return __uint_as_float(((uint32_t)e << 23) | mant);
 }
 
 __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
@@ -1097,7 +1124,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
   bool on = false, on_n = false;
   if (tile < C.ntiles) {
     d = C.tiles[tile];
-    on = tile_on_chip(d, C.stage_cap, C.err);
+    on = tile_on_chip(d, C.st.cap, C.err);
     if (on) prefetch_tile(S, 0, d, C);
   }
   if (tile + gridDim.x < C.ntiles) dn = C.tiles[tile + gridDim.x];
@@ -1109,7 +1136,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
     cp_async_wait_all();
     __syncthreads();  // records of this tile in place; the previous tile is done
     if (tile + gridDim.x < C.ntiles) {
-      on_n = tile_on_chip(dn, C.stage_cap, C.err);
+      on_n = tile_on_chip(dn, C.st.cap, C.err);
       if (on_n) prefetch_tile(S, buf ^ 1, dn, C);
     } else {
       on_n = false;
@@ -1118,6 +1145,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
     for (int i = threadIdx.x; i < kSlots / 32; i += kCellThreads) S.psibit[buf ^ 1][i] = 0u;
     const uint32_t npsi = d.psi_hi - d.psi_lo;
     const bool psi_local = npsi <= (uint32_t)kPsiCap;
+    const bool packed = d.kind == kTilePacked;
     if (on && psi_local) {
       // psi markers: claim a slot, or flag the slot a record already holds
       for (uint32_t q = threadIdx.x; q < npsi; q += kCellThreads) {
@@ -1134,7 +1162,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
               break;
             }
           }
-          if (slot_key(S, buf, cur) == key) break;
+          if (slot_key(S, buf, cur, packed, d.alpha) == key) break;
           h = (h + 1) & (kSlots - 1);
         }
         if (probe == kSlots) atomicOr(C.err, kErrTile);  // cannot happen at load < 3/4
@@ -1150,8 +1178,8 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
       for (int base = 0; base + warp_base < nrec; base += kCellThreads) {
         const int e = base + (int)threadIdx.x;
         int claimed = -1;
-        if (e < nrec && !is_dropped(S.val[buf][e])) {
-          const uint64_t key = S.key[buf][e];
+        if (e < nrec && !is_dropped(S.rec[buf][e].v)) {
+          const uint64_t key = rec_key(S, buf, (uint32_t)e, packed, d.alpha);
           uint32_t h = (uint32_t)mix_key(key) & (kSlots - 1);
           int probe = 0;
           for (; probe < kSlots; ++probe) {
@@ -1164,7 +1192,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
                 break;
               }
             }
-            if (slot_key(S, buf, cur) == key) {
+            if (slot_key(S, buf, cur, packed, d.alpha) == key) {
               const uint32_t old = atomicExch(&S.slot[h], (uint32_t)e);
               if (old & kPsiBit) {  // the first record of a psi marker's target
                 S.next[e] = kEndList;
@@ -1212,7 +1240,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
           const uint32_t h = S.targets[idx];
           const uint32_t e = S.slot[h];
           S.slot[h] = kEmptySlot;
-          key = S.key[buf][e];
+          key = rec_key(S, buf, e, packed, d.alpha);
           ++my_unique;
           const bool in_psi = psi_local ? ((S.psibit[buf][h >> 5] >> (h & 31)) & 1u) != 0u
                                         : psi_contains(C.psi_ht, C.psi_mask, key, C.err);
@@ -1220,18 +1248,14 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
             ++my_excl;
           } else {
             const double num = list_numerator(S, buf, e, C.err);
-            const int64_t den_x = C.E0_x - S.haa[buf][e];
             pass = true;
             if (C.tau > 0.0) {
-              bool okn, okd;
+              bool okn;
               const float nf = abs_as_float(num, &okn);
-              const float df = abs_scaled_as_float(den_x, C.s, &okd);
-              if (okn && okd) pass = nf >= C.tau_f * df * 0.99999f;  // else the exact test decides
+              const float df = fabsf(S.rec[buf][e].den);
+              if (okn && df != 0.0f) pass = nf >= C.tau_f * df * 0.99999f;  // else the exact test decides
             }
-            if (pass) {
-              sc = num / (__ll2double_rn(den_x) * C.inv_scale);
-              pass = fabs(sc) >= C.tau;
-            }
+            sc = num;  // the exact score is formed after the launch (k_exact_scores)
           }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, pass);
@@ -1280,7 +1304,7 @@ __global__ void k_tile_gather(const TileDesc *tiles, const uint32_t *list, uint3
 
 // Records of every oversized tile, concatenated: key = (tile position << 32 |
 // beta'), payload = position in the concatenation; src = staging index.
-__global__ void k_big_gather(const uint64_t *sb_key, const uint32_t *start, const uint32_t *off,
+__global__ void k_big_gather(const StageRec *rec, const uint32_t *start, const uint32_t *off,
                              uint32_t nt, uint64_t total, uint64_t *keys, uint32_t *idx,
                              uint32_t *src) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -1291,7 +1315,7 @@ __global__ void k_big_gather(const uint64_t *sb_key, const uint32_t *start, cons
       if (off[mid] <= i) lo = mid; else hi = mid - 1;
     }
     const uint32_t st = start[lo] + (uint32_t)(i - off[lo]);
-    keys[i] = ((uint64_t)lo << 32) | (sb_key[st] >> 32);  // beta' is the high word
+    keys[i] = ((uint64_t)lo << 32) | rec[st].beta;
     idx[i] = (uint32_t)i;
     src[i] = st;
   }
@@ -1309,7 +1333,7 @@ __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const ui
     int emax = 1, live = 0;
     double w[4] = {0.0, 0.0, 0.0, 0.0};
     for (uint64_t e = i; e < n && keys[e] == sk; ++e) {
-      const double v = C.sb_val[src[idx[e]]];
+      const double v = C.st.rec[src[idx[e]]].v;
       if (is_dropped(v)) continue;
       const int ex = fx_exponent(v);
       emax = ex > emax ? ex : emax;
@@ -1329,7 +1353,7 @@ __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const ui
       Fx192 acc = {0, 0, 0};
       unsigned ovf = 0;
       for (uint64_t e = i; e < n && keys[e] == sk; ++e) {
-        const double v = C.sb_val[src[idx[e]]];
+        const double v = C.st.rec[src[idx[e]]].v;
         if (is_dropped(v)) continue;
         Fx192 x = fx_from_double(v, frac, &ovf);
         fx_add(acc, x);
@@ -1343,9 +1367,15 @@ __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const ui
       ++my_excl;
       continue;
     }
-    const int64_t den_x = C.E0_x - C.sb_haa[src[idx[i]]];
-    const double sc = num / (__ll2double_rn(den_x) * C.inv_scale);
-    if (fabs(sc) >= C.tau) {
+    bool pass = true;
+    if (C.tau > 0.0) {  // float screen first, as on chip
+      bool okn;
+      const float nf = abs_as_float(num, &okn);
+      const float df = fabsf(C.st.rec[src[idx[i]]].den);
+      if (okn && df != 0.0f) pass = nf >= C.tau_f * df * 0.99999f;
+    }
+    if (pass) {  // the exact score is formed after the launch (k_exact_scores)
+      const double sc = num;
       const unsigned long long slot = atomicAdd(C.cand_count, 1ull);
       if (slot < C.cand_cap) {
         C.cand_key[slot] = full;
@@ -1542,8 +1572,8 @@ static unsigned emit_grid(size_t ntl) {
 }
 
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
-                uint32_t gb0, uint32_t gb1, uint64_t *sb_key, double *sb_val, int64_t *sb_haa,
-                uint64_t stage_cap, double eps, unsigned long long *survivors, unsigned *err,
+                uint32_t gb0, uint32_t gb1, const Stage &st, double eps,
+                unsigned long long *survivors, unsigned *err,
                 void **tiles_out, size_t *ntiles_out, const uint64_t **psi_list_out,
                 std::vector<uint32_t> *oversized, Arena &arena) {
   cudaStream_t s = arena.stream();
@@ -1676,14 +1706,11 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   A.ad_total = (uint32_t)ad_total;
   A.ad_tile_item = ad_tile_item;
   A.ad_tiles = ad_tiles;
-  A.sb_key = sb_key;
-  A.sb_val = sb_val;
-  A.sb_haa = sb_haa;
+  A.st = st;
   A.eps = eps;
   A.E0_x = F.E0_x;
   A.inv_scale = ldexp(1.0, -F.X.s);
   A.survivors = survivors;
-  A.stage_cap = stage_cap;
   A.ncore = F.ncore;
   A.err = err;
   const size_t emit_smem = 2 * (size_t)F.X.n * F.X.n * sizeof(int64_t);
@@ -1767,17 +1794,15 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
 
 size_t tile_capacity() { return (size_t)kCap; }
 
-static CellArgs cell_args(const FusedCore &F, const uint64_t *sb_key,
-                          const double *sb_val, const int64_t *sb_haa, uint64_t stage_cap,
+static CellArgs cell_args(const FusedCore &F, const Stage &st,
                           double tau, uint64_t *cand_key, double *cand_score,
                           unsigned long long *cand_count, unsigned long long cand_cap,
                           unsigned long long *n_unique, unsigned long long *n_excluded,
                           unsigned *err) {
   CellArgs CA;
   memset(&CA, 0, sizeof(CA));
-  CA.sb_key = sb_key;
-  CA.sb_val = sb_val;
-  CA.sb_haa = sb_haa;
+  CA.st = st;
+  CA.X = F.X;
   CA.E0_x = F.E0_x;
   CA.inv_scale = ldexp(1.0, -F.X.s);
   CA.s = F.X.s;
@@ -1792,7 +1817,6 @@ static CellArgs cell_args(const FusedCore &F, const uint64_t *sb_key,
   CA.cand_cap = cand_cap;
   CA.n_unique = n_unique;
   CA.n_excluded = n_excluded;
-  CA.stage_cap = stage_cap;
   CA.err = err;
   return CA;
 }
@@ -1800,15 +1824,15 @@ static CellArgs cell_args(const FusedCore &F, const uint64_t *sb_key,
 // Reduce tiles [tile_begin, tile_end) of a staged batch on chip and append the
 // targets with |S| >= tau to the candidate buffer (at most kCap per tile).
 int fused_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
-                uint32_t tile_begin, uint32_t tile_end, const uint64_t *sb_key, const double *sb_val, const int64_t *sb_haa,
-                uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
+                uint32_t tile_begin, uint32_t tile_end, const Stage &st, double tau,
+                uint64_t *cand_key, double *cand_score,
                 unsigned long long *cand_count, unsigned long long cand_cap,
                 unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
                 Arena &arena) {
   if (tile_end <= tile_begin) return ASCI_OK;
   cudaStream_t s = arena.stream();
-  CellArgs CA = cell_args(F, sb_key, sb_val, sb_haa, stage_cap, tau, cand_key, cand_score,
-                          cand_count, cand_cap, n_unique, n_excluded, err);
+  CellArgs CA = cell_args(F, st, tau, cand_key, cand_score, cand_count, cand_cap, n_unique,
+                          n_excluded, err);
   CA.tiles = static_cast<const TileDesc *>(tiles);
   CA.psi_list = psi_list;
   CA.tile0 = tile_begin;
@@ -1857,8 +1881,8 @@ int tile_info(const void *tiles, const std::vector<uint32_t> &list, std::vector<
 // at once: their records are gathered under keys (position << 32 | beta'),
 // radix-sorted in global memory and reduced one target per thread.  Appends at
 // most as many candidates as there are records.
-int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const uint64_t *sb_key,
-                    const double *sb_val, const int64_t *sb_haa, uint64_t stage_cap, double tau,
+int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const Stage &st,
+                    double tau,
                     uint64_t *cand_key, double *cand_score, unsigned long long *cand_count,
                     unsigned long long cand_cap, unsigned long long *n_unique,
                     unsigned long long *n_excluded, unsigned *err, uint64_t *nrec_out,
@@ -1869,7 +1893,7 @@ int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const u
   std::vector<uint32_t> start(nt), off(nt + 1), alpha(nt);
   uint64_t total = 0;
   for (size_t i = 0; i < nt; ++i) {
-    if ((uint64_t)info[3 * i] + info[3 * i + 1] > stage_cap) return ASCI_ECUDA;
+    if ((uint64_t)info[3 * i] + info[3 * i + 1] > st.cap) return ASCI_ECUDA;
     start[i] = info[3 * i];
     alpha[i] = info[3 * i + 2];
     off[i] = (uint32_t)total;
@@ -1892,17 +1916,43 @@ int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const u
   ASCI_TRY_CUDA(cudaMemcpyAsync(d_start, start.data(), nt * 4, cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaMemcpyAsync(d_off, off.data(), (nt + 1) * 4, cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaMemcpyAsync(d_alpha, alpha.data(), nt * 4, cudaMemcpyDefault, s));
-  k_big_gather<<<grid_for(total), 256, 0, s>>>(sb_key, d_start, d_off, (uint32_t)nt, total, k0,
+  k_big_gather<<<grid_for(total), 256, 0, s>>>(st.rec, d_start, d_off, (uint32_t)nt, total, k0,
                                                i0, src);
   ASCI_CHECK_LAUNCH();
   int topbit = 0;
   while ((1ull << topbit) < (uint64_t)nt) ++topbit;
   ASCI_TRY(radix_sort_u64_u32(&k0, &k1, &i0, &i1, total, 0, 32 + topbit, ta));
-  CellArgs CA = cell_args(F, sb_key, sb_val, sb_haa, stage_cap, tau, cand_key, cand_score,
-                          cand_count, cand_cap, n_unique, n_excluded, err);
+  CellArgs CA = cell_args(F, st, tau, cand_key, cand_score, cand_count, cand_cap, n_unique,
+                          n_excluded, err);
   k_big_reduce<<<grid_for(total), 256, 0, s>>>(k0, i0, src, total, d_alpha, CA);
   ASCI_CHECK_LAUNCH();
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));  // the host vectors above are read by the copies
+  return ASCI_OK;
+}
+
+namespace {
+
+// Exact scores of appended candidates, which hold their numerator:
+// S = num / (E0 - H_ii), with H_ii summed in fixed point (exact) and E0 - H_ii
+// rounded once to a double.
+__global__ void k_exact_scores(const uint64_t *key, double *score, size_t n, FxInts X,
+                               int64_t E0_x, double inv_scale) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t k = key[i];
+    const int64_t den_x = E0_x - fx_diag(X, key_alpha(k), (uint32_t)(k >> 32));
+    score[i] = score[i] / (__ll2double_rn(den_x) * inv_scale);
+  }
+}
+
+}  // namespace
+
+int exact_scores(const FusedCore &F, const uint64_t *key, double *score, size_t n,
+                 cudaStream_t s) {
+  if (!n) return ASCI_OK;
+  k_exact_scores<<<grid_for(n, 152 * 32), 256, 0, s>>>(key, score, n, F.X, F.E0_x,
+                                                      ldexp(1.0, -F.X.s));
+  ASCI_CHECK_LAUNCH();
   return ASCI_OK;
 }
 

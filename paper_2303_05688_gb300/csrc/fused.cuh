@@ -20,6 +20,25 @@ struct FxInts {
   const int64_t *h1x, *ssx, *sox;
 };
 
+// One staged pair (16 bytes, written with one vector store): the value
+// H_ij c_j, the target's beta string and the denominator E0 - H_ii as a float,
+// which serves the threshold screen only; the exact diagonal is recomputed for
+// targets that pass it.
+struct __align__(16) StageRec {
+  double v;
+  uint32_t beta;
+  float den;
+};
+static_assert(sizeof(StageRec) == 16, "staged pair layout");
+
+// The staging buffer of a batch: records, and the target alpha string of the
+// records of classes packed several to a tile (other tiles know theirs).
+struct Stage {
+  StageRec *rec;
+  uint32_t *alpha;
+  uint64_t cap;  // records the buffer holds
+};
+
 // Everything the batch kernels read that stays fixed during one search.
 struct FusedCore {
   DevInts I;

@@ -48,25 +48,27 @@ int item_groups(const uint64_t *items, const uint64_t *Wexcl, uint64_t T, uint32
 int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t *mask,
                    Arena &arena);
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
-                uint32_t gb0, uint32_t gb1, uint64_t *sb_key, double *sb_val, int64_t *sb_haa,
-                uint64_t stage_cap, double eps, unsigned long long *survivors, unsigned *err,
+                uint32_t gb0, uint32_t gb1, const Stage &st, double eps,
+                unsigned long long *survivors, unsigned *err,
                 void **tiles_out, size_t *ntiles_out, const uint64_t **psi_list_out,
                 std::vector<uint32_t> *oversized, Arena &arena);
 int tile_info(const void *tiles, const std::vector<uint32_t> &list, std::vector<uint32_t> *info,
               cudaStream_t s);
-int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const uint64_t *sb_key,
-                    const double *sb_val, const int64_t *sb_haa, uint64_t stage_cap, double tau,
+int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const Stage &st,
+                    double tau,
                     uint64_t *cand_key, double *cand_score, unsigned long long *cand_count,
                     unsigned long long cand_cap, unsigned long long *n_unique,
                     unsigned long long *n_excluded, unsigned *err, uint64_t *nrec_out,
                     Arena &arena);
 int fused_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
-                uint32_t tile_begin, uint32_t tile_end, const uint64_t *sb_key, const double *sb_val, const int64_t *sb_haa,
-                uint64_t stage_cap, double tau, uint64_t *cand_key, double *cand_score,
+                uint32_t tile_begin, uint32_t tile_end, const Stage &st, double tau,
+                uint64_t *cand_key, double *cand_score,
                 unsigned long long *cand_count, unsigned long long cand_cap,
                 unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
                 Arena &arena);
 size_t tile_capacity();
+int exact_scores(const FusedCore &F, const uint64_t *key, double *score, size_t n,
+                 cudaStream_t s);
 int abs_min(const double *s, size_t n, double *host_min, Arena &arena);
 
 static thread_local char g_last_error[512] = "";
@@ -578,7 +580,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     if (bmax == 0) {
       size_t fr = 0, tot = 0;
       ASCI_TRY_CUDA(cudaMemGetInfo(&fr, &tot));
-      bmax = (uint64_t)(fr / 2) / 32;  // staging record: 24 bytes
+      bmax = (uint64_t)(fr / 2) / 28;  // staging record: 16 bytes, alpha word: 4
       bmax = std::max<uint64_t>(bmax, 1ull << 20);
       bmax = std::min<uint64_t>(bmax, 1ull << 31);
     }
@@ -662,17 +664,14 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   const size_t cap_extra =
       std::max<size_t>(tile_capacity() * (size_t)sms * 16, std::min<uint64_t>(bcap, 1ull << 28));
   const size_t pool_cap = N + cap_extra;
-  uint64_t *sb_key = nullptr;
-  double *sb_val = nullptr;
-  int64_t *sb_haa = nullptr;
+  Stage stg = {nullptr, nullptr, bcap};
   uint64_t *pool_k[2] = {nullptr, nullptr};
   double *pool_s[2] = {nullptr, nullptr};
   unsigned long long *dcount = nullptr;  // [0] candidates, [1] unique, [2] excluded, [3] survivors
   unsigned *derr2 = nullptr;
   if (bcap) {
-    ASCI_TRY(arena.alloc(&sb_key, bcap));
-    ASCI_TRY(arena.alloc(&sb_val, bcap));
-    ASCI_TRY(arena.alloc(&sb_haa, bcap));
+    ASCI_TRY(arena.alloc(&stg.rec, bcap));
+    ASCI_TRY(arena.alloc(&stg.alpha, bcap));
     for (int i = 0; i < 2; ++i) {
       ASCI_TRY(arena.alloc(&pool_k[i], pool_cap));
       ASCI_TRY(arena.alloc(&pool_s[i], pool_cap));
@@ -717,9 +716,8 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
                (unsigned long long)b.P1, gg[0], gg[1] + 1);
     std::vector<uint32_t> oversized;
     const uint64_t *psi_list = nullptr;
-    ASCI_TRY(fused_stage(F, b.t0, b.t1, b.P0, b.P1, gg[0], gg[1] + 1, sb_key, sb_val, sb_haa,
-                         bcap, o.eps_search, dcount + 3, derr2, &tiles, &ntiles, &psi_list,
-                         &oversized, ba));
+    ASCI_TRY(fused_stage(F, b.t0, b.t1, b.P0, b.P1, gg[0], gg[1] + 1, stg, o.eps_search,
+                         dcount + 3, derr2, &tiles, &ntiles, &psi_list, &oversized, ba));
     ASCI_TRACE("staged: tiles=%zu oversized=%zu", ntiles, oversized.size());
     tm.stop(&tl[2]);
     tm.start();
@@ -738,7 +736,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
       }
       const size_t t1 = std::min(ntiles, t + room);
       ASCI_TRACE("cells: tiles [%zu,%zu) tau=%.6g pool=%zu", t, t1, tau, pool_n);
-      ASCI_TRY(fused_cells(F, tiles, psi_list, (uint32_t)t, (uint32_t)t1, sb_key, sb_val, sb_haa, bcap, tau,
+      ASCI_TRY(fused_cells(F, tiles, psi_list, (uint32_t)t, (uint32_t)t1, stg, tau,
                            pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1, dcount + 2,
                            derr2, ba));
       unsigned long long c = 0;
@@ -753,6 +751,9 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
         return ASCI_ECUDA;
       }
       if (c > pool_cap) return ASCI_ECUDA;  // cannot happen: room bounds the appends
+      // appended candidates carry their numerator: form their exact scores
+      ASCI_TRY(exact_scores(F, pool_k[pcur] + pool_n, pool_s[pcur] + pool_n, (size_t)c - pool_n,
+                            stream));
       pool_n = (size_t)c;
       t = t1;
       if (pool_n > N && (pool_cap - pool_n) < pool_cap / 2) {
@@ -782,9 +783,9 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
         size_t j = i;
         while (j < oversized.size() && total + info[3 * j + 1] <= room) total += info[3 * j++ + 1];
         uint64_t nrec = 0;
-        ASCI_TRY(fused_big_tiles(F, info.data() + 3 * i, j - i, sb_key, sb_val, sb_haa, bcap,
-                                 tau, pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1,
-                                 dcount + 2, derr2, &nrec, ba));
+        ASCI_TRY(fused_big_tiles(F, info.data() + 3 * i, j - i, stg, tau, pool_k[pcur],
+                                 pool_s[pcur], dcount, pool_cap, dcount + 1, dcount + 2, derr2,
+                                 &nrec, ba));
         unsigned long long c = 0;
         unsigned he = 0;
         ASCI_TRY_CUDA(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDefault, stream));
@@ -797,6 +798,8 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
           return ASCI_ECUDA;
         }
         if (c > pool_cap) return ASCI_ECUDA;
+        ASCI_TRY(exact_scores(F, pool_k[pcur] + pool_n, pool_s[pcur] + pool_n,
+                              (size_t)c - pool_n, stream));
         pool_n = (size_t)c;
         ASCI_TRACE("oversized tiles: [%zu,%zu) %llu records, pool=%zu", i, j,
                    (unsigned long long)nrec, pool_n);
