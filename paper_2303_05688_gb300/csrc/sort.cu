@@ -133,69 +133,85 @@ __global__ void k_digit_hist(const uint64_t *keys, size_t n, int shift, uint32_t
   hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// lanes of this warp whose digit equals mine (8 ballots)
-__device__ __forceinline__ uint32_t digit_peers(uint32_t d, uint32_t active) {
-  uint32_t peers = active;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-    peers &= ((d >> b) & 1u) ? bal : ~bal;
-  }
-  return peers;
+// Shared memory of the scatter: the tile's keys (and values) in digit order,
+// per-warp digit counters, and each digit's tile start and global offset.
+template <typename V, bool kHasVals>
+constexpr size_t scatter_smem() {
+  return (size_t)kSortTile * sizeof(uint64_t) + (kHasVals ? (size_t)kSortTile * sizeof(V) : 0) +
+         (size_t)(kSortWarps + 2) * kRadix * sizeof(uint32_t);
 }
 
 // Stable scatter of one tile.  Warp w owns elements [w*32*kSortItems, ...) of
 // the tile in rounds of 32 consecutive elements, so tile order is preserved.
+// The tile is first placed in shared memory in digit order; each digit's run
+// is then written to its global position with consecutive threads on
+// consecutive addresses.
 template <typename V, bool kHasVals>
 __global__ void __launch_bounds__(kSortThreads)
     k_digit_scatter(const uint64_t *keys_in, const V *vals_in, uint64_t *keys_out, V *vals_out,
                     size_t n, int shift, const uint32_t *offsets, uint32_t ntiles) {
-  __shared__ uint32_t warp_base[kSortWarps][kRadix];
+  extern __shared__ __align__(16) unsigned char sm[];
+  uint64_t *sk = reinterpret_cast<uint64_t *>(sm);
+  V *sv = reinterpret_cast<V *>(sk + kSortTile);
+  uint32_t *wb = reinterpret_cast<uint32_t *>(sm + (size_t)kSortTile * sizeof(uint64_t) +
+                                              (kHasVals ? (size_t)kSortTile * sizeof(V) : 0));
+  uint32_t *dstart = wb + kSortWarps * kRadix;  // digit start within the tile
+  uint32_t *dglob = dstart + kRadix;            // digit start in the output
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads)
-    (&warp_base[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) wb[i] = 0;
   __syncthreads();
-  const size_t wbase = (size_t)blockIdx.x * kSortTile + (size_t)warp * 32 * kSortItems;
+  const size_t base = (size_t)blockIdx.x * kSortTile;
+  const size_t wbase = base + (size_t)warp * 32 * kSortItems;
   uint64_t k[kSortItems];
   uint32_t d[kSortItems];
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    size_t idx = wbase + (size_t)r * 32 + lane;
-    bool ok = idx < n;
+    const size_t idx = wbase + (size_t)r * 32 + lane;
+    const bool ok = idx < n;
     k[r] = ok ? keys_in[idx] : 0ull;
-    d[r] = ok ? (uint32_t)((k[r] >> shift) & 0xffu) : 0u;
-    uint32_t active = __ballot_sync(0xffffffffu, ok);
-    uint32_t peers = digit_peers(d[r], active);
-    if (ok && lane == __ffs(peers) - 1) warp_base[warp][d[r]] += __popc(peers);
+    d[r] = ok ? (uint32_t)((k[r] >> shift) & 0xffu) : (uint32_t)kRadix;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d[r]);
+    if (ok && lane == __ffs(peers) - 1) wb[warp * kRadix + d[r]] += __popc(peers);
   }
   __syncthreads();
-  // per digit: tile offset + counts of earlier warps
   {
+    // per digit: offsets of the warps within the digit's run, the run's start
+    // in the tile (scan over digits) and in the output
     const int dig = threadIdx.x;  // kSortThreads == kRadix
-    uint32_t run = offsets[(size_t)dig * ntiles + blockIdx.x];
+    uint32_t cnt = 0;
     for (int w = 0; w < kSortWarps; ++w) {
-      uint32_t c = warp_base[w][dig];
-      warp_base[w][dig] = run;
-      run += c;
+      const uint32_t c = wb[w * kRadix + dig];
+      wb[w * kRadix + dig] = cnt;
+      cnt += c;
     }
+    dstart[dig] = block_exclusive_scan<uint32_t>(cnt, nullptr);
+    dglob[dig] = offsets[(size_t)dig * ntiles + blockIdx.x];
   }
   __syncthreads();
   const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    size_t idx = wbase + (size_t)r * 32 + lane;
-    bool ok = idx < n;
-    uint32_t active = __ballot_sync(0xffffffffu, ok);
-    uint32_t peers = digit_peers(d[r], active);
+    const size_t idx = wbase + (size_t)r * 32 + lane;
+    const bool ok = idx < n;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d[r]);
     uint32_t pos = 0;
-    if (ok) pos = warp_base[warp][d[r]] + __popc(peers & lt);
+    if (ok) pos = dstart[d[r]] + wb[warp * kRadix + d[r]] + __popc(peers & lt);
     __syncwarp();
-    if (ok && lane == __ffs(peers) - 1) warp_base[warp][d[r]] += __popc(peers);
+    if (ok && lane == __ffs(peers) - 1) wb[warp * kRadix + d[r]] += __popc(peers);
     __syncwarp();
     if (ok) {
-      keys_out[pos] = k[r];
-      if (kHasVals) vals_out[pos] = vals_in[idx];
+      sk[pos] = k[r];
+      if (kHasVals) sv[pos] = vals_in[idx];
     }
+  }
+  __syncthreads();
+  const uint32_t tn = (uint32_t)((n - base) < (size_t)kSortTile ? (n - base) : (size_t)kSortTile);
+  for (uint32_t i = threadIdx.x; i < tn; i += kSortThreads) {
+    const uint64_t key = sk[i];
+    const uint32_t dg = (uint32_t)((key >> shift) & 0xffu);
+    const uint32_t gpos = dglob[dg] + (i - dstart[dg]);
+    keys_out[gpos] = key;
+    if (kHasVals) vals_out[gpos] = sv[i];
   }
 }
 
@@ -208,6 +224,13 @@ int radix_sort_impl(uint64_t **keys, uint64_t **keys_alt, V **vals, V **vals_alt
   uint32_t ntiles = (uint32_t)((n + kSortTile - 1) / kSortTile);
   uint32_t *hist = nullptr;
   ASCI_TRY(arena.alloc(&hist, (size_t)kRadix * ntiles));
+  static bool attr_set = false;  // one flag per instantiation
+  if (!attr_set) {
+    ASCI_TRY_CUDA(cudaFuncSetAttribute(k_digit_scatter<V, kHasVals>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)scatter_smem<V, kHasVals>()));
+    attr_set = true;
+  }
   uint64_t mask = 0;
   ASCI_TRY(varying_bits_u64(*keys, n, &mask, arena));
   for (int shift = begin_bit; shift < end_bit; shift += 8) {
@@ -217,7 +240,7 @@ int radix_sort_impl(uint64_t **keys, uint64_t **keys_alt, V **vals, V **vals_alt
     k_digit_hist<<<ntiles, kSortThreads, 0, s>>>(*keys, n, shift, hist, ntiles);
     ASCI_CHECK_LAUNCH();
     ASCI_TRY(scan_exclusive<uint32_t>(hist, hist, (size_t)kRadix * ntiles, arena));
-    k_digit_scatter<V, kHasVals><<<ntiles, kSortThreads, 0, s>>>(
+    k_digit_scatter<V, kHasVals><<<ntiles, kSortThreads, scatter_smem<V, kHasVals>(), s>>>(
         *keys, kHasVals ? *vals : nullptr, *keys_alt, kHasVals ? *vals_alt : nullptr, n, shift,
         hist, ntiles);
     ASCI_CHECK_LAUNCH();
