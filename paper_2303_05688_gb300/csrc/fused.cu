@@ -299,9 +299,11 @@ constexpr uint32_t kGroupsPerTile = 1024;
 
 namespace {
 
+// Tile kind of each class and its staging slots: its pairs in place, or kCap
+// slots for each hash bucket of a big class.
 __global__ void k_group_class(const uint64_t *g_P0, uint32_t gb0, uint32_t gb1, uint64_t Pend,
                               uint32_t *kind, uint32_t *nb, uint64_t *small_pairs,
-                              uint32_t *small_cnt) {
+                              uint32_t *small_cnt, uint64_t *slots) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < gb1 - gb0;
        i += gridDim.x * blockDim.x) {
     const uint32_t g = gb0 + i;
@@ -310,6 +312,7 @@ __global__ void k_group_class(const uint64_t *g_P0, uint32_t gb0, uint32_t gb1, 
     kind[i] = k;
     nb[i] = k == kTileBucket ? (uint32_t)((P + kBucketTarget - 1) / kBucketTarget) : 0u;
     small_pairs[i] = k == kTilePacked ? P : 0;
+    slots[i] = k == kTileBucket ? (uint64_t)nb[i] * kCap : P;
     small_cnt[i] = k == kTilePacked ? 1u : 0u;
   }
 }
@@ -329,17 +332,14 @@ __global__ void k_tile_count(uint32_t ng, const uint32_t *kind, const uint32_t *
                                       : (kind[i] == kTileMedium ? 1u : nb[i]);
 }
 
-__global__ void k_tile_write(uint32_t gb0, uint32_t ng, uint64_t P0, uint64_t Pend,
+__global__ void k_tile_write(uint32_t gb0, uint32_t ng, const uint64_t *soff, uint64_t Pend,
                              const uint64_t *g_P0, const uint32_t *g_alpha,
                              const uint32_t *kind, const uint32_t *nb, const uint64_t *Ws,
-                             const uint32_t *Ns, const uint32_t *tile_base,
-                             const uint32_t *cellbase, const uint32_t *cnt,
-                             const uint32_t *cnt_scan, TileDesc *tiles, uint32_t *cell_pos0,
-                             unsigned *n_over, uint32_t *over_list, uint32_t over_cap) {
+                             const uint32_t *Ns, const uint32_t *tile_base, TileDesc *tiles) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
     const uint32_t g = gb0 + i;
     const uint64_t P = ((i + 1 < ng) ? g_P0[g + 1] : Pend) - g_P0[g];
-    const uint32_t start = (uint32_t)(g_P0[g] - P0);
+    const uint32_t start = (uint32_t)soff[i];
     const uint32_t k = kind[i];
     if (k == kTilePacked) {
       const bool st = packed_start(i, kind, Ws, Ns);
@@ -362,25 +362,59 @@ __global__ void k_tile_write(uint32_t gb0, uint32_t ng, uint64_t P0, uint64_t Pe
       d.alpha = g_alpha[g];
       d.psi_lo = d.psi_hi = 0;
       tiles[tile_base[i]] = d;
-    } else {
-      const uint32_t cb = cellbase[i];
-      for (uint32_t b = 0; b < nb[i]; ++b) {
-        TileDesc d;
-        d.start = start + (cnt_scan[cb + b] - cnt_scan[cb]);
-        d.npairs = cnt[cb + b];
-        d.g0 = g;
-        d.ng = 1;
-        d.kind = kTileBucket;
-        d.alpha = g_alpha[g];
-        d.psi_lo = d.psi_hi = 0;
-        if (d.npairs > (uint32_t)kCap) {
-          // too large for one tile on chip: reduced through the global sort
-          const unsigned slot = atomicAdd(n_over, 1u);
-          if (slot < over_cap) over_list[slot] = tile_base[i] + b;
-        }
-        tiles[tile_base[i] + b] = d;
-        cell_pos0[cb + b] = d.start;
-      }
+    }
+  }
+}
+
+// Bucket tiles of big classes, one thread per cell: the class holding cell c
+// is the last one whose first cell is at or before c.  Bucket b of a class
+// owns kCap staging slots; its record count is known after emission.
+__global__ void k_cell_write(uint32_t gb0, uint32_t ng, uint32_t ncells, const uint64_t *soff,
+                             const uint32_t *g_alpha, const uint32_t *tile_base,
+                             const uint32_t *cellbase, TileDesc *tiles, uint32_t *cell_pos0,
+                             uint32_t *cell_tile) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
+       c += gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = ng - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (cellbase[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t g = gb0 + lo, b = c - cellbase[lo];
+    TileDesc d;
+    d.start = (uint32_t)(soff[lo] + (uint64_t)b * kCap);
+    d.npairs = 0;
+    d.g0 = g;
+    d.ng = 1;
+    d.kind = kTileBucket;
+    d.alpha = g_alpha[g];
+    d.psi_lo = d.psi_hi = 0;
+    tiles[tile_base[lo] + b] = d;
+    cell_pos0[c] = d.start;
+    cell_tile[c] = tile_base[lo] + b;
+  }
+}
+
+// Sort keys of the spilled records: tile << 32 | spill index.
+__global__ void k_spill_keys(const uint32_t *spill_cell, const uint32_t *cell_tile, uint32_t n,
+                             uint64_t *keys) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    keys[j] = ((uint64_t)cell_tile[spill_cell[j]] << 32) | j;
+}
+
+// Record counts of the bucket tiles after emission; a bucket that received
+// more than kCap records (its surplus is in the spill list) is reduced by the
+// global path.
+__global__ void k_cell_finish(uint32_t ncells, const uint32_t *fill, const uint32_t *cell_tile,
+                              TileDesc *tiles, unsigned *n_over, uint32_t *over_list,
+                              uint32_t over_cap) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
+       c += gridDim.x * blockDim.x) {
+    const uint32_t f = fill[c], t = cell_tile[c];
+    tiles[t].npairs = f;
+    if (f > (uint32_t)kCap) {
+      const unsigned slot = atomicAdd(n_over, 1u);
+      if (slot < over_cap) over_list[slot] = t;
     }
   }
 }
@@ -429,9 +463,14 @@ struct EmitArgs {
   const int64_t *Dx, *Fa, *Fb;
   uint32_t gb0;
   const uint32_t *kind, *nb, *cellbase;
-  uint32_t *cnt;              // count mode
-  const uint32_t *cell_pos0;  // emit mode
-  uint32_t *fill;             // emit mode
+  const uint64_t *soff;       // first staging slot of each class of the batch
+  const uint64_t *g_P0;       // first pair of each class
+  const uint32_t *cell_pos0;  // first staging slot of each bucket cell
+  uint32_t *fill;             // records placed in each bucket cell
+  StageRec *spill_rec;        // records beyond a cell's kCap slots
+  uint32_t *spill_cell;
+  unsigned *n_spill;
+  uint32_t spill_cap;
   const uint64_t *runs;       // (item - t0) << 32 | determinant in the group
   uint64_t nruns;
   const uint32_t *adl;        // alpha-double items (item - t0)
@@ -492,29 +531,32 @@ __device__ __forceinline__ int64_t shfl64(int64_t x, int src) {
   return (int64_t)__shfl_sync(0xffffffffu, (long long)x, src);
 }
 
-// Staging position of one pair: in place for classes that fit a tile, else
-// the next free slot of its hash-bucket cell (warp-aggregated counters).  In
-// count mode only the cell counters advance.  Returns false in count mode or
-// for an idle lane.
-template <int MODE>
+// Staging position of one pair: in place for classes that fit a tile (slot
+// `inplace`), else the next free slot of its hash-bucket cell (warp-aggregated
+// counters) or, once the cell holds kCap records, the next entry of the spill
+// list (*spill set, *pos the entry).  Returns false for an idle lane.
 __device__ __forceinline__ bool pair_position(const EmitArgs &A, bool big, bool valid,
-                                              uint32_t cell, uint64_t p, uint32_t *pos) {
+                                              uint32_t cell, uint32_t inplace, uint32_t *pos,
+                                              bool *spill) {
   const int lane = threadIdx.x & 31;
+  *spill = false;
   if (big) {  // warp-uniform
     const uint32_t peers = __match_any_sync(0xffffffffu, valid ? cell : 0xffffffffu);
     const int leader = __ffs(peers) - 1;
-    if (MODE == 0) {
-      if (valid && lane == leader) atomicAdd(&A.cnt[cell], (uint32_t)__popc(peers));
-      return false;
-    }
     uint32_t base = 0;
     if (valid && lane == leader) base = atomicAdd(&A.fill[cell], (uint32_t)__popc(peers));
     base = __shfl_sync(0xffffffffu, base, leader);
-    *pos = A.cell_pos0[cell] + base + __popc(peers & ((1u << lane) - 1u));
+    const uint32_t slot = base + __popc(peers & ((1u << lane) - 1u));
+    if (slot < (uint32_t)kCap) {
+      *pos = A.cell_pos0[cell] + slot;
+    } else if (valid) {
+      *spill = true;
+      *pos = atomicAdd(A.n_spill, 1u);
+    }
   } else {
-    *pos = (uint32_t)(p - A.P0);
+    *pos = inplace;
   }
-  return MODE == 1 && valid;
+  return valid;
 }
 
 // z * 2^-s as a float built from the bits (truncated, relative error below
@@ -530,39 +572,42 @@ __device__ __forceinline__ float scaled_as_float(int64_t z, int s) {
 }
 
 template <bool EPS>
-__device__ __forceinline__ void write_record(const EmitArgs &A, uint32_t pos, uint32_t talpha,
-                                             uint32_t tb, bool packed, double v, int64_t haa,
-                                             bool *kept) {
+__device__ __forceinline__ void write_record(const EmitArgs &A, uint32_t pos, bool spill,
+                                             uint32_t cell, uint32_t talpha, uint32_t tb,
+                                             bool packed, double v, int64_t haa, bool *kept) {
   if (EPS) {
     // |v / (E0 - H_ii)| > eps, without a division
     const double den = __ll2double_rn(A.E0_x - haa) * A.inv_scale;
     if (!(fabs(v) > A.eps * fabs(den))) v = drop_marker();
     *kept = !is_dropped(v);
   }
-  if (pos < A.st.cap) {
-    const uint64_t vb = (uint64_t)__double_as_longlong(v);
-    reinterpret_cast<uint4 *>(A.st.rec)[pos] =
-        make_uint4((uint32_t)vb, (uint32_t)(vb >> 32), tb,
-                   __float_as_uint(scaled_as_float(A.E0_x - haa, A.X.s)));
+  const uint64_t vb = (uint64_t)__double_as_longlong(v);
+  const uint4 r = make_uint4((uint32_t)vb, (uint32_t)(vb >> 32), tb,
+                             __float_as_uint(scaled_as_float(A.E0_x - haa, A.X.s)));
+  if (spill) {
+    if (pos < A.spill_cap) {  // beyond: counted only, the host reports it
+      reinterpret_cast<uint4 *>(A.spill_rec)[pos] = r;
+      A.spill_cell[pos] = cell;
+    }
+  } else if (pos < A.st.cap) {
+    reinterpret_cast<uint4 *>(A.st.rec)[pos] = r;
     if (packed) A.st.alpha[pos] = talpha;
   } else {
     atomicOr(A.err, kErrStage);
   }
 }
 
-// MODE 0 counts the bucket sizes of big classes, MODE 1 emits the records;
 // EPS compiles Alg. 2's screen in (eps > 0).
-template <int MODE, bool EPS>
+template <bool EPS>
 __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
   extern __shared__ int64_t s_fx[];  // emit mode: jk[n*n], jj[n*n]
   __shared__ uint16_t s_pair[kPairTab];
   const int n = A.I.n;
   int64_t *s_jk = s_fx, *s_jj = s_fx + n * n;
-  if (MODE == 1)
-    for (int t = threadIdx.x; t < n * n; t += kRunThreads) {
-      s_jk[t] = A.X.jk[t];
-      s_jj[t] = A.X.jj[t];
-    }
+  for (int t = threadIdx.x; t < n * n; t += kRunThreads) {
+    s_jk[t] = A.X.jk[t];
+    s_jj[t] = A.X.jj[t];
+  }
   for (int r = threadIdx.x; r < kPairTab; r += kRunThreads) {
     int x, y;
     unrank_pair((uint32_t)r, &x, &y);
@@ -585,7 +630,6 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
     const uint32_t gi = A.item_group[t] - A.gb0;
     const uint32_t kd = A.kind[gi];
     const bool big = kd == kTileBucket, packed = kd == kTilePacked;
-    if (MODE == 0 && !big) continue;
     const uint32_t jdx = A.grp_start[k] + m;
     if (jdx >= A.ncore) {
       if (lane == 0) atomicOr(A.err, kErrCore);
@@ -595,6 +639,8 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
     const uint32_t Ak = A.grp_alpha[k], B = A.core_beta[jdx];
     const uint32_t npd = o == 0 ? A.npd0 : A.npd1;
     const uint64_t p0 = A.Wexcl[t] + (uint64_t)m * npd;
+    // in-place staging slot of the run's first pair (classes that fit a tile)
+    const uint32_t off0 = (uint32_t)(A.soff[gi] + (p0 - A.g_P0[A.gb0 + gi]));
     const uint32_t cell0 = big ? A.cellbase[gi] : 0u, nbk = big ? A.nb[gi] : 1u;
     // lane L: the L-th occupied and the L-th virtual beta orbital of B
     const int occL = lane < (int)A.E.nb ? nth_set_bit(B, lane) : 0;
@@ -608,7 +654,7 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
     uint32_t pa = 0;
     double h0 = 0.0;  // the alpha single alone
     const double *erow = A.I.eri;
-    if (MODE == 1) {
+    {
       c = A.core_c[jdx];
       base_x = A.Dx[jdx];
       const int64_t *Fb = A.Fb + (size_t)jdx * n;
@@ -641,8 +687,8 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
     struct Chunk {
       uint32_t h1, h2, p1, p2;
       int op, bi, bj, ba, bb;
-      uint32_t tb, pos;
-      bool valid, wr;
+      uint32_t tb, pos, cell;
+      bool valid, wr, spill;
     };
     auto decode = [&](uint32_t e0, Chunk &q) {
       const uint32_t e = e0 + lane;
@@ -672,9 +718,9 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
       q.tb = B;
       if (q.op == 1) q.tb ^= (1u << q.bi) | (1u << q.ba);
       if (q.op == 2) q.tb ^= (1u << q.bi) | (1u << q.bj) | (1u << q.ba) | (1u << q.bb);
-      const uint32_t cell = big ? cell0 + bucket_of(q.tb, nbk) : 0u;
+      q.cell = big ? cell0 + bucket_of(q.tb, nbk) : 0u;
       q.pos = 0;
-      q.wr = pair_position<MODE>(A, big, q.valid, cell, p0 + e, &q.pos);
+      q.wr = pair_position(A, big, q.valid, q.cell, off0 + e, &q.pos, &q.spill);
     };
     // software-pipelined: the next chunk's staging slots (an atomic for big
     // classes) are claimed before this chunk's matrix elements are formed
@@ -685,7 +731,7 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
       if (e0 + 32 < npd) decode(e0 + 32, nxt);  // warp-uniform
       double h = 0.0;
       int64_t dh = 0;
-      if (MODE == 1) {
+      {
         const int64_t vo1 = shfl64(Vo, (int)cur.h1), vv1 = shfl64(Vv, (int)cur.p1);
         int64_t vo2 = 0, vv2 = 0;
         if (o == 0) {  // warp-uniform
@@ -710,7 +756,9 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
         }
       }
       bool kept = false;
-      if (cur.wr) write_record<EPS>(A, cur.pos, talpha, cur.tb, packed, h * c, base_x + dh, &kept);
+      if (cur.wr)
+        write_record<EPS>(A, cur.pos, cur.spill, cur.cell, talpha, cur.tb, packed, h * c,
+                          base_x + dh, &kept);
       if (EPS) {
         const uint32_t nk = __popc(__ballot_sync(0xffffffffu, kept));
         if (lane == 0 && nk) atomicAdd(A.survivors, (unsigned long long)nk);
@@ -721,16 +769,17 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
 }
 
 // Alpha-double pairs, flat: CTA step s covers flat pairs [s * kAdTile, ...).
-template <int MODE, bool EPS>
+template <bool EPS>
 __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
   __shared__ uint32_t sF[kAdTile + 1];    // first flat pair of each item in the step
-  __shared__ uint64_t sW[kAdTile + 1];    // first pair of the item in the batch order
+  __shared__ uint32_t sPos[kAdTile + 1];  // in-place staging slot of the item's first pair
   __shared__ uint32_t sG[kAdTile + 1];    // first core determinant of the item's group
   __shared__ uint32_t sOrb[kAdTile + 1];  // i | a << 5 | j << 10 | b << 15
   __shared__ uint32_t sTA[kAdTile + 1];   // target alpha string
   __shared__ uint32_t sCls[kAdTile + 1];  // class (relative to the batch)
   __shared__ double sH[kAdTile + 1];      // signed matrix element
   __shared__ int64_t sD[kAdTile + 1];     // determinant-independent diagonal change
+  __shared__ uint16_t sItem[kAdTile];     // item of each pair of the step
   const int n = A.I.n;
   const uint32_t full = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
   const uint32_t omask = (1u << A.opbits) - 1u;
@@ -747,12 +796,13 @@ __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
       const uint64_t t = A.t0 + A.adl[ja + i];
       const uint64_t it = A.items[t];
       const uint32_t k = (uint32_t)it >> A.opbits, o = (uint32_t)it & omask;
+      const uint32_t gi = A.item_group[t] - A.gb0;
       sF[i] = A.ad_off[ja + i];
-      sW[i] = A.Wexcl[t];
+      sPos[i] = (uint32_t)(A.soff[gi] + (A.Wexcl[t] - A.g_P0[A.gb0 + gi]));
       sG[i] = A.grp_start[k];
       sTA[i] = (uint32_t)(it >> 32);
-      sCls[i] = A.item_group[t] - A.gb0;
-      if (MODE == 1) {
+      sCls[i] = gi;
+      {
         const uint32_t Ak = A.grp_alpha[k];
         int ia, ja2, aa, ba;
         dec_double(Ak, ~Ak & full, o - 1 - A.E.sa, A.dv_pa_p, &ia, &ja2, &aa, &ba);
@@ -765,68 +815,57 @@ __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
       }
     }
     __syncthreads();
+    // pair -> item map of the step: each item marks its pairs
+    for (int i = threadIdx.x; i < nspan; i += kAdThreads) {
+      const uint32_t a0 = sF[i] > fb ? sF[i] : fb;
+      const uint32_t e1 = i + 1 < nspan ? sF[i + 1] : fe;
+      const uint32_t a1 = e1 < fe ? e1 : fe;
+      for (uint32_t f = a0; f < a1; ++f) sItem[f - fb] = (uint16_t)i;
+    }
+    __syncthreads();
 #pragma unroll 1
     for (uint32_t f0 = fb + (threadIdx.x & ~31u); f0 < fe; f0 += kAdThreads) {
       const uint32_t f = f0 + lane;
       const bool valid = f < fe;
-      // item of flat pair f: lane 0 searches the span, the others the next 32 items
-      int lo0 = 0;
-      if (lane == 0) {
-        int lo = 0, hi = nspan - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (sF[mid] <= f0) lo = mid; else hi = mid - 1;
-        }
-        lo0 = lo;
-      }
-      lo0 = __shfl_sync(0xffffffffu, lo0, 0);
-      int lo = lo0;
-      if (valid) {
-        int hi = (lo0 + 32 < nspan - 1) ? lo0 + 32 : nspan - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (sF[mid] <= f) lo = mid; else hi = mid - 1;
-        }
-      }
+      const int lo = valid ? (int)sItem[f - fb] : 0;
       const uint32_t q = valid ? f - sF[lo] : 0u;
       uint32_t jdx = sG[lo] + q;
       const uint32_t gi = sCls[lo];
       const bool bigl = valid && A.kind[gi] == kTileBucket;
       const bool big = __any_sync(0xffffffffu, bigl);
-      if (MODE == 0 && !big) continue;
       if (valid && jdx >= A.ncore) {
         atomicOr(A.err, kErrCore);
         jdx = 0;
       }
       const uint32_t B = valid ? A.core_beta[jdx] : 0u;
       // lanes of one warp may straddle classes of both kinds: position per lane
-      uint32_t pos = 0;
-      bool emit = false;
+      uint32_t pos = sPos[lo] + q, cell = 0;
+      bool spill = false;
       if (big) {
-        const uint32_t cell = bigl ? A.cellbase[gi] + bucket_of(B, A.nb[gi]) : 0u;
+        cell = bigl ? A.cellbase[gi] + bucket_of(B, A.nb[gi]) : 0u;
         const uint32_t peers = __match_any_sync(0xffffffffu, bigl ? cell : 0xffffffffu);
         const int leader = __ffs(peers) - 1;
-        if (MODE == 0) {
-          if (bigl && lane == leader) atomicAdd(&A.cnt[cell], (uint32_t)__popc(peers));
-          continue;
-        }
         uint32_t base = 0;
         if (bigl && lane == leader) base = atomicAdd(&A.fill[cell], (uint32_t)__popc(peers));
         base = __shfl_sync(0xffffffffu, base, leader);
-        pos = bigl ? A.cell_pos0[cell] + base + __popc(peers & ((1u << lane) - 1u))
-                   : (uint32_t)(sW[lo] + q - A.P0);
-      } else {
-        pos = (uint32_t)(sW[lo] + q - A.P0);
+        if (bigl) {
+          const uint32_t slot = base + __popc(peers & ((1u << lane) - 1u));
+          if (slot < (uint32_t)kCap) {
+            pos = A.cell_pos0[cell] + slot;
+          } else {
+            spill = true;
+            pos = atomicAdd(A.n_spill, 1u);
+          }
+        }
       }
-      emit = valid;
       bool kept = false;
-      if (MODE == 1 && emit) {
+      if (valid) {
         const uint32_t ob = sOrb[lo];
         const int64_t *Fa = A.Fa + (size_t)jdx * n;
         const int64_t dh = sD[lo] + Fa[(ob >> 5) & 31u] + Fa[(ob >> 15) & 31u] - Fa[ob & 31u] -
                            Fa[(ob >> 10) & 31u];
-        write_record<EPS>(A, pos, sTA[lo], B, A.kind[gi] == kTilePacked, sH[lo] * A.core_c[jdx],
-                          A.Dx[jdx] + dh, &kept);
+        write_record<EPS>(A, pos, spill, cell, sTA[lo], B, A.kind[gi] == kTilePacked,
+                          sH[lo] * A.core_c[jdx], A.Dx[jdx] + dh, &kept);
       }
       if (EPS) {
         const uint32_t nk = __popc(__ballot_sync(0xffffffffu, kept));
@@ -1040,7 +1079,8 @@ __device__ __forceinline__ bool tile_on_chip(const TileDesc &d, uint64_t stage_c
                                              unsigned *err) {
   const bool fits = d.npairs <= (uint32_t)kCap && (uint64_t)d.start + d.npairs <= stage_cap;
   if (!fits && threadIdx.x == 0 &&
-      !(d.kind == kTileBucket && (uint64_t)d.start + d.npairs <= stage_cap))
+      !(d.kind == kTileBucket && d.npairs > (uint32_t)kCap &&
+        (uint64_t)d.start + kCap <= stage_cap))
     atomicOr(err, kErrTile);
   return fits;
 }
@@ -1292,21 +1332,42 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
 // A bucket holding more records than one tile is sorted in global memory on
 // beta' and its runs are reduced one target per thread.
 
+// Per listed oversized tile: first in-place record, in-place count, target
+// alpha string, and its range of the tile-ordered spill list.
 __global__ void k_tile_gather(const TileDesc *tiles, const uint32_t *list, uint32_t n,
-                              uint32_t *info) {
+                              const uint64_t *spill_keys, uint32_t nspill, uint32_t *info) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const TileDesc d = tiles[list[i]];
-    info[3 * i] = d.start;
-    info[3 * i + 1] = d.npairs;
-    info[3 * i + 2] = d.alpha;
+    const uint32_t t = list[i];
+    const TileDesc d = tiles[t];
+    uint32_t lo = 0, hi = nspill;  // first spill key of tile t
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if ((uint32_t)(spill_keys[mid] >> 32) < t) lo = mid + 1; else hi = mid;
+    }
+    uint32_t e = lo;
+    while (e < nspill && (uint32_t)(spill_keys[e] >> 32) == t) ++e;
+    info[5 * i] = d.start;
+    info[5 * i + 1] = d.npairs < (uint32_t)kCap ? d.npairs : (uint32_t)kCap;
+    info[5 * i + 2] = d.alpha;
+    info[5 * i + 3] = lo;
+    info[5 * i + 4] = e - lo;
   }
 }
 
-// Records of every oversized tile, concatenated: key = (tile position << 32 |
-// beta'), payload = position in the concatenation; src = staging index.
-__global__ void k_big_gather(const StageRec *rec, const uint32_t *start, const uint32_t *off,
+// Records of every oversized tile, concatenated (in-place records, then the
+// tile's spilled ones): key = (tile position << 32 | beta'), payload =
+// position in the concatenation; src = staging index, or spill index with the
+// top bit set.
+__device__ __forceinline__ const StageRec &big_rec(const StageRec *rec, const StageRec *spill,
+                                                   uint64_t src) {
+  return (src >> 63) ? spill[(uint32_t)src] : rec[src];
+}
+
+__global__ void k_big_gather(const StageRec *rec, const StageRec *spill,
+                             const uint64_t *spill_keys, const uint32_t *start,
+                             const uint32_t *nin, const uint32_t *slo, const uint32_t *off,
                              uint32_t nt, uint64_t total, uint64_t *keys, uint32_t *idx,
-                             uint32_t *src) {
+                             uint64_t *src) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t lo = 0, hi = nt - 1;  // tile holding record i
@@ -1314,15 +1375,19 @@ __global__ void k_big_gather(const StageRec *rec, const uint32_t *start, const u
       const uint32_t mid = (lo + hi + 1) >> 1;
       if (off[mid] <= i) lo = mid; else hi = mid - 1;
     }
-    const uint32_t st = start[lo] + (uint32_t)(i - off[lo]);
-    keys[i] = ((uint64_t)lo << 32) | rec[st].beta;
+    const uint32_t o = (uint32_t)(i - off[lo]);
+    const uint64_t sr = o < nin[lo]
+                            ? (uint64_t)start[lo] + o
+                            : ((1ull << 63) | (uint32_t)spill_keys[slo[lo] + (o - nin[lo])]);
+    keys[i] = ((uint64_t)lo << 32) | big_rec(rec, spill, sr).beta;
     idx[i] = (uint32_t)i;
-    src[i] = st;
+    src[i] = sr;
   }
 }
 
-__global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const uint32_t *src,
-                             uint64_t n, const uint32_t *alpha, CellArgs C) {
+__global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const uint64_t *src,
+                             uint64_t n, const uint32_t *alpha, const StageRec *spill,
+                             CellArgs C) {
   unsigned long long my_unique = 0, my_excl = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -1333,7 +1398,7 @@ __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const ui
     int emax = 1, live = 0;
     double w[4] = {0.0, 0.0, 0.0, 0.0};
     for (uint64_t e = i; e < n && keys[e] == sk; ++e) {
-      const double v = C.st.rec[src[idx[e]]].v;
+      const double v = big_rec(C.st.rec, spill, src[idx[e]]).v;
       if (is_dropped(v)) continue;
       const int ex = fx_exponent(v);
       emax = ex > emax ? ex : emax;
@@ -1353,7 +1418,7 @@ __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const ui
       Fx192 acc = {0, 0, 0};
       unsigned ovf = 0;
       for (uint64_t e = i; e < n && keys[e] == sk; ++e) {
-        const double v = C.st.rec[src[idx[e]]].v;
+        const double v = big_rec(C.st.rec, spill, src[idx[e]]).v;
         if (is_dropped(v)) continue;
         Fx192 x = fx_from_double(v, frac, &ovf);
         fx_add(acc, x);
@@ -1371,7 +1436,7 @@ __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const ui
     if (C.tau > 0.0) {  // float screen first, as on chip
       bool okn;
       const float nf = abs_as_float(num, &okn);
-      const float df = fabsf(C.st.rec[src[idx[i]]].den);
+      const float df = fabsf(big_rec(C.st.rec, spill, src[idx[i]]).den);
       if (okn && df != 0.0f) pass = nf >= C.tau_f * df * 0.99999f;
     }
     if (pass) {  // the exact score is formed after the launch (k_exact_scores)
@@ -1575,15 +1640,18 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
                 uint32_t gb0, uint32_t gb1, const Stage &st, double eps,
                 unsigned long long *survivors, unsigned *err,
                 void **tiles_out, size_t *ntiles_out, const uint64_t **psi_list_out,
-                std::vector<uint32_t> *oversized, Arena &arena) {
+                Spill *spill_out, std::vector<uint32_t> *oversized, Arena &arena) {
   cudaStream_t s = arena.stream();
   const uint32_t ng = gb1 - gb0;
   *psi_list_out = nullptr;
+  *spill_out = Spill{nullptr, nullptr, 0};
   *ntiles_out = 0;
   oversized->clear();
   if (P1 <= P0 || ng == 0) return ASCI_OK;
   uint32_t *kind, *nb, *small_cnt, *Ns, *cellbase, *ntile, *tile_base;
-  uint64_t *small_pairs, *Ws;
+  uint64_t *small_pairs, *Ws, *slots, *soff;
+  ASCI_TRY(arena.alloc(&slots, ng));
+  ASCI_TRY(arena.alloc(&soff, ng));
   ASCI_TRY(arena.alloc(&kind, ng));
   ASCI_TRY(arena.alloc(&nb, ng));
   ASCI_TRY(arena.alloc(&small_cnt, ng));
@@ -1594,9 +1662,21 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   ASCI_TRY(arena.alloc(&small_pairs, ng));
   ASCI_TRY(arena.alloc(&Ws, ng));
   k_group_class<<<grid_for(ng), 256, 0, s>>>(F.g_P0, gb0, gb1, P1, kind, nb, small_pairs,
-                                             small_cnt);
+                                             small_cnt, slots);
   ASCI_CHECK_LAUNCH();
   ASCI_TRACE("stage: classified %u groups", ng);
+  ASCI_TRY(scan_exclusive_u64(slots, soff, ng, arena));
+  {
+    uint64_t last[2];
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&last[0], soff + ng - 1, 8, cudaMemcpyDefault, s));
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&last[1], slots + ng - 1, 8, cudaMemcpyDefault, s));
+    ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+    if (last[0] + last[1] > st.cap) {
+      record_error("staging buffer too small for the batch's hash buckets (lower max_batch_pairs)",
+                   __FILE__, __LINE__);
+      return ASCI_ENOMEM;
+    }
+  }
   ASCI_TRY(scan_exclusive_u64(small_pairs, Ws, ng, arena));
   ASCI_TRY(scan_exclusive_u32(small_cnt, Ns, ng, arena));
   ASCI_TRY(scan_exclusive_u32(nb, cellbase, ng, arena));
@@ -1657,13 +1737,54 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   }
   ASCI_TRACE("stage: runs=%zu alpha-double items=%zu pairs=%zu", nruns, nad, ad_total);
 
-  uint32_t *cnt, *cnt_scan, *cell_pos0, *fill;
-  ASCI_TRY(arena.alloc(&cnt, ncells + 1));
-  ASCI_TRY(arena.alloc(&cnt_scan, ncells + 1));
+  // tiles: packed and medium classes in place; each bucket of a big class owns
+  // kCap slots from its class's first slot on
+  TileDesc *tiles;
+  unsigned *n_over, *n_spill;
+  uint32_t *over_list, *cell_pos0, *cell_tile, *fill, *spill_cell;
+  const uint32_t over_cap = (uint32_t)std::min<size_t>(ncells + 1, 1u << 20);
+  uint32_t spill_cap = (uint32_t)std::min<uint64_t>(
+      std::max<uint64_t>(1ull << 20, (P1 - P0) / 32), 1ull << 30);
+  StageRec *spill_rec;
+  ASCI_TRY(arena.alloc(&tiles, ntiles + 1));
+  ASCI_TRY(arena.alloc(&n_over, 2));
+  n_spill = n_over + 1;
+  ASCI_TRY(arena.alloc(&over_list, over_cap));
   ASCI_TRY(arena.alloc(&cell_pos0, ncells + 1));
+  ASCI_TRY(arena.alloc(&cell_tile, ncells + 1));
   ASCI_TRY(arena.alloc(&fill, ncells + 1));
-  ASCI_TRY_CUDA(cudaMemsetAsync(cnt, 0, (ncells + 1) * sizeof(uint32_t), s));
+  ASCI_TRY(arena.alloc(&spill_rec, spill_cap));
+  ASCI_TRY(arena.alloc(&spill_cell, spill_cap));
+  ASCI_TRY_CUDA(cudaMemsetAsync(tiles, 0, (ntiles + 1) * sizeof(TileDesc), s));
+  ASCI_TRY_CUDA(cudaMemsetAsync(n_over, 0, 2 * sizeof(unsigned), s));
   ASCI_TRY_CUDA(cudaMemsetAsync(fill, 0, (ncells + 1) * sizeof(uint32_t), s));
+  k_tile_write<<<grid_for(ng), 256, 0, s>>>(gb0, ng, soff, P1, F.g_P0, F.g_alpha, kind, nb, Ws, Ns,
+                                            tile_base, tiles);
+  ASCI_CHECK_LAUNCH();
+  if (ncells) {
+    k_cell_write<<<grid_for(ncells), 256, 0, s>>>(gb0, ng, (uint32_t)ncells, soff, F.g_alpha,
+                                                  tile_base, cellbase, tiles, cell_pos0,
+                                                  cell_tile);
+    ASCI_CHECK_LAUNCH();
+  }
+  ASCI_TRACE("stage: tiles written");
+  // psi determinants routed to their tiles (entered there as markers)
+  uint64_t *psi_list = nullptr;
+  if (F.npsi) {
+    uint64_t *pk, *pk_alt;
+    ASCI_TRY(arena.alloc(&pk, F.npsi));
+    ASCI_TRY(arena.alloc(&pk_alt, F.npsi));
+    ASCI_TRY(arena.alloc(&psi_list, F.npsi));
+    k_psi_route<<<grid_for(F.npsi), 256, 0, s>>>(F.psi_keys, F.npsi, F.g_alpha, gb0, ng, kind, nb,
+                                                 Ws, Ns, tile_base, pk);
+    ASCI_CHECK_LAUNCH();
+    int topbit = 1;
+    while ((1ull << topbit) <= (uint64_t)ntiles) ++topbit;
+    ASCI_TRY(radix_sort_u64(&pk, &pk_alt, F.npsi, 0, 32 + topbit, arena));
+    k_psi_ranges<<<grid_for(F.npsi), 256, 0, s>>>(pk, F.npsi, F.psi_keys, psi_list, tiles);
+    ASCI_CHECK_LAUNCH();
+  }
+  *psi_list_out = psi_list;
 
   EmitArgs A;
   memset(&A, 0, sizeof(A));
@@ -1694,9 +1815,14 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   A.kind = kind;
   A.nb = nb;
   A.cellbase = cellbase;
-  A.cnt = cnt;
+  A.soff = soff;
+  A.g_P0 = F.g_P0;
   A.cell_pos0 = cell_pos0;
   A.fill = fill;
+  A.spill_rec = spill_rec;
+  A.spill_cell = spill_cell;
+  A.n_spill = n_spill;
+  A.spill_cap = spill_cap;
   A.runs = runs;
   A.nruns = nruns;
   A.adl = adl;
@@ -1716,70 +1842,74 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   const size_t emit_smem = 2 * (size_t)F.X.n * F.X.n * sizeof(int64_t);
   const unsigned run_grid = emit_grid((nruns + 7) / 8);
   const unsigned ad_grid = emit_grid(ad_tiles);
-  if (ncells) {  // count the hash buckets of big classes
+  unsigned long long surv0 = 0;
+  if (eps > 0.0) {
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&surv0, survivors, sizeof(surv0), cudaMemcpyDefault, s));
+    ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  }
+  unsigned hov = 0, hsp = 0;
+  for (int attempt = 0;; ++attempt) {
     if (nruns) {
-      k_emit_runs<0, false><<<run_grid, kRunThreads, 0, s>>>(A);
+      if (eps > 0.0)
+        k_emit_runs<true><<<run_grid, kRunThreads, emit_smem, s>>>(A);
+      else
+        k_emit_runs<false><<<run_grid, kRunThreads, emit_smem, s>>>(A);
       ASCI_CHECK_LAUNCH();
     }
     if (ad_tiles) {
-      k_emit_ad<0, false><<<ad_grid, kAdThreads, 0, s>>>(A);
+      if (eps > 0.0)
+        k_emit_ad<true><<<ad_grid, kAdThreads, 0, s>>>(A);
+      else
+        k_emit_ad<false><<<ad_grid, kAdThreads, 0, s>>>(A);
       ASCI_CHECK_LAUNCH();
     }
-  }
-  ASCI_TRY(scan_exclusive_u32(cnt, cnt_scan, ncells + 1, arena));
-  TileDesc *tiles;
-  unsigned *n_over;
-  uint32_t *over_list;
-  const uint32_t over_cap = (uint32_t)std::min<size_t>(ncells + 1, 1u << 20);
-  ASCI_TRY(arena.alloc(&tiles, ntiles + 1));
-  ASCI_TRY(arena.alloc(&n_over, 1));
-  ASCI_TRY(arena.alloc(&over_list, over_cap));
-  ASCI_TRY_CUDA(cudaMemsetAsync(tiles, 0, (ntiles + 1) * sizeof(TileDesc), s));
-  ASCI_TRY_CUDA(cudaMemsetAsync(n_over, 0, sizeof(unsigned), s));
-  k_tile_write<<<grid_for(ng), 256, 0, s>>>(gb0, ng, P0, P1, F.g_P0, F.g_alpha, kind, nb, Ws, Ns,
-                                            tile_base, cellbase, cnt, cnt_scan, tiles, cell_pos0,
-                                            n_over, over_list, over_cap);
-  ASCI_CHECK_LAUNCH();
-  ASCI_TRACE("stage: tiles written");
-  // psi determinants routed to their tiles (entered there as markers)
-  uint64_t *psi_list = nullptr;
-  if (F.npsi) {
-    uint64_t *pk, *pk_alt;
-    ASCI_TRY(arena.alloc(&pk, F.npsi));
-    ASCI_TRY(arena.alloc(&pk_alt, F.npsi));
-    ASCI_TRY(arena.alloc(&psi_list, F.npsi));
-    k_psi_route<<<grid_for(F.npsi), 256, 0, s>>>(F.psi_keys, F.npsi, F.g_alpha, gb0, ng, kind, nb,
-                                                 Ws, Ns, tile_base, pk);
-    ASCI_CHECK_LAUNCH();
-    int topbit = 1;
-    while ((1ull << topbit) <= (uint64_t)ntiles) ++topbit;
-    ASCI_TRY(radix_sort_u64(&pk, &pk_alt, F.npsi, 0, 32 + topbit, arena));
-    k_psi_ranges<<<grid_for(F.npsi), 256, 0, s>>>(pk, F.npsi, F.psi_keys, psi_list, tiles);
-    ASCI_CHECK_LAUNCH();
-  }
-  *psi_list_out = psi_list;
-  if (nruns) {
+    ASCI_TRACE("stage: emission launched");
+    if (ncells) {
+      k_cell_finish<<<grid_for(ncells), 256, 0, s>>>((uint32_t)ncells, fill, cell_tile, tiles,
+                                                     n_over, over_list, over_cap);
+      ASCI_CHECK_LAUNCH();
+    }
+    unsigned hcnt[2] = {0, 0};
+    ASCI_TRY_CUDA(cudaMemcpyAsync(hcnt, n_over, sizeof(hcnt), cudaMemcpyDefault, s));
+    ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+    hov = hcnt[0];
+    hsp = hcnt[1];
+    if (hsp <= spill_cap) break;
+    if (attempt > 0) {
+      record_error("spill list inconsistent between emissions", __FILE__, __LINE__);
+      return ASCI_ECUDA;
+    }
+    // Hot targets overfilled their buckets beyond the spill list.  Bucket fills
+    // do not depend on the order of the atomics, so the spill count is exact:
+    // size the list to it and emit the batch again.
+    ASCI_TRACE("stage: %u spilled records exceed the list (%u); emitting again", hsp, spill_cap);
+    spill_cap = hsp;
+    ASCI_TRY(arena.alloc(&spill_rec, spill_cap));
+    ASCI_TRY(arena.alloc(&spill_cell, spill_cap));
+    A.spill_rec = spill_rec;
+    A.spill_cell = spill_cell;
+    A.spill_cap = spill_cap;
+    ASCI_TRY_CUDA(cudaMemsetAsync(n_over, 0, 2 * sizeof(unsigned), s));
+    ASCI_TRY_CUDA(cudaMemsetAsync(fill, 0, (ncells + 1) * sizeof(uint32_t), s));
     if (eps > 0.0)
-      k_emit_runs<1, true><<<run_grid, kRunThreads, emit_smem, s>>>(A);
-    else
-      k_emit_runs<1, false><<<run_grid, kRunThreads, emit_smem, s>>>(A);
-    ASCI_CHECK_LAUNCH();
+      ASCI_TRY_CUDA(cudaMemcpyAsync(survivors, &surv0, sizeof(surv0), cudaMemcpyDefault, s));
   }
-  if (ad_tiles) {
-    if (eps > 0.0)
-      k_emit_ad<1, true><<<ad_grid, kAdThreads, 0, s>>>(A);
-    else
-      k_emit_ad<1, false><<<ad_grid, kAdThreads, 0, s>>>(A);
-    ASCI_CHECK_LAUNCH();
-  }
-  ASCI_TRACE("stage: emission launched");
-  unsigned hov = 0;
-  ASCI_TRY_CUDA(cudaMemcpyAsync(&hov, n_over, sizeof(hov), cudaMemcpyDefault, s));
-  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
   if (hov > over_cap) {
     record_error("too many oversized hash buckets", __FILE__, __LINE__);
     return ASCI_ENOMEM;
   }
+  if (hsp) {  // spilled records in tile order
+    uint64_t *sk, *sk_alt;
+    ASCI_TRY(arena.alloc(&sk, hsp));
+    ASCI_TRY(arena.alloc(&sk_alt, hsp));
+    k_spill_keys<<<grid_for(hsp), 256, 0, s>>>(spill_cell, cell_tile, hsp, sk);
+    ASCI_CHECK_LAUNCH();
+    int topbit = 1;
+    while ((1ull << topbit) <= (uint64_t)ntiles) ++topbit;
+    ASCI_TRY(radix_sort_u64(&sk, &sk_alt, hsp, 0, 32 + topbit, arena));
+    *spill_out = Spill{spill_rec, sk, hsp};
+  }
+  ASCI_TRACE("stage: oversized buckets=%u spilled records=%u", hov, hsp);
   if (hov) {
     oversized->resize(hov);
     ASCI_TRY_CUDA(cudaMemcpyAsync(oversized->data(), over_list, hov * sizeof(uint32_t),
@@ -1857,55 +1987,59 @@ int fused_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
   return ASCI_OK;
 }
 
-// (start, records, target alpha) of each listed tile: one gather kernel and
-// one copy back.
-int tile_info(const void *tiles, const std::vector<uint32_t> &list, std::vector<uint32_t> *info,
-              cudaStream_t s) {
+// Per listed tile (start, in-place records, target alpha, first spill entry,
+// spilled records): one gather kernel and one copy back.
+int tile_info(const void *tiles, const std::vector<uint32_t> &list, const Spill &spill,
+              std::vector<uint32_t> *info, cudaStream_t s) {
   const size_t n = list.size();
-  info->assign(3 * n, 0u);
+  info->assign(5 * n, 0u);
   if (!n) return ASCI_OK;
   Arena ta(s);
   uint32_t *d_list, *d_info;
   ASCI_TRY(ta.alloc(&d_list, n));
-  ASCI_TRY(ta.alloc(&d_info, 3 * n));
+  ASCI_TRY(ta.alloc(&d_info, 5 * n));
   ASCI_TRY_CUDA(cudaMemcpyAsync(d_list, list.data(), n * 4, cudaMemcpyDefault, s));
   k_tile_gather<<<grid_for(n), 256, 0, s>>>(static_cast<const TileDesc *>(tiles), d_list,
-                                            (uint32_t)n, d_info);
+                                            (uint32_t)n, spill.keys, spill.n, d_info);
   ASCI_CHECK_LAUNCH();
-  ASCI_TRY_CUDA(cudaMemcpyAsync(info->data(), d_info, 3 * n * 4, cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(info->data(), d_info, 5 * n * 4, cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
   return ASCI_OK;
 }
 
-// Reduce the oversized bucket tiles described by info[3i..3i+2], i in [0, nt),
-// at once: their records are gathered under keys (position << 32 | beta'),
-// radix-sorted in global memory and reduced one target per thread.  Appends at
-// most as many candidates as there are records.
+// Reduce the oversized bucket tiles described by info[5i..5i+4], i in
+// [0, nt), at once: their records are gathered under keys (position << 32 |
+// beta'), radix-sorted in global memory and reduced one target per thread.
+// Appends at most as many candidates as there are records.
 int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const Stage &st,
-                    double tau,
-                    uint64_t *cand_key, double *cand_score, unsigned long long *cand_count,
-                    unsigned long long cand_cap, unsigned long long *n_unique,
-                    unsigned long long *n_excluded, unsigned *err, uint64_t *nrec_out,
-                    Arena &arena) {
+                    const Spill &spill, double tau, uint64_t *cand_key, double *cand_score,
+                    unsigned long long *cand_count, unsigned long long cand_cap,
+                    unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
+                    uint64_t *nrec_out, Arena &arena) {
   cudaStream_t s = arena.stream();
   *nrec_out = 0;
   if (!nt) return ASCI_OK;
-  std::vector<uint32_t> start(nt), off(nt + 1), alpha(nt);
+  std::vector<uint32_t> start(nt), nin(nt), slo(nt), off(nt + 1), alpha(nt);
   uint64_t total = 0;
   for (size_t i = 0; i < nt; ++i) {
-    if ((uint64_t)info[3 * i] + info[3 * i + 1] > st.cap) return ASCI_ECUDA;
-    start[i] = info[3 * i];
-    alpha[i] = info[3 * i + 2];
+    const uint32_t *r = info + 5 * i;
+    if ((uint64_t)r[0] + r[1] > st.cap || (uint64_t)r[3] + r[4] > spill.n) return ASCI_ECUDA;
+    start[i] = r[0];
+    nin[i] = r[1];
+    alpha[i] = r[2];
+    slo[i] = r[3];
     off[i] = (uint32_t)total;
-    total += info[3 * i + 1];
+    total += (uint64_t)r[1] + r[4];
   }
   if (total >= (1ull << 32)) return ASCI_ENOMEM;
   off[nt] = (uint32_t)total;
   *nrec_out = total;
   Arena ta(s);
-  uint32_t *d_start, *d_off, *d_alpha, *i0, *i1, *src;
-  uint64_t *k0, *k1;
+  uint32_t *d_start, *d_nin, *d_slo, *d_off, *d_alpha, *i0, *i1;
+  uint64_t *k0, *k1, *src;
   ASCI_TRY(ta.alloc(&d_start, nt));
+  ASCI_TRY(ta.alloc(&d_nin, nt));
+  ASCI_TRY(ta.alloc(&d_slo, nt));
   ASCI_TRY(ta.alloc(&d_off, nt + 1));
   ASCI_TRY(ta.alloc(&d_alpha, nt));
   ASCI_TRY(ta.alloc(&k0, total));
@@ -1914,17 +2048,19 @@ int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const S
   ASCI_TRY(ta.alloc(&i1, total));
   ASCI_TRY(ta.alloc(&src, total));
   ASCI_TRY_CUDA(cudaMemcpyAsync(d_start, start.data(), nt * 4, cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(d_nin, nin.data(), nt * 4, cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(d_slo, slo.data(), nt * 4, cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaMemcpyAsync(d_off, off.data(), (nt + 1) * 4, cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaMemcpyAsync(d_alpha, alpha.data(), nt * 4, cudaMemcpyDefault, s));
-  k_big_gather<<<grid_for(total), 256, 0, s>>>(st.rec, d_start, d_off, (uint32_t)nt, total, k0,
-                                               i0, src);
+  k_big_gather<<<grid_for(total), 256, 0, s>>>(st.rec, spill.rec, spill.keys, d_start, d_nin,
+                                               d_slo, d_off, (uint32_t)nt, total, k0, i0, src);
   ASCI_CHECK_LAUNCH();
   int topbit = 0;
   while ((1ull << topbit) < (uint64_t)nt) ++topbit;
   ASCI_TRY(radix_sort_u64_u32(&k0, &k1, &i0, &i1, total, 0, 32 + topbit, ta));
   CellArgs CA = cell_args(F, st, tau, cand_key, cand_score, cand_count, cand_cap, n_unique,
                           n_excluded, err);
-  k_big_reduce<<<grid_for(total), 256, 0, s>>>(k0, i0, src, total, d_alpha, CA);
+  k_big_reduce<<<grid_for(total), 256, 0, s>>>(k0, i0, src, total, d_alpha, spill.rec, CA);
   ASCI_CHECK_LAUNCH();
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));  // the host vectors above are read by the copies
   return ASCI_OK;

@@ -39,6 +39,14 @@ struct Stage {
   uint64_t cap;  // records the buffer holds
 };
 
+// Records that found their hash-bucket cell full (kCap records), and their
+// order by tile: keys[j] = tile << 32 | index into rec.
+struct Spill {
+  const StageRec *rec;
+  const uint64_t *keys;
+  uint32_t n;
+};
+
 // Everything the batch kernels read that stays fixed during one search.
 struct FusedCore {
   DevInts I;

@@ -51,11 +51,11 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
                 uint32_t gb0, uint32_t gb1, const Stage &st, double eps,
                 unsigned long long *survivors, unsigned *err,
                 void **tiles_out, size_t *ntiles_out, const uint64_t **psi_list_out,
-                std::vector<uint32_t> *oversized, Arena &arena);
-int tile_info(const void *tiles, const std::vector<uint32_t> &list, std::vector<uint32_t> *info,
-              cudaStream_t s);
+                Spill *spill_out, std::vector<uint32_t> *oversized, Arena &arena);
+int tile_info(const void *tiles, const std::vector<uint32_t> &list, const Spill &spill,
+              std::vector<uint32_t> *info, cudaStream_t s);
 int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const Stage &st,
-                    double tau,
+                    const Spill &spill, double tau,
                     uint64_t *cand_key, double *cand_score, unsigned long long *cand_count,
                     unsigned long long cand_cap, unsigned long long *n_unique,
                     unsigned long long *n_excluded, unsigned *err, uint64_t *nrec_out,
@@ -580,7 +580,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     if (bmax == 0) {
       size_t fr = 0, tot = 0;
       ASCI_TRY_CUDA(cudaMemGetInfo(&fr, &tot));
-      bmax = (uint64_t)(fr / 2) / 28;  // staging record: 16 bytes, alpha word: 4
+      bmax = (uint64_t)(fr / 2) / 40;  // staging: 1.5 slots of 20 bytes per pair
       bmax = std::max<uint64_t>(bmax, 1ull << 20);
       bmax = std::min<uint64_t>(bmax, 1ull << 31);
     }
@@ -664,14 +664,17 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   const size_t cap_extra =
       std::max<size_t>(tile_capacity() * (size_t)sms * 16, std::min<uint64_t>(bcap, 1ull << 28));
   const size_t pool_cap = N + cap_extra;
-  Stage stg = {nullptr, nullptr, bcap};
+  // staging: pairs of classes that fit a tile in place, kCap slots per hash
+  // bucket of a big class (expected fill about 13/16)
+  const uint64_t scap = std::min<uint64_t>(bcap + bcap / 2 + (1u << 16), 0xfff00000ull);
+  Stage stg = {nullptr, nullptr, scap};
   uint64_t *pool_k[2] = {nullptr, nullptr};
   double *pool_s[2] = {nullptr, nullptr};
   unsigned long long *dcount = nullptr;  // [0] candidates, [1] unique, [2] excluded, [3] survivors
   unsigned *derr2 = nullptr;
   if (bcap) {
-    ASCI_TRY(arena.alloc(&stg.rec, bcap));
-    ASCI_TRY(arena.alloc(&stg.alpha, bcap));
+    ASCI_TRY(arena.alloc(&stg.rec, scap));
+    ASCI_TRY(arena.alloc(&stg.alpha, scap));
     for (int i = 0; i < 2; ++i) {
       ASCI_TRY(arena.alloc(&pool_k[i], pool_cap));
       ASCI_TRY(arena.alloc(&pool_s[i], pool_cap));
@@ -716,8 +719,9 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
                (unsigned long long)b.P1, gg[0], gg[1] + 1);
     std::vector<uint32_t> oversized;
     const uint64_t *psi_list = nullptr;
+    Spill spill{nullptr, nullptr, 0};
     ASCI_TRY(fused_stage(F, b.t0, b.t1, b.P0, b.P1, gg[0], gg[1] + 1, stg, o.eps_search,
-                         dcount + 3, derr2, &tiles, &ntiles, &psi_list, &oversized, ba));
+                         dcount + 3, derr2, &tiles, &ntiles, &psi_list, &spill, &oversized, ba));
     ASCI_TRACE("staged: tiles=%zu oversized=%zu", ntiles, oversized.size());
     tm.stop(&tl[2]);
     tm.start();
@@ -767,23 +771,24 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     // buckets too large for one tile: global sorts over as many of them as
     // the free candidate capacity allows (every record may become one)
     if (!oversized.empty()) {
-      std::vector<uint32_t> info;  // (start, records, alpha) per oversized tile
-      ASCI_TRY(tile_info(tiles, oversized, &info, stream));
+      std::vector<uint32_t> info;  // 5 words per oversized tile
+      ASCI_TRY(tile_info(tiles, oversized, spill, &info, stream));
+      auto recs = [&](size_t k) { return (uint64_t)info[5 * k + 1] + info[5 * k + 4]; };
       size_t i = 0;
       while (i < oversized.size()) {
-        if ((uint64_t)(pool_cap - pool_n) < info[3 * i + 1]) {
+        if ((uint64_t)(pool_cap - pool_n) < recs(i)) {
           tm.stop(&tl[5]);
           tm.start();
           ASCI_TRY(prune(ba));
           tm.stop(&tl[6]);
           tm.start();
-          if ((uint64_t)(pool_cap - pool_n) < info[3 * i + 1]) return ASCI_ENOMEM;
+          if ((uint64_t)(pool_cap - pool_n) < recs(i)) return ASCI_ENOMEM;
         }
         uint64_t room = pool_cap - pool_n, total = 0;
         size_t j = i;
-        while (j < oversized.size() && total + info[3 * j + 1] <= room) total += info[3 * j++ + 1];
+        while (j < oversized.size() && total + recs(j) <= room) total += recs(j++);
         uint64_t nrec = 0;
-        ASCI_TRY(fused_big_tiles(F, info.data() + 3 * i, j - i, stg, tau, pool_k[pcur],
+        ASCI_TRY(fused_big_tiles(F, info.data() + 5 * i, j - i, stg, spill, tau, pool_k[pcur],
                                  pool_s[pcur], dcount, pool_cap, dcount + 1, dcount + 2, derr2,
                                  &nrec, ba));
         unsigned long long c = 0;
