@@ -93,8 +93,14 @@ typedef struct {
   uint64_t max_batch;  /* pairs in the largest batch */
   uint64_t ncore;      /* core determinants used (min(C, ndets)) */
   uint64_t max_level;  /* deepest constraint level the planner used */
-  uint64_t reserved[3];
-  double t_stage[8];   /* prepare, plan, generate, sort, accumulate, score, select, total */
+  uint64_t tile_launches;      /* launches of the on-chip tile kernel */
+  uint64_t tile_records;       /* staged pairs reduced on chip (16 bytes read each) */
+  uint64_t oversized_records;  /* staged pairs reduced by the global-sort path */
+  /* device milliseconds: prepare, plan, generate (emission into the staging
+     buffer), tiles (the on-chip tile kernel alone), oversized (global-sort
+     path alone), score (tiles + oversized + exact scores + pruning), select,
+     total */
+  double t_stage[8];
 } asci_stats;
 
 /* Fill `opts` with the defaults (eps 0, no level cap, FP64, auto batch, unsorted). */

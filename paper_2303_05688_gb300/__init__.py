@@ -53,7 +53,8 @@ class _Stats(ct.Structure):
     _fields_ = [("generated", ct.c_uint64), ("surviving", ct.c_uint64), ("unique", ct.c_uint64),
                 ("excluded", ct.c_uint64), ("selected", ct.c_uint64), ("batches", ct.c_uint64),
                 ("max_batch", ct.c_uint64), ("ncore", ct.c_uint64), ("max_level", ct.c_uint64),
-                ("reserved", ct.c_uint64 * 3), ("t_stage", ct.c_double * 8)]
+                ("tile_launches", ct.c_uint64), ("tile_records", ct.c_uint64),
+                ("oversized_records", ct.c_uint64), ("t_stage", ct.c_double * 8)]
 
 
 @dataclass
@@ -67,14 +68,17 @@ class SearchStats:
     max_batch: int
     ncore: int
     max_level: int
+    tile_launches: int
+    tile_records: int
+    oversized_records: int
     t_stage_ms: dict
 
     @classmethod
     def _from(cls, s: _Stats):
-        names = ["prepare", "plan", "generate", "sort_accumulate", "unused", "score", "select",
-                 "total"]
+        names = ["prepare", "plan", "generate", "tiles", "oversized", "score", "select", "total"]
         return cls(s.generated, s.surviving, s.unique, s.excluded, s.selected, s.batches,
-                   s.max_batch, s.ncore, s.max_level, {k: s.t_stage[i] for i, k in enumerate(names)})
+                   s.max_batch, s.ncore, s.max_level, s.tile_launches, s.tile_records,
+                   s.oversized_records, {k: s.t_stage[i] for i, k in enumerate(names)})
 
 
 _lib = None

@@ -425,7 +425,8 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
                        cudaStream_t stream) {
   Arena arena(stream);
   double tl[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per-stage device milliseconds
-  StageTimer tm(stream), total_tm(stream);
+  uint64_t tile_launches = 0, staged_records = 0, oversized_records = 0;
+  StageTimer tm(stream), total_tm(stream), ktm(stream);
   total_tm.start();
   tm.start();
   const int n = ints->norb;
@@ -724,6 +725,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
                          dcount + 3, derr2, &tiles, &ntiles, &psi_list, &spill, &oversized, ba));
     ASCI_TRACE("staged: tiles=%zu oversized=%zu", ntiles, oversized.size());
     tm.stop(&tl[2]);
+    staged_records += b.P1 - b.P0;
     tm.start();
     size_t t = 0;
     while (t < ntiles) {
@@ -740,9 +742,12 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
       }
       const size_t t1 = std::min(ntiles, t + room);
       ASCI_TRACE("cells: tiles [%zu,%zu) tau=%.6g pool=%zu", t, t1, tau, pool_n);
+      ktm.start();
       ASCI_TRY(fused_cells(F, tiles, psi_list, (uint32_t)t, (uint32_t)t1, stg, tau,
                            pool_k[pcur], pool_s[pcur], dcount, pool_cap, dcount + 1, dcount + 2,
                            derr2, ba));
+      ktm.stop(&tl[3]);
+      ++tile_launches;
       unsigned long long c = 0;
       unsigned he = 0;
       ASCI_TRY_CUDA(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDefault, stream));
@@ -788,9 +793,12 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
         size_t j = i;
         while (j < oversized.size() && total + recs(j) <= room) total += recs(j++);
         uint64_t nrec = 0;
+        ktm.start();
         ASCI_TRY(fused_big_tiles(F, info.data() + 5 * i, j - i, stg, spill, tau, pool_k[pcur],
                                  pool_s[pcur], dcount, pool_cap, dcount + 1, dcount + 2, derr2,
                                  &nrec, ba));
+        ktm.stop(&tl[4]);
+        oversized_records += nrec;
         unsigned long long c = 0;
         unsigned he = 0;
         ASCI_TRY_CUDA(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDefault, stream));
@@ -875,7 +883,12 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   (void)g_item0;
   (void)G;
   total_tm.stop(&tl[7]);
-  if (st) memcpy(st->t_stage, tl, sizeof(tl));
+  if (st) {
+    memcpy(st->t_stage, tl, sizeof(tl));
+    st->tile_launches = tile_launches;
+    st->oversized_records = oversized_records;
+    st->tile_records = staged_records - oversized_records;
+  }
   return ASCI_OK;
 }
 
