@@ -1,5 +1,5 @@
-// Exact summation of doubles in a 192-bit two's-complement fixed-point
-// accumulator (three 64-bit limbs) whose grid is anchored to the run's largest
+// Summation of doubles in a 192-bit (and, below, a 128-bit) two's-complement
+// fixed-point accumulator whose grid is anchored to the run's largest
 // exponent.
 //
 // For a run whose largest value has biased exponent emax, values are held as
@@ -192,6 +192,121 @@ __host__ __device__ __forceinline__ double fx_to_double(Fx192 a, int frac) {
     v = fx_bits2d(((uint64_t)(e + 1023) << 52) | (mant & ((1ull << 52) - 1)));
   } else {
     // outside the normal range (a run cancelling far below 1e-300): scale in steps
+    v = (double)mant;
+    int sh = e - 52;
+    while (sh > 0) { const int t = sh > 1000 ? 1000 : sh; v *= fx_bits2d((uint64_t)(t + 1023) << 52); sh -= t; }
+    while (sh < 0) { const int t = sh < -1000 ? -1000 : sh; v *= fx_bits2d((uint64_t)(t + 1023) << 52); sh -= t; }
+  }
+  return neg ? -v : v;
+}
+
+// ---- 128-bit variant ------------------------------------------------------
+// The same construction on two limbs, with the largest value's leading one at
+// bit 100 (27 bits of headroom: up to 2^26 values).  Values within 2^-48 of the
+// largest convert exactly; smaller ones round to the grid, an error of at most
+// 2^-101 relative to the largest value.  Cheaper per value than the 192-bit
+// form; the sum is again a function of the multiset of values only.
+
+constexpr int kFx128Lead = 100;
+
+__host__ __device__ __forceinline__ int fx128_frac_for(int emax) {
+  return kFx128Lead - 52 + 1075 - emax;
+}
+
+struct Fx128 {
+  uint64_t lo, hi;  // two's complement
+};
+
+__host__ __device__ __forceinline__ void fx128_add(Fx128 &a, const Fx128 &b) {
+#ifdef __CUDA_ARCH__
+  asm("add.cc.u64 %0, %0, %2;\n\t"
+      "addc.u64 %1, %1, %3;"
+      : "+l"(a.lo), "+l"(a.hi)
+      : "l"(b.lo), "l"(b.hi));
+#else
+  const uint64_t s0 = a.lo + b.lo;
+  a.hi = a.hi + b.hi + (s0 < a.lo ? 1u : 0u);
+  a.lo = s0;
+#endif
+}
+
+__host__ __device__ __forceinline__ void fx128_neg(Fx128 &a) {
+  a.lo = ~a.lo;
+  a.hi = ~a.hi;
+  const Fx128 one = {1, 0};
+  fx128_add(a, one);
+}
+
+// x -> multiple of 2^-frac (round to nearest even); *ovf set when x is not
+// finite or does not fit below bit 126.
+__host__ __device__ __forceinline__ Fx128 fx128_from_double(double x, int frac, unsigned *ovf) {
+  Fx128 r = {0, 0};
+  const uint64_t b = fx_dbits(x);
+  int eb = (int)((b >> 52) & 0x7ff);
+  uint64_t m = b & ((1ull << 52) - 1);
+  if (eb == 0x7ff) {  // inf or nan
+    *ovf = 1;
+    return r;
+  }
+  if (eb) m |= (1ull << 52); else eb = 1;
+  if (m == 0) return r;
+  const int k = eb - 1075 + frac;  // value = m * 2^(k - frac)
+  if (k >= 0) {
+    if (k >= 127 - 52) {
+      *ovf = 1;
+      return r;
+    }
+    if (k < 64) {
+      r.lo = m << k;
+      r.hi = k ? (m >> (64 - k)) : 0;
+    } else {
+      r.hi = m << (k - 64);
+    }
+  } else {
+    const int s = -k;  // right shift with round to nearest even
+    if (s > 54) return r;
+    const uint64_t q = m >> s;
+    const uint64_t rem = m & ((1ull << s) - 1);
+    const uint64_t half = 1ull << (s - 1);
+    r.lo = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+  }
+  if (b >> 63) fx128_neg(r);
+  return r;
+}
+
+// Round a * 2^-frac to the nearest double (ties to even).
+__host__ __device__ __forceinline__ double fx128_to_double(Fx128 a, int frac) {
+  const bool neg = (a.hi >> 63) != 0;
+  if (neg) fx128_neg(a);
+  if (!(a.lo | a.hi)) return 0.0;
+  int P = a.hi ? 64 + 63 - fx_clz64(a.hi) : 63 - fx_clz64(a.lo);  // highest set bit
+  uint64_t mant;
+  if (P <= 52) {
+    mant = a.lo << (52 - P);  // exact
+  } else {
+    // mant = bits [P-52, P]; round bit P-53; sticky = bits below
+    const int sh = P - 52;
+    const uint64_t win =
+        sh < 64 ? ((a.lo >> sh) | (sh ? (a.hi << (64 - sh)) : 0)) : (a.hi >> (sh - 64));
+    mant = win & ((1ull << 53) - 1);
+    const int rb = sh - 1;
+    const uint64_t rbit = rb < 64 ? ((a.lo >> rb) & 1) : ((a.hi >> (rb - 64)) & 1);
+    bool sticky;
+    if (rb < 64) sticky = (rb ? (a.lo & ((1ull << rb) - 1)) : 0) != 0;
+    else sticky = a.lo != 0 || ((rb - 64) ? (a.hi & ((1ull << (rb - 64)) - 1)) : 0) != 0;
+    if (rbit && (sticky || (mant & 1))) {
+      mant += 1;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        P += 1;
+      }
+    }
+  }
+  const int e = P - frac;  // unbiased exponent of the result
+  double v;
+  if (e + 1023 >= 1 && e + 1023 <= 2046) {
+    v = fx_bits2d(((uint64_t)(e + 1023) << 52) | (mant & ((1ull << 52) - 1)));
+  } else {
     v = (double)mant;
     int sh = e - 52;
     while (sh > 0) { const int t = sh > 1000 ? 1000 : sh; v *= fx_bits2d((uint64_t)(t + 1023) << 52); sh -= t; }

@@ -1108,6 +1108,28 @@ __device__ __forceinline__ uint64_t slot_key(const CellSmem &S, int buf, uint32_
   return (v & kPsiBit) ? S.psik[buf][v & ~kPsiBit] : rec_key(S, buf, v, packed, alpha);
 }
 
+// Sum of five or more values (list from e through next) in the 128-bit
+// fixed-point accumulator anchored to their largest exponent: equal bit for bit
+// for any order.  Kept out of line: rare, and it would weigh on the common
+// path's registers.
+__device__ __noinline__ double long_numerator(const StageRec *r, const uint16_t *next,
+                                              uint32_t e, unsigned *err) {
+  int emax = 1;
+  for (uint32_t i = e; i != kEndList; i = next[i]) {
+    const int ex = fx_exponent(r[i].v);
+    emax = ex > emax ? ex : emax;
+  }
+  const int frac = fx128_frac_for(emax);
+  Fx128 acc = {0, 0};
+  unsigned ovf = 0;
+  for (uint32_t i = e; i != kEndList; i = next[i]) {
+    Fx128 x = fx128_from_double(r[i].v, frac, &ovf);
+    fx128_add(acc, x);
+  }
+  if (ovf) atomicOr(err, kErrAccum);
+  return fx128_to_double(acc, frac);
+}
+
 // Exact numerator over the record list starting at e (values of screened-out
 // records are never inserted).
 __device__ __forceinline__ double list_numerator(const CellSmem &S, int buf, uint32_t e,
@@ -1118,24 +1140,12 @@ __device__ __forceinline__ double list_numerator(const CellSmem &S, int buf, uin
   // two records: IEEE addition rounds their exact sum once
   const uint32_t e3 = S.next[e2];
   if (e3 == kEndList) return r[e].v + r[e2].v;
-  // three or four: an order-independent FP64 sum; more: the exact accumulator
+  // three or four: an order-independent FP64 sum; more: the 128-bit
+  // fixed-point accumulator anchored to the largest exponent
   const uint32_t e4 = S.next[e3];
   if (e4 == kEndList) return sum4_ordered(0.0, r[e].v, r[e2].v, r[e3].v);
   if (S.next[e4] == kEndList) return sum4_ordered(r[e].v, r[e2].v, r[e3].v, r[e4].v);
-  int emax = 1;
-  for (uint32_t i = e; i != kEndList; i = S.next[i]) {
-    const int ex = fx_exponent(r[i].v);
-    emax = ex > emax ? ex : emax;
-  }
-  const int frac = fx_frac_for(emax);
-  Fx192 acc = {0, 0, 0};
-  unsigned ovf = 0;
-  for (uint32_t i = e; i != kEndList; i = S.next[i]) {
-    Fx192 x = fx_from_double(r[i].v, frac, &ovf);
-    fx_add(acc, x);
-  }
-  if (ovf) atomicOr(err, kErrAccum);
-  return fx_to_double(acc, frac);
+  return long_numerator(r, S.next, e, err);
 }
 
 // |x| as a float built from the bits, truncated (relative error below 2^-23);
@@ -1394,7 +1404,7 @@ __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const ui
     const uint64_t sk = keys[i];
     if (i > 0 && keys[i - 1] == sk) continue;
     // the same rule as on chip: one or two values by IEEE addition, three or
-    // four by the ordered FP64 sum, more by the exact accumulator
+    // four by the ordered FP64 sum, more by the 128-bit accumulator
     int emax = 1, live = 0;
     double w[4] = {0.0, 0.0, 0.0, 0.0};
     for (uint64_t e = i; e < n && keys[e] == sk; ++e) {
@@ -1414,17 +1424,17 @@ __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const ui
     } else if (live <= 4) {
       num = sum4_ordered(w[0], w[1], w[2], w[3]);
     } else {
-      const int frac = fx_frac_for(emax);
-      Fx192 acc = {0, 0, 0};
+      const int frac = fx128_frac_for(emax);
+      Fx128 acc = {0, 0};
       unsigned ovf = 0;
       for (uint64_t e = i; e < n && keys[e] == sk; ++e) {
         const double v = big_rec(C.st.rec, spill, src[idx[e]]).v;
         if (is_dropped(v)) continue;
-        Fx192 x = fx_from_double(v, frac, &ovf);
-        fx_add(acc, x);
+        Fx128 x = fx128_from_double(v, frac, &ovf);
+        fx128_add(acc, x);
       }
       if (ovf) atomicOr(C.err, kErrAccum);
-      num = fx_to_double(acc, frac);
+      num = fx128_to_double(acc, frac);
     }
     const uint64_t full = pack_key(alpha[sk >> 32], (uint32_t)sk);
     ++my_unique;

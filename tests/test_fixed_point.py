@@ -1,5 +1,5 @@
-"""The GPU path's exact numerator accumulator (fixed192.cuh), compiled for the
-host, against exact rational arithmetic (CPU)."""
+"""The GPU path's fixed-point numerator accumulators (fixed192.cuh: 192- and
+128-bit), compiled for the host, against exact rational arithmetic (CPU)."""
 import os
 import random
 import struct
@@ -27,18 +27,19 @@ def _dbl(b):
     return struct.unpack("<d", struct.pack("<Q", b))[0]
 
 
-def _exact_rounded(vals):
+def _exact_rounded(vals, lead=166):
     """Round each value to the run's grid, sum exactly, round to double.
 
-    The grid is 2^(e - 166) where 2^e <= max|x| < 2^(e+1) (e of the run's largest
-    normal exponent; subnormals and zeros count as 2^-1022).
+    The grid is 2^(e - lead) where 2^e <= max|x| < 2^(e+1) (e of the run's largest
+    normal exponent; subnormals and zeros count as 2^-1022); lead is 166 for the
+    192-bit accumulator and 100 for the 128-bit one.
     """
     import math
     e = -1022
     for v in vals:
         if v != 0.0:
             e = max(e, math.frexp(abs(v))[1] - 1)
-    q = Fraction(2) ** (e - 166)
+    q = Fraction(2) ** (e - lead)
     tot = Fraction(0)
     for v in vals:
         f = Fraction(v) / q
@@ -47,9 +48,10 @@ def _exact_rounded(vals):
     return float(tot)  # correctly rounded (ties to even)
 
 
-def _run(exe, groups):
+def _run(exe, groups, width=192):
     inp = "".join(f"{len(g)} " + " ".join(f"{_bits(x):x}" for x in g) + "\n" for g in groups)
-    out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    args = [exe] + (["128"] if width == 128 else [])
+    out = subprocess.run(args, input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
     res = []
     for line in out:
         if line.strip():
@@ -58,7 +60,8 @@ def _run(exe, groups):
     return res
 
 
-def test_exact_sum_matches_rationals(harness):
+@pytest.mark.parametrize("width,lead", [(192, 166), (128, 100)])
+def test_exact_sum_matches_rationals(harness, width, lead):
     rng = random.Random(7)
     groups = []
     for _ in range(400):
@@ -72,22 +75,24 @@ def test_exact_sum_matches_rationals(harness):
                [1e-40, -1e-40, 1e-200], [1e-36, -0.9e-36, 3e-52],
                [1.0, 1.5 * 2.0 ** -167], [1.0, 2.5 * 2.0 ** -167], [1.0, 2.0 ** -200],
                [1e-310, 2e-310, -1e-311], [1e300, -1e300, 1e200]]
-    res = _run(harness, groups)
+    res = _run(harness, groups, width)
     for g, (got, ovf) in zip(groups, res):
         assert ovf == 0
-        want = _exact_rounded(g)
+        want = _exact_rounded(g, lead)
         assert got == want or (got == 0.0 and want == 0.0), (g[:4], got, want)
 
 
-def test_order_independent(harness):
+@pytest.mark.parametrize("width", [192, 128])
+def test_order_independent(harness, width):
     rng = random.Random(3)
     g = [rng.uniform(-1, 1) * 10.0 ** rng.uniform(-15, 1) for _ in range(1000)]
     perms = [g, list(reversed(g)), sorted(g), sorted(g, key=abs)]
-    res = _run(harness, perms)
+    res = _run(harness, perms, width)
     assert len({r[0] for r in res}) == 1
 
 
-def test_overflow_flagged(harness):
-    res = _run(harness, [[float("inf")], [2.0 ** 1000, 2.0 ** 1000], [1e308, 1e308]])
+@pytest.mark.parametrize("width", [192, 128])
+def test_overflow_flagged(harness, width):
+    res = _run(harness, [[float("inf")], [2.0 ** 1000, 2.0 ** 1000], [1e308, 1e308]], width)
     assert res[0][1] == 1 and res[1][1] == 0 and res[2][1] == 0
     assert res[1][0] == 2.0 ** 1001
