@@ -559,6 +559,35 @@ __device__ __forceinline__ bool pair_position(const EmitArgs &A, bool big, bool 
   return valid;
 }
 
+// A float widened to a double exactly, by operations on the bits (a widening
+// conversion would take the FP64 pipe, which is scarce).
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  if (e == 0xffu)  // inf or nan
+    return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | ((uint64_t)m << 29)));
+  if (e == 0) {    // zero or subnormal: normalise the mantissa
+    if (!m) return __longlong_as_double((long long)sign);
+    const int lz = __clz(m) - 8;  // leading zeros within the 23-bit field, plus one
+    const uint64_t mm = ((uint64_t)m << lz) & 0x7fffffu;
+    return __longlong_as_double(
+        (long long)(sign | ((uint64_t)(1023 - 126 - lz) << 52) | (mm << 29)));
+  }
+  return __longlong_as_double(
+      (long long)(sign | ((uint64_t)(e + 1023 - 127) << 52) | ((uint64_t)m << 29)));
+}
+
+// Precision of the pair values (the a8 variant): 0 = FP64 integrals and
+// product; 1 = two-electron elements gathered from FP32 tables, FP64 product;
+// 2 = FP32 tables and an FP32 product H_ij c_j.  Sums and diagonals are the
+// same in all three.
+template <int PREC>
+__device__ __forceinline__ double pair_value(double h, double c, float cf) {
+  if (PREC == 2) return widen((float)h * cf);
+  return h * c;
+}
+
 // z * 2^-s as a float built from the bits (truncated, relative error below
 // 2^-23); 0 when z is zero or the value lies outside the normal float range.
 __device__ __forceinline__ float scaled_as_float(int64_t z, int s) {
@@ -597,8 +626,9 @@ __device__ __forceinline__ void write_record(const EmitArgs &A, uint32_t pos, bo
   }
 }
 
-// EPS compiles Alg. 2's screen in (eps > 0).
-template <bool EPS>
+// EPS compiles Alg. 2's screen in (eps > 0); PREC selects the pair-value
+// precision (pair_value).
+template <bool EPS, int PREC>
 __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
   extern __shared__ int64_t s_fx[];  // emit mode: jk[n*n], jj[n*n]
   __shared__ uint16_t s_pair[kPairTab];
@@ -654,8 +684,11 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
     uint32_t pa = 0;
     double h0 = 0.0;  // the alpha single alone
     const double *erow = A.I.eri;
+    const float *erow32 = A.I.eri32;
+    float cf = 0.0f;
     {
       c = A.core_c[jdx];
+      cf = (float)c;
       base_x = A.Dx[jdx];
       const int64_t *Fb = A.Fb + (size_t)jdx * n;
       Vo = Fb[occL];
@@ -679,6 +712,7 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
         Vo += s_jj[aa * n + occL] - s_jj[ia * n + occL];
         Vv += s_jj[aa * n + virL] - s_jj[ia * n + virL];
         erow = A.I.eri + ((size_t)ia * n + aa) * n * n;
+        if (PREC != 0) erow32 = A.I.eri32 + ((size_t)ia * n + aa) * n * n;
       }
     }
     // one chunk of 32 pairs: the beta operation as positions in the occupied /
@@ -746,10 +780,12 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
             h = flip_sign(fx64_to_double(fx_single(A.X, B, Ak, bi, ba), A.X.s1),
                           (uint32_t)single_parity(B, bi, ba));
           else
-            h = flip_sign(erow[bi * n + ba], pa ^ (uint32_t)single_parity(B, bi, ba));
+            h = flip_sign(PREC != 0 ? widen(erow32[bi * n + ba]) : erow[bi * n + ba],
+                          pa ^ (uint32_t)single_parity(B, bi, ba));
           dh = vv1 - vo1 - s_jk[ba * n + bi];
         } else {
-          h = flip_sign(A.I.asym[(((size_t)bi * n + ba) * n + bj) * n + bb],
+          const size_t ix = (((size_t)bi * n + ba) * n + bj) * n + bb;
+          h = flip_sign(PREC != 0 ? widen(A.I.asym32[ix]) : A.I.asym[ix],
                         (uint32_t)par_double(B, bi, bj, ba, bb));
           dh = vv1 + vv2 - vo1 - vo2 + s_jk[bi * n + bj] + s_jk[ba * n + bb] - s_jk[ba * n + bi] -
                s_jk[ba * n + bj] - s_jk[bb * n + bi] - s_jk[bb * n + bj];
@@ -757,8 +793,8 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
       }
       bool kept = false;
       if (cur.wr)
-        write_record<EPS>(A, cur.pos, cur.spill, cur.cell, talpha, cur.tb, packed, h * c,
-                          base_x + dh, &kept);
+        write_record<EPS>(A, cur.pos, cur.spill, cur.cell, talpha, cur.tb, packed,
+                          pair_value<PREC>(h, c, cf), base_x + dh, &kept);
       if (EPS) {
         const uint32_t nk = __popc(__ballot_sync(0xffffffffu, kept));
         if (lane == 0 && nk) atomicAdd(A.survivors, (unsigned long long)nk);
@@ -769,7 +805,7 @@ __global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
 }
 
 // Alpha-double pairs, flat: CTA step s covers flat pairs [s * kAdTile, ...).
-template <bool EPS>
+template <bool EPS, int PREC>
 __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
   __shared__ uint32_t sF[kAdTile + 1];    // first flat pair of each item in the step
   __shared__ uint32_t sPos[kAdTile + 1];  // in-place staging slot of the item's first pair
@@ -807,7 +843,8 @@ __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
         int ia, ja2, aa, ba;
         dec_double(Ak, ~Ak & full, o - 1 - A.E.sa, A.dv_pa_p, &ia, &ja2, &aa, &ba);
         sOrb[i] = (uint32_t)ia | ((uint32_t)aa << 5) | ((uint32_t)ja2 << 10) | ((uint32_t)ba << 15);
-        sH[i] = flip_sign(A.I.asym[(((size_t)ia * n + aa) * n + ja2) * n + ba],
+        const size_t ix = (((size_t)ia * n + aa) * n + ja2) * n + ba;
+        sH[i] = flip_sign(PREC != 0 ? widen(A.I.asym32[ix]) : A.I.asym[ix],
                           (uint32_t)par_double(Ak, ia, ja2, aa, ba));
         const int64_t *jk = A.X.jk;
         sD[i] = jk[ia * n + ja2] + jk[aa * n + ba] - jk[aa * n + ia] - jk[aa * n + ja2] -
@@ -865,7 +902,8 @@ __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
         const int64_t dh = sD[lo] + Fa[(ob >> 5) & 31u] + Fa[(ob >> 15) & 31u] - Fa[ob & 31u] -
                            Fa[(ob >> 10) & 31u];
         write_record<EPS>(A, pos, spill, cell, sTA[lo], B, A.kind[gi] == kTilePacked,
-                          sH[lo] * A.core_c[jdx], A.Dx[jdx] + dh, &kept);
+                          pair_value<PREC>(sH[lo], A.core_c[jdx], (float)A.core_c[jdx]),
+                          A.Dx[jdx] + dh, &kept);
       }
       if (EPS) {
         const uint32_t nk = __popc(__ballot_sync(0xffffffffu, kept));
@@ -1637,6 +1675,15 @@ int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t 
 // Stage one batch (items [t0, t1), pairs [P0, P1), groups [gb0, gb1)): plan
 // its tiles, count the hash buckets of big classes and emit every record into
 // the staging buffer.  The tile table is left in *tiles_out (arena memory).
+// Launch of an emission kernel instantiated by (eps screen, precision).
+using EmitKernel = void (*)(EmitArgs);
+static void launch_emit(EmitKernel e0, EmitKernel n0, EmitKernel e1, EmitKernel n1,
+                        EmitKernel e2, EmitKernel n2, bool eps, int prec, unsigned grid,
+                        int threads, size_t smem, cudaStream_t s, const EmitArgs &A) {
+  EmitKernel k = prec == 2 ? (eps ? e2 : n2) : prec == 1 ? (eps ? e1 : n1) : (eps ? e0 : n0);
+  k<<<grid, threads, smem, s>>>(A);
+}
+
 // Persistent emission grid: a few CTAs per SM, at most one per tile.
 static unsigned emit_grid(size_t ntl) {
   int dev = 0, sms = 152;
@@ -1860,17 +1907,15 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   unsigned hov = 0, hsp = 0;
   for (int attempt = 0;; ++attempt) {
     if (nruns) {
-      if (eps > 0.0)
-        k_emit_runs<true><<<run_grid, kRunThreads, emit_smem, s>>>(A);
-      else
-        k_emit_runs<false><<<run_grid, kRunThreads, emit_smem, s>>>(A);
+      launch_emit(k_emit_runs<true, 0>, k_emit_runs<false, 0>, k_emit_runs<true, 1>,
+                  k_emit_runs<false, 1>, k_emit_runs<true, 2>, k_emit_runs<false, 2>, eps > 0.0,
+                  F.prec, run_grid, kRunThreads, emit_smem, s, A);
       ASCI_CHECK_LAUNCH();
     }
     if (ad_tiles) {
-      if (eps > 0.0)
-        k_emit_ad<true><<<ad_grid, kAdThreads, 0, s>>>(A);
-      else
-        k_emit_ad<false><<<ad_grid, kAdThreads, 0, s>>>(A);
+      launch_emit(k_emit_ad<true, 0>, k_emit_ad<false, 0>, k_emit_ad<true, 1>,
+                  k_emit_ad<false, 1>, k_emit_ad<true, 2>, k_emit_ad<false, 2>, eps > 0.0,
+                  F.prec, ad_grid, kAdThreads, 0, s, A);
       ASCI_CHECK_LAUNCH();
     }
     ASCI_TRACE("stage: emission launched");

@@ -66,6 +66,7 @@ struct FusedCore {
   const uint64_t *psi_keys;  // psi keys, sorted
   size_t npsi;
   uint32_t ncore;
+  int prec;  // pair-value precision: 0 FP64, 1 FP32 integrals, 2 FP32 integrals and product
 };
 
 }  // namespace asci

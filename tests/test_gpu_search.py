@@ -312,3 +312,31 @@ def test_search_hot_target_beyond_one_tile(torch_cuda, asci, oracle_mod):
     assert st.generated == C * W.n_excitations(n, na, nb)
     # sampled selected outputs against brute-force numerators
     _check_sampled(oracle_mod, h1, eri, ec, ta, tb, c, E0, C, ga, gb, gs, 24, seed=2)
+
+
+@pytest.mark.parametrize("prec", ["FP32_INT_FP64_ACC", "FP32_INT_COMP_ACC"])
+def test_search_fp32_integrals_against_fp64_oracle(torch_cuda, asci, oracle_mod, prec):
+    """The precision variant (FP32-stored two-electron elements, and for the
+    second mode an FP32 product H_ij c_j): the candidate key set is exact, every
+    score is within 1e-6 relative of the FP64 oracle (with the same cancellation
+    budget scaled to 1e-6), and the selected top N overlaps the oracle's by at
+    least 99.9%."""
+    torch = torch_cuda
+    _, h1, eri, ec, A, B, c, E0 = _random("random_14e20o")
+    C, N = 400, 20000
+    ref = oracle_mod.search(oracle_mod.Ints(h1, eri, ec), A, B, c, E0, C)
+    ga, gb, gs, st = _run(asci, torch, A, B, c, E0, h1, eri, ec, C, 10**7,
+                          precision=getattr(asci, prec))
+    assert len(ga) == len(ref.a)
+    o1, o2 = key_order(ga, gb), key_order(ref.a, ref.b)
+    assert np.array_equal(ga[o1], ref.a[o2]) and np.array_equal(gb[o1], ref.b[o2])
+    tol = score_tol(ref.score[o2], ref.abssum[o2], ref.haa[o2], E0, rel=1e-6)
+    err = np.abs(gs[o1] - ref.score[o2])
+    assert np.all(err <= tol), float(np.max(err / np.maximum(tol, 1e-300)))
+    # selected-set overlap of the top N
+    sa, sb, ss, _ = _run(asci, torch, A, B, c, E0, h1, eri, ec, C, N, precision=getattr(asci, prec))
+    sel = ref.topn(N)
+    want = set(zip(ref.a[sel].tolist(), ref.b[sel].tolist()))
+    got = set(zip(sa.tolist(), sb.tolist()))
+    assert len(got) == len(want) == N
+    assert len(got & want) >= 0.999 * N
