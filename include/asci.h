@@ -60,12 +60,14 @@ typedef struct {
   const double *eri; /* norb^4 */
 } asci_ints;
 
-/* Arithmetic of the per-pair values and numerator sums (the diagonal, E0 and
- * the denominator E0 - H_ii are FP64 in every mode). */
+/* Arithmetic of the per-pair values H_ij c_j (not in the paper; a variant of
+ * its method).  The numerator sums, the diagonal, E0 and the denominator
+ * E0 - H_ii are the same in every mode (exact fixed-point or order-independent
+ * rules, FP64 results). */
 enum {
-  ASCI_FP64 = 0,              /* FP64 integrals, FP64 products and sums */
-  ASCI_FP32_INT_FP64_ACC = 1, /* FP32-stored integrals, FP64 accumulation */
-  ASCI_FP32_INT_COMP_ACC = 2  /* FP32-stored integrals, compensated FP32 sums */
+  ASCI_FP64 = 0,              /* FP64 integrals and products */
+  ASCI_FP32_INT_FP64_ACC = 1, /* two-electron elements from FP32 tables, FP64 products */
+  ASCI_FP32_INT_COMP_ACC = 2  /* two-electron elements from FP32 tables, FP32 products */
 };
 
 typedef struct {
@@ -79,7 +81,15 @@ typedef struct {
   int32_t precision;         /* ASCI_FP64 | ASCI_FP32_INT_FP64_ACC | ASCI_FP32_INT_COMP_ACC */
   uint64_t max_batch_pairs;  /* pairs per constraint batch; 0 = sized from free memory */
   int32_t sort_output;       /* 1: outputs sorted by key ascending; 0: unspecified order */
-  int32_t reserved;
+  /* Constraint sharding across processes (Sec. 2.2, Alg. 3): with
+   * shard_count > 1 the search covers only the target alpha classes of shard
+   * shard_index (0-based) and returns that shard's top N; the classes partition
+   * the targets, so the top N of the union of every shard's output is the
+   * unsharded result.  Classes heavier than 1/(64 shard_count) of the pairs are
+   * placed by asci_shard_assign (Alg. 3's greedy), the others by a hash of their
+   * alpha string.  0 or 1: no sharding. */
+  int32_t shard_index;
+  int32_t shard_count;
 } asci_opts;
 
 /* Counters and per-stage device times (milliseconds) of one search. */
@@ -213,6 +223,15 @@ int asci_sort_accumulate_noalloc(const asci_det *keys, const double *values, siz
  * breaking ties at the cutoff by key ascending.  Keys must be distinct.
  * Device pointers; output order unspecified.
  */
+/* Alg. 3's greedy placement (longest processing time first): the n classes
+ * of weights[n] (pairs) are visited in descending weight (ties: lower index
+ * first) and each goes to the shard with the smallest load so far (ties: lower
+ * shard), loads starting from initial_loads[shards] (nullable: zeros).  Writes
+ * shard_out[n] (values in [0, shards)).  Host memory only; runs on the host.
+ * Returns ASCI_EINVAL for shards < 1 or null arrays with n > 0. */
+int asci_shard_assign(const uint64_t *weights, size_t n, int32_t shards,
+                      const uint64_t *initial_loads, int32_t *shard_out);
+
 int asci_select_topn(const asci_det *keys, const double *scores, size_t n, size_t N,
                      asci_det *out_keys, double *out_scores, size_t *out_n,
                      void *cuda_stream);

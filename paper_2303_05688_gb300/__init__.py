@@ -19,7 +19,7 @@ import numpy as np
 
 __all__ = ["load", "lib_path", "launch_count", "search", "excitations", "diagonal", "sort_accumulate",
            "select_topn", "SearchStats", "AsciError", "FP64", "FP32_INT_FP64_ACC",
-           "FP32_INT_COMP_ACC"]
+           "FP32_INT_COMP_ACC", "shard_assign", "gather_candidates", "sharded_search"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "lib", "libasci.so")
@@ -46,7 +46,8 @@ class _Ints(ct.Structure):
 class _Opts(ct.Structure):
     _fields_ = [("eps_search", ct.c_double), ("max_constraint_level", ct.c_int32),
                 ("precision", ct.c_int32), ("max_batch_pairs", ct.c_uint64),
-                ("sort_output", ct.c_int32), ("reserved", ct.c_int32)]
+                ("sort_output", ct.c_int32), ("shard_index", ct.c_int32),
+                ("shard_count", ct.c_int32)]
 
 
 class _Stats(ct.Structure):
@@ -109,6 +110,7 @@ def load():
     lib.asci_sort_accumulate.argtypes = [vp, vp, sz, vp, vp, szp, vp]
     lib.asci_select_topn.restype = ct.c_int
     lib.asci_select_topn.argtypes = [vp, vp, sz, sz, vp, vp, szp, vp]
+    lib.asci_shard_assign.argtypes = [vp, sz, ct.c_int32, vp, vp]
     lib.asci_default_opts.argtypes = [ct.POINTER(_Opts)]
     lib.asci_version.restype = ct.c_char_p
     lib.asci_strerror.restype = ct.c_char_p
@@ -213,10 +215,12 @@ def _out(n, dtype_np, device, cols=None):
 def search(dets, coeffs, E0: float, h1, eri, ecore: float, C: int, N: int, *,
            eps: float = 0.0, precision: int = FP64, max_batch_pairs: int = 0,
            max_constraint_level: int = 0, sort_output: bool = False, stream=None,
-           return_stats: bool = True):
+           return_stats: bool = True, shard=None):
     """The ASCI search (Alg. 2 with Eq. 1).  Returns (dets[(m, 2)], scores[m], stats).
 
     Outputs live where ``dets`` lives (device torch tensors in, device tensors out).
+    ``shard=(index, count)`` restricts the search to one shard of the target
+    alpha classes (Sec. 2.2, Alg. 3) and returns that shard's top N.
     """
     lib = load()
     keep = []
@@ -235,6 +239,8 @@ def search(dets, coeffs, E0: float, h1, eri, ecore: float, C: int, N: int, *,
     opts.max_batch_pairs = int(max_batch_pairs)
     opts.max_constraint_level = int(max_constraint_level)
     opts.sort_output = 1 if sort_output else 0
+    if shard is not None:
+        opts.shard_index, opts.shard_count = int(shard[0]), int(shard[1])
     st = _Stats()
     n_out = ct.c_size_t(0)
     code = lib.asci_search(db.ptr, cb.ptr, nd, float(E0), ct.byref(ints), int(C), int(N),
@@ -306,6 +312,68 @@ def sort_accumulate(keys, values, stream=None):
                                     ct.byref(n_out), _stream_ptr(stream, True)),
            "asci_sort_accumulate")
     return ok[:n_out.value], os_[:n_out.value]
+
+
+def shard_assign(weights, shards: int, initial_loads=None):
+    """Alg. 3's greedy placement of classes of the given weights onto shards
+    (heaviest first, each to the least-loaded shard; host computation)."""
+    lib = load()
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.uint64))
+    out = np.empty(len(w), dtype=np.int32)
+    init = None
+    if initial_loads is not None:
+        init = np.ascontiguousarray(np.asarray(initial_loads, dtype=np.uint64))
+        if len(init) != shards:
+            raise ValueError("initial_loads needs one entry per shard")
+    _check(lib.asci_shard_assign(w.ctypes.data if len(w) else None, len(w), int(shards),
+                                 init.ctypes.data if init is not None else None,
+                                 out.ctypes.data if len(w) else None), "asci_shard_assign")
+    return out
+
+
+def gather_candidates(keys, scores, group=None):
+    """All ranks' candidates, concatenated in rank order, on every rank.
+
+    keys: (m, 2) int64 tensor, scores: (m,) float64 tensor, m may differ by
+    rank.  Uses torch.distributed (NCCL for CUDA tensors, gloo for CPU ones):
+    the counts first, then the padded lists.
+    """
+    torch = _torch()
+    import torch.distributed as dist
+    W = dist.get_world_size(group)
+    dev = keys.device
+    m = torch.tensor([keys.shape[0]], dtype=torch.int64, device=dev)
+    counts = [torch.zeros_like(m) for _ in range(W)]
+    dist.all_gather(counts, m, group=group)
+    counts = [int(c.item()) for c in counts]
+    mx = max(counts) if counts else 0
+    kp = torch.zeros((mx, 2), dtype=torch.int64, device=dev)
+    sp = torch.zeros(mx, dtype=torch.float64, device=dev)
+    kp[:keys.shape[0]] = keys
+    sp[:scores.shape[0]] = scores
+    kl = [torch.empty_like(kp) for _ in range(W)]
+    sl = [torch.empty_like(sp) for _ in range(W)]
+    dist.all_gather(kl, kp, group=group)
+    dist.all_gather(sl, sp, group=group)
+    return (torch.cat([k[:c] for k, c in zip(kl, counts)]),
+            torch.cat([v[:c] for v, c in zip(sl, counts)]))
+
+
+def sharded_search(dets, coeffs, E0: float, h1, eri, ecore: float, C: int, N: int, *,
+                   group=None, **kw):
+    """One search sharded over the ranks of a torch.distributed group (one GPU
+    per rank): each rank searches its shard of the target alpha classes and
+    keeps its top N; the ranks exchange those lists and every rank selects the
+    global top N from the union (the shards partition the targets, so this is
+    the unsharded result).  Returns (dets, scores, local stats)."""
+    import torch.distributed as dist
+    r, W = dist.get_rank(group), dist.get_world_size(group)
+    od, osc, st = search(dets, coeffs, E0, h1, eri, ecore, C, N, shard=(r, W), **kw)
+    ak, asc = gather_candidates(od, osc, group)
+    if ak.shape[0] == 0:
+        return ak, asc, st
+    gk, gs = select_topn(ak, asc, N)
+    return gk, gs, st
 
 
 def select_topn(keys, scores, N: int, stream=None):

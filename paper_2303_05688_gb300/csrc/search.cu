@@ -20,6 +20,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <numeric>
+#include <queue>
 #include <vector>
 
 #include "asci_internal.cuh"
@@ -264,6 +266,139 @@ __global__ void k_unpack(const uint64_t *keys, size_t n, asci_det *out) {
 }
 
 // ------------------------------- timing ------------------------------------
+
+// ---------------------------------------------------------- sharding ---
+// Shard of each target alpha class (Sec. 2.2, Alg. 3): light classes by a
+// hash of their alpha string, heavy ones by the greedy placement on the host.
+
+__device__ __forceinline__ uint32_t class_hash(uint32_t a) {
+  uint32_t x = a * 0x9E3779B1u;
+  x ^= x >> 16;
+  x *= 0x85EBCA6Bu;
+  x ^= x >> 13;
+  return x;
+}
+
+// Light classes: shard by hash, loads summed per block; heavy classes listed.
+__global__ void k_class_shard(const uint32_t *g_alpha, const uint64_t *g_P0, size_t G,
+                              uint64_t Pend, uint64_t heavy, int32_t W, int32_t *shard,
+                              unsigned long long *light_load, uint32_t *heavy_ids,
+                              unsigned *n_heavy, uint32_t heavy_cap) {
+  extern __shared__ unsigned long long sload[];
+  for (int i = threadIdx.x; i < W; i += blockDim.x) sload[i] = 0;
+  __syncthreads();
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < G;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t wg = (g + 1 < G ? g_P0[g + 1] : Pend) - g_P0[g];
+    if (wg >= heavy) {
+      const unsigned k = atomicAdd(n_heavy, 1u);
+      if (k < heavy_cap) heavy_ids[k] = (uint32_t)g;
+      shard[g] = -1;
+    } else {
+      const int32_t r = (int32_t)(class_hash(g_alpha[g]) % (uint32_t)W);
+      shard[g] = r;
+      atomicAdd(&sload[r], (unsigned long long)wg);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < W; i += blockDim.x)
+    if (sload[i]) atomicAdd(&light_load[i], sload[i]);
+}
+
+__global__ void k_heavy_set(const uint32_t *ids, const int32_t *sh, uint32_t n, int32_t *shard) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    shard[ids[i]] = sh[i];
+}
+
+__global__ void k_keep_items(const uint32_t *item_group, const int32_t *shard, uint64_t T,
+                             int32_t r, uint32_t *keep) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+       t += (uint64_t)gridDim.x * blockDim.x)
+    keep[t] = shard[item_group[t]] == r ? 1u : 0u;
+}
+
+__global__ void k_compact_items(const uint64_t *in, const uint32_t *keep, const uint32_t *pos,
+                                uint64_t T, uint64_t *out) {
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+       t += (uint64_t)gridDim.x * blockDim.x)
+    if (keep[t]) out[pos[t]] = in[t];
+}
+
+// Keep the items of shard r's classes: *items (sorted by target alpha, T
+// entries, weights summing to P with exclusive prefix Wexcl) is compacted in
+// place into *T_out entries.
+int shard_items(uint64_t **items, uint64_t **items_alt, const uint64_t *Wexcl, uint64_t T,
+                uint64_t P, int32_t r, int32_t W, uint64_t *T_out, Arena &arena) {
+  cudaStream_t s = arena.stream();
+  Arena sa(s);
+  uint32_t *item_group, *g_alpha;
+  uint64_t *g_P0, *g_item0;
+  size_t G = 0;
+  ASCI_TRY(sa.alloc(&item_group, T));
+  ASCI_TRY(item_groups(*items, Wexcl, T, item_group, &g_alpha, &g_P0, &g_item0, &G, sa));
+  const uint64_t heavy = std::max<uint64_t>(1, P / (64ull * (uint64_t)W));
+  const uint32_t heavy_cap = (uint32_t)std::min<uint64_t>(G, 64ull * W + 1);
+  int32_t *shard;
+  unsigned long long *light;
+  uint32_t *heavy_ids;
+  unsigned *n_heavy;
+  ASCI_TRY(sa.alloc(&shard, G));
+  ASCI_TRY(sa.alloc(&light, (size_t)W));
+  ASCI_TRY(sa.alloc(&heavy_ids, heavy_cap));
+  ASCI_TRY(sa.alloc(&n_heavy, 1));
+  ASCI_TRY_CUDA(cudaMemsetAsync(light, 0, (size_t)W * sizeof(unsigned long long), s));
+  ASCI_TRY_CUDA(cudaMemsetAsync(n_heavy, 0, sizeof(unsigned), s));
+  k_class_shard<<<grid_for(G), 256, (size_t)W * sizeof(unsigned long long), s>>>(
+      g_alpha, g_P0, G, P, heavy, W, shard, light, heavy_ids, n_heavy, heavy_cap);
+  ASCI_CHECK_LAUNCH();
+  unsigned nh = 0;
+  std::vector<uint64_t> loads((size_t)W);
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&nh, n_heavy, sizeof(nh), cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(loads.data(), light, (size_t)W * 8, cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  if (nh > heavy_cap) return ASCI_ECUDA;  // at most 64 W classes reach the threshold
+  if (nh) {
+    std::vector<uint32_t> ids(nh);
+    std::vector<uint64_t> p0(nh), p1(nh), wts(nh);
+    ASCI_TRY_CUDA(cudaMemcpyAsync(ids.data(), heavy_ids, nh * 4, cudaMemcpyDefault, s));
+    ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+    std::sort(ids.begin(), ids.end());  // placement independent of the listing order
+    for (unsigned i = 0; i < nh; ++i) {
+      ASCI_TRY_CUDA(cudaMemcpyAsync(&p0[i], g_P0 + ids[i], 8, cudaMemcpyDefault, s));
+      if (ids[i] + 1 < G)
+        ASCI_TRY_CUDA(cudaMemcpyAsync(&p1[i], g_P0 + ids[i] + 1, 8, cudaMemcpyDefault, s));
+      else
+        p1[i] = P;
+    }
+    ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+    for (unsigned i = 0; i < nh; ++i) wts[i] = p1[i] - p0[i];
+    std::vector<int32_t> sh(nh);
+    ASCI_TRY(asci_shard_assign(wts.data(), nh, W, loads.data(), sh.data()));
+    uint32_t *d_ids;
+    int32_t *d_sh;
+    ASCI_TRY(sa.alloc(&d_ids, nh));
+    ASCI_TRY(sa.alloc(&d_sh, nh));
+    ASCI_TRY_CUDA(cudaMemcpyAsync(d_ids, ids.data(), nh * 4, cudaMemcpyDefault, s));
+    ASCI_TRY_CUDA(cudaMemcpyAsync(d_sh, sh.data(), nh * 4, cudaMemcpyDefault, s));
+    k_heavy_set<<<grid_for(nh), 256, 0, s>>>(d_ids, d_sh, nh, shard);
+    ASCI_CHECK_LAUNCH();
+    ASCI_TRY_CUDA(cudaStreamSynchronize(s));  // the host vectors above are read by the copies
+  }
+  uint32_t *keep, *pos;
+  ASCI_TRY(sa.alloc(&keep, T));
+  ASCI_TRY(sa.alloc(&pos, T));
+  k_keep_items<<<grid_for(T), 256, 0, s>>>(item_group, shard, T, r, keep);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(scan_exclusive_u32(keep, pos, T, sa));
+  size_t kept = 0;
+  ASCI_TRY(kept_count(keep, pos, T, &kept, sa));
+  k_compact_items<<<grid_for(T), 256, 0, s>>>(*items, keep, pos, T, *items_alt);
+  ASCI_CHECK_LAUNCH();
+  std::swap(*items, *items_alt);
+  *T_out = kept;
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  return ASCI_OK;
+}
 
 struct StageTimer {
   cudaStream_t s;
@@ -554,7 +689,8 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
       return ASCI_EINVAL;
     }
   }
-  const uint64_t T = (uint64_t)ngroups * (nops - o_begin);
+  uint64_t T = (uint64_t)ngroups * (nops - o_begin);
+  const int32_t W = o.shard_count > 1 ? o.shard_count : 1;
   std::vector<Batch> batches;
   int max_level = 0;
   uint64_t *items = nullptr, *items_alt = nullptr, *w = nullptr, *Wexcl = nullptr;
@@ -577,6 +713,24 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
       record_error("pair count does not match the closed form", __FILE__, __LINE__);
       return ASCI_ECUDA;
     }
+    if (W > 1) {  // this shard's classes only
+      uint64_t T1 = 0;
+      ASCI_TRY(shard_items(&items, &items_alt, Wexcl, T, P, o.shard_index, W, &T1, arena));
+      ASCI_TRACE("shard %d of %d: items %llu of %llu", o.shard_index, W,
+                 (unsigned long long)T1, (unsigned long long)T);
+      T = T1;
+      P = 0;
+      if (T) {
+        ASCI_TRY(item_weights(items, T, opbits, grp_count, X, w, arena));
+        ASCI_TRY(scan_exclusive_u64(w, Wexcl, T, arena));
+        ASCI_TRY_CUDA(cudaMemcpyAsync(&last[0], Wexcl + T - 1, 8, cudaMemcpyDefault, stream));
+        ASCI_TRY_CUDA(cudaMemcpyAsync(&last[1], w + T - 1, 8, cudaMemcpyDefault, stream));
+        ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+        P = last[0] + last[1];
+      }
+    }
+  }
+  if (T > 0 && P > 0) {
     uint64_t bmax = o.max_batch_pairs;
     if (bmax == 0) {
       size_t fr = 0, tot = 0;
@@ -594,6 +748,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   }
   uint64_t bcap = 0;
   for (auto &b : batches) bcap = std::max(bcap, b.P1 - b.P0);
+  if (st) st->generated = P;  // C n_exc, or this shard's part of it
   ASCI_TRACE("planned: items=%llu pairs=%llu batches=%zu max_batch=%llu level=%d",
              (unsigned long long)T, (unsigned long long)P, batches.size(),
              (unsigned long long)bcap, max_level);
@@ -827,7 +982,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
       tm.stop(&tl[6]);
     }
   }
-  uint64_t unique = 0, excluded = 0, surviving = (uint64_t)m * X.total;
+  uint64_t unique = 0, excluded = 0, surviving = P;
   if (bcap) {
     unsigned long long hc[4];
     ASCI_TRY_CUDA(cudaMemcpyAsync(hc, dcount, sizeof(hc), cudaMemcpyDefault, stream));
@@ -983,6 +1138,9 @@ int asci_search(const asci_det *dets, const double *coeffs, size_t ndets, double
   if (opts) o = *opts;
   if (!(o.eps_search >= 0.0) || !std::isfinite(o.eps_search)) return ASCI_EINVAL;
   if (o.precision < ASCI_FP64 || o.precision > ASCI_FP32_INT_COMP_ACC) return ASCI_EINVAL;
+  if (o.shard_count < 0 || o.shard_count > 1024 ||
+      (o.shard_count > 1 && (o.shard_index < 0 || o.shard_index >= o.shard_count)))
+    return ASCI_EINVAL;
   cudaStream_t s;
   ASCI_TRY(begin_call(cuda_stream, &s));
   int r = search_impl(dets, coeffs, ndets, E0, ints, C, N, o, out_dets, out_scores, out_n, stats,
@@ -1135,6 +1293,26 @@ int asci_sort_accumulate(const asci_det *keys, const double *values, size_t n,
   ASCI_TRY(finish_out(out_keys, dok, u, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
   *out_n = u;
+  return ASCI_OK;
+}
+
+int asci_shard_assign(const uint64_t *weights, size_t n, int32_t shards,
+                      const uint64_t *initial_loads, int32_t *shard_out) {
+  if (shards < 1 || (n > 0 && (!weights || !shard_out))) return ASCI_EINVAL;
+  std::vector<size_t> order(n);
+  std::iota(order.begin(), order.end(), (size_t)0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](size_t a, size_t b) { return weights[a] > weights[b]; });
+  using Load = std::pair<uint64_t, int32_t>;  // (load, shard): smallest first
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> q;
+  for (int32_t i = 0; i < shards; ++i) q.push({initial_loads ? initial_loads[i] : 0ull, i});
+  for (size_t c : order) {
+    Load l = q.top();
+    q.pop();
+    shard_out[c] = l.second;
+    l.first += weights[c];
+    q.push(l);
+  }
   return ASCI_OK;
 }
 

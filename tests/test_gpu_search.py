@@ -340,3 +340,34 @@ def test_search_fp32_integrals_against_fp64_oracle(torch_cuda, asci, oracle_mod,
     got = set(zip(sa.tolist(), sb.tolist()))
     assert len(got) == len(want) == N
     assert len(got & want) >= 0.999 * N
+
+
+@pytest.mark.parametrize("W", [2, 3])
+def test_sharded_search_merges_to_the_unsharded_result(torch_cuda, asci, W):
+    """Shards of the target alpha classes (Alg. 3) run one after another on one
+    GPU; the top N of the union of their outputs, selected by the library's
+    kernel, is the unsharded result bit for bit, and the shards' counters add
+    up to the unsharded ones."""
+    torch = torch_cuda
+    _, h1, eri, ec, A, B, c, E0 = _random("random_14e20o")
+    C, N = 400, 5000
+    d = _dev(torch, A, B)
+    cf = torch.tensor(c, device="cuda")
+    hh, ee = torch.tensor(h1, device="cuda"), torch.tensor(eri, device="cuda")
+    full_k, full_s, full_st = asci.search(d, cf, E0, hh, ee, ec, C, N)
+    ks, ss, sts = [], [], []
+    for r in range(W):
+        k, s_, st = asci.search(d, cf, E0, hh, ee, ec, C, N, shard=(r, W))
+        ks.append(k)
+        ss.append(s_)
+        sts.append(st)
+    assert sum(st.generated for st in sts) == full_st.generated
+    assert sum(st.unique for st in sts) == full_st.unique
+    assert sum(st.excluded for st in sts) == full_st.excluded
+    assert min(st.generated for st in sts) > 0
+    gk, gs = asci.select_topn(torch.cat(ks), torch.cat(ss), N)
+    ga, gb = to_u64_pairs(gk)
+    fa, fb = to_u64_pairs(full_k)
+    o1, o2 = key_order(ga, gb), key_order(fa, fb)
+    assert np.array_equal(ga[o1], fa[o2]) and np.array_equal(gb[o1], fb[o2])
+    assert np.array_equal(gs.cpu().numpy()[o1], full_s.cpu().numpy()[o2])

@@ -1,0 +1,139 @@
+"""Constraint sharding (Sec. 2.2, Alg. 3) and the exchange of the sharded
+search, on the CPU: the greedy placement exported by the library, and the
+candidate exchange over torch.distributed with the gloo backend (world size 2).
+"""
+import os
+import socket
+
+import shutil
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def asci():
+    """The library, built here if needed (the functions used run on the host)."""
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    import paper_2303_05688_gb300 as m
+    from paper_2303_05688_gb300 import build
+    build.build()
+    m.load()
+    return m
+
+
+def _greedy(weights, shards, init=None):
+    """Alg. 3 written out: heaviest first (ties: lower index), each class to the
+    least-loaded shard (ties: lower shard)."""
+    loads = list(init) if init is not None else [0] * shards
+    out = [None] * len(weights)
+    for c in sorted(range(len(weights)), key=lambda i: (-weights[i], i)):
+        s = min(range(shards), key=lambda k: (loads[k], k))
+        out[c] = s
+        loads[s] += weights[c]
+    return out
+
+
+def test_shard_assign_is_the_greedy_placement(asci):
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        n = int(rng.integers(0, 60))
+        W = int(rng.integers(1, 9))
+        w = rng.integers(0, 1000, n).tolist()
+        init = rng.integers(0, 500, W).tolist() if rng.random() < 0.5 else None
+        got = asci.shard_assign(w, W, init)
+        assert got.tolist() == _greedy(w, W, init)
+
+
+def test_shard_assign_balance_bound(asci):
+    # Graham's bound for the greedy placement: makespan <= (4/3 - 1/(3W)) OPT,
+    # and OPT >= max(total / W, largest weight)
+    rng = np.random.default_rng(6)
+    for W in (2, 3, 8):
+        w = rng.integers(1, 10**6, 500)
+        sh = asci.shard_assign(w, W)
+        loads = np.bincount(sh, weights=w, minlength=W)
+        lower = max(w.sum() / W, w.max())
+        assert loads.max() <= (4 / 3 - 1 / (3 * W)) * lower * (1 + 1e-12)
+
+
+def test_shard_assign_rejects_bad_arguments(asci):
+    with pytest.raises(asci.AsciError):
+        asci.shard_assign([1, 2], 0)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _exchange_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import paper_2303_05688_gb300 as asci
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # shards hold disjoint targets; rank r has 3 + 2 r candidates
+        m = 3 + 2 * rank
+        keys = torch.tensor([[100 * rank + i, rank] for i in range(m)], dtype=torch.int64)
+        scores = torch.tensor([(-1) ** i * (m - i) / (rank + 1.0) for i in range(m)],
+                              dtype=torch.float64)
+        gk, gs = asci.gather_candidates(keys, scores)
+        q.put((rank, gk.numpy().tolist(), gs.numpy().tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_candidate_exchange_gloo_world2():
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_exchange_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in range(2):
+        r, k, s = q.get(timeout=120)
+        res[r] = (k, s)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    # every rank holds the union, in rank order
+    want_k, want_s = [], []
+    for rank in range(2):
+        m = 3 + 2 * rank
+        want_k += [[100 * rank + i, rank] for i in range(m)]
+        want_s += [(-1) ** i * (m - i) / (rank + 1.0) for i in range(m)]
+    for r in range(2):
+        assert res[r][0] == want_k and res[r][1] == want_s
+
+
+def test_union_of_local_topn_is_global_topn():
+    # the exchange's premise: shards partition the targets, so the top N of the
+    # union of each shard's top N is the top N of all (|S| descending, key
+    # ascending), checked by brute force on random partitions
+    rng = np.random.default_rng(8)
+
+    def top(keys, s, N):
+        o = np.lexsort((keys, -np.abs(s)))
+        return keys[o[:N]]
+
+    for _ in range(40):
+        n, W, N = int(rng.integers(1, 300)), int(rng.integers(1, 5)), int(rng.integers(1, 50))
+        keys = rng.permutation(10**6)[:n]
+        s = rng.normal(size=n) * np.where(rng.random(n) < 0.2, 1.0, 1e-3)
+        s[rng.random(n) < 0.1] = 0.5  # ties in |S|
+        part = rng.integers(0, W, n)
+        score_of = dict(zip(keys.tolist(), s.tolist()))
+        local = [top(keys[part == r], s[part == r], N) for r in range(W)]
+        uk = np.concatenate(local)
+        us = np.array([score_of[k] for k in uk.tolist()])
+        assert np.array_equal(top(uk, us, N), top(keys, s, N))
