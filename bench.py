@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--workload", default="random_24e30o")
     p.add_argument("--eps", type=float, default=0.0)
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32_fp64acc", "fp32_comp"])
+    p.add_argument("--sharded", action="store_true",
+                   help="under torchrun: one search split over the ranks by constraint class "
+                        "(strong scaling) instead of one search per rank")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-core", type=int, default=0,
@@ -218,7 +221,12 @@ def main():
     stream = torch.cuda.current_stream()
     asci.load()
 
+    sharded = args.sharded and world > 1
+
     def one(d=dets, cc=cf, hh=h1d, ee=erid):
+        if sharded:
+            return asci.sharded_search(d, cc, E0, hh, ee, ec, w.C, w.N, eps=args.eps,
+                                       precision=prec)
         return asci.search(d, cc, E0, hh, ee, ec, w.C, w.N, eps=args.eps, precision=prec)
 
     for _ in range(args.warmup):
@@ -256,7 +264,13 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_total = float(t.item())
     pairs = stats.generated
-    value = world * pairs * args.steps / t_total
+    if sharded:  # every rank's shard of one search: total pairs of the search
+        pt = torch.tensor([pairs], device=dev, dtype=torch.int64)
+        dist.all_reduce(pt)
+        pairs = int(pt.item())
+        value = pairs * args.steps / t_total
+    else:
+        value = world * pairs * args.steps / t_total
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -282,7 +296,7 @@ def main():
             t_e2e = float(t.item())
         h2d = hd.numel() * 8 + hc.numel() * 8 + hh.numel() * 8 + he.numel() * 8
         d2h = len(od) * 16 + len(osc) * 8
-        e2e = {"value": world * pairs * args.steps / t_e2e, "unit": UNIT,
+        e2e = {"value": (1 if sharded else world) * pairs * args.steps / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     if rank != 0:
@@ -325,13 +339,14 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "strong" if sharded else "weak", "vs_baseline": None,
         "dtype": "f64" if prec == asci.FP64 else "f32+f64", "data": "synthetic",
         "config": {"workload": w.name, "norb": w.norb, "nelec": [w.na, w.nb], "ndets": w.ndets,
                    "C": w.C, "N": w.N, "eps": args.eps, "precision": args.precision,
                    "excitations_per_step": pairs, "unique_per_step": stats.unique,
                    "batches": stats.batches, "l2": "flushed (512 MB write) before each step",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": (f"constraint shards x{world}" if sharded
+                                   else f"replicas x{world}")},
         "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
         "roofline": roofline, "cpu_baseline": cpu,
     }
