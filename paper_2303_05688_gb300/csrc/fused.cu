@@ -446,7 +446,7 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t beta, uint32_t nb) {
 constexpr int kRunThreads = 256;
 constexpr int kPairTab = 496;  // C(32, 2): unranked index pairs
 constexpr int kAdThreads = 256;
-constexpr int kAdTile = 1024;  // alpha-double pairs per CTA step
+constexpr int kAdTile = 512;   // alpha-double pairs per CTA step
 
 struct EmitArgs {
   DevInts I;
@@ -629,7 +629,7 @@ __device__ __forceinline__ void write_record(const EmitArgs &A, uint32_t pos, bo
 // EPS compiles Alg. 2's screen in (eps > 0); PREC selects the pair-value
 // precision (pair_value).
 template <bool EPS, int PREC>
-__global__ void __launch_bounds__(kRunThreads) k_emit_runs(EmitArgs A) {
+__global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
   extern __shared__ int64_t s_fx[];  // emit mode: jk[n*n], jj[n*n]
   __shared__ uint16_t s_pair[kPairTab];
   const int n = A.I.n;
