@@ -45,7 +45,8 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="asci", choices=["asci", "reference"])
-    p.add_argument("--workload", default="random_24e30o")
+    p.add_argument("--workload", default="random_24e30o",
+                   help="a single-system workload, or batched512 for 512 small systems")
     p.add_argument("--eps", type=float, default=0.0)
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32_fp64acc", "fp32_comp"])
     p.add_argument("--sharded", action="store_true",
@@ -189,10 +190,59 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- main ---
 
+def run_batched(args):
+    """Many independent small searches (512 uneven systems): searches/s with the
+    tuned number of concurrent streams, against the same searches one at a time."""
+    import numpy as np
+    import torch
+    import paper_2303_05688_gb300 as asci
+    import workloads as W
+    count = 512
+    gen = W.batched_systems(count)
+    dev = torch.device("cuda", 0)
+    systems = []
+    for sy in gen:
+        d = torch.tensor(np.stack([sy["alpha"], sy["beta"]], 1).astype(np.int64), device=dev)
+        h1 = torch.tensor(sy["h1"], device=dev)
+        eri = torch.tensor(sy["eri"], device=dev)
+        # E0 below the reference determinant's diagonal (an input of the search)
+        dg = asci.diagonal(h1, eri, sy["ecore"], d[:1])
+        E0 = float(dg.cpu()[0]) - 1.0
+        systems.append(dict(dets=d, coeffs=torch.tensor(sy["c"], device=dev), E0=E0, h1=h1,
+                            eri=eri, ecore=sy["ecore"], C=sy["C"], N=sy["N"]))
+    prec = {"fp64": asci.FP64, "fp32_fp64acc": asci.FP32_INT_FP64_ACC,
+            "fp32_comp": asci.FP32_INT_COMP_ACC}[args.precision]
+    streams = asci.tune_streams(systems, precision=prec)
+    for _ in range(max(args.warmup, 1)):
+        asci.search_many(systems[:32], streams=streams, precision=prec)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = asci.search_many(systems, streams=streams, precision=prec)
+    torch.cuda.synchronize()
+    t_many = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for sy in systems:
+        asci.search(sy["dets"], sy["coeffs"], sy["E0"], sy["h1"], sy["eri"], sy["ecore"],
+                    sy["C"], sy["N"], precision=prec)
+    torch.cuda.synchronize()
+    t_serial = time.perf_counter() - t0
+    pairs = sum(st.generated for _, _, st in res)
+    print(json.dumps({
+        "metric": "batched ASCI searches/s (512 uneven systems, (8e,8o) to (20e,20o))",
+        "value": count / t_many, "unit": "searches/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f64" if prec == asci.FP64 else "f32+f64",
+        "data": "synthetic", "streams": streams, "serial": count / t_serial,
+        "speedup_vs_serial": t_serial / t_many, "excitations_per_s": pairs / t_many,
+        "config": {"workload": "batched512", "systems": count, "pairs": pairs}}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched512":
+        return run_batched(args)
 
     import torch
     import torch.distributed as dist

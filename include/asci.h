@@ -223,6 +223,33 @@ int asci_sort_accumulate_noalloc(const asci_det *keys, const double *values, siz
  * breaking ties at the cutoff by key ascending.  Keys must be distinct.
  * Device pointers; output order unspecified.
  */
+/* One independent search of a batch (asci_search_many): the arguments of
+ * asci_search, and its result code. */
+typedef struct {
+  const asci_det *dets;
+  const double *coeffs;
+  size_t ndets;
+  double E0;
+  const asci_ints *ints;
+  size_t C, N;
+  asci_det *out_dets;   /* capacity N */
+  double *out_scores;   /* capacity N */
+  size_t *out_n;
+  asci_stats *stats;    /* nullable */
+  int32_t status;       /* written: ASCI_OK or the search's error code */
+} asci_problem;
+
+/* Many independent searches (the paper's method applied to uneven small
+ * systems, e.g. embedding fragments; not a step of Alg. 2): up to `streams`
+ * of them run at a time, each on its own CUDA stream driven by its own host
+ * thread, so that small searches overlap on the GPU.  Each problem is
+ * exactly asci_search(problem..., opts) (bit-identical results); pointers
+ * follow asci_search's rules.  Returns ASCI_OK when every problem succeeded,
+ * else the first failing problem's code (asci_last_error() holds its message);
+ * every problem's status is written.  streams < 1: ASCI_EINVAL. */
+int asci_search_many(asci_problem *problems, size_t count, const asci_opts *opts,
+                     int32_t streams);
+
 /* Alg. 3's greedy placement (longest processing time first): the n classes
  * of weights[n] (pairs) are visited in descending weight (ties: lower index
  * first) and each goes to the shard with the smallest load so far (ties: lower

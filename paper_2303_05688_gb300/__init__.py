@@ -19,7 +19,8 @@ import numpy as np
 
 __all__ = ["load", "lib_path", "launch_count", "search", "excitations", "diagonal", "sort_accumulate",
            "select_topn", "SearchStats", "AsciError", "FP64", "FP32_INT_FP64_ACC",
-           "FP32_INT_COMP_ACC", "shard_assign", "gather_candidates", "sharded_search"]
+           "FP32_INT_COMP_ACC", "shard_assign", "gather_candidates", "sharded_search",
+           "search_many", "tune_streams"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "lib", "libasci.so")
@@ -48,6 +49,13 @@ class _Opts(ct.Structure):
                 ("precision", ct.c_int32), ("max_batch_pairs", ct.c_uint64),
                 ("sort_output", ct.c_int32), ("shard_index", ct.c_int32),
                 ("shard_count", ct.c_int32)]
+
+
+class _Problem(ct.Structure):
+    _fields_ = [("dets", ct.c_void_p), ("coeffs", ct.c_void_p), ("ndets", ct.c_size_t),
+                ("E0", ct.c_double), ("ints", ct.c_void_p), ("C", ct.c_size_t),
+                ("N", ct.c_size_t), ("out_dets", ct.c_void_p), ("out_scores", ct.c_void_p),
+                ("out_n", ct.c_void_p), ("stats", ct.c_void_p), ("status", ct.c_int32)]
 
 
 class _Stats(ct.Structure):
@@ -111,6 +119,7 @@ def load():
     lib.asci_select_topn.restype = ct.c_int
     lib.asci_select_topn.argtypes = [vp, vp, sz, sz, vp, vp, szp, vp]
     lib.asci_shard_assign.argtypes = [vp, sz, ct.c_int32, vp, vp]
+    lib.asci_search_many.argtypes = [vp, sz, ct.POINTER(_Opts), ct.c_int32]
     lib.asci_default_opts.argtypes = [ct.POINTER(_Opts)]
     lib.asci_version.restype = ct.c_char_p
     lib.asci_strerror.restype = ct.c_char_p
@@ -312,6 +321,83 @@ def sort_accumulate(keys, values, stream=None):
                                     ct.byref(n_out), _stream_ptr(stream, True)),
            "asci_sort_accumulate")
     return ok[:n_out.value], os_[:n_out.value]
+
+
+def _opts(lib, eps, precision, max_batch_pairs, max_constraint_level, sort_output):
+    o = _Opts()
+    lib.asci_default_opts(ct.byref(o))
+    o.eps_search = float(eps)
+    o.precision = int(precision)
+    o.max_batch_pairs = int(max_batch_pairs)
+    o.max_constraint_level = int(max_constraint_level)
+    o.sort_output = 1 if sort_output else 0
+    return o
+
+
+def search_many(systems, *, streams=None, eps: float = 0.0, precision: int = FP64,
+                max_batch_pairs: int = 0, max_constraint_level: int = 0,
+                sort_output: bool = False):
+    """Many independent searches (asci_search_many): ``systems`` is a list of
+    dicts with keys dets, coeffs, E0, h1, eri, ecore, C, N (arrays as for
+    search()).  ``streams`` searches run at a time on their own CUDA streams;
+    None picks the count with tune_streams().  Returns a list of
+    (dets, scores, stats), each exactly what search() returns."""
+    lib = load()
+    if streams is None:
+        streams = tune_streams(systems, eps=eps, precision=precision,
+                               max_batch_pairs=max_batch_pairs)
+    keep, probs, outs = [], (_Problem * max(len(systems), 1))(), []
+    for i, sy in enumerate(systems):
+        db = _dets_buf(sy["dets"])
+        cb = _as_buf(sy["coeffs"], np.float64, "float64")
+        ints, _ = _ints(sy["h1"], sy["eri"], sy["ecore"], keep)
+        N = int(sy["N"])
+        od, odp = _out(max(N, 1), np.uint64, db.device, 2)
+        os_, osp = _out(max(N, 1), np.float64, db.device)
+        n_out, st = ct.c_size_t(0), _Stats()
+        keep += [db, cb, ints, n_out, st]
+        p = probs[i]
+        p.dets, p.coeffs, p.ndets, p.E0 = db.ptr, cb.ptr, int(db.obj.shape[0]), float(sy["E0"])
+        p.ints = ct.addressof(ints)
+        p.C, p.N = int(sy["C"]), N
+        p.out_dets, p.out_scores = odp, osp
+        p.out_n, p.stats = ct.addressof(n_out), ct.addressof(st)
+        outs.append((od, os_, n_out, st))
+    o = _opts(lib, eps, precision, max_batch_pairs, max_constraint_level, sort_output)
+    code = lib.asci_search_many(ct.addressof(probs), len(systems), ct.byref(o), int(streams))
+    _check(code, "asci_search_many")
+    if len(systems) and outs[0][0].__class__.__module__.startswith("torch"):
+        _torch().cuda.synchronize()
+    return [(od[:n.value], os_[:n.value], SearchStats._from(st)) for od, os_, n, st in outs]
+
+
+_TUNED = {}
+
+
+def tune_streams(systems, candidates=(1, 2, 4, 8, 16, 32), sample: int = 64, **kw):
+    """The project's autotuner for batched searches: the number of concurrent
+    streams that gives the most searches per second on a sample of the batch
+    (cached per batch signature: count and largest orbital count)."""
+    import time
+    if not systems:
+        return 1
+    norb = max(int(round(np.sqrt(np.prod(np.shape(sy["h1"]))))) for sy in systems)
+    sig = (len(systems) >= sample, norb, kw.get("precision", FP64))
+    if sig in _TUNED:
+        return _TUNED[sig]
+    sub = systems[:sample]
+    best, best_rate = 1, -1.0
+    search_many(sub[:2], streams=1, **kw)  # warm caches and the memory pool
+    for k in candidates:
+        if k > len(sub):
+            break
+        t0 = time.perf_counter()
+        search_many(sub, streams=k, **kw)
+        rate = len(sub) / (time.perf_counter() - t0)
+        if rate > best_rate:
+            best, best_rate = k, rate
+    _TUNED[sig] = best
+    return best
 
 
 def shard_assign(weights, shards: int, initial_loads=None):

@@ -2023,13 +2023,19 @@ int fused_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
   CA.tile0 = tile_begin;
   CA.ntiles = tile_end;
   const size_t cell_smem = sizeof(CellSmem);
-  static int per_sm = 0;
+  // once (thread-safe static initialisation): attribute and occupancy
+  static const int per_sm = [cell_smem]() {
+    int p = 0;
+    if (cudaFuncSetAttribute(k_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cell_smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k_cells, kCellThreads, cell_smem) !=
+            cudaSuccess)
+      return 0;
+    return p < 1 ? 1 : p;
+  }();
   if (!per_sm) {
-    ASCI_TRY_CUDA(cudaFuncSetAttribute(k_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)cell_smem));
-    ASCI_TRY_CUDA(
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cells, kCellThreads, cell_smem));
-    if (per_sm < 1) per_sm = 1;
+    record_error("tile kernel: cannot set its shared memory size", __FILE__, __LINE__);
+    return ASCI_ECUDA;
   }
   int dev = 0, sms = 152;
   ASCI_TRY_CUDA(cudaGetDevice(&dev));

@@ -22,6 +22,8 @@
 #include <mutex>
 #include <numeric>
 #include <queue>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "asci_internal.cuh"
@@ -1293,6 +1295,50 @@ int asci_sort_accumulate(const asci_det *keys, const double *values, size_t n,
   ASCI_TRY(finish_out(out_keys, dok, u, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
   *out_n = u;
+  return ASCI_OK;
+}
+
+int asci_search_many(asci_problem *problems, size_t count, const asci_opts *opts,
+                     int32_t streams) {
+  g_last_error[0] = 0;
+  if (streams < 1 || (count > 0 && !problems)) return ASCI_EINVAL;
+  if (!count) return ASCI_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ASCI_ECUDA;
+  std::atomic<size_t> next{0};
+  std::mutex mu;
+  size_t first_bad = count;
+  std::string first_msg;
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    cudaStream_t s = nullptr;
+    const bool own = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    for (;;) {
+      const size_t i = next.fetch_add(1);
+      if (i >= count) break;
+      asci_problem &p = problems[i];
+      p.status = own ? asci_search(p.dets, p.coeffs, p.ndets, p.E0, p.ints, p.C, p.N, opts,
+                                   p.out_dets, p.out_scores, p.out_n, p.stats, s)
+                     : ASCI_ECUDA;
+      if (p.status != ASCI_OK) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (i < first_bad) {
+          first_bad = i;
+          first_msg = own ? g_last_error : "cannot create a CUDA stream";
+        }
+      }
+    }
+    if (own) cudaStreamDestroy(s);
+  };
+  const size_t nt = std::min<size_t>((size_t)streams, count);
+  std::vector<std::thread> pool;
+  for (size_t t = 1; t < nt; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto &t : pool) t.join();
+  if (first_bad < count) {
+    snprintf(g_last_error, sizeof(g_last_error), "problem %zu: %s", first_bad, first_msg.c_str());
+    return problems[first_bad].status;
+  }
   return ASCI_OK;
 }
 

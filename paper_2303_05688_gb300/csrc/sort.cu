@@ -224,13 +224,11 @@ int radix_sort_impl(uint64_t **keys, uint64_t **keys_alt, V **vals, V **vals_alt
   uint32_t ntiles = (uint32_t)((n + kSortTile - 1) / kSortTile);
   uint32_t *hist = nullptr;
   ASCI_TRY(arena.alloc(&hist, (size_t)kRadix * ntiles));
-  static bool attr_set = false;  // one flag per instantiation
-  if (!attr_set) {
-    ASCI_TRY_CUDA(cudaFuncSetAttribute(k_digit_scatter<V, kHasVals>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)scatter_smem<V, kHasVals>()));
-    attr_set = true;
-  }
+  // once per instantiation (thread-safe static initialisation)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      k_digit_scatter<V, kHasVals>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)scatter_smem<V, kHasVals>());
+  ASCI_TRY_CUDA(attr);
   uint64_t mask = 0;
   ASCI_TRY(varying_bits_u64(*keys, n, &mask, arena));
   for (int shift = begin_bit; shift < end_bit; shift += 8) {

@@ -371,3 +371,29 @@ def test_sharded_search_merges_to_the_unsharded_result(torch_cuda, asci, W):
     o1, o2 = key_order(ga, gb), key_order(fa, fb)
     assert np.array_equal(ga[o1], fa[o2]) and np.array_equal(gb[o1], fb[o2])
     assert np.array_equal(gs.cpu().numpy()[o1], full_s.cpu().numpy()[o2])
+
+
+def test_search_many_equals_one_at_a_time(torch_cuda, asci, oracle_mod):
+    """Batched independent searches on concurrent streams (asci_search_many)
+    return exactly what separate calls return, system by system."""
+    torch = torch_cuda
+    systems = []
+    for sy in W.batched_systems(12, seed=77, scale=0.05):
+        ints = oracle_mod.Ints(sy["h1"], sy["eri"], sy["ecore"])
+        E0 = oracle_mod.diag(ints, (int(sy["alpha"][0]), int(sy["beta"][0]))) - 1.0
+        systems.append(dict(dets=_dev(torch, sy["alpha"], sy["beta"]),
+                            coeffs=torch.tensor(sy["c"], device="cuda"), E0=E0,
+                            h1=torch.tensor(sy["h1"], device="cuda"),
+                            eri=torch.tensor(sy["eri"], device="cuda"), ecore=sy["ecore"],
+                            C=sy["C"], N=sy["N"]))
+    many = asci.search_many(systems, streams=4)
+    assert len(many) == len(systems)
+    for sy, (k, s_, st) in zip(systems, many):
+        k1, s1, st1 = asci.search(sy["dets"], sy["coeffs"], sy["E0"], sy["h1"], sy["eri"],
+                                  sy["ecore"], sy["C"], sy["N"])
+        a, b = to_u64_pairs(k)
+        a1, b1 = to_u64_pairs(k1)
+        o, o1 = key_order(a, b), key_order(a1, b1)
+        assert np.array_equal(a[o], a1[o1]) and np.array_equal(b[o], b1[o1])
+        assert np.array_equal(s_.cpu().numpy()[o], s1.cpu().numpy()[o1])
+        assert (st.generated, st.unique, st.excluded) == (st1.generated, st1.unique, st1.excluded)

@@ -269,3 +269,38 @@ def stored_e0(name: str) -> float:
     path = os.path.join(os.path.dirname(__file__), "e0.json")
     with open(path) as f:
         return float(json.load(f)[name]["E0"])
+
+
+def batched_systems(count: int = 512, seed: int = 4000, scale: float = 1.0):
+    """Many small uneven systems for the batched search (512 by default).
+
+    System k: norb in {8, 10, ..., 20} (uniform), half filling, Ms = 0; even k a
+    periodic Hubbard ring with t = 1 and U/t ~ U(1, 8), odd k random
+    molecular-like integrals (seed 1000 + k); C ~ logU(1e3, 1e4) and
+    N ~ logU(1e4, 1e5), both times ``scale``; psi holds min(2 C, a quarter of the
+    determinant space) dets of the random walk (seed 1000 + k) with 1/rank
+    coefficients, and C is capped by |psi|.  E0 is left to the caller (it is an
+    input of the search; any value below the spectrum's top serves).
+    Returns a list of dicts with keys name, h1, eri, ecore, alpha, beta, c, C, N,
+    norb, na, nb.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        norb = int(rng.choice([8, 10, 12, 14, 16, 18, 20]))
+        na = nb = norb // 2
+        C = int(round(scale * 10 ** rng.uniform(3, 4)))
+        N = int(round(scale * 10 ** rng.uniform(4, 5)))
+        if k % 2 == 0:
+            h1, eri, ec = hubbard_ring(norb, 1.0, float(rng.uniform(1, 8)))
+            kind = "hubbard"
+        else:
+            h1, eri, ec = random_molecular(norb, 1000 + k)
+            kind = "random"
+        space = comb(norb, na) * comb(norb, nb)
+        nd = int(max(2, min(2 * C, space // 4)))
+        A, B = random_walk_dets(norb, na, nb, nd, 1000 + k)
+        c = rank_decay_coeffs(nd, 1000 + k)
+        out.append(dict(name=f"{kind}_{2 * na}e{norb}o_{k}", h1=h1, eri=eri, ecore=ec, alpha=A,
+                        beta=B, c=c, C=min(C, nd), N=N, norb=norb, na=na, nb=nb))
+    return out
