@@ -326,10 +326,48 @@ def run_served(args):
     return 0
 
 
+def run_levels(args):
+    """Constraint-level study (Sec. 2.2, Fig. 2-3 analogue) on the (24e,30o)
+    workload: for each deepest refinement level (3, 4, 5, 6 and n_alpha) and
+    batch cap, the number of batches, the largest batch against the mean, and
+    the search time (mean of args.steps after args.warmup)."""
+    import torch
+    import paper_2303_05688_gb300 as asci
+    w, h1, eri, ec, A, B, c, E0, np = load_workload("random_24e30o")
+    dev = torch.device("cuda", 0)
+    d = torch.tensor(np.stack([A, B], 1).astype(np.int64), device=dev)
+    cf, h1d, ed = (torch.tensor(x, device=dev) for x in (c, h1, eri))
+    rows = []
+    for bmax in (1 << 27, 1 << 29):
+        for lvl in (3, 4, 5, 6, w.na):
+            def one():
+                return asci.search(d, cf, E0, h1d, ed, ec, w.C, w.N, max_batch_pairs=bmax,
+                                   max_constraint_level=lvl)
+            for _ in range(max(args.warmup, 1)):
+                one()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(max(args.steps, 1)):
+                t0 = time.perf_counter()
+                _, _, st = one()
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            mean_batch = st.generated / max(st.batches, 1)
+            rows.append({"max_batch_pairs": bmax, "max_level": lvl, "level_used": st.max_level,
+                         "batches": st.batches, "largest_batch": st.max_batch,
+                         "largest_over_mean": st.max_batch / mean_batch,
+                         "ms": 1e3 * statistics.mean(ts)})
+    print(json.dumps({"metric": "constraint-level study, (24e,30o)", "unit": "ms",
+                      "data": "synthetic", "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "levels":
+        return run_levels(args)
     if args.workload == "batched512":
         return run_batched(args)
     if args.workload == "served":

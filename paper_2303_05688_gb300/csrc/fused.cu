@@ -194,11 +194,6 @@ __global__ void k_core_fock(FxInts X, const uint32_t *core_alpha, const uint32_t
   }
 }
 
-__global__ void k_fx_check_diag(FxInts X, const uint64_t *keys, size_t n, int64_t *out) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    out[i] = fx_diag(X, key_alpha(keys[i]), key_beta(keys[i]));
-}
 
 // ------------------------------------------------------ groups of items ---
 
@@ -295,7 +290,6 @@ constexpr int kCap = 1024;                          // records per tile
 constexpr int kSlots = 2 * kCap;                    // hash slots per tile (load <= 1/2)
 constexpr uint32_t kSmallMax = kCap / 2;            // packable class size
 constexpr uint32_t kBucketTarget = kCap * 13 / 16;  // expected records per hash bucket
-constexpr uint32_t kGroupsPerTile = 1024;
 
 namespace {
 
@@ -303,7 +297,7 @@ namespace {
 // slots for each hash bucket of a big class.
 __global__ void k_group_class(const uint64_t *g_P0, uint32_t gb0, uint32_t gb1, uint64_t Pend,
                               uint32_t *kind, uint32_t *nb, uint64_t *small_pairs,
-                              uint32_t *small_cnt, uint64_t *slots) {
+                              uint64_t *slots) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < gb1 - gb0;
        i += gridDim.x * blockDim.x) {
     const uint32_t g = gb0 + i;
@@ -313,36 +307,34 @@ __global__ void k_group_class(const uint64_t *g_P0, uint32_t gb0, uint32_t gb1, 
     nb[i] = k == kTileBucket ? (uint32_t)((P + kBucketTarget - 1) / kBucketTarget) : 0u;
     small_pairs[i] = k == kTilePacked ? P : 0;
     slots[i] = k == kTileBucket ? (uint64_t)nb[i] * kCap : P;
-    small_cnt[i] = k == kTilePacked ? 1u : 0u;
   }
 }
 
 __device__ __forceinline__ bool packed_start(uint32_t i, const uint32_t *kind,
-                                             const uint64_t *Ws, const uint32_t *Ns) {
+                                             const uint64_t *Ws) {
   if (kind[i] != kTilePacked) return false;
   if (i == 0 || kind[i - 1] != kTilePacked) return true;
-  return (Ws[i] / kSmallMax) != (Ws[i - 1] / kSmallMax) ||
-         (Ns[i] / kGroupsPerTile) != (Ns[i - 1] / kGroupsPerTile);
+  return (Ws[i] / kSmallMax) != (Ws[i - 1] / kSmallMax);
 }
 
 __global__ void k_tile_count(uint32_t ng, const uint32_t *kind, const uint32_t *nb,
-                             const uint64_t *Ws, const uint32_t *Ns, uint32_t *ntile) {
+                             const uint64_t *Ws, uint32_t *ntile) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x)
-    ntile[i] = kind[i] == kTilePacked ? (packed_start(i, kind, Ws, Ns) ? 1u : 0u)
+    ntile[i] = kind[i] == kTilePacked ? (packed_start(i, kind, Ws) ? 1u : 0u)
                                       : (kind[i] == kTileMedium ? 1u : nb[i]);
 }
 
 __global__ void k_tile_write(uint32_t gb0, uint32_t ng, const uint64_t *soff, uint64_t Pend,
                              const uint64_t *g_P0, const uint32_t *g_alpha,
                              const uint32_t *kind, const uint32_t *nb, const uint64_t *Ws,
-                             const uint32_t *Ns, const uint32_t *tile_base, TileDesc *tiles) {
+                             const uint32_t *tile_base, TileDesc *tiles) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
     const uint32_t g = gb0 + i;
     const uint64_t P = ((i + 1 < ng) ? g_P0[g + 1] : Pend) - g_P0[g];
     const uint32_t start = (uint32_t)soff[i];
     const uint32_t k = kind[i];
     if (k == kTilePacked) {
-      const bool st = packed_start(i, kind, Ws, Ns);
+      const bool st = packed_start(i, kind, Ws);
       const uint32_t t = st ? tile_base[i] : tile_base[i] - 1;
       if (st) {
         tiles[t].start = start;
@@ -962,7 +954,7 @@ __global__ void k_batch_lists(const uint64_t *items, uint64_t t0, uint64_t nt, i
 // all ones.
 __global__ void k_psi_route(const uint64_t *psi_keys, size_t npsi, const uint32_t *g_alpha,
                             uint32_t gb0, uint32_t ng, const uint32_t *kind, const uint32_t *nb,
-                            const uint64_t *Ws, const uint32_t *Ns, const uint32_t *tile_base,
+                            const uint64_t *Ws, const uint32_t *tile_base,
                             uint64_t *out) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npsi;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -977,7 +969,7 @@ __global__ void k_psi_route(const uint64_t *psi_keys, size_t npsi, const uint32_
     if (lo < ng && g_alpha[gb0 + lo] == a) {
       const uint32_t k = kind[lo];
       uint32_t t;
-      if (k == kTilePacked) t = packed_start(lo, kind, Ws, Ns) ? tile_base[lo] : tile_base[lo] - 1;
+      if (k == kTilePacked) t = packed_start(lo, kind, Ws) ? tile_base[lo] : tile_base[lo] - 1;
       else if (k == kTileMedium) t = tile_base[lo];
       else t = tile_base[lo] + bucket_of(b, nb[lo]);
       r = ((uint64_t)t << 32) | (uint64_t)i;
@@ -1027,7 +1019,6 @@ struct CellArgs {
   FxInts X;          // exact diagonal of the targets that pass the screen
   int64_t E0_x;
   double inv_scale;  // 2^-s
-  int s;             // fixed-point scale of the diagonal: 2^-s
   double tau;
   float tau_f;
   const uint64_t *psi_ht;
@@ -1625,13 +1616,6 @@ int core_fock(const FxInts &X, const uint32_t *core_alpha, const uint32_t *core_
   return ASCI_OK;
 }
 
-int fx_diag_keys(const FxInts &X, const uint64_t *keys, size_t n, int64_t *out, Arena &arena) {
-  if (!n) return ASCI_OK;
-  k_fx_check_diag<<<grid_for(n), 256, 0, arena.stream()>>>(X, keys, n, out);
-  ASCI_CHECK_LAUNCH();
-  return ASCI_OK;
-}
-
 // Groups (distinct target alpha strings) of the sorted item list.
 int item_groups(const uint64_t *items, const uint64_t *Wexcl, uint64_t T, uint32_t *item_group,
                 uint32_t **g_alpha, uint64_t **g_P0, uint64_t **g_item0, size_t *G,
@@ -1705,21 +1689,19 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   *ntiles_out = 0;
   oversized->clear();
   if (P1 <= P0 || ng == 0) return ASCI_OK;
-  uint32_t *kind, *nb, *small_cnt, *Ns, *cellbase, *ntile, *tile_base;
+  uint32_t *kind, *nb, *cellbase, *ntile, *tile_base;
   uint64_t *small_pairs, *Ws, *slots, *soff;
   ASCI_TRY(arena.alloc(&slots, ng));
   ASCI_TRY(arena.alloc(&soff, ng));
   ASCI_TRY(arena.alloc(&kind, ng));
   ASCI_TRY(arena.alloc(&nb, ng));
-  ASCI_TRY(arena.alloc(&small_cnt, ng));
-  ASCI_TRY(arena.alloc(&Ns, ng));
   ASCI_TRY(arena.alloc(&cellbase, ng));
   ASCI_TRY(arena.alloc(&ntile, ng));
   ASCI_TRY(arena.alloc(&tile_base, ng));
   ASCI_TRY(arena.alloc(&small_pairs, ng));
   ASCI_TRY(arena.alloc(&Ws, ng));
   k_group_class<<<grid_for(ng), 256, 0, s>>>(F.g_P0, gb0, gb1, P1, kind, nb, small_pairs,
-                                             small_cnt, slots);
+                                             slots);
   ASCI_CHECK_LAUNCH();
   ASCI_TRACE("stage: classified %u groups", ng);
   ASCI_TRY(scan_exclusive_u64(slots, soff, ng, arena));
@@ -1735,11 +1717,10 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
     }
   }
   ASCI_TRY(scan_exclusive_u64(small_pairs, Ws, ng, arena));
-  ASCI_TRY(scan_exclusive_u32(small_cnt, Ns, ng, arena));
   ASCI_TRY(scan_exclusive_u32(nb, cellbase, ng, arena));
   size_t ncells = 0, ntiles = 0;
   ASCI_TRY(kept_count(nb, cellbase, ng, &ncells, arena));
-  k_tile_count<<<grid_for(ng), 256, 0, s>>>(ng, kind, nb, Ws, Ns, ntile);
+  k_tile_count<<<grid_for(ng), 256, 0, s>>>(ng, kind, nb, Ws, ntile);
   ASCI_CHECK_LAUNCH();
   ASCI_TRY(scan_exclusive_u32(ntile, tile_base, ng, arena));
   ASCI_TRY(kept_count(ntile, tile_base, ng, &ntiles, arena));
@@ -1815,7 +1796,7 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   ASCI_TRY_CUDA(cudaMemsetAsync(tiles, 0, (ntiles + 1) * sizeof(TileDesc), s));
   ASCI_TRY_CUDA(cudaMemsetAsync(n_over, 0, 2 * sizeof(unsigned), s));
   ASCI_TRY_CUDA(cudaMemsetAsync(fill, 0, (ncells + 1) * sizeof(uint32_t), s));
-  k_tile_write<<<grid_for(ng), 256, 0, s>>>(gb0, ng, soff, P1, F.g_P0, F.g_alpha, kind, nb, Ws, Ns,
+  k_tile_write<<<grid_for(ng), 256, 0, s>>>(gb0, ng, soff, P1, F.g_P0, F.g_alpha, kind, nb, Ws,
                                             tile_base, tiles);
   ASCI_CHECK_LAUNCH();
   if (ncells) {
@@ -1833,7 +1814,7 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
     ASCI_TRY(arena.alloc(&pk_alt, F.npsi));
     ASCI_TRY(arena.alloc(&psi_list, F.npsi));
     k_psi_route<<<grid_for(F.npsi), 256, 0, s>>>(F.psi_keys, F.npsi, F.g_alpha, gb0, ng, kind, nb,
-                                                 Ws, Ns, tile_base, pk);
+                                                 Ws, tile_base, pk);
     ASCI_CHECK_LAUNCH();
     int topbit = 1;
     while ((1ull << topbit) <= (uint64_t)ntiles) ++topbit;
@@ -1990,7 +1971,6 @@ static CellArgs cell_args(const FusedCore &F, const Stage &st,
   CA.X = F.X;
   CA.E0_x = F.E0_x;
   CA.inv_scale = ldexp(1.0, -F.X.s);
-  CA.s = F.X.s;
   CA.tau = tau;
   CA.tau_f = (float)tau;
   if ((double)CA.tau_f > tau) CA.tau_f = nextafterf(CA.tau_f, 0.0f);
