@@ -338,7 +338,7 @@ def run_levels(args):
     d = torch.tensor(np.stack([A, B], 1).astype(np.int64), device=dev)
     cf, h1d, ed = (torch.tensor(x, device=dev) for x in (c, h1, eri))
     rows = []
-    for bmax in (1 << 27, 1 << 29):
+    for bmax in (1 << 24, 1 << 26, 1 << 29):
         for lvl in (3, 4, 5, 6, w.na):
             def one():
                 return asci.search(d, cf, E0, h1d, ed, ec, w.C, w.N, max_batch_pairs=bmax,
