@@ -397,3 +397,43 @@ def test_search_many_equals_one_at_a_time(torch_cuda, asci, oracle_mod):
         assert np.array_equal(a[o], a1[o1]) and np.array_equal(b[o], b1[o1])
         assert np.array_equal(s_.cpu().numpy()[o], s1.cpu().numpy()[o1])
         assert (st.generated, st.unique, st.excluded) == (st1.generated, st1.unique, st1.excluded)
+
+
+def test_search_boundary_cases(torch_cuda, asci, oracle_mod):
+    """norb = 32 (keys use all 64 bits), a fully occupied alpha string (no alpha
+    excitation exists), tied |c| in the core selection, and a core energy."""
+    torch = torch_cuda
+    rng = np.random.default_rng(12)
+    # norb = 32, two electrons per spin: alpha and beta words reach bit 31
+    n = 32
+    h1, eri, _ = W.random_molecular(n, 21)
+    A, B = W.random_walk_dets(n, 2, 2, 24, 21)
+    A[3] = np.uint64((1 << 31) | (1 << 30))
+    B[5] = np.uint64((1 << 31) | 1)
+    c = W.rank_decay_coeffs(24, 21)
+    ints = oracle_mod.Ints(h1, eri, 0.0)
+    E0 = oracle_mod.diag(ints, (int(A[0]), int(B[0]))) - 0.5
+    ref = oracle_mod.search(ints, A, B, c, E0, 10)
+    ga, gb, gs, st = _run(asci, torch, A, B, c, E0, h1, eri, 0.0, 10, 10**7)
+    compare_candidates(ga, gb, gs, ref, E0)
+    # alpha fully occupied (n_alpha = norb): only beta operations
+    n = 6
+    h1, eri, _ = W.random_molecular(n, 22)
+    A = np.full(8, (1 << n) - 1, dtype=np.uint64)
+    B = np.array([0b000111, 0b001011, 0b010011, 0b100011, 0b001101, 0b010101, 0b100101,
+                  0b011001], dtype=np.uint64)
+    c = rng.normal(size=8)
+    ints = oracle_mod.Ints(h1, eri, 1.25)
+    E0 = oracle_mod.diag(ints, (int(A[0]), int(B[0]))) - 1.0
+    ref = oracle_mod.search(ints, A, B, c, E0, 5)
+    ga, gb, gs, st = _run(asci, torch, A, B, c, E0, h1, eri, 1.25, 5, 10**6)
+    compare_candidates(ga, gb, gs, ref, E0)
+    # tied |c|: the core is the C smallest keys among the ties (key ascending)
+    _, h1, eri, ec, A, B, c, E0 = _random("random_12e12o")
+    c = np.where(np.arange(len(c)) % 2 == 0, 0.01, -0.01)
+    c[:3] = [0.9, -0.5, 0.3]
+    ints = oracle_mod.Ints(h1, eri, 2.5)
+    ref = oracle_mod.search(ints, A, B, c, E0 + 2.5, 60)
+    ga, gb, gs, st = _run(asci, torch, A, B, c, E0 + 2.5, h1, eri, 2.5, 60, 10**6)
+    assert st.ncore == 60
+    compare_candidates(ga, gb, gs, ref, E0 + 2.5)
