@@ -5,8 +5,12 @@ may import this package.  It shares no code with the GPU path; the C source
 ``asci_oracle.c`` is compiled with gcc into ``liboracle.so`` beside it.
 
 Functions follow arXiv:2303.05688: Eq. 1 (the ASCI score), Algorithm 2 (the
-search: core selection, single/double enumeration, sort-and-accumulate) and the
-duplicate-aware top-N selection of Sec. 2.2.  ``fock`` holds an independent
+search: core selection, single/double enumeration, sort-and-accumulate), the
+duplicate-aware top-N selection of Sec. 2.2, and Algorithm 1 (the ASCI loop:
+search, select, diagonalise in the selected space, repeat) with the
+diagonalisation written as its definition, the lowest eigenpair of the dense
+Hamiltonian restricted to the space (Sec. 2.3 computes it by Davidson,
+Algorithm 5).  ``fock`` holds an independent
 brute-force second-quantised Hamiltonian that pins the oracle's Slater-Condon
 evaluator.
 """
@@ -64,6 +68,8 @@ def _load():
             lib.oracle_diag.argtypes = [ct.c_int, f64p, f64p, ct.c_double, ct.c_uint64, ct.c_uint64]
             lib.oracle_dense_h.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p,
                                            ct.c_size_t, f64p]
+            lib.oracle_h_rows.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p,
+                                          ct.c_size_t, szp, ct.c_size_t, f64p]
             lib.oracle_pairs.restype = ct.c_size_t
             lib.oracle_pairs.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p, f64p,
                                          ct.c_size_t, ct.c_size_t, u64p, u64p, f64p]
@@ -221,3 +227,61 @@ def ground_state(ints: Ints, A, B):
     if v[np.argmax(np.abs(v))] < 0:
         v = -v
     return float(w[0]), v
+
+
+def h_rows(ints: Ints, A, B, rows) -> np.ndarray:
+    """Dense rows H[r, :] = <D_rows[r]|H|D_j> over the determinant list (A, B)."""
+    A, B = _u64(A), _u64(B)
+    rows = np.ascontiguousarray(rows, dtype=np.uintp)
+    out = np.empty((len(rows), len(A)))
+    _load().oracle_h_rows(*ints.args(), _p(A, ct.c_uint64), _p(B, ct.c_uint64), len(A),
+                          _p(rows, ct.c_size_t), len(rows), _p(out, ct.c_double))
+    return out
+
+
+def key_order(A, B) -> np.ndarray:
+    """Indices that sort determinants by key (beta word high, alpha word low)."""
+    return np.lexsort((_u64(A), _u64(B)))
+
+
+def asci_step(ints: Ints, A, B, c, E0: float, ncdets: int, ntdets: int, eps: float = 0.0):
+    """One pass of Algorithm 1 from the wavefunction (A, B, c) with energy E0.
+
+    The search (Algorithm 2) runs with the ncdets core; the next space holds
+    the ntdets determinants of largest magnitude among the current ones
+    (valued by their coefficient c_i) and the candidates (valued by their score
+    S_i, Eq. 1), ties by key ascending; its ground state is the lowest
+    eigenpair of H restricted to it.  Returns (A', B', c', E', changed) with
+    the determinants in key order and c' normalised, largest |c'| positive;
+    ``changed`` tells whether the determinant set differs from (A, B).
+    """
+    A, B, c = _u64(A), _u64(B), _f64(c)
+    res = search(ints, A, B, c, E0, ncdets, eps)
+    ua = np.concatenate([A, res.a])
+    ub = np.concatenate([B, res.b])
+    val = np.concatenate([c, res.score])
+    idx = topn(ua, ub, val, ntdets)
+    na, nb = ua[idx], ub[idx]
+    o = key_order(na, nb)
+    na, nb = na[o], nb[o]
+    changed = len(na) != len(A) or bool(np.any(idx >= len(A)))
+    E, v = ground_state(ints, na, nb)
+    return na, nb, v, E, changed
+
+
+def asci_loop(ints: Ints, A, B, c, ncdets: int, ntdets: int, max_iter: int, etol: float = 0.0,
+              eps: float = 0.0):
+    """Algorithm 1: from the start (A, B, c) (energy <psi|H|psi>/<psi|psi>),
+    repeat the step until the energy changes by at most etol, the determinant
+    set stops changing, or max_iter steps have run.  Returns (A, B, c, E,
+    history) with history a list of (size, energy) per step."""
+    E = variational_energy(ints, A, B, c)
+    hist = []
+    for _ in range(max_iter):
+        A2, B2, c2, E2, changed = asci_step(ints, A, B, c, E, ncdets, ntdets, eps)
+        hist.append((len(A2), E2))
+        done = abs(E2 - E) <= etol or not changed
+        A, B, c, E = A2, B2, c2, E2
+        if done:
+            break
+    return A, B, c, E, hist

@@ -525,6 +525,17 @@ void oracle_dense_h(int n, const double *h1, const double *eri, double ecore, co
     for (j = 0; j < nd; j++) out[i * nd + j] = oracle_hij_impl(&I, da[i], db[i], da[j], db[j]);
 }
 
+/* Selected dense rows of the same matrix: out[r][j] = <D_rows[r]|H|D_j>. */
+void oracle_h_rows(int n, const double *h1, const double *eri, double ecore, const uint64_t *da,
+                   const uint64_t *db, size_t nd, const size_t *rows, size_t nrows, double *out) {
+  oints I = {n, ecore, h1, eri};
+  size_t r, j;
+  for (r = 0; r < nrows; r++) {
+    size_t i = rows[r];
+    for (j = 0; j < nd; j++) out[r * nd + j] = oracle_hij_impl(&I, da[i], db[i], da[j], db[j]);
+  }
+}
+
 /* The pre-sort pair list of Alg. 2 for the given core determinants, in
  * generation order (eps = 0).  Returns the number of pairs written; call with
  * cap == 0 to get the count only. */

@@ -16,6 +16,7 @@ namespace asci {
 // ---------------------------------------------------------------------------
 
 void record_error(const char *what, const char *file, int line);
+void clear_last_error();
 
 // Stage tracing to stderr, enabled by the environment variable ASCI_TRACE=1.
 bool trace_on();
@@ -113,6 +114,50 @@ class Arena {
   size_t bump_cap_ = 0, bump_off_ = 0;
 };
 
+// Host or device memory: inputs are used in place when on the device and
+// staged through the arena otherwise; outputs that are host memory are written
+// through a device buffer and copied out at the end of the call.
+inline bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+int to_device(const T *src, size_t count, const T **dst, Arena &arena) {
+  if (is_device_ptr(src)) {
+    *dst = src;
+    return ASCI_OK;
+  }
+  T *d = nullptr;
+  ASCI_TRY(arena.alloc(&d, count));
+  if (count)
+    ASCI_TRY_CUDA(cudaMemcpyAsync(d, src, count * sizeof(T), cudaMemcpyDefault,
+                                  arena.stream()));
+  *dst = d;
+  return ASCI_OK;
+}
+
+template <typename T>
+int out_buffer(T *user, size_t count, T **dev, Arena &arena) {
+  if (is_device_ptr(user)) {
+    *dev = user;
+    return ASCI_OK;
+  }
+  return arena.alloc(dev, count);
+}
+
+template <typename T>
+int finish_out(T *user, const T *dev, size_t count, cudaStream_t s) {
+  if ((const T *)user != dev && count)
+    ASCI_TRY_CUDA(cudaMemcpyAsync(user, dev, count * sizeof(T), cudaMemcpyDefault, s));
+  return ASCI_OK;
+}
+
 // ---------------------------------------------------------------------------
 // determinants and keys
 // ---------------------------------------------------------------------------
@@ -193,6 +238,35 @@ struct DevInts {
   const float *eri32;   // n^4 FP32 copy (precision variants)
   const float *asym32;  // n^4 FP32 copy
 };
+
+// Slater-Condon pieces shared by the excitation generator and the
+// Hamiltonian build.  Single i -> a on the string s (other spin o), without
+// its sign: h_ia + sum_{k in s} ((ia|kk) - (ik|ka)) + sum_{k in o} (ia|kk).
+__device__ __forceinline__ double single_value(const DevInts &I, uint32_t s, uint32_t o, int i,
+                                               int a) {
+  const int n = I.n;
+  const double *ss = I.s_same + ((size_t)i * n + a) * n;
+  const double *so = I.s_opp + ((size_t)i * n + a) * n;
+  double v = I.h1[i * n + a];
+  for (uint32_t m = s; m; m &= m - 1) v += ss[__ffs(m) - 1];
+  for (uint32_t m = o; m; m &= m - 1) v += so[__ffs(m) - 1];
+  return v;
+}
+
+__device__ __forceinline__ double eri4(const double *t, int n, int i, int a, int j, int b) {
+  return t[(((size_t)i * n + a) * n + j) * n + b];
+}
+
+// Sign bit of the same-spin double i<j -> a<b on s, taken as i -> a, then j -> b.
+__device__ __forceinline__ int double_parity(uint32_t s, int i, int j, int a, int b) {
+  int p1 = single_parity(s, i, a);
+  uint32_t s1 = s ^ (1u << i) ^ (1u << a);
+  return p1 ^ single_parity(s1, j, b);
+}
+
+__device__ __forceinline__ uint32_t full_mask(int n) {
+  return n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+}
 
 // Counts of one determinant's excitations (Sec. 2.1: singles and doubles).
 struct ExcCounts {

@@ -73,21 +73,6 @@ __global__ void k_tables_n2(const double *eri, int n, double *jk, double *jj) {
 
 // ------------------------------ evaluation ---------------------------------
 
-__device__ __forceinline__ double single_value(const DevInts &I, uint32_t s, uint32_t o, int i,
-                                               int a) {
-  const int n = I.n;
-  const double *ss = I.s_same + ((size_t)i * n + a) * n;
-  const double *so = I.s_opp + ((size_t)i * n + a) * n;
-  double v = I.h1[i * n + a];
-  for (uint32_t m = s; m; m &= m - 1) v += ss[__ffs(m) - 1];
-  for (uint32_t m = o; m; m &= m - 1) v += so[__ffs(m) - 1];
-  return v;
-}
-
-__device__ __forceinline__ double eri4(const double *t, int n, int i, int a, int j, int b) {
-  return t[(((size_t)i * n + a) * n + j) * n + b];
-}
-
 __device__ __forceinline__ void decode_single(uint32_t s, uint32_t virt, uint32_t idx, uint32_t nv,
                                               int *i, int *a) {
   *i = nth_set_bit(s, (int)(idx / nv));
@@ -103,16 +88,6 @@ __device__ __forceinline__ void decode_double(uint32_t s, uint32_t virt, uint32_
   *j = nth_set_bit(s, h2);
   *a = nth_set_bit(virt, p1);
   *b = nth_set_bit(virt, p2);
-}
-
-__device__ __forceinline__ int double_parity(uint32_t s, int i, int j, int a, int b) {
-  int p1 = single_parity(s, i, a);
-  uint32_t s1 = s ^ (1u << i) ^ (1u << a);
-  return p1 ^ single_parity(s1, j, b);
-}
-
-__device__ __forceinline__ uint32_t full_mask(int n) {
-  return n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
 }
 
 // Excitation e (fixed order) of determinant (A, B): target and H_ij.

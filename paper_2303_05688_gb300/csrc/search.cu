@@ -92,38 +92,14 @@ void record_error(const char *what, const char *file, int line) {
   snprintf(g_last_error, sizeof(g_last_error), "%s (%s:%d)", what, file, line);
 }
 
+void clear_last_error() { g_last_error[0] = 0; }
+
 namespace {
 
 inline unsigned grid_for(size_t n, unsigned cap = 152 * 16) {
   size_t b = (n + 255) / 256;
   if (b < 1) b = 1;
   return (unsigned)(b < cap ? b : cap);
-}
-
-bool is_device_ptr(const void *p) {
-  if (!p) return false;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
-// Copy `count` elements to a device buffer (alloc + copy when host memory).
-template <typename T>
-int to_device(const T *src, size_t count, const T **dst, Arena &arena) {
-  if (is_device_ptr(src)) {
-    *dst = src;
-    return ASCI_OK;
-  }
-  T *d = nullptr;
-  ASCI_TRY(arena.alloc(&d, count));
-  if (count)
-    ASCI_TRY_CUDA(cudaMemcpyAsync(d, src, count * sizeof(T), cudaMemcpyDefault,
-                                  arena.stream()));
-  *dst = d;
-  return ASCI_OK;
 }
 
 // ------------------------------ kernels ------------------------------------
@@ -1060,22 +1036,6 @@ static int stage_ints(const asci_ints *ints, Arena &arena, const double **h1, co
   const size_t n = (size_t)ints->norb;
   ASCI_TRY(to_device(ints->h1, n * n, h1, arena));
   ASCI_TRY(to_device(ints->eri, n * n * n * n, eri, arena));
-  return ASCI_OK;
-}
-
-template <typename T>
-static int out_buffer(T *user, size_t count, T **dev, Arena &arena) {
-  if (is_device_ptr(user)) {
-    *dev = user;
-    return ASCI_OK;
-  }
-  return arena.alloc(dev, count);
-}
-
-template <typename T>
-static int finish_out(T *user, const T *dev, size_t count, cudaStream_t s) {
-  if ((const T *)user != dev && count)
-    ASCI_TRY_CUDA(cudaMemcpyAsync(user, dev, count * sizeof(T), cudaMemcpyDefault, s));
   return ASCI_OK;
 }
 

@@ -9,7 +9,10 @@
   structural set of dets within two excitations of the core and outside psi,
   counts follow the closed form, and the single-determinant case reduces to
   Epstein-Nesbet coefficients.
-* The ASCI loop with N = infinity converges to full CI on the Hubbard ring.
+* The ASCI loop (Alg. 1) with N = infinity converges to full CI on the Hubbard
+  ring; each step's selection equals a brute-force sort of |c| and |S| with key
+  ties, its eigenpair satisfies H v = E v on the space, and its energies stay
+  above full CI (Rayleigh-Ritz).
 * Mutation tests plant plausible mistakes in a copy of the oracle and check
   that a pin catches each one.
 """
@@ -253,18 +256,64 @@ def test_asci_loop_reaches_full_ci_on_hubbard_ring(oracle_mod):
     E_fci = _lowest(fock.hamiltonian(n, h1, eri, ec, A, B))
     from tests.golden.make_golden import hubbard_start
     pa, pb, c, E0 = hubbard_start(oracle_mod)
-    for _ in range(10):
-        res = oracle_mod.search(ints, pa, pb, c, E0, len(pa))
-        if len(res.a) == 0:
-            break
-        pa = np.concatenate([pa, res.a])
-        pb = np.concatenate([pb, res.b])
-        import scipy.linalg as sl
-        H = oracle_mod.dense_h(ints, pa, pb)
-        w, V = sl.eigh(H, subset_by_index=[0, 0])
-        E0, c = float(w[0]), V[:, 0]
+    big = 10 ** 6
+    pa, pb, c, E, hist = oracle_mod.asci_loop(ints, pa, pb, c, big, big, max_iter=10)
     assert len(pa) == len(A) == 4900
-    assert abs(E0 - E_fci) < 1e-9
+    assert abs(E - E_fci) < 1e-9
+    # the last step found nothing new: the sector is closed under H
+    assert hist[-1][0] == 4900 and len(hist) < 10
+
+
+def test_asci_step_selects_by_magnitude_with_key_ties(oracle_mod):
+    """The next space is the ntdets largest of |c_i| (current dets) and |S_i|
+    (candidates), ties by key ascending: brute force with Python sorting."""
+    n, na, nb = 6, 3, 3
+    h1, eri, ec = W.random_molecular(n, 11)
+    ints = oracle_mod.Ints(h1, eri, ec)
+    A, B = W.random_walk_dets(n, na, nb, 12, seed=5)
+    c = W.rank_decay_coeffs(12, seed=5)
+    E0 = oracle_mod.variational_energy(ints, A, B, c)
+    res = oracle_mod.search(ints, A, B, c, E0, 6)
+    pool = [(abs(float(v)), int(b), int(a)) for a, b, v in zip(A, B, c)]
+    pool += [(abs(float(v)), int(b), int(a)) for a, b, v in zip(res.a, res.b, res.score)]
+    pool.sort(key=lambda t: (-t[0], t[1], t[2]))
+    for ntd in (1, 5, 12, 30, 10 ** 6):
+        na_, nb_, v, E, changed = oracle_mod.asci_step(ints, A, B, c, E0, 6, ntd)
+        want = sorted((b, a) for _, b, a in pool[:ntd])
+        assert [(int(b), int(a)) for a, b in zip(na_, nb_)] == want
+        # c' is the ground vector of the dense H on that space
+        H = fock.hamiltonian(n, h1, eri, ec, na_, nb_)
+        assert abs(E - _lowest(H)) < 1e-10
+        assert np.allclose(H @ v, E * v, atol=1e-9) and abs(np.linalg.norm(v) - 1) < 1e-12
+        assert v[np.argmax(np.abs(v))] > 0
+        assert changed == (set(want) != set(zip(B.tolist(), A.tolist())))
+
+
+def test_asci_loop_energies_are_variational(oracle_mod):
+    """Every step's energy lies above full CI of the sector (Rayleigh-Ritz) and
+    the loop's output is that step's ground state."""
+    n, na, nb = 8, 4, 4
+    h1, eri, ec = W.random_molecular(n, 3)
+    ints = oracle_mod.Ints(h1, eri, ec)
+    A, B = fock.sector(n, na, nb)
+    E_fci = _lowest(fock.hamiltonian(n, h1, eri, ec, A, B))
+    a0 = np.array([W.aufbau(na)], dtype=np.uint64)
+    b0 = np.array([W.aufbau(nb)], dtype=np.uint64)
+    pa, pb, c, E, hist = oracle_mod.asci_loop(ints, a0, b0, np.ones(1), 50, 400, max_iter=6)
+    assert len(hist) >= 3
+    for size, e in hist:
+        assert e >= E_fci - 1e-10 and size <= 400
+    assert hist[-1][1] == E and E - E_fci < 0.05 * abs(E_fci)
+
+
+def test_h_rows_equal_bruteforce_rows(oracle_mod):
+    n, na, nb = 5, 2, 3
+    h1, eri, ec = W.random_molecular(n, 7)
+    ints = oracle_mod.Ints(h1, eri, ec)
+    A, B = fock.sector(n, na, nb)
+    H = fock.hamiltonian(n, h1, eri, ec, A, B)
+    rows = [0, 3, len(A) - 1, 17]
+    assert np.allclose(oracle_mod.h_rows(ints, A, B, rows), H[rows], atol=1e-13, rtol=0)
 
 
 # --------------------------------------------------------------------------
