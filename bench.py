@@ -31,11 +31,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ASCI search scored excitations/s at (24e,30o)"
-# DRAM bytes (read + write) per staged pair reduced by the tile kernel k_cells,
-# from ncu (dram__bytes_read.sum + dram__bytes_write.sum over one launch on the
-# (24e,30o) workload, divided by the launch's records).  None until measured
-# for the current kernel.
-TILE_DRAM_BYTES_PER_RECORD = None
+# DRAM bytes (read + write) per staged pair reduced by the tile kernel k_cells
+# on the (24e,30o) workload: ncu's dram__bytes_read.sum + dram__bytes_write.sum
+# summed over the 39 launches of one search (112.16 GB), divided by that
+# search's 6.675e9 staged pairs (profiles/k_cells_random24e30o.md).  Reported
+# as `traffic` for that workload only.
+TILE_DRAM_BYTES_PER_RECORD = {"random_24e30o": 16.80}
 UNIT = "excitations/s"
 
 
@@ -491,8 +492,8 @@ def main():
     per_launch_s = tiles_ms / 1e3 / max(tile_launches, 1)
     bytes_per_launch = 16.0 * tile_records / max(tile_launches, 1)
     achieved = bytes_per_launch / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
-    traffic = (TILE_DRAM_BYTES_PER_RECORD * tile_records / max(tile_launches, 1)
-               if TILE_DRAM_BYTES_PER_RECORD else None)
+    per_rec = TILE_DRAM_BYTES_PER_RECORD.get(w.name)
+    traffic = per_rec * tile_records / max(tile_launches, 1) if per_rec else None
     # the search as a whole against its algorithmic floor,
     # B_alg = 32 P + 24 C + 16 |psi| + 32 U + 16 N bytes
     b_alg = (32 * stats.surviving + 24 * stats.ncore + 16 * w.ndets + 32 * stats.unique
