@@ -7,7 +7,10 @@
  * single and double excitation, evaluates H_ij by the Slater-Condon rules,
  * accumulates the numerator sum_j H_ij c_j per unique target
  * (sort-and-accumulate), scores each target outside psi as
- * num / (E0 - H_ii) and keeps the N targets of largest |score|.
+ * num / (E0 - H_ii) and keeps the N targets of largest |score|.  Around it,
+ * the variational step (Sec. 2.3: the sparse Hamiltonian of a determinant
+ * list, its product with vectors, the Davidson eigensolver) closes the ASCI
+ * loop of Algorithm 1.
  *
  * Conventions shared by every entry point:
  *  - A determinant is a pair of occupation words; bit p of `alpha` (`beta`) is
@@ -217,12 +220,6 @@ int asci_sort_accumulate_noalloc(const asci_det *keys, const double *values, siz
                                  asci_det *out_keys, double *out_sums, size_t *out_n,
                                  void *cuda_stream);
 
-/*
- * Top-N selection by |score| (Sec. 2.2, the duplicate-aware selection that
- * replaces a full sort): returns the min(N, n) entries of largest |score|,
- * breaking ties at the cutoff by key ascending.  Keys must be distinct.
- * Device pointers; output order unspecified.
- */
 /* One independent search of a batch (asci_search_many): the arguments of
  * asci_search, and its result code. */
 typedef struct {
@@ -259,9 +256,152 @@ int asci_search_many(asci_problem *problems, size_t count, const asci_opts *opts
 int asci_shard_assign(const uint64_t *weights, size_t n, int32_t shards,
                       const uint64_t *initial_loads, int32_t *shard_out);
 
+/*
+ * Top-N selection by |score| (Sec. 2.2, the duplicate-aware selection that
+ * replaces a full sort): returns the min(N, n) entries of largest |score|,
+ * breaking ties at the cutoff by key ascending.  Keys must be distinct.
+ * Device pointers; output order unspecified.
+ */
 int asci_select_topn(const asci_det *keys, const double *scores, size_t n, size_t N,
                      asci_det *out_keys, double *out_scores, size_t *out_n,
                      void *cuda_stream);
+
+
+/* ---------------------------------------------------------------------------
+ * The variational step of the ASCI loop (Algorithm 1: "diagonalize the
+ * Hamiltonian in the selected determinant space"; Sec. 2.3).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * The Hamiltonian restricted to a determinant list, as a sparse matrix in
+ * compressed sparse row form (Sec. 2.3: the double loop approach over pairs of
+ * determinants, CSR storage).  Row and column i belong to dets[i].  Row i holds
+ * its diagonal element H_ii and every H_ij != 0 with dets[j] singly or doubly
+ * excited from dets[i] (by the Slater-Condon rules of the conventions above),
+ * columns ascending; the matrix is symmetric.
+ *
+ *  dets[n]       distinct determinants with equal electron counts (n < 2^31).
+ *  row_ptr[n+1]  out (int64): row i is entries row_ptr[i] .. row_ptr[i+1]-1.
+ *  col, val      out: column indices (int32) and elements (FP64), capacity
+ *                entries each.  Both may be NULL with capacity 0.
+ *  *nnz          out: the number of stored elements (always written).
+ * When capacity < *nnz only row_ptr and *nnz are written (a size query) and
+ * the call still returns ASCI_OK; call again with capacity >= *nnz.  Every
+ * call runs the counting pass; a call with room also runs the filling pass.
+ *
+ * Errors: ASCI_EINVAL for norb outside 1..32, n == 0 or n >= 2^31, NULL
+ * pointers, determinants with bits at or above norb, mixed electron counts,
+ * duplicates, or non-finite integrals; ASCI_ENOMEM; ASCI_ECUDA.
+ */
+int asci_hamiltonian(const asci_det *dets, size_t n, const asci_ints *ints, int64_t *row_ptr,
+                     int32_t *col, double *val, size_t capacity, size_t *nnz,
+                     void *cuda_stream);
+
+/*
+ * y = H x for a matrix from asci_hamiltonian (the local sparse product of
+ * Sec. 2.3, Algorithm 6 on one device).  x[n] in, y[n] out (distinct
+ * buffers).  Each y_i is summed in a fixed order: repeated calls give the same
+ * bits.
+ */
+int asci_spmv(const int64_t *row_ptr, const int32_t *col, const double *val, size_t n,
+              const double *x, double *y, void *cuda_stream);
+
+/* Davidson controls (Algorithm 5). */
+typedef struct {
+  int32_t max_subspace; /* Krylov dimension k before a restart, 2..48 (default 24) */
+  int32_t max_iter;     /* products with H at most (default 300) */
+  double tol;           /* stop when ||H v - E v|| <= tol, v normalised (default 1e-8) */
+} asci_davidson_opts;
+
+void asci_default_davidson_opts(asci_davidson_opts *opts);
+
+/*
+ * Lowest eigenpair of a matrix from asci_hamiltonian by the Davidson method
+ * (Sec. 2.3, Algorithm 5, on one device): the subspace grows by the
+ * preconditioned residual R / (E - H_ii) (the shifted Jacobi preconditioner),
+ * orthogonalised against the basis by two passes of Gram-Schmidt; the
+ * subspace eigenproblem is solved on the device (Jacobi rotations); at
+ * max_subspace vectors the basis restarts from the four lowest Ritz vectors
+ * (fewer when max_subspace <= 4).  The
+ * first expansion vector is the unpreconditioned H v0 - (v0.H v0) v0, as in
+ * Algorithm 5.
+ *
+ *  guess[n]    start vector (nullable: the unit vector of the smallest H_ii).
+ *  *energy     out: the Ritz value.
+ *  vec[n]      out: the Ritz vector, unit norm, largest |component| positive
+ *              (lowest index among equal magnitudes).
+ *  *iterations out (nullable): products with H performed.
+ *  *residual   out (nullable): the final ||H v - E v||.
+ * Returns ASCI_OK when converged to tol, ASCI_ETIMEOUT when max_iter products
+ * ran first (the outputs then hold the last Ritz pair).
+ */
+int asci_davidson(const int64_t *row_ptr, const int32_t *col, const double *val, size_t n,
+                  const double *guess, const asci_davidson_opts *opts, double *energy,
+                  double *vec, int32_t *iterations, double *residual, void *cuda_stream);
+
+/* Controls of the ASCI loop. */
+#define ASCI_LOOP_MAX_STEPS 64
+typedef struct {
+  uint64_t ncdets;    /* core size N_cdets of each search (Alg. 2) */
+  uint64_t ntdets;    /* wavefunction size N_tdets kept by each step */
+  int32_t max_steps;  /* 1..ASCI_LOOP_MAX_STEPS */
+  double etol;        /* stop once a step changes the energy by at most etol */
+  asci_opts search;   /* options of every search */
+  asci_davidson_opts davidson;
+} asci_loop_opts;
+
+/* Per-step record of the ASCI loop (device milliseconds). */
+typedef struct {
+  int32_t steps;        /* steps run */
+  double start_energy;  /* <psi0|H|psi0> / <psi0|psi0> of the start */
+  double energy[ASCI_LOOP_MAX_STEPS];
+  uint64_t ndets[ASCI_LOOP_MAX_STEPS];       /* |psi| after the step */
+  uint64_t new_dets[ASCI_LOOP_MAX_STEPS];    /* determinants that entered */
+  uint64_t nnz[ASCI_LOOP_MAX_STEPS];         /* stored elements of H on the step's space */
+  int32_t davidson_iters[ASCI_LOOP_MAX_STEPS];
+  double t_search[ASCI_LOOP_MAX_STEPS];
+  double t_hamiltonian[ASCI_LOOP_MAX_STEPS];
+  double t_davidson[ASCI_LOOP_MAX_STEPS];
+} asci_loop_stats;
+
+/* Defaults: ncdets 1e4, ntdets 1e5, 8 steps, etol 1e-6 Hartree, default search
+ * and Davidson options. */
+void asci_default_loop_opts(asci_loop_opts *opts);
+
+/*
+ * The ASCI loop (Algorithm 1) from a start wavefunction (for instance the
+ * Hartree-Fock determinant with coefficient 1).  E_0 is the start's energy
+ * <psi|H|psi>/<psi|psi>.  Each step:
+ *   1. searches (asci_search, Algorithm 2) from (psi_k, c_k, E_k) with the
+ *      min(ncdets, |psi_k|) core and N = ntdets;
+ *   2. keeps the ntdets determinants of largest magnitude among psi_k (valued
+ *      by c_k) and the candidates (valued by their score S, Eq. 1), ties by
+ *      key ascending, ordered by key;
+ *   3. builds H on that space (asci_hamiltonian) and takes its lowest
+ *      eigenpair (asci_davidson, guess: the values of step 2) as
+ *      (c_{k+1}, E_{k+1}).
+ * A candidate whose H_ii equals E_k has no finite score: the call then
+ * returns ASCI_EINVAL (start from a wavefunction whose energy lies below the
+ * diagonal of every determinant it connects to, e.g. a small CI).
+ * The loop stops after max_steps, once |E_{k+1} - E_k| <= etol, or once a
+ * step leaves the determinant set unchanged.  The final ASCI-PT2 step of
+ * Algorithm 1 is not part of this call.
+ *
+ *  dets[ndets], coeffs[ndets]  the start (distinct determinants, equal counts).
+ *  out_dets, out_coeffs        capacity entries each, capacity >= ntdets: the
+ *                              final space in key order and its ground vector
+ *                              (unit norm, largest |c| positive).
+ *  *out_n, *energy             its size and energy.
+ *  stats                       nullable.
+ * Errors: those of asci_search, asci_hamiltonian and asci_davidson (a
+ * Davidson that reaches max_iter unconverged returns ASCI_ETIMEOUT), and
+ * ASCI_EINVAL for ncdets or ntdets == 0, capacity < ntdets or max_steps
+ * outside 1..ASCI_LOOP_MAX_STEPS.
+ */
+int asci_loop(const asci_det *dets, const double *coeffs, size_t ndets, const asci_ints *ints,
+              const asci_loop_opts *opts, asci_det *out_dets, double *out_coeffs,
+              size_t capacity, size_t *out_n, double *energy, asci_loop_stats *stats,
+              void *cuda_stream);
 
 #ifdef __cplusplus
 }

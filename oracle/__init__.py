@@ -244,27 +244,38 @@ def key_order(A, B) -> np.ndarray:
     return np.lexsort((_u64(A), _u64(B)))
 
 
-def asci_step(ints: Ints, A, B, c, E0: float, ncdets: int, ntdets: int, eps: float = 0.0):
-    """One pass of Algorithm 1 from the wavefunction (A, B, c) with energy E0.
-
-    The search (Algorithm 2) runs with the ncdets core; the next space holds
-    the ntdets determinants of largest magnitude among the current ones
-    (valued by their coefficient c_i) and the candidates (valued by their score
-    S_i, Eq. 1), ties by key ascending; its ground state is the lowest
-    eigenpair of H restricted to it.  Returns (A', B', c', E', changed) with
-    the determinants in key order and c' normalised, largest |c'| positive;
-    ``changed`` tells whether the determinant set differs from (A, B).
-    """
+def asci_merge(ints: Ints, A, B, c, E0: float, ncdets: int, ntdets: int, eps: float = 0.0):
+    """Steps 2-3 of Algorithm 1 before the diagonalisation: the search
+    (Algorithm 2, ncdets core), then the ntdets determinants of largest
+    magnitude among the current ones (valued by c_i) and the candidates
+    (valued by their score S_i, Eq. 1), ties by key ascending.  Returns
+    (A', B', values, kept_min, dropped_max, changed): the kept determinants in
+    key order with their values, the smallest kept and the largest dropped
+    magnitude (0 when nothing is dropped), and whether the set differs from
+    (A, B)."""
     A, B, c = _u64(A), _u64(B), _f64(c)
     res = search(ints, A, B, c, E0, ncdets, eps)
     ua = np.concatenate([A, res.a])
     ub = np.concatenate([B, res.b])
     val = np.concatenate([c, res.score])
     idx = topn(ua, ub, val, ntdets)
-    na, nb = ua[idx], ub[idx]
+    mag = np.abs(val)
+    keep = np.zeros(len(val), dtype=bool)
+    keep[idx] = True
+    kept_min = float(mag[keep].min()) if keep.any() else 0.0
+    dropped_max = float(mag[~keep].max()) if (~keep).any() else 0.0
+    na, nb, v = ua[idx], ub[idx], val[idx]
     o = key_order(na, nb)
-    na, nb = na[o], nb[o]
-    changed = len(na) != len(A) or bool(np.any(idx >= len(A)))
+    changed = len(idx) != len(A) or bool(np.any(idx >= len(A)))
+    return na[o], nb[o], v[o], kept_min, dropped_max, changed
+
+
+def asci_step(ints: Ints, A, B, c, E0: float, ncdets: int, ntdets: int, eps: float = 0.0):
+    """One pass of Algorithm 1 from the wavefunction (A, B, c) with energy E0:
+    asci_merge, then the ground state of the new space, the lowest eigenpair
+    of H restricted to it.  Returns (A', B', c', E', changed) with the
+    determinants in key order and c' normalised, largest |c'| positive."""
+    na, nb, _, _, _, changed = asci_merge(ints, A, B, c, E0, ncdets, ntdets, eps)
     E, v = ground_state(ints, na, nb)
     return na, nb, v, E, changed
 

@@ -20,7 +20,8 @@ import numpy as np
 __all__ = ["load", "lib_path", "launch_count", "search", "excitations", "diagonal", "sort_accumulate",
            "select_topn", "SearchStats", "AsciError", "FP64", "FP32_INT_FP64_ACC",
            "FP32_INT_COMP_ACC", "shard_assign", "gather_candidates", "sharded_search",
-           "search_many", "tune_streams"]
+           "search_many", "tune_streams", "hamiltonian", "spmv", "davidson", "asci_loop",
+           "LoopStats"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "lib", "libasci.so")
@@ -64,6 +65,50 @@ class _Stats(ct.Structure):
                 ("max_batch", ct.c_uint64), ("ncore", ct.c_uint64), ("max_level", ct.c_uint64),
                 ("tile_launches", ct.c_uint64), ("tile_records", ct.c_uint64),
                 ("oversized_records", ct.c_uint64), ("t_stage", ct.c_double * 8)]
+
+
+class _DavOpts(ct.Structure):
+    _fields_ = [("max_subspace", ct.c_int32), ("max_iter", ct.c_int32), ("tol", ct.c_double)]
+
+
+_MAX_STEPS = 64
+
+
+class _LoopOpts(ct.Structure):
+    _fields_ = [("ncdets", ct.c_uint64), ("ntdets", ct.c_uint64), ("max_steps", ct.c_int32),
+                ("etol", ct.c_double), ("search", _Opts), ("davidson", _DavOpts)]
+
+
+class _LoopStats(ct.Structure):
+    _fields_ = [("steps", ct.c_int32), ("start_energy", ct.c_double),
+                ("energy", ct.c_double * _MAX_STEPS), ("ndets", ct.c_uint64 * _MAX_STEPS),
+                ("new_dets", ct.c_uint64 * _MAX_STEPS), ("nnz", ct.c_uint64 * _MAX_STEPS),
+                ("davidson_iters", ct.c_int32 * _MAX_STEPS),
+                ("t_search", ct.c_double * _MAX_STEPS),
+                ("t_hamiltonian", ct.c_double * _MAX_STEPS),
+                ("t_davidson", ct.c_double * _MAX_STEPS)]
+
+
+@dataclass
+class LoopStats:
+    """Per-step record of asci_loop(): energies, sizes, H nonzeros, Davidson
+    products and device milliseconds of the search, the build and Davidson."""
+    start_energy: float
+    energy: list
+    ndets: list
+    new_dets: list
+    nnz: list
+    davidson_iters: list
+    t_search_ms: list
+    t_hamiltonian_ms: list
+    t_davidson_ms: list
+
+    @classmethod
+    def _from(cls, s: _LoopStats):
+        k = s.steps
+        return cls(s.start_energy, list(s.energy[:k]), list(s.ndets[:k]), list(s.new_dets[:k]),
+                   list(s.nnz[:k]), list(s.davidson_iters[:k]), list(s.t_search[:k]),
+                   list(s.t_hamiltonian[:k]), list(s.t_davidson[:k]))
 
 
 @dataclass
@@ -121,6 +166,17 @@ def load():
     lib.asci_shard_assign.argtypes = [vp, sz, ct.c_int32, vp, vp]
     lib.asci_search_many.argtypes = [vp, sz, ct.POINTER(_Opts), ct.c_int32]
     lib.asci_default_opts.argtypes = [ct.POINTER(_Opts)]
+    lib.asci_hamiltonian.restype = ct.c_int
+    lib.asci_hamiltonian.argtypes = [vp, sz, ct.POINTER(_Ints), vp, vp, vp, sz, szp, vp]
+    lib.asci_spmv.restype = ct.c_int
+    lib.asci_spmv.argtypes = [vp, vp, vp, sz, vp, vp, vp]
+    lib.asci_davidson.restype = ct.c_int
+    lib.asci_davidson.argtypes = [vp, vp, vp, sz, vp, ct.POINTER(_DavOpts), vp, vp, vp, vp, vp]
+    lib.asci_default_davidson_opts.argtypes = [ct.POINTER(_DavOpts)]
+    lib.asci_default_loop_opts.argtypes = [ct.POINTER(_LoopOpts)]
+    lib.asci_loop.restype = ct.c_int
+    lib.asci_loop.argtypes = [vp, vp, sz, ct.POINTER(_Ints), ct.POINTER(_LoopOpts), vp, vp, sz,
+                              szp, vp, ct.POINTER(_LoopStats), vp]
     lib.asci_version.restype = ct.c_char_p
     lib.asci_strerror.restype = ct.c_char_p
     lib.asci_strerror.argtypes = [ct.c_int]
@@ -478,3 +534,95 @@ def select_topn(keys, scores, N: int, stream=None):
     _check(lib.asci_select_topn(kb.ptr, sb.ptr, n, int(N), ok.data_ptr(), os_.data_ptr(),
                                 ct.byref(n_out), _stream_ptr(stream, True)), "asci_select_topn")
     return ok[:n_out.value], os_[:n_out.value]
+
+
+# ------------------------- the variational step ----------------------------
+
+def hamiltonian(dets, h1, eri, ecore, stream=None):
+    """H restricted to the determinant list (Sec. 2.3), CSR on the device:
+    (row_ptr int64[n+1], col int32[nnz], val float64[nnz]).  Two calls of
+    asci_hamiltonian: the size query, then the fill."""
+    torch = _torch()
+    lib = load()
+    keep = []
+    db = _dets_buf(dets)
+    keep.append(db)
+    ints, _ = _ints(h1, eri, ecore, keep)
+    n = int(db.obj.shape[0])
+    rp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    nnz = ct.c_size_t(0)
+    sp = _stream_ptr(stream, True)
+    _check(lib.asci_hamiltonian(db.ptr, n, ct.byref(ints), rp.data_ptr(), None, None, 0,
+                                ct.byref(nnz), sp), "asci_hamiltonian")
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device="cuda")
+    val = torch.empty(max(nnz.value, 1), dtype=torch.float64, device="cuda")
+    _check(lib.asci_hamiltonian(db.ptr, n, ct.byref(ints), rp.data_ptr(), col.data_ptr(),
+                                val.data_ptr(), nnz.value, ct.byref(nnz), sp), "asci_hamiltonian")
+    return rp, col[:nnz.value], val[:nnz.value]
+
+
+def spmv(H, x, stream=None):
+    """y = H x for H = (row_ptr, col, val) from hamiltonian() (device)."""
+    torch = _torch()
+    lib = load()
+    rp, col, val = H
+    n = rp.shape[0] - 1
+    xb = _as_buf(x, np.float64, "float64")
+    if not xb.device:
+        raise ValueError("spmv() takes CUDA tensors")
+    y = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    _check(lib.asci_spmv(rp.data_ptr(), col.data_ptr(), val.data_ptr(), n, xb.ptr, y.data_ptr(),
+                         _stream_ptr(stream, True)), "asci_spmv")
+    return y[:n]
+
+
+def davidson(H, guess=None, *, max_subspace: int = 24, max_iter: int = 300, tol: float = 1e-8,
+             stream=None):
+    """Lowest eigenpair of H = (row_ptr, col, val) by Davidson (Alg. 5).
+    Returns (energy, vector (device), products with H, residual norm)."""
+    torch = _torch()
+    lib = load()
+    rp, col, val = H
+    n = rp.shape[0] - 1
+    gp = None
+    if guess is not None:
+        gb = _as_buf(guess, np.float64, "float64")
+        if not gb.device:
+            raise ValueError("davidson() takes a CUDA guess")
+        guess, gp = gb.obj, gb.ptr
+    o = _DavOpts(int(max_subspace), int(max_iter), float(tol))
+    vec = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    e, it, res = ct.c_double(0.0), ct.c_int32(0), ct.c_double(0.0)
+    _check(lib.asci_davidson(rp.data_ptr(), col.data_ptr(), val.data_ptr(), n, gp, ct.byref(o),
+                             ct.byref(e), vec.data_ptr(), ct.byref(it), ct.byref(res),
+                             _stream_ptr(stream, True)), "asci_davidson")
+    return e.value, vec[:n], it.value, res.value
+
+
+def asci_loop(dets, coeffs, h1, eri, ecore, *, ncdets: int, ntdets: int, max_steps: int = 8,
+              etol: float = 1e-6, eps: float = 0.0, precision: int = FP64,
+              max_batch_pairs: int = 0, max_subspace: int = 24, max_iter: int = 300,
+              tol: float = 1e-8, stream=None):
+    """The ASCI loop (Alg. 1): search, keep the ntdets largest of |c| and |S|,
+    build H on that space, Davidson; repeat.  Returns (dets, coeffs, energy,
+    LoopStats); outputs live where ``dets`` lives."""
+    lib = load()
+    keep = []
+    db = _dets_buf(dets)
+    cb = _as_buf(coeffs, np.float64, "float64")
+    keep += [db, cb]
+    ints, _ = _ints(h1, eri, ecore, keep)
+    o = _LoopOpts()
+    lib.asci_default_loop_opts(ct.byref(o))
+    o.ncdets, o.ntdets, o.max_steps, o.etol = int(ncdets), int(ntdets), int(max_steps), float(etol)
+    o.search = _opts(lib, eps, precision, max_batch_pairs, 0, False)
+    o.davidson = _DavOpts(int(max_subspace), int(max_iter), float(tol))
+    cap = int(ntdets)
+    od, odp = _out(max(cap, 1), np.uint64, db.device, 2)
+    oc, ocp = _out(max(cap, 1), np.float64, db.device)
+    n_out, energy, st = ct.c_size_t(0), ct.c_double(0.0), _LoopStats()
+    _check(lib.asci_loop(db.ptr, cb.ptr, int(db.obj.shape[0]), ct.byref(ints), ct.byref(o), odp,
+                         ocp, cap, ct.byref(n_out), ct.byref(energy), ct.byref(st),
+                         _stream_ptr(stream, db.device)), "asci_loop")
+    m = n_out.value
+    return od[:m], oc[:m], energy.value, LoopStats._from(st)

@@ -158,6 +158,34 @@ int finish_out(T *user, const T *dev, size_t count, cudaStream_t s) {
   return ASCI_OK;
 }
 
+// Device time between start() and stop() on one stream, added to *acc in
+// milliseconds (stop() waits for the stream to reach the end event).
+struct StageTimer {
+  cudaStream_t s;
+  cudaEvent_t ev[2];
+  bool ok = false;
+  explicit StageTimer(cudaStream_t st) : s(st) {
+    ok = cudaEventCreate(&ev[0]) == cudaSuccess && cudaEventCreate(&ev[1]) == cudaSuccess;
+  }
+  ~StageTimer() {
+    if (ok) {
+      cudaEventDestroy(ev[0]);
+      cudaEventDestroy(ev[1]);
+    }
+  }
+  void start() {
+    if (ok) cudaEventRecord(ev[0], s);
+  }
+  void stop(double *acc) {
+    if (!ok) return;
+    cudaEventRecord(ev[1], s);
+    cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    *acc += ms;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // determinants and keys
 // ---------------------------------------------------------------------------

@@ -378,31 +378,6 @@ int shard_items(uint64_t **items, uint64_t **items_alt, const uint64_t *Wexcl, u
   return ASCI_OK;
 }
 
-struct StageTimer {
-  cudaStream_t s;
-  cudaEvent_t ev[2];
-  bool ok = false;
-  explicit StageTimer(cudaStream_t st) : s(st) {
-    ok = cudaEventCreate(&ev[0]) == cudaSuccess && cudaEventCreate(&ev[1]) == cudaSuccess;
-  }
-  ~StageTimer() {
-    if (ok) {
-      cudaEventDestroy(ev[0]);
-      cudaEventDestroy(ev[1]);
-    }
-  }
-  void start() {
-    if (ok) cudaEventRecord(ev[0], s);
-  }
-  void stop(double *acc) {
-    if (!ok) return;
-    cudaEventRecord(ev[1], s);
-    cudaEventSynchronize(ev[1]);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ev[0], ev[1]);
-    *acc += ms;
-  }
-};
 
 int bits_for(uint32_t v) {
   int b = 0;
