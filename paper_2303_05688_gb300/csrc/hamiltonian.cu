@@ -197,51 +197,59 @@ HamGeom ham_geom(uint32_t n) {
 
 // ------------------------------ products -----------------------------------
 
-__global__ void k_spmv(const int64_t *rp, const int32_t *col, const double *val, uint32_t n,
-                       const double *x, double *y) {
+__global__ void k_spmv(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                       const double *__restrict__ val, uint32_t n, const double *__restrict__ x,
+                       double *__restrict__ y) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
     const int64_t b = rp[r], e = rp[r + 1];
     double s = 0.0;
-    for (int64_t k = b + lane; k < e; k += 32) s = fma(val[k], __ldg(x + col[k]), s);
+#pragma unroll 4
+    for (int64_t k = b + lane; k < e; k += 32) s = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) y[r] = s;
   }
 }
 
-// part[k * gridDim.x + block] = partial sum of V_k . b over the block's slice
-// (V_k = V + k * ld), for k < m.
-__global__ void __launch_bounds__(kDotThreads) k_dots(const double *V, size_t ld, int m,
-                                                      const double *b, size_t n, double *part) {
+// out[k * s1] (and out2[k * s2] when given) = V_k . b for k = blockIdx.y
+// (V_k = V + k * ld).  Each block writes the partial sum of its slice; the
+// last block of a vector to finish (a ticket counter, reset by that block)
+// adds the partials in block order, so the result does not depend on which
+// block finishes last.
+__global__ void __launch_bounds__(kDotThreads) k_dots(const double *V, size_t ld,
+                                                      const double *b, size_t n, double *part,
+                                                      unsigned *ticket, double *out, int s1,
+                                                      double *out2, int s2) {
   __shared__ double red[kDotThreads / 32];
+  __shared__ bool last;
   const size_t per = (n + gridDim.x - 1) / gridDim.x;
   const size_t lo = (size_t)blockIdx.x * per, hi = min(n, lo + per);
-  for (int k = 0; k < m; ++k) {
-    const double *v = V + (size_t)k * ld;
-    double s = 0.0;
-    for (size_t i = lo + threadIdx.x; i < hi; i += kDotThreads) s = fma(v[i], b[i], s);
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31u) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < kDotThreads / 32; ++w) t += red[w];
-      part[(size_t)k * gridDim.x + blockIdx.x] = t;
-    }
-    __syncthreads();
-  }
-}
-
-// out[k * s1] (and out2[k * s2] when given) = sum over blocks of part[k], in
-// block order.
-__global__ void k_dots_final(const double *part, int m, int nblk, double *out, int s1,
-                             double *out2, int s2) {
-  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+  const int k = blockIdx.y;
+  const double *v = V + (size_t)k * ld;
+  double s = 0.0;
+  for (size_t i = lo + threadIdx.x; i < hi; i += kDotThreads) s = fma(v[i], b[i], s);
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31u) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int g = 0; g < nblk; ++g) t += part[(size_t)k * nblk + g];
+    for (int w = 0; w < kDotThreads / 32; ++w) t += red[w];
+    part[(size_t)k * gridDim.x + blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(ticket + k, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x >= 32) return;
+  __threadfence();
+  const volatile double *pk = part + (size_t)k * gridDim.x;
+  double t = 0.0;
+  for (unsigned g = threadIdx.x; g < gridDim.x; g += 32) t += pk[g];
+  for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (threadIdx.x == 0) {
     out[(size_t)k * s1] = t;
     if (out2) out2[(size_t)k * s2] = t;
+    ticket[k] = 0u;
   }
 }
 
@@ -256,6 +264,24 @@ __global__ void k_combine(const double *V, size_t ld, int m, const double *coef,
     double s = base ? base[i] * sb : 0.0;
     for (int k = 0; k < m; ++k) s = fma(cf[k], V[(size_t)k * ld + i], s);
     out[i] = s;
+  }
+}
+
+// x = V c and wx = W c in one pass (c = the lowest Ritz vector's coefficients).
+__global__ void k_ritz(const double *V, const double *W, size_t ld, int m, const double *coef,
+                       size_t n, double *x, double *wx) {
+  __shared__ double cf[kMaxSub];
+  for (int k = threadIdx.x; k < m; k += blockDim.x) cf[k] = coef[k];
+  __syncthreads();
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < m; ++k) {
+      a = fma(cf[k], V[(size_t)k * ld + i], a);
+      b = fma(cf[k], W[(size_t)k * ld + i], b);
+    }
+    x[i] = a;
+    wx[i] = b;
   }
 }
 
@@ -297,10 +323,15 @@ __global__ void k_normalize(double *v, size_t n, const double *norm2) {
 // eigenvector matrix), then to the rows.  Sweeps end when the off-diagonal
 // norm falls below 1e-15 of the diagonal's, or after 60.  out: theta[r] in
 // ascending order (ties by index), eigenvector r in Ct[r * kMaxSub + k].
+// Warm start (`warm`: the basis grew by one vector since the last call, whose
+// m - 1 eigenvectors Ct still holds): the rotations start from those
+// eigenvectors, P = diag(old eigenvectors, 1), so that P^T Hs P is diagonal
+// but for its last row and column and two or three sweeps finish it.
 constexpr int kEigThreads = 256;
+constexpr int kEigPer = (kMaxSub * kMaxSub + kEigThreads - 1) / kEigThreads;
 
 __global__ void __launch_bounds__(kEigThreads) k_small_eig(const double *Hs, int ld, int m,
-                                                           double *theta, double *Ct) {
+                                                           bool warm, double *theta, double *Ct) {
   __shared__ double A[kMaxSub][kMaxSub + 1];
   __shared__ double Q[kMaxSub][kMaxSub + 1];
   __shared__ double rc[kMaxSub / 2], rs[kMaxSub / 2];
@@ -312,10 +343,37 @@ __global__ void __launch_bounds__(kEigThreads) k_small_eig(const double *Hs, int
   const int half = M / 2;
   for (int e = tid; e < m * m; e += kEigThreads) {
     const int i = e / m, k = e - (e / m) * m;
-    A[i][k] = Hs[(size_t)i * ld + k];
-    Q[i][k] = (i == k) ? 1.0 : 0.0;
+    double q = (i == k) ? 1.0 : 0.0;
+    if (warm && i < m - 1 && k < m - 1) q = Ct[(size_t)k * kMaxSub + i];
+    Q[i][k] = q;
+    if (!warm) A[i][k] = Hs[(size_t)i * ld + k];
   }
   __syncthreads();
+  if (warm) {  // A = P^T Hs P, through A = Hs P and registers
+    for (int e = tid; e < m * m; e += kEigThreads) {
+      const int i = e / m, j = e - (e / m) * m;
+      double t = 0.0;
+      for (int l = 0; l < m; ++l) t = fma(Hs[(size_t)i * ld + l], Q[l][j], t);
+      A[i][j] = t;
+    }
+    __syncthreads();
+    double keep[kEigPer];
+    for (int u = 0; u < kEigPer; ++u) {
+      const int e = tid + u * kEigThreads;
+      double t = 0.0;
+      if (e < m * m) {
+        const int i = e / m, j = e - (e / m) * m;
+        for (int k = 0; k < m; ++k) t = fma(Q[k][i], A[k][j], t);
+      }
+      keep[u] = t;
+    }
+    __syncthreads();
+    for (int u = 0; u < kEigPer; ++u) {
+      const int e = tid + u * kEigThreads;
+      if (e < m * m) A[e / m][e - (e / m) * m] = keep[u];
+    }
+    __syncthreads();
+  }
   for (int sweep = 0; sweep < 60 && m > 1; ++sweep) {
     double off = 0.0, dg = 0.0;
     for (int e = tid; e < m * m; e += kEigThreads) {
@@ -580,12 +638,24 @@ static int spmv(const Csr &H, const double *x, double *y, cudaStream_t s) {
 }
 
 // out[k * s1] (and out2[k * s2]) = V_k . b for k < m
-static int dots(const double *V, size_t ld, int m, const double *b, size_t n, double *part,
-                double *out, int s1, double *out2, int s2, cudaStream_t s) {
+// Scratch of the dot products: partial sums and the per-vector tickets (zero
+// between calls).
+struct DotScratch {
+  double *part;
+  unsigned *ticket;
+};
+
+static int dot_scratch(DotScratch *d, Arena &arena) {
+  ASCI_TRY(arena.alloc(&d->part, (size_t)kMaxSub * kDotBlocks));
+  ASCI_TRY(arena.alloc(&d->ticket, kMaxSub));
+  ASCI_TRY_CUDA(cudaMemsetAsync(d->ticket, 0, kMaxSub * sizeof(unsigned), arena.stream()));
+  return ASCI_OK;
+}
+
+static int dots(const double *V, size_t ld, int m, const double *b, size_t n,
+                const DotScratch &d, double *out, int s1, double *out2, int s2, cudaStream_t s) {
   const int nblk = (int)std::min<size_t>(kDotBlocks, std::max<size_t>(1, (n + 1023) / 1024));
-  k_dots<<<nblk, kDotThreads, 0, s>>>(V, ld, m, b, n, part);
-  ASCI_CHECK_LAUNCH();
-  k_dots_final<<<1, 64, 0, s>>>(part, m, nblk, out, s1, out2, s2);
+  k_dots<<<dim3(nblk, m), kDotThreads, 0, s>>>(V, ld, b, n, d.part, d.ticket, out, s1, out2, s2);
   ASCI_CHECK_LAUNCH();
   return ASCI_OK;
 }
@@ -605,7 +675,8 @@ static int davidson(const Csr &H, const double *diag, const double *guess,
   const int mmax = (int)std::min<size_t>((size_t)o.max_subspace, n);
   const unsigned gb = blocks_for(n, 256);
   const int keep = std::min(kKeep, mmax - 1);  // Ritz vectors kept at a restart
-  double *V, *W, *Hs, *Ct, *th, *h, *part, *sc, *x, *wx, *r, *t, *TV = nullptr, *TW = nullptr;
+  double *V, *W, *Hs, *Ct, *th, *h, *sc, *x, *wx, *r, *t, *TV = nullptr, *TW = nullptr;
+  DotScratch part;
   ASCI_TRY(arena.alloc(&V, (size_t)std::max(mmax, 1) * n));
   ASCI_TRY(arena.alloc(&W, (size_t)std::max(mmax, 1) * n));
   if (keep > 0) {
@@ -616,7 +687,7 @@ static int davidson(const Csr &H, const double *diag, const double *guess,
   ASCI_TRY(arena.alloc(&Ct, (size_t)kMaxSub * kMaxSub));
   ASCI_TRY(arena.alloc(&th, kMaxSub));
   ASCI_TRY(arena.alloc(&h, kMaxSub));
-  ASCI_TRY(arena.alloc(&part, (size_t)kMaxSub * kDotBlocks));
+  ASCI_TRY(dot_scratch(&part, arena));
   ASCI_TRY(arena.alloc(&sc, 8));  // scratch, |r|^2, |t|^2, sign
   ASCI_TRY(arena.alloc(&x, n));
   ASCI_TRY(arena.alloc(&wx, n));
@@ -643,6 +714,7 @@ static int davidson(const Csr &H, const double *diag, const double *guess,
   int m = 1;         // basis vectors in V
   int have_w = 0;    // products already in W
   bool first = true;
+  int prev_m = -1;  // dimension of the last subspace solve (-1: none to warm-start from)
   double theta = 0.0, rn = 0.0;
   for (;;) {
     // products of the new basis vectors and their column of V^T H V
@@ -652,18 +724,41 @@ static int davidson(const Csr &H, const double *diag, const double *guess,
       ASCI_TRY(dots(V, n, have_w + 1, W + (size_t)have_w * n, n, part, Hs + have_w, kMaxSub,
                     Hs + (size_t)have_w * kMaxSub, 1, s));
     }
-    k_small_eig<<<1, kEigThreads, 0, s>>>(Hs, kMaxSub, m, th, Ct);
+    k_small_eig<<<1, kEigThreads, 0, s>>>(Hs, kMaxSub, m, m == prev_m + 1, th, Ct);
+    prev_m = m;
     ASCI_CHECK_LAUNCH();
-    k_combine<<<gb, 256, 0, s>>>(V, n, m, Ct, 1.0, nullptr, 0.0, n, x);
-    ASCI_CHECK_LAUNCH();
-    k_combine<<<gb, 256, 0, s>>>(W, n, m, Ct, 1.0, nullptr, 0.0, n, wx);
+    k_ritz<<<gb, 256, 0, s>>>(V, W, n, m, Ct, n, x, wx);
     ASCI_CHECK_LAUNCH();
     k_residual<<<gb, 256, 0, s>>>(wx, x, th, diag, n, !first, r, t);
     ASCI_CHECK_LAUNCH();
     ASCI_TRY(dots(r, n, 1, r, n, part, sc + 1, 1, nullptr, 0, s));
-    double hs[2];
+    // the next expansion vector is prepared before the convergence test is
+    // read back, so that one host round trip serves both; when the test
+    // stops the iteration, that work is simply dropped
+    const bool restart = m == mmax && (size_t)m < n;
+    if (restart) {  // thick restart: the `keep` lowest Ritz vectors and their products
+      for (int k = 0; k < keep; ++k) {
+        k_ritz<<<gb, 256, 0, s>>>(V, W, n, m, Ct + (size_t)k * kMaxSub, n, TV + (size_t)k * n,
+                                  TW + (size_t)k * n);
+        ASCI_CHECK_LAUNCH();
+      }
+      ASCI_TRY_CUDA(cudaMemcpyAsync(V, TV, (size_t)keep * n * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s));
+      ASCI_TRY_CUDA(cudaMemcpyAsync(W, TW, (size_t)keep * n * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s));
+      k_restart_hs<<<1, 256, 0, s>>>(Hs, th, keep);
+      ASCI_CHECK_LAUNCH();
+    }
+    const int mb = restart ? keep : m;  // basis the correction is orthogonalised against
+    for (int pass = 0; pass < 2; ++pass) {  // two passes of classical Gram-Schmidt
+      ASCI_TRY(dots(V, n, mb, t, n, part, h, 1, nullptr, 0, s));
+      k_combine<<<gb, 256, 0, s>>>(V, n, mb, h, -1.0, t, 1.0, n, t);
+      ASCI_CHECK_LAUNCH();
+    }
+    ASCI_TRY(dots(t, n, 1, t, n, part, sc + 2, 1, nullptr, 0, s));
+    double hs[3];
     ASCI_TRY_CUDA(cudaMemcpyAsync(&hs[0], th, sizeof(double), cudaMemcpyDeviceToHost, s));
-    ASCI_TRY_CUDA(cudaMemcpyAsync(&hs[1], sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&hs[1], sc + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     ASCI_TRY_CUDA(cudaStreamSynchronize(s));
     theta = hs[0];
     rn = std::sqrt(std::max(hs[1], 0.0));
@@ -676,35 +771,12 @@ static int davidson(const Csr &H, const double *diag, const double *guess,
       break;
     }
     first = false;
-    if (m == mmax) {  // thick restart: the `keep` lowest Ritz vectors and their products
-      for (int k = 0; k < keep; ++k) {
-        k_combine<<<gb, 256, 0, s>>>(V, n, m, Ct + (size_t)k * kMaxSub, 1.0, nullptr, 0.0, n,
-                                     TV + (size_t)k * n);
-        ASCI_CHECK_LAUNCH();
-        k_combine<<<gb, 256, 0, s>>>(W, n, m, Ct + (size_t)k * kMaxSub, 1.0, nullptr, 0.0, n,
-                                     TW + (size_t)k * n);
-        ASCI_CHECK_LAUNCH();
-      }
-      ASCI_TRY_CUDA(cudaMemcpyAsync(V, TV, (size_t)keep * n * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, s));
-      ASCI_TRY_CUDA(cudaMemcpyAsync(W, TW, (size_t)keep * n * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, s));
-      k_restart_hs<<<1, 256, 0, s>>>(Hs, th, keep);
-      ASCI_CHECK_LAUNCH();
+    if (restart) {
       m = keep;
       have_w = keep;
+      prev_m = -1;
     }
-    // two passes of classical Gram-Schmidt against V, then normalise
-    for (int pass = 0; pass < 2; ++pass) {
-      ASCI_TRY(dots(V, n, m, t, n, part, h, 1, nullptr, 0, s));
-      k_combine<<<gb, 256, 0, s>>>(V, n, m, h, -1.0, t, 1.0, n, t);
-      ASCI_CHECK_LAUNCH();
-    }
-    ASCI_TRY(dots(t, n, 1, t, n, part, sc + 2, 1, nullptr, 0, s));
-    double tn2 = 0.0;
-    ASCI_TRY_CUDA(cudaMemcpyAsync(&tn2, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
-    ASCI_TRY_CUDA(cudaStreamSynchronize(s));
-    if (!(tn2 > 1e-28)) {  // the correction lies in the basis: nothing left to add
+    if (!(hs[2] > 1e-28)) {  // the correction lies in the basis: nothing left to add
       res->converged = rn <= o.tol;
       break;
     }
@@ -866,8 +938,9 @@ static int loop_impl(const asci_det *dets_in, const double *coeffs_in, size_t nd
   ASCI_TRY(arena.alloc(&c_alt, nd));
   ASCI_TRY_CUDA(cudaMemcpyAsync(c, coeffs, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
   ASCI_TRY(radix_sort_u64_f64(&keys, &keys_alt, &c, &c_alt, nd, 0, 64, arena));
-  double *part, *sc;
-  ASCI_TRY(arena.alloc(&part, kDotBlocks));
+  double *sc;
+  DotScratch part;
+  ASCI_TRY(dot_scratch(&part, arena));
   ASCI_TRY(arena.alloc(&sc, 2));
   // E_0 = c.Hc / c.c on the start
   double E = 0.0;

@@ -291,16 +291,17 @@ def test_asci_loop_whole_run_equals_oracle(torch_cuda, asci, oracle_mod):
     gA, gB = to_u64_pairs(d)
     assert [int(x) for x in st.ndets] == [h[0] for h in hist]
     assert np.allclose(st.energy, [h[1] for h in hist], rtol=0, atol=1e-9)
-    # energies agree at every step; the two runs diagonalise with different
-    # solvers, so candidates whose |S| lie within ~1e-9 of each other at a
-    # cutoff may swap, and the runs drift apart in low-weight determinants only
-    got, want = set(zip(gB.tolist(), gA.tolist())), set(zip(pb.tolist(), pa.tolist()))
-    assert len(got & want) >= 0.9 * len(want)
-    gcn = gc.cpu().numpy()
-    thresh = np.median(np.abs(gcn))
-    for k, cc in zip(zip(gB.tolist(), gA.tolist()), gcn):
-        if k not in want:
-            assert abs(cc) < thresh
+    # energies agree at every step.  With n_alpha = n_beta the ground state is
+    # spin-symmetric, so a determinant and its alpha-beta swap carry equal |c|
+    # and |S|; where the cutoff falls between such a pair, the key tie-break
+    # meets values that the two runs round differently, and the runs may keep
+    # different partners.  Compared modulo that swap, the final spaces agree.
+    from collections import Counter
+
+    def canon(a, b):
+        return Counter(min((int(x), int(y)), (int(y), int(x))) for x, y in zip(a, b))
+    cg, cp = canon(gA, gB), canon(pa, pb)
+    assert sum((cg & cp).values()) >= 0.99 * len(pa)
     assert abs(gE - pE) < 1e-9
     assert all(t >= 0 for t in st.t_search_ms + st.t_hamiltonian_ms + st.t_davidson_ms)
     assert st.new_dets[0] == st.ndets[0] - 1
