@@ -120,50 +120,71 @@ __device__ double offdiag_element(const DevInts &I, uint32_t ai, uint32_t bi, ui
   return double_parity(ket, h1, h2, p1, p2) ? -v : v;
 }
 
-// Count (kFill false) or store (kFill true) the elements of rows
-// [blockIdx.x * 256, +256) in columns [blockIdx.y * chunk, +chunk).  The
-// diagonal element is always stored; off-diagonal ones when nonzero.
+// The build works on determinants in key order (beta word high), so that
+// every beta string's determinants form one contiguous group.  Two
+// determinants are within two excitations iff
+//   popc(alpha_i ^ alpha_j) + popc(beta_i ^ beta_j) <= 4,
+// so a row only has to visit the groups whose beta string is within two
+// excitations of its own (the group graph, built once per list by a tiled
+// double loop over the G group strings), and inside such a group only the
+// alpha test remains, with the threshold 4 - popc(beta_i ^ beta_j).  A warp
+// takes a row and walks its neighbour groups in ascending order, 32 columns
+// at a time; a ballot places the hits, so each row's columns come out
+// ascending.  A counting pass gives the row lengths, a scan the row
+// pointers, and the filling pass writes (never past a row's counted end).
+
+// head[i] = 1 where a new beta string starts (keys sorted)
+__global__ void k_beta_heads(const uint64_t *keys, uint32_t n, uint32_t *head) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    head[i] = (i == 0 || key_beta(keys[i]) != key_beta(keys[i - 1])) ? 1u : 0u;
+}
+
+// group of each row; start and beta string of each group (gid: exclusive scan of head)
+__global__ void k_beta_groups(const uint64_t *keys, uint32_t n, const uint32_t *head,
+                              const uint32_t *gid, uint32_t *of_row, uint32_t *gstart,
+                              uint32_t *gbeta) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t g = gid[i] + head[i] - 1u;
+    of_row[i] = g;
+    if (head[i]) {
+      gstart[g] = i;
+      gbeta[g] = key_beta(keys[i]);
+    }
+    if (i == n - 1) gstart[g + 1] = n;  // end of the last group
+  }
+}
+
+// Group graph: count (kFill false) or list (kFill true) the groups g2 with
+// popc(beta_g1 ^ beta_g2) <= 4, for the groups g1 = [blockIdx.x * 256, +256)
+// (one per thread) against the groups [blockIdx.y * chunk, +chunk) staged in
+// shared memory.
 template <bool kFill>
-__global__ void __launch_bounds__(kRowThreads) k_ham_pass(DevInts I, const uint64_t *keys,
-                                                          uint32_t n, uint32_t chunk,
-                                                          uint32_t nchunks, const double *diag,
-                                                          uint64_t *cnt_off, int32_t *col,
-                                                          double *val) {
-  __shared__ uint64_t sk[kColStage];
-  const uint32_t row = blockIdx.x * kRowThreads + threadIdx.x;
-  const bool live = row < n;
-  const uint64_t ki = live ? keys[row] : 0ull;
-  const uint32_t ai = key_alpha(ki), bi = key_beta(ki);
+__global__ void __launch_bounds__(kRowThreads) k_beta_pairs(const uint32_t *gbeta, uint32_t G,
+                                                            uint32_t chunk, uint32_t nchunks,
+                                                            uint64_t *cnt_off, uint32_t *nbr) {
+  __shared__ uint32_t sb[kColStage];
+  const uint32_t g1 = blockIdx.x * kRowThreads + threadIdx.x;
+  const bool live = g1 < G;
+  const uint32_t b1 = live ? gbeta[g1] : 0u;
   const uint32_t c0 = blockIdx.y * chunk;
-  const uint32_t c1 = min(n, c0 + chunk);
-  const size_t slot = (size_t)row * nchunks + blockIdx.y;
+  const uint32_t c1 = min(G, c0 + chunk);
+  const size_t slot = (size_t)g1 * nchunks + blockIdx.y;
   uint64_t cnt = 0, pos = 0, end = 0;
-  if (kFill && live) {  // this (row, slice)'s range; writes never leave it
+  if (kFill && live) {
     pos = cnt_off[slot];
     end = cnt_off[slot + 1];
   }
   for (uint32_t s = c0; s < c1; s += kColStage) {
     const uint32_t m = min((uint32_t)kColStage, c1 - s);
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < m; t += kRowThreads) sk[t] = keys[s + t];
+    for (uint32_t t = threadIdx.x; t < m; t += kRowThreads) sb[t] = gbeta[s + t];
     __syncthreads();
     if (!live) continue;
 #pragma unroll 4
     for (uint32_t t = 0; t < m; ++t) {
-      const uint64_t x = ki ^ sk[t];
-      if (__popcll(x) > 4) continue;
-      double v;
-      if (x == 0ull) {
-        v = diag[row];
-      } else {
-        v = offdiag_element(I, ai, bi, key_alpha(sk[t]), key_beta(sk[t]));
-        if (v == 0.0) continue;
-      }
+      if (__popc(b1 ^ sb[t]) > 4) continue;
       if (kFill) {
-        if (pos < end) {
-          col[pos] = (int32_t)(s + t);
-          val[pos] = v;
-        }
+        if (pos < end) nbr[pos] = s + t;
         ++pos;
       } else {
         ++cnt;
@@ -173,9 +194,139 @@ __global__ void __launch_bounds__(kRowThreads) k_ham_pass(DevInts I, const uint6
   if (!kFill && live) cnt_off[slot] = cnt;
 }
 
+// Row lengths (kFill false: rp[r] = count) or elements (kFill true: rp holds
+// the row pointers) of rows r = warp, warp + warps, ...  The diagonal is
+// always stored; off-diagonal elements when nonzero.  The columns that pass
+// the excitation test are queued in shared memory (in column order) and
+// evaluated 32 at a time, one per lane, so that the Slater-Condon work runs
+// on full warps rather than on the one or two lanes that hit in a step.
+constexpr int kRowWarps = 8;
+
+template <bool kFill>
+__device__ __forceinline__ void flush_queue(const DevInts &I, const uint64_t *keys, uint32_t r,
+                                            uint32_t ai, uint32_t bi, const double *diag,
+                                            uint32_t *q, int k, uint32_t lane, uint32_t below,
+                                            int64_t &pos, int64_t end, int64_t &cnt, int32_t *col,
+                                            double *val) {
+  double v = 0.0;
+  uint32_t j = 0;
+  bool nz = false;
+  if ((int)lane < k) {
+    j = q[lane];
+    if (j == r) {
+      v = diag[r];
+      nz = true;
+    } else {
+      const uint64_t kj = keys[j];
+      v = offdiag_element(I, ai, bi, key_alpha(kj), key_beta(kj));
+      nz = v != 0.0;
+    }
+  }
+  const uint32_t bal = __ballot_sync(0xffffffffu, nz);
+  if (kFill) {
+    if (nz) {
+      const int64_t p = pos + __popc(bal & below);
+      if (p < end) {
+        col[p] = (int32_t)j;
+        val[p] = v;
+      }
+    }
+    pos += __popc(bal);
+  } else {
+    cnt += __popc(bal);
+  }
+}
+
+template <bool kFill>
+__global__ void __launch_bounds__(kRowWarps * 32) k_ham_rows(
+    DevInts I, const uint64_t *__restrict__ keys, uint32_t n, const uint32_t *__restrict__ of_row,
+    const uint32_t *__restrict__ gstart, const uint32_t *__restrict__ gbeta,
+    const int64_t *__restrict__ nbr_ptr, const uint32_t *__restrict__ nbr,
+    const double *__restrict__ diag, int64_t *rp, int32_t *col, double *val) {
+  __shared__ uint32_t queue[kRowWarps][64];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t below = (1u << lane) - 1u;
+  uint32_t *q = queue[threadIdx.x >> 5];
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+    const uint64_t ki = keys[r];
+    const uint32_t ai = key_alpha(ki), bi = key_beta(ki);
+    const uint32_t g = of_row[r];
+    int64_t pos = 0, end = 0, cnt = 0;
+    if (kFill) {
+      pos = rp[r];
+      end = rp[r + 1];
+    }
+    int qn = 0;  // queued columns (warp-uniform, < 64)
+    for (int64_t e = nbr_ptr[g]; e < nbr_ptr[g + 1]; ++e) {
+      const uint32_t g2 = nbr[e];
+      const uint32_t j0 = gstart[g2], j1 = gstart[g2 + 1];
+      const int thr = 4 - __popc(bi ^ gbeta[g2]);
+      for (uint32_t base = j0; base < j1; base += 32) {
+        const uint32_t j = base + lane;
+        const bool hit = j < j1 && __popc(ai ^ key_alpha(keys[j])) <= thr;
+        const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) q[qn + __popc(bal & below)] = j;
+        qn += __popc(bal);
+        __syncwarp();
+        if (qn >= 32) {
+          flush_queue<kFill>(I, keys, r, ai, bi, diag, q, 32, lane, below, pos, end, cnt, col,
+                             val);
+          const uint32_t rest = (lane + 32 < (uint32_t)qn) ? q[lane + 32] : 0u;
+          __syncwarp();
+          if (lane + 32 < (uint32_t)qn) q[lane] = rest;
+          qn -= 32;
+          __syncwarp();
+        }
+      }
+    }
+    if (qn > 0)
+      flush_queue<kFill>(I, keys, r, ai, bi, diag, q, qn, lane, below, pos, end, cnt, col, val);
+    __syncwarp();
+    if (!kFill && lane == 0) rp[r] = cnt;
+  }
+}
+
 __global__ void k_row_ptr(const uint64_t *off, uint32_t n, uint32_t nchunks, int64_t *row_ptr) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
     row_ptr[i] = (int64_t)off[(size_t)i * nchunks];
+}
+
+// Remapping a key-ordered CSR to the caller's order: perm[r] is the caller's
+// index of key-ordered row r.
+__global__ void k_user_counts(const int64_t *rp, const uint32_t *perm, uint32_t n,
+                              int64_t *cnt_user) {
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+    cnt_user[perm[r]] = rp[r + 1] - rp[r];
+}
+
+__global__ void k_user_entries(const int64_t *rp, const int32_t *col, const uint32_t *perm,
+                               uint32_t n, uint64_t *ekey) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+    const uint64_t u = (uint64_t)perm[r] << 32;
+    for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) {
+      const uint32_t c = (uint32_t)col[k];
+      ekey[k] = u | (c < n ? perm[c] : 0xffffffffu);
+    }
+  }
+}
+
+__global__ void k_low_cols(const uint64_t *ekey, size_t nnz, int32_t *col) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;
+       k += (size_t)gridDim.x * blockDim.x)
+    col[k] = (int32_t)(uint32_t)ekey[k];
+}
+
+__global__ void k_iota(uint32_t *v, uint32_t n) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    v[i] = i;
+}
+
+__global__ void k_not_identity(const uint32_t *perm, uint32_t n, unsigned *flag) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (perm[i] != i) *flag = 1u;
 }
 
 struct HamGeom {
@@ -596,35 +747,83 @@ struct Csr {
   size_t n;
 };
 
-// Counting pass, scan and row pointers; *off holds the (row, slice) write
-// offsets for the filling pass.
-static int ham_count(const DevInts &I, const uint64_t *keys, uint32_t n, const double *diag,
-                     int64_t *row_ptr, uint64_t **off, HamGeom *geom, size_t *nnz,
-                     Arena &arena) {
+// Beta groups of key-ordered determinants and their neighbour graph.
+struct BetaGraph {
+  uint32_t G = 0;
+  uint32_t *of_row = nullptr, *gstart = nullptr, *gbeta = nullptr, *nbr = nullptr;
+  int64_t *nbr_ptr = nullptr;
+};
+
+static int beta_graph(const uint64_t *keys, uint32_t n, BetaGraph *bg, Arena &arena) {
   cudaStream_t s = arena.stream();
-  const HamGeom g = ham_geom(n);
-  const size_t slots = (size_t)n * g.gy;
-  ASCI_TRY(arena.alloc(off, slots + 1));
-  ASCI_TRY_CUDA(cudaMemsetAsync(*off + slots, 0, sizeof(uint64_t), s));
-  k_ham_pass<false><<<dim3(g.gx, g.gy), kRowThreads, 0, s>>>(I, keys, n, g.chunk, g.gy, diag,
-                                                              *off, nullptr, nullptr);
+  uint32_t *head, *gid;
+  ASCI_TRY(arena.alloc(&head, n));
+  ASCI_TRY(arena.alloc(&gid, n));
+  k_beta_heads<<<blocks_for(n, 256), 256, 0, s>>>(keys, n, head);
   ASCI_CHECK_LAUNCH();
-  ASCI_TRY(scan_exclusive_u64(*off, *off, slots + 1, arena));
-  k_row_ptr<<<blocks_for((size_t)n + 1, 256), 256, 0, s>>>(*off, n, g.gy, row_ptr);
+  ASCI_TRY(scan_exclusive_u32(head, gid, n, arena));
+  uint32_t last[2];
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&last[0], gid + n - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&last[1], head + n - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  const uint32_t G = last[0] + last[1];
+  ASCI_TRY(arena.alloc(&bg->of_row, n));
+  ASCI_TRY(arena.alloc(&bg->gstart, (size_t)G + 1));
+  ASCI_TRY(arena.alloc(&bg->gbeta, G));
+  k_beta_groups<<<blocks_for(n, 256), 256, 0, s>>>(keys, n, head, gid, bg->of_row, bg->gstart,
+                                                    bg->gbeta);
+  ASCI_CHECK_LAUNCH();
+  // the group graph: count, scan, list
+  const HamGeom g = ham_geom(G);
+  const size_t slots = (size_t)G * g.gy;
+  uint64_t *off;
+  ASCI_TRY(arena.alloc(&off, slots + 1));
+  ASCI_TRY_CUDA(cudaMemsetAsync(off + slots, 0, sizeof(uint64_t), s));
+  k_beta_pairs<false><<<dim3(g.gx, g.gy), kRowThreads, 0, s>>>(bg->gbeta, G, g.chunk, g.gy, off,
+                                                                nullptr);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(scan_exclusive_u64(off, off, slots + 1, arena));
+  ASCI_TRY(arena.alloc(&bg->nbr_ptr, (size_t)G + 1));
+  k_row_ptr<<<blocks_for((size_t)G + 1, 256), 256, 0, s>>>(off, G, g.gy, bg->nbr_ptr);
   ASCI_CHECK_LAUNCH();
   uint64_t total = 0;
-  ASCI_TRY_CUDA(cudaMemcpyAsync(&total, *off + slots, sizeof(total), cudaMemcpyDeviceToHost, s));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&total, off + slots, sizeof(total), cudaMemcpyDeviceToHost, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
-  *geom = g;
+  ASCI_TRY(arena.alloc(&bg->nbr, total));
+  k_beta_pairs<true><<<dim3(g.gx, g.gy), kRowThreads, 0, s>>>(bg->gbeta, G, g.chunk, g.gy, off,
+                                                               bg->nbr);
+  ASCI_CHECK_LAUNCH();
+  bg->G = G;
+  return ASCI_OK;
+}
+
+static unsigned row_blocks(uint32_t n) {
+  return blocks_for((size_t)n * 32, kRowWarps * 32, 152 * 16);
+}
+
+// Counting pass and row pointers (rp[n + 1], device) of key-ordered keys.
+static int ham_count(const DevInts &I, const uint64_t *keys, uint32_t n, const double *diag,
+                     const BetaGraph &bg, int64_t *rp, size_t *nnz, Arena &arena) {
+  cudaStream_t s = arena.stream();
+  ASCI_TRY_CUDA(cudaMemsetAsync(rp + n, 0, sizeof(int64_t), s));
+  k_ham_rows<false><<<row_blocks(n), kRowWarps * 32, 0, s>>>(I, keys, n, bg.of_row, bg.gstart, bg.gbeta,
+                                                   bg.nbr_ptr, bg.nbr, diag, rp, nullptr,
+                                                   nullptr);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(scan_exclusive_u64(reinterpret_cast<uint64_t *>(rp), reinterpret_cast<uint64_t *>(rp),
+                              (size_t)n + 1, arena));
+  int64_t total = 0;
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&total, rp + n, sizeof(total), cudaMemcpyDeviceToHost, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
   *nnz = (size_t)total;
   return ASCI_OK;
 }
 
 static int ham_fill(const DevInts &I, const uint64_t *keys, uint32_t n, const double *diag,
-                    const uint64_t *off, const HamGeom &g, int32_t *col, double *val,
-                    Arena &arena) {
-  k_ham_pass<true><<<dim3(g.gx, g.gy), kRowThreads, 0, arena.stream()>>>(
-      I, keys, n, g.chunk, g.gy, diag, const_cast<uint64_t *>(off), col, val);
+                    const BetaGraph &bg, int64_t *rp, int32_t *col, double *val, Arena &arena) {
+  k_ham_rows<true><<<row_blocks(n), kRowWarps * 32, 0, arena.stream()>>>(I, keys, n, bg.of_row, bg.gstart,
+                                                              bg.gbeta, bg.nbr_ptr, bg.nbr, diag,
+                                                              rp, col, val);
   ASCI_CHECK_LAUNCH();
   return ASCI_OK;
 }
@@ -875,7 +1074,7 @@ static int stage_tables(const asci_ints *ints, int na, int nb, Arena &arena, Dev
   return build_tables(h1, eri, (int)n, na, nb, ints->ecore, false, arena, I);
 }
 
-// H over sorted-or-not packed keys, allocated in the arena.
+// H over key-ordered packed keys, allocated in the arena.
 static int ham_build(const DevInts &I, const uint64_t *keys, size_t n, Arena &arena, Csr *H,
                      double **diag_out) {
   double *diag;
@@ -883,15 +1082,15 @@ static int ham_build(const DevInts &I, const uint64_t *keys, size_t n, Arena &ar
   ASCI_TRY(arena.alloc(&diag, n));
   ASCI_TRY(arena.alloc(&rp, n + 1));
   ASCI_TRY(diagonal_packed(I, keys, n, diag, arena));
-  uint64_t *off;
-  HamGeom g;
+  BetaGraph bg;
+  ASCI_TRY(beta_graph(keys, (uint32_t)n, &bg, arena));
   size_t nnz = 0;
-  ASCI_TRY(ham_count(I, keys, (uint32_t)n, diag, rp, &off, &g, &nnz, arena));
+  ASCI_TRY(ham_count(I, keys, (uint32_t)n, diag, bg, rp, &nnz, arena));
   int32_t *col;
   double *val;
   ASCI_TRY(arena.alloc(&col, nnz));
   ASCI_TRY(arena.alloc(&val, nnz));
-  ASCI_TRY(ham_fill(I, keys, (uint32_t)n, diag, off, g, col, val, arena));
+  ASCI_TRY(ham_fill(I, keys, (uint32_t)n, diag, bg, rp, col, val, arena));
   H->row_ptr = rp;
   H->col = col;
   H->val = val;
@@ -1130,31 +1329,80 @@ int asci_hamiltonian(const asci_det *dets, size_t n, const asci_ints *ints, int6
   Arena arena(s);
   const asci_det *dd;
   ASCI_TRY(to_device(dets, n, &dd, arena));
-  uint64_t *keys;
+  uint64_t *keys, *keys_alt;
+  uint32_t *perm, *perm_alt;
   int na, nb;
   ASCI_TRY(arena.alloc(&keys, n));
+  ASCI_TRY(arena.alloc(&keys_alt, n));
+  ASCI_TRY(arena.alloc(&perm, n));
+  ASCI_TRY(arena.alloc(&perm_alt, n));
   ASCI_TRY(det_keys(dd, n, ints->norb, keys, &na, &nb, arena));
   DevInts I;
   ASCI_TRY(stage_tables(ints, na, nb, arena, &I));
+  // key order, and whether the caller's order already is key order
+  k_iota<<<blocks_for(n, 256), 256, 0, s>>>(perm, (uint32_t)n);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(radix_sort_u64_u32(&keys, &keys_alt, &perm, &perm_alt, n, 0, 64, arena));
+  unsigned *flag, hflag = 0;
+  ASCI_TRY(arena.alloc(&flag, 1));
+  ASCI_TRY_CUDA(cudaMemsetAsync(flag, 0, sizeof(unsigned), s));
+  k_not_identity<<<blocks_for(n, 256), 256, 0, s>>>(perm, (uint32_t)n, flag);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
   double *diag;
   ASCI_TRY(arena.alloc(&diag, n));
   ASCI_TRY(diagonal_packed(I, keys, n, diag, arena));
-  int64_t *rp;
-  ASCI_TRY(out_buffer(row_ptr, n + 1, &rp, arena));
-  uint64_t *off;
-  HamGeom g;
+  BetaGraph bg;
+  ASCI_TRY(beta_graph(keys, (uint32_t)n, &bg, arena));
+  const bool same_order = hflag == 0;
+  int64_t *rp, *urp;
+  ASCI_TRY(out_buffer(row_ptr, n + 1, &urp, arena));
+  if (same_order) rp = urp;
+  else ASCI_TRY(arena.alloc(&rp, n + 1));
   size_t total = 0;
-  ASCI_TRY(ham_count(I, keys, (uint32_t)n, diag, rp, &off, &g, &total, arena));
+  ASCI_TRY(ham_count(I, keys, (uint32_t)n, diag, bg, rp, &total, arena));
+  if (!same_order) {  // row pointers in the caller's order
+    ASCI_TRY_CUDA(cudaMemsetAsync(urp + n, 0, sizeof(int64_t), s));
+    k_user_counts<<<blocks_for(n, 256), 256, 0, s>>>(rp, perm, (uint32_t)n, urp);
+    ASCI_CHECK_LAUNCH();
+    ASCI_TRY(scan_exclusive_u64(reinterpret_cast<uint64_t *>(urp),
+                                reinterpret_cast<uint64_t *>(urp), n + 1, arena));
+  }
   if (total <= capacity) {
     int32_t *dc;
     double *dv;
     ASCI_TRY(out_buffer(col, total, &dc, arena));
     ASCI_TRY(out_buffer(val, total, &dv, arena));
-    ASCI_TRY(ham_fill(I, keys, (uint32_t)n, diag, off, g, dc, dv, arena));
+    if (same_order) {
+      ASCI_TRY(ham_fill(I, keys, (uint32_t)n, diag, bg, rp, dc, dv, arena));
+    } else {
+      // build in key order, then sort the entries on (caller row, caller column)
+      if (total >= (1ull << 32)) {
+        record_error("too many elements to reorder; pass the determinants in key order",
+                     __FILE__, __LINE__);
+        return ASCI_ENOMEM;
+      }
+      int32_t *kc;
+      double *kv, *kv_alt;
+      uint64_t *ek, *ek_alt;
+      ASCI_TRY(arena.alloc(&kc, total));
+      ASCI_TRY(arena.alloc(&kv, total));
+      ASCI_TRY(arena.alloc(&kv_alt, total));
+      ASCI_TRY(arena.alloc(&ek, total));
+      ASCI_TRY(arena.alloc(&ek_alt, total));
+      ASCI_TRY(ham_fill(I, keys, (uint32_t)n, diag, bg, rp, kc, kv, arena));
+      k_user_entries<<<row_blocks((uint32_t)n), 256, 0, s>>>(rp, kc, perm, (uint32_t)n, ek);
+      ASCI_CHECK_LAUNCH();
+      ASCI_TRY(radix_sort_u64_f64(&ek, &ek_alt, &kv, &kv_alt, total, 0, 64, arena));
+      k_low_cols<<<blocks_for(total, 256), 256, 0, s>>>(ek, total, dc);
+      ASCI_CHECK_LAUNCH();
+      ASCI_TRY_CUDA(cudaMemcpyAsync(dv, kv, total * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     ASCI_TRY(finish_out(col, dc, total, s));
     ASCI_TRY(finish_out(val, dv, total, s));
   }
-  ASCI_TRY(finish_out(row_ptr, rp, n + 1, s));
+  ASCI_TRY(finish_out(row_ptr, urp, n + 1, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
   *nnz = total;
   return ASCI_OK;
