@@ -576,7 +576,7 @@ def spmv(H, x, stream=None):
     return y[:n]
 
 
-def davidson(H, guess=None, *, max_subspace: int = 24, max_iter: int = 300, tol: float = 1e-8,
+def davidson(H, guess=None, *, max_subspace: int = 16, max_iter: int = 300, tol: float = 1e-8,
              stream=None):
     """Lowest eigenpair of H = (row_ptr, col, val) by Davidson (Alg. 5).
     Returns (energy, vector (device), products with H, residual norm)."""
@@ -601,7 +601,7 @@ def davidson(H, guess=None, *, max_subspace: int = 24, max_iter: int = 300, tol:
 
 def asci_loop(dets, coeffs, h1, eri, ecore, *, ncdets: int, ntdets: int, max_steps: int = 8,
               etol: float = 1e-6, eps: float = 0.0, precision: int = FP64,
-              max_batch_pairs: int = 0, max_subspace: int = 24, max_iter: int = 300,
+              max_batch_pairs: int = 0, max_subspace: int = 16, max_iter: int = 300,
               tol: float = 1e-8, stream=None):
     """The ASCI loop (Alg. 1): search, keep the ntdets largest of |c| and |S|,
     build H on that space, Davidson; repeat.  Returns (dets, coeffs, energy,

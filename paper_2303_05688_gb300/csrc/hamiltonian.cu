@@ -258,13 +258,37 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_ham_rows(
       end = rp[r + 1];
     }
     int qn = 0;  // queued columns (warp-uniform, < 64)
-    for (int64_t e = nbr_ptr[g]; e < nbr_ptr[g + 1]; ++e) {
-      const uint32_t g2 = nbr[e];
-      const uint32_t j0 = gstart[g2], j1 = gstart[g2 + 1];
-      const int thr = 4 - __popc(bi ^ gbeta[g2]);
-      for (uint32_t base = j0; base < j1; base += 32) {
-        const uint32_t j = base + lane;
-        const bool hit = j < j1 && __popc(ai ^ key_alpha(keys[j])) <= thr;
+    // 32 neighbour groups at a time: lane k holds group k's first column,
+    // length and alpha threshold; their columns are walked as one
+    // concatenated range, 32 columns per step, each lane finding its group
+    // by a binary search over the lanes' offsets
+    const int64_t e1 = nbr_ptr[g + 1];
+    for (int64_t e0 = nbr_ptr[g]; e0 < e1; e0 += 32) {
+      uint32_t gs = 0, len = 0;
+      int thr = -1;
+      if (e0 + lane < e1) {
+        const uint32_t g2 = nbr[e0 + lane];
+        gs = gstart[g2];
+        len = gstart[g2 + 1] - gs;
+        thr = 4 - __popc(bi ^ gbeta[g2]);
+      }
+      uint32_t off = len;  // inclusive scan of the lengths
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, off, o);
+        if ((int)lane >= o) off += y;
+      }
+      const uint32_t total = __shfl_sync(0xffffffffu, off, 31);
+      off -= len;  // exclusive
+      for (uint32_t c = 0; c < total; c += 32) {
+        const uint32_t idx = c + lane;
+        int k = 0;  // the last lane whose offset is <= idx
+        for (int step = 16; step; step >>= 1) {
+          const uint32_t o2 = __shfl_sync(0xffffffffu, off, k + step);
+          if (o2 <= idx) k += step;
+        }
+        const uint32_t j = __shfl_sync(0xffffffffu, gs, k) + (idx - __shfl_sync(0xffffffffu, off, k));
+        const int t = __shfl_sync(0xffffffffu, thr, k);
+        const bool hit = idx < total && __popc(ai ^ key_alpha(keys[idx < total ? j : r])) <= t;
         const uint32_t bal = __ballot_sync(0xffffffffu, hit);
         if (hit) q[qn + __popc(bal & below)] = j;
         qn += __popc(bal);
@@ -479,6 +503,46 @@ __global__ void k_normalize(double *v, size_t n, const double *norm2) {
 // eigenvectors, P = diag(old eigenvectors, 1), so that P^T Hs P is diagonal
 // but for its last row and column and two or three sweeps finish it.
 constexpr int kEigThreads = 256;
+
+// 1/x and 1/sqrt(x) to FP64 accuracy from the FP32 estimates (__frcp_rn,
+// rsqrtf) and two Newton-Raphson steps each (y <- y(2 - xy) and
+// y <- y(3 - xy^2)/2; each step squares the relative error, 2^-23 -> 2^-92),
+// valid for |x| in [1e-30, 1e30]; GB300 has little FP64 throughput, and this
+// avoids the longer FP64 division and square-root sequences.
+__device__ __forceinline__ double recip_fast(double x) {
+  double y = (double)__frcp_rn((float)x);
+  y = y * fma(-x, y, 2.0);
+  return y * fma(-x, y, 2.0);
+}
+__device__ __forceinline__ double rsqrt_fast(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  return y * fma(-0.5 * x, y * y, 1.5);
+}
+
+// The Jacobi rotation (c, s) that zeroes a_pq: tau = (a_qq - a_pp) / (2 a_pq),
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c
+// (Golub and Van Loan, Alg. 8.5.1), with the fast reciprocals when every
+// operand is in their range and the exact operations otherwise.
+__device__ __forceinline__ void rotation(double app, double aqq, double apq, double *c,
+                                         double *s) {
+  const double d = aqq - app, a2 = 2.0 * apq;
+  const bool fast = fabs(a2) > 1e-30 && fabs(a2) < 1e30 && fabs(d) < 1e15 * fabs(a2);
+  double t;
+  if (fast) {
+    const double tau = d * recip_fast(a2);  // |tau| < 1e15
+    const double y = fma(tau, tau, 1.0);
+    const double den = fabs(tau) + y * rsqrt_fast(y);  // in [1, 2e15]
+    t = (tau >= 0.0 ? 1.0 : -1.0) * recip_fast(den);
+  } else {
+    const double tau = d / a2;
+    t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  }
+  const double cs = rsqrt_fast(fma(t, t, 1.0));  // 1 + t^2 in [1, 2]
+  *c = cs;
+  *s = t * cs;
+}
+
 constexpr int kEigPer = (kMaxSub * kMaxSub + kEigThreads - 1) / kEigThreads;
 
 __global__ void __launch_bounds__(kEigThreads) k_small_eig(const double *Hs, int ld, int m,
@@ -560,12 +624,7 @@ __global__ void __launch_bounds__(kEigThreads) k_small_eig(const double *Hs, int
         double cs = 1.0, sn = 0.0;
         if (q < m) {
           const double apq = A[p][q];
-          if (fabs(apq) >= 1e-300) {
-            const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            cs = 1.0 / sqrt(1.0 + t * t);
-            sn = t * cs;
-          }
+          if (fabs(apq) >= 1e-300) rotation(A[p][p], A[q][q], apq, &cs, &sn);
         }
         rc[tid] = cs;
         rs[tid] = sn;
@@ -1302,7 +1361,7 @@ extern "C" {
 
 void asci_default_davidson_opts(asci_davidson_opts *o) {
   if (!o) return;
-  o->max_subspace = 24;
+  o->max_subspace = 16;
   o->max_iter = 300;
   o->tol = 1e-8;
 }
