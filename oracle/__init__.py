@@ -10,7 +10,7 @@ duplicate-aware top-N selection of Sec. 2.2, and Algorithm 1 (the ASCI loop:
 search, select, diagonalise in the selected space, repeat) with the
 diagonalisation written as its definition, the lowest eigenpair of the dense
 Hamiltonian restricted to the space (Sec. 2.3 computes it by Davidson,
-Algorithm 5).  ``fock`` holds an independent
+Algorithm 5), and the ASCI-PT2 energy that ends Algorithm 1.  ``fock`` holds an independent
 brute-force second-quantised Hamiltonian that pins the oracle's Slater-Condon
 evaluator.
 """
@@ -296,3 +296,13 @@ def asci_loop(ints: Ints, A, B, c, ncdets: int, ntdets: int, max_iter: int, etol
         if done:
             break
     return A, B, c, E, hist
+
+
+def pt2(ints: Ints, A, B, c, E0: float, C: int, eps: float = 0.0) -> float:
+    """ASCI-PT2 (the last step of Algorithm 1): the sum over every unique
+    candidate i outside psi of num_i^2 / (E0 - H_ii), num_i = sum over the C
+    core determinants of H_ij c_j (the search's numerator, Eq. 1), summed
+    exactly rounded (math.fsum)."""
+    import math
+    res = search(ints, A, B, c, E0, C, eps)
+    return math.fsum((res.num * res.num / (E0 - res.haa)).tolist())

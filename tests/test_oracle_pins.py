@@ -317,6 +317,35 @@ def test_h_rows_equal_bruteforce_rows(oracle_mod):
 
 
 # --------------------------------------------------------------------------
+# ASCI-PT2 (last step of Alg. 1) against the dense brute-force Hamiltonian
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("npsi,C", [(1, 1), (30, 30), (30, 12)])
+def test_pt2_equals_dense_second_order_sum(oracle_mod, npsi, C):
+    """E_PT2 = sum_{i not in psi} ((H c_core)_i)^2 / (E0 - H_ii) over the whole
+    sector, with H from the second-quantised brute force."""
+    n, na, nb = 6, 3, 3
+    h1, eri, ec = W.random_molecular(n, 21)
+    ec = 0.4
+    ints = oracle_mod.Ints(h1, eri, ec)
+    SA, SB = fock.sector(n, na, nb)
+    H = fock.hamiltonian(n, h1, eri, ec, SA, SB)
+    rng = np.random.default_rng(npsi + C)
+    idx = rng.choice(len(SA), npsi, replace=False)
+    A, B = SA[idx], SB[idx]
+    c = rng.normal(size=npsi)
+    E0 = float(np.min(np.diag(H))) - 0.5  # below every H_ii: no vanishing denominator
+    core = oracle_mod.core_select(A, B, c, C)
+    y = H[:, idx[core]] @ c[core]
+    out = np.ones(len(SA), dtype=bool)
+    out[idx] = False
+    ref = float(np.sum(y[out] ** 2 / (E0 - np.diag(H)[out])))
+    got = oracle_mod.pt2(ints, A, B, c, E0, C)
+    assert abs(got - ref) <= 1e-12 * abs(ref)
+    assert got < 0
+
+
+# --------------------------------------------------------------------------
 # planted mistakes: each must be caught by a pin
 # --------------------------------------------------------------------------
 
