@@ -363,6 +363,44 @@ def run_levels(args):
     return 0
 
 
+def run_pt2(args):
+    """ASCI-PT2 (the last step of Alg. 1) on the (24e,30o) workload with the
+    search's 1e5-determinant core: every unique target outside psi (5.5e9)
+    contributes num^2 / (E0 - H_ii).  Mean of args.steps calls after
+    args.warmup, inputs resident; L2 flushed before each call."""
+    import torch
+    import numpy as np
+    import paper_2303_05688_gb300 as asci
+    w, h1, eri, ec, A, B, c, E0, _ = load_workload("random_24e30o")
+    dev = torch.device("cuda", 0)
+    d = torch.tensor(np.stack([A, B], 1).astype(np.int64), device=dev)
+    cf, h1d, ed = (torch.tensor(x, device=dev) for x in (c, h1, eri))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 1)):
+        asci.pt2(d, cf, E0, h1d, ed, ec, w.C)
+    times = []
+    for _ in range(max(args.steps, 1)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        val, st = asci.pt2(d, cf, E0, h1d, ed, ec, w.C)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times)
+    print(json.dumps({
+        "metric": "ASCI-PT2 scored excitations/s at (24e,30o)", "unit": "excitations/s",
+        "value": st.generated / (ms / 1e3), "ms_per_step": ms, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": "f64",
+        "config": {"workload": "random_24e30o pt2", "C": w.C, "ndets": w.ndets,
+                   "l2": "flushed (512 MB write) before each step"},
+        "e_pt2": val, "targets": st.unique - st.excluded, "generated": st.generated,
+        "batches": st.batches, "stage_ms": {k: round(v, 3) for k, v in st.t_stage_ms.items()}}),
+        flush=True)
+    return 0
+
+
 def run_loop(args):
     """The ASCI loop (Alg. 1) on the (16e,16o) workload: three steps from its
     psi (1e5 determinants) with the (1e4, 1e5) core and wavefunction sizes;
@@ -441,6 +479,8 @@ def main():
         return run_served(args)
     if args.workload == "asci_loop":
         return run_loop(args)
+    if args.workload == "pt2":
+        return run_pt2(args)
 
     import torch
     import torch.distributed as dist

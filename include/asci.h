@@ -164,6 +164,24 @@ int asci_search(const asci_det *dets, const double *coeffs, size_t ndets, double
                 void *cuda_stream);
 
 /*
+ * ASCI-PT2 (the last step of Algorithm 1): the second-order energy of the
+ * determinants outside psi,
+ *     E_PT2 = sum_{i not in psi} (sum_{j in core} H_ij c_j)^2 / (E0 - H_ii),
+ * with the core the C determinants of largest |c| (C >= ndets: the whole
+ * wavefunction, the usual PT2).  It runs the search's generation, constraint
+ * batching and on-chip accumulation (a2-a5) with no threshold, and sums the
+ * terms of every unique target in an exact fixed-point accumulator (grid
+ * 2^-216, terms truncated to it), so the value does not depend on batching or
+ * scheduling.  eps_search in opts screens pairs as in the search (0: none).
+ *
+ * Errors: those of asci_search; ASCI_EINVAL also when a term is not finite or
+ * exceeds 2^40 in magnitude (E0 equal or too close to a target's H_ii).
+ */
+int asci_pt2(const asci_det *dets, const double *coeffs, size_t ndets, double E0,
+             const asci_ints *ints, size_t C, const asci_opts *opts, double *e_pt2,
+             asci_stats *stats, void *cuda_stream);
+
+/*
  * Generation stage of Algorithm 2 (the inner loops: "single and double
  * connections from D_j" and the partial quantity H_ij C_j), for testing the
  * excitation kernel in isolation.  For each core determinant, in input order,
@@ -385,7 +403,7 @@ void asci_default_loop_opts(asci_loop_opts *opts);
  * diagonal of every determinant it connects to, e.g. a small CI).
  * The loop stops after max_steps, once |E_{k+1} - E_k| <= etol, or once a
  * step leaves the determinant set unchanged.  The final ASCI-PT2 step of
- * Algorithm 1 is not part of this call.
+ * Algorithm 1 is asci_pt2 on the result.
  *
  *  dets[ndets], coeffs[ndets]  the start (distinct determinants, equal counts).
  *  out_dets, out_coeffs        capacity entries each, capacity >= ntdets: the

@@ -21,7 +21,7 @@ __all__ = ["load", "lib_path", "launch_count", "search", "excitations", "diagona
            "select_topn", "SearchStats", "AsciError", "FP64", "FP32_INT_FP64_ACC",
            "FP32_INT_COMP_ACC", "shard_assign", "gather_candidates", "sharded_search",
            "search_many", "tune_streams", "hamiltonian", "spmv", "davidson", "asci_loop",
-           "LoopStats"]
+           "LoopStats", "pt2"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "lib", "libasci.so")
@@ -155,6 +155,9 @@ def load():
     lib.asci_search.restype = ct.c_int
     lib.asci_search.argtypes = [vp, vp, sz, ct.c_double, ct.POINTER(_Ints), sz, sz,
                                 ct.POINTER(_Opts), vp, vp, szp, ct.POINTER(_Stats), vp]
+    lib.asci_pt2.restype = ct.c_int
+    lib.asci_pt2.argtypes = [vp, vp, sz, ct.c_double, ct.POINTER(_Ints), sz, ct.POINTER(_Opts),
+                             ct.POINTER(ct.c_double), ct.POINTER(_Stats), vp]
     lib.asci_excitations.restype = ct.c_int
     lib.asci_excitations.argtypes = [ct.POINTER(_Ints), vp, vp, sz, vp, vp, sz, szp, vp]
     lib.asci_diagonal.restype = ct.c_int
@@ -314,6 +317,27 @@ def search(dets, coeffs, E0: float, h1, eri, ecore: float, C: int, N: int, *,
     _check(code, "asci_search")
     m = n_out.value
     return od[:m], os_[:m], (SearchStats._from(st) if return_stats else None)
+
+
+def pt2(dets, coeffs, E0: float, h1, eri, ecore: float, C: int = None, *, eps: float = 0.0,
+        precision: int = FP64, max_batch_pairs: int = 0, max_constraint_level: int = 0,
+        stream=None):
+    """ASCI-PT2 (Alg. 1, last step): sum over targets i outside psi of
+    (sum_j H_ij c_j)^2 / (E0 - H_ii) with the C-determinant core (default: all
+    of psi).  Returns (E_PT2, SearchStats)."""
+    lib = load()
+    keep = []
+    db = _dets_buf(dets)
+    cb = _as_buf(coeffs, np.float64, "float64")
+    keep += [db, cb]
+    ints, _ = _ints(h1, eri, ecore, keep)
+    nd = int(db.obj.shape[0])
+    o = _opts(lib, eps, precision, max_batch_pairs, max_constraint_level, False)
+    st = _Stats()
+    e = ct.c_double(0.0)
+    _check(lib.asci_pt2(db.ptr, cb.ptr, nd, float(E0), ct.byref(ints), int(C or nd), ct.byref(o),
+                        ct.byref(e), ct.byref(st), _stream_ptr(stream, db.device)), "asci_pt2")
+    return e.value, SearchStats._from(st)
 
 
 def excitations(h1, eri, ecore, core_dets, core_coeffs, stream=None):

@@ -2122,7 +2122,94 @@ __global__ void k_exact_scores(const uint64_t *key, double *score, size_t n, FxI
   }
 }
 
+// ASCI-PT2 terms num^2 / (E0 - H_ii) of appended candidates (Alg. 1, last
+// step), summed without rounding in a fixed-point grid of 2^-216 held as eight
+// signed 32-bit limbs in 64-bit counters (a term of magnitude below 2^40 spans
+// at most three limbs; bits below the grid are truncated).  Integer addition
+// is exact and associative, so the sum does not depend on the order of the
+// terms, on the batches or on the tiles: the result is a function of the set
+// of targets.  Per-thread limb sums are reduced over the warp and the block,
+// then added to the counters with one atomic per limb and block; a launch
+// holds fewer than 2^31 terms, so no counter overflows.
+constexpr int kPt2Limbs = 8;
+constexpr int kPt2Grid = 216;  // the grid is 2^-216
+
+__device__ __forceinline__ void pt2_add(double t, long long *acc, unsigned *bad) {
+  if (t == 0.0) return;
+  if (!(fabs(t) < 0x1p40)) {  // also catches NaN and infinities
+    *bad = 1u;
+    return;
+  }
+  const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+  const int e = (int)((b >> 52) & 0x7ffu);
+  unsigned long long m = (b & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
+  int p = (e ? e : 1) - 1075 + kPt2Grid;  // grid position of m's lowest bit
+  if (p < 0) {
+    if (p <= -64) return;
+    m >>= -p;
+    p = 0;
+  }
+  const int k0 = p >> 5, o = p & 31;
+  const unsigned long long lo = m << o;
+  const unsigned long long hi = o ? (m >> (64 - o)) : 0ull;
+  const long long sg = t < 0.0 ? -1 : 1;
+  acc[k0] += sg * (long long)(lo & 0xffffffffull);
+  if (k0 + 1 < kPt2Limbs) acc[k0 + 1] += sg * (long long)(lo >> 32);
+  if (k0 + 2 < kPt2Limbs) acc[k0 + 2] += sg * (long long)(hi & 0xffffffffull);
+}
+
+__global__ void __launch_bounds__(256) k_pt2_terms(const uint64_t *key, const double *num,
+                                                   size_t n, FxInts X, int64_t E0_x,
+                                                   double inv_scale, long long *limbs,
+                                                   unsigned *err) {
+  __shared__ long long red[8][kPt2Limbs];
+  long long acc[kPt2Limbs];
+  for (int k = 0; k < kPt2Limbs; ++k) acc[k] = 0;
+  unsigned bad = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t k = key[i];
+    const int64_t den_x = E0_x - fx_diag(X, key_alpha(k), (uint32_t)(k >> 32));
+    const double v = num[i];
+    pt2_add(v * (v / (__ll2double_rn(den_x) * inv_scale)), acc, &bad);
+  }
+  if (bad) atomicOr(err, kErrAccum);
+  for (int k = 0; k < kPt2Limbs; ++k)
+    for (int o = 16; o; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < kPt2Limbs; ++k) red[threadIdx.x >> 5][k] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < kPt2Limbs) {
+    long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+    if (t) atomicAdd((unsigned long long *)&limbs[threadIdx.x], (unsigned long long)t);
+  }
+}
+
+// The counters as one double: the limbs in a fixed order, low to high.
+__global__ void k_pt2_value(const long long *limbs, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double x = 0.0;
+  for (int k = 0; k < kPt2Limbs; ++k) x += ldexp((double)limbs[k], 32 * k - kPt2Grid);
+  *out = x;
+}
+
 }  // namespace
+
+int pt2_terms(const FusedCore &F, const uint64_t *key, const double *num, size_t n,
+              long long *limbs, unsigned *err, cudaStream_t s) {
+  if (!n) return ASCI_OK;
+  k_pt2_terms<<<grid_for(n, 152 * 8), 256, 0, s>>>(key, num, n, F.X, F.E0_x,
+                                                   ldexp(1.0, -F.X.s), limbs, err);
+  ASCI_CHECK_LAUNCH();
+  return ASCI_OK;
+}
+
+int pt2_value(const long long *limbs, double *out, cudaStream_t s) {
+  k_pt2_value<<<1, 32, 0, s>>>(limbs, out);
+  ASCI_CHECK_LAUNCH();
+  return ASCI_OK;
+}
 
 int exact_scores(const FusedCore &F, const uint64_t *key, double *score, size_t n,
                  cudaStream_t s) {

@@ -74,6 +74,9 @@ size_t tile_capacity();
 int exact_scores(const FusedCore &F, const uint64_t *key, double *score, size_t n,
                  cudaStream_t s);
 int abs_min(const double *s, size_t n, double *host_min, Arena &arena);
+int pt2_terms(const FusedCore &F, const uint64_t *key, const double *num, size_t n,
+              long long *limbs, unsigned *err, cudaStream_t s);
+int pt2_value(const long long *limbs, double *out, cudaStream_t s);
 
 static thread_local char g_last_error[512] = "";
 static std::atomic<unsigned long long> g_launches{0};
@@ -507,10 +510,13 @@ int device_pool(int dev, cudaMemPool_t *pool) {
 }
 
 // The search proper.  All pointers resolved; `arena` owns the scratch.
+// With pt2_out set, the same pipeline runs without a threshold and, instead
+// of keeping candidates, folds every unique target outside psi into the
+// ASCI-PT2 sum num^2 / (E0 - H_ii) (N must be 0).
 static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t nd, double E0,
                        const asci_ints *ints, size_t C, size_t N, const asci_opts &o,
                        asci_det *out_dets, double *out_scores, size_t *out_n, asci_stats *st,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, double *pt2_out = nullptr) {
   Arena arena(stream);
   double tl[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per-stage device milliseconds
   uint64_t tile_launches = 0, staged_records = 0, oversized_records = 0;
@@ -797,6 +803,27 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   size_t pool_n = 0;
   int pcur = 0;
   double tau = 0.0;
+  long long *pt2_limbs = nullptr;  // ASCI-PT2 fixed-point counters
+  if (pt2_out) {
+    ASCI_TRY(arena.alloc(&pt2_limbs, 8));
+    ASCI_TRY_CUDA(cudaMemsetAsync(pt2_limbs, 0, 8 * sizeof(long long), stream));
+  }
+  // Candidates [pool_n, c) were appended with their numerators: form their
+  // exact scores, or (PT2) add their terms and drop them.
+  auto consume = [&](unsigned long long c) -> int {
+    if (pt2_out) {
+      ASCI_TRY(pt2_terms(F, pool_k[pcur] + pool_n, pool_s[pcur] + pool_n, (size_t)c - pool_n,
+                         pt2_limbs, derr2, stream));
+      const unsigned long long keep = pool_n;
+      ASCI_TRY_CUDA(cudaMemcpyAsync(dcount, &keep, sizeof(keep), cudaMemcpyHostToDevice, stream));
+      ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+      return ASCI_OK;
+    }
+    ASCI_TRY(exact_scores(F, pool_k[pcur] + pool_n, pool_s[pcur] + pool_n, (size_t)c - pool_n,
+                          stream));
+    pool_n = (size_t)c;
+    return ASCI_OK;
+  };
   // Prune the pool to the top N and raise tau to its N-th |S| (a lower bound of
   // the final cutoff, so nothing that can still be selected is ever dropped).
   auto prune = [&](Arena &pa) -> int {
@@ -869,10 +896,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
         return ASCI_ECUDA;
       }
       if (c > pool_cap) return ASCI_ECUDA;  // cannot happen: room bounds the appends
-      // appended candidates carry their numerator: form their exact scores
-      ASCI_TRY(exact_scores(F, pool_k[pcur] + pool_n, pool_s[pcur] + pool_n, (size_t)c - pool_n,
-                            stream));
-      pool_n = (size_t)c;
+      ASCI_TRY(consume(c));
       t = t1;
       if (pool_n > N && (pool_cap - pool_n) < pool_cap / 2) {
         tm.stop(&tl[5]);
@@ -920,9 +944,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
           return ASCI_ECUDA;
         }
         if (c > pool_cap) return ASCI_ECUDA;
-        ASCI_TRY(exact_scores(F, pool_k[pcur] + pool_n, pool_s[pcur] + pool_n,
-                              (size_t)c - pool_n, stream));
-        pool_n = (size_t)c;
+        ASCI_TRY(consume(c));
         ASCI_TRACE("oversized tiles: [%zu,%zu) %llu records, pool=%zu", i, j,
                    (unsigned long long)nrec, pool_n);
         i = j;
@@ -943,6 +965,39 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     unique = hc[1];
     excluded = hc[2];
     if (o.eps_search > 0.0) surviving = hc[3];
+  }
+  if (pt2_out) {
+    double v = 0.0;
+    unsigned he = 0;
+    if (bcap) {
+      double *dv;
+      ASCI_TRY(arena.alloc(&dv, 1));
+      ASCI_TRY(pt2_value(pt2_limbs, dv, stream));
+      ASCI_TRY_CUDA(cudaMemcpyAsync(&v, dv, sizeof(v), cudaMemcpyDeviceToHost, stream));
+      ASCI_TRY_CUDA(cudaMemcpyAsync(&he, derr2, sizeof(he), cudaMemcpyDeviceToHost, stream));
+      ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+    }
+    if (he) {
+      record_error("a PT2 term is not finite or exceeds 2^40 (E0 equals or nearly equals a "
+                   "target's H_ii)", __FILE__, __LINE__);
+      return ASCI_EINVAL;
+    }
+    *pt2_out = v;
+    *out_n = 0;
+    if (st) {
+      st->surviving = surviving;
+      st->unique = unique;
+      st->excluded = excluded;
+      st->selected = 0;
+    }
+    total_tm.stop(&tl[7]);
+    if (st) {
+      memcpy(st->t_stage, tl, sizeof(tl));
+      st->tile_launches = tile_launches;
+      st->oversized_records = oversized_records;
+      st->tile_records = staged_records - oversized_records;
+    }
+    return ASCI_OK;
   }
   ASCI_TRACE("select: pool=%zu N=%zu", pool_n, N);
   // ------------------------------ select -----------------------------------
@@ -1083,6 +1138,33 @@ int asci_search(const asci_det *dets, const double *coeffs, size_t ndets, double
   int r = search_impl(dets, coeffs, ndets, E0, ints, C, N, o, out_dets, out_scores, out_n, stats,
                       s);
   if (r != ASCI_OK) *out_n = 0;
+  return r;
+}
+
+int asci_pt2(const asci_det *dets, const double *coeffs, size_t ndets, double E0,
+             const asci_ints *ints, size_t C, const asci_opts *opts, double *e_pt2,
+             asci_stats *stats, void *cuda_stream) {
+  if (e_pt2) *e_pt2 = 0.0;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (!dets || !coeffs || !ints || !ints->h1 || !ints->eri || !e_pt2) return ASCI_EINVAL;
+  if (ints->norb < 1 || ints->norb > 32 || ndets == 0 || C == 0) return ASCI_EINVAL;
+  if (!std::isfinite(E0) || !std::isfinite(ints->ecore)) return ASCI_EINVAL;
+  if (ndets >= (1ull << 32)) return ASCI_EINVAL;
+  asci_opts o;
+  asci_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.eps_search >= 0.0) || !std::isfinite(o.eps_search)) return ASCI_EINVAL;
+  if (o.precision < ASCI_FP64 || o.precision > ASCI_FP32_INT_COMP_ACC) return ASCI_EINVAL;
+  if (o.shard_count < 0 || o.shard_count > 1024 ||
+      (o.shard_count > 1 && (o.shard_index < 0 || o.shard_index >= o.shard_count)))
+    return ASCI_EINVAL;
+  cudaStream_t s;
+  ASCI_TRY(begin_call(cuda_stream, &s));
+  size_t n_out = 0;
+  double v = 0.0;
+  int r = search_impl(dets, coeffs, ndets, E0, ints, C, 0, o, nullptr, nullptr, &n_out, stats, s,
+                      &v);
+  if (r == ASCI_OK) *e_pt2 = v;
   return r;
 }
 
