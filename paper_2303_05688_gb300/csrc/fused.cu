@@ -1497,17 +1497,23 @@ __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const ui
   }
 }
 
-__global__ void k_psi_insert(const uint64_t *keys, size_t n, uint64_t *ht, uint64_t mask) {
+// Linear-probing insert; the table is at most 1/4 full, so a free slot is
+// always found, and the probe count is bounded by the table size regardless
+// (exceeding it sets *err).
+__global__ void k_psi_insert(const uint64_t *keys, size_t n, uint64_t *ht, uint64_t mask,
+                             unsigned *err) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
     const uint64_t k = keys[i];
     uint64_t h = mix_key(k) & mask;
-    for (;;) {
+    uint64_t probe = 0;
+    for (; probe <= mask; ++probe) {
       unsigned long long prev =
           atomicCAS((unsigned long long *)&ht[h], ~0ull, (unsigned long long)k);
       if (prev == ~0ull || prev == k) break;
       h = (h + 1) & mask;
     }
+    if (probe > mask) atomicOr(err, kErrProbe);
   }
 }
 
@@ -1649,8 +1655,17 @@ int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t 
   ASCI_TRY(arena.alloc(ht, size));
   cudaStream_t s = arena.stream();
   ASCI_TRY_CUDA(cudaMemsetAsync(*ht, 0xff, size * sizeof(uint64_t), s));
-  k_psi_insert<<<grid_for(nd), 256, 0, s>>>(psi_keys, nd, *ht, size - 1);
+  unsigned *err, herr = 0;
+  ASCI_TRY(arena.alloc(&err, 1));
+  ASCI_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
+  k_psi_insert<<<grid_for(nd), 256, 0, s>>>(psi_keys, nd, *ht, size - 1, err);
   ASCI_CHECK_LAUNCH();
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  if (herr) {
+    record_error("psi hash table full", __FILE__, __LINE__);
+    return ASCI_ECUDA;
+  }
   *mask = size - 1;
   return ASCI_OK;
 }
