@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--sharded", action="store_true",
                    help="under torchrun: one search split over the ranks by constraint class "
                         "(strong scaling) instead of one search per rank")
+    p.add_argument("--pt2-workload", default="random_24e30o",
+                   help="system of --workload pt2 (its psi and core size)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-core", type=int, default=0,
@@ -364,14 +366,15 @@ def run_levels(args):
 
 
 def run_pt2(args):
-    """ASCI-PT2 (the last step of Alg. 1) on the (24e,30o) workload with the
-    search's 1e5-determinant core: every unique target outside psi (5.5e9)
-    contributes num^2 / (E0 - H_ii).  Mean of args.steps calls after
-    args.warmup, inputs resident; L2 flushed before each call."""
+    """ASCI-PT2 (the last step of Alg. 1) on the (24e,30o) workload (or
+    --pt2-workload) with the search's core (1e5 determinants): every unique
+    target outside psi (5.5e9) contributes num^2 / (E0 - H_ii).  Mean of
+    args.steps calls after args.warmup, inputs resident; L2 flushed before
+    each call."""
     import torch
     import numpy as np
     import paper_2303_05688_gb300 as asci
-    w, h1, eri, ec, A, B, c, E0, _ = load_workload("random_24e30o")
+    w, h1, eri, ec, A, B, c, E0, _ = load_workload(args.pt2_workload)
     dev = torch.device("cuda", 0)
     d = torch.tensor(np.stack([A, B], 1).astype(np.int64), device=dev)
     cf, h1d, ed = (torch.tensor(x, device=dev) for x in (c, h1, eri))
@@ -390,10 +393,10 @@ def run_pt2(args):
         times.append(e0.elapsed_time(e1))
     ms = statistics.mean(times)
     print(json.dumps({
-        "metric": "ASCI-PT2 scored excitations/s at (24e,30o)", "unit": "excitations/s",
+        "metric": f"ASCI-PT2 scored excitations/s on {w.name}", "unit": "excitations/s",
         "value": st.generated / (ms / 1e3), "ms_per_step": ms, "higher_is_better": True,
         "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": "f64",
-        "config": {"workload": "random_24e30o pt2", "C": w.C, "ndets": w.ndets,
+        "config": {"workload": f"{w.name} pt2", "C": w.C, "ndets": w.ndets,
                    "l2": "flushed (512 MB write) before each step"},
         "e_pt2": val, "targets": st.unique - st.excluded, "generated": st.generated,
         "batches": st.batches, "stage_ms": {k: round(v, 3) for k, v in st.t_stage_ms.items()}}),

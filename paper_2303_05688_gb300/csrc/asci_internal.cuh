@@ -296,6 +296,16 @@ __device__ __forceinline__ uint32_t full_mask(int n) {
   return n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
 }
 
+// 1/x to FP64 accuracy from the FP32 estimate __frcp_rn and two
+// Newton-Raphson steps y <- y(2 - xy) (each squares the relative error:
+// 2^-23 -> 2^-46 -> 2^-92), for |x| in [1e-30, 1e30].  GB300 has little FP64
+// throughput, and this avoids the longer FP64 division sequence.
+__device__ __forceinline__ double recip_fast(double x) {
+  double y = (double)__frcp_rn((float)x);
+  y = y * fma(-x, y, 2.0);
+  return y * fma(-x, y, 2.0);
+}
+
 // Counts of one determinant's excitations (Sec. 2.1: singles and doubles).
 struct ExcCounts {
   uint32_t na, nb, va, vb;

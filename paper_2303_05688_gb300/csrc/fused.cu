@@ -2168,9 +2168,59 @@ __device__ __forceinline__ void pt2_add(double t, long long *acc, unsigned *bad)
   const unsigned long long lo = m << o;
   const unsigned long long hi = o ? (m >> (64 - o)) : 0ull;
   const long long sg = t < 0.0 ? -1 : 1;
-  acc[k0] += sg * (long long)(lo & 0xffffffffull);
-  if (k0 + 1 < kPt2Limbs) acc[k0 + 1] += sg * (long long)(lo >> 32);
-  if (k0 + 2 < kPt2Limbs) acc[k0 + 2] += sg * (long long)(hi & 0xffffffffull);
+  const long long l0 = sg * (long long)(lo & 0xffffffffull), l1 = sg * (long long)(lo >> 32),
+                  l2 = sg * (long long)(hi & 0xffffffffull);
+  // selects, not indexing, so that acc stays in registers
+#pragma unroll
+  for (int k = 0; k < kPt2Limbs; ++k)
+    acc[k] += k == k0 ? l0 : (k == k0 + 1 ? l1 : (k == k0 + 2 ? l2 : 0ll));
+}
+
+// The exact fixed-point H_ii of the 32 targets of a warp (lanes with live
+// false take no part), equal bit for bit to fx_diag.  Targets of one tile
+// mostly share their alpha string, so the alpha part is formed once per
+// distinct alpha string of the warp (at most four; any others take fx_diag):
+// D_a = sum_{p in A} h_pp + sum_{p<r in A} jk_pr by the lanes p of A, and
+// J_A[q] = sum_{p in A} jj_pq by lane q; each lane then adds its beta part
+// sum_{q in B} (h_qq + J_A[q]) + sum_{q<r in B} jk_qr.
+__device__ __forceinline__ int64_t warp_diag(const FxInts &X, uint32_t A, uint32_t B,
+                                             bool live) {
+  const int n = X.n;
+  const uint32_t lane = threadIdx.x & 31u;
+  int64_t diag = 0;
+  uint32_t pending = __ballot_sync(0xffffffffu, live);
+  for (int round = 0; pending && round < 4; ++round) {
+    const uint32_t AL = __shfl_sync(0xffffffffu, A, __ffs(pending) - 1);
+    int64_t part = 0, ja = 0;
+    if ((int)lane < n) {
+      if ((AL >> lane) & 1u) {
+        part = X.hh[lane];
+        for (uint32_t r = AL & ~((2u << lane) - 1u); r; r &= r - 1)
+          part += X.jk[lane * n + __ffs(r) - 1];
+      }
+      for (uint32_t p = AL; p; p &= p - 1) ja += X.jj[(__ffs(p) - 1) * n + lane];
+    }
+    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const bool mine = live && A == AL && ((pending >> lane) & 1u);
+    const uint32_t group = __ballot_sync(0xffffffffu, mine);
+    int64_t cross = 0;
+    for (int q = 0; q < n; ++q) {
+      const int64_t t = __shfl_sync(0xffffffffu, ja, q);
+      if (mine && ((B >> q) & 1u)) cross += t;
+    }
+    if (mine) {
+      int64_t s = X.ecore_x + part + cross;
+      for (uint32_t m = B; m; m &= m - 1) {
+        const int q = __ffs(m) - 1;
+        s += X.hh[q];
+        for (uint32_t r = m & (m - 1); r; r &= r - 1) s += X.jk[q * n + __ffs(r) - 1];
+      }
+      diag = s;
+    }
+    pending &= ~group;
+  }
+  if (live && ((pending >> lane) & 1u)) diag = fx_diag(X, A, B);
+  return diag;
 }
 
 __global__ void __launch_bounds__(256) k_pt2_terms(const uint64_t *key, const double *num,
@@ -2181,12 +2231,19 @@ __global__ void __launch_bounds__(256) k_pt2_terms(const uint64_t *key, const do
   long long acc[kPt2Limbs];
   for (int k = 0; k < kPt2Limbs; ++k) acc[k] = 0;
   unsigned bad = 0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const uint64_t k = key[i];
-    const int64_t den_x = E0_x - fx_diag(X, key_alpha(k), (uint32_t)(k >> 32));
+  // warp-uniform loop: warp_diag needs every lane
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t base = (size_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n;
+       base += stride) {
+    const size_t i = base + (threadIdx.x & 31u);
+    const bool live = i < n;
+    const uint64_t k = live ? key[i] : 0ull;
+    const int64_t dg = warp_diag(X, key_alpha(k), (uint32_t)(k >> 32), live);
+    if (!live) continue;
+    const double den = __ll2double_rn(E0_x - dg) * inv_scale;
     const double v = num[i];
-    pt2_add(v * (v / (__ll2double_rn(den_x) * inv_scale)), acc, &bad);
+    const double r = (fabs(den) >= 1e-30 && fabs(den) <= 1e30) ? recip_fast(den) : 1.0 / den;
+    pt2_add(v * v * r, acc, &bad);
   }
   if (bad) atomicOr(err, kErrAccum);
   for (int k = 0; k < kPt2Limbs; ++k)

@@ -504,16 +504,10 @@ __global__ void k_normalize(double *v, size_t n, const double *norm2) {
 // but for its last row and column and two or three sweeps finish it.
 constexpr int kEigThreads = 256;
 
-// 1/x and 1/sqrt(x) to FP64 accuracy from the FP32 estimates (__frcp_rn,
-// rsqrtf) and two Newton-Raphson steps each (y <- y(2 - xy) and
-// y <- y(3 - xy^2)/2; each step squares the relative error, 2^-23 -> 2^-92),
-// valid for |x| in [1e-30, 1e30]; GB300 has little FP64 throughput, and this
-// avoids the longer FP64 division and square-root sequences.
-__device__ __forceinline__ double recip_fast(double x) {
-  double y = (double)__frcp_rn((float)x);
-  y = y * fma(-x, y, 2.0);
-  return y * fma(-x, y, 2.0);
-}
+// 1/sqrt(x) to FP64 accuracy from the FP32 estimate rsqrtf and two
+// Newton-Raphson steps y <- y(3 - xy^2)/2 (2^-23 -> 2^-92), for x in
+// [1e-30, 1e30]; with recip_fast it avoids the FP64 division and square-root
+// sequences.
 __device__ __forceinline__ double rsqrt_fast(double x) {
   double y = (double)rsqrtf((float)x);
   y = y * fma(-0.5 * x, y * y, 1.5);
