@@ -238,6 +238,30 @@ int asci_sort_accumulate_noalloc(const asci_det *keys, const double *values, siz
                                  asci_det *out_keys, double *out_sums, size_t *out_n,
                                  void *cuda_stream);
 
+/*
+ * Building blocks of a top-N selection across ranks (the role of Alg. 4: the
+ * global N largest |score| of candidates spread over processes, found without
+ * gathering them).  The rank word of an entry is the 128-bit unsigned
+ * R = (~bits(|score|), key), words {hi, lo}: ascending R is |score|
+ * descending, then key ascending (keys distinct), so the global top N are the
+ * entries with R <= R_N.  A caller finds R_N byte by byte from the most
+ * significant end, summing the ranks' histograms (an all-reduce of 256
+ * counters per byte), then keeps its entries at or below R_N.
+ *
+ * asci_select_histogram: hist[256] (host memory, out) counts the entries whose
+ * R agrees with prefix on the bits set in mask, by the value of byte `digit`
+ * of R (15: the most significant byte of hi ... 0: the least significant byte
+ * of lo).  n may be 0 (a zero histogram).
+ * asci_select_below: the entries with R <= threshold (out_* hold n entries;
+ * order unspecified).
+ */
+int asci_select_histogram(const asci_det *keys, const double *scores, size_t n, int32_t digit,
+                          const uint64_t prefix[2], const uint64_t mask[2], uint64_t hist[256],
+                          void *cuda_stream);
+int asci_select_below(const asci_det *keys, const double *scores, size_t n,
+                      const uint64_t threshold[2], asci_det *out_keys, double *out_scores,
+                      size_t *out_n, void *cuda_stream);
+
 /* One independent search of a batch (asci_search_many): the arguments of
  * asci_search, and its result code. */
 typedef struct {

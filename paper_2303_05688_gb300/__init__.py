@@ -21,7 +21,7 @@ __all__ = ["load", "lib_path", "launch_count", "search", "excitations", "diagona
            "select_topn", "SearchStats", "AsciError", "FP64", "FP32_INT_FP64_ACC",
            "FP32_INT_COMP_ACC", "shard_assign", "gather_candidates", "sharded_search",
            "search_many", "tune_streams", "hamiltonian", "spmv", "davidson", "asci_loop",
-           "LoopStats", "pt2"]
+           "LoopStats", "pt2", "select_histogram", "select_below", "distributed_topn"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "lib", "libasci.so")
@@ -164,6 +164,10 @@ def load():
     lib.asci_diagonal.argtypes = [ct.POINTER(_Ints), vp, sz, vp, vp]
     lib.asci_sort_accumulate.restype = ct.c_int
     lib.asci_sort_accumulate.argtypes = [vp, vp, sz, vp, vp, szp, vp]
+    lib.asci_select_histogram.restype = ct.c_int
+    lib.asci_select_histogram.argtypes = [vp, vp, sz, ct.c_int32, vp, vp, vp, vp]
+    lib.asci_select_below.restype = ct.c_int
+    lib.asci_select_below.argtypes = [vp, vp, sz, vp, vp, vp, szp, vp]
     lib.asci_select_topn.restype = ct.c_int
     lib.asci_select_topn.argtypes = [vp, vp, sz, sz, vp, vp, szp, vp]
     lib.asci_shard_assign.argtypes = [vp, sz, ct.c_int32, vp, vp]
@@ -525,20 +529,93 @@ def gather_candidates(keys, scores, group=None):
             torch.cat([v[:c] for v, c in zip(sl, counts)]))
 
 
+def select_histogram(keys, scores, digit: int, prefix, mask, stream=None):
+    """Histogram (numpy uint64[256]) of byte `digit` of the rank word
+    (~bits(|score|), key) over the entries matching prefix on mask (device)."""
+    lib = load()
+    kb = _dets_buf(keys)
+    sb = _as_buf(scores, np.float64, "float64")
+    n = int(kb.obj.shape[0])
+    pre = np.ascontiguousarray(prefix, dtype=np.uint64)
+    msk = np.ascontiguousarray(mask, dtype=np.uint64)
+    h = np.zeros(256, dtype=np.uint64)
+    _check(lib.asci_select_histogram(kb.ptr if n else None, sb.ptr if n else None, n, int(digit),
+                                     pre.ctypes.data, msk.ctypes.data, h.ctypes.data,
+                                     _stream_ptr(stream, kb.device)), "asci_select_histogram")
+    return h
+
+
+def select_below(keys, scores, threshold, stream=None):
+    """The entries whose rank word is at most threshold ({hi, lo}) (device)."""
+    torch = _torch()
+    lib = load()
+    kb = _dets_buf(keys)
+    sb = _as_buf(scores, np.float64, "float64")
+    n = int(kb.obj.shape[0])
+    ok = torch.empty((max(n, 1), 2), dtype=torch.int64, device="cuda")
+    os_ = torch.empty(max(n, 1), dtype=torch.float64, device="cuda")
+    thr = np.ascontiguousarray(threshold, dtype=np.uint64)
+    n_out = ct.c_size_t(0)
+    _check(lib.asci_select_below(kb.ptr if n else None, sb.ptr if n else None, n, thr.ctypes.data,
+                                 ok.data_ptr(), os_.data_ptr(), ct.byref(n_out),
+                                 _stream_ptr(stream, True)), "asci_select_below")
+    return ok[:n_out.value], os_[:n_out.value]
+
+
+_ALL = (1 << 64) - 1
+
+
+def distributed_topn(keys, scores, N: int, group=None, hist_fn=None, below_fn=None):
+    """The global top N (|score| descending, key ascending) of candidates
+    spread over the ranks of a torch.distributed group, the role of Alg. 4:
+    the N-th rank word is found byte by byte from the most significant end,
+    each byte by an all-reduce of the ranks' 256-bin histograms (2 KB), then
+    each rank keeps its entries at or below it and the winners, N in all, are
+    gathered to every rank.  hist_fn(digit, prefix, mask) and
+    below_fn(threshold) are the local steps (the library's kernels by
+    default).  Returns (keys, scores) of the global top N on every rank."""
+    torch = _torch()
+    import torch.distributed as dist
+    hist_fn = hist_fn or (lambda d, p, m: select_histogram(keys, scores, d, p, m))
+    below_fn = below_fn or (lambda t: select_below(keys, scores, t))
+    dev = keys.device
+    total = torch.tensor([keys.shape[0]], dtype=torch.int64, device=dev)
+    dist.all_reduce(total, group=group)
+    thr = [_ALL, _ALL]
+    if int(total.item()) > N:
+        pre, msk, remaining = [0, 0], [0, 0], N
+        for digit in range(15, -1, -1):
+            h = torch.tensor(np.asarray(hist_fn(digit, [w & _ALL for w in pre],
+                                                [w & _ALL for w in msk])).astype(np.int64),
+                             device=dev)
+            dist.all_reduce(h, group=group)
+            h = h.cpu().numpy()
+            cum = np.cumsum(h)
+            d = int(np.searchsorted(cum, remaining))  # first byte value reaching `remaining`
+            remaining -= int(cum[d - 1]) if d else 0
+            word, shift = (0, 8 * (digit - 8)) if digit >= 8 else (1, 8 * digit)
+            pre[word] |= d << shift
+            msk[word] |= 0xff << shift
+            if int(h[d]) == remaining:  # the whole bucket is in: all lower bits free
+                thr = [pre[0] | (~msk[0] & _ALL), pre[1] | (~msk[1] & _ALL)]
+                break
+            thr = list(pre)
+    wk, ws = below_fn(thr)
+    return gather_candidates(wk, ws, group)
+
+
 def sharded_search(dets, coeffs, E0: float, h1, eri, ecore: float, C: int, N: int, *,
                    group=None, **kw):
     """One search sharded over the ranks of a torch.distributed group (one GPU
     per rank): each rank searches its shard of the target alpha classes and
-    keeps its top N; the ranks exchange those lists and every rank selects the
-    global top N from the union (the shards partition the targets, so this is
-    the unsharded result).  Returns (dets, scores, local stats)."""
+    keeps its top N; the global top N of the union is then selected across the
+    ranks (distributed_topn) without gathering the shards' lists (the shards
+    partition the targets, so this is the unsharded result).  Returns (dets,
+    scores, local stats) with the global top N on every rank."""
     import torch.distributed as dist
     r, W = dist.get_rank(group), dist.get_world_size(group)
     od, osc, st = search(dets, coeffs, E0, h1, eri, ecore, C, N, shard=(r, W), **kw)
-    ak, asc = gather_candidates(od, osc, group)
-    if ak.shape[0] == 0:
-        return ak, asc, st
-    gk, gs = select_topn(ak, asc, N)
+    gk, gs = distributed_topn(od, osc, N, group)
     return gk, gs, st
 
 

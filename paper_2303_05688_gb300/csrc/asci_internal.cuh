@@ -359,6 +359,15 @@ int diagonal_packed(const DevInts &I, const uint64_t *keys, size_t n, double *ou
 int select_topn_packed(const uint64_t *keys, const double *scores, size_t n, size_t N,
                        uint64_t *out_keys, double *out_scores, size_t *host_out_n, Arena &arena);
 
+// Histogram of byte `digit` of the rank word (~bits(|S|), key) over entries
+// matching pre on the bits of msk ({hi, lo}); hist is host memory.
+int select_histogram(const uint64_t *keys, const double *scores, size_t n, int digit,
+                     const uint64_t pre[2], const uint64_t msk[2], uint64_t hist[256],
+                     Arena &arena);
+// Entries whose rank word is at most thr ({hi, lo}), compacted.
+int select_below(const uint64_t *keys, const double *scores, size_t n, const uint64_t thr[2],
+                 uint64_t *out_keys, double *out_scores, size_t *host_out_n, Arena &arena);
+
 // Excitation emission in the fixed per-determinant order (component entry).
 int emit_fixed_order(const DevInts &I, const uint64_t *core_keys, const double *core_c,
                      size_t ncore, uint64_t *out_keys, double *out_vals, Arena &arena);

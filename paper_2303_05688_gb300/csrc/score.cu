@@ -242,4 +242,43 @@ int select_topn_packed(const uint64_t *keys, const double *scores, size_t n, siz
   return ASCI_OK;
 }
 
+// Building blocks of a selection across ranks: the histogram of one byte of
+// the rank word over the entries that match a prefix, and the entries at or
+// below a rank threshold.
+int select_histogram(const uint64_t *keys, const double *scores, size_t n, int digit,
+                     const uint64_t pre[2], const uint64_t msk[2], uint64_t hist[256],
+                     Arena &arena) {
+  cudaStream_t s = arena.stream();
+  unsigned long long *dhist;
+  ASCI_TRY(arena.alloc(&dhist, 256));
+  ASCI_TRY_CUDA(cudaMemsetAsync(dhist, 0, 256 * sizeof(unsigned long long), s));
+  if (n) {
+    k_select_hist<<<grid_for(n), 256, 0, s>>>(keys, scores, n, digit, pre[0], pre[1], msk[0],
+                                              msk[1], dhist);
+    ASCI_CHECK_LAUNCH();
+  }
+  ASCI_TRY_CUDA(cudaMemcpyAsync(hist, dhist, 256 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  return ASCI_OK;
+}
+
+int select_below(const uint64_t *keys, const double *scores, size_t n, const uint64_t thr[2],
+                 uint64_t *out_keys, double *out_scores, size_t *host_out_n, Arena &arena) {
+  *host_out_n = 0;
+  if (!n) return ASCI_OK;
+  cudaStream_t s = arena.stream();
+  uint32_t *flag, *pos;
+  ASCI_TRY(arena.alloc(&flag, n));
+  ASCI_TRY(arena.alloc(&pos, n));
+  k_select_flags<<<grid_for(n), 256, 0, s>>>(keys, scores, n, thr[0], thr[1], flag);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(scan_exclusive_u32(flag, pos, n, arena));
+  size_t m = 0;
+  ASCI_TRY(kept_count(flag, pos, n, &m, arena));
+  ASCI_TRY(compact_u64(keys, flag, pos, n, out_keys, arena));
+  ASCI_TRY(compact_f64(scores, flag, pos, n, out_scores, arena));
+  *host_out_n = m;
+  return ASCI_OK;
+}
+
 }  // namespace asci

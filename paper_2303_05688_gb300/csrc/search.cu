@@ -1379,6 +1379,63 @@ int asci_shard_assign(const uint64_t *weights, size_t n, int32_t shards,
   return ASCI_OK;
 }
 
+int asci_select_histogram(const asci_det *keys, const double *scores, size_t n, int32_t digit,
+                          const uint64_t prefix[2], const uint64_t mask[2], uint64_t hist[256],
+                          void *cuda_stream) {
+  if ((n && (!keys || !scores)) || !prefix || !mask || !hist || digit < 0 || digit > 15)
+    return ASCI_EINVAL;
+  if (n >= (1ull << 32)) return ASCI_EINVAL;
+  cudaStream_t s;
+  ASCI_TRY(begin_call(cuda_stream, &s));
+  Arena arena(s);
+  uint64_t *k = nullptr;
+  const double *ds = nullptr;
+  if (n) {
+    const asci_det *dk;
+    ASCI_TRY(to_device(keys, n, &dk, arena));
+    ASCI_TRY(to_device(scores, n, &ds, arena));
+    ASCI_TRY(arena.alloc(&k, n));
+    k_input_keys<<<grid_for(n), 256, 0, s>>>(dk, n, k);
+    ASCI_CHECK_LAUNCH();
+  }
+  return select_histogram(k, ds, n, digit, prefix, mask, hist, arena);
+}
+
+int asci_select_below(const asci_det *keys, const double *scores, size_t n,
+                      const uint64_t threshold[2], asci_det *out_keys, double *out_scores,
+                      size_t *out_n, void *cuda_stream) {
+  if (out_n) *out_n = 0;
+  if (!out_n || !threshold || (n && (!keys || !scores || !out_keys || !out_scores)))
+    return ASCI_EINVAL;
+  if (n >= (1ull << 32)) return ASCI_EINVAL;
+  if (n == 0) return ASCI_OK;
+  cudaStream_t s;
+  ASCI_TRY(begin_call(cuda_stream, &s));
+  Arena arena(s);
+  const asci_det *dk;
+  const double *ds;
+  ASCI_TRY(to_device(keys, n, &dk, arena));
+  ASCI_TRY(to_device(scores, n, &ds, arena));
+  uint64_t *k, *ok;
+  double *os;
+  asci_det *dok;
+  ASCI_TRY(arena.alloc(&k, n));
+  ASCI_TRY(arena.alloc(&ok, n));
+  ASCI_TRY(out_buffer(out_scores, n, &os, arena));
+  ASCI_TRY(out_buffer(out_keys, n, &dok, arena));
+  k_input_keys<<<grid_for(n), 256, 0, s>>>(dk, n, k);
+  ASCI_CHECK_LAUNCH();
+  size_t m = 0;
+  ASCI_TRY(select_below(k, ds, n, threshold, ok, os, &m, arena));
+  k_unpack<<<grid_for(m), 256, 0, s>>>(ok, m, dok);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(finish_out(out_scores, os, m, s));
+  ASCI_TRY(finish_out(out_keys, dok, m, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  *out_n = m;
+  return ASCI_OK;
+}
+
 int asci_select_topn(const asci_det *keys, const double *scores, size_t n, size_t N,
                      asci_det *out_keys, double *out_scores, size_t *out_n,
                      void *cuda_stream) {

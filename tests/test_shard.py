@@ -137,3 +137,97 @@ def test_union_of_local_topn_is_global_topn():
         uk = np.concatenate(local)
         us = np.array([score_of[k] for k in uk.tolist()])
         assert np.array_equal(top(uk, us, N), top(keys, s, N))
+
+
+# --------------------------------------------------------------------------
+# distributed top-N: byte-wise radix select with an all-reduce per byte
+# --------------------------------------------------------------------------
+
+def _rank_words(keys, s):
+    """(hi, lo) rank words of the library's selection: ~bits(|s|), packed key
+    (beta word high, alpha word low), as Python integers."""
+    out = []
+    for (a, b), v in zip(keys.tolist(), s.tolist()):
+        bits = int(np.array([abs(v)], dtype=np.float64).view(np.uint64)[0])
+        out.append((~bits & ((1 << 64) - 1), ((b & 0xffffffff) << 32) | (a & 0xffffffff)))
+    return out
+
+
+def _np_hist(keys, s, digit, pre, msk):
+    h = np.zeros(256, dtype=np.uint64)
+    for hi, lo in _rank_words(keys, s):
+        if (hi & msk[0]) == pre[0] and (lo & msk[1]) == pre[1]:
+            d = (hi >> (8 * (digit - 8))) & 0xff if digit >= 8 else (lo >> (8 * digit)) & 0xff
+            h[d] += 1
+    return h
+
+
+def _np_below(keys, s, thr):
+    keep = [i for i, (hi, lo) in enumerate(_rank_words(keys, s))
+            if hi < thr[0] or (hi == thr[0] and lo <= thr[1])]
+    import torch
+    return keys[keep] if keep else keys[:0], s[keep] if keep else s[:0]
+
+
+def _select_worker(rank, world, port, q, seed, N):
+    import torch
+    import torch.distributed as dist
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import paper_2303_05688_gb300 as asci
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        keys, s = _select_case(seed, world)
+        part = np.arange(len(keys)) % world == rank
+        k = torch.tensor(keys[part], dtype=torch.int64)
+        v = torch.tensor(s[part], dtype=torch.float64)
+        gk, gs = asci.distributed_topn(
+            k, v, N, hist_fn=lambda d, p, m: _np_hist(k, v, d, p, m),
+            below_fn=lambda t: _np_below(k, v, t))
+        q.put((rank, gk.numpy().tolist(), gs.numpy().tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+def _select_case(seed, world):
+    rng = np.random.default_rng(seed)
+    n = 60 + 7 * world
+    alpha = rng.permutation(1000)[:n]
+    beta = rng.integers(0, 4, n)
+    keys = np.stack([alpha, beta], 1).astype(np.int64)
+    s = rng.normal(size=n)
+    s[rng.random(n) < 0.3] = 0.25   # ties in |S| decided by the key
+    s[rng.random(n) < 0.1] = -0.25
+    return keys, s
+
+
+@pytest.mark.parametrize("world,N", [(2, 17), (3, 40), (2, 500)])
+def test_distributed_topn_gloo(world, N):
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    seed = 100 + world
+    procs = [ctx.Process(target=_select_worker, args=(r, world, port, q, seed, N))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in range(world):
+        r, k, s = q.get(timeout=120)
+        res[r] = (k, s)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    keys, s = _select_case(seed, world)
+    # brute force: |S| descending, then the packed key (beta high) ascending
+    packed = (keys[:, 1] << 32) | keys[:, 0]
+    o = np.lexsort((packed, -np.abs(s)))[:N]
+    want = sorted(zip(packed[o].tolist(), s[o].tolist()))
+    for r in range(world):
+        gk = np.array(res[r][0], dtype=np.int64).reshape(-1, 2)
+        got = sorted(zip(((gk[:, 1] << 32) | gk[:, 0]).tolist(), res[r][1]))
+        assert got == want
