@@ -127,10 +127,11 @@ __device__ double offdiag_element(const DevInts &I, uint32_t ai, uint32_t bi, ui
 // so a row only has to visit the groups whose beta string is within two
 // excitations of its own (the group graph, built once per list by a tiled
 // double loop over the G group strings), and inside such a group only the
-// alpha test remains, with the threshold 4 - popc(beta_i ^ beta_j).  A warp
-// takes a row and walks its neighbour groups in ascending order, 32 columns
-// at a time; a ballot places the hits, so each row's columns come out
-// ascending.  A counting pass gives the row lengths, a scan the row
+// alpha test remains, with the threshold 4 - popc(beta_i ^ beta_j) (for beta
+// strings a double apart, alpha_j must equal alpha_i: a binary search in the
+// alpha-sorted group).  A warp takes a row and walks its neighbour groups in
+// ascending order, 32 columns at a time; a ballot places the hits, so each
+// row's columns come out ascending.  A counting pass gives the row lengths, a scan the row
 // pointers, and the filling pass writes (never past a row's counted end).
 
 // head[i] = 1 where a new beta string starts (keys sorted)
@@ -271,6 +272,20 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_ham_rows(
         gs = gstart[g2];
         len = gstart[g2 + 1] - gs;
         thr = 4 - __popc(bi ^ gbeta[g2]);
+        if (thr == 0) {
+          // beta strings a double apart: only alpha_j == alpha_i connects, and
+          // the group is sorted by alpha, so one binary search replaces the
+          // walk (the group becomes that one column, or nothing)
+          uint32_t lo = gs, hi = gs + len;
+          while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (key_alpha(keys[mid]) < ai) lo = mid + 1;
+            else hi = mid;
+          }
+          const bool found = lo < gs + len && key_alpha(keys[lo]) == ai;
+          gs = lo;
+          len = found ? 1u : 0u;
+        }
       }
       uint32_t off = len;  // inclusive scan of the lengths
       for (int o = 1; o < 32; o <<= 1) {
