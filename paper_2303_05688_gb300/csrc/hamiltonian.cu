@@ -1,15 +1,18 @@
 // The variational step of the ASCI loop (Algorithm 1, "diagonalize the
 // Hamiltonian in the selected determinant space"; Sec. 2.3).
 //
-//  * H over a determinant list by the double loop approach of Sec. 2.3: every
-//    ordered pair (i, j) is tested for an excitation degree of at most two
-//    (popcount of the XOR of the packed keys <= 4); connected pairs get H_ij by
-//    the Slater-Condon rules and nonzero elements are stored in CSR.  A CTA
-//    owns 256 rows (one per thread, the row key in a register) and one slice of
-//    the columns, whose keys it stages through shared memory and reads as
-//    broadcasts.  A counting pass writes the nonzeros of every (row, slice); a
-//    scan turns them into write offsets, so the filling pass stores every row's
-//    columns in ascending order without atomics.
+//  * H over a determinant list (Sec. 2.3, CSR): the paper's double loop over
+//    determinant pairs, pruned by the structure of the keys.  In key order
+//    (beta word high) each beta string's determinants are one group; a row
+//    visits only the groups whose beta string is within two excitations (a
+//    group graph built by a tiled double loop over the beta strings), tests
+//    the alpha distance against 4 - popc(beta_i ^ beta_j), and for groups a
+//    beta double away looks its own alpha string up by binary search.
+//    Connected pairs get H_ij by the Slater-Condon rules, evaluated 32 at a
+//    time from a per-warp queue; nonzero elements are stored, each row's
+//    columns ascending.  A counting pass and a scan give the row pointers, the
+//    filling pass the elements; rows in the caller's order come from one sort
+//    of the key-ordered entries.
 //  * y = H x (Algorithm 6 on one device): a warp per row, lanes strided over
 //    the row, a fixed shuffle tree: the same bits on every call.
 //  * Davidson (Algorithm 5): basis V and products W = H V resident on the
@@ -22,7 +25,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <vector>
 
 #include "asci_internal.cuh"
 
