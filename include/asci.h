@@ -317,7 +317,7 @@ int asci_select_topn(const asci_det *keys, const double *scores, size_t n, size_
 /*
  * The Hamiltonian restricted to a determinant list, as a sparse matrix in
  * compressed sparse row form (Sec. 2.3: the double loop approach over pairs of
- * determinants, CSR storage).  Row and column i belong to dets[i].  Row i holds
+ * determinants, here pruned by beta-string groups; CSR storage).  Row and column i belong to dets[i].  Row i holds
  * its diagonal element H_ii and every H_ij != 0 with dets[j] singly or doubly
  * excited from dets[i] (by the Slater-Condon rules of the conventions above),
  * columns ascending; the matrix is symmetric.
