@@ -1041,6 +1041,21 @@ __device__ __forceinline__ uint64_t mix_key(uint64_t z) {
   return z;
 }
 
+// Slot hash of the tile's table (2048 slots): the 32-bit finalizer of
+// MurmurHash3 (Appleby) over the alpha word times an odd constant xor the beta
+// word.  Bucket tiles hold one alpha string and the betas of one bucket, so
+// the finalizer's avalanche is what spreads them; cheaper than mix_key's two
+// 64-bit products.
+__device__ __forceinline__ uint32_t slot_hash(uint64_t key) {
+  uint32_t h = (uint32_t)key * 0x9E3779B1u ^ (uint32_t)(key >> 32);
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h & (uint32_t)(kSlots - 1);
+}
+
 // Open addressing with linear probing; the table is at most 1/4 full, and the
 // probe count is bounded by the table size (exceeding it sets *err).
 __device__ __forceinline__ bool psi_contains(const uint64_t *ht, uint64_t mask, uint64_t key,
@@ -1229,7 +1244,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
       // psi markers: claim a slot, or flag the slot a record already holds
       for (uint32_t q = threadIdx.x; q < npsi; q += kCellThreads) {
         const uint64_t key = S.psik[buf][q];
-        uint32_t h = (uint32_t)mix_key(key) & (kSlots - 1);
+        uint32_t h = slot_hash(key);
         uint16_t claimed = kEndList;
         int probe = 0;
         for (; probe < kSlots; ++probe) {
@@ -1259,7 +1274,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
         int claimed = -1;
         if (e < nrec && !is_dropped(S.rec[buf][e].v)) {
           const uint64_t key = rec_key(S, buf, (uint32_t)e, packed, d.alpha);
-          uint32_t h = (uint32_t)mix_key(key) & (kSlots - 1);
+          uint32_t h = slot_hash(key);
           int probe = 0;
           for (; probe < kSlots; ++probe) {
             uint32_t cur = S.slot[h];
