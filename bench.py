@@ -617,6 +617,10 @@ def main():
                 "alg_bytes_per_launch": bytes_per_launch, "ms_per_launch": per_launch_s * 1e3,
                 "search": {"alg_bytes_per_step": b_alg, "achieved": b_alg / t_search / 1e9,
                            "frac": b_alg / t_search / 1e9 / peak},
+                # the sort-and-accumulate rate: staged pairs reduced per second
+                # of the on-chip tile kernel and the global-sort path together
+                "accumulate_pairs_per_s": (stats.tile_records + stats.oversized_records) / max(
+                    (ts["tiles"] + ts["oversized"]) / 1e3, 1e-12),
                 "stage_ms": {k: round(v, 3) for k, v in ts.items()}}
 
     cpu = None
