@@ -90,3 +90,16 @@ def test_pt2_rejects_vanishing_denominators(torch_cuda, asci):
     E0 = float(np.trace(h1[:4, :4]) * 2 + 4 * 4.0)
     with pytest.raises(asci.AsciError, match="PT2 term"):
         asci.pt2(_dev(torch, A, A.copy()), torch.tensor([1.0], device="cuda"), E0, h1, eri, ec, 1)
+
+
+def test_pt2_with_screening(torch_cuda, asci, oracle_mod):
+    """eps_search > 0 screens pairs as Alg. 2 does (|H_ij c_j / (E0 - H_ii)| >
+    eps) before the PT2 sum."""
+    torch = torch_cuda
+    h1, eri, ec, A, B, c, E0 = _system("random_12e12o")
+    for eps in (1e-6, 1e-4):
+        ref = oracle_mod.pt2(oracle_mod.Ints(h1, eri, ec), A, B, c, E0, 2000, eps)
+        e, st = asci.pt2(_dev(torch, A, B), torch.tensor(c, device="cuda"), E0, h1, eri, ec, 2000,
+                         eps=eps)
+        assert abs(e - ref) <= 1e-9 * abs(ref), (eps, e, ref)
+        assert st.surviving < st.generated

@@ -335,3 +335,54 @@ def test_asci_loop_rejects_bad_options(torch_cuda, asci):
     with pytest.raises(asci.AsciError):
         asci.asci_loop(_dev(torch, A, B), torch.tensor(c, device="cuda"), h1, eri, ec, ncdets=5,
                        ntdets=10, max_subspace=1)
+
+
+# ------------------------------------------------------- host-memory paths ---
+
+def test_host_pointer_paths(torch_cuda, asci, oracle_mod):
+    """asci_hamiltonian, asci_spmv, asci_davidson and asci_loop with every
+    array in host memory (the library stages them) give what the device paths
+    give."""
+    import ctypes as ct
+    torch = torch_cuda
+    lib = asci.load()
+    h1, eri, ec = W.random_molecular(8, 5)
+    A, B = W.random_walk_dets(8, 4, 4, 500, seed=5)
+    n = len(A)
+    dets = np.ascontiguousarray(np.stack([A, B], 1).astype(np.uint64))
+    keep = []
+    ints, _ = asci._ints(h1, eri, ec, keep)
+    rp = np.empty(n + 1, dtype=np.int64)
+    nnz = ct.c_size_t(0)
+    assert lib.asci_hamiltonian(dets.ctypes.data, n, ct.byref(ints), rp.ctypes.data, None, None,
+                                0, ct.byref(nnz), None) == 0
+    col = np.empty(nnz.value, dtype=np.int32)
+    val = np.empty(nnz.value, dtype=np.float64)
+    assert lib.asci_hamiltonian(dets.ctypes.data, n, ct.byref(ints), rp.ctypes.data,
+                                col.ctypes.data, val.ctypes.data, nnz.value, ct.byref(nnz),
+                                None) == 0
+    Hd = asci.hamiltonian(_dev(torch, A, B), h1, eri, ec)
+    assert np.array_equal(rp, Hd[0].cpu().numpy()) and np.array_equal(col, Hd[1].cpu().numpy())
+    assert np.array_equal(val, Hd[2].cpu().numpy())
+    x = np.random.default_rng(2).normal(size=n)
+    y = np.empty(n)
+    assert lib.asci_spmv(rp.ctypes.data, col.ctypes.data, val.ctypes.data, n, x.ctypes.data,
+                         y.ctypes.data, None) == 0
+    assert np.array_equal(y, asci.spmv(Hd, torch.tensor(x, device="cuda")).cpu().numpy())
+    o = asci._DavOpts(16, 500, 1e-10)
+    e, it, res = ct.c_double(0), ct.c_int32(0), ct.c_double(0)
+    vec = np.empty(n)
+    assert lib.asci_davidson(rp.ctypes.data, col.ctypes.data, val.ctypes.data, n, None,
+                             ct.byref(o), ct.byref(e), vec.ctypes.data, ct.byref(it),
+                             ct.byref(res), None) == 0
+    Ed, vd, _, _ = asci.davidson(Hd, None, max_subspace=16, max_iter=500, tol=1e-10)
+    assert e.value == Ed and np.array_equal(vec, vd.cpu().numpy())
+    # the loop with numpy inputs returns numpy outputs equal to the device run
+    a0 = np.array([W.aufbau(4)], dtype=np.uint64)
+    hd, hc, hE, _ = asci.asci_loop(np.stack([a0, a0], 1), np.ones(1), h1, eri, ec, ncdets=5,
+                                   ntdets=300, max_steps=2, tol=1e-10)
+    dd, dc, dE, _ = asci.asci_loop(_dev(torch, a0, a0), torch.ones(1, dtype=torch.float64,
+                                                                    device="cuda"),
+                                   h1, eri, ec, ncdets=5, ntdets=300, max_steps=2, tol=1e-10)
+    assert isinstance(hd, np.ndarray) and hE == dE
+    assert np.array_equal(hd.view(np.int64), dd.cpu().numpy()) and np.array_equal(hc, dc.cpu().numpy())
