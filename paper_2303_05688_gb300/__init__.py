@@ -1,7 +1,11 @@
-"""Python binding of libasci, the GB300 ASCI determinant search (arXiv:2303.05688).
+"""Python binding of libasci, the GB300 ASCI library (arXiv:2303.05688): the
+determinant search (Alg. 2, Eq. 1) and its stages, batched and sharded
+searches with a distributed top-N (the role of Alg. 4), the variational step
+(Hamiltonian, sparse product, Davidson: Sec. 2.3, Alg. 5), the ASCI loop
+(Alg. 1) and ASCI-PT2.
 
-Argument marshalling only: every step of the search runs in the CUDA kernels
-of ``lib/libasci.so`` behind the C ABI declared in ``include/asci.h``.  There is
+Argument marshalling only: every step runs in the CUDA kernels of
+``lib/libasci.so`` behind the C ABI declared in ``include/asci.h``.  There is
 no CPU fallback; importing works without a GPU, but every call needs the built
 library and a CUDA device, and raises otherwise.
 
