@@ -260,6 +260,49 @@ def test_search_full_size_16e16o_sampled(torch_cuda, asci, oracle_mod):
     _check_sampled(oracle_mod, h1, eri, ec, A, B, c, E0, w.C, ga, gb, gs, 64, seed=1)
 
 
+def test_search_full_size_24e30o_sampled(torch_cuda, asci, oracle_mod):
+    """The benchmark's workload and launch configuration ((24e,30o), C = 1e5,
+    N = 1e6, automatic batches): sampled selected targets against the oracle's
+    numerators and diagonals, and completeness: randomly generated excitations
+    of the core that were not selected score no higher than the cutoff."""
+    torch = torch_cuda
+    w, h1, eri, ec, A, B, c, E0 = _random("random_24e30o")
+    ga, gb, gs, st = _run(asci, torch, A, B, c, E0, h1, eri, ec, w.C, w.N)
+    assert st.generated == w.C * W.n_excitations(30, 12, 12)
+    assert len(ga) == w.N and st.batches > 1
+    _check_sampled(oracle_mod, h1, eri, ec, A, B, c, E0, w.C, ga, gb, gs, 48, seed=3)
+    ints = oracle_mod.Ints(h1, eri, ec)
+    core = oracle_mod.core_select(A, B, c, w.C)
+    CA, CB, CC = A[core], B[core], c[core]
+    psi = set(zip(A.tolist(), B.tolist()))
+    sel = set(zip(ga.tolist(), gb.tolist()))
+    cutoff = float(np.min(np.abs(gs)))
+    rng = np.random.default_rng(11)
+    full = (1 << 30) - 1
+    checked = 0
+    while checked < 48:
+        j = int(rng.integers(len(core)))
+        a, b = int(CA[j]), int(CB[j])
+        occ_a = [p for p in range(30) if a >> p & 1]
+        occ_b = [p for p in range(30) if b >> p & 1]
+        vir_a = [p for p in range(30) if not (a >> p & 1)]
+        vir_b = [p for p in range(30) if not (b >> p & 1)]
+        kind = int(rng.integers(3))
+        if kind != 1:  # alpha part: single (kind 0) or with a beta single (kind 2)
+            a ^= (1 << int(rng.choice(occ_a))) | (1 << int(rng.choice(vir_a)))
+        if kind != 0:
+            b ^= (1 << int(rng.choice(occ_b))) | (1 << int(rng.choice(vir_b)))
+        assert a & ~full == 0 and b & ~full == 0
+        t = (a, b)
+        if t in psi or t in sel:
+            continue
+        num, abss = oracle_mod.numerator(ints, t, CA, CB, CC)
+        haa = oracle_mod.diag(ints, t)
+        S = num / (E0 - haa)
+        assert abs(S) <= cutoff + score_tol(S, abss, haa, E0), (t, S, cutoff)
+        checked += 1
+
+
 def _check_sampled(oracle_mod, h1, eri, ec, A, B, c, E0, C, ga, gb, gs, nsample, seed):
     ints = oracle_mod.Ints(h1, eri, ec)
     core = oracle_mod.core_select(A, B, c, C)
