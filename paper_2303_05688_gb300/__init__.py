@@ -24,7 +24,7 @@ import numpy as np
 __all__ = ["load", "lib_path", "launch_count", "search", "excitations", "diagonal", "sort_accumulate",
            "select_topn", "SearchStats", "AsciError", "FP64", "FP32_INT_FP64_ACC",
            "FP32_INT_COMP_ACC", "shard_assign", "gather_candidates", "sharded_search",
-           "search_many", "tune_streams", "hamiltonian", "spmv", "davidson", "asci_loop",
+           "search_many", "tune_streams", "tune_batched", "hamiltonian", "spmv", "davidson", "asci_loop",
            "LoopStats", "pt2", "select_histogram", "select_below", "distributed_topn"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -428,12 +428,12 @@ def search_many(systems, *, streams=None, eps: float = 0.0, precision: int = FP6
     """Many independent searches (asci_search_many): ``systems`` is a list of
     dicts with keys dets, coeffs, E0, h1, eri, ecore, C, N (arrays as for
     search()).  ``streams`` searches run at a time on their own CUDA streams;
-    None picks the count with tune_streams().  Returns a list of
+    None picks the count and the batch cap with tune_batched().  Returns a list of
     (dets, scores, stats), each exactly what search() returns."""
     lib = load()
     if streams is None:
-        streams = tune_streams(systems, eps=eps, precision=precision,
-                               max_batch_pairs=max_batch_pairs)
+        t = tune_batched(systems, eps=eps, precision=precision, max_batch_pairs=max_batch_pairs)
+        streams, max_batch_pairs = t["streams"], t["max_batch_pairs"]
     keep, probs, outs = [], (_Problem * max(len(systems), 1))(), []
     for i, sy in enumerate(systems):
         db = _dets_buf(sy["dets"])
@@ -462,30 +462,46 @@ def search_many(systems, *, streams=None, eps: float = 0.0, precision: int = FP6
 _TUNED = {}
 
 
-def tune_streams(systems, candidates=(1, 2, 4, 8, 16, 32), sample: int = 64, **kw):
-    """The project's autotuner for batched searches: the number of concurrent
-    streams that gives the most searches per second on a sample of the batch
-    (cached per batch signature: count and largest orbital count)."""
+def tune_batched(systems, streams=(1, 2, 4, 8, 16, 32), batch_caps=(0, 1 << 22, 1 << 20),
+                 sample: int = 64, **kw):
+    """The project's autotuner for batched searches: a grid search over the
+    number of concurrent streams and the constraint-batch cap (pairs per batch;
+    0 = sized from free memory), keeping the pair that gives the most searches
+    per second on a sample of the batch.  Cached per batch signature (whether
+    the batch exceeds the sample, the largest orbital count, the precision).
+    Returns {"streams": k, "max_batch_pairs": b}.  A given max_batch_pairs in
+    kw fixes the cap."""
     import time
     if not systems:
-        return 1
+        return {"streams": 1, "max_batch_pairs": int(kw.get("max_batch_pairs", 0))}
     norb = max(int(round(np.sqrt(np.prod(np.shape(sy["h1"]))))) for sy in systems)
-    sig = (len(systems) >= sample, norb, kw.get("precision", FP64))
+    fixed = int(kw.pop("max_batch_pairs", 0) or 0)
+    caps = (fixed,) if fixed else tuple(batch_caps)
+    sig = (len(systems) >= sample, norb, kw.get("precision", FP64), caps)
     if sig in _TUNED:
-        return _TUNED[sig]
+        return dict(_TUNED[sig])
     sub = systems[:sample]
-    best, best_rate = 1, -1.0
-    search_many(sub[:2], streams=1, **kw)  # warm caches and the memory pool
-    for k in candidates:
-        if k > len(sub):
-            break
-        t0 = time.perf_counter()
-        search_many(sub, streams=k, **kw)
-        rate = len(sub) / (time.perf_counter() - t0)
-        if rate > best_rate:
-            best, best_rate = k, rate
-    _TUNED[sig] = best
+    best, best_rate = {"streams": 1, "max_batch_pairs": caps[0]}, -1.0
+    search_many(sub[:2], streams=1, max_batch_pairs=caps[0], **kw)  # warm caches and the pool
+    for b in caps:
+        for k in streams:
+            if k > len(sub):
+                break
+            t0 = time.perf_counter()
+            search_many(sub, streams=k, max_batch_pairs=b, **kw)
+            rate = len(sub) / (time.perf_counter() - t0)
+            if rate > best_rate:
+                best, best_rate = {"streams": k, "max_batch_pairs": b}, rate
+    _TUNED[sig] = dict(best)
     return best
+
+
+def tune_streams(systems, candidates=(1, 2, 4, 8, 16, 32), sample: int = 64, **kw):
+    """The stream count of tune_batched with the batch cap fixed to kw's
+    max_batch_pairs (default 0: sized from free memory)."""
+    cap = int(kw.pop("max_batch_pairs", 0) or 0)
+    return tune_batched(systems, streams=candidates, batch_caps=(cap,), sample=sample,
+                        **kw)["streams"]
 
 
 def shard_assign(weights, shards: int, initial_loads=None):
