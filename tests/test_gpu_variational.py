@@ -386,3 +386,22 @@ def test_host_pointer_paths(torch_cuda, asci, oracle_mod):
                                    h1, eri, ec, ncdets=5, ntdets=300, max_steps=2, tol=1e-10)
     assert isinstance(hd, np.ndarray) and hE == dE
     assert np.array_equal(hd.view(np.int64), dd.cpu().numpy()) and np.array_equal(hc, dc.cpu().numpy())
+
+
+def test_asci_loop_truncates_a_large_start(torch_cuda, asci, oracle_mod):
+    """A start larger than N_tdets: the first step keeps the N_tdets largest of
+    |c| and |S| (some of the start's determinants are dropped), as the oracle's
+    step does."""
+    torch = torch_cuda
+    h1, eri, ec = W.random_molecular(10, 4)
+    ints = oracle_mod.Ints(h1, eri, ec)
+    A, B = W.random_walk_dets(10, 5, 5, 400, seed=4)
+    c = W.rank_decay_coeffs(400, seed=4)
+    E = oracle_mod.variational_energy(ints, A, B, c)
+    d, gc, gE, st = asci.asci_loop(_dev(torch, A, B), torch.tensor(c, device="cuda"), h1, eri, ec,
+                                   ncdets=60, ntdets=150, max_steps=1, tol=1e-10)
+    gA, gB = to_u64_pairs(d)
+    assert len(gA) == 150 and st.ndets == [150]
+    assert len(set(zip(gA.tolist(), gB.tolist())) & set(zip(A.tolist(), B.tolist()))) < 150 or \
+        st.new_dets[0] == 0
+    _check_step(oracle_mod, ints, A, B, c, E, 60, 150, gA, gB, gc.cpu().numpy(), gE)
