@@ -1439,14 +1439,47 @@ __global__ void k_big_gather(const StageRec *rec, const StageRec *spill,
   }
 }
 
+// A target whose numerator is formed: its psi test, the float screen against
+// tau and the append, as on chip; counts unique and excluded targets.
+__device__ __forceinline__ void big_emit(double num, uint64_t full, float den, const CellArgs &C,
+                                         unsigned long long *my_unique,
+                                         unsigned long long *my_excl) {
+  ++*my_unique;
+  if (psi_contains(C.psi_ht, C.psi_mask, full, C.err)) {
+    ++*my_excl;
+    return;
+  }
+  bool pass = true;
+  if (C.tau > 0.0) {  // float screen first, as on chip
+    bool okn;
+    const float nf = abs_as_float(num, &okn);
+    const float df = fabsf(den);
+    if (okn && df != 0.0f) pass = nf >= C.tau_f * df * 0.99999f;
+  }
+  if (pass) {  // the exact score is formed after the launch (k_exact_scores)
+    const unsigned long long slot = atomicAdd(C.cand_count, 1ull);
+    if (slot < C.cand_cap) {
+      C.cand_key[slot] = full;
+      C.cand_score[slot] = num;
+    }
+  }
+}
+
+// Runs (targets) longer than this go to k_big_reduce_long: a CTA per run.
+constexpr uint64_t kLongRun = 64;
+
 __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const uint64_t *src,
                              uint64_t n, const uint32_t *alpha, const StageRec *spill,
-                             CellArgs C) {
+                             CellArgs C, uint64_t *long_runs, unsigned *n_long) {
   unsigned long long my_unique = 0, my_excl = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t sk = keys[i];
     if (i > 0 && keys[i - 1] == sk) continue;
+    if (i + kLongRun < n && keys[i + kLongRun] == sk) {  // sorted: the run is long
+      long_runs[atomicAdd(n_long, 1u)] = i;
+      continue;
+    }
     // the same rule as on chip: one or two values by IEEE addition, three or
     // four by the ordered FP64 sum, more by the 128-bit accumulator
     int emax = 1, live = 0;
@@ -1481,32 +1514,93 @@ __global__ void k_big_reduce(const uint64_t *keys, const uint32_t *idx, const ui
       num = fx128_to_double(acc, frac);
     }
     const uint64_t full = pack_key(alpha[sk >> 32], (uint32_t)sk);
-    ++my_unique;
-    if (psi_contains(C.psi_ht, C.psi_mask, full, C.err)) {
-      ++my_excl;
-      continue;
-    }
-    bool pass = true;
-    if (C.tau > 0.0) {  // float screen first, as on chip
-      bool okn;
-      const float nf = abs_as_float(num, &okn);
-      const float df = fabsf(big_rec(C.st.rec, spill, src[idx[i]]).den);
-      if (okn && df != 0.0f) pass = nf >= C.tau_f * df * 0.99999f;
-    }
-    if (pass) {  // the exact score is formed after the launch (k_exact_scores)
-      const double sc = num;
-      const unsigned long long slot = atomicAdd(C.cand_count, 1ull);
-      if (slot < C.cand_cap) {
-        C.cand_key[slot] = full;
-        C.cand_score[slot] = sc;
-      }
-    }
+    big_emit(num, full, big_rec(C.st.rec, spill, src[idx[i]]).den, C, &my_unique, &my_excl);
   }
   for (int dl = 16; dl; dl >>= 1) {
     my_unique += __shfl_xor_sync(0xffffffffu, my_unique, dl);
     my_excl += __shfl_xor_sync(0xffffffffu, my_excl, dl);
   }
   if ((threadIdx.x & 31) == 0) {
+    if (my_unique) atomicAdd(C.n_unique, my_unique);
+    if (my_excl) atomicAdd(C.n_excluded, my_excl);
+  }
+}
+
+// Long runs (hot targets with more than kLongRun records), one CTA per run:
+// the run's largest exponent and live count by block reductions, then each
+// thread's share in the 128-bit fixed-point accumulator anchored to that
+// exponent, added exactly across the block: the same value as one thread
+// walking the run (the sum is a function of the multiset).  A run with at
+// most four live values (the rest dropped by the screen) takes the ordered
+// FP64 rule on thread 0.
+__global__ void __launch_bounds__(256) k_big_reduce_long(const uint64_t *keys, const uint32_t *idx,
+                                                         const uint64_t *src, uint64_t n,
+                                                         const uint32_t *alpha,
+                                                         const StageRec *spill, CellArgs C,
+                                                         const uint64_t *long_runs,
+                                                         const unsigned *n_long) {
+  __shared__ int s_emax, s_live;
+  __shared__ Fx128 part[256];
+  unsigned long long my_unique = 0, my_excl = 0;
+  const unsigned nl = *n_long;
+  for (unsigned r = blockIdx.x; r < nl; r += gridDim.x) {
+    const uint64_t i = long_runs[r];
+    const uint64_t sk = keys[i];
+    if (threadIdx.x == 0) {
+      s_emax = 1;
+      s_live = 0;
+    }
+    __syncthreads();
+    int emax = 1, live = 0;
+    for (uint64_t e = i + threadIdx.x; e < n && keys[e] == sk; e += blockDim.x) {
+      const double v = big_rec(C.st.rec, spill, src[idx[e]]).v;
+      if (is_dropped(v)) continue;
+      const int ex = fx_exponent(v);
+      emax = ex > emax ? ex : emax;
+      ++live;
+    }
+    atomicMax(&s_emax, emax);
+    atomicAdd(&s_live, live);
+    __syncthreads();
+    const int frac = fx128_frac_for(s_emax);
+    const int nlive = s_live;
+    Fx128 acc = {0, 0};
+    unsigned ovf = 0;
+    if (nlive > 4)
+      for (uint64_t e = i + threadIdx.x; e < n && keys[e] == sk; e += blockDim.x) {
+        const double v = big_rec(C.st.rec, spill, src[idx[e]]).v;
+        if (is_dropped(v)) continue;
+        Fx128 x = fx128_from_double(v, frac, &ovf);
+        fx128_add(acc, x);
+      }
+    if (ovf) atomicOr(C.err, kErrAccum);
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = 128; st; st >>= 1) {
+      if ((int)threadIdx.x < st) fx128_add(part[threadIdx.x], part[threadIdx.x + st]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0 && nlive > 0) {
+      double num;
+      if (nlive > 4) {
+        num = fx128_to_double(part[0], frac);
+      } else {  // the rare run whose values the screen dropped: the on-chip rule
+        double w[4] = {0.0, 0.0, 0.0, 0.0};
+        int k = 0;
+        for (uint64_t e = i; e < n && keys[e] == sk && k < 4; ++e) {
+          const double v = big_rec(C.st.rec, spill, src[idx[e]]).v;
+          if (!is_dropped(v)) w[k++] = v;
+        }
+        num = nlive == 1 ? w[0]
+              : nlive == 2 ? w[0] + w[1]
+                           : sum4_ordered(w[0], w[1], w[2], w[3]);
+      }
+      const uint64_t full = pack_key(alpha[sk >> 32], (uint32_t)sk);
+      big_emit(num, full, big_rec(C.st.rec, spill, src[idx[i]]).den, C, &my_unique, &my_excl);
+    }
+    __syncthreads();  // part[] and the shared counters are reused by the next run
+  }
+  if (threadIdx.x == 0) {
     if (my_unique) atomicAdd(C.n_unique, my_unique);
     if (my_excl) atomicAdd(C.n_excluded, my_excl);
   }
@@ -2131,7 +2225,16 @@ int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const S
   ASCI_TRY(radix_sort_u64_u32(&k0, &k1, &i0, &i1, total, 0, 32 + topbit, ta));
   CellArgs CA = cell_args(F, st, tau, cand_key, cand_score, cand_count, cand_cap, n_unique,
                           n_excluded, err);
-  k_big_reduce<<<grid_for(total), 256, 0, s>>>(k0, i0, src, total, d_alpha, spill.rec, CA);
+  uint64_t *long_runs;
+  unsigned *n_long;
+  ASCI_TRY(ta.alloc(&long_runs, total / kLongRun + 1));
+  ASCI_TRY(ta.alloc(&n_long, 1));
+  ASCI_TRY_CUDA(cudaMemsetAsync(n_long, 0, sizeof(unsigned), s));
+  k_big_reduce<<<grid_for(total), 256, 0, s>>>(k0, i0, src, total, d_alpha, spill.rec, CA,
+                                               long_runs, n_long);
+  ASCI_CHECK_LAUNCH();
+  k_big_reduce_long<<<152 * 2, 256, 0, s>>>(k0, i0, src, total, d_alpha, spill.rec, CA,
+                                            long_runs, n_long);
   ASCI_CHECK_LAUNCH();
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));  // the host vectors above are read by the copies
   return ASCI_OK;
