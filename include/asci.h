@@ -47,7 +47,7 @@ extern "C" {
 #define ASCI_EINVAL (-1)   /* invalid argument or input data */
 #define ASCI_ENOMEM (-2)   /* device memory exhausted or a batch cannot fit */
 #define ASCI_ECUDA (-3)    /* a CUDA runtime call failed */
-#define ASCI_ETIMEOUT (-4) /* a bounded device-side wait gave up */
+#define ASCI_ETIMEOUT (-4) /* a bounded wait or an iteration limit ran out (Davidson) */
 
 /* One determinant: occupation words of the alpha and beta spin strings. */
 typedef struct {

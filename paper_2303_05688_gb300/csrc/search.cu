@@ -1089,7 +1089,7 @@ const char *asci_strerror(int code) {
     case ASCI_EINVAL: return "invalid argument";
     case ASCI_ENOMEM: return "out of device memory";
     case ASCI_ECUDA: return "CUDA error";
-    case ASCI_ETIMEOUT: return "device wait timed out";
+    case ASCI_ETIMEOUT: return "a bounded wait or an iteration limit ran out";
     default: return "unknown error";
   }
 }
