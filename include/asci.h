@@ -350,7 +350,7 @@ int asci_spmv(const int64_t *row_ptr, const int32_t *col, const double *val, siz
 
 /* Davidson controls (Algorithm 5). */
 typedef struct {
-  int32_t max_subspace; /* Krylov dimension k before a restart, 2..48 (default 16) */
+  int32_t max_subspace; /* Krylov dimension k before a restart, 2..32 (default 16) */
   int32_t max_iter;     /* products with H at most (default 300) */
   double tol;           /* stop when ||H v - E v|| <= tol, v normalised (default 1e-8) */
 } asci_davidson_opts;

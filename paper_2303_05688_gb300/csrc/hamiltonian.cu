@@ -17,7 +17,8 @@
 //    the row, a fixed shuffle tree: the same bits on every call.
 //  * Davidson (Algorithm 5): basis V and products W = H V resident on the
 //    device, the subspace matrix V^T H V grown one column per product, its
-//    eigenpairs by parallel-order Jacobi in one CTA, the shifted Jacobi
+//    eigenpairs by parallel-order Jacobi in one CTA (FP32 sweeps refined by
+//    FP64 sweeps), the shifted Jacobi
 //    preconditioner, two passes of classical Gram-Schmidt, a thick restart
 //    (the four lowest Ritz vectors) at the subspace limit.  Every reduction
 //    has a fixed order.
@@ -33,7 +34,7 @@ namespace {
 
 constexpr int kRowThreads = 256;   // rows per CTA of the build
 constexpr int kColStage = 2048;    // column keys staged in shared memory at a time
-constexpr int kMaxSub = 48;        // largest Davidson subspace (shared-memory Jacobi)
+constexpr int kMaxSub = 32;        // largest Davidson subspace (shared-memory Jacobi)
 constexpr int kDotBlocks = 296;    // fixed partial-sum grid of the dot products
 constexpr int kKeep = 4;           // Ritz vectors kept by a Davidson restart
 constexpr int kDotThreads = 256;
@@ -512,13 +513,17 @@ __global__ void k_normalize(double *v, size_t n, const double *norm2) {
 // round pairs every index with one other, so its M / 2 rotations act on
 // disjoint planes.  One thread per pair forms its rotation from the round's
 // matrix, then the CTA applies all of them to the columns (and to the
-// eigenvector matrix), then to the rows.  Sweeps end when the off-diagonal
-// norm falls below 1e-15 of the diagonal's, or after 60.  out: theta[r] in
-// ascending order (ties by index), eigenvector r in Ct[r * kMaxSub + k].
-// Warm start (`warm`: the basis grew by one vector since the last call, whose
-// m - 1 eigenvectors Ct still holds): the rotations start from those
-// eigenvectors, P = diag(old eigenvectors, 1), so that P^T Hs P is diagonal
-// but for its last row and column and two or three sweeps finish it.
+// eigenvector matrix), then to the rows.
+//
+// GB300 executes about 1.7 FP64 operations per clock per SM, against some 126
+// FP32 ones, so the sweeps run in two precisions: FP32 sweeps take the matrix
+// to near-diagonal form (off-diagonal norm below 1e-6 of the diagonal's); the
+// FP32 eigenvectors, promoted to FP64 and orthonormalised by two passes of
+// classical Gram-Schmidt, transform Hs in FP64 (Q^T Hs Q, an exact similarity
+// up to rounding); FP64 sweeps then finish (off-diagonal norm below 1e-13 of
+// the diagonal's, one or two sweeps by quadratic convergence), accumulating
+// into the same eigenvectors.  out: theta[r] in ascending order (ties by
+// index), eigenvector r in Ct[r * kMaxSub + k].
 constexpr int kEigThreads = 256;
 
 // 1/sqrt(x) to FP64 accuracy from the FP32 estimate rsqrtf and two
@@ -554,57 +559,38 @@ __device__ __forceinline__ void rotation(double app, double aqq, double apq, dou
   *s = t * cs;
 }
 
+// The FP32 rotation of the same formulas (IEEE FP32 division and square root).
+__device__ __forceinline__ void rotation_f(float app, float aqq, float apq, float *c, float *s) {
+  const float tau = (aqq - app) / (2.0f * apq);
+  const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+  const float cs = 1.0f / sqrtf(fmaf(t, t, 1.0f));
+  *c = cs;
+  *s = t * cs;
+}
+
 constexpr int kEigPer = (kMaxSub * kMaxSub + kEigThreads - 1) / kEigThreads;
 
-__global__ void __launch_bounds__(kEigThreads) k_small_eig(const double *Hs, int ld, int m,
-                                                           bool warm, double *theta, double *Ct) {
-  __shared__ double A[kMaxSub][kMaxSub + 1];
-  __shared__ double Q[kMaxSub][kMaxSub + 1];
-  __shared__ double rc[kMaxSub / 2], rs[kMaxSub / 2];
-  __shared__ int rp[kMaxSub / 2], rq[kMaxSub / 2];
-  __shared__ double red[2][kEigThreads / 32];
-  __shared__ int done;
+struct EigScratch {
+  int rp[kMaxSub / 2], rq[kMaxSub / 2];
+  double rc[kMaxSub / 2], rs[kMaxSub / 2];
+  double red[2][kEigThreads / 32];
+  int done;
+};
+
+// Parallel-order Jacobi sweeps on A (symmetric, m x m) accumulating into Q,
+// until the off-diagonal norm is at most sqrt(thr) of the diagonal's or after
+// max_sweeps.  T is float or double; every thread of the CTA calls it.
+template <typename T>
+__device__ void jacobi_sweeps(T (*A)[kMaxSub + 1], T (*Q)[kMaxSub + 1], int m, int max_sweeps,
+                              double thr, EigScratch &E) {
   const int tid = threadIdx.x;
   const int M = m + (m & 1);
   const int half = M / 2;
-  for (int e = tid; e < m * m; e += kEigThreads) {
-    const int i = e / m, k = e - (e / m) * m;
-    double q = (i == k) ? 1.0 : 0.0;
-    if (warm && i < m - 1 && k < m - 1) q = Ct[(size_t)k * kMaxSub + i];
-    Q[i][k] = q;
-    if (!warm) A[i][k] = Hs[(size_t)i * ld + k];
-  }
-  __syncthreads();
-  if (warm) {  // A = P^T Hs P, through A = Hs P and registers
-    for (int e = tid; e < m * m; e += kEigThreads) {
-      const int i = e / m, j = e - (e / m) * m;
-      double t = 0.0;
-      for (int l = 0; l < m; ++l) t = fma(Hs[(size_t)i * ld + l], Q[l][j], t);
-      A[i][j] = t;
-    }
-    __syncthreads();
-    double keep[kEigPer];
-    for (int u = 0; u < kEigPer; ++u) {
-      const int e = tid + u * kEigThreads;
-      double t = 0.0;
-      if (e < m * m) {
-        const int i = e / m, j = e - (e / m) * m;
-        for (int k = 0; k < m; ++k) t = fma(Q[k][i], A[k][j], t);
-      }
-      keep[u] = t;
-    }
-    __syncthreads();
-    for (int u = 0; u < kEigPer; ++u) {
-      const int e = tid + u * kEigThreads;
-      if (e < m * m) A[e / m][e - (e / m) * m] = keep[u];
-    }
-    __syncthreads();
-  }
-  for (int sweep = 0; sweep < 60 && m > 1; ++sweep) {
+  for (int sweep = 0; sweep < max_sweeps && m > 1; ++sweep) {
     double off = 0.0, dg = 0.0;
     for (int e = tid; e < m * m; e += kEigThreads) {
       const int i = e / m, k = e - (e / m) * m;
-      const double a = A[i][k];
+      const double a = (double)A[i][k];
       if (i == k) dg += a * a;
       else off += a * a;
     }
@@ -613,20 +599,20 @@ __global__ void __launch_bounds__(kEigThreads) k_small_eig(const double *Hs, int
       dg += __shfl_xor_sync(0xffffffffu, dg, o);
     }
     if ((tid & 31) == 0) {
-      red[0][tid >> 5] = off;
-      red[1][tid >> 5] = dg;
+      E.red[0][tid >> 5] = off;
+      E.red[1][tid >> 5] = dg;
     }
     __syncthreads();
     if (tid == 0) {
       double so = 0.0, sd = 0.0;
       for (int w = 0; w < kEigThreads / 32; ++w) {
-        so += red[0][w];
-        sd += red[1][w];
+        so += E.red[0][w];
+        sd += E.red[1][w];
       }
-      done = so <= 1e-30 * sd;
+      E.done = so <= thr * sd;
     }
     __syncthreads();
-    if (done) break;
+    if (E.done) break;
     for (int r = 0; r < M - 1; ++r) {
       if (tid < half) {
         const int pa = tid == 0 ? 0 : 1 + (tid - 1 + r) % (M - 1);
@@ -634,40 +620,124 @@ __global__ void __launch_bounds__(kEigThreads) k_small_eig(const double *Hs, int
         const int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
         double cs = 1.0, sn = 0.0;
         if (q < m) {
-          const double apq = A[p][q];
-          if (fabs(apq) >= 1e-300) rotation(A[p][p], A[q][q], apq, &cs, &sn);
+          if (sizeof(T) == sizeof(float)) {
+            const float apq = (float)A[p][q];
+            if (fabsf(apq) >= 1e-30f) {
+              float c, s;
+              rotation_f((float)A[p][p], (float)A[q][q], apq, &c, &s);
+              cs = c;
+              sn = s;
+            }
+          } else {
+            const double apq = (double)A[p][q];
+            if (fabs(apq) >= 1e-300) rotation((double)A[p][p], (double)A[q][q], apq, &cs, &sn);
+          }
         }
-        rc[tid] = cs;
-        rs[tid] = sn;
-        rp[tid] = p;
-        rq[tid] = q;
+        E.rc[tid] = cs;
+        E.rs[tid] = sn;
+        E.rp[tid] = p;
+        E.rq[tid] = q;
       }
       __syncthreads();
       for (int e = tid; e < half * m; e += kEigThreads) {  // columns p, q of A and Q
         const int k = e / m, i = e - (e / m) * m;
-        const int p = rp[k], q = rq[k];
-        if (q >= m || rs[k] == 0.0) continue;
-        const double cs = rc[k], sn = rs[k];
-        const double aip = A[i][p], aiq = A[i][q];
+        const int p = E.rp[k], q = E.rq[k];
+        if (q >= m || E.rs[k] == 0.0) continue;
+        const T cs = (T)E.rc[k], sn = (T)E.rs[k];
+        const T aip = A[i][p], aiq = A[i][q];
         A[i][p] = cs * aip - sn * aiq;
         A[i][q] = sn * aip + cs * aiq;
-        const double qip = Q[i][p], qiq = Q[i][q];
+        const T qip = Q[i][p], qiq = Q[i][q];
         Q[i][p] = cs * qip - sn * qiq;
         Q[i][q] = sn * qip + cs * qiq;
       }
       __syncthreads();
       for (int e = tid; e < half * m; e += kEigThreads) {  // rows p, q of A
         const int k = e / m, j = e - (e / m) * m;
-        const int p = rp[k], q = rq[k];
-        if (q >= m || rs[k] == 0.0) continue;
-        const double cs = rc[k], sn = rs[k];
-        const double apj = A[p][j], aqj = A[q][j];
+        const int p = E.rp[k], q = E.rq[k];
+        if (q >= m || E.rs[k] == 0.0) continue;
+        const T cs = (T)E.rc[k], sn = (T)E.rs[k];
+        const T apj = A[p][j], aqj = A[q][j];
         A[p][j] = cs * apj - sn * aqj;
         A[q][j] = sn * apj + cs * aqj;
       }
       __syncthreads();
     }
   }
+}
+
+__global__ void __launch_bounds__(kEigThreads) k_small_eig(const double *Hs, int ld, int m,
+                                                           double *theta, double *Ct) {
+  __shared__ double A[kMaxSub][kMaxSub + 1];
+  __shared__ double Q[kMaxSub][kMaxSub + 1];
+  __shared__ float Af[kMaxSub][kMaxSub + 1];
+  __shared__ float Qf[kMaxSub][kMaxSub + 1];
+  __shared__ double gsr[kMaxSub];
+  __shared__ double nrm;
+  __shared__ EigScratch E;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < m * m; e += kEigThreads) {
+    const int i = e / m, k = e - (e / m) * m;
+    Af[i][k] = (float)Hs[(size_t)i * ld + k];
+    Qf[i][k] = (i == k) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  jacobi_sweeps<float>(Af, Qf, m, 16, 1e-12, E);
+  for (int e = tid; e < m * m; e += kEigThreads) {
+    const int i = e / m, k = e - (e / m) * m;
+    Q[i][k] = (double)Qf[i][k];
+  }
+  __syncthreads();
+  // orthonormal columns in FP64: two passes of classical Gram-Schmidt each
+  for (int k = 0; k < m; ++k) {
+    for (int pass = 0; pass < 2; ++pass) {
+      if (tid < k) {
+        double t = 0.0;
+        for (int i = 0; i < m; ++i) t = fma(Q[i][tid], Q[i][k], t);
+        gsr[tid] = t;
+      }
+      __syncthreads();
+      if (tid < m) {
+        double t = Q[tid][k];
+        for (int j = 0; j < k; ++j) t = fma(-gsr[j], Q[tid][j], t);
+        Q[tid][k] = t;
+      }
+      __syncthreads();
+    }
+    if (tid < 32) {
+      double v = tid < m ? Q[tid][k] * Q[tid][k] : 0.0;
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (tid == 0) nrm = v;
+    }
+    __syncthreads();
+    if (tid < m) Q[tid][k] *= rsqrt_fast(nrm);
+    __syncthreads();
+  }
+  // A = Q^T Hs Q, through A = Hs Q and registers
+  for (int e = tid; e < m * m; e += kEigThreads) {
+    const int i = e / m, j = e - (e / m) * m;
+    double t = 0.0;
+    for (int l = 0; l < m; ++l) t = fma(Hs[(size_t)i * ld + l], Q[l][j], t);
+    A[i][j] = t;
+  }
+  __syncthreads();
+  double keep[kEigPer];
+  for (int u = 0; u < kEigPer; ++u) {
+    const int e = tid + u * kEigThreads;
+    double t = 0.0;
+    if (e < m * m) {
+      const int i = e / m, j = e - (e / m) * m;
+      for (int k = 0; k < m; ++k) t = fma(Q[k][i], A[k][j], t);
+    }
+    keep[u] = t;
+  }
+  __syncthreads();
+  for (int u = 0; u < kEigPer; ++u) {
+    const int e = tid + u * kEigThreads;
+    if (e < m * m) A[e / m][e - (e / m) * m] = keep[u];
+  }
+  __syncthreads();
+  jacobi_sweeps<double>(A, Q, m, 8, 1e-26, E);
   for (int i = tid; i < m; i += kEigThreads) {
     const double d = A[i][i];
     int rk = 0;
@@ -983,7 +1053,6 @@ static int davidson(const Csr &H, const double *diag, const double *guess,
   int m = 1;         // basis vectors in V
   int have_w = 0;    // products already in W
   bool first = true;
-  int prev_m = -1;  // dimension of the last subspace solve (-1: none to warm-start from)
   double theta = 0.0, rn = 0.0;
   for (;;) {
     // products of the new basis vectors and their column of V^T H V
@@ -993,8 +1062,7 @@ static int davidson(const Csr &H, const double *diag, const double *guess,
       ASCI_TRY(dots(V, n, have_w + 1, W + (size_t)have_w * n, n, part, Hs + have_w, kMaxSub,
                     Hs + (size_t)have_w * kMaxSub, 1, s));
     }
-    k_small_eig<<<1, kEigThreads, 0, s>>>(Hs, kMaxSub, m, m == prev_m + 1, th, Ct);
-    prev_m = m;
+    k_small_eig<<<1, kEigThreads, 0, s>>>(Hs, kMaxSub, m, th, Ct);
     ASCI_CHECK_LAUNCH();
     k_ritz<<<gb, 256, 0, s>>>(V, W, n, m, Ct, n, x, wx);
     ASCI_CHECK_LAUNCH();
@@ -1043,7 +1111,6 @@ static int davidson(const Csr &H, const double *diag, const double *guess,
     if (restart) {
       m = keep;
       have_w = keep;
-      prev_m = -1;
     }
     if (!(hs[2] > 1e-28)) {  // the correction lies in the basis: nothing left to add
       res->converged = rn <= o.tol;
