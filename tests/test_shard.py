@@ -169,7 +169,7 @@ def _np_below(keys, s, thr):
     return keys[keep] if keep else keys[:0], s[keep] if keep else s[:0]
 
 
-def _select_worker(rank, world, port, q, seed, N):
+def _select_worker(rank, world, port, q, seed, N, empty_rank0=False):
     import torch
     import torch.distributed as dist
     import sys
@@ -180,7 +180,10 @@ def _select_worker(rank, world, port, q, seed, N):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         keys, s = _select_case(seed, world)
-        part = np.arange(len(keys)) % world == rank
+        owner = np.arange(len(keys)) % world
+        if empty_rank0:  # rank 0 holds no candidates at all
+            owner[owner == 0] = 1 % world
+        part = owner == rank
         k = torch.tensor(keys[part], dtype=torch.int64)
         v = torch.tensor(s[part], dtype=torch.float64)
         gk, gs = asci.distributed_topn(
@@ -203,15 +206,16 @@ def _select_case(seed, world):
     return keys, s
 
 
-@pytest.mark.parametrize("world,N", [(2, 17), (3, 40), (2, 500)])
-def test_distributed_topn_gloo(world, N):
+@pytest.mark.parametrize("world,N,empty", [(2, 17, False), (3, 40, False), (2, 500, False),
+                                           (4, 1, False), (3, 25, True)])
+def test_distributed_topn_gloo(world, N, empty):
     torch = pytest.importorskip("torch")
     import torch.multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
     seed = 100 + world
-    procs = [ctx.Process(target=_select_worker, args=(r, world, port, q, seed, N))
+    procs = [ctx.Process(target=_select_worker, args=(r, world, port, q, seed, N, empty))
              for r in range(world)]
     for p in procs:
         p.start()
