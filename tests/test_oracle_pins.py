@@ -278,7 +278,11 @@ def test_asci_step_selects_by_magnitude_with_key_ties(oracle_mod):
     pool += [(abs(float(v)), int(b), int(a)) for a, b, v in zip(res.a, res.b, res.score)]
     pool.sort(key=lambda t: (-t[0], t[1], t[2]))
     for ntd in (1, 5, 12, 30, 10 ** 6):
+        ma, mb, mv, kept_min, dropped_max, _ = oracle_mod.asci_merge(ints, A, B, c, E0, 6, ntd)
+        assert kept_min >= dropped_max and len(ma) == min(ntd, len(pool))
+        assert np.isclose(kept_min, np.min(np.abs(mv)))
         na_, nb_, v, E, changed = oracle_mod.asci_step(ints, A, B, c, E0, 6, ntd)
+        assert np.array_equal(na_, ma) and np.array_equal(nb_, mb)
         want = sorted((b, a) for _, b, a in pool[:ntd])
         assert [(int(b), int(a)) for a, b in zip(na_, nb_)] == want
         # c' is the ground vector of the dense H on that space
