@@ -253,7 +253,10 @@ int asci_sort_accumulate_noalloc(const asci_det *keys, const double *values, siz
  * of R (15: the most significant byte of hi ... 0: the least significant byte
  * of lo).  n may be 0 (a zero histogram).
  * asci_select_below: the entries with R <= threshold (out_* hold n entries;
- * order unspecified).
+ * order unspecified); *out_n receives their count.
+ * Pointers may be host or device memory; prefix, mask and threshold are host
+ * memory.  Errors: ASCI_EINVAL for NULL arrays with n > 0, NULL prefix, mask,
+ * threshold, hist or out_n, digit outside 0..15, or n >= 2^32.
  */
 int asci_select_histogram(const asci_det *keys, const double *scores, size_t n, int32_t digit,
                           const uint64_t prefix[2], const uint64_t mask[2], uint64_t hist[256],
