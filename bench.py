@@ -433,9 +433,14 @@ def run_loop(args):
     H = asci.hamiltonian(od, h1d, ed, ec)
     n, nnz = od.shape[0], H[1].numel()
     times = []
+    # a device-side spin keeps the stream busy while the host prepares the call,
+    # so that the events time the kernel alone (torch's private helper; without
+    # it the time includes the host work of the call)
+    spin = getattr(torch.cuda, "_sleep", None)
     for _ in range(max(args.steps, 5)):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda._sleep(2_000_000)
+        if spin is not None:
+            spin(2_000_000)
         e0.record()
         asci.spmv(H, oc)
         e1.record()
