@@ -148,6 +148,30 @@ def cpu_sample(w, h1, eri, ec, A, B, c, E0, core, np):
     return r.generated, dt
 
 
+def oracle_rows_per_s(h1, eri, ec, A, B, rows=16):
+    """The oracle (as it stands) forming dense Hamiltonian rows of a
+    determinant list: rows per second on one host core, over `rows` rows."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    ints = oracle.Ints(h1, eri, ec)
+    rows = min(rows, len(A))
+    t0 = time.perf_counter()
+    oracle.h_rows(ints, A, B, np.arange(rows))
+    return rows / (time.perf_counter() - t0)
+
+
+def oracle_pt2_rate(w, h1, eri, ec, A, B, c, E0, core):
+    """The oracle's ASCI-PT2 on the top `core` core determinants: excitations
+    per second on one host core."""
+    import oracle
+    import workloads as W
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.pt2(oracle.Ints(h1, eri, ec), A, B, c, E0, core)
+    return core * W.n_excitations(w.norb, w.na, w.nb) / (time.perf_counter() - t0)
+
+
 def size_cpu_sample(w, args):
     if args.cpu_sample_core:
         return args.cpu_sample_core
@@ -395,12 +419,17 @@ def run_pt2(args):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     ms = statistics.mean(times)
+    core = size_cpu_sample(w, args)
+    cpu = oracle_pt2_rate(w, h1, eri, ec, A, B, c, E0, core)
     print(json.dumps({
         "metric": f"ASCI-PT2 scored excitations/s on {w.name}", "unit": "excitations/s",
         "value": st.generated / (ms / 1e3), "ms_per_step": ms, "higher_is_better": True,
         "steps": args.steps, "warmup": args.warmup, "data": "synthetic", "dtype": "f64",
         "config": {"workload": f"{w.name} pt2", "C": w.C, "ndets": w.ndets,
                    "l2": "flushed (512 MB write) before each step"},
+        "cpu_baseline": {"value": cpu, "unit": "excitations/s", "cores": 1, "kind": "oracle",
+                         "sample": f"oracle PT2 with the top {core} of {w.C} core dets of "
+                                   f"{w.name}, full psi for exclusion"},
         "e_pt2": val, "targets": st.unique - st.excluded, "generated": st.generated,
         "batches": st.batches, "stage_ms": {k: round(v, 3) for k, v in st.t_stage_ms.items()}}),
         flush=True)
@@ -459,6 +488,8 @@ def run_loop(args):
                       "davidson_ms": round(st.t_davidson_ms[k], 3),
                       "elements_per_s": st.nnz[k] / (st.t_hamiltonian_ms[k] / 1e3)})
     last = steps[-1]
+    pairs = od.cpu().numpy().view(np.uint64)
+    cpu_rows = oracle_rows_per_s(h1, eri, ec, pairs[:, 0].copy(), pairs[:, 1].copy())
     print(json.dumps({
         "metric": "ASCI loop step time at (16e,16o)", "unit": "ms",
         "value": round(1e3 * wall / len(steps), 3), "higher_is_better": False,
@@ -470,9 +501,13 @@ def run_loop(args):
         # given per stored element and, for context, per pair of the full
         # double loop it stands in for (2 n^2 pairs: counting and filling)
         "hamiltonian": {"ms": last["hamiltonian_ms"], "nnz": last["nnz"],
+                        "rows_per_s": last["ndets"] / (last["hamiltonian_ms"] / 1e3),
                         "elements_per_s": last["elements_per_s"],
                         "double_loop_pairs_per_s": 2.0 * last["ndets"] ** 2 / (
                             last["hamiltonian_ms"] / 1e3)},
+        "cpu_baseline": {"value": cpu_rows, "unit": "Hamiltonian rows/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"oracle dense rows of 16 of the final space's {n} determinants"},
         "spmv_roofline": {"bound": "hbm", "achieved": spmv_bytes / (spmv_ms / 1e3) / 1e9,
                           "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                           "frac": spmv_bytes / (spmv_ms / 1e3) / 1e9 / peak,
