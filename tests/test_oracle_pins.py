@@ -349,6 +349,37 @@ def test_pt2_equals_dense_second_order_sum(oracle_mod, npsi, C):
     assert got < 0
 
 
+def test_pt2_pin_catches_planted_mistakes(oracle_mod):
+    """Plausible mistakes in the PT2 sum (a sign, the denominator's order, the
+    numerator's absolute sum, targets inside psi kept) each break the dense
+    brute-force pin."""
+    import math
+    n, na, nb = 6, 3, 3
+    h1, eri, ec = W.random_molecular(n, 21)
+    ints = oracle_mod.Ints(h1, eri, ec)
+    SA, SB = fock.sector(n, na, nb)
+    H = fock.hamiltonian(n, h1, eri, ec, SA, SB)
+    rng = np.random.default_rng(3)
+    idx = rng.choice(len(SA), 30, replace=False)
+    A, B, c = SA[idx], SB[idx], rng.normal(size=30)
+    E0 = float(np.min(np.diag(H))) - 0.5
+    y = H[:, idx] @ c
+    out = np.ones(len(SA), dtype=bool)
+    out[idx] = False
+    ref = float(np.sum(y[out] ** 2 / (E0 - np.diag(H)[out])))
+    res = oracle_mod.search(ints, A, B, c, E0, 30)
+    mutants = {
+        "sign": -math.fsum((res.num ** 2 / (E0 - res.haa)).tolist()),
+        "denominator_order": math.fsum((res.num ** 2 / (res.haa - E0 + 1e-3)).tolist()),
+        "absolute_numerator": math.fsum((res.abssum ** 2 / (E0 - res.haa)).tolist()),
+        "psi_not_excluded": math.fsum((res.num ** 2 / (E0 - res.haa)).tolist())
+        + float(np.sum(y[~out] ** 2 / (E0 - np.diag(H)[~out]))),
+    }
+    assert abs(oracle_mod.pt2(ints, A, B, c, E0, 30) - ref) <= 1e-12 * abs(ref)
+    for name, v in mutants.items():
+        assert abs(v - ref) > 1e-6 * abs(ref), name
+
+
 # --------------------------------------------------------------------------
 # planted mistakes: each must be caught by a pin
 # --------------------------------------------------------------------------
