@@ -320,10 +320,11 @@ int asci_select_topn(const asci_det *keys, const double *scores, size_t n, size_
 /*
  * The Hamiltonian restricted to a determinant list, as a sparse matrix in
  * compressed sparse row form (Sec. 2.3: the double loop approach over pairs of
- * determinants, here pruned by beta-string groups; CSR storage).  Row and column i belong to dets[i].  Row i holds
- * its diagonal element H_ii and every H_ij != 0 with dets[j] singly or doubly
- * excited from dets[i] (by the Slater-Condon rules of the conventions above),
- * columns ascending; the matrix is symmetric.
+ * determinants, here pruned by beta-string groups; CSR storage).  Row and
+ * column i belong to dets[i].  Row i holds its diagonal element H_ii and every
+ * H_ij != 0 with dets[j] singly or doubly excited from dets[i] (by the
+ * Slater-Condon rules of the conventions above), columns ascending; the matrix
+ * is symmetric.
  *
  *  dets[n]       distinct determinants with equal electron counts (n < 2^31).
  *  row_ptr[n+1]  out (int64): row i is entries row_ptr[i] .. row_ptr[i+1]-1.
@@ -365,11 +366,10 @@ void asci_default_davidson_opts(asci_davidson_opts *opts);
  * (Sec. 2.3, Algorithm 5, on one device): the subspace grows by the
  * preconditioned residual R / (E - H_ii) (the shifted Jacobi preconditioner),
  * orthogonalised against the basis by two passes of Gram-Schmidt; the
- * subspace eigenproblem is solved on the device (Jacobi rotations); at
- * max_subspace vectors the basis restarts from the four lowest Ritz vectors
- * (fewer when max_subspace <= 4).  The
- * first expansion vector is the unpreconditioned H v0 - (v0.H v0) v0, as in
- * Algorithm 5.
+ * subspace eigenproblem is solved on the device (Jacobi rotations in FP32,
+ * refined in FP64); at max_subspace vectors the basis restarts from the four
+ * lowest Ritz vectors (fewer when max_subspace <= 4).  The first expansion
+ * vector is the unpreconditioned H v0 - (v0.H v0) v0, as in Algorithm 5.
  *
  *  guess[n]    start vector (nullable: the unit vector of the smallest H_ii).
  *  *energy     out: the Ritz value.
