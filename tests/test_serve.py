@@ -70,6 +70,39 @@ def test_oversized_request_rejected():
             srv.submit("s", 5, 100)
 
 
+def test_failed_search_reaches_its_future_and_frees_its_slot():
+    """A search that raises reports through its own future; its memory and slot
+    are released, so the requests behind it still run."""
+    calls = []
+
+    def flaky(dets, coeffs, E0, h1, eri, ecore, C, N, **kw):
+        calls.append(C)
+        if C == 3:
+            raise RuntimeError("planted failure")
+        return dets[:1], coeffs[:1], {"C": C}
+
+    torch, srv = _server_cpu(slots=1, budget=1 << 40, search_fn=flaky)
+    with srv:
+        srv.register("s", np.zeros((10, 2), np.int64), np.ones(10), -1.0, np.zeros((8, 8)),
+                     np.zeros(8 ** 4), 0.0)
+        futs = [srv.submit("s", c, 100) for c in range(1, 6)]
+        with pytest.raises(RuntimeError, match="planted failure"):
+            futs[2].result(timeout=30)
+        for i in (0, 1, 3, 4):
+            assert futs[i].result(timeout=30)[2]["C"] == i + 1
+    assert calls == [1, 2, 3, 4, 5]
+    assert srv._in_use == 0 and srv._running == 0
+
+
+def test_submit_after_close_is_refused():
+    torch, srv = _server_cpu(slots=1, budget=1 << 40, search_fn=lambda *a, **k: None)
+    srv.register("s", np.zeros((10, 2), np.int64), np.ones(10), -1.0, np.zeros((8, 8)),
+                 np.zeros(8 ** 4), 0.0)
+    srv.close()
+    with pytest.raises(RuntimeError, match="closed"):
+        srv.submit("s", 1, 10)
+
+
 @pytest.mark.gpu
 def test_served_results_equal_standalone(oracle_mod):
     torch = pytest.importorskip("torch")
