@@ -61,3 +61,33 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(m, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         m.load()
+
+
+def test_header_compiles_as_c_and_links(built_lib, tmp_path):
+    """include/asci.h is plain C99 (warning-free) and a C program links against
+    the library and runs its host-only calls."""
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    src = tmp_path / "use.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "asci.h"
+int main(void) {
+  asci_opts o; asci_davidson_opts d; asci_loop_opts l;
+  asci_default_opts(&o); asci_default_davidson_opts(&d); asci_default_loop_opts(&l);
+  if (o.precision != ASCI_FP64 || d.max_subspace != 16 || l.max_steps != 8) return 2;
+  if (strstr(asci_version(), "sm_103a") == NULL) return 3;
+  if (asci_launch_count() != 0) return 4;
+  printf("%s\n", asci_strerror(ASCI_EINVAL));
+  return 0;
+}
+""")
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(built_lib)
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lasci",
+                        f"-Wl,-rpath,{libdir}", "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "invalid argument"
