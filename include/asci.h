@@ -109,6 +109,12 @@ typedef struct {
   uint64_t tile_launches;      /* launches of the on-chip tile kernel */
   uint64_t tile_records;       /* staged pairs reduced on chip (16 bytes read each) */
   uint64_t oversized_records;  /* staged pairs reduced by the global-sort path */
+  /* The diagonal H_ii is summed exactly in 64-bit fixed point on the grid
+   * 2^-diag_grid_bits: E0, ecore and each integral term of H_ii (h_pp, J - K of
+   * a same-spin pair, J of an opposite-spin pair) is rounded once to the grid,
+   * so E0 - H_ii carries at most (terms + 2) * 2^-(diag_grid_bits + 1) of
+   * rounding before its one conversion to FP64. */
+  uint64_t diag_grid_bits;
   /* device milliseconds: prepare, plan, generate (emission into the staging
      buffer), tiles (the on-chip tile kernel alone), oversized (global-sort
      path alone), score (tiles + oversized + exact scores + pruning), select,
@@ -206,7 +212,9 @@ int asci_diagonal(const asci_ints *ints, const asci_det *dets, size_t n, double 
  * Sort-and-accumulate (Sec. 2.2): sorts the (key, value) pairs on the key and
  * sums the values of each unique key.  Device pointers; out_keys / out_sums
  * hold n elements; *out_n receives the number of unique keys, written in key
- * order.  Equal keys are summed in input order.
+ * order.  Equal keys are summed in input order.  Keys are packed into 64
+ * bits, so each word must be below 2^32 (at most 32 orbitals); a key with a
+ * higher bit returns ASCI_EINVAL.
  */
 int asci_sort_accumulate(const asci_det *keys, const double *values, size_t n,
                          asci_det *out_keys, double *out_sums, size_t *out_n,
@@ -219,19 +227,27 @@ int asci_sort_accumulate(const asci_det *keys, const double *values, size_t n,
  * capped, or an embedder (a latency-bound or certified code path) whose policy
  * forbids allocation behind its back.
  *
- * Same results as asci_sort_accumulate for n <= ASCI_NOALLOC_MAX_PAIRS
- * (ASCI_EINVAL above that, with a message in asci_last_error()).  Every scratch
- * buffer is carved from one fixed device array inside the library, which each
- * GPU that loads the library holds (about 104 bytes per pair of the maximum
- * plus 2 MiB, ~7 MB) until the process exits.  No cudaMalloc, cudaFree or
- * allocating library routine is called.
+ * Same results as asci_sort_accumulate (bit for bit) for
+ * n <= ASCI_NOALLOC_MAX_PAIRS (ASCI_EINVAL above that, with a message in
+ * asci_last_error(); also for a key word with bits at or above 32).  Every
+ * scratch buffer is carved from one fixed device array inside the library
+ * (about 104 bytes per pair of the maximum plus 2 MiB, ~7 MB).  No cudaMalloc,
+ * cudaFree or allocating library routine is called.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array, so calls that
- * overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller; the call itself returns after its results are in
- * the output buffers.  Inputs and outputs may be host or device memory.
+ * The array belongs to the library's device code module: each context that
+ * loads the module holds one copy until the process exits (or the context is
+ * destroyed).  CUDA loads modules lazily by default, so the first call on a
+ * device is the one that loads the module and commits the array: make one
+ * call as a warm-up before the section that must not allocate, and before any
+ * stream capture.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) with the calling thread's current device.
+ *
+ * All calls share the one array and it keeps the last call's contents, so
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  Every return, an error included, comes
+ * after the call's GPU work has finished (the stream is synchronised), so a
+ * call that has returned no longer touches the array.  Inputs and outputs may
+ * be host or device memory.
  */
 #define ASCI_NOALLOC_MAX_PAIRS 65536
 int asci_sort_accumulate_noalloc(const asci_det *keys, const double *values, size_t n,

@@ -34,9 +34,54 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C, -O2, no target-specific flags)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-o", tmp,
+                               _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def _bind(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    u64p = ct.POINTER(ct.c_uint64)
+    f64p = ct.POINTER(ct.c_double)
+    szp = ct.POINTER(ct.c_size_t)
+    lib.oracle_search.restype = ct.c_void_p
+    lib.oracle_search.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p, f64p,
+                                  ct.c_size_t, ct.c_double, ct.c_size_t, ct.c_double,
+                                  ct.c_uint64, ct.c_uint64]
+    lib.oracle_search_parallel.restype = ct.c_void_p
+    lib.oracle_search_parallel.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p, f64p,
+                                           ct.c_size_t, ct.c_double, ct.c_size_t, ct.c_double,
+                                           ct.c_int]
+    lib.oracle_free.argtypes = [ct.c_void_p]
+    lib.oracle_result_count.restype = ct.c_size_t
+    lib.oracle_result_count.argtypes = [ct.c_void_p]
+    lib.oracle_result_stats.argtypes = [ct.c_void_p, szp]
+    lib.oracle_result_copy.argtypes = [ct.c_void_p, u64p, u64p, f64p, f64p, f64p, f64p, f64p]
+    lib.oracle_topn.restype = ct.c_size_t
+    lib.oracle_topn.argtypes = [u64p, u64p, f64p, ct.c_size_t, ct.c_size_t, szp]
+    lib.oracle_core_select.restype = ct.c_size_t
+    lib.oracle_core_select.argtypes = [u64p, u64p, f64p, ct.c_size_t, ct.c_size_t, szp]
+    lib.oracle_hij.restype = ct.c_double
+    lib.oracle_hij.argtypes = [ct.c_int, f64p, f64p, ct.c_double, ct.c_uint64, ct.c_uint64,
+                               ct.c_uint64, ct.c_uint64]
+    lib.oracle_diag.restype = ct.c_double
+    lib.oracle_diag.argtypes = [ct.c_int, f64p, f64p, ct.c_double, ct.c_uint64, ct.c_uint64]
+    lib.oracle_diag_abs.restype = ct.c_double
+    lib.oracle_diag_abs.argtypes = [ct.c_int, f64p, f64p, ct.c_double, ct.c_uint64, ct.c_uint64]
+    lib.oracle_dense_h.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p,
+                                   ct.c_size_t, f64p]
+    lib.oracle_h_rows.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p,
+                                  ct.c_size_t, szp, ct.c_size_t, f64p]
+    lib.oracle_pairs.restype = ct.c_size_t
+    lib.oracle_pairs.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p, f64p,
+                                 ct.c_size_t, ct.c_size_t, u64p, u64p, f64p]
+    lib.oracle_numerator.restype = ct.c_double
+    lib.oracle_numerator.argtypes = [ct.c_int, f64p, f64p, ct.c_double, ct.c_uint64,
+                                     ct.c_uint64, u64p, u64p, f64p, ct.c_size_t, f64p]
+    lib.oracle_bucket_of.restype = ct.c_uint64
+    lib.oracle_bucket_of.argtypes = [ct.c_uint64, ct.c_uint64, ct.c_uint64]
+    return lib
 
 
 def _load():
@@ -44,42 +89,29 @@ def _load():
     with _lock:
         if _lib is None:
             build()
-            lib = ct.CDLL(_LIB)
-            u64p = ct.POINTER(ct.c_uint64)
-            f64p = ct.POINTER(ct.c_double)
-            szp = ct.POINTER(ct.c_size_t)
-            lib.oracle_search.restype = ct.c_void_p
-            lib.oracle_search.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p, f64p,
-                                          ct.c_size_t, ct.c_double, ct.c_size_t, ct.c_double,
-                                          ct.c_uint64, ct.c_uint64]
-            lib.oracle_free.argtypes = [ct.c_void_p]
-            lib.oracle_result_count.restype = ct.c_size_t
-            lib.oracle_result_count.argtypes = [ct.c_void_p]
-            lib.oracle_result_stats.argtypes = [ct.c_void_p, szp]
-            lib.oracle_result_copy.argtypes = [ct.c_void_p, u64p, u64p, f64p, f64p, f64p, f64p]
-            lib.oracle_topn.restype = ct.c_size_t
-            lib.oracle_topn.argtypes = [u64p, u64p, f64p, ct.c_size_t, ct.c_size_t, szp]
-            lib.oracle_core_select.restype = ct.c_size_t
-            lib.oracle_core_select.argtypes = [u64p, u64p, f64p, ct.c_size_t, ct.c_size_t, szp]
-            lib.oracle_hij.restype = ct.c_double
-            lib.oracle_hij.argtypes = [ct.c_int, f64p, f64p, ct.c_double, ct.c_uint64, ct.c_uint64,
-                                       ct.c_uint64, ct.c_uint64]
-            lib.oracle_diag.restype = ct.c_double
-            lib.oracle_diag.argtypes = [ct.c_int, f64p, f64p, ct.c_double, ct.c_uint64, ct.c_uint64]
-            lib.oracle_dense_h.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p,
-                                           ct.c_size_t, f64p]
-            lib.oracle_h_rows.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p,
-                                          ct.c_size_t, szp, ct.c_size_t, f64p]
-            lib.oracle_pairs.restype = ct.c_size_t
-            lib.oracle_pairs.argtypes = [ct.c_int, f64p, f64p, ct.c_double, u64p, u64p, f64p,
-                                         ct.c_size_t, ct.c_size_t, u64p, u64p, f64p]
-            lib.oracle_numerator.restype = ct.c_double
-            lib.oracle_numerator.argtypes = [ct.c_int, f64p, f64p, ct.c_double, ct.c_uint64,
-                                             ct.c_uint64, u64p, u64p, f64p, ct.c_size_t, f64p]
-            lib.oracle_bucket_of.restype = ct.c_uint64
-            lib.oracle_bucket_of.argtypes = [ct.c_uint64, ct.c_uint64, ct.c_uint64]
-            _lib = lib
+            _lib = _bind(ct.CDLL(_LIB))
     return _lib
+
+
+class substitute:
+    """Context manager for the mutation tests: every oracle function of this
+    module runs on the library at `path` (a copy of asci_oracle.c with a
+    planted mistake, compiled by the test) until the block ends."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        _load()
+        self._saved = _lib
+        _lib = _bind(ct.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+        return False
 
 
 def _f64(x):
@@ -115,6 +147,12 @@ def hij(ints: Ints, bra, ket) -> float:
 def diag(ints: Ints, det) -> float:
     """<D|H|D>."""
     return _load().oracle_diag(*ints.args(), int(det[0]), int(det[1]))
+
+
+def diag_abs(ints: Ints, det) -> float:
+    """Sum of the magnitudes of the terms of <D|H|D> (ecore, h_pp, the
+    same-spin (J - K) / 2 of ordered pairs, the opposite-spin J)."""
+    return _load().oracle_diag_abs(*ints.args(), int(det[0]), int(det[1]))
 
 
 def dense_h(ints: Ints, A, B) -> np.ndarray:
@@ -165,9 +203,10 @@ def bucket_of(a: int, b: int, nbuckets: int) -> int:
 class SearchResult:
     """Every unique candidate outside psi (Alg. 2 before the final selection)."""
 
-    def __init__(self, a, b, num, abssum, haa, score, stats):
+    def __init__(self, a, b, num, abssum, haa, haa_abs, score, stats):
         self.a, self.b = a, b
         self.num, self.abssum, self.haa, self.score = num, abssum, haa, score
+        self.haa_abs = haa_abs
         (self.generated, self.surviving, self.unique, self.excluded, self.ncore) = stats
 
     @property
@@ -180,13 +219,21 @@ class SearchResult:
 
 
 def search(ints: Ints, A, B, c, E0: float, C: int, eps: float = 0.0,
-           nbuckets: int = 1, bucket: int = 0) -> SearchResult:
-    """Algorithm 2 + Eq. 1: all unique candidates with numerator, H_ii and score."""
+           nbuckets: int = 1, bucket: int = 0, threads: int = 1) -> SearchResult:
+    """Algorithm 2 + Eq. 1: all unique candidates with numerator, H_ii and score.
+    threads > 1 runs the all-core form (same result bit for bit; no buckets)."""
     A, B, c = _u64(A), _u64(B), _f64(c)
     lib = _load()
-    h = lib.oracle_search(*ints.args(), _p(A, ct.c_uint64), _p(B, ct.c_uint64),
-                          _p(c, ct.c_double), len(A), float(E0), int(C), float(eps),
-                          int(nbuckets), int(bucket))
+    if threads > 1:
+        if nbuckets > 1:
+            raise ValueError("the all-core form takes no bucket filter")
+        h = lib.oracle_search_parallel(*ints.args(), _p(A, ct.c_uint64), _p(B, ct.c_uint64),
+                                       _p(c, ct.c_double), len(A), float(E0), int(C),
+                                       float(eps), int(threads))
+    else:
+        h = lib.oracle_search(*ints.args(), _p(A, ct.c_uint64), _p(B, ct.c_uint64),
+                              _p(c, ct.c_double), len(A), float(E0), int(C), float(eps),
+                              int(nbuckets), int(bucket))
     if not h:
         raise MemoryError("oracle_search failed")
     try:
@@ -195,12 +242,13 @@ def search(ints: Ints, A, B, c, E0: float, C: int, eps: float = 0.0,
         lib.oracle_result_stats(h, _p(st, ct.c_size_t))
         a = np.empty(k, dtype=np.uint64)
         b = np.empty(k, dtype=np.uint64)
-        num, abss, haa, sc = (np.empty(k) for _ in range(4))
+        num, abss, haa, habs, sc = (np.empty(k) for _ in range(5))
         lib.oracle_result_copy(h, _p(a, ct.c_uint64), _p(b, ct.c_uint64), _p(num, ct.c_double),
-                               _p(abss, ct.c_double), _p(haa, ct.c_double), _p(sc, ct.c_double))
+                               _p(abss, ct.c_double), _p(haa, ct.c_double),
+                               _p(habs, ct.c_double), _p(sc, ct.c_double))
     finally:
         lib.oracle_free(h)
-    return SearchResult(a, b, num, abss, haa, sc, tuple(int(x) for x in st))
+    return SearchResult(a, b, num, abss, haa, habs, sc, tuple(int(x) for x in st))
 
 
 def topn(a, b, score, N: int) -> np.ndarray:

@@ -40,6 +40,9 @@
  * Every function below states the passage it follows.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -100,26 +103,39 @@ static int single_sign(uint64_t s, int p, int q) {
 /* Slater-Condon rules (textbook; reading of the Hamiltonian above)          */
 /* ------------------------------------------------------------------------ */
 
-/* Diagonal element <D|H|D>. */
-double oracle_diag_impl(const oints *I, uint64_t a, uint64_t b) {
+/* One term of the diagonal sum: added to the value and, by magnitude, to the
+ * sum of |terms| that bounds the rounding error of any evaluation order. */
+static void diag_term(nsum *acc, nsum *mag, double t) {
+  nsum_add(acc, t);
+  nsum_add(mag, fabs(t));
+}
+
+/* Diagonal element <D|H|D>; *abs_out (nullable) receives the sum of the
+ * magnitudes of its terms. */
+static double diag_with_abs(const oints *I, uint64_t a, uint64_t b, double *abs_out) {
   int n = I->n, p, q;
-  nsum acc = {0.0, 0.0};
-  nsum_add(&acc, I->ecore);
+  nsum acc = {0.0, 0.0}, mag = {0.0, 0.0};
+  diag_term(&acc, &mag, I->ecore);
   for (p = 0; p < n; p++) {
-    if (occupied(a, p)) nsum_add(&acc, H1(I, p, p));
-    if (occupied(b, p)) nsum_add(&acc, H1(I, p, p));
+    if (occupied(a, p)) diag_term(&acc, &mag, H1(I, p, p));
+    if (occupied(b, p)) diag_term(&acc, &mag, H1(I, p, p));
   }
   for (p = 0; p < n; p++)
     for (q = 0; q < n; q++) {
       /* same-spin pairs, 1/2 sum over ordered pairs */
       if (occupied(a, p) && occupied(a, q))
-        nsum_add(&acc, 0.5 * (ERI(I, p, p, q, q) - ERI(I, p, q, q, p)));
+        diag_term(&acc, &mag, 0.5 * (ERI(I, p, p, q, q) - ERI(I, p, q, q, p)));
       if (occupied(b, p) && occupied(b, q))
-        nsum_add(&acc, 0.5 * (ERI(I, p, p, q, q) - ERI(I, p, q, q, p)));
+        diag_term(&acc, &mag, 0.5 * (ERI(I, p, p, q, q) - ERI(I, p, q, q, p)));
       /* opposite-spin Coulomb */
-      if (occupied(a, p) && occupied(b, q)) nsum_add(&acc, ERI(I, p, p, q, q));
+      if (occupied(a, p) && occupied(b, q)) diag_term(&acc, &mag, ERI(I, p, p, q, q));
     }
+  if (abs_out) *abs_out = nsum_get(&mag);
   return nsum_get(&acc);
+}
+
+double oracle_diag_impl(const oints *I, uint64_t a, uint64_t b) {
+  return diag_with_abs(I, a, b, NULL);
 }
 
 /* Single excitation i -> a on spin string s (the other spin string is o),
@@ -321,7 +337,7 @@ static void enumerate(ogen *g, int n, uint64_t ka, uint64_t kb, double cj) {
 typedef struct {
   size_t ncand;
   uint64_t *a, *b;
-  double *num, *abssum, *haa, *score;
+  double *num, *abssum, *haa, *haa_abs, *score;
   size_t generated, surviving, unique, excluded, ncore;
 } oresult;
 
@@ -332,6 +348,7 @@ void oracle_free(oresult *r) {
   free(r->num);
   free(r->abssum);
   free(r->haa);
+  free(r->haa_abs);
   free(r->score);
   free(r);
 }
@@ -410,6 +427,7 @@ oresult *oracle_search(int n, const double *h1, const double *eri, double ecore,
   r->num = (double *)malloc((u ? u : 1) * sizeof(double));
   r->abssum = (double *)malloc((u ? u : 1) * sizeof(double));
   r->haa = (double *)malloc((u ? u : 1) * sizeof(double));
+  r->haa_abs = (double *)malloc((u ? u : 1) * sizeof(double));
   r->score = (double *)malloc((u ? u : 1) * sizeof(double));
   k = 0;
   for (i = 0; i < g.P.n;) {
@@ -427,12 +445,13 @@ oresult *oracle_search(int n, const double *h1, const double *eri, double ecore,
     if (nd && bsearch(&key, psi, nd, sizeof(okey), okey_cmp)) {
       r->excluded++;
     } else {
-      double hii = oracle_diag_impl(&I, key.a, key.b);
+      double habs = 0.0, hii = diag_with_abs(&I, key.a, key.b, &habs);
       r->a[k] = key.a;
       r->b[k] = key.b;
       r->num[k] = nsum_get(&num);
       r->abssum[k] = nsum_get(&abssum);
       r->haa[k] = hii;
+      r->haa_abs[k] = habs;
       r->score[k] = r->num[k] / (E0 - hii);
       k++;
     }
@@ -441,6 +460,235 @@ oresult *oracle_search(int n, const double *h1, const double *eri, double ecore,
   r->ncand = k;
   free(psi);
   free(g.P.v);
+  return r;
+}
+
+/*
+ * All-core form of oracle_search (eps, no bucket filter), for the CPU baseline
+ * and for parity runs at sizes the single-core form takes minutes on.  It
+ * computes the same result bit for bit: the same core, the same pairs and
+ * values, and each target's contributions summed in the same order.
+ *  1. The core determinants are enumerated in parallel, each into its
+ *     thread's list; a pair's order field is (core rank, position in that
+ *     determinant's enumeration), which sorts like the single-core counter.
+ *  2. Pairs are scattered into `parts` lists by oracle_bucket_of(target), so
+ *     every target's contributions land in one list.
+ *  3. The lists are sorted and accumulated in parallel (the loop of
+ *     oracle_search), then the candidates of all lists are put in key order.
+ */
+typedef struct {
+  uint64_t a, b;
+  double num, abssum, haa, haa_abs, score;
+} ocand;
+
+static int ocand_cmp(const void *x, const void *y) {
+  const ocand *p = (const ocand *)x, *q = (const ocand *)y;
+  return key_cmp(p->a, p->b, q->a, q->b);
+}
+
+oresult *oracle_search_parallel(int n, const double *h1, const double *eri, double ecore,
+                                const uint64_t *da, const uint64_t *db, const double *c,
+                                size_t nd, double E0, size_t C, double eps, int threads) {
+  oints I = {n, ecore, h1, eri};
+  size_t i, m, t, nparts, total = 0;
+  size_t *core, *fill, *cnt, *off;
+  ogen *gens;
+  opair **part;
+  ocand **cand;
+  size_t *ncand, *nuniq, *nexcl;
+  okey *psi;
+  int nt, bad = 0;
+  oresult *r = (oresult *)calloc(1, sizeof(oresult));
+  if (!r) return NULL;
+  nt = threads > 0 ? threads : 1;
+  nparts = (size_t)nt * 8;
+  core = (size_t *)malloc((nd ? nd : 1) * sizeof(size_t));
+  m = oracle_core_select(da, db, c, nd, C, core);
+  r->ncore = m;
+  gens = (ogen *)calloc((size_t)nt, sizeof(ogen));
+  cnt = (size_t *)calloc((size_t)nt * nparts, sizeof(size_t));
+  off = (size_t *)calloc((size_t)nt * nparts, sizeof(size_t));
+  fill = (size_t *)calloc(nparts + 1, sizeof(size_t));
+  part = (opair **)calloc(nparts, sizeof(opair *));
+  cand = (ocand **)calloc(nparts, sizeof(ocand *));
+  ncand = (size_t *)calloc(nparts, sizeof(size_t));
+  nuniq = (size_t *)calloc(nparts, sizeof(size_t));
+  nexcl = (size_t *)calloc(nparts, sizeof(size_t));
+  psi = (okey *)malloc((nd ? nd : 1) * sizeof(okey));
+  if (!core || !gens || !cnt || !off || !fill || !part || !cand || !ncand || !nuniq || !nexcl ||
+      !psi) {
+    bad = 1;
+    goto done;
+  }
+  for (i = 0; i < nd; i++) {
+    psi[i].a = da[i];
+    psi[i].b = db[i];
+  }
+  qsort(psi, nd, sizeof(okey), okey_cmp);
+
+  /* 1. enumeration, one list per thread */
+#pragma omp parallel num_threads(nt)
+  {
+#ifdef _OPENMP
+    int me = omp_get_thread_num();
+#else
+    int me = 0;
+#endif
+    ogen *g = &gens[me];
+    long long k;
+    g->I = &I;
+    g->E0 = E0;
+    g->eps = eps;
+    g->nbuckets = 1;
+#pragma omp for schedule(dynamic, 4)
+    for (k = 0; k < (long long)m; k++) {
+      g->P.order = (size_t)k << 32;
+      enumerate(g, n, da[core[k]], db[core[k]], c[core[k]]);
+    }
+  }
+  for (t = 0; t < (size_t)nt; t++) {
+    if (gens[t].err) bad = 1;
+    r->generated += gens[t].generated;
+    r->surviving += gens[t].surviving;
+  }
+  if (bad) goto done;
+
+  /* 2. scatter by target bucket (counts per thread and bucket, then offsets) */
+#pragma omp parallel for num_threads(nt) schedule(static, 1)
+  for (t = 0; t < (size_t)nt; t++) {
+    size_t q;
+    for (q = 0; q < gens[t].P.n; q++)
+      cnt[t * nparts + oracle_bucket_of(gens[t].P.v[q].a, gens[t].P.v[q].b, nparts)]++;
+  }
+  for (i = 0; i < nparts; i++) {
+    size_t run = 0;
+    for (t = 0; t < (size_t)nt; t++) {
+      off[t * nparts + i] = run;
+      run += cnt[t * nparts + i];
+    }
+    fill[i] = run;
+    total += run;
+    part[i] = (opair *)malloc((run ? run : 1) * sizeof(opair));
+    if (!part[i]) bad = 1;
+  }
+  if (bad) goto done;
+#pragma omp parallel for num_threads(nt) schedule(static, 1)
+  for (t = 0; t < (size_t)nt; t++) {
+    size_t q;
+    for (q = 0; q < gens[t].P.n; q++) {
+      const opair *p = &gens[t].P.v[q];
+      size_t bkt = oracle_bucket_of(p->a, p->b, nparts);
+      part[bkt][off[t * nparts + bkt]++] = *p;
+    }
+    free(gens[t].P.v);
+    gens[t].P.v = NULL;
+  }
+
+  /* 3. sort and accumulate each list */
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1)
+  for (i = 0; i < nparts; i++) {
+    size_t q, u = 0, k = 0, np = fill[i];
+    opair *v = part[i];
+    qsort(v, np, sizeof(opair), opair_cmp);
+    for (q = 0; q < np; q++)
+      if (q == 0 || key_cmp(v[q].a, v[q].b, v[q - 1].a, v[q - 1].b)) u++;
+    nuniq[i] = u;
+    cand[i] = (ocand *)malloc((u ? u : 1) * sizeof(ocand));
+    if (!cand[i]) continue;
+    for (q = 0; q < np;) {
+      size_t j = q;
+      nsum num = {0.0, 0.0}, abssum = {0.0, 0.0};
+      okey key;
+      while (j < np && !key_cmp(v[j].a, v[j].b, v[q].a, v[q].b)) {
+        nsum_add(&num, v[j].v);
+        nsum_add(&abssum, fabs(v[j].v));
+        j++;
+      }
+      key.a = v[q].a;
+      key.b = v[q].b;
+      if (nd && bsearch(&key, psi, nd, sizeof(okey), okey_cmp)) {
+        nexcl[i]++;
+      } else {
+        ocand *o = &cand[i][k++];
+        o->a = key.a;
+        o->b = key.b;
+        o->haa = diag_with_abs(&I, key.a, key.b, &o->haa_abs);
+        o->num = nsum_get(&num);
+        o->abssum = nsum_get(&abssum);
+        o->score = o->num / (E0 - o->haa);
+      }
+      q = j;
+    }
+    ncand[i] = k;
+    free(part[i]);
+    part[i] = NULL;
+  }
+
+  /* 4. every list's candidates, in key order */
+  {
+    size_t u = 0, k = 0, e = 0;
+    ocand *all;
+    for (i = 0; i < nparts; i++) {
+      if (!cand[i]) bad = 1;
+      u += ncand[i];
+      r->unique += nuniq[i];
+      e += nexcl[i];
+    }
+    r->excluded = e;
+    if (bad) goto done;
+    all = (ocand *)malloc((u ? u : 1) * sizeof(ocand));
+    r->a = (uint64_t *)malloc((u ? u : 1) * sizeof(uint64_t));
+    r->b = (uint64_t *)malloc((u ? u : 1) * sizeof(uint64_t));
+    r->num = (double *)malloc((u ? u : 1) * sizeof(double));
+    r->abssum = (double *)malloc((u ? u : 1) * sizeof(double));
+    r->haa = (double *)malloc((u ? u : 1) * sizeof(double));
+    r->haa_abs = (double *)malloc((u ? u : 1) * sizeof(double));
+    r->score = (double *)malloc((u ? u : 1) * sizeof(double));
+    if (!all || !r->a || !r->b || !r->num || !r->abssum || !r->haa || !r->haa_abs || !r->score) {
+      free(all);
+      bad = 1;
+      goto done;
+    }
+    for (i = 0; i < nparts; i++) {
+      memcpy(all + k, cand[i], ncand[i] * sizeof(ocand));
+      k += ncand[i];
+    }
+    qsort(all, u, sizeof(ocand), ocand_cmp);
+    for (k = 0; k < u; k++) {
+      r->a[k] = all[k].a;
+      r->b[k] = all[k].b;
+      r->num[k] = all[k].num;
+      r->abssum[k] = all[k].abssum;
+      r->haa[k] = all[k].haa;
+      r->haa_abs[k] = all[k].haa_abs;
+      r->score[k] = all[k].score;
+    }
+    r->ncand = u;
+    free(all);
+  }
+
+done:
+  if (gens)
+    for (t = 0; t < (size_t)nt; t++) free(gens[t].P.v);
+  if (part)
+    for (i = 0; i < nparts; i++) free(part[i]);
+  if (cand)
+    for (i = 0; i < nparts; i++) free(cand[i]);
+  free(gens);
+  free(cnt);
+  free(off);
+  free(fill);
+  free(part);
+  free(cand);
+  free(ncand);
+  free(nuniq);
+  free(nexcl);
+  free(psi);
+  free(core);
+  if (bad) {
+    oracle_free(r);
+    return NULL;
+  }
   return r;
 }
 
@@ -455,13 +703,14 @@ void oracle_result_stats(const oresult *r, size_t *out5) {
 }
 
 void oracle_result_copy(const oresult *r, uint64_t *a, uint64_t *b, double *num, double *abssum,
-                        double *haa, double *score) {
+                        double *haa, double *haa_abs, double *score) {
   size_t k = r->ncand;
   memcpy(a, r->a, k * sizeof(uint64_t));
   memcpy(b, r->b, k * sizeof(uint64_t));
   memcpy(num, r->num, k * sizeof(double));
   memcpy(abssum, r->abssum, k * sizeof(double));
   memcpy(haa, r->haa, k * sizeof(double));
+  memcpy(haa_abs, r->haa_abs, k * sizeof(double));
   memcpy(score, r->score, k * sizeof(double));
 }
 
@@ -514,6 +763,16 @@ double oracle_diag(int n, const double *h1, const double *eri, double ecore, uin
                    uint64_t b) {
   oints I = {n, ecore, h1, eri};
   return oracle_diag_impl(&I, a, b);
+}
+
+/* Sum of the magnitudes of the terms of <D|H|D> (the scale of its rounding
+ * error). */
+double oracle_diag_abs(int n, const double *h1, const double *eri, double ecore, uint64_t a,
+                       uint64_t b) {
+  oints I = {n, ecore, h1, eri};
+  double m = 0.0;
+  diag_with_abs(&I, a, b, &m);
+  return m;
 }
 
 /* Dense matrix H[i][j] = <D_i|H|D_j> over a list of determinants (row-major). */

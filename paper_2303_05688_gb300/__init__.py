@@ -68,7 +68,8 @@ class _Stats(ct.Structure):
                 ("excluded", ct.c_uint64), ("selected", ct.c_uint64), ("batches", ct.c_uint64),
                 ("max_batch", ct.c_uint64), ("ncore", ct.c_uint64), ("max_level", ct.c_uint64),
                 ("tile_launches", ct.c_uint64), ("tile_records", ct.c_uint64),
-                ("oversized_records", ct.c_uint64), ("t_stage", ct.c_double * 8)]
+                ("oversized_records", ct.c_uint64), ("diag_grid_bits", ct.c_uint64),
+                ("t_stage", ct.c_double * 8)]
 
 
 class _DavOpts(ct.Structure):
@@ -129,6 +130,7 @@ class SearchStats:
     tile_launches: int
     tile_records: int
     oversized_records: int
+    diag_grid_bits: int
     t_stage_ms: dict
 
     @classmethod
@@ -136,7 +138,8 @@ class SearchStats:
         names = ["prepare", "plan", "generate", "tiles", "oversized", "score", "select", "total"]
         return cls(s.generated, s.surviving, s.unique, s.excluded, s.selected, s.batches,
                    s.max_batch, s.ncore, s.max_level, s.tile_launches, s.tile_records,
-                   s.oversized_records, {k: s.t_stage[i] for i, k in enumerate(names)})
+                   s.oversized_records, s.diag_grid_bits,
+                   {k: s.t_stage[i] for i, k in enumerate(names)})
 
 
 _lib = None

@@ -8,14 +8,18 @@
 // buffer carved from one fixed device array that the library owns.
 //
 // The array below is a file-scope __device__ variable: every GPU that loads
-// the library holds it (kNoAllocBytes) until the process exits.  Host code
-// cannot use the name g_noalloc_scratch as a device address, so the address is
-// looked up once per device with cudaGetSymbolAddress, with that device
-// current, the first time the entry point runs on it.
+// the library's device code holds it (kNoAllocBytes) until the process exits.
+// Host code cannot use the name g_noalloc_scratch as a device address; every
+// call looks the address up with cudaGetSymbolAddress, with the call's device
+// current.  The lookup is a host-side query of the loaded module, and doing it
+// on every call keeps the address right for whatever context is current (a
+// primary context re-created after cudaDeviceReset holds a new copy of the
+// array at a new address).  With CUDA's lazy module loading the module, and
+// with it the array, is loaded on a device at the first lookup or launch: the
+// first call on a device is where the array is committed.
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 
 #include "asci_internal.cuh"
 
@@ -25,26 +29,16 @@ namespace {
 constexpr size_t kNoAllocMaxPairs = ASCI_NOALLOC_MAX_PAIRS;
 // Per pair: keys (3 x 8 B), values (2 x 8 B), sums (8 B), unpacked keys (16 B),
 // staged inputs (24 B), run flags and positions (12 B); plus radix histograms,
-// scan partials and alignment slack.
+// scan partials, the error word and alignment slack.
 constexpr size_t kNoAllocBytes = kNoAllocMaxPairs * 104 + (2u << 20);
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[64] = {};
-
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array in the current context.
 int noalloc_region(void **out) {
-  int dev = 0;
-  ASCI_TRY_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return ASCI_ECUDA;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void *ptr = nullptr;
-    ASCI_TRY_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = ptr;
-  }
-  *out = g_noalloc_ptr[dev];
+  void *ptr = nullptr;
+  ASCI_TRY_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+  *out = ptr;
   return ASCI_OK;
 }
 
@@ -57,10 +51,15 @@ bool device_accessible(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-__global__ void k_na_pack(const asci_det *d, size_t n, uint64_t *keys) {
+// Packs (alpha, beta) into the 64-bit key; a word with a bit at or above 32
+// does not fit and sets *bad.
+__global__ void k_na_pack(const asci_det *d, size_t n, uint64_t *keys, unsigned *bad) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    keys[i] = pack_key((uint32_t)d[i].alpha, (uint32_t)d[i].beta);
+       i += (size_t)gridDim.x * blockDim.x) {
+    const asci_det x = d[i];
+    if ((x.alpha | x.beta) >> 32) *bad = 1u;
+    keys[i] = pack_key((uint32_t)x.alpha, (uint32_t)x.beta);
+  }
 }
 
 __global__ void k_na_unpack(const uint64_t *keys, size_t n, asci_det *out) {
@@ -78,11 +77,22 @@ unsigned na_grid(size_t n) {
   return (unsigned)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
 }
 
+// Work queued on `s` reads and writes the shared array; every return path
+// waits for it, so that no call leaves work on the array behind it.
+struct SyncOnExit {
+  cudaStream_t s;
+  ~SyncOnExit() { cudaStreamSynchronize(s); }
+};
+
 int sort_accumulate_noalloc(const asci_det *keys, const double *values, size_t n,
                             asci_det *out_keys, double *out_sums, size_t *out_n, cudaStream_t s) {
   void *region = nullptr;
   ASCI_TRY(noalloc_region(&region));
+  SyncOnExit guard{s};
   Arena arena(s, region, kNoAllocBytes);  // bump mode: allocates nothing
+  unsigned *bad;
+  ASCI_TRY(arena.alloc(&bad, 1));
+  ASCI_TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned), s));
   const asci_det *dk = keys;
   const double *dv = values;
   if (!device_accessible(keys)) {
@@ -107,8 +117,16 @@ int sort_accumulate_noalloc(const asci_det *keys, const double *values, size_t n
   ASCI_TRY(arena.alloc(&v1, n));
   ASCI_TRY(arena.alloc(&us, n));
   ASCI_TRY(arena.alloc(&dok, n));
-  k_na_pack<<<na_grid(n), 256, 0, s>>>(dk, n, k0);
+  k_na_pack<<<na_grid(n), 256, 0, s>>>(dk, n, k0, bad);
   ASCI_CHECK_LAUNCH();
+  unsigned hbad = 0;
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  if (hbad) {
+    record_error("asci_sort_accumulate_noalloc: a key word has bits at or above 32", __FILE__,
+                 __LINE__);
+    return ASCI_EINVAL;
+  }
   ASCI_TRY_CUDA(cudaMemcpyAsync(v0, dv, n * sizeof(double), cudaMemcpyDefault, s));
   size_t u = 0;
   ASCI_TRY(sort_accumulate(&k0, &k1, &v0, &v1, n, uk, us, &u, arena));

@@ -180,6 +180,18 @@ __global__ void k_input_keys(const asci_det *dets, size_t nd, uint64_t *keys) {
     keys[i] = pack_key((uint32_t)dets[i].alpha, (uint32_t)dets[i].beta);
 }
 
+// As k_input_keys for keys not validated before: a word with a bit at or
+// above 32 does not fit the packed key and sets *bad.
+__global__ void k_input_keys_checked(const asci_det *dets, size_t nd, uint64_t *keys,
+                                     unsigned *bad) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const asci_det d = dets[i];
+    if ((d.alpha | d.beta) >> 32) *bad = 1u;
+    keys[i] = pack_key((uint32_t)d.alpha, (uint32_t)d.beta);
+  }
+}
+
 // core sorted by alpha: group heads, per-det beta and coefficient in that order
 __global__ void k_group_heads(const uint64_t *alpha_sorted, const uint32_t *pos,
                               const uint64_t *core_keys, const double *core_c, size_t m,
@@ -746,6 +758,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   F.ncore = (uint32_t)m;
   F.prec = o.precision == ASCI_FP32_INT_COMP_ACC ? 2 : (o.precision == ASCI_FP32_INT_FP64_ACC ? 1 : 0);
   ASCI_TRY(build_fx(h1, eri, n, na, nb, ints->ecore, E0, arena, &F.X, &F.E0_x));
+  if (st) st->diag_grid_bits = (uint64_t)F.X.s;
   {
     uint32_t *core_alpha32;
     int64_t *Dx, *Fa, *Fb;
@@ -1301,8 +1314,17 @@ int asci_sort_accumulate(const asci_det *keys, const double *values, size_t n,
   ASCI_TRY(arena.alloc(&v1, n));
   ASCI_TRY(out_buffer(out_sums, n, &us, arena));
   ASCI_TRY(out_buffer(out_keys, n, &dok, arena));
-  k_input_keys<<<grid_for(n), 256, 0, s>>>(dk, n, k0);
+  unsigned *bad, hbad = 0;
+  ASCI_TRY(arena.alloc(&bad, 1));
+  ASCI_TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned), s));
+  k_input_keys_checked<<<grid_for(n), 256, 0, s>>>(dk, n, k0, bad);
   ASCI_CHECK_LAUNCH();
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  if (hbad) {
+    record_error("asci_sort_accumulate: a key word has bits at or above 32", __FILE__, __LINE__);
+    return ASCI_EINVAL;
+  }
   ASCI_TRY_CUDA(cudaMemcpyAsync(v0, dv, n * sizeof(double), cudaMemcpyDefault, s));
   size_t u = 0;
   ASCI_TRY(sort_accumulate(&k0, &k1, &v0, &v1, n, uk, us, &u, arena));

@@ -381,6 +381,196 @@ def test_pt2_pin_catches_planted_mistakes(oracle_mod):
 
 
 # --------------------------------------------------------------------------
+# Alg. 2's partial-score screen, the brute-force numerator and the core order
+# --------------------------------------------------------------------------
+
+def _excitation_level(A, B, i_idx, j_idx):
+    """Excitation level between determinants i and j of (A, B), as a matrix."""
+    a, b = A.astype(np.int64), B.astype(np.int64)
+    xa = a[i_idx][:, None] ^ a[j_idx][None, :]
+    xb = b[i_idx][:, None] ^ b[j_idx][None, :]
+    pop = np.vectorize(lambda x: bin(int(x)).count("1"))
+    return (pop(xa) + pop(xb)) // 2
+
+
+def _screen_bruteforce(H, A, B, psi, c, E0, C, eps):
+    """Alg. 2 over the dense brute-force H: the generated pairs are (i, j) with j
+    a core determinant (the C largest |c|, distinct here) and i one or two
+    excitations away (H_ij = 0 included); a pair survives when
+    |H_ij c_j / (E0 - H_ii)| > eps (eps = 0: every pair).  Returns the surviving
+    pair count and {i: (numerator, sum |H_ij c_j|)} over targets outside psi."""
+    order = np.argsort(-np.abs(c), kind="stable")[:C]
+    core, cc = psi[order], c[order]
+    lvl = _excitation_level(A, B, np.arange(len(A)), core)
+    inpsi = np.zeros(len(A), dtype=bool)
+    inpsi[psi] = True
+    surv, out = 0, {}
+    for jj, j in enumerate(core):
+        for i in np.nonzero((lvl[:, jj] == 1) | (lvl[:, jj] == 2))[0]:
+            v = H[i, j] * cc[jj]
+            if eps > 0.0 and not abs(v / (E0 - H[i, i])) > eps:
+                continue
+            surv += 1
+            if not inpsi[i]:
+                n0, a0 = out.get(i, (0.0, 0.0))
+                out[i] = (n0 + v, a0 + abs(v))
+    return surv, out
+
+
+def _partial_scores(H, A, B, psi, c, E0, C):
+    order = np.argsort(-np.abs(c), kind="stable")[:C]
+    core, cc = psi[order], c[order]
+    lvl = _excitation_level(A, B, np.arange(len(A)), core)
+    ps = []
+    for jj, j in enumerate(core):
+        for i in np.nonzero((lvl[:, jj] == 1) | (lvl[:, jj] == 2))[0]:
+            ps.append(abs(H[i, j] * cc[jj] / (E0 - H[i, i])))
+    return np.array(ps)
+
+
+def _check_screen(om, ints, H, A, B, psi, c, E0, C, eps):
+    surv, want = _screen_bruteforce(H, A, B, psi, c, E0, C, eps)
+    res = om.search(ints, A[psi], B[psi], c, E0, C, eps=eps)
+    assert res.surviving == surv, (eps, res.surviving, surv)
+    key_of = {(int(A[i]), int(B[i])): i for i in range(len(A))}
+    got = {key_of[(int(a), int(b))]: k for k, (a, b) in enumerate(zip(res.a, res.b))}
+    assert set(got) == set(want), eps
+    for i, k in got.items():
+        num, mag = want[i]
+        assert abs(res.num[k] - num) <= 1e-13 * max(1.0, mag)
+    return surv
+
+
+def pin_eps_screen(om):
+    """The oracle's eps screen equals the brute-force screen on a complete
+    sector with random integrals, for eps at quantiles of the partial scores and
+    within 1e-13 relative of one pair's partial score on either side; and, on
+    the Hubbard ring where every quantity is exact, a pair whose partial score
+    equals eps is dropped (the screen is strict)."""
+    n, na, nb = 6, 3, 3
+    h1, eri, _ = W.random_molecular(n, 41)
+    ec = 0.25
+    ints = om.Ints(h1, eri, ec)
+    A, B = fock.sector(n, na, nb)
+    H = fock.hamiltonian(n, h1, eri, ec, A, B)
+    rng = np.random.default_rng(17)
+    psi = rng.choice(len(A), 30, replace=False)
+    c = rng.normal(size=30)
+    C = 14
+    E0 = float(np.min(np.diag(H))) - 0.4
+    ps = np.sort(_partial_scores(H, A, B, psi, c, E0, C))
+    ps = ps[ps > 0]
+    counts = []
+    for q in (0.1, 0.5, 0.9):
+        counts.append(_check_screen(om, ints, H, A, B, psi, c, E0, C, float(np.quantile(ps, q))))
+    assert counts[0] > counts[1] > counts[2] > 0
+    # a partial score isolated from its neighbours by more than 1e-12 relative
+    gaps = np.minimum(np.diff(ps)[:-1], np.diff(ps)[1:]) / ps[1:-1]
+    k = 1 + int(np.argmax(gaps > 1e-9))
+    p = float(ps[k])
+    above = _check_screen(om, ints, H, A, B, psi, c, E0, C, p * (1.0 - 1e-13))
+    below = _check_screen(om, ints, H, A, B, psi, c, E0, C, p * (1.0 + 1e-13))
+    assert above == below + 1
+    # exact arithmetic: Hubbard ring, c powers of two, E0 exact
+    h1, eri, ec = W.hubbard_ring(n, 1.0, 4.0)
+    ints = om.Ints(h1, eri, ec)
+    H = fock.hamiltonian(n, h1, eri, ec, A, B)
+    assert np.array_equal(H, om.dense_h(ints, A, B))
+    psi = rng.choice(len(A), 12, replace=False)
+    c = np.array([(-1.0) ** k * 2.0 ** -k for k in range(12)])
+    E0 = -3.5
+    ps = _partial_scores(H, A, B, psi, c, E0, 12)
+    p = float(np.unique(ps[ps > 0])[len(np.unique(ps[ps > 0])) // 2])
+    tied = int(np.sum(ps == p))
+    at = _check_screen(om, ints, H, A, B, psi, c, E0, 12, p)
+    just_below = _check_screen(om, ints, H, A, B, psi, c, E0, 12, float(np.nextafter(p, 0.0)))
+    assert tied > 0 and just_below == at + tied
+
+
+def pin_numerator(om):
+    """oracle.numerator(target, core) = sum over core j != target of
+    H_target,j c_j, for every determinant of two complete sectors (inside and
+    outside the core), with the brute-force H; also its sum of magnitudes."""
+    for n, na, nb, ncore in ((6, 3, 3, 25), (7, 3, 2, 40)):
+        h1, eri, _ = W.random_molecular(n, 5 * n + nb)
+        ec = -0.6
+        ints = om.Ints(h1, eri, ec)
+        A, B = fock.sector(n, na, nb)
+        H = fock.hamiltonian(n, h1, eri, ec, A, B)
+        rng = np.random.default_rng(n)
+        core = rng.choice(len(A), ncore, replace=False)
+        cc = rng.normal(size=ncore)
+        Hoff = H - np.diag(np.diag(H))
+        want = Hoff[:, core] @ cc
+        want_abs = np.abs(Hoff[:, core]) @ np.abs(cc)
+        for i in range(len(A)):
+            got, mag = om.numerator(ints, (A[i], B[i]), A[core], B[core], cc)
+            assert abs(got - want[i]) <= 1e-13 * max(1.0, want_abs[i]), i
+            assert abs(mag - want_abs[i]) <= 1e-13 * max(1.0, want_abs[i]), i
+
+
+def pin_core_ties(om):
+    """core_select under tied |c| equals a plain sort by (|c| descending, beta
+    word, alpha word), for C across the ties."""
+    A, B = fock.sector(6, 3, 2)
+    rng = np.random.default_rng(23)
+    idx = rng.choice(len(A), 70, replace=False)
+    A, B = A[idx], B[idx]
+    c = rng.choice([-0.5, 0.5, -0.25, 0.25, 0.125], 70)
+    want = sorted(range(70), key=lambda i: (-abs(c[i]), int(B[i]), int(A[i])))
+    for C in (1, 3, 10, 25, 40, 69, 70, 100):
+        assert list(om.core_select(A, B, c, C)) == want[:C], C
+
+
+def test_eps_screen_equals_bruteforce(oracle_mod):
+    pin_eps_screen(oracle_mod)
+
+
+def test_numerator_equals_dense_product(oracle_mod):
+    pin_numerator(oracle_mod)
+
+
+def test_core_select_ties_by_key(oracle_mod):
+    pin_core_ties(oracle_mod)
+
+
+@pytest.mark.parametrize("eps", [0.0, 2e-6])
+def test_all_core_oracle_equals_single_core(oracle_mod, eps):
+    """The all-core form of the search returns the single-core result bit for
+    bit (keys, numerators, sums of magnitudes, diagonals, scores, counters)."""
+    w, h1, eri, ec, A, B, c = _small_random_case()
+    ints = oracle_mod.Ints(h1, eri, ec)
+    E0 = -20.0
+    r1 = oracle_mod.search(ints, A, B, c, E0, 60, eps=eps)
+    for threads in (2, 5):
+        r2 = oracle_mod.search(ints, A, B, c, E0, 60, eps=eps, threads=threads)
+        for f in ("a", "b", "num", "abssum", "haa", "haa_abs", "score"):
+            assert np.array_equal(getattr(r1, f), getattr(r2, f)), f
+        assert (r1.generated, r1.surviving, r1.unique, r1.excluded, r1.ncore) == \
+            (r2.generated, r2.surviving, r2.unique, r2.excluded, r2.ncore)
+    if eps > 0:
+        assert r1.surviving < r1.generated
+
+
+def test_diag_abs_is_sum_of_term_magnitudes(oracle_mod):
+    """diag_abs: |ecore| + sum |h_pp| + sum over same-spin pairs p<q |J - K| +
+    sum over opposite-spin pairs |J|, written out with numpy."""
+    n = 7
+    h1, eri, _ = W.random_molecular(n, 8)
+    ints = oracle_mod.Ints(h1, eri, -1.5)
+    for a, b in ((0b0010111, 0b1000011), (0b1110000, 0b0000111)):
+        oa = [p for p in range(n) if a >> p & 1]
+        ob = [p for p in range(n) if b >> p & 1]
+        J = lambda p, q: eri[p, p, q, q]
+        K = lambda p, q: eri[p, q, q, p]
+        want = 1.5 + sum(abs(h1[p, p]) for p in oa + ob)
+        for o in (oa, ob):
+            want += sum(abs(J(p, q) - K(p, q)) for p in o for q in o if p < q)
+        want += sum(abs(J(p, q)) for p in oa for q in ob)
+        assert abs(oracle_mod.diag_abs(ints, (a, b)) - want) <= 1e-13 * want
+
+
+# --------------------------------------------------------------------------
 # planted mistakes: each must be caught by a pin
 # --------------------------------------------------------------------------
 
@@ -390,7 +580,8 @@ MUTATIONS = {
                          "return -sg * (ERI(I, i, a, j, b) - ERI(I, i, b, j, a));"),
     "transpose_double_operand": ("ERI(I, i, a, j, b) - ERI(I, i, b, j, a)",
                                  "ERI(I, i, j, a, b) - ERI(I, i, b, j, a)"),
-    "drop_cross_coulomb": ("if (occupied(a, p) && occupied(b, q)) nsum_add(&acc, ERI(I, p, p, q, q));", ""),
+    "drop_cross_coulomb": ("if (occupied(a, p) && occupied(b, q)) diag_term(&acc, &mag, ERI(I, p, p, q, q));",
+                           ""),
     "wrong_phase_range": ("for (k = lo + 1; k < hi; k++)", "for (k = lo; k < hi; k++)"),
     "opposite_spin_sign": ("int s = single_sign(ket_a, ha[0], pa[0]) * single_sign(ket_b, hb[0], pb[0]);",
                            "int s = single_sign(ket_a, ha[0], pa[0]);"),
@@ -424,3 +615,43 @@ def test_pins_catch_planted_mistakes(tmp_path, name):
             caught = True
             break
     assert caught, f"planted mistake {name} went unnoticed"
+
+
+# mistakes in the search's screen, the brute-force numerator and the core order,
+# each with the pin that must catch it
+SEARCH_MUTATIONS = {
+    "screen_on_value_alone": ("if (!(fabs(v / (g->E0 - hii)) > g->eps)) return;",
+                              "if (!(fabs(v) > g->eps)) return;", "pin_eps_screen"),
+    "screen_not_strict": ("if (!(fabs(v / (g->E0 - hii)) > g->eps)) return;",
+                          "if (!(fabs(v / (g->E0 - hii)) >= g->eps)) return;", "pin_eps_screen"),
+    "screen_denominator_sign": ("if (!(fabs(v / (g->E0 - hii)) > g->eps)) return;",
+                                "if (!(fabs(v / (g->E0 + hii)) > g->eps)) return;",
+                                "pin_eps_screen"),
+    "numerator_skips_doubles": ("if (count_bits(xa) + count_bits(xb) > 4 || (xa == 0 && xb == 0)) continue;",
+                                "if (count_bits(xa) + count_bits(xb) >= 4 || (xa == 0 && xb == 0)) continue;",
+                                "pin_numerator"),
+    "numerator_keeps_diagonal": ("if (count_bits(xa) + count_bits(xb) > 4 || (xa == 0 && xb == 0)) continue;",
+                                 "if (count_bits(xa) + count_bits(xb) > 4) continue;", "pin_numerator"),
+    "core_ties_reversed": ("if (p->absc != q->absc) return p->absc > q->absc ? -1 : 1;\n"
+                           "  return key_cmp(p->a, p->b, q->a, q->b);",
+                           "if (p->absc != q->absc) return p->absc > q->absc ? -1 : 1;\n"
+                           "  return key_cmp(q->a, q->b, p->a, p->b);", "pin_core_ties"),
+    "core_ties_alpha_high": ("if (p->absc != q->absc) return p->absc > q->absc ? -1 : 1;\n"
+                             "  return key_cmp(p->a, p->b, q->a, q->b);",
+                             "if (p->absc != q->absc) return p->absc > q->absc ? -1 : 1;\n"
+                             "  return key_cmp(p->b, p->a, q->b, q->a);", "pin_core_ties"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SEARCH_MUTATIONS))
+def test_search_pins_catch_planted_mistakes(tmp_path, oracle_mod, name):
+    src = open(os.path.join(os.path.dirname(os.path.dirname(__file__)), "oracle", "asci_oracle.c")).read()
+    old, new, pin = SEARCH_MUTATIONS[name]
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    path = tmp_path / "mut.c"
+    path.write_text(src.replace(old, new, 1))
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c99", "-fPIC", "-shared", "-o", str(so), str(path), "-lm"])
+    with oracle_mod.substitute(str(so)):
+        with pytest.raises(AssertionError):
+            globals()[pin](oracle_mod)
