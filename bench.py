@@ -31,12 +31,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ASCI search scored excitations/s at (24e,30o)"
-# DRAM bytes (read + write) per staged pair reduced by the tile kernel k_cells
-# on the (24e,30o) workload: ncu's dram__bytes_read.sum + dram__bytes_write.sum
-# summed over the 39 launches of one search (112.16 GB), divided by that
-# search's 6.675e9 staged pairs (profiles/k_cells_random24e30o.md).  Reported
-# as `traffic` for that workload only.
-TILE_DRAM_BYTES_PER_RECORD = {"random_24e30o": 16.80}
+# DRAM bytes (read + write) per staged pair reduced by the tile kernel k_cells,
+# from one ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum over every tile launch of one search, divided by its
+# staged pairs); `traffic` is this figure scaled to one launch, and null for
+# a workload without a capture.
+TILE_DRAM_BYTES_PER_RECORD: dict = {}
+TILE_DRAM_SOURCE = ""
 UNIT = "excitations/s"
 
 
@@ -57,6 +58,12 @@ def parse():
                    help="system of --workload pt2 (its psi and core size)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-rows", action="store_true",
+                   help="skip the extra measured rows (eps 1e-10, FP32 variants, configs 1-2)")
+    p.add_argument("--C", type=int, default=0,
+                   help="core size override (0: the workload's); for profiling a smaller case")
+    p.add_argument("--max-batch-pairs", type=int, default=0,
+                   help="constraint-batch cap in pairs (0: sized from free memory)")
     p.add_argument("--cpu-sample-core", type=int, default=0,
                    help="core dets in each oracle sample (0: sized to ~10 s)")
     return p.parse_args()
@@ -138,12 +145,17 @@ def peaks():
 
 # -------------------------------------------------------------- reference ---
 
-def cpu_sample(w, h1, eri, ec, A, B, c, E0, core, np):
-    """Time the oracle (as it stands) on the top `core` core dets of the workload."""
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def cpu_sample(w, h1, eri, ec, A, B, c, E0, core, np, threads=1):
+    """Time the oracle (as it stands) on the top `core` core dets of the
+    workload, single-core or its all-core form (`threads`)."""
     import oracle
     ints = oracle.Ints(h1, eri, ec)
     t0 = time.perf_counter()
-    r = oracle.search(ints, A, B, c, E0, core)
+    r = oracle.search(ints, A, B, c, E0, core, threads=threads)
     dt = time.perf_counter() - t0
     return r.generated, dt
 
@@ -172,14 +184,16 @@ def oracle_pt2_rate(w, h1, eri, ec, A, B, c, E0, core):
     return core * W.n_excitations(w.norb, w.na, w.nb) / (time.perf_counter() - t0)
 
 
-def size_cpu_sample(w, args):
+def size_cpu_sample(w, args, threads=1):
     if args.cpu_sample_core:
         return args.cpu_sample_core
-    # about 10 s of oracle work on this host class (measured ~1e6 pairs/s)
+    # about 10-15 s of oracle work on this host class (measured ~7e5 pairs/s
+    # per core; the all-core form scales to about half of the cores' sum)
     from math import ceil
     import workloads as W
     nexc = W.n_excitations(w.norb, w.na, w.nb)
-    return max(1, min(w.C, int(ceil(1.0e7 / nexc))))
+    scale = 1.0 if threads <= 1 else max(1.0, 0.5 * threads)
+    return max(1, min(w.C, int(ceil(1.0e7 * scale / nexc))))
 
 
 def run_reference(args):
@@ -189,17 +203,19 @@ def run_reference(args):
     w, h1, eri, ec, A, B, c, E0, np = load_workload(args.workload)
     import oracle
     oracle.build()
-    core = size_cpu_sample(w, args)
+    cores = host_cores()
+    core = size_cpu_sample(w, args, cores)
     for _ in range(args.warmup):
-        cpu_sample(w, h1, eri, ec, A, B, c, E0, max(1, core // 10), np)
+        cpu_sample(w, h1, eri, ec, A, B, c, E0, max(1, core // 10), np, cores)
     tot_pairs, tot_t = 0, 0.0
     for _ in range(args.steps):
-        p, dt = cpu_sample(w, h1, eri, ec, A, B, c, E0, core, np)
+        p, dt = cpu_sample(w, h1, eri, ec, A, B, c, E0, core, np, cores)
         tot_pairs += p
         tot_t += dt
     value = tot_pairs / tot_t
-    sample = (f"oracle on the top {core} of {w.C} core dets of {w.name} per step "
-              f"({tot_pairs // args.steps} excitations/step), full psi for exclusion")
+    sample = (f"all-core oracle ({cores} threads) on the top {core} of {w.C} core dets of "
+              f"{w.name} per step ({tot_pairs // args.steps} excitations/step), full psi for "
+              f"exclusion")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -207,7 +223,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "norb": w.norb, "nelec": [w.na, w.nb], "ndets": w.ndets,
                    "C": w.C, "N": w.N, "eps": args.eps},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -216,6 +232,66 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------- main ---
+
+def timed_search(torch, fn, flush, stream, steps):
+    """Mean device milliseconds of fn() over `steps` calls (L2 flushed before
+    each, CUDA events on the search's stream) and the last call's stats."""
+    ts, st = [], None
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, st = fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.mean(ts), st
+
+
+def extra_rows(asci, torch, w, dets, cf, h1d, erid, ec, E0, flush, stream, args):
+    import workloads as W
+    rows = []
+    steps = max(3, min(args.steps, 5))
+
+    def add(label, ms, st, **extra):
+        rows.append(dict(row=label, ms_per_step=round(ms, 3),
+                         value=st.generated / (ms / 1e3), unit=UNIT, surviving=st.surviving,
+                         unique=st.unique, **extra))
+
+    fn = lambda: asci.search(dets, cf, E0, h1d, erid, ec, w.C, w.N, eps=1e-10)
+    fn()
+    ms, st = timed_search(torch, fn, flush, stream, steps)
+    add(f"{w.name} eps=1e-10", ms, st)
+    for name, prec in (("fp32_fp64acc", asci.FP32_INT_FP64_ACC), ("fp32_comp", asci.FP32_INT_COMP_ACC)):
+        fn = lambda prec=prec: asci.search(dets, cf, E0, h1d, erid, ec, w.C, w.N, precision=prec)
+        fn()
+        ms, st = timed_search(torch, fn, flush, stream, steps)
+        add(f"{w.name} precision={name}", ms, st)
+    dev = dets.device
+    for name in ("hubbard_8e8o", "random_16e16o"):
+        if name not in W.WORKLOADS or name == w.name:
+            continue
+        ww = W.WORKLOADS[name]
+        h1, eri, ec2 = ww.integrals()
+        if ww.kind == "hubbard":  # the 100-determinant CI start of the (8e,8o) ring
+            with open(os.path.join(ROOT, "tests", "golden", "hubbard_8e8o_psi.json")) as f:
+                g = json.load(f)
+            A, B, c, E02 = g["alpha"], g["beta"], g["c"], float(g["E0"])
+        else:
+            A, B, c = ww.psi()
+            E02 = W.stored_e0(name)
+        np_ = __import__("numpy")
+        d = torch.tensor(np_.stack([np_.asarray(A, dtype=np_.uint64),
+                                    np_.asarray(B, dtype=np_.uint64)], 1).astype("int64"),
+                         device=dev)
+        cc, hh, ee = (torch.tensor(np_.asarray(x, dtype=np_.float64), device=dev)
+                      for x in (c, h1, eri))
+        fn = lambda: asci.search(d, cc, E02, hh, ee, ec2, ww.C, ww.N)
+        fn()
+        ms, st = timed_search(torch, fn, flush, stream, max(steps, 5))
+        add(name, ms, st, C=ww.C, N=ww.N, ndets=ww.ndets)
+    return rows
+
 
 def run_batched(args):
     """Many independent small searches (512 uneven systems): searches/s with the
@@ -559,11 +635,15 @@ def main():
 
     sharded = args.sharded and world > 1
 
+    Ccore = args.C or w.C
+    kw = dict(eps=args.eps, precision=prec)
+    if args.max_batch_pairs:
+        kw["max_batch_pairs"] = args.max_batch_pairs
+
     def one(d=dets, cc=cf, hh=h1d, ee=erid):
         if sharded:
-            return asci.sharded_search(d, cc, E0, hh, ee, ec, w.C, w.N, eps=args.eps,
-                                       precision=prec)
-        return asci.search(d, cc, E0, hh, ee, ec, w.C, w.N, eps=args.eps, precision=prec)
+            return asci.sharded_search(d, cc, E0, hh, ee, ec, Ccore, w.N, **kw)
+        return asci.search(d, cc, E0, hh, ee, ec, Ccore, w.N, **kw)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -650,14 +730,16 @@ def main():
     achieved = bytes_per_launch / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
     per_rec = TILE_DRAM_BYTES_PER_RECORD.get(w.name)
     traffic = per_rec * tile_records / max(tile_launches, 1) if per_rec else None
+    traffic_note = (f"{per_rec} DRAM bytes per staged pair from {TILE_DRAM_SOURCE}, scaled to "
+                    "one launch" if per_rec else "no capture of the current kernel")
     # the search as a whole against its algorithmic floor,
     # B_alg = 32 P + 24 C + 16 |psi| + 32 U + 16 N bytes
     b_alg = (32 * stats.surviving + 24 * stats.ncore + 16 * w.ndets + 32 * stats.unique
              + 16 * stats.selected)
     t_search = statistics.mean(times) / 1e3
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_cells (on-chip hash reduction of staged pairs)",
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_note,
+                "kernel": "k_cells (on-chip counting-sort reduction of staged pairs)",
                 "peak_kind": peak_kind, "launches_per_step": tile_launches / args.steps,
                 "alg_bytes_per_launch": bytes_per_launch, "ms_per_launch": per_launch_s * 1e3,
                 "search": {"alg_bytes_per_step": b_alg, "achieved": b_alg / t_search / 1e9,
@@ -668,13 +750,26 @@ def main():
                     (ts["tiles"] + ts["oversized"]) / 1e3, 1e-12),
                 "stage_ms": {k: round(v, 3) for k, v in ts.items()}}
 
-    cpu = None
+    # further measured rows (same inputs, device-resident, L2 flushed, CUDA
+    # events): the paper's screen eps = 1e-10 (Sec. 3), the two FP32-integral
+    # variants, and the two smaller configurations
+    rows = None
+    if not args.no_rows and world == 1 and not sharded:
+        rows = extra_rows(asci, torch, w, dets, cf, h1d, erid, ec, E0, flush, stream, args)
+
+    cpu = cpu1 = None
     if not args.no_cpu_baseline and world == 1:
-        core = size_cpu_sample(w, args)
-        p, dt = cpu_sample(w, h1, eri, ec, A, B, c, E0, core, np)
-        cpu = {"value": p / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"oracle on the top {core} of {w.C} core dets of {w.name} "
-                         f"({p} excitations, {dt:.1f} s), full psi for exclusion"}
+        cores = host_cores()
+        core = size_cpu_sample(w, args, cores)
+        p, dt = cpu_sample(w, h1, eri, ec, A, B, c, E0, core, np, cores)
+        cpu = {"value": p / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"all-core oracle ({cores} threads) on the top {core} of {Ccore} core dets "
+                         f"of {w.name} ({p} excitations, {dt:.1f} s), full psi for exclusion"}
+        core1 = size_cpu_sample(w, args)
+        p1, dt1 = cpu_sample(w, h1, eri, ec, A, B, c, E0, core1, np)
+        cpu1 = {"value": p1 / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"single-core oracle on the top {core1} of {w.C} core dets of {w.name} "
+                          f"({p1} excitations, {dt1:.1f} s), full psi for exclusion"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -682,13 +777,13 @@ def main():
         "higher_is_better": True, "scaling": "strong" if sharded else "weak", "vs_baseline": None,
         "dtype": "f64" if prec == asci.FP64 else "f32+f64", "data": "synthetic",
         "config": {"workload": w.name, "norb": w.norb, "nelec": [w.na, w.nb], "ndets": w.ndets,
-                   "C": w.C, "N": w.N, "eps": args.eps, "precision": args.precision,
+                   "C": Ccore, "N": w.N, "eps": args.eps, "precision": args.precision,
                    "excitations_per_step": pairs, "unique_per_step": stats.unique,
                    "batches": stats.batches, "l2": "flushed (512 MB write) before each step",
                    "parallelism": (f"constraint shards x{world}" if sharded
                                    else f"replicas x{world}")},
         "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
-        "roofline": roofline, "cpu_baseline": cpu,
+        "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_1core": cpu1, "rows": rows,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

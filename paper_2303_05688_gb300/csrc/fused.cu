@@ -525,11 +525,12 @@ __device__ __forceinline__ int64_t shfl64(int64_t x, int src) {
 
 // Staging position of one pair: in place for classes that fit a tile (slot
 // `inplace`), else the next free slot of its hash-bucket cell (warp-aggregated
-// counters) or, once the cell holds kCap records, the next entry of the spill
-// list (*spill set, *pos the entry).  Returns false for an idle lane.
+// counters; the cell's slots start at `cellpos`) or, once the cell holds kCap
+// records, the next entry of the spill list (*spill set, *pos the entry).
+// Returns false for an idle lane.
 __device__ __forceinline__ bool pair_position(const EmitArgs &A, bool big, bool valid,
-                                              uint32_t cell, uint32_t inplace, uint32_t *pos,
-                                              bool *spill) {
+                                              uint32_t cell, uint32_t cellpos, uint32_t inplace,
+                                              uint32_t *pos, bool *spill) {
   const int lane = threadIdx.x & 31;
   *spill = false;
   if (big) {  // warp-uniform
@@ -540,7 +541,7 @@ __device__ __forceinline__ bool pair_position(const EmitArgs &A, bool big, bool 
     base = __shfl_sync(0xffffffffu, base, leader);
     const uint32_t slot = base + __popc(peers & ((1u << lane) - 1u));
     if (slot < (uint32_t)kCap) {
-      *pos = A.cell_pos0[cell] + slot;
+      *pos = cellpos + slot;
     } else if (valid) {
       *spill = true;
       *pos = atomicAdd(A.n_spill, 1u);
@@ -664,6 +665,7 @@ __global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
     // in-place staging slot of the run's first pair (classes that fit a tile)
     const uint32_t off0 = (uint32_t)(A.soff[gi] + (p0 - A.g_P0[A.gb0 + gi]));
     const uint32_t cell0 = big ? A.cellbase[gi] : 0u, nbk = big ? A.nb[gi] : 1u;
+    const uint32_t cls0 = (uint32_t)A.soff[gi];  // bucket b's slots start at cls0 + b kCap
     // lane L: the L-th occupied and the L-th virtual beta orbital of B
     const int occL = lane < (int)A.E.nb ? nth_set_bit(B, lane) : 0;
     const int virL = lane < (int)vb ? nth_set_bit(~B & full, lane) : 0;
@@ -744,9 +746,11 @@ __global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
       q.tb = B;
       if (q.op == 1) q.tb ^= (1u << q.bi) | (1u << q.ba);
       if (q.op == 2) q.tb ^= (1u << q.bi) | (1u << q.bj) | (1u << q.ba) | (1u << q.bb);
-      q.cell = big ? cell0 + bucket_of(q.tb, nbk) : 0u;
+      const uint32_t bkt = big ? bucket_of(q.tb, nbk) : 0u;
+      q.cell = cell0 + bkt;
       q.pos = 0;
-      q.wr = pair_position(A, big, q.valid, q.cell, off0 + e, &q.pos, &q.spill);
+      q.wr = pair_position(A, big, q.valid, q.cell, cls0 + bkt * (uint32_t)kCap, off0 + e, &q.pos,
+                           &q.spill);
     };
     // software-pipelined: the next chunk's staging slots (an atomic for big
     // classes) are claimed before this chunk's matrix elements are formed
@@ -805,6 +809,7 @@ __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
   __shared__ uint32_t sOrb[kAdTile + 1];  // i | a << 5 | j << 10 | b << 15
   __shared__ uint32_t sTA[kAdTile + 1];   // target alpha string
   __shared__ uint32_t sCls[kAdTile + 1];  // class (relative to the batch)
+  __shared__ uint32_t sBase[kAdTile + 1]; // first staging slot of the class
   __shared__ double sH[kAdTile + 1];      // signed matrix element
   __shared__ int64_t sD[kAdTile + 1];     // determinant-independent diagonal change
   __shared__ uint16_t sItem[kAdTile];     // item of each pair of the step
@@ -827,6 +832,7 @@ __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
       const uint32_t gi = A.item_group[t] - A.gb0;
       sF[i] = A.ad_off[ja + i];
       sPos[i] = (uint32_t)(A.soff[gi] + (A.Wexcl[t] - A.g_P0[A.gb0 + gi]));
+      sBase[i] = (uint32_t)A.soff[gi];
       sG[i] = A.grp_start[k];
       sTA[i] = (uint32_t)(it >> 32);
       sCls[i] = gi;
@@ -870,8 +876,10 @@ __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
       // lanes of one warp may straddle classes of both kinds: position per lane
       uint32_t pos = sPos[lo] + q, cell = 0;
       bool spill = false;
+      uint32_t bkt = 0;
       if (big) {
-        cell = bigl ? A.cellbase[gi] + bucket_of(B, A.nb[gi]) : 0u;
+        bkt = bigl ? bucket_of(B, A.nb[gi]) : 0u;
+        cell = bigl ? A.cellbase[gi] + bkt : 0u;
         const uint32_t peers = __match_any_sync(0xffffffffu, bigl ? cell : 0xffffffffu);
         const int leader = __ffs(peers) - 1;
         uint32_t base = 0;
@@ -880,7 +888,7 @@ __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
         if (bigl) {
           const uint32_t slot = base + __popc(peers & ((1u << lane) - 1u));
           if (slot < (uint32_t)kCap) {
-            pos = A.cell_pos0[cell] + slot;
+            pos = sBase[lo] + bkt * (uint32_t)kCap + slot;
           } else {
             spill = true;
             pos = atomicAdd(A.n_spill, 1u);
@@ -1030,6 +1038,7 @@ struct CellArgs {
   unsigned long long cand_cap;
   unsigned long long *n_unique, *n_excluded;
   unsigned *err;
+  int screened;  // records may carry the eps screen's drop marker
 };
 
 __device__ __forceinline__ uint64_t mix_key(uint64_t z) {
@@ -1152,16 +1161,49 @@ __device__ __forceinline__ uint64_t slot_key(const CellSmem &S, int buf, uint32_
   return (v & kPsiBit) ? S.psik[buf][v & ~kPsiBit] : rec_key(S, buf, v, packed, alpha);
 }
 
+// |x| as a float built from the bits, truncated (relative error below 2^-23);
+// *ok is false when |x| lies outside the normal float range.
+__device__ __forceinline__ float abs_as_float(double x, bool *ok) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  int e = (int)(b >> 52) - 1023 + 127;
+  *ok = e >= 1 && e <= 254;
+  e = e < 1 ? 1 : (e > 254 ? 254 : e);
+  return __uint_as_float(((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
+}
+
+// |v| as a float for the threshold bound: from the bits (no FP64 instruction),
+// +inf when |v| lies above the float range so that the bound always passes.
+__device__ __forceinline__ float abs_bound(double v) {
+  bool ok;
+  const float f = abs_as_float(v, &ok);
+  return (ok || fx_exponent(v) < 1023) ? f : __int_as_float(0x7f800000);
+}
+
 // Sum of five or more values (list from e through next) in the 128-bit
 // fixed-point accumulator anchored to their largest exponent: equal bit for bit
-// for any order.  Kept out of line: rare, and it would weigh on the common
-// path's registers.
+// for any order.  The first walk also sums |v| in float.  |num| <= sum |v|, so
+// a target whose bound cannot reach the running threshold tau |E0 - H_ii|
+// fails the screen whatever its exact numerator: *reach is cleared and the
+// exact sum is skipped.  The test is conservative: a list holds at most kCap =
+// 1024 values, so the float sum lies within 1023 * 2^-24 < 6.1e-5 below the
+// exact sum of the (truncated, hence smaller) terms, which the factor 1.0001
+// covers; tau_f is rounded down and den truncated, and the 0.99999 margin
+// covers the float product.  Kept out of line: rare, and it would weigh on
+// the common path's registers.
 __device__ __noinline__ double long_numerator(const StageRec *r, const uint16_t *next,
-                                              uint32_t e, unsigned *err) {
+                                              uint32_t e, float tau_f, float den, bool *reach,
+                                              unsigned *err) {
   int emax = 1;
+  float sabs = 0.0f;
   for (uint32_t i = e; i != kEndList; i = next[i]) {
     const int ex = fx_exponent(r[i].v);
     emax = ex > emax ? ex : emax;
+    sabs += abs_bound(r[i].v);
+  }
+  const float df = fabsf(den);
+  if (tau_f > 0.0f && df != 0.0f && !(sabs * 1.0001f >= tau_f * df * 0.99999f)) {
+    *reach = false;
+    return 0.0;
   }
   const int frac = fx128_frac_for(emax);
   Fx128 acc = {0, 0};
@@ -1175,9 +1217,10 @@ __device__ __noinline__ double long_numerator(const StageRec *r, const uint16_t 
 }
 
 // Exact numerator over the record list starting at e (values of screened-out
-// records are never inserted).
+// records are never inserted); *reach is cleared when a list of five or more
+// cannot reach the threshold (its sum is then not formed).
 __device__ __forceinline__ double list_numerator(const CellSmem &S, int buf, uint32_t e,
-                                                 unsigned *err) {
+                                                 float tau_f, bool *reach, unsigned *err) {
   const StageRec *r = S.rec[buf];
   const uint32_t e2 = S.next[e];
   if (e2 == kEndList) return r[e].v;
@@ -1189,17 +1232,7 @@ __device__ __forceinline__ double list_numerator(const CellSmem &S, int buf, uin
   const uint32_t e4 = S.next[e3];
   if (e4 == kEndList) return sum4_ordered(0.0, r[e].v, r[e2].v, r[e3].v);
   if (S.next[e4] == kEndList) return sum4_ordered(r[e].v, r[e2].v, r[e3].v, r[e4].v);
-  return long_numerator(r, S.next, e, err);
-}
-
-// |x| as a float built from the bits, truncated (relative error below 2^-23);
-// *ok is false when |x| lies outside the normal float range.
-__device__ __forceinline__ float abs_as_float(double x, bool *ok) {
-  const uint64_t b = (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
-  int e = (int)(b >> 52) - 1023 + 127;
-  *ok = e >= 1 && e <= 254;
-  e = e < 1 ? 1 : (e > 254 ? 254 : e);
-  return __uint_as_float(((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
+  return long_numerator(r, S.next, e, tau_f, r[e].den, reach, err);
 }
 
 __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
@@ -1272,7 +1305,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
       for (int base = 0; base + warp_base < nrec; base += kCellThreads) {
         const int e = base + (int)threadIdx.x;
         int claimed = -1;
-        if (e < nrec && !is_dropped(S.rec[buf][e].v)) {
+        if (e < nrec && !(C.screened && is_dropped(S.rec[buf][e].v))) {
           const uint64_t key = rec_key(S, buf, (uint32_t)e, packed, d.alpha);
           uint32_t h = slot_hash(key);
           int probe = 0;
@@ -1341,9 +1374,11 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
           if (in_psi) {
             ++my_excl;
           } else {
-            const double num = list_numerator(S, buf, e, C.err);
-            pass = true;
-            if (C.tau > 0.0) {
+            bool reach = true;
+            const double num = list_numerator(S, buf, e, C.tau > 0.0 ? C.tau_f : 0.0f, &reach,
+                                              C.err);
+            pass = reach;
+            if (reach && C.tau > 0.0) {
               bool okn;
               const float nf = abs_as_float(num, &okn);
               const float df = fabsf(S.rec[buf][e].den);
@@ -2107,6 +2142,7 @@ static CellArgs cell_args(const FusedCore &F, const Stage &st,
   CA.n_unique = n_unique;
   CA.n_excluded = n_excluded;
   CA.err = err;
+  CA.screened = F.screened;
   return CA;
 }
 

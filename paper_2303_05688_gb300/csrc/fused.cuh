@@ -67,6 +67,7 @@ struct FusedCore {
   size_t npsi;
   uint32_t ncore;
   int prec;  // pair-value precision: 0 FP64, 1 FP32 integrals, 2 FP32 integrals and product
+  int screened;  // Alg. 2's eps screen is on: staged records may be marked dropped
 };
 
 }  // namespace asci

@@ -757,6 +757,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   F.psi_mask = psi_mask;
   F.ncore = (uint32_t)m;
   F.prec = o.precision == ASCI_FP32_INT_COMP_ACC ? 2 : (o.precision == ASCI_FP32_INT_FP64_ACC ? 1 : 0);
+  F.screened = o.eps_search > 0.0 ? 1 : 0;
   ASCI_TRY(build_fx(h1, eri, n, na, nb, ints->ecore, E0, arena, &F.X, &F.E0_x));
   if (st) st->diag_grid_bits = (uint64_t)F.X.s;
   {

@@ -104,10 +104,13 @@ def test_noalloc_host_buffers_at_the_maximum(lib):
 
 def test_noalloc_degenerate_inputs(lib):
     import torch
-    # n = 0: nothing to do, nothing written
-    keys, vals = _case(15, 0)
-    code, k, s = _call(lib, "asci_sort_accumulate_noalloc", keys, vals)
-    assert code == 0 and len(k) == 0
+    # n = 0 (valid buffers): nothing to do, nothing written
+    keys, vals = _case(15, 1)
+    ok = torch.full((1, 2), -1, dtype=torch.int64, device="cuda")
+    m = ct.c_size_t(7)
+    code = lib.asci_sort_accumulate_noalloc(keys.data_ptr(), vals.data_ptr(), 0, ok.data_ptr(),
+                                            ok.data_ptr(), ct.byref(m), None)
+    assert code == 0 and m.value == 0 and int(ok[0, 0]) == -1
     # every key equal: one output, the sum of all values
     n = 4097
     keys = torch.tensor(np.tile(np.array([[5, 9 << 20]], dtype=np.int64), (n, 1)), device="cuda")
