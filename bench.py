@@ -361,7 +361,7 @@ def run_served(args):
                          sy["ecore"], None))
         reqs.append((sy["name"], sy["C"], sy["N"], 0.9 / 24))
     for name, C, N, p in (("random_16e16o", 10000, 100000, 0.08),
-                          ("random_24e30o", 20000, 10 ** 6, 0.02)):
+                          ("random_24e30o", 20000, 10 ** 7, 0.02)):
         w, h1, eri, ec, A, B, c, E0, _ = load_workload(name)
         resident.append((name, A, B, c, h1, eri, ec, E0))
         reqs.append((name, C, N, p))
@@ -428,7 +428,7 @@ def run_served(args):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": "served", "requests": len(stream_reqs),
                    "systems": [r[0] for r in reqs], "mix": "90% 24 small systems, "
-                   "8% (16e,16o) C=1e4 N=1e5, 2% (24e,30o) C=2e4 N=1e6"}}), flush=True)
+                   "8% (16e,16o) C=1e4 N=1e5, 2% (24e,30o) C=2e4 N=1e7"}}), flush=True)
     return 0
 
 
@@ -463,8 +463,23 @@ def run_levels(args):
                          "batches": st.batches, "largest_batch": st.max_batch,
                          "largest_over_mean": st.max_batch / mean_batch,
                          "ms": 1e3 * statistics.mean(ts)})
+    # Fig. 3 analogue: the work (pairs) of every constraint class per level,
+    # from the item weights of the search's own planning step
+    classes = []
+    for lvl in (3, 4, 5, 6):
+        cnt = asci.constraint_classes(d, cf, h1d, ed, ec, w.C, lvl).astype(np.float64)
+        hist = {}
+        for k in np.floor(np.log2(cnt)).astype(int).tolist():
+            hist[k] = hist.get(k, 0) + 1
+        classes.append({"level": lvl, "classes": int(len(cnt)), "pairs": int(cnt.sum()),
+                        "largest": int(cnt.max()), "mean": float(cnt.mean()),
+                        "largest_over_mean": float(cnt.max() / cnt.mean()),
+                        "median": float(np.median(cnt)),
+                        "share_of_largest_1pct": float(np.sort(cnt)[::-1][:max(1, len(cnt) // 100)]
+                                                       .sum() / cnt.sum()),
+                        "log2_histogram": {f"2^{k}": v for k, v in sorted(hist.items())}})
     print(json.dumps({"metric": "constraint-level study, (24e,30o)", "unit": "ms",
-                      "data": "synthetic", "rows": rows}), flush=True)
+                      "data": "synthetic", "rows": rows, "classes": classes}), flush=True)
     return 0
 
 

@@ -93,6 +93,12 @@ typedef struct {
    * alpha string.  0 or 1: no sharding. */
   int32_t shard_index;
   int32_t shard_count;
+  /* CTAs per SM of the persistent generation and on-chip accumulation
+   * kernels (a launch shape, not in the paper): 0 = as many as fit.  Fewer
+   * leave room on the GPU for other searches running at the same time (many
+   * small independent searches, asci_search_many); results do not depend on
+   * it. */
+  int32_t ctas_per_sm;
 } asci_opts;
 
 /* Counters and per-stage device times (milliseconds) of one search. */
@@ -140,6 +146,15 @@ unsigned long long asci_launch_count(void);
 /* Scratch memory is cached per device between calls (a stream-ordered pool);
  * this returns the cached memory of the current device to the system. */
 void asci_trim_cache(void);
+
+/* Fault injection for tests of the error path (no counterpart in the paper):
+ * after `after` more successful scratch allocations (in any thread), the next
+ * one fails as if the device had no memory left, once; the call that makes it
+ * returns ASCI_ENOMEM ("injected allocation failure" in asci_last_error())
+ * after releasing its scratch, and later calls run normally.  A negative
+ * value cancels a pending injection.  The allocation-free entry point
+ * allocates nothing and is unaffected. */
+void asci_debug_fail_allocation(int64_t after);
 
 /*
  * The ASCI search (Algorithm 2 with Eq. 1; constraint batching of Sec. 2.2).
@@ -277,6 +292,36 @@ int asci_sort_accumulate_noalloc(const asci_det *keys, const double *values, siz
 int asci_select_histogram(const asci_det *keys, const double *scores, size_t n, int32_t digit,
                           const uint64_t prefix[2], const uint64_t mask[2], uint64_t hist[256],
                           void *cuda_stream);
+
+/* The digit choice of that selection (host only; no GPU).  The state holds
+ * the fixed bits of R_N (prefix, with mask marking them), the rank of R_N
+ * among the entries that match them (remaining) and the next byte to fix
+ * (digit, 15 down to 0).
+ *
+ * asci_select_begin: total = the number of entries over all ranks, N the
+ * number to select.  With total <= N every entry is selected: done = 1 and
+ * threshold = all ones.  Otherwise prefix = mask = 0, remaining = N, digit =
+ * 15, done = 0.
+ * asci_select_step: hist[256] = the sum over the ranks of
+ * asci_select_histogram(.., digit, prefix, mask, ..).  Fixes byte `digit` of
+ * R_N to the value whose bucket holds the remaining-th matching entry
+ * (counting from the smallest byte value), lowers remaining by the entries of
+ * the smaller values and sets threshold = prefix; when that bucket is taken
+ * whole, threshold = prefix with every unfixed bit set and done = 1; after
+ * byte 0, done = 1.  Callers keep, on every rank, the entries with
+ * R <= threshold (asci_select_below): N in all.
+ * Errors: ASCI_EINVAL for NULL arguments, a finished state, or a histogram
+ * holding fewer than `remaining` entries (the message names it). */
+typedef struct {
+  uint64_t prefix[2];     /* fixed bits of R_N: {hi, lo} */
+  uint64_t mask[2];       /* which bits of prefix are fixed */
+  uint64_t threshold[2];  /* the bound to keep entries at or below, once done */
+  uint64_t remaining;     /* rank of R_N among the entries matching prefix on mask */
+  int32_t digit;          /* next byte to fix; -1 when done */
+  int32_t done;
+} asci_select_state;
+int asci_select_begin(uint64_t total, uint64_t N, asci_select_state *st);
+int asci_select_step(asci_select_state *st, const uint64_t hist[256]);
 int asci_select_below(const asci_det *keys, const double *scores, size_t n,
                       const uint64_t threshold[2], asci_det *out_keys, double *out_scores,
                       size_t *out_n, void *cuda_stream);
@@ -307,6 +352,23 @@ typedef struct {
  * every problem's status is written.  streams < 1: ASCI_EINVAL. */
 int asci_search_many(asci_problem *problems, size_t count, const asci_opts *opts,
                      int32_t streams);
+
+/*
+ * The constraint classes of one level and their work (Sec. 2.2: a class is
+ * the set of targets whose alpha string has the same `level` highest occupied
+ * orbitals; its work is the number of (target, core) pairs it receives, the
+ * quantity Alg. 3 balances and Fig. 3 plots).  The core is the C
+ * determinants of largest |c| as in asci_search; level is clamped to n_alpha.
+ * out_pairs[i] (host or device, capacity entries) receives the pair count of
+ * the i-th non-empty class in ascending order of its target alpha strings;
+ * *out_n the number of non-empty classes (always written).  With capacity <
+ * *out_n nothing else is written and the call returns ASCI_OK (a size query).
+ * The counts add up to C n_exc.  Errors: those of asci_search's input checks,
+ * and ASCI_EINVAL for level < 1.
+ */
+int asci_constraint_classes(const asci_det *dets, const double *coeffs, size_t ndets,
+                            const asci_ints *ints, size_t C, int32_t level, uint64_t *out_pairs,
+                            size_t capacity, size_t *out_n, void *cuda_stream);
 
 /* Alg. 3's greedy placement (longest processing time first): the n classes
  * of weights[n] (pairs) are visited in descending weight (ties: lower index

@@ -25,7 +25,8 @@ __all__ = ["load", "lib_path", "launch_count", "search", "excitations", "diagona
            "select_topn", "SearchStats", "AsciError", "FP64", "FP32_INT_FP64_ACC",
            "FP32_INT_COMP_ACC", "shard_assign", "gather_candidates", "sharded_search",
            "search_many", "tune_streams", "tune_batched", "hamiltonian", "spmv", "davidson", "asci_loop",
-           "LoopStats", "pt2", "select_histogram", "select_below", "distributed_topn"]
+           "LoopStats", "pt2", "select_histogram", "select_below", "distributed_topn",
+           "constraint_classes"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "lib", "libasci.so")
@@ -53,7 +54,13 @@ class _Opts(ct.Structure):
     _fields_ = [("eps_search", ct.c_double), ("max_constraint_level", ct.c_int32),
                 ("precision", ct.c_int32), ("max_batch_pairs", ct.c_uint64),
                 ("sort_output", ct.c_int32), ("shard_index", ct.c_int32),
-                ("shard_count", ct.c_int32)]
+                ("shard_count", ct.c_int32), ("ctas_per_sm", ct.c_int32)]
+
+
+class _SelectState(ct.Structure):
+    _fields_ = [("prefix", ct.c_uint64 * 2), ("mask", ct.c_uint64 * 2),
+                ("threshold", ct.c_uint64 * 2), ("remaining", ct.c_uint64),
+                ("digit", ct.c_int32), ("done", ct.c_int32)]
 
 
 class _Problem(ct.Structure):
@@ -173,11 +180,18 @@ def load():
     lib.asci_sort_accumulate.argtypes = [vp, vp, sz, vp, vp, szp, vp]
     lib.asci_select_histogram.restype = ct.c_int
     lib.asci_select_histogram.argtypes = [vp, vp, sz, ct.c_int32, vp, vp, vp, vp]
+    lib.asci_select_begin.restype = ct.c_int
+    lib.asci_select_begin.argtypes = [ct.c_uint64, ct.c_uint64, ct.POINTER(_SelectState)]
+    lib.asci_select_step.restype = ct.c_int
+    lib.asci_select_step.argtypes = [ct.POINTER(_SelectState), vp]
     lib.asci_select_below.restype = ct.c_int
     lib.asci_select_below.argtypes = [vp, vp, sz, vp, vp, vp, szp, vp]
     lib.asci_select_topn.restype = ct.c_int
     lib.asci_select_topn.argtypes = [vp, vp, sz, sz, vp, vp, szp, vp]
     lib.asci_shard_assign.argtypes = [vp, sz, ct.c_int32, vp, vp]
+    lib.asci_constraint_classes.restype = ct.c_int
+    lib.asci_constraint_classes.argtypes = [vp, vp, sz, ct.POINTER(_Ints), sz, ct.c_int32, vp, sz,
+                                            szp, vp]
     lib.asci_search_many.argtypes = [vp, sz, ct.POINTER(_Opts), ct.c_int32]
     lib.asci_default_opts.argtypes = [ct.POINTER(_Opts)]
     lib.asci_hamiltonian.restype = ct.c_int
@@ -197,6 +211,8 @@ def load():
     lib.asci_last_error.restype = ct.c_char_p
     lib.asci_launch_count.restype = ct.c_ulonglong
     lib.asci_trim_cache.restype = None
+    lib.asci_debug_fail_allocation.restype = None
+    lib.asci_debug_fail_allocation.argtypes = [ct.c_int64]
     _lib = lib
     return lib
 
@@ -294,12 +310,13 @@ def _out(n, dtype_np, device, cols=None):
 def search(dets, coeffs, E0: float, h1, eri, ecore: float, C: int, N: int, *,
            eps: float = 0.0, precision: int = FP64, max_batch_pairs: int = 0,
            max_constraint_level: int = 0, sort_output: bool = False, stream=None,
-           return_stats: bool = True, shard=None):
+           return_stats: bool = True, shard=None, ctas_per_sm: int = 0):
     """The ASCI search (Alg. 2 with Eq. 1).  Returns (dets[(m, 2)], scores[m], stats).
 
     Outputs live where ``dets`` lives (device torch tensors in, device tensors out).
     ``shard=(index, count)`` restricts the search to one shard of the target
     alpha classes (Sec. 2.2, Alg. 3) and returns that shard's top N.
+    ``ctas_per_sm`` caps the persistent kernels' CTAs per SM (0: as many as fit).
     """
     lib = load()
     keep = []
@@ -318,6 +335,7 @@ def search(dets, coeffs, E0: float, h1, eri, ecore: float, C: int, N: int, *,
     opts.max_batch_pairs = int(max_batch_pairs)
     opts.max_constraint_level = int(max_constraint_level)
     opts.sort_output = 1 if sort_output else 0
+    opts.ctas_per_sm = int(ctas_per_sm)
     if shard is not None:
         opts.shard_index, opts.shard_count = int(shard[0]), int(shard[1])
     st = _Stats()
@@ -414,7 +432,8 @@ def sort_accumulate(keys, values, stream=None):
     return ok[:n_out.value], os_[:n_out.value]
 
 
-def _opts(lib, eps, precision, max_batch_pairs, max_constraint_level, sort_output):
+def _opts(lib, eps, precision, max_batch_pairs, max_constraint_level, sort_output,
+          ctas_per_sm=0):
     o = _Opts()
     lib.asci_default_opts(ct.byref(o))
     o.eps_search = float(eps)
@@ -422,21 +441,24 @@ def _opts(lib, eps, precision, max_batch_pairs, max_constraint_level, sort_outpu
     o.max_batch_pairs = int(max_batch_pairs)
     o.max_constraint_level = int(max_constraint_level)
     o.sort_output = 1 if sort_output else 0
+    o.ctas_per_sm = int(ctas_per_sm)
     return o
 
 
 def search_many(systems, *, streams=None, eps: float = 0.0, precision: int = FP64,
                 max_batch_pairs: int = 0, max_constraint_level: int = 0,
-                sort_output: bool = False):
+                sort_output: bool = False, ctas_per_sm: int = 0):
     """Many independent searches (asci_search_many): ``systems`` is a list of
     dicts with keys dets, coeffs, E0, h1, eri, ecore, C, N (arrays as for
     search()).  ``streams`` searches run at a time on their own CUDA streams;
-    None picks the count and the batch cap with tune_batched().  Returns a list of
-    (dets, scores, stats), each exactly what search() returns."""
+    None picks the count, the batch cap and the CTAs per SM with
+    tune_batched().  Returns a list of (dets, scores, stats), each exactly what
+    search() returns."""
     lib = load()
     if streams is None:
         t = tune_batched(systems, eps=eps, precision=precision, max_batch_pairs=max_batch_pairs)
         streams, max_batch_pairs = t["streams"], t["max_batch_pairs"]
+        ctas_per_sm = t.get("ctas_per_sm", ctas_per_sm)
     keep, probs, outs = [], (_Problem * max(len(systems), 1))(), []
     for i, sy in enumerate(systems):
         db = _dets_buf(sy["dets"])
@@ -454,7 +476,8 @@ def search_many(systems, *, streams=None, eps: float = 0.0, precision: int = FP6
         p.out_dets, p.out_scores = odp, osp
         p.out_n, p.stats = ct.addressof(n_out), ct.addressof(st)
         outs.append((od, os_, n_out, st))
-    o = _opts(lib, eps, precision, max_batch_pairs, max_constraint_level, sort_output)
+    o = _opts(lib, eps, precision, max_batch_pairs, max_constraint_level, sort_output,
+              ctas_per_sm)
     code = lib.asci_search_many(ct.addressof(probs), len(systems), ct.byref(o), int(streams))
     _check(code, "asci_search_many")
     if len(systems) and outs[0][0].__class__.__module__.startswith("torch"):
@@ -466,35 +489,41 @@ _TUNED = {}
 
 
 def tune_batched(systems, streams=(1, 2, 4, 8, 16, 32), batch_caps=(0, 1 << 22, 1 << 20),
-                 sample: int = 64, **kw):
+                 ctas=(0, 2, 1), sample: int = 64, **kw):
     """The project's autotuner for batched searches: a grid search over the
-    number of concurrent streams and the constraint-batch cap (pairs per batch;
-    0 = sized from free memory), keeping the pair that gives the most searches
-    per second on a sample of the batch.  Cached per batch signature (whether
-    the batch exceeds the sample, the largest orbital count, the precision).
-    Returns {"streams": k, "max_batch_pairs": b}.  A given max_batch_pairs in
-    kw fixes the cap."""
+    number of concurrent streams, the constraint-batch cap (pairs per batch;
+    0 = sized from free memory) and the launch shape of the persistent kernels
+    (CTAs per SM; 0 = as many as fit: fewer leave the GPU to the other
+    streams' searches), keeping the point that gives the most searches per
+    second on a sample of the batch.  Cached per batch signature (whether the
+    batch exceeds the sample, the largest orbital count, the precision).
+    Returns {"streams": k, "max_batch_pairs": b, "ctas_per_sm": c}.  A given
+    max_batch_pairs or ctas_per_sm in kw fixes that coordinate."""
     import time
-    if not systems:
-        return {"streams": 1, "max_batch_pairs": int(kw.get("max_batch_pairs", 0))}
-    norb = max(int(round(np.sqrt(np.prod(np.shape(sy["h1"]))))) for sy in systems)
     fixed = int(kw.pop("max_batch_pairs", 0) or 0)
+    fixed_ctas = kw.pop("ctas_per_sm", None)
+    if not systems:
+        return {"streams": 1, "max_batch_pairs": fixed, "ctas_per_sm": int(fixed_ctas or 0)}
+    norb = max(int(round(np.sqrt(np.prod(np.shape(sy["h1"]))))) for sy in systems)
     caps = (fixed,) if fixed else tuple(batch_caps)
-    sig = (len(systems) >= sample, norb, kw.get("precision", FP64), caps)
+    shapes = (int(fixed_ctas),) if fixed_ctas is not None else tuple(ctas)
+    sig = (len(systems) >= sample, norb, kw.get("precision", FP64), caps, shapes)
     if sig in _TUNED:
         return dict(_TUNED[sig])
     sub = systems[:sample]
-    best, best_rate = {"streams": 1, "max_batch_pairs": caps[0]}, -1.0
-    search_many(sub[:2], streams=1, max_batch_pairs=caps[0], **kw)  # warm caches and the pool
-    for b in caps:
-        for k in streams:
-            if k > len(sub):
-                break
-            t0 = time.perf_counter()
-            search_many(sub, streams=k, max_batch_pairs=b, **kw)
-            rate = len(sub) / (time.perf_counter() - t0)
-            if rate > best_rate:
-                best, best_rate = {"streams": k, "max_batch_pairs": b}, rate
+    best, best_rate = {"streams": 1, "max_batch_pairs": caps[0], "ctas_per_sm": shapes[0]}, -1.0
+    search_many(sub[:2], streams=1, max_batch_pairs=caps[0], ctas_per_sm=shapes[0],
+                **kw)  # warm caches and the pool
+    for c in shapes:
+        for b in caps:
+            for k in streams:
+                if k > len(sub):
+                    break
+                t0 = time.perf_counter()
+                search_many(sub, streams=k, max_batch_pairs=b, ctas_per_sm=c, **kw)
+                rate = len(sub) / (time.perf_counter() - t0)
+                if rate > best_rate:
+                    best, best_rate = {"streams": k, "max_batch_pairs": b, "ctas_per_sm": c}, rate
     _TUNED[sig] = dict(best)
     return best
 
@@ -552,6 +581,28 @@ def gather_candidates(keys, scores, group=None):
             torch.cat([v[:c] for v, c in zip(sl, counts)]))
 
 
+def constraint_classes(dets, coeffs, h1, eri, ecore: float, C: int, level: int, stream=None):
+    """Pair counts of the constraint classes of one level (Sec. 2.2: targets
+    sharing their `level` highest occupied alpha orbitals), in ascending
+    order of the classes' alpha strings: numpy uint64 array (a size query,
+    then the call)."""
+    lib = load()
+    keep = []
+    db = _dets_buf(dets)
+    cb = _as_buf(coeffs, np.float64, "float64")
+    keep += [db, cb]
+    ints, _ = _ints(h1, eri, ecore, keep)
+    n_out = ct.c_size_t(0)
+    sp = _stream_ptr(stream, db.device)
+    args = (db.ptr, cb.ptr, int(db.obj.shape[0]), ct.byref(ints), int(C), int(level))
+    _check(lib.asci_constraint_classes(*args, None, 0, ct.byref(n_out), sp),
+           "asci_constraint_classes")
+    out = np.zeros(max(n_out.value, 1), dtype=np.uint64)
+    _check(lib.asci_constraint_classes(*args, out.ctypes.data, out.size, ct.byref(n_out), sp),
+           "asci_constraint_classes")
+    return out[:n_out.value]
+
+
 def select_histogram(keys, scores, digit: int, prefix, mask, stream=None):
     """Histogram (numpy uint64[256]) of byte `digit` of the rank word
     (~bits(|score|), key) over the entries matching prefix on mask (device)."""
@@ -585,9 +636,6 @@ def select_below(keys, scores, threshold, stream=None):
     return ok[:n_out.value], os_[:n_out.value]
 
 
-_ALL = (1 << 64) - 1
-
-
 def distributed_topn(keys, scores, N: int, group=None, hist_fn=None, below_fn=None):
     """The global top N (|score| descending, key ascending) of candidates
     spread over the ranks of a torch.distributed group, the role of Alg. 4:
@@ -599,31 +647,21 @@ def distributed_topn(keys, scores, N: int, group=None, hist_fn=None, below_fn=No
     default).  Returns (keys, scores) of the global top N on every rank."""
     torch = _torch()
     import torch.distributed as dist
+    lib = load()
     hist_fn = hist_fn or (lambda d, p, m: select_histogram(keys, scores, d, p, m))
     below_fn = below_fn or (lambda t: select_below(keys, scores, t))
     dev = keys.device
     total = torch.tensor([keys.shape[0]], dtype=torch.int64, device=dev)
     dist.all_reduce(total, group=group)
-    thr = [_ALL, _ALL]
-    if int(total.item()) > N:
-        pre, msk, remaining = [0, 0], [0, 0], N
-        for digit in range(15, -1, -1):
-            h = torch.tensor(np.asarray(hist_fn(digit, [w & _ALL for w in pre],
-                                                [w & _ALL for w in msk])).astype(np.int64),
-                             device=dev)
-            dist.all_reduce(h, group=group)
-            h = h.cpu().numpy()
-            cum = np.cumsum(h)
-            d = int(np.searchsorted(cum, remaining))  # first byte value reaching `remaining`
-            remaining -= int(cum[d - 1]) if d else 0
-            word, shift = (0, 8 * (digit - 8)) if digit >= 8 else (1, 8 * digit)
-            pre[word] |= d << shift
-            msk[word] |= 0xff << shift
-            if int(h[d]) == remaining:  # the whole bucket is in: all lower bits free
-                thr = [pre[0] | (~msk[0] & _ALL), pre[1] | (~msk[1] & _ALL)]
-                break
-            thr = list(pre)
-    wk, ws = below_fn(thr)
+    st = _SelectState()
+    _check(lib.asci_select_begin(int(total.item()), int(N), ct.byref(st)), "asci_select_begin")
+    while not st.done:
+        h = torch.tensor(np.asarray(hist_fn(st.digit, list(st.prefix), list(st.mask)))
+                         .astype(np.int64), device=dev)
+        dist.all_reduce(h, group=group)
+        hh = np.ascontiguousarray(h.cpu().numpy().astype(np.uint64))
+        _check(lib.asci_select_step(ct.byref(st), hh.ctypes.data), "asci_select_step")
+    wk, ws = below_fn(list(st.threshold))
     return gather_candidates(wk, ws, group)
 
 

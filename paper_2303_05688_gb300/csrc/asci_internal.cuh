@@ -16,6 +16,9 @@ namespace asci {
 // ---------------------------------------------------------------------------
 
 void record_error(const char *what, const char *file, int line);
+// Allocation fault injection for tests of the error path (asci_debug_fail_allocation):
+// true when this allocation is to fail.
+bool injected_alloc_failure();
 void clear_last_error();
 
 // Stage tracing to stderr, enabled by the environment variable ASCI_TRACE=1.
@@ -86,6 +89,11 @@ class Arena {
       bump_off_ = off + bytes;
       *p = reinterpret_cast<T *>(bump_base_ + off);
       return ASCI_OK;
+    }
+    if (injected_alloc_failure()) {
+      record_error("injected allocation failure", __FILE__, __LINE__);
+      *p = nullptr;
+      return ASCI_ENOMEM;
     }
     cudaError_t e = pool_ ? cudaMallocFromPoolAsync(&q, bytes, pool_, stream_)
                           : cudaMallocAsync(&q, bytes, stream_);
@@ -265,6 +273,11 @@ struct DevInts {
   const double *jj;     // n*n, (pp|qq)
   const float *eri32;   // n^4 FP32 copy (precision variants)
   const float *asym32;  // n^4 FP32 copy
+  // the asym values again, laid out [((j*n+b)*n+i)*n+a] (equal bit for bit):
+  // the beta doubles of one warp's chunk vary a fastest, so this layout puts
+  // a chunk's gathers in a few contiguous rows
+  const double *asymT;
+  const float *asymT32;
 };
 
 // Slater-Condon pieces shared by the excitation generator and the

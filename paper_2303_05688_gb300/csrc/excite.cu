@@ -37,15 +37,21 @@ namespace {
 
 // ------------------------------ tables -------------------------------------
 
-__global__ void k_tables_n4(const double *eri, int n, double *asym, float *eri32, float *asym32) {
+__global__ void k_tables_n4(const double *eri, int n, double *asym, float *eri32, float *asym32,
+                            double *asymT, float *asymT32) {
   size_t n4 = (size_t)n * n * n * n;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4;
        t += (size_t)gridDim.x * blockDim.x) {
     int b = (int)(t % n), j = (int)((t / n) % n), a = (int)((t / n / n) % n), i = (int)(t / n / n / n);
     double v = eri[t] - eri[(((size_t)i * n + b) * n + j) * n + a];
+    const size_t tt = (((size_t)j * n + b) * n + i) * n + a;
     asym[t] = v;
+    asymT[tt] = v;
     if (eri32) eri32[t] = (float)eri[t];
-    if (asym32) asym32[t] = (float)v;
+    if (asym32) {
+      asym32[t] = (float)v;
+      asymT32[tt] = (float)v;
+    }
   }
 }
 
@@ -170,9 +176,10 @@ int build_tables(const double *h1_dev, const double *eri_dev, int n, int na, int
   I.h1 = h1_dev;
   I.eri = eri_dev;
   size_t n2 = (size_t)n * n, n3 = n2 * n, n4 = n3 * n;
-  double *asym, *s_same, *s_opp, *jk, *jj;
-  float *eri32 = nullptr, *asym32 = nullptr;
+  double *asym, *asymT, *s_same, *s_opp, *jk, *jj;
+  float *eri32 = nullptr, *asym32 = nullptr, *asymT32 = nullptr;
   ASCI_TRY(arena.alloc(&asym, n4));
+  ASCI_TRY(arena.alloc(&asymT, n4));
   ASCI_TRY(arena.alloc(&s_same, n3));
   ASCI_TRY(arena.alloc(&s_opp, n3));
   ASCI_TRY(arena.alloc(&jk, n2));
@@ -180,10 +187,11 @@ int build_tables(const double *h1_dev, const double *eri_dev, int n, int na, int
   if (want_fp32) {
     ASCI_TRY(arena.alloc(&eri32, n4));
     ASCI_TRY(arena.alloc(&asym32, n4));
+    ASCI_TRY(arena.alloc(&asymT32, n4));
   }
   cudaStream_t s = arena.stream();
   k_tables_n4<<<(unsigned)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096), 256, 0, s>>>(
-      eri_dev, n, asym, eri32, asym32);
+      eri_dev, n, asym, eri32, asym32, asymT, asymT32);
   ASCI_CHECK_LAUNCH();
   k_tables_n3<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(eri_dev, n, s_same, s_opp);
   ASCI_CHECK_LAUNCH();
@@ -196,6 +204,8 @@ int build_tables(const double *h1_dev, const double *eri_dev, int n, int na, int
   I.jj = jj;
   I.eri32 = eri32;
   I.asym32 = asym32;
+  I.asymT = asymT;
+  I.asymT32 = asymT32;
   *out = I;
   return ASCI_OK;
 }

@@ -168,7 +168,9 @@ __device__ __forceinline__ int64_t fx_diag(const FxInts &X, uint32_t A, uint32_t
 namespace {
 
 // Parent data of each core det (alpha-sorted order): H_jj and both Fock-like
-// diagonals.
+// diagonals.  Fb is determinant-major (Fb[j n + p]: a warp's lanes read one
+// determinant's row); Fa is orbital-major (Fa[p m + j]: the lanes of an
+// alpha-double step read one orbital of consecutive determinants).
 __global__ void k_core_fock(FxInts X, const uint32_t *core_alpha, const uint32_t *core_beta,
                             size_t m, int64_t *Dx, int64_t *Fa, int64_t *Fb) {
   const int n = X.n;
@@ -188,7 +190,7 @@ __global__ void k_core_fock(FxInts X, const uint32_t *core_alpha, const uint32_t
         fb += X.jk[p * n + q];
         fa += X.jj[p * n + q];
       }
-      Fa[j * n + p] = fa;
+      Fa[(size_t)p * m + j] = fa;
       Fb[j * n + p] = fb;
     }
   }
@@ -465,6 +467,7 @@ struct EmitArgs {
   uint32_t spill_cap;
   const uint64_t *runs;       // (item - t0) << 32 | determinant in the group
   uint64_t nruns;
+  unsigned long long *run_next;  // next unclaimed run (zeroed before each launch)
   const uint32_t *adl;        // alpha-double items (item - t0)
   const uint32_t *ad_off;     // first flat pair of each (exclusive prefix)
   uint32_t nad, ad_total;
@@ -521,35 +524,6 @@ __device__ __forceinline__ int64_t fx_single(const FxInts &X, uint32_t s, uint32
 
 __device__ __forceinline__ int64_t shfl64(int64_t x, int src) {
   return (int64_t)__shfl_sync(0xffffffffu, (long long)x, src);
-}
-
-// Staging position of one pair: in place for classes that fit a tile (slot
-// `inplace`), else the next free slot of its hash-bucket cell (warp-aggregated
-// counters; the cell's slots start at `cellpos`) or, once the cell holds kCap
-// records, the next entry of the spill list (*spill set, *pos the entry).
-// Returns false for an idle lane.
-__device__ __forceinline__ bool pair_position(const EmitArgs &A, bool big, bool valid,
-                                              uint32_t cell, uint32_t cellpos, uint32_t inplace,
-                                              uint32_t *pos, bool *spill) {
-  const int lane = threadIdx.x & 31;
-  *spill = false;
-  if (big) {  // warp-uniform
-    const uint32_t peers = __match_any_sync(0xffffffffu, valid ? cell : 0xffffffffu);
-    const int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (valid && lane == leader) base = atomicAdd(&A.fill[cell], (uint32_t)__popc(peers));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    const uint32_t slot = base + __popc(peers & ((1u << lane) - 1u));
-    if (slot < (uint32_t)kCap) {
-      *pos = cellpos + slot;
-    } else if (valid) {
-      *spill = true;
-      *pos = atomicAdd(A.n_spill, 1u);
-    }
-  } else {
-    *pos = inplace;
-  }
-  return valid;
 }
 
 // A float widened to a double exactly, by operations on the bits (a widening
@@ -641,10 +615,15 @@ __global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
   const uint32_t omask = (1u << A.opbits) - 1u;
   const int lane = threadIdx.x & 31;
   const uint32_t sb = A.E.sb, vb = A.E.vb;
-  const uint64_t nw = ((uint64_t)gridDim.x * kRunThreads) >> 5;
+  // runs are claimed one at a time from a shared counter (their lengths differ
+  // by a factor of about fifty); the next claim is issued before the current
+  // run is emitted
+  unsigned long long claim = 0;
+  if (lane == 0) claim = atomicAdd(A.run_next, 1ull);
+  uint64_t r = (uint64_t)__shfl_sync(0xffffffffu, claim, 0);
 #pragma unroll 1
-  for (uint64_t r = ((uint64_t)blockIdx.x * kRunThreads + threadIdx.x) >> 5; r < A.nruns;
-       r += nw) {
+  for (; r < A.nruns; r = (uint64_t)__shfl_sync(0xffffffffu, claim, 0)) {
+    if (lane == 0) claim = atomicAdd(A.run_next, 1ull);
     const uint64_t run = A.runs[r];
     const uint64_t t = A.t0 + (run >> 32);
     const uint32_t m = (uint32_t)run;
@@ -701,8 +680,8 @@ __global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
 #pragma unroll
         for (int d = 16; d; d >>= 1) part += (int64_t)__shfl_xor_sync(0xffffffffu, (long long)part, d);
         h0 = flip_sign(fx64_to_double(part + A.X.h1x[ia * n + aa], A.X.s1), pa);
-        const int64_t *Fa = A.Fa + (size_t)jdx * n;
-        base_x += Fa[aa] - Fa[ia] - s_jk[aa * n + ia];
+        base_x += A.Fa[(size_t)aa * A.ncore + jdx] - A.Fa[(size_t)ia * A.ncore + jdx] -
+                  s_jk[aa * n + ia];
         Vo += s_jj[aa * n + occL] - s_jj[ia * n + occL];
         Vv += s_jj[aa * n + virL] - s_jj[ia * n + virL];
         erow = A.I.eri + ((size_t)ia * n + aa) * n * n;
@@ -717,6 +696,7 @@ __global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
       int op, bi, bj, ba, bb;
       uint32_t tb, pos, cell;
       bool valid, wr, spill;
+      double g;  // the gathered integral (beta double; alpha x beta single), issued ahead
     };
     auto decode = [&](uint32_t e0, Chunk &q) {
       const uint32_t e = e0 + lane;
@@ -749,11 +729,36 @@ __global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
       const uint32_t bkt = big ? bucket_of(q.tb, nbk) : 0u;
       q.cell = cell0 + bkt;
       q.pos = 0;
-      q.wr = pair_position(A, big, q.valid, q.cell, cls0 + bkt * (uint32_t)kCap, off0 + e, &q.pos,
-                           &q.spill);
+      q.spill = false;
+      q.wr = q.valid;
+      if (big) {  // warp-uniform: the next free slot of the lane's bucket cell
+        const uint32_t peers = __match_any_sync(0xffffffffu, q.valid ? q.cell : 0xffffffffu);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (q.valid && lane == leader) base = atomicAdd(&A.fill[q.cell], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        const uint32_t slot = base + __popc(peers & ((1u << lane) - 1u));
+        if (slot < (uint32_t)kCap) {
+          q.pos = cls0 + bkt * (uint32_t)kCap + slot;
+        } else if (q.valid) {  // the cell is full: the spill list
+          q.spill = true;
+          q.pos = atomicAdd(A.n_spill, 1u);
+        }
+      } else {
+        q.pos = off0 + e;
+      }
+      // the chunk's integral gather, issued now and used one chunk later
+      q.g = 0.0;
+      if (q.op == 2) {
+        const size_t ix = (((size_t)q.bj * n + q.bb) * n + q.bi) * n + q.ba;
+        q.g = PREC != 0 ? widen(A.I.asymT32[ix]) : A.I.asymT[ix];
+      } else if (q.op == 1 && o != 0) {
+        q.g = PREC != 0 ? widen(erow32[q.bi * n + q.ba]) : erow[q.bi * n + q.ba];
+      }
     };
     // software-pipelined: the next chunk's staging slots (an atomic for big
-    // classes) are claimed before this chunk's matrix elements are formed
+    // classes) and integrals are requested before this chunk's matrix
+    // elements are formed
     Chunk cur, nxt;
     decode(0, cur);
 #pragma unroll 1
@@ -776,13 +781,10 @@ __global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
             h = flip_sign(fx64_to_double(fx_single(A.X, B, Ak, bi, ba), A.X.s1),
                           (uint32_t)single_parity(B, bi, ba));
           else
-            h = flip_sign(PREC != 0 ? widen(erow32[bi * n + ba]) : erow[bi * n + ba],
-                          pa ^ (uint32_t)single_parity(B, bi, ba));
+            h = flip_sign(cur.g, pa ^ (uint32_t)single_parity(B, bi, ba));
           dh = vv1 - vo1 - s_jk[ba * n + bi];
         } else {
-          const size_t ix = (((size_t)bi * n + ba) * n + bj) * n + bb;
-          h = flip_sign(PREC != 0 ? widen(A.I.asym32[ix]) : A.I.asym[ix],
-                        (uint32_t)par_double(B, bi, bj, ba, bb));
+          h = flip_sign(cur.g, (uint32_t)par_double(B, bi, bj, ba, bb));
           dh = vv1 + vv2 - vo1 - vo2 + s_jk[bi * n + bj] + s_jk[ba * n + bb] - s_jk[ba * n + bi] -
                s_jk[ba * n + bj] - s_jk[bb * n + bi] - s_jk[bb * n + bj];
         }
@@ -898,9 +900,10 @@ __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
       bool kept = false;
       if (valid) {
         const uint32_t ob = sOrb[lo];
-        const int64_t *Fa = A.Fa + (size_t)jdx * n;
-        const int64_t dh = sD[lo] + Fa[(ob >> 5) & 31u] + Fa[(ob >> 15) & 31u] - Fa[ob & 31u] -
-                           Fa[(ob >> 10) & 31u];
+        const int64_t *Fa = A.Fa + jdx;  // orbital p at Fa[p * ncore]
+        const size_t m = A.ncore;
+        const int64_t dh = sD[lo] + Fa[((ob >> 5) & 31u) * m] + Fa[((ob >> 15) & 31u) * m] -
+                           Fa[(ob & 31u) * m] - Fa[((ob >> 10) & 31u) * m];
         write_record<EPS>(A, pos, spill, cell, sTA[lo], B, A.kind[gi] == kTilePacked,
                           pair_value<PREC>(sH[lo], A.core_c[jdx], (float)A.core_c[jdx]),
                           A.Dx[jdx] + dh, &kept);
@@ -1820,20 +1823,29 @@ int psi_hash_build(const uint64_t *psi_keys, size_t nd, uint64_t **ht, uint64_t 
 // the staging buffer.  The tile table is left in *tiles_out (arena memory).
 // Launch of an emission kernel instantiated by (eps screen, precision).
 using EmitKernel = void (*)(EmitArgs);
+static unsigned emit_grid(EmitKernel k, int threads, size_t smem, size_t ntl, int cap);
 static void launch_emit(EmitKernel e0, EmitKernel n0, EmitKernel e1, EmitKernel n1,
-                        EmitKernel e2, EmitKernel n2, bool eps, int prec, unsigned grid,
-                        int threads, size_t smem, cudaStream_t s, const EmitArgs &A) {
+                        EmitKernel e2, EmitKernel n2, bool eps, int prec, size_t work,
+                        int threads, size_t smem, int cap, cudaStream_t s, const EmitArgs &A) {
   EmitKernel k = prec == 2 ? (eps ? e2 : n2) : prec == 1 ? (eps ? e1 : n1) : (eps ? e0 : n0);
-  k<<<grid, threads, smem, s>>>(A);
+  k<<<emit_grid(k, threads, smem, work, cap), threads, smem, s>>>(A);
 }
 
-// Persistent emission grid: a few CTAs per SM, at most one per tile.
-static unsigned emit_grid(size_t ntl) {
-  int dev = 0, sms = 152;
+// Persistent emission grid: as many CTAs as the GPU holds at once (the
+// kernel's occupancy at this block size and shared memory, at most `cap` per
+// SM when cap > 0), at most `ntl`.
+static unsigned emit_grid(EmitKernel k, int threads, size_t smem, size_t ntl, int cap) {
+  int dev = 0, sms = 152, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     sms = 152;
-  return (unsigned)std::max<size_t>(1, std::min<size_t>(ntl, (size_t)sms * 8));
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem) != cudaSuccess ||
+      per < 1) {
+    cudaGetLastError();
+    per = 1;
+  }
+  if (cap > 0 && cap < per) per = cap;
+  return (unsigned)std::max<size_t>(1, std::min<size_t>(ntl, (size_t)sms * per));
 }
 
 int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint64_t P1,
@@ -2037,8 +2049,9 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   A.ncore = F.ncore;
   A.err = err;
   const size_t emit_smem = 2 * (size_t)F.X.n * F.X.n * sizeof(int64_t);
-  const unsigned run_grid = emit_grid((nruns + 7) / 8);
-  const unsigned ad_grid = emit_grid(ad_tiles);
+  unsigned long long *run_next;
+  ASCI_TRY(arena.alloc(&run_next, 1));
+  A.run_next = run_next;
   unsigned long long surv0 = 0;
   if (eps > 0.0) {
     ASCI_TRY_CUDA(cudaMemcpyAsync(&surv0, survivors, sizeof(surv0), cudaMemcpyDefault, s));
@@ -2047,15 +2060,16 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   unsigned hov = 0, hsp = 0;
   for (int attempt = 0;; ++attempt) {
     if (nruns) {
+      ASCI_TRY_CUDA(cudaMemsetAsync(run_next, 0, sizeof(unsigned long long), s));
       launch_emit(k_emit_runs<true, 0>, k_emit_runs<false, 0>, k_emit_runs<true, 1>,
                   k_emit_runs<false, 1>, k_emit_runs<true, 2>, k_emit_runs<false, 2>, eps > 0.0,
-                  F.prec, run_grid, kRunThreads, emit_smem, s, A);
+                  F.prec, (nruns + 7) / 8, kRunThreads, emit_smem, F.ctas_per_sm, s, A);
       ASCI_CHECK_LAUNCH();
     }
     if (ad_tiles) {
       launch_emit(k_emit_ad<true, 0>, k_emit_ad<false, 0>, k_emit_ad<true, 1>,
                   k_emit_ad<false, 1>, k_emit_ad<true, 2>, k_emit_ad<false, 2>, eps > 0.0,
-                  F.prec, ad_grid, kAdThreads, 0, s, A);
+                  F.prec, ad_tiles, kAdThreads, 0, F.ctas_per_sm, s, A);
       ASCI_CHECK_LAUNCH();
     }
     ASCI_TRACE("stage: emission launched");
@@ -2180,8 +2194,8 @@ int fused_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
   int dev = 0, sms = 152;
   ASCI_TRY_CUDA(cudaGetDevice(&dev));
   ASCI_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned grid =
-      (unsigned)std::min<size_t>((size_t)sms * per_sm, tile_end - tile_begin);
+  const int per = (F.ctas_per_sm > 0 && F.ctas_per_sm < per_sm) ? F.ctas_per_sm : per_sm;
+  const unsigned grid = (unsigned)std::min<size_t>((size_t)sms * per, tile_end - tile_begin);
   ASCI_TRACE("cells: launch grid=%u smem=%zu per_sm=%d", grid, cell_smem, per_sm);
   k_cells<<<grid, kCellThreads, cell_smem, s>>>(CA);
   ASCI_CHECK_LAUNCH();

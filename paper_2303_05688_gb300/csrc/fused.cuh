@@ -68,6 +68,7 @@ struct FusedCore {
   uint32_t ncore;
   int prec;  // pair-value precision: 0 FP64, 1 FP32 integrals, 2 FP32 integrals and product
   int screened;  // Alg. 2's eps screen is on: staged records may be marked dropped
+  int ctas_per_sm;  // cap on the persistent kernels' CTAs per SM (0: as many as fit)
 };
 
 }  // namespace asci

@@ -83,6 +83,14 @@ static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// Pool allocations left before an injected failure; negative: none pending.
+static std::atomic<long long> g_alloc_fault{-1};
+
+bool injected_alloc_failure() {
+  if (g_alloc_fault.load(std::memory_order_relaxed) < 0) return false;
+  return g_alloc_fault.fetch_sub(1, std::memory_order_relaxed) == 0;
+}
+
 bool trace_on() {
   static const bool on = [] {
     const char *v = getenv("ASCI_TRACE");
@@ -413,6 +421,11 @@ class Planner {
       : items_(items), W_(Wexcl), bmax_(bmax), first_cap_(first_cap), lmax_(lmax),
         arena_(arena) {}
 
+  // Classes of level L over items [0, T): first items and first pairs.
+  int classes(uint64_t T, int L, std::vector<uint64_t> *starts, std::vector<uint64_t> *wst) {
+    return query(0, T, L, starts, wst);
+  }
+
   int run(uint64_t T, uint64_t P, int L0, std::vector<Batch> *out, int *max_level) {
     batches_.clear();
     cur_open_ = false;
@@ -521,6 +534,15 @@ int device_pool(int dev, cudaMemPool_t *pool) {
   return ASCI_OK;
 }
 
+// A request for the pair counts of the constraint classes of one level
+// (asci_constraint_classes): the search stops once its items are weighed.
+struct ClassQuery {
+  int level;
+  uint64_t *out;     // host or device, capacity entries
+  size_t capacity;
+  size_t n;          // classes found
+};
+
 // The search proper.  All pointers resolved; `arena` owns the scratch.
 // With pt2_out set, the same pipeline runs without a threshold and, instead
 // of keeping candidates, folds every unique target outside psi into the
@@ -528,7 +550,8 @@ int device_pool(int dev, cudaMemPool_t *pool) {
 static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t nd, double E0,
                        const asci_ints *ints, size_t C, size_t N, const asci_opts &o,
                        asci_det *out_dets, double *out_scores, size_t *out_n, asci_stats *st,
-                       cudaStream_t stream, double *pt2_out = nullptr) {
+                       cudaStream_t stream, double *pt2_out = nullptr,
+                       ClassQuery *cq = nullptr) {
   Arena arena(stream);
   double tl[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per-stage device milliseconds
   uint64_t tile_launches = 0, staged_records = 0, oversized_records = 0;
@@ -701,6 +724,23 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
       }
     }
   }
+  if (cq) {  // the classes of one level, in constraint order, and their pairs
+    cq->n = 0;
+    if (T > 0 && P > 0) {
+      Planner pl(items, Wexcl, P, P, na, arena);
+      std::vector<uint64_t> starts, wst;
+      ASCI_TRY(pl.classes(T, std::min(cq->level, na), &starts, &wst));
+      cq->n = starts.size();
+      if (cq->capacity >= cq->n && cq->n) {
+        std::vector<uint64_t> w(cq->n);
+        for (size_t i = 0; i < cq->n; ++i) w[i] = (i + 1 < cq->n ? wst[i + 1] : P) - wst[i];
+        ASCI_TRY_CUDA(cudaMemcpyAsync(cq->out, w.data(), cq->n * 8, cudaMemcpyDefault, stream));
+        ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+      }
+    }
+    if (st) st->generated = P;
+    return ASCI_OK;
+  }
   if (T > 0 && P > 0) {
     uint64_t bmax = o.max_batch_pairs;
     if (bmax == 0) {
@@ -758,6 +798,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   F.ncore = (uint32_t)m;
   F.prec = o.precision == ASCI_FP32_INT_COMP_ACC ? 2 : (o.precision == ASCI_FP32_INT_FP64_ACC ? 1 : 0);
   F.screened = o.eps_search > 0.0 ? 1 : 0;
+  F.ctas_per_sm = o.ctas_per_sm;
   ASCI_TRY(build_fx(h1, eri, n, na, nb, ints->ecore, E0, arena, &F.X, &F.E0_x));
   if (st) st->diag_grid_bits = (uint64_t)F.X.s;
   {
@@ -1112,6 +1153,8 @@ const char *asci_last_error(void) { return g_last_error; }
 
 unsigned long long asci_launch_count(void) { return g_launches.load(); }
 
+void asci_debug_fail_allocation(int64_t after) { g_alloc_fault.store(after < 0 ? -1 : after); }
+
 void asci_trim_cache(void) {
   int dev = 0;
   cudaMemPool_t pool;
@@ -1144,6 +1187,7 @@ int asci_search(const asci_det *dets, const double *coeffs, size_t ndets, double
   if (opts) o = *opts;
   if (!(o.eps_search >= 0.0) || !std::isfinite(o.eps_search)) return ASCI_EINVAL;
   if (o.precision < ASCI_FP64 || o.precision > ASCI_FP32_INT_COMP_ACC) return ASCI_EINVAL;
+  if (o.ctas_per_sm < 0 || o.ctas_per_sm > 64) return ASCI_EINVAL;
   if (o.shard_count < 0 || o.shard_count > 1024 ||
       (o.shard_count > 1 && (o.shard_index < 0 || o.shard_index >= o.shard_count)))
     return ASCI_EINVAL;
@@ -1169,6 +1213,7 @@ int asci_pt2(const asci_det *dets, const double *coeffs, size_t ndets, double E0
   if (opts) o = *opts;
   if (!(o.eps_search >= 0.0) || !std::isfinite(o.eps_search)) return ASCI_EINVAL;
   if (o.precision < ASCI_FP64 || o.precision > ASCI_FP32_INT_COMP_ACC) return ASCI_EINVAL;
+  if (o.ctas_per_sm < 0 || o.ctas_per_sm > 64) return ASCI_EINVAL;
   if (o.shard_count < 0 || o.shard_count > 1024 ||
       (o.shard_count > 1 && (o.shard_index < 0 || o.shard_index >= o.shard_count)))
     return ASCI_EINVAL;
@@ -1382,6 +1427,27 @@ int asci_search_many(asci_problem *problems, size_t count, const asci_opts *opts
   return ASCI_OK;
 }
 
+int asci_constraint_classes(const asci_det *dets, const double *coeffs, size_t ndets,
+                            const asci_ints *ints, size_t C, int32_t level, uint64_t *out_pairs,
+                            size_t capacity, size_t *out_n, void *cuda_stream) {
+  if (out_n) *out_n = 0;
+  if (!dets || !coeffs || !ints || !ints->h1 || !ints->eri || !out_n) return ASCI_EINVAL;
+  if (capacity > 0 && !out_pairs) return ASCI_EINVAL;
+  if (ints->norb < 1 || ints->norb > 32 || ndets == 0 || C == 0 || level < 1) return ASCI_EINVAL;
+  if (!std::isfinite(ints->ecore) || ndets >= (1ull << 32)) return ASCI_EINVAL;
+  asci_opts o;
+  asci_default_opts(&o);
+  cudaStream_t s;
+  ASCI_TRY(begin_call(cuda_stream, &s));
+  ClassQuery q{level, out_pairs, capacity, 0};
+  size_t dummy = 0;
+  const int r = search_impl(dets, coeffs, ndets, 0.0, ints, C, 0, o, nullptr, nullptr, &dummy,
+                            nullptr, s, nullptr, &q);
+  if (r != ASCI_OK) return r;
+  *out_n = q.n;
+  return ASCI_OK;
+}
+
 int asci_shard_assign(const uint64_t *weights, size_t n, int32_t shards,
                       const uint64_t *initial_loads, int32_t *shard_out) {
   if (shards < 1 || (n > 0 && (!weights || !shard_out))) return ASCI_EINVAL;
@@ -1399,6 +1465,53 @@ int asci_shard_assign(const uint64_t *weights, size_t n, int32_t shards,
     l.first += weights[c];
     q.push(l);
   }
+  return ASCI_OK;
+}
+
+int asci_select_begin(uint64_t total, uint64_t N, asci_select_state *st) {
+  if (!st) return ASCI_EINVAL;
+  memset(st, 0, sizeof(*st));
+  st->remaining = N;
+  if (total <= N) {  // every entry is selected
+    st->threshold[0] = st->threshold[1] = ~0ull;
+    st->digit = -1;
+    st->done = 1;
+    return ASCI_OK;
+  }
+  st->digit = 15;
+  return ASCI_OK;
+}
+
+int asci_select_step(asci_select_state *st, const uint64_t hist[256]) {
+  if (!st || !hist || st->done || st->digit < 0 || st->digit > 15 || st->remaining == 0)
+    return ASCI_EINVAL;
+  // the byte value d whose bucket holds the remaining-th entry of the class
+  uint64_t below = 0;
+  int d = 0;
+  for (; d < 256; ++d) {
+    if (below + hist[d] >= st->remaining) break;
+    below += hist[d];
+  }
+  if (d == 256) {
+    record_error("asci_select_step: the histogram holds fewer entries than remain", __FILE__,
+                 __LINE__);
+    return ASCI_EINVAL;
+  }
+  st->remaining -= below;
+  const int word = st->digit >= 8 ? 0 : 1;
+  const int shift = 8 * (st->digit >= 8 ? st->digit - 8 : st->digit);
+  st->prefix[word] |= (uint64_t)d << shift;
+  st->mask[word] |= 0xffull << shift;
+  if (hist[d] == st->remaining) {  // the whole bucket is selected: lower bits are free
+    st->threshold[0] = st->prefix[0] | ~st->mask[0];
+    st->threshold[1] = st->prefix[1] | ~st->mask[1];
+    st->digit = -1;
+    st->done = 1;
+    return ASCI_OK;
+  }
+  st->threshold[0] = st->prefix[0];
+  st->threshold[1] = st->prefix[1];
+  if (--st->digit < 0) st->done = 1;  // every byte fixed: threshold is the N-th word
   return ASCI_OK;
 }
 

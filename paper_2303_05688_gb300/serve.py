@@ -62,6 +62,7 @@ class Server:
         self._closed = False
         self.peak_bytes = 0
         self.peak_running = 0
+        self.cancelled = 0  # requests withdrawn before admission
         self._workers = [threading.Thread(target=self._work, daemon=True) for _ in range(slots)]
         for t in self._workers:
             t.start()
@@ -84,18 +85,27 @@ class Server:
     # ------------------------------------------------------------- requests ---
     def submit(self, name, C: int, N: int, precision: int = FP64, batch_pairs: int = 1 << 26):
         """Queue a search of system ``name``; returns a Future of
-        (dets, scores, stats, latency_s) with latency from submission."""
+        (dets, scores, stats, latency_s) with latency from submission.  A
+        request still in the queue is withdrawn by the future's cancel()
+        (which then returns True); one already admitted runs to its end."""
         sy = self._systems[name]
         fp = footprint(sy["norb"], sy["ndets"], C, N, batch_pairs)
         if fp > self.budget:
             raise ValueError(f"request needs {fp} bytes, more than the budget {self.budget}")
         fut = Future()
+        fut.add_done_callback(self._on_done)
         with self._cv:
             if self._closed:
                 raise RuntimeError("server closed")
             self._pending.append((name, C, N, precision, batch_pairs, fp, fut, time.perf_counter()))
             self._cv.notify_all()
         return fut
+
+    def _on_done(self, fut):
+        # a withdrawn request may have been the one holding up the queue
+        if fut.cancelled():
+            with self._cv:
+                self._cv.notify_all()
 
     def close(self):
         with self._cv:
@@ -116,10 +126,17 @@ class Server:
         a large request is not overtaken indefinitely)."""
         with self._cv:
             while True:
+                # withdrawn requests leave the queue without taking a slot
+                while self._pending and self._pending[0][6].cancelled():
+                    self._pending.popleft()
+                    self.cancelled += 1
                 if self._pending:
                     fp = self._pending[0][5]
                     if self._in_use + fp <= self.budget:
                         req = self._pending.popleft()
+                        if not req[6].set_running_or_notify_cancel():  # withdrawn just now
+                            self.cancelled += 1
+                            continue
                         self._in_use += fp
                         self._running += 1
                         self.peak_bytes = max(self.peak_bytes, self._in_use)

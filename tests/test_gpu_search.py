@@ -503,7 +503,8 @@ def test_sharded_search_merges_to_the_unsharded_result(torch_cuda, asci, W):
 
 def test_search_many_equals_one_at_a_time(torch_cuda, asci, oracle_mod):
     """Batched independent searches on concurrent streams (asci_search_many)
-    return exactly what separate calls return, system by system."""
+    return exactly what separate calls return, system by system; members of
+    the mix (Hubbard rings and random integrals) match the oracle."""
     torch = torch_cuda
     systems = []
     for sy in W.batched_systems(12, seed=77, scale=0.05):
@@ -516,6 +517,29 @@ def test_search_many_equals_one_at_a_time(torch_cuda, asci, oracle_mod):
                             C=sy["C"], N=sy["N"]))
     many = asci.search_many(systems, streams=4)
     assert len(many) == len(systems)
+    # members of the mix against the oracle: the selected set under the tie band
+    kinds = set()
+    for sy, raw, (k, s_, st) in list(zip(systems, W.batched_systems(12, seed=77, scale=0.05),
+                                         many))[:4]:
+        ints = oracle_mod.Ints(raw["h1"], raw["eri"], raw["ecore"])
+        ref = oracle_mod.search(ints, raw["alpha"], raw["beta"], raw["c"], sy["E0"], sy["C"])
+        sel = ref.topn(sy["N"])
+        a, b = to_u64_pairs(k)
+        compare_selection(a, b, ref, sel, sy["E0"], st.diag_grid_bits)
+        assert (st.generated, st.unique, st.excluded) == (ref.generated, ref.unique, ref.excluded)
+        kinds.add(raw["name"].split("_")[0])
+    assert kinds == {"hubbard", "random"}
+    # the launch shape of the persistent kernels changes no result bit
+    sy = systems[0]
+    k1, s1, _ = asci.search(sy["dets"], sy["coeffs"], sy["E0"], sy["h1"], sy["eri"], sy["ecore"],
+                            sy["C"], sy["N"])
+    k2, s2, _ = asci.search(sy["dets"], sy["coeffs"], sy["E0"], sy["h1"], sy["eri"], sy["ecore"],
+                            sy["C"], sy["N"], ctas_per_sm=1)
+    a1, b1 = to_u64_pairs(k1)
+    a2, b2 = to_u64_pairs(k2)
+    o1, o2 = key_order(a1, b1), key_order(a2, b2)
+    assert np.array_equal(a1[o1], a2[o2]) and np.array_equal(s1.cpu().numpy()[o1],
+                                                             s2.cpu().numpy()[o2])
     for sy, (k, s_, st) in zip(systems, many):
         k1, s1, st1 = asci.search(sy["dets"], sy["coeffs"], sy["E0"], sy["h1"], sy["eri"],
                                   sy["ecore"], sy["C"], sy["N"])
@@ -565,3 +589,29 @@ def test_search_boundary_cases(torch_cuda, asci, oracle_mod):
     ga, gb, gs, st = _run(asci, torch, A, B, c, E0 + 2.5, h1, eri, 2.5, 60, 10**6)
     assert st.ncore == 60
     compare_candidates(ga, gb, gs, ref, E0 + 2.5, st.diag_grid_bits, label="tied |c|")
+
+
+def test_constraint_class_counts_match_oracle_pairs(torch_cuda, asci, oracle_mod):
+    """Pair counts per constraint class (Sec. 2.2; the work Alg. 3 balances)
+    at every level against the oracle's pair list: each pair's class is the
+    set of its target alpha string's `level` highest occupied orbitals;
+    classes in ascending order of that set's bit pattern."""
+    torch = torch_cuda
+    _, h1, eri, ec, A, B, c, E0 = _random("random_10e14o")
+    C = 150
+    core = oracle_mod.core_select(A, B, c, C)
+    ta, tb, _ = oracle_mod.pairs(oracle_mod.Ints(h1, eri, ec), A[core], B[core], c[core])
+    n_alpha = bin(int(A[0])).count("1")
+    for level in range(1, n_alpha + 2):
+        L = min(level, n_alpha)
+        counts = {}
+        for a in ta.tolist():
+            bits = [p for p in range(14) if a >> p & 1]
+            k = sum(1 << p for p in bits[-L:])
+            counts[k] = counts.get(k, 0) + 1
+        want = [counts[k] for k in sorted(counts)]
+        got = asci.constraint_classes(_dev(torch, A, B), torch.tensor(c, device="cuda"),
+                                      torch.tensor(h1, device="cuda"),
+                                      torch.tensor(eri, device="cuda"), ec, C, level)
+        assert got.tolist() == want, level
+        assert int(got.sum()) == C * W.n_excitations(14, 5, 5)

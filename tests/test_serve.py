@@ -94,6 +94,69 @@ def test_failed_search_reaches_its_future_and_frees_its_slot():
     assert srv._in_use == 0 and srv._running == 0
 
 
+def test_queued_request_can_be_cancelled():
+    """A request still queued is withdrawn by its future's cancel(): it never
+    runs, takes no slot, and the requests behind it run; a running request
+    cannot be cancelled.  A withdrawn request at the head of the queue that
+    did not fit the budget no longer holds up the smaller one behind it."""
+    from paper_2303_05688_gb300.serve import footprint
+    gate = threading.Event()
+    calls = []
+
+    def gated(dets, coeffs, E0, h1, eri, ecore, C, N, **kw):
+        calls.append(C)
+        if C == 1:
+            gate.wait(30)
+        return dets[:1], coeffs[:1], {"C": C}
+
+    torch, srv = _server_cpu(slots=1, budget=1 << 40, search_fn=gated)
+    with srv:
+        srv.register("s", np.zeros((10, 2), np.int64), np.ones(10), -1.0, np.zeros((8, 8)),
+                     np.zeros(8 ** 4), 0.0)
+        futs = [srv.submit("s", c, 100) for c in (1, 2, 3)]
+        t0 = time.perf_counter()
+        while not futs[0].running() and time.perf_counter() - t0 < 10:
+            time.sleep(0.005)
+        assert futs[0].running() and not futs[0].cancel()
+        assert futs[1].cancel() and futs[1].cancelled()
+        gate.set()
+        assert futs[0].result(timeout=30)[2]["C"] == 1
+        assert futs[2].result(timeout=30)[2]["C"] == 3
+    assert calls == [1, 3] and srv.cancelled == 1
+    assert srv._in_use == 0 and srv._running == 0
+    # budget: a running request holds most of it, a big request waits at the
+    # head of the queue, a small one behind it; cancelling the big one lets
+    # the small one start while the first still runs
+    fp_small = footprint(8, 10, 1, 100, 1 << 20)
+    fp_big = footprint(8, 10, 1, 100, 1 << 26)
+    gate2, started = threading.Event(), []
+
+    def gated2(dets, coeffs, E0, h1, eri, ecore, C, N, **kw):
+        started.append(C)
+        if C == 1:
+            gate2.wait(30)
+        return dets[:1], coeffs[:1], {"C": C}
+
+    torch, srv = _server_cpu(slots=2, budget=fp_small + fp_big - 1, search_fn=gated2)
+    with srv:
+        srv.register("s", np.zeros((10, 2), np.int64), np.ones(10), -1.0, np.zeros((8, 8)),
+                     np.zeros(8 ** 4), 0.0)
+        f1 = srv.submit("s", 1, 100, batch_pairs=1 << 20)
+        t0 = time.perf_counter()
+        while not f1.running() and time.perf_counter() - t0 < 10:
+            time.sleep(0.005)
+        fbig = srv.submit("s", 2, 100, batch_pairs=1 << 26)
+        fsmall = srv.submit("s", 3, 100, batch_pairs=1 << 20)
+        time.sleep(0.05)
+        assert started == [1]  # the big one does not fit beside the first; the small one waits
+        assert fbig.cancel()
+        assert fsmall.result(timeout=10)[2]["C"] == 3  # while the first still runs
+        assert not f1.done()
+        gate2.set()
+        f1.result(timeout=30)
+    assert started == [1, 3] and srv.cancelled == 1
+
+
 def test_submit_after_close_is_refused():
     torch, srv = _server_cpu(slots=1, budget=1 << 40, search_fn=lambda *a, **k: None)
     srv.register("s", np.zeros((10, 2), np.int64), np.ones(10), -1.0, np.zeros((8, 8)),

@@ -235,3 +235,39 @@ def test_distributed_topn_gloo(world, N, empty):
         gk = np.array(res[r][0], dtype=np.int64).reshape(-1, 2)
         got = sorted(zip(((gk[:, 1] << 32) | gk[:, 0]).tolist(), res[r][1]))
         assert got == want
+
+
+def test_select_state_machine_on_the_host(asci):
+    """asci_select_begin / asci_select_step (host only): fed the exact
+    histograms of one list, the threshold keeps exactly the top N by rank word
+    (|S| descending, key ascending); total <= N selects everything; a
+    histogram short of the remaining count is rejected."""
+    import ctypes as ct
+    lib = asci.load()
+    rng = np.random.default_rng(9)
+    n = 300
+    keys = np.stack([rng.permutation(5000)[:n], rng.integers(0, 3, n)], 1).astype(np.int64)
+    s = rng.normal(size=n)
+    s[rng.random(n) < 0.4] = 0.5          # many ties in |S|
+    words = _rank_words(keys, s)
+    order = sorted(range(n), key=lambda i: words[i])
+    for N in (1, 2, 57, 119, 120, 299):
+        st = asci._SelectState()
+        assert lib.asci_select_begin(n, N, ct.byref(st)) == 0 and not st.done
+        steps = 0
+        while not st.done:
+            h = np.ascontiguousarray(_np_hist(keys, s, st.digit, list(st.prefix), list(st.mask)))
+            assert lib.asci_select_step(ct.byref(st), h.ctypes.data) == 0
+            steps += 1
+            assert steps <= 16
+        thr = (st.threshold[0], st.threshold[1])
+        kept = sorted(i for i in range(n) if words[i] <= thr)
+        assert kept == sorted(order[:N]), N
+    st = asci._SelectState()
+    assert lib.asci_select_begin(10, 10, ct.byref(st)) == 0 and st.done
+    assert st.threshold[0] == (1 << 64) - 1 and st.threshold[1] == (1 << 64) - 1
+    st = asci._SelectState()
+    lib.asci_select_begin(100, 50, ct.byref(st))
+    short = np.zeros(256, dtype=np.uint64)
+    short[3] = 10
+    assert lib.asci_select_step(ct.byref(st), short.ctypes.data) == -1
