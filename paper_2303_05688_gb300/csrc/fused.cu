@@ -1053,19 +1053,23 @@ __device__ __forceinline__ uint64_t mix_key(uint64_t z) {
   return z;
 }
 
-// Slot hash of the tile's table (2048 slots): the 32-bit finalizer of
-// MurmurHash3 (Appleby) over the alpha word times an odd constant xor the beta
-// word.  Bucket tiles hold one alpha string and the betas of one bucket, so
-// the finalizer's avalanche is what spreads them; cheaper than mix_key's two
-// 64-bit products.
-__device__ __forceinline__ uint32_t slot_hash(uint64_t key) {
+// Hash of a target key within a tile: the 32-bit finalizer of MurmurHash3
+// (Appleby) over the alpha word times an odd constant xor the beta word.
+// Bucket tiles hold one alpha string and the betas of one bucket, so the
+// finalizer's avalanche is what spreads them; cheaper than mix_key's two
+// 64-bit products.  Its low bits pick the slot of the tile's hash table
+// (2048 slots), its high 13 bits the bit of the tile's singleton filter.
+__device__ __forceinline__ uint32_t tile_mix(uint64_t key) {
   uint32_t h = (uint32_t)key * 0x9E3779B1u ^ (uint32_t)(key >> 32);
   h ^= h >> 16;
   h *= 0x85EBCA6Bu;
   h ^= h >> 13;
   h *= 0xC2B2AE35u;
   h ^= h >> 16;
-  return h & (uint32_t)(kSlots - 1);
+  return h;
+}
+__device__ __forceinline__ uint32_t slot_hash(uint64_t key) {
+  return tile_mix(key) & (uint32_t)(kSlots - 1);
 }
 
 // Open addressing with linear probing; the table is at most 1/4 full, and the
@@ -1083,7 +1087,14 @@ __device__ __forceinline__ bool psi_contains(const uint64_t *ht, uint64_t mask, 
   return false;
 }
 
-// A tile groups its records by target in a shared-memory hash table: a slot
+// A tile first sorts out its singletons: every key of the tile (records and
+// the psi determinants routed to it) sets its bit of a filter of kFilterBits
+// bits, and a key that finds its bit set marks it in a second filter.  A
+// record whose bit is not marked shares its hash with no other key of the
+// tile, so it is the only contribution to its target, which is not in psi:
+// it is scored and appended at once.  (About three records in four are the
+// only contribution to their target; most of those are recognised so.)
+// The other records are grouped by target in a shared-memory hash table: a slot
 // holds the newest record of its target and each record the index of the
 // previous one, so that every target ends up with the list of its records.
 // The psi determinants that fall in the tile are entered first as markers, so
@@ -1097,8 +1108,13 @@ constexpr uint32_t kPsiBit = 0x80000000u;  // slot holds psi marker (index in lo
 constexpr uint16_t kEndList = 0xffffu;
 constexpr int kPsiCap = 64;                // psi markers per tile; more: global lookups
 
+constexpr int kFilterBits = 8192;           // singleton filter bits per tile
+constexpr int kFilterWords = kFilterBits / 32;
+
 struct CellSmem {
   StageRec rec[2][kCap];     // records (double-buffered by tile)
+  uint32_t seen[kFilterWords];  // filter bits of the tile's keys (records and psi entries)
+  uint32_t dup[kFilterWords];   // filter bits met twice or more
   uint32_t alpha[2][kCap];   // record target alpha strings (packed tiles)
   uint64_t psik[2][kPsiCap]; // psi keys of the tile
   uint32_t slot[kSlots];     // newest record of the slot's target, a psi marker, or empty
@@ -1246,6 +1262,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
   unsigned long long my_unique = 0, my_excl = 0;
   for (int i = threadIdx.x; i < kSlots; i += kCellThreads) S.slot[i] = kEmptySlot;
   for (int i = threadIdx.x; i < kSlots / 32; i += kCellThreads) S.psibit[0][i] = S.psibit[1][i] = 0u;
+  for (int i = threadIdx.x; i < kFilterWords; i += kCellThreads) S.seen[i] = S.dup[i] = 0u;
   if (threadIdx.x == 0) S.ntargets[0] = S.ntargets[1] = 0;
   // tiles blockIdx.x + k * gridDim.x; descriptors are read one tile ahead of
   // the record copies, which run one tile ahead of the reduction
@@ -1276,11 +1293,32 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
     const uint32_t npsi = d.psi_hi - d.psi_lo;
     const bool psi_local = npsi <= (uint32_t)kPsiCap;
     const bool packed = d.kind == kTilePacked;
+    const int nrec = on ? (int)d.npairs : 0;
+    // singleton filter: every key sets its bit; a bit met twice is marked
+    for (int e = threadIdx.x; e < nrec; e += kCellThreads)
+      if (!(C.screened && is_dropped(S.rec[buf][e].v))) {
+        const uint32_t f = tile_mix(rec_key(S, buf, (uint32_t)e, packed, d.alpha)) >> 19;
+        const uint32_t bit = 1u << (f & 31u);
+        if (atomicOr(&S.seen[f >> 5], bit) & bit) atomicOr(&S.dup[f >> 5], bit);
+      }
+    if (on && psi_local)
+      for (uint32_t q = threadIdx.x; q < npsi; q += kCellThreads) {
+        const uint32_t f = tile_mix(S.psik[buf][q]) >> 19;
+        const uint32_t bit = 1u << (f & 31u);
+        if (atomicOr(&S.seen[f >> 5], bit) & bit) atomicOr(&S.dup[f >> 5], bit);
+      }
+    __syncthreads();  // filters complete
     if (on && psi_local) {
       // psi markers: claim a slot, or flag the slot a record already holds
+      // (a marker whose filter bit is unmarked meets no record: left out)
       for (uint32_t q = threadIdx.x; q < npsi; q += kCellThreads) {
         const uint64_t key = S.psik[buf][q];
-        uint32_t h = slot_hash(key);
+        const uint32_t mix = tile_mix(key), f = mix >> 19;
+        if (!((S.dup[f >> 5] >> (f & 31u)) & 1u)) {
+          S.psi_slot[q] = kEndList;
+          continue;
+        }
+        uint32_t h = mix & (uint32_t)(kSlots - 1);
         uint16_t claimed = kEndList;
         int probe = 0;
         for (; probe < kSlots; ++probe) {
@@ -1301,16 +1339,54 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
       }
     }
     if (on) {
-      // link each record into its target's list; warps append the slots they
-      // claim to the target list with one shared atomic per round
-      const int nrec = (int)d.npairs;
+      // singletons are scored and appended at once; every other record is
+      // linked into its target's list (warps append the slots they claim to
+      // the target list with one shared atomic per round)
 #pragma unroll 1
       for (int base = 0; base + warp_base < nrec; base += kCellThreads) {
         const int e = base + (int)threadIdx.x;
         int claimed = -1;
+        bool single = false, pass1 = false;
+        uint64_t key = 0;
+        double v1 = 0.0;
         if (e < nrec && !(C.screened && is_dropped(S.rec[buf][e].v))) {
-          const uint64_t key = rec_key(S, buf, (uint32_t)e, packed, d.alpha);
-          uint32_t h = slot_hash(key);
+          key = rec_key(S, buf, (uint32_t)e, packed, d.alpha);
+          const uint32_t mix = tile_mix(key), f = mix >> 19;
+          single = !((S.dup[f >> 5] >> (f & 31u)) & 1u);
+          if (single) {
+            ++my_unique;
+            if (!psi_local && psi_contains(C.psi_ht, C.psi_mask, key, C.err)) {
+              ++my_excl;
+            } else {
+              const StageRec r = S.rec[buf][e];
+              v1 = r.v;
+              pass1 = true;
+              if (C.tau > 0.0) {
+                bool okn;
+                const float nf = abs_as_float(r.v, &okn);
+                const float df = fabsf(r.den);
+                if (okn && df != 0.0f) pass1 = nf >= C.tau_f * df * 0.99999f;
+              }
+            }
+          }
+        }
+        {  // the singletons that pass the threshold
+          const unsigned bal = __ballot_sync(0xffffffffu, pass1);
+          if (bal) {
+            unsigned long long b0 = 0;
+            if (lane == 0) b0 = atomicAdd(C.cand_count, (unsigned long long)__popc(bal));
+            b0 = __shfl_sync(0xffffffffu, b0, 0);
+            if (pass1) {
+              const unsigned long long slotc = b0 + __popc(bal & ((1u << lane) - 1u));
+              if (slotc < C.cand_cap) {
+                C.cand_key[slotc] = key;
+                C.cand_score[slotc] = v1;  // the exact score is formed after the launch
+              }
+            }
+          }
+        }
+        if (e < nrec && !single && !(C.screened && is_dropped(S.rec[buf][e].v))) {
+          uint32_t h = tile_mix(key) & (uint32_t)(kSlots - 1);
           int probe = 0;
           for (; probe < kSlots; ++probe) {
             uint32_t cur = S.slot[h];
@@ -1347,6 +1423,8 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
     }
     __syncthreads();  // lists complete
     if (threadIdx.x == 0) S.ntargets[buf ^ 1] = 0;  // read by no one until the next barrier
+    // the filters are read by no one until the next tile's filter phase
+    for (int i = threadIdx.x; i < kFilterWords; i += kCellThreads) S.seen[i] = S.dup[i] = 0u;
     if (on) {
       // markers that no record joined are emptied by their inserting thread
       if (psi_local)
