@@ -438,6 +438,7 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t beta, uint32_t nb) {
 // fit a tile are staged in place and big classes go through bucket counters.
 
 constexpr int kRunThreads = 256;
+constexpr int kRunClaim = 4;   // runs a warp claims at a time
 constexpr int kPairTab = 496;  // C(32, 2): unranked index pairs
 constexpr int kAdThreads = 256;
 constexpr int kAdTile = 512;   // alpha-double pairs per CTA step
@@ -476,6 +477,7 @@ struct EmitArgs {
   uint32_t ad_tiles;
   Stage st;
   double eps;                 // Alg. 2 screen; 0 keeps every pair
+  float eps_f;                // eps as a float (the screen's float pre-test)
   int64_t E0_x;
   double inv_scale;
   unsigned long long *survivors;
@@ -567,19 +569,45 @@ __device__ __forceinline__ float scaled_as_float(int64_t z, int s) {
   return __uint_as_float((z < 0 ? 0x80000000u : 0u) | ((uint32_t)e << 23) | mant);
 }
 
+// |x| as a float built from the bits, truncated (relative error below 2^-23);
+// *ok is false when |x| lies outside the normal float range.
+__device__ __forceinline__ float abs_as_float(double x, bool *ok) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  int e = (int)(b >> 52) - 1023 + 127;
+  *ok = e >= 1 && e <= 254;
+  e = e < 1 ? 1 : (e > 254 ? 254 : e);
+  return __uint_as_float(((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
+}
+
 template <bool EPS>
 __device__ __forceinline__ void write_record(const EmitArgs &A, uint32_t pos, bool spill,
                                              uint32_t cell, uint32_t talpha, uint32_t tb,
                                              bool packed, double v, int64_t haa, bool *kept) {
+  const float df = scaled_as_float(A.E0_x - haa, A.X.s);
   if (EPS) {
-    // |v / (E0 - H_ii)| > eps, without a division
-    const double den = __ll2double_rn(A.E0_x - haa) * A.inv_scale;
-    if (!(fabs(v) > A.eps * fabs(den))) v = drop_marker();
-    *kept = !is_dropped(v);
+    // Alg. 2's screen |v / (E0 - H_ii)| > eps, without a division.  A float
+    // test settles every pair that is not within 4e-6 relative of the
+    // threshold (|v| and |E0 - H_ii| truncated to floats lie within 2^-23
+    // below their values, eps_f within 2^-24 of eps, the product within
+    // 2^-24); the rest take the FP64 test, so every decision is the FP64
+    // test's.  (FP64 instructions are scarce on this GPU.)
+    bool okv;
+    const float vf = abs_as_float(v, &okv);
+    const float t = A.eps_f * fabsf(df);
+    bool keep;
+    if (okv && t > 1e-37f && t < 1e37f && vf > t * 1.000004f) {
+      keep = true;
+    } else if (okv && t > 1e-37f && t < 1e37f && vf < t * 0.999996f) {
+      keep = false;
+    } else {
+      const double den = __ll2double_rn(A.E0_x - haa) * A.inv_scale;
+      keep = fabs(v) > A.eps * fabs(den);
+    }
+    if (!keep) v = drop_marker();
+    *kept = keep;
   }
   const uint64_t vb = (uint64_t)__double_as_longlong(v);
-  const uint4 r = make_uint4((uint32_t)vb, (uint32_t)(vb >> 32), tb,
-                             __float_as_uint(scaled_as_float(A.E0_x - haa, A.X.s)));
+  const uint4 r = make_uint4((uint32_t)vb, (uint32_t)(vb >> 32), tb, __float_as_uint(df));
   if (spill) {
     if (pos < A.spill_cap) {  // beyond: counted only, the host reports it
       reinterpret_cast<uint4 *>(A.spill_rec)[pos] = r;
@@ -591,6 +619,14 @@ __device__ __forceinline__ void write_record(const EmitArgs &A, uint32_t pos, bo
   } else {
     atomicOr(A.err, kErrStage);
   }
+}
+
+// The pairs an emission thread kept under the eps screen, added to the
+// search's counter once per warp when the kernel ends (one counter for the
+// whole grid: an atomic per chunk would serialise on it).
+__device__ __forceinline__ void add_survivors(const EmitArgs &A, unsigned long long kept) {
+  for (int d = 16; d; d >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, d);
+  if ((threadIdx.x & 31) == 0 && kept) atomicAdd(A.survivors, kept);
 }
 
 // EPS compiles Alg. 2's screen in (eps > 0); PREC selects the pair-value
@@ -615,15 +651,19 @@ __global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
   const uint32_t omask = (1u << A.opbits) - 1u;
   const int lane = threadIdx.x & 31;
   const uint32_t sb = A.E.sb, vb = A.E.vb;
-  // runs are claimed one at a time from a shared counter (their lengths differ
-  // by a factor of about fifty); the next claim is issued before the current
-  // run is emitted
+  unsigned long long my_kept = 0;  // pairs kept by the eps screen (EPS)
+  // runs are claimed kRunClaim at a time from a shared counter (their lengths
+  // differ by a factor of about fifty); the next claim is issued before the
+  // claimed runs are emitted
   unsigned long long claim = 0;
-  if (lane == 0) claim = atomicAdd(A.run_next, 1ull);
-  uint64_t r = (uint64_t)__shfl_sync(0xffffffffu, claim, 0);
+  if (lane == 0) claim = atomicAdd(A.run_next, (unsigned long long)kRunClaim);
+  uint64_t r0 = (uint64_t)__shfl_sync(0xffffffffu, claim, 0);
 #pragma unroll 1
-  for (; r < A.nruns; r = (uint64_t)__shfl_sync(0xffffffffu, claim, 0)) {
-    if (lane == 0) claim = atomicAdd(A.run_next, 1ull);
+  for (; r0 < A.nruns; r0 = (uint64_t)__shfl_sync(0xffffffffu, claim, 0)) {
+    if (lane == 0) claim = atomicAdd(A.run_next, (unsigned long long)kRunClaim);
+    const uint64_t r1 = r0 + kRunClaim < A.nruns ? r0 + kRunClaim : A.nruns;
+#pragma unroll 1
+  for (uint64_t r = r0; r < r1; ++r) {
     const uint64_t run = A.runs[r];
     const uint64_t t = A.t0 + (run >> 32);
     const uint32_t m = (uint32_t)run;
@@ -793,13 +833,12 @@ __global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
       if (cur.wr)
         write_record<EPS>(A, cur.pos, cur.spill, cur.cell, talpha, cur.tb, packed,
                           pair_value<PREC>(h, c, cf), base_x + dh, &kept);
-      if (EPS) {
-        const uint32_t nk = __popc(__ballot_sync(0xffffffffu, kept));
-        if (lane == 0 && nk) atomicAdd(A.survivors, (unsigned long long)nk);
-      }
+      if (EPS) my_kept += kept ? 1u : 0u;
       cur = nxt;
     }
   }
+  }
+  if (EPS) add_survivors(A, my_kept);
 }
 
 // Alpha-double pairs, flat: CTA step s covers flat pairs [s * kAdTile, ...).
@@ -819,6 +858,7 @@ __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
   const uint32_t full = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
   const uint32_t omask = (1u << A.opbits) - 1u;
   const int lane = threadIdx.x & 31;
+  unsigned long long my_kept = 0;  // pairs kept by the eps screen (EPS)
 #pragma unroll 1
   for (uint32_t step = blockIdx.x; step < A.ad_tiles; step += gridDim.x) {
     const uint32_t fb = step * kAdTile;
@@ -908,13 +948,11 @@ __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
                           pair_value<PREC>(sH[lo], A.core_c[jdx], (float)A.core_c[jdx]),
                           A.Dx[jdx] + dh, &kept);
       }
-      if (EPS) {
-        const uint32_t nk = __popc(__ballot_sync(0xffffffffu, kept));
-        if (lane == 0 && nk) atomicAdd(A.survivors, (unsigned long long)nk);
-      }
+      if (EPS) my_kept += kept ? 1u : 0u;
     }
     __syncthreads();  // the next step overwrites the item arrays
   }
+  if (EPS) add_survivors(A, my_kept);
 }
 
 // Per item of the batch: determinant runs (o = 0 or an alpha single) and the
@@ -1068,9 +1106,6 @@ __device__ __forceinline__ uint32_t tile_mix(uint64_t key) {
   h ^= h >> 16;
   return h;
 }
-__device__ __forceinline__ uint32_t slot_hash(uint64_t key) {
-  return tile_mix(key) & (uint32_t)(kSlots - 1);
-}
 
 // Open addressing with linear probing; the table is at most 1/4 full, and the
 // probe count is bounded by the table size (exceeding it sets *err).
@@ -1180,15 +1215,6 @@ __device__ __forceinline__ uint64_t slot_key(const CellSmem &S, int buf, uint32_
   return (v & kPsiBit) ? S.psik[buf][v & ~kPsiBit] : rec_key(S, buf, v, packed, alpha);
 }
 
-// |x| as a float built from the bits, truncated (relative error below 2^-23);
-// *ok is false when |x| lies outside the normal float range.
-__device__ __forceinline__ float abs_as_float(double x, bool *ok) {
-  const uint64_t b = (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
-  int e = (int)(b >> 52) - 1023 + 127;
-  *ok = e >= 1 && e <= 254;
-  e = e < 1 ? 1 : (e > 254 ? 254 : e);
-  return __uint_as_float(((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
-}
 
 // |v| as a float for the threshold bound: from the bits (no FP64 instruction),
 // +inf when |v| lies above the float range so that the bound always passes.
@@ -2121,6 +2147,7 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   A.ad_tiles = ad_tiles;
   A.st = st;
   A.eps = eps;
+  A.eps_f = (float)eps;
   A.E0_x = F.E0_x;
   A.inv_scale = ldexp(1.0, -F.X.s);
   A.survivors = survivors;
@@ -2370,18 +2397,6 @@ int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const S
 
 namespace {
 
-// Exact scores of appended candidates, which hold their numerator:
-// S = num / (E0 - H_ii), with H_ii summed in fixed point (exact) and E0 - H_ii
-// rounded once to a double.
-__global__ void k_exact_scores(const uint64_t *key, double *score, size_t n, FxInts X,
-                               int64_t E0_x, double inv_scale) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const uint64_t k = key[i];
-    const int64_t den_x = E0_x - fx_diag(X, key_alpha(k), (uint32_t)(k >> 32));
-    score[i] = score[i] / (__ll2double_rn(den_x) * inv_scale);
-  }
-}
 
 // ASCI-PT2 terms num^2 / (E0 - H_ii) of appended candidates (Alg. 1, last
 // step), summed without rounding in a fixed-point grid of 2^-216 held as eight
@@ -2467,6 +2482,25 @@ __device__ __forceinline__ int64_t warp_diag(const FxInts &X, uint32_t A, uint32
   }
   if (live && ((pending >> lane) & 1u)) diag = fx_diag(X, A, B);
   return diag;
+}
+
+// Exact scores of appended candidates, which hold their numerator:
+// S = num / (E0 - H_ii), with H_ii summed in fixed point (exact; warp_diag
+// shares the alpha part among the warp's candidates, which come from a few
+// tiles and mostly share their alpha string) and E0 - H_ii rounded once to a
+// double.
+__global__ void __launch_bounds__(256) k_exact_scores(const uint64_t *key, double *score, size_t n,
+                                                      FxInts X, int64_t E0_x, double inv_scale) {
+  // warp-uniform loop: warp_diag needs every lane
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t base = (size_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n;
+       base += stride) {
+    const size_t i = base + (threadIdx.x & 31u);
+    const bool live = i < n;
+    const uint64_t k = live ? key[i] : 0ull;
+    const int64_t dg = warp_diag(X, key_alpha(k), (uint32_t)(k >> 32), live);
+    if (live) score[i] = score[i] / (__ll2double_rn(E0_x - dg) * inv_scale);
+  }
 }
 
 __global__ void __launch_bounds__(256) k_pt2_terms(const uint64_t *key, const double *num,
