@@ -341,6 +341,14 @@ int build_tables(const double *h1_dev, const double *eri_dev, int n, int na, int
 // Exclusive prefix sum, device-wide; in and out may alias.
 int scan_exclusive_u32(const uint32_t *in, uint32_t *out, size_t n, Arena &arena);
 int scan_exclusive_u64(const uint64_t *in, uint64_t *out, size_t n, Arena &arena);
+// Exclusive scan of the pairs of each item of the constraint-batched
+// generation (group in the bits above opbits, alpha operation below): writes
+// T + 1 entries, the last one the total.
+int scan_item_weights(const uint64_t *items, uint64_t T, int opbits, const uint32_t *grp_count,
+                      const ExcCounts &X, uint64_t *Wexcl, Arena &arena);
+// Exclusive scan of the flags "item i starts a new target alpha string" of a
+// sorted item list: T + 1 entries, the last one the number of strings.
+int scan_item_heads(const uint64_t *items, uint64_t T, uint32_t *excl, Arena &arena);
 
 // Stable LSD radix sort of 64-bit keys on bits [begin_bit, end_bit), with an
 // optional payload.  The sorted data ends in *keys / *vals (the two buffers of

@@ -241,39 +241,49 @@ int emit_fixed_order(const DevInts &I, const uint64_t *core_keys, const double *
 
 namespace {
 
-__global__ void k_make_items(ExcCounts X, int n, const uint32_t *grp_alpha, uint32_t ngroups,
-                             uint32_t o_begin, uint32_t nops, int opbits, uint64_t *items) {
+// One CTA per group (persistent over groups): the group's occupied and
+// virtual orbitals and the unranked orbital-index pairs sit in shared memory,
+// so an operation's target costs two table reads per orbital pair and the
+// items of a group are written contiguously.  The operation numbering is the
+// one of decode_single / decode_double.
+__global__ void __launch_bounds__(256)
+    k_make_items(ExcCounts X, int n, const uint32_t *grp_alpha, uint32_t ngroups,
+                 uint32_t o_begin, uint32_t nops, int opbits, FastDiv by_nv, FastDiv by_npp,
+                 uint64_t *items) {
+  __shared__ uint8_t occ[32], vir[32];
+  __shared__ uint8_t pr_x[496], pr_y[496];  // pair r -> (x, y), x < y < 32
   const uint32_t per = nops - o_begin;
-  const uint64_t total = (uint64_t)ngroups * per;
   const uint32_t full = full_mask(n);
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t k = (uint32_t)(t / per), o = o_begin + (uint32_t)(t % per);
-    uint32_t A = grp_alpha[k], va = ~A & full, At = A;
-    int i, j, a, b;
-    if (o == 0) {
-      At = A;
-    } else if (o <= X.sa) {
-      decode_single(A, va, o - 1, X.va, &i, &a);
-      At = A ^ (1u << i) ^ (1u << a);
-    } else {
-      decode_double(A, va, o - 1 - X.sa, X.pa_p, &i, &j, &a, &b);
-      At = A ^ (1u << i) ^ (1u << j) ^ (1u << a) ^ (1u << b);
-    }
-    items[t] = ((uint64_t)At << 32) | ((uint64_t)k << opbits) | o;
+  for (int r = threadIdx.x; r < 496; r += blockDim.x) {
+    int x, y;
+    unrank_pair((uint32_t)r, &x, &y);
+    pr_x[r] = (uint8_t)x;
+    pr_y[r] = (uint8_t)y;
   }
-}
-
-__global__ void k_item_weights(const uint64_t *items, uint64_t nitems, int opbits,
-                               const uint32_t *grp_count, ExcCounts X, uint64_t *w) {
-  const uint32_t omask = (1u << opbits) - 1u;
-  const uint64_t npd0 = (uint64_t)X.sb + X.dbb, npd1 = 1ull + X.sb;
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nitems;
-       t += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t lo = (uint32_t)items[t];
-    uint32_t k = lo >> opbits, o = lo & omask;
-    uint64_t npd = (o == 0) ? npd0 : (o <= X.sa ? npd1 : 1ull);
-    w[t] = npd * grp_count[k];
+  for (uint32_t k = blockIdx.x; k < ngroups; k += gridDim.x) {
+    const uint32_t A = grp_alpha[k], va = ~A & full;
+    __syncthreads();  // previous group's lists no longer read
+    if (threadIdx.x < 32) {
+      const uint32_t bit = 1u << threadIdx.x;
+      if (A & bit) occ[__popc(A & (bit - 1u))] = (uint8_t)threadIdx.x;
+      if (va & bit) vir[__popc(va & (bit - 1u))] = (uint8_t)threadIdx.x;
+    }
+    __syncthreads();
+    uint64_t *out = items + (uint64_t)k * per;
+    const uint64_t lo_k = (uint64_t)k << opbits;
+    for (uint32_t t = threadIdx.x; t < per; t += blockDim.x) {
+      const uint32_t o = o_begin + t;
+      uint32_t At = A;
+      if (o != 0 && o <= X.sa) {
+        const uint32_t idx = o - 1, h = by_nv.div(idx);
+        At ^= (1u << occ[h]) ^ (1u << vir[idx - h * X.va]);
+      } else if (o != 0) {
+        const uint32_t idx = o - 1 - X.sa, hp = by_npp.div(idx), pp = idx - hp * X.pa_p;
+        At ^= (1u << occ[pr_x[hp]]) ^ (1u << occ[pr_y[hp]]) ^ (1u << vir[pr_x[pp]]) ^
+              (1u << vir[pr_y[pp]]);
+      }
+      out[t] = ((uint64_t)At << 32) | lo_k | o;
+    }
   }
 }
 
@@ -283,21 +293,10 @@ int make_items(const ExcCounts &X, int n, const uint32_t *grp_alpha, uint32_t ng
                uint32_t o_begin, uint32_t nops, int opbits, uint64_t *items, Arena &arena) {
   uint64_t total = (uint64_t)ngroups * (nops - o_begin);
   if (!total) return ASCI_OK;
-  uint64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  k_make_items<<<(unsigned)blocks, 256, 0, arena.stream()>>>(X, n, grp_alpha, ngroups, o_begin,
-                                                             nops, opbits, items);
-  ASCI_CHECK_LAUNCH();
-  return ASCI_OK;
-}
-
-int item_weights(const uint64_t *items, uint64_t nitems, int opbits, const uint32_t *grp_count,
-                 const ExcCounts &X, uint64_t *w, Arena &arena) {
-  if (!nitems) return ASCI_OK;
-  uint64_t blocks = (nitems + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  k_item_weights<<<(unsigned)blocks, 256, 0, arena.stream()>>>(items, nitems, opbits, grp_count,
-                                                               X, w);
+  const unsigned blocks = (unsigned)std::min<uint64_t>(ngroups, 152 * 8);
+  k_make_items<<<blocks, 256, 0, arena.stream()>>>(X, n, grp_alpha, ngroups, o_begin, nops, opbits,
+                                                   FastDiv(X.va ? X.va : 1),
+                                                   FastDiv(X.pa_p ? X.pa_p : 1), items);
   ASCI_CHECK_LAUNCH();
   return ASCI_OK;
 }

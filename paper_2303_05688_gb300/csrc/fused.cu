@@ -199,30 +199,28 @@ __global__ void k_core_fock(FxInts X, const uint32_t *core_alpha, const uint32_t
 
 // ------------------------------------------------------ groups of items ---
 
-__global__ void k_item_gflags(const uint64_t *items, uint64_t T, uint32_t *flag) {
+// gid holds the exclusive scan of the head flags; it becomes each item's group
+// (heads up to and including it, less one), and each head fills its group's
+// row.  Row G (one past the last group) gets the totals: T items, P pairs.
+__global__ void k_group_tab(const uint64_t *items, uint32_t *gid, const uint64_t *Wexcl, uint64_t T,
+                            uint32_t *g_alpha, uint64_t *g_P0, uint64_t *g_item0) {
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
-       t += (uint64_t)gridDim.x * blockDim.x)
-    flag[t] = (t == 0 || (items[t] >> 32) != (items[t - 1] >> 32)) ? 1u : 0u;
-}
-
-// group of each item = (group starts up to and including it) - 1
-__global__ void k_item_gfix(const uint32_t *flag, uint64_t T, uint32_t *gid) {
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
-       t += (uint64_t)gridDim.x * blockDim.x)
-    gid[t] = gid[t] + flag[t] - 1u;
-}
-
-__global__ void k_group_tab(const uint64_t *items, const uint32_t *flag, const uint32_t *gid,
-                            const uint64_t *Wexcl, uint64_t T, uint32_t *g_alpha, uint64_t *g_P0,
-                            uint64_t *g_item0) {
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
-       t += (uint64_t)gridDim.x * blockDim.x)
-    if (flag[t]) {
-      uint32_t g = gid[t];
-      g_alpha[g] = (uint32_t)(items[t] >> 32);
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t hi = (uint32_t)(items[t] >> 32);
+    const bool head = t == 0 || hi != (uint32_t)(items[t - 1] >> 32);
+    const uint32_t g = gid[t] + (head ? 1u : 0u) - 1u;
+    gid[t] = g;
+    if (head) {
+      g_alpha[g] = hi;
       g_P0[g] = Wexcl[t];
       g_item0[g] = t;
     }
+    if (t == T - 1) {
+      g_alpha[g + 1] = 0;
+      g_P0[g + 1] = Wexcl[T];
+      g_item0[g + 1] = T;
+    }
+  }
 }
 
 // ------------------------------------------------------- tile planning ---
@@ -1873,28 +1871,21 @@ int core_fock(const FxInts &X, const uint32_t *core_alpha, const uint32_t *core_
   return ASCI_OK;
 }
 
-// Groups (distinct target alpha strings) of the sorted item list.
+// Groups (distinct target alpha strings) of the sorted item list.  item_group
+// has T + 1 entries; the group tables have G + 1 rows (row G: T and P).
 int item_groups(const uint64_t *items, const uint64_t *Wexcl, uint64_t T, uint32_t *item_group,
                 uint32_t **g_alpha, uint64_t **g_P0, uint64_t **g_item0, size_t *G,
                 Arena &arena) {
   cudaStream_t s = arena.stream();
-  uint32_t *flag;
-  Arena tmp(s);
-  ASCI_TRY(tmp.alloc(&flag, T));
-  k_item_gflags<<<grid_for(T), 256, 0, s>>>(items, T, flag);
-  ASCI_CHECK_LAUNCH();
-  ASCI_TRY(scan_exclusive_u32(flag, item_group, T, tmp));
-  size_t ng = 0;
-  ASCI_TRY(kept_count(flag, item_group, T, &ng, tmp));
-  k_item_gfix<<<grid_for(T), 256, 0, s>>>(flag, T, item_group);
-  ASCI_CHECK_LAUNCH();
-  ASCI_TRY(arena.alloc(g_alpha, ng));
-  ASCI_TRY(arena.alloc(g_P0, ng));
-  ASCI_TRY(arena.alloc(g_item0, ng));
-  k_group_tab<<<grid_for(T), 256, 0, s>>>(items, flag, item_group, Wexcl, T, *g_alpha, *g_P0,
-                                          *g_item0);
-  ASCI_CHECK_LAUNCH();
+  ASCI_TRY(scan_item_heads(items, T, item_group, arena));
+  uint32_t ng = 0;
+  ASCI_TRY_CUDA(cudaMemcpyAsync(&ng, item_group + T, 4, cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  ASCI_TRY(arena.alloc(g_alpha, (size_t)ng + 1));
+  ASCI_TRY(arena.alloc(g_P0, (size_t)ng + 1));
+  ASCI_TRY(arena.alloc(g_item0, (size_t)ng + 1));
+  k_group_tab<<<grid_for(T), 256, 0, s>>>(items, item_group, Wexcl, T, *g_alpha, *g_P0, *g_item0);
+  ASCI_CHECK_LAUNCH();
   *G = ng;
   return ASCI_OK;
 }

@@ -33,8 +33,6 @@ namespace asci {
 
 int make_items(const ExcCounts &X, int n, const uint32_t *grp_alpha, uint32_t ngroups,
                uint32_t o_begin, uint32_t nops, int opbits, uint64_t *items, Arena &arena);
-int item_weights(const uint64_t *items, uint64_t nitems, int opbits, const uint32_t *grp_count,
-                 const ExcCounts &X, uint64_t *w, Arena &arena);
 int compact_u64(const uint64_t *in, const uint32_t *keep, const uint32_t *pos, size_t n,
                 uint64_t *out, Arena &arena);
 int compact_f64(const double *in, const uint32_t *keep, const uint32_t *pos, size_t n, double *out,
@@ -235,24 +233,26 @@ __device__ __forceinline__ uint32_t top_bits(uint32_t x, int L) {
   return x;
 }
 
-// class starts at level L inside items [s, e)
-__global__ void k_class_heads(const uint64_t *items, uint64_t s, uint64_t e, int L,
+// class starts at level L inside target groups [s, e)
+__global__ void k_class_heads(const uint32_t *g_alpha, uint64_t s, uint64_t e, int L,
                               uint32_t *head) {
-  for (uint64_t t = s + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < e;
-       t += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t cur = top_bits((uint32_t)(items[t] >> 32), L);
-    uint32_t prv = (t == s) ? ~cur : top_bits((uint32_t)(items[t - 1] >> 32), L);
-    head[t - s] = (t == s || cur != prv) ? 1u : 0u;
+  for (uint64_t g = s + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < e;
+       g += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t cur = top_bits(g_alpha[g], L);
+    head[g - s] = (g == s || cur != top_bits(g_alpha[g - 1], L)) ? 1u : 0u;
   }
 }
 
+// each class's first group, first item and first pair
 __global__ void k_class_list(const uint32_t *head, const uint32_t *pos, uint64_t s, uint64_t cnt,
-                             const uint64_t *Wexcl, uint64_t *starts, uint64_t *wstarts) {
+                             const uint64_t *g_item0, const uint64_t *g_P0, uint64_t *gstarts,
+                             uint64_t *istarts, uint64_t *wstarts) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
        i += (uint64_t)gridDim.x * blockDim.x)
     if (head[i]) {
-      starts[pos[i]] = s + i;
-      wstarts[pos[i]] = Wexcl[s + i];
+      gstarts[pos[i]] = s + i;
+      istarts[pos[i]] = g_item0[s + i];
+      wstarts[pos[i]] = g_P0[s + i];
     }
 }
 
@@ -335,7 +335,7 @@ int shard_items(uint64_t **items, uint64_t **items_alt, const uint64_t *Wexcl, u
   uint32_t *item_group, *g_alpha;
   uint64_t *g_P0, *g_item0;
   size_t G = 0;
-  ASCI_TRY(sa.alloc(&item_group, T));
+  ASCI_TRY(sa.alloc(&item_group, T + 1));
   ASCI_TRY(item_groups(*items, Wexcl, T, item_group, &g_alpha, &g_P0, &g_item0, &G, sa));
   const uint64_t heavy = std::max<uint64_t>(1, P / (64ull * (uint64_t)W));
   const uint32_t heavy_cap = (uint32_t)std::min<uint64_t>(G, 64ull * W + 1);
@@ -413,24 +413,33 @@ struct Batch {
 };
 
 // Cut items [0, T) into batches of at most bmax pairs at class boundaries
-// (Sec. 2.2 constraints; Alg. 3's work counts h are the class weights).
+// (Sec. 2.2 constraints; Alg. 3's work counts h are the class weights).  A
+// class is a set of target alpha strings, so the classes are found on the
+// table of distinct target strings (groups; row G holds T and P).
 class Planner {
  public:
-  Planner(const uint64_t *items, const uint64_t *Wexcl, uint64_t bmax, uint64_t first_cap,
-          int lmax, Arena &arena)
-      : items_(items), W_(Wexcl), bmax_(bmax), first_cap_(first_cap), lmax_(lmax),
-        arena_(arena) {}
+  Planner(const uint32_t *g_alpha, const uint64_t *g_item0, const uint64_t *g_P0, uint64_t G,
+          uint64_t bmax, uint64_t first_cap, int lmax, Arena &arena)
+      : ga_(g_alpha), gi_(g_item0), gp_(g_P0), G_(G), bmax_(bmax), first_cap_(first_cap),
+        lmax_(lmax), arena_(arena) {}
 
-  // Classes of level L over items [0, T): first items and first pairs.
-  int classes(uint64_t T, int L, std::vector<uint64_t> *starts, std::vector<uint64_t> *wst) {
-    return query(0, T, L, starts, wst);
+  // The pairs of each class of level L, in constraint order.
+  int class_weights(int L, std::vector<uint64_t> *w) {
+    std::vector<uint64_t> gst, ist, wst;
+    ASCI_TRY(query(0, G_, L, &gst, &ist, &wst));
+    uint64_t P = 0;
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&P, gp_ + G_, 8, cudaMemcpyDefault, arena_.stream()));
+    ASCI_TRY_CUDA(cudaStreamSynchronize(arena_.stream()));
+    w->resize(wst.size());
+    for (size_t i = 0; i < wst.size(); ++i) (*w)[i] = (i + 1 < wst.size() ? wst[i + 1] : P) - wst[i];
+    return ASCI_OK;
   }
 
   int run(uint64_t T, uint64_t P, int L0, std::vector<Batch> *out, int *max_level) {
     batches_.clear();
     cur_open_ = false;
     max_level_ = L0;
-    ASCI_TRY(visit(0, T, 0, P, L0));
+    ASCI_TRY(visit(0, G_, 0, T, 0, P, L0));
     flush();
     *out = batches_;
     *max_level = max_level_;
@@ -438,7 +447,7 @@ class Planner {
   }
 
  private:
-  int query(uint64_t s, uint64_t e, int L, std::vector<uint64_t> *starts,
+  int query(uint64_t s, uint64_t e, int L, std::vector<uint64_t> *gst, std::vector<uint64_t> *ist,
             std::vector<uint64_t> *wst) {
     uint64_t cnt = e - s;
     Arena qa(arena_.stream());  // released when the query returns
@@ -446,19 +455,22 @@ class Planner {
     ASCI_TRY(qa.alloc(&head, cnt));
     ASCI_TRY(qa.alloc(&pos, cnt));
     cudaStream_t st = qa.stream();
-    k_class_heads<<<grid_for(cnt), 256, 0, st>>>(items_, s, e, L, head);
+    k_class_heads<<<grid_for(cnt), 256, 0, st>>>(ga_, s, e, L, head);
     ASCI_CHECK_LAUNCH();
     ASCI_TRY(scan_exclusive_u32(head, pos, cnt, qa));
     size_t nc = 0;
     ASCI_TRY(kept_count(head, pos, cnt, &nc, qa));
-    uint64_t *ds, *dw;
-    ASCI_TRY(qa.alloc(&ds, nc));
+    uint64_t *dg, *di, *dw;
+    ASCI_TRY(qa.alloc(&dg, nc));
+    ASCI_TRY(qa.alloc(&di, nc));
     ASCI_TRY(qa.alloc(&dw, nc));
-    k_class_list<<<grid_for(cnt), 256, 0, st>>>(head, pos, s, cnt, W_, ds, dw);
+    k_class_list<<<grid_for(cnt), 256, 0, st>>>(head, pos, s, cnt, gi_, gp_, dg, di, dw);
     ASCI_CHECK_LAUNCH();
-    starts->resize(nc);
+    gst->resize(nc);
+    ist->resize(nc);
     wst->resize(nc);
-    ASCI_TRY_CUDA(cudaMemcpyAsync(starts->data(), ds, nc * 8, cudaMemcpyDefault, st));
+    ASCI_TRY_CUDA(cudaMemcpyAsync(gst->data(), dg, nc * 8, cudaMemcpyDefault, st));
+    ASCI_TRY_CUDA(cudaMemcpyAsync(ist->data(), di, nc * 8, cudaMemcpyDefault, st));
     ASCI_TRY_CUDA(cudaMemcpyAsync(wst->data(), dw, nc * 8, cudaMemcpyDefault, st));
     ASCI_TRY_CUDA(cudaStreamSynchronize(st));
     return ASCI_OK;
@@ -481,25 +493,30 @@ class Planner {
     }
   }
 
-  int visit(uint64_t s, uint64_t e, uint64_t ws, uint64_t we, int L) {
+  // groups [gs, ge) = items [is, ie) = pairs [ws, we), split at level L
+  int visit(uint64_t gs, uint64_t ge, uint64_t is, uint64_t ie, uint64_t ws, uint64_t we, int L) {
     if (L > max_level_) max_level_ = L;
-    std::vector<uint64_t> starts, wst;
-    ASCI_TRY(query(s, e, L, &starts, &wst));
-    for (size_t c = 0; c < starts.size(); ++c) {
-      uint64_t cs = starts[c], ce = (c + 1 < starts.size()) ? starts[c + 1] : e;
-      uint64_t w0 = wst[c], w1 = (c + 1 < starts.size()) ? wst[c + 1] : we;
-      if (w1 - w0 > bmax_ && L < lmax_ && ce - cs > 1) {
+    std::vector<uint64_t> gst, ist, wst;
+    ASCI_TRY(query(gs, ge, L, &gst, &ist, &wst));
+    for (size_t c = 0; c < gst.size(); ++c) {
+      const bool last = c + 1 == gst.size();
+      const uint64_t g0 = gst[c], g1 = last ? ge : gst[c + 1];
+      const uint64_t i0 = ist[c], i1 = last ? ie : ist[c + 1];
+      const uint64_t w0 = wst[c], w1 = last ? we : wst[c + 1];
+      if (w1 - w0 > bmax_ && L < lmax_ && g1 - g0 > 1) {
         flush();
-        ASCI_TRY(visit(cs, ce, w0, w1, L + 1));
+        ASCI_TRY(visit(g0, g1, i0, i1, w0, w1, L + 1));
       } else {
-        add(cs, ce, w0, w1);
+        add(i0, i1, w0, w1);
       }
     }
     return ASCI_OK;
   }
 
-  const uint64_t *items_;
-  const uint64_t *W_;
+  const uint32_t *ga_;
+  const uint64_t *gi_;
+  const uint64_t *gp_;
+  uint64_t G_;
   uint64_t bmax_;
   uint64_t first_cap_;
   int lmax_;
@@ -687,22 +704,17 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   const int32_t W = o.shard_count > 1 ? o.shard_count : 1;
   std::vector<Batch> batches;
   int max_level = 0;
-  uint64_t *items = nullptr, *items_alt = nullptr, *w = nullptr, *Wexcl = nullptr;
+  uint64_t *items = nullptr, *items_alt = nullptr, *Wexcl = nullptr;
   uint64_t P = 0;
   if (T > 0) {
     ASCI_TRY(arena.alloc(&items, T));
     ASCI_TRY(arena.alloc(&items_alt, T));
     ASCI_TRY(make_items(X, n, grp_alpha, (uint32_t)ngroups, o_begin, nops, opbits, items, arena));
     ASCI_TRY(radix_sort_u64(&items, &items_alt, T, 32, 32 + n, arena));
-    ASCI_TRY(arena.alloc(&w, T));
-    ASCI_TRY(arena.alloc(&Wexcl, T));
-    ASCI_TRY(item_weights(items, T, opbits, grp_count, X, w, arena));
-    ASCI_TRY(scan_exclusive_u64(w, Wexcl, T, arena));
-    uint64_t last[2];
-    ASCI_TRY_CUDA(cudaMemcpyAsync(&last[0], Wexcl + T - 1, 8, cudaMemcpyDefault, stream));
-    ASCI_TRY_CUDA(cudaMemcpyAsync(&last[1], w + T - 1, 8, cudaMemcpyDefault, stream));
+    ASCI_TRY(arena.alloc(&Wexcl, T + 1));
+    ASCI_TRY(scan_item_weights(items, T, opbits, grp_count, X, Wexcl, arena));
+    ASCI_TRY_CUDA(cudaMemcpyAsync(&P, Wexcl + T, 8, cudaMemcpyDefault, stream));
     ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
-    P = last[0] + last[1];
     if (P != (uint64_t)m * X.total) {
       record_error("pair count does not match the closed form", __FILE__, __LINE__);
       return ASCI_ECUDA;
@@ -715,25 +727,29 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
       T = T1;
       P = 0;
       if (T) {
-        ASCI_TRY(item_weights(items, T, opbits, grp_count, X, w, arena));
-        ASCI_TRY(scan_exclusive_u64(w, Wexcl, T, arena));
-        ASCI_TRY_CUDA(cudaMemcpyAsync(&last[0], Wexcl + T - 1, 8, cudaMemcpyDefault, stream));
-        ASCI_TRY_CUDA(cudaMemcpyAsync(&last[1], w + T - 1, 8, cudaMemcpyDefault, stream));
+        ASCI_TRY(scan_item_weights(items, T, opbits, grp_count, X, Wexcl, arena));
+        ASCI_TRY_CUDA(cudaMemcpyAsync(&P, Wexcl + T, 8, cudaMemcpyDefault, stream));
         ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
-        P = last[0] + last[1];
       }
     }
+  }
+  // the distinct target alpha strings (groups) of the items
+  uint32_t *item_group = nullptr;
+  uint32_t *g_alpha = nullptr;
+  uint64_t *g_P0 = nullptr, *g_item0 = nullptr;
+  size_t G = 0;
+  if (T > 0) {
+    ASCI_TRY(arena.alloc(&item_group, T + 1));
+    ASCI_TRY(item_groups(items, Wexcl, T, item_group, &g_alpha, &g_P0, &g_item0, &G, arena));
   }
   if (cq) {  // the classes of one level, in constraint order, and their pairs
     cq->n = 0;
     if (T > 0 && P > 0) {
-      Planner pl(items, Wexcl, P, P, na, arena);
-      std::vector<uint64_t> starts, wst;
-      ASCI_TRY(pl.classes(T, std::min(cq->level, na), &starts, &wst));
-      cq->n = starts.size();
+      Planner pl(g_alpha, g_item0, g_P0, G, P, P, na, arena);
+      std::vector<uint64_t> w;
+      ASCI_TRY(pl.class_weights(std::min(cq->level, na), &w));
+      cq->n = w.size();
       if (cq->capacity >= cq->n && cq->n) {
-        std::vector<uint64_t> w(cq->n);
-        for (size_t i = 0; i < cq->n; ++i) w[i] = (i + 1 < cq->n ? wst[i + 1] : P) - wst[i];
         ASCI_TRY_CUDA(cudaMemcpyAsync(cq->out, w.data(), cq->n * 8, cudaMemcpyDefault, stream));
         ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
       }
@@ -754,7 +770,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     const int L0 = std::min(3, lmax);
     // a small first batch fixes the selection threshold early
     const uint64_t first_cap = std::min<uint64_t>(bmax, std::max<uint64_t>(1ull << 22, P / 64));
-    Planner planner(items, Wexcl, bmax, first_cap, lmax, arena);
+    Planner planner(g_alpha, g_item0, g_P0, G, bmax, first_cap, lmax, arena);
     ASCI_TRY(planner.run(T, P, L0, &batches, &max_level));
   }
   uint64_t bcap = 0;
@@ -814,14 +830,6 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     F.Dx = Dx;
     F.Fa = Fa;
     F.Fb = Fb;
-  }
-  uint32_t *item_group = nullptr;
-  uint32_t *g_alpha = nullptr;
-  uint64_t *g_P0 = nullptr, *g_item0 = nullptr;
-  size_t G = 0;
-  if (T > 0) {
-    ASCI_TRY(arena.alloc(&item_group, T));
-    ASCI_TRY(item_groups(items, Wexcl, T, item_group, &g_alpha, &g_P0, &g_item0, &G, arena));
   }
   F.item_group = item_group;
   F.g_alpha = g_alpha;

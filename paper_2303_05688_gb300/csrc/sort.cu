@@ -43,71 +43,122 @@ __device__ T block_exclusive_scan(T v, T *total) {
   return warp_prefix + x - v;
 }
 
+// Scan inputs: an array, or a value computed from each index.
 template <typename T>
-__global__ void k_tile_reduce(const T *in, size_t n, T *partial) {
+struct ArrayIn {
+  const T *p;
+  __device__ T operator()(size_t i) const { return p[i]; }
+};
+
+// Pairs of item i (the constraint-batched generation's item format, alpha
+// operation in the low opbits, group above it): the beta singles and doubles
+// for o = 0, the single itself and its alpha-beta doubles for an alpha
+// single, one pair for an alpha double; times the group's core determinants.
+// Index T (one past the end) is 0, so the scan's last entry is the total.
+struct ItemWeightIn {
+  const uint64_t *items;
+  const uint32_t *grp_count;
+  uint64_t T, npd0, npd1;
+  uint32_t omask, sa;
+  int opbits;
+  __device__ uint64_t operator()(size_t i) const {
+    if (i >= T) return 0;
+    const uint32_t lo = (uint32_t)items[i];
+    const uint32_t k = lo >> opbits, o = lo & omask;
+    const uint64_t npd = (o == 0) ? npd0 : (o <= sa ? npd1 : 1ull);
+    return npd * grp_count[k];
+  }
+};
+
+// 1 where item i starts a new target alpha string (its high word changes);
+// index T (one past the end) is 0, so the scan's last entry is the count.
+struct ItemHeadIn {
+  const uint64_t *items;
+  uint64_t T;
+  __device__ uint32_t operator()(size_t i) const {
+    if (i >= T) return 0u;
+    return (i == 0 || (items[i] >> 32) != (items[i - 1] >> 32)) ? 1u : 0u;
+  }
+};
+
+template <typename T, typename In>
+__global__ void k_tile_reduce(In in, size_t n, T *partial) {
   size_t base = (size_t)blockIdx.x * kScanTile;
   T s = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     size_t idx = base + (size_t)i * kScanThreads + threadIdx.x;
-    if (idx < n) s += in[idx];
+    if (idx < n) s += in(idx);
   }
   T total;
   block_exclusive_scan<T>(s, &total);
   if (threadIdx.x == 0) partial[blockIdx.x] = total;
 }
 
+// Shared-memory index of tile element e, padded by one element per 128 bytes
+// so that the transposed pass (thread t on elements 16t .. 16t+15) falls on
+// distinct banks: without the pad every thread of a warp hits one or two banks.
 template <typename T>
-__global__ void k_tile_scan(const T *in, T *out, size_t n, const T *partial) {
-  __shared__ T tile[kScanTile];
+__device__ __forceinline__ int scan_pad(int e) {
+  return e + e / (int)(128 / sizeof(T));
+}
+
+template <typename T, typename In>
+__global__ void k_tile_scan(In in, T *out, size_t n, const T *partial) {
+  __shared__ T tile[kScanTile + kScanTile / (128 / sizeof(T))];
   size_t base = (size_t)blockIdx.x * kScanTile;
   // coalesced load into shared memory
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     size_t idx = base + (size_t)i * kScanThreads + threadIdx.x;
-    tile[i * kScanThreads + threadIdx.x] = idx < n ? in[idx] : T(0);
+    tile[scan_pad<T>(i * kScanThreads + threadIdx.x)] = idx < n ? in(idx) : T(0);
   }
   __syncthreads();
   T v[kScanItems];
   T s = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    v[i] = tile[threadIdx.x * kScanItems + i];
+    v[i] = tile[scan_pad<T>(threadIdx.x * kScanItems + i)];
     s += v[i];
   }
   T pre = block_exclusive_scan<T>(s, nullptr);
   if (partial) pre += partial[blockIdx.x];
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    tile[threadIdx.x * kScanItems + i] = pre;
+    tile[scan_pad<T>(threadIdx.x * kScanItems + i)] = pre;
     pre += v[i];
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     size_t idx = base + (size_t)i * kScanThreads + threadIdx.x;
-    if (idx < n) out[idx] = tile[i * kScanThreads + threadIdx.x];
+    if (idx < n) out[idx] = tile[scan_pad<T>(i * kScanThreads + threadIdx.x)];
   }
 }
 
-template <typename T>
-int scan_exclusive(const T *in, T *out, size_t n, Arena &arena) {
+template <typename T, typename In>
+int scan_exclusive_by(In in, T *out, size_t n, Arena &arena) {
   if (n == 0) return ASCI_OK;
   size_t nb = (n + kScanTile - 1) / kScanTile;
   cudaStream_t s = arena.stream();
   if (nb == 1) {
-    k_tile_scan<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    k_tile_scan<T, In><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
     ASCI_CHECK_LAUNCH();
     return ASCI_OK;
   }
   T *partial = nullptr;
   ASCI_TRY(arena.alloc(&partial, nb));
-  k_tile_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial);
+  k_tile_reduce<T, In><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial);
   ASCI_CHECK_LAUNCH();
-  ASCI_TRY(scan_exclusive<T>(partial, partial, nb, arena));
-  k_tile_scan<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partial);
+  ASCI_TRY(scan_exclusive_by<T>(ArrayIn<T>{partial}, partial, nb, arena));
+  k_tile_scan<T, In><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, partial);
   ASCI_CHECK_LAUNCH();
   return ASCI_OK;
+}
+
+template <typename T>
+int scan_exclusive(const T *in, T *out, size_t n, Arena &arena) {
+  return scan_exclusive_by<T>(ArrayIn<T>{in}, out, n, arena);
 }
 
 // ----------------------------- radix sort ---------------------------------
@@ -147,7 +198,7 @@ constexpr size_t scatter_smem() {
 // is then written to its global position with consecutive threads on
 // consecutive addresses.
 template <typename V, bool kHasVals>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 4)
     k_digit_scatter(const uint64_t *keys_in, const V *vals_in, uint64_t *keys_out, V *vals_out,
                     size_t n, int shift, const uint32_t *offsets, uint32_t ntiles) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -162,16 +213,21 @@ __global__ void __launch_bounds__(kSortThreads)
   __syncthreads();
   const size_t base = (size_t)blockIdx.x * kSortTile;
   const size_t wbase = base + (size_t)warp * 32 * kSortItems;
+  // the tile's keys stay in registers (four CTAs of 256 threads per SM); a
+  // key's digit is recomputed where it is needed, out-of-range slots get the
+  // digit kRadix, which no counter holds
   uint64_t k[kSortItems];
-  uint32_t d[kSortItems];
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const size_t idx = wbase + (size_t)r * 32 + lane;
-    const bool ok = idx < n;
-    k[r] = ok ? keys_in[idx] : 0ull;
-    d[r] = ok ? (uint32_t)((k[r] >> shift) & 0xffu) : (uint32_t)kRadix;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d[r]);
-    if (ok && lane == __ffs(peers) - 1) wb[warp * kRadix + d[r]] += __popc(peers);
+    k[r] = idx < n ? keys_in[idx] : 0ull;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const bool ok = wbase + (size_t)r * 32 + lane < n;
+    const uint32_t d = ok ? (uint32_t)((k[r] >> shift) & 0xffu) : (uint32_t)kRadix;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (ok && lane == __ffs(peers) - 1) wb[warp * kRadix + d] += __popc(peers);
   }
   __syncthreads();
   {
@@ -193,11 +249,12 @@ __global__ void __launch_bounds__(kSortThreads)
   for (int r = 0; r < kSortItems; ++r) {
     const size_t idx = wbase + (size_t)r * 32 + lane;
     const bool ok = idx < n;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d[r]);
+    const uint32_t d = ok ? (uint32_t)((k[r] >> shift) & 0xffu) : (uint32_t)kRadix;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t pos = 0;
-    if (ok) pos = dstart[d[r]] + wb[warp * kRadix + d[r]] + __popc(peers & lt);
+    if (ok) pos = dstart[d] + wb[warp * kRadix + d] + __popc(peers & lt);
     __syncwarp();
-    if (ok && lane == __ffs(peers) - 1) wb[warp * kRadix + d[r]] += __popc(peers);
+    if (ok && lane == __ffs(peers) - 1) wb[warp * kRadix + d] += __popc(peers);
     __syncwarp();
     if (ok) {
       sk[pos] = k[r];
@@ -270,6 +327,17 @@ int scan_exclusive_u32(const uint32_t *in, uint32_t *out, size_t n, Arena &arena
 }
 int scan_exclusive_u64(const uint64_t *in, uint64_t *out, size_t n, Arena &arena) {
   return scan_exclusive<uint64_t>(in, out, n, arena);
+}
+
+int scan_item_weights(const uint64_t *items, uint64_t T, int opbits, const uint32_t *grp_count,
+                      const ExcCounts &X, uint64_t *Wexcl, Arena &arena) {
+  ItemWeightIn in{items, grp_count, T, (uint64_t)X.sb + X.dbb, 1ull + X.sb,
+                  (1u << opbits) - 1u, X.sa, opbits};
+  return scan_exclusive_by<uint64_t>(in, Wexcl, (size_t)T + 1, arena);
+}
+
+int scan_item_heads(const uint64_t *items, uint64_t T, uint32_t *excl, Arena &arena) {
+  return scan_exclusive_by<uint32_t>(ItemHeadIn{items, T}, excl, (size_t)T + 1, arena);
 }
 
 int varying_bits_u64(const uint64_t *keys, size_t n, uint64_t *host_mask, Arena &arena) {
