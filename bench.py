@@ -756,7 +756,7 @@ def main():
     t_search = statistics.mean(times) / 1e3
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_note,
-                "kernel": "k_cells (on-chip counting-sort reduction of staged pairs)",
+                "kernel": "k_cells (on-chip hash reduction of staged pairs)",
                 "peak_kind": peak_kind, "launches_per_step": tile_launches / args.steps,
                 "alg_bytes_per_launch": bytes_per_launch, "ms_per_launch": per_launch_s * 1e3,
                 "search": {"alg_bytes_per_step": b_alg, "achieved": b_alg / t_search / 1e9,
@@ -765,6 +765,10 @@ def main():
                 # of the on-chip tile kernel and the global-sort path together
                 "accumulate_pairs_per_s": (stats.tile_records + stats.oversized_records) / max(
                     (ts["tiles"] + ts["oversized"]) / 1e3, 1e-12),
+                # pairs of hash buckets that hot targets overfilled, and those of
+                # them reduced on chip by the large tile kernel
+                "oversized_records": stats.oversized_records,
+                "big_tile_records": stats.big_tile_records,
                 "stage_ms": {k: round(v, 3) for k, v in ts.items()}}
 
     # further measured rows (same inputs, device-resident, L2 flushed, CUDA

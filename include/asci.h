@@ -114,16 +114,19 @@ typedef struct {
   uint64_t max_level;  /* deepest constraint level the planner used */
   uint64_t tile_launches;      /* launches of the on-chip tile kernel */
   uint64_t tile_records;       /* staged pairs reduced on chip (16 bytes read each) */
-  uint64_t oversized_records;  /* staged pairs reduced by the global-sort path */
+  uint64_t oversized_records;  /* staged pairs of hash buckets overfilled by hot
+                                  targets: reduced by the large tile kernel (up
+                                  to 4096 records a bucket) or the global sort */
   /* The diagonal H_ii is summed exactly in 64-bit fixed point on the grid
    * 2^-diag_grid_bits: E0, ecore and each integral term of H_ii (h_pp, J - K of
    * a same-spin pair, J of an opposite-spin pair) is rounded once to the grid,
    * so E0 - H_ii carries at most (terms + 2) * 2^-(diag_grid_bits + 1) of
    * rounding before its one conversion to FP64. */
   uint64_t diag_grid_bits;
+  uint64_t big_tile_records;  /* of oversized_records, those reduced on chip */
   /* device milliseconds: prepare, plan, generate (emission into the staging
-     buffer), tiles (the on-chip tile kernel alone), oversized (global-sort
-     path alone), score (tiles + oversized + exact scores + pruning), select,
+     buffer), tiles (the on-chip tile kernel alone), oversized (overfilled
+     buckets alone: the large tile kernel and the global-sort path), score (tiles + oversized + exact scores + pruning), select,
      total */
   double t_stage[8];
 } asci_stats;

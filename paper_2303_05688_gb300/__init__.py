@@ -76,7 +76,7 @@ class _Stats(ct.Structure):
                 ("max_batch", ct.c_uint64), ("ncore", ct.c_uint64), ("max_level", ct.c_uint64),
                 ("tile_launches", ct.c_uint64), ("tile_records", ct.c_uint64),
                 ("oversized_records", ct.c_uint64), ("diag_grid_bits", ct.c_uint64),
-                ("t_stage", ct.c_double * 8)]
+                ("big_tile_records", ct.c_uint64), ("t_stage", ct.c_double * 8)]
 
 
 class _DavOpts(ct.Structure):
@@ -138,6 +138,7 @@ class SearchStats:
     tile_records: int
     oversized_records: int
     diag_grid_bits: int
+    big_tile_records: int
     t_stage_ms: dict
 
     @classmethod
@@ -145,7 +146,7 @@ class SearchStats:
         names = ["prepare", "plan", "generate", "tiles", "oversized", "score", "select", "total"]
         return cls(s.generated, s.surviving, s.unique, s.excluded, s.selected, s.batches,
                    s.max_batch, s.ncore, s.max_level, s.tile_launches, s.tile_records,
-                   s.oversized_records, s.diag_grid_bits,
+                   s.oversized_records, s.diag_grid_bits, s.big_tile_records,
                    {k: s.t_stage[i] for i, k in enumerate(names)})
 
 

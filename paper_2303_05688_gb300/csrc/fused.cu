@@ -1141,23 +1141,42 @@ constexpr uint32_t kPsiBit = 0x80000000u;  // slot holds psi marker (index in lo
 constexpr uint16_t kEndList = 0xffffu;
 constexpr int kPsiCap = 64;                // psi markers per tile; more: global lookups
 
-constexpr int kFilterBits = 8192;           // singleton filter bits per tile
-constexpr int kFilterWords = kFilterBits / 32;
+// The tile kernel comes in two sizes: tiles of kCap records (every packed,
+// medium and bucket tile) and tiles of kBigCap records for the hash buckets
+// that hot targets overfilled (bucket tiles only, one CTA per SM).  Per
+// record: two hash slots and eight filter bits.
+constexpr int kBigCap = 4096;
+constexpr int kBigThreads = 1024;
 
+template <int CAP>
+constexpr int log2_of() {
+  int b = 0;
+  while ((1 << b) < CAP) ++b;
+  return b;
+}
+
+template <int CAP, bool PACKED>
 struct CellSmem {
-  StageRec rec[2][kCap];     // records (double-buffered by tile)
+  static constexpr int kRecs = CAP;
+  static constexpr int kTab = 2 * CAP;           // hash slots (load <= 1/2)
+  static constexpr int kFilterWords = CAP / 4;   // 8 CAP filter bits
+  static constexpr int kFilterShift = 32 - (log2_of<CAP>() + 3);  // top bits pick a filter bit
+  StageRec rec[2][CAP];      // records (double-buffered by tile)
   uint32_t seen[kFilterWords];  // filter bits of the tile's keys (records and psi entries)
   uint32_t dup[kFilterWords];   // filter bits met twice or more
-  uint32_t alpha[2][kCap];   // record target alpha strings (packed tiles)
+  uint32_t alpha[2][PACKED ? CAP : 1];  // record target alpha strings (packed tiles)
   uint64_t psik[2][kPsiCap]; // psi keys of the tile
-  uint32_t slot[kSlots];     // newest record of the slot's target, a psi marker, or empty
-  uint32_t psibit[2][kSlots / 32];  // slots whose key is in psi
-  uint16_t next[kCap];       // previous record of the same target, or kEndList
-  uint16_t targets[kCap];    // slots claimed by records, in order of claiming
+  uint32_t slot[kTab];       // newest record of the slot's target, a psi marker, or empty
+  uint32_t psibit[2][kTab / 32];  // slots whose key is in psi
+  uint16_t next[CAP];        // previous record of the same target, or kEndList
+  uint16_t targets[CAP];     // slots claimed by records, in order of claiming
   uint16_t psi_slot[kPsiCap];  // slot claimed by each psi marker, or kEndList
   uint32_t ntargets[2];      // by tile parity
+  static_assert(CAP < 0xffff && kTab <= 0xffff, "indices must fit 16 bits");
+  static_assert((1 << log2_of<CAP>()) == CAP, "capacity must be a power of two");
 };
-static_assert(kCap < 0xffff && kSlots <= 0xffff, "indices must fit 16 bits");
+using TileSmem = CellSmem<kCap, true>;
+using BigTileSmem = CellSmem<kBigCap, false>;
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -1180,9 +1199,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // A tile that the kernel reduces on chip; oversized hash buckets go to the
 // global path, anything else outside the limits is a planning bug.
+template <int CAP>
 __device__ __forceinline__ bool tile_on_chip(const TileDesc &d, uint64_t stage_cap,
                                              unsigned *err) {
-  const bool fits = d.npairs <= (uint32_t)kCap && (uint64_t)d.start + d.npairs <= stage_cap;
+  const bool fits = d.npairs <= (uint32_t)CAP && (uint64_t)d.start + d.npairs <= stage_cap;
   if (!fits && threadIdx.x == 0 &&
       !(d.kind == kTileBucket && d.npairs > (uint32_t)kCap &&
         (uint64_t)d.start + kCap <= stage_cap))
@@ -1190,26 +1210,29 @@ __device__ __forceinline__ bool tile_on_chip(const TileDesc &d, uint64_t stage_c
   return fits;
 }
 
-__device__ __forceinline__ void prefetch_tile(CellSmem &S, int buf, const TileDesc &d,
-                                              const CellArgs &C) {
-  for (uint32_t e = threadIdx.x; e < d.npairs; e += kCellThreads) {
+template <int CAP, bool PACKED>
+__device__ __forceinline__ void prefetch_tile(CellSmem<CAP, PACKED> &S, int buf,
+                                              const TileDesc &d, const CellArgs &C) {
+  for (uint32_t e = threadIdx.x; e < d.npairs; e += blockDim.x) {
     cp_async16(&S.rec[buf][e], C.st.rec + d.start + e);
-    if (d.kind == kTilePacked) cp_async4(&S.alpha[buf][e], C.st.alpha + d.start + e);
+    if (PACKED && d.kind == kTilePacked) cp_async4(&S.alpha[buf][e], C.st.alpha + d.start + e);
   }
   const uint32_t np = d.psi_hi - d.psi_lo;
   if (np <= (uint32_t)kPsiCap)
-    for (uint32_t q = threadIdx.x; q < np; q += kCellThreads)
+    for (uint32_t q = threadIdx.x; q < np; q += blockDim.x)
       cp_async8(&S.psik[buf][q], C.psi_list + d.psi_lo + q);
   cp_async_commit();
 }
 
 // Target key of record e (bucket and medium tiles share one alpha string).
-__device__ __forceinline__ uint64_t rec_key(const CellSmem &S, int buf, uint32_t e, bool packed,
-                                            uint32_t alpha) {
-  return pack_key(packed ? S.alpha[buf][e] : alpha, S.rec[buf][e].beta);
+template <int CAP, bool PACKED>
+__device__ __forceinline__ uint64_t rec_key(const CellSmem<CAP, PACKED> &S, int buf, uint32_t e,
+                                            bool packed, uint32_t alpha) {
+  return pack_key(PACKED && packed ? S.alpha[buf][PACKED ? e : 0] : alpha, S.rec[buf][e].beta);
 }
-__device__ __forceinline__ uint64_t slot_key(const CellSmem &S, int buf, uint32_t v, bool packed,
-                                             uint32_t alpha) {
+template <int CAP, bool PACKED>
+__device__ __forceinline__ uint64_t slot_key(const CellSmem<CAP, PACKED> &S, int buf, uint32_t v,
+                                             bool packed, uint32_t alpha) {
   return (v & kPsiBit) ? S.psik[buf][v & ~kPsiBit] : rec_key(S, buf, v, packed, alpha);
 }
 
@@ -1227,24 +1250,28 @@ __device__ __forceinline__ float abs_bound(double v) {
 // for any order.  The first walk also sums |v| in float.  |num| <= sum |v|, so
 // a target whose bound cannot reach the running threshold tau |E0 - H_ii|
 // fails the screen whatever its exact numerator: *reach is cleared and the
-// exact sum is skipped.  The test is conservative: a list holds at most kCap =
-// 1024 values, so the float sum lies within 1023 * 2^-24 < 6.1e-5 below the
-// exact sum of the (truncated, hence smaller) terms, which the factor 1.0001
+// exact sum is skipped.  The test is conservative: a list holds at most kBigCap
+// = 4096 values, so the float sum lies within 4095 * 2^-24 < 2.45e-4 below the
+// exact sum of the (truncated, hence smaller) terms, which the factor 1.0003
 // covers; tau_f is rounded down and den truncated, and the 0.99999 margin
 // covers the float product.  Kept out of line: rare, and it would weigh on
 // the common path's registers.
 __device__ __noinline__ double long_numerator(const StageRec *r, const uint16_t *next,
-                                              uint32_t e, float tau_f, float den, bool *reach,
-                                              unsigned *err) {
-  int emax = 1;
+                                              uint32_t e, float tau_f, float den, int walk_max,
+                                              bool *reach, bool *deferred, unsigned *err) {
+  int emax = 1, len = 0;
   float sabs = 0.0f;
   for (uint32_t i = e; i != kEndList; i = next[i]) {
+    if (++len > walk_max) {  // a hot target: its warp sums it (warp_numerator)
+      *deferred = true;
+      return 0.0;
+    }
     const int ex = fx_exponent(r[i].v);
     emax = ex > emax ? ex : emax;
     sabs += abs_bound(r[i].v);
   }
   const float df = fabsf(den);
-  if (tau_f > 0.0f && df != 0.0f && !(sabs * 1.0001f >= tau_f * df * 0.99999f)) {
+  if (tau_f > 0.0f && df != 0.0f && !(sabs * 1.0003f >= tau_f * df * 0.99999f)) {
     *reach = false;
     return 0.0;
   }
@@ -1259,11 +1286,67 @@ __device__ __noinline__ double long_numerator(const StageRec *r, const uint16_t 
   return fx128_to_double(acc, frac);
 }
 
+// The numerator of a target with more than CAP / 32 records (a hot target),
+// formed by the whole warp: the lanes scan the tile's records for the key and
+// sum the matching values in the same 128-bit fixed-point accumulator as
+// long_numerator, then combine their partial sums (integer addition, so the
+// result is the same bit for bit); the float bound of sum |v| is formed the
+// same way, in another order, within the same error bound.  The records of
+// the target are exactly those with its key: a key met twice or more has no
+// singleton record, and screened-out records were never linked.
+template <int CAP, bool PACKED>
+__device__ __noinline__ double warp_numerator(const CellSmem<CAP, PACKED> &S, int buf, int nrec,
+                                              bool packed, uint32_t alpha, bool screened,
+                                              uint64_t key, float tau_f, float den, bool *reach,
+                                              unsigned *err) {
+  const int lane = (int)(threadIdx.x & 31u);
+  const StageRec *r = S.rec[buf];
+  int emax = 1;
+  float sabs = 0.0f;
+  for (int i = lane; i < nrec; i += 32)
+    if (rec_key(S, buf, (uint32_t)i, packed, alpha) == key && !(screened && is_dropped(r[i].v))) {
+      const int ex = fx_exponent(r[i].v);
+      emax = ex > emax ? ex : emax;
+      sabs += abs_bound(r[i].v);
+    }
+  for (int o = 16; o; o >>= 1) {
+    const int em = __shfl_xor_sync(0xffffffffu, emax, o);
+    emax = em > emax ? em : emax;
+    sabs += __shfl_xor_sync(0xffffffffu, sabs, o);
+  }
+  const float df = fabsf(den);
+  if (tau_f > 0.0f && df != 0.0f && !(sabs * 1.0003f >= tau_f * df * 0.99999f)) {
+    *reach = false;
+    return 0.0;
+  }
+  const int frac = fx128_frac_for(emax);
+  Fx128 acc = {0, 0};
+  unsigned ovf = 0;
+  for (int i = lane; i < nrec; i += 32)
+    if (rec_key(S, buf, (uint32_t)i, packed, alpha) == key && !(screened && is_dropped(r[i].v))) {
+      Fx128 x = fx128_from_double(r[i].v, frac, &ovf);
+      fx128_add(acc, x);
+    }
+  for (int o = 16; o; o >>= 1) {
+    Fx128 t;
+    t.lo = __shfl_xor_sync(0xffffffffu, acc.lo, o);
+    t.hi = __shfl_xor_sync(0xffffffffu, acc.hi, o);
+    fx128_add(acc, t);
+    ovf |= __shfl_xor_sync(0xffffffffu, ovf, o);
+  }
+  if (ovf && lane == 0) atomicOr(err, kErrAccum);
+  *reach = true;
+  return fx128_to_double(acc, frac);
+}
+
 // Exact numerator over the record list starting at e (values of screened-out
 // records are never inserted); *reach is cleared when a list of five or more
-// cannot reach the threshold (its sum is then not formed).
-__device__ __forceinline__ double list_numerator(const CellSmem &S, int buf, uint32_t e,
-                                                 float tau_f, bool *reach, unsigned *err) {
+// cannot reach the threshold (its sum is then not formed), and *deferred is
+// set for a list longer than walk_max (left to warp_numerator).
+template <int CAP, bool PACKED>
+__device__ __forceinline__ double list_numerator(const CellSmem<CAP, PACKED> &S, int buf, uint32_t e,
+                                                 float tau_f, int walk_max, bool *reach,
+                                                 bool *deferred, unsigned *err) {
   const StageRec *r = S.rec[buf];
   const uint32_t e2 = S.next[e];
   if (e2 == kEndList) return r[e].v;
@@ -1275,18 +1358,26 @@ __device__ __forceinline__ double list_numerator(const CellSmem &S, int buf, uin
   const uint32_t e4 = S.next[e3];
   if (e4 == kEndList) return sum4_ordered(0.0, r[e].v, r[e2].v, r[e3].v);
   if (S.next[e4] == kEndList) return sum4_ordered(r[e].v, r[e2].v, r[e3].v, r[e4].v);
-  return long_numerator(r, S.next, e, tau_f, r[e].den, reach, err);
+  return long_numerator(r, S.next, e, tau_f, r[e].den, walk_max, reach, deferred, err);
 }
 
-__global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
+template <int CAP, int THREADS, bool PACKED>
+__global__ void __launch_bounds__(THREADS) k_cells(CellArgs C) {
+  using Smem = CellSmem<CAP, PACKED>;
+  constexpr int kTab = Smem::kTab;
+  constexpr int kRPT = CAP / THREADS;  // records per thread
+  // hot targets (lists longer than CAP / 32) are summed by their warp in the
+  // large tiles; in kCap tiles one thread walks every list
+  constexpr bool kHotWarp = CAP > kCap;
+  static_assert(CAP % THREADS == 0 && kRPT <= 32, "records per thread");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CellSmem &S = *reinterpret_cast<CellSmem *>(smem_raw);
+  Smem &S = *reinterpret_cast<Smem *>(smem_raw);
   const int lane = threadIdx.x & 31;
   const int warp_base = (int)(threadIdx.x & ~31u);
   unsigned long long my_unique = 0, my_excl = 0;
-  for (int i = threadIdx.x; i < kSlots; i += kCellThreads) S.slot[i] = kEmptySlot;
-  for (int i = threadIdx.x; i < kSlots / 32; i += kCellThreads) S.psibit[0][i] = S.psibit[1][i] = 0u;
-  for (int i = threadIdx.x; i < kFilterWords; i += kCellThreads) S.seen[i] = S.dup[i] = 0u;
+  for (int i = threadIdx.x; i < kTab; i += THREADS) S.slot[i] = kEmptySlot;
+  for (int i = threadIdx.x; i < kTab / 32; i += THREADS) S.psibit[0][i] = S.psibit[1][i] = 0u;
+  for (int i = threadIdx.x; i < Smem::kFilterWords; i += THREADS) S.seen[i] = S.dup[i] = 0u;
   if (threadIdx.x == 0) S.ntargets[0] = S.ntargets[1] = 0;
   // tiles blockIdx.x + k * gridDim.x; descriptors are read one tile ahead of
   // the record copies, which run one tile ahead of the reduction
@@ -1295,7 +1386,7 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
   bool on = false, on_n = false;
   if (tile < C.ntiles) {
     d = C.tiles[tile];
-    on = tile_on_chip(d, C.st.cap, C.err);
+    on = tile_on_chip<CAP>(d, C.st.cap, C.err);
     if (on) prefetch_tile(S, 0, d, C);
   }
   if (tile + gridDim.x < C.ntiles) dn = C.tiles[tile + gridDim.x];
@@ -1307,27 +1398,47 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
     cp_async_wait_all();
     __syncthreads();  // records of this tile in place; the previous tile is done
     if (tile + gridDim.x < C.ntiles) {
-      on_n = tile_on_chip(dn, C.st.cap, C.err);
+      on_n = tile_on_chip<CAP>(dn, C.st.cap, C.err);
       if (on_n) prefetch_tile(S, buf ^ 1, dn, C);
     } else {
       on_n = false;
     }
     // psi bits of the previous tile are read by no one until the next barrier
-    for (int i = threadIdx.x; i < kSlots / 32; i += kCellThreads) S.psibit[buf ^ 1][i] = 0u;
+    for (int i = threadIdx.x; i < kTab / 32; i += THREADS) S.psibit[buf ^ 1][i] = 0u;
     const uint32_t npsi = d.psi_hi - d.psi_lo;
     const bool psi_local = npsi <= (uint32_t)kPsiCap;
-    const bool packed = d.kind == kTilePacked;
+    const bool packed = PACKED && d.kind == kTilePacked;
     const int nrec = on ? (int)d.npairs : 0;
-    // singleton filter: every key sets its bit; a bit met twice is marked
-    for (int e = threadIdx.x; e < nrec; e += kCellThreads)
-      if (!(C.screened && is_dropped(S.rec[buf][e].v))) {
-        const uint32_t f = tile_mix(rec_key(S, buf, (uint32_t)e, packed, d.alpha)) >> 19;
-        const uint32_t bit = 1u << (f & 31u);
-        if (atomicOr(&S.seen[f >> 5], bit) & bit) atomicOr(&S.dup[f >> 5], bit);
+    // singleton filter: every key sets its bit; a bit met twice is marked.
+    // Thread t holds records t + k THREADS (k < kRPT); their hashes stay in
+    // registers for the insert phase, and the filter atomics of all of them
+    // are issued before any result is used.
+    uint32_t fm[kRPT], old[kRPT];
+    uint32_t live = 0;
+#pragma unroll
+    for (int k = 0; k < kRPT; ++k) {
+      const int e = (int)threadIdx.x + k * THREADS;
+      fm[k] = 0u;
+      old[k] = 0u;
+      if (e < nrec && !(C.screened && is_dropped(S.rec[buf][e].v))) {
+        live |= 1u << k;
+        fm[k] = tile_mix(rec_key(S, buf, (uint32_t)e, packed, d.alpha));
       }
+    }
+#pragma unroll
+    for (int k = 0; k < kRPT; ++k)
+      if ((live >> k) & 1u) {
+        const uint32_t f = fm[k] >> Smem::kFilterShift;
+        old[k] = atomicOr(&S.seen[f >> 5], 1u << (f & 31u));
+      }
+#pragma unroll
+    for (int k = 0; k < kRPT; ++k) {
+      const uint32_t f = fm[k] >> Smem::kFilterShift, bit = 1u << (f & 31u);
+      if (((live >> k) & 1u) && (old[k] & bit)) atomicOr(&S.dup[f >> 5], bit);
+    }
     if (on && psi_local)
-      for (uint32_t q = threadIdx.x; q < npsi; q += kCellThreads) {
-        const uint32_t f = tile_mix(S.psik[buf][q]) >> 19;
+      for (uint32_t q = threadIdx.x; q < npsi; q += THREADS) {
+        const uint32_t f = tile_mix(S.psik[buf][q]) >> Smem::kFilterShift;
         const uint32_t bit = 1u << (f & 31u);
         if (atomicOr(&S.seen[f >> 5], bit) & bit) atomicOr(&S.dup[f >> 5], bit);
       }
@@ -1335,17 +1446,17 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
     if (on && psi_local) {
       // psi markers: claim a slot, or flag the slot a record already holds
       // (a marker whose filter bit is unmarked meets no record: left out)
-      for (uint32_t q = threadIdx.x; q < npsi; q += kCellThreads) {
+      for (uint32_t q = threadIdx.x; q < npsi; q += THREADS) {
         const uint64_t key = S.psik[buf][q];
-        const uint32_t mix = tile_mix(key), f = mix >> 19;
+        const uint32_t mix = tile_mix(key), f = mix >> Smem::kFilterShift;
         if (!((S.dup[f >> 5] >> (f & 31u)) & 1u)) {
           S.psi_slot[q] = kEndList;
           continue;
         }
-        uint32_t h = mix & (uint32_t)(kSlots - 1);
+        uint32_t h = mix & (uint32_t)(kTab - 1);
         uint16_t claimed = kEndList;
         int probe = 0;
-        for (; probe < kSlots; ++probe) {
+        for (; probe < kTab; ++probe) {
           uint32_t cur = S.slot[h];
           if (cur == kEmptySlot) {
             cur = atomicCAS(&S.slot[h], kEmptySlot, kPsiBit | q);
@@ -1355,9 +1466,9 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
             }
           }
           if (slot_key(S, buf, cur, packed, d.alpha) == key) break;
-          h = (h + 1) & (kSlots - 1);
+          h = (h + 1) & (kTab - 1);
         }
-        if (probe == kSlots) atomicOr(C.err, kErrTile);  // cannot happen at load < 3/4
+        if (probe == kTab) atomicOr(C.err, kErrTile);  // cannot happen at load < 3/4
         else atomicOr(&S.psibit[buf][h >> 5], 1u << (h & 31));
         S.psi_slot[q] = claimed;
       }
@@ -1366,16 +1477,19 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
       // singletons are scored and appended at once; every other record is
       // linked into its target's list (warps append the slots they claim to
       // the target list with one shared atomic per round)
-#pragma unroll 1
-      for (int base = 0; base + warp_base < nrec; base += kCellThreads) {
+#pragma unroll
+      for (int k = 0; k < kRPT; ++k) {
+        const int base = k * THREADS;
+        if (base + warp_base >= nrec) break;
         const int e = base + (int)threadIdx.x;
         int claimed = -1;
         bool single = false, pass1 = false;
         uint64_t key = 0;
         double v1 = 0.0;
-        if (e < nrec && !(C.screened && is_dropped(S.rec[buf][e].v))) {
+        const uint32_t mix = fm[k];
+        if ((live >> k) & 1u) {
           key = rec_key(S, buf, (uint32_t)e, packed, d.alpha);
-          const uint32_t mix = tile_mix(key), f = mix >> 19;
+          const uint32_t f = mix >> Smem::kFilterShift;
           single = !((S.dup[f >> 5] >> (f & 31u)) & 1u);
           if (single) {
             ++my_unique;
@@ -1409,10 +1523,10 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
             }
           }
         }
-        if (e < nrec && !single && !(C.screened && is_dropped(S.rec[buf][e].v))) {
-          uint32_t h = tile_mix(key) & (uint32_t)(kSlots - 1);
+        if (((live >> k) & 1u) && !single) {
+          uint32_t h = mix & (uint32_t)(kTab - 1);
           int probe = 0;
-          for (; probe < kSlots; ++probe) {
+          for (; probe < kTab; ++probe) {
             uint32_t cur = S.slot[h];
             if (cur == kEmptySlot) {
               cur = atomicCAS(&S.slot[h], kEmptySlot, (uint32_t)e);
@@ -1432,9 +1546,9 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
               }
               break;
             }
-            h = (h + 1) & (kSlots - 1);
+            h = (h + 1) & (kTab - 1);
           }
-          if (probe == kSlots) atomicOr(C.err, kErrTile);  // cannot happen at load < 3/4
+          if (probe == kTab) atomicOr(C.err, kErrTile);  // cannot happen at load < 3/4
         }
         const unsigned bal = __ballot_sync(0xffffffffu, claimed >= 0);
         if (bal) {
@@ -1448,11 +1562,11 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
     __syncthreads();  // lists complete
     if (threadIdx.x == 0) S.ntargets[buf ^ 1] = 0;  // read by no one until the next barrier
     // the filters are read by no one until the next tile's filter phase
-    for (int i = threadIdx.x; i < kFilterWords; i += kCellThreads) S.seen[i] = S.dup[i] = 0u;
+    for (int i = threadIdx.x; i < Smem::kFilterWords; i += THREADS) S.seen[i] = S.dup[i] = 0u;
     if (on) {
       // markers that no record joined are emptied by their inserting thread
       if (psi_local)
-        for (uint32_t q = threadIdx.x; q < npsi; q += kCellThreads) {
+        for (uint32_t q = threadIdx.x; q < npsi; q += THREADS) {
           const uint32_t h = S.psi_slot[q];
           if (h != kEndList) {
             const uint32_t v = S.slot[h];
@@ -1462,11 +1576,13 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
       // one target per thread: numerator, exclusion, threshold; the slot is
       // emptied by its owner for the next tile
       const int ntg = (int)S.ntargets[buf];
+      const float tau_f = C.tau > 0.0 ? C.tau_f : 0.0f;
 #pragma unroll 1
-      for (int base = 0; base + warp_base < ntg; base += kCellThreads) {
+      for (int base = 0; base + warp_base < ntg; base += THREADS) {
         const int idx = base + (int)threadIdx.x;
-        bool pass = false;
-        double sc = 0.0;
+        bool live = false, deferred = false, reach = true;
+        double num = 0.0;
+        float den = 0.0f;
         uint64_t key = 0;
         if (idx < ntg) {
           const uint32_t h = S.targets[idx];
@@ -1479,19 +1595,36 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(CellArgs C) {
           if (in_psi) {
             ++my_excl;
           } else {
-            bool reach = true;
-            const double num = list_numerator(S, buf, e, C.tau > 0.0 ? C.tau_f : 0.0f, &reach,
-                                              C.err);
-            pass = reach;
-            if (reach && C.tau > 0.0) {
-              bool okn;
-              const float nf = abs_as_float(num, &okn);
-              const float df = fabsf(S.rec[buf][e].den);
-              if (okn && df != 0.0f) pass = nf >= C.tau_f * df * 0.99999f;  // else the exact test decides
-            }
-            sc = num;  // the exact score is formed after the launch (k_exact_scores)
+            live = true;
+            den = S.rec[buf][e].den;
+            num = list_numerator(S, buf, e, tau_f, kHotWarp ? CAP / 32 : CAP, &reach, &deferred,
+                                 C.err);
           }
         }
+        // hot targets: each summed by the whole warp
+        if (kHotWarp)
+        for (unsigned m = __ballot_sync(0xffffffffu, deferred); m; m &= m - 1) {
+          const int src = __ffs(m) - 1;
+          bool r2 = true;
+          const double n2 = warp_numerator(S, buf, nrec, packed, d.alpha, C.screened != 0,
+                                           __shfl_sync(0xffffffffu, key, src), tau_f,
+                                           __shfl_sync(0xffffffffu, den, src), &r2, C.err);
+          if (lane == src) {
+            num = n2;
+            reach = r2;
+          }
+        }
+        bool pass = false;
+        if (live) {
+          pass = reach;
+          if (reach && C.tau > 0.0) {
+            bool okn;
+            const float nf = abs_as_float(num, &okn);
+            const float df = fabsf(den);
+            if (okn && df != 0.0f) pass = nf >= C.tau_f * df * 0.99999f;  // else the exact test decides
+          }
+        }
+        const double sc = num;  // the exact score is formed after the launch (k_exact_scores)
         const unsigned bal = __ballot_sync(0xffffffffu, pass);
         if (bal) {
           unsigned long long b0 = 0;
@@ -1576,6 +1709,29 @@ __global__ void k_big_gather(const StageRec *rec, const StageRec *spill,
     keys[i] = ((uint64_t)lo << 32) | big_rec(rec, spill, sr).beta;
     idx[i] = (uint32_t)i;
     src[i] = sr;
+  }
+}
+
+// One CTA per oversized bucket tile of at most kBigCap records: its in-place
+// records and its spilled ones (info row: start, in-place count, alpha, first
+// entry of the tile-ordered spill list, spilled count) are copied into one
+// range of a scratch staging buffer, and its descriptor is rewritten to point
+// there (kind, alpha and psi range unchanged).
+__global__ void k_big_tile_gather(const TileDesc *tiles, const uint32_t *list,
+                                  const uint32_t *info, const uint32_t *off,
+                                  const StageRec *rec, const StageRec *spill_rec,
+                                  const uint64_t *spill_keys, StageRec *out, TileDesc *out_desc) {
+  const uint32_t i = blockIdx.x;
+  const uint32_t *r = info + 5 * (size_t)i;
+  const uint32_t start = r[0], nin = r[1], slo = r[3], nsp = r[4], o = off[i];
+  for (uint32_t e = threadIdx.x; e < nin; e += blockDim.x) out[o + e] = rec[start + e];
+  for (uint32_t e = threadIdx.x; e < nsp; e += blockDim.x)
+    out[o + nin + e] = spill_rec[(uint32_t)spill_keys[slo + e]];
+  if (threadIdx.x == 0) {
+    TileDesc d = tiles[list[i]];
+    d.start = o;
+    d.npairs = nin + nsp;
+    out_desc[i] = d;
   }
 }
 
@@ -2228,6 +2384,7 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
 }
 
 size_t tile_capacity() { return (size_t)kCap; }
+size_t big_tile_capacity() { return (size_t)kBigCap; }
 
 static CellArgs cell_args(const FusedCore &F, const Stage &st,
                           double tau, uint64_t *cand_key, double *cand_score,
@@ -2272,13 +2429,14 @@ int fused_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
   CA.psi_list = psi_list;
   CA.tile0 = tile_begin;
   CA.ntiles = tile_end;
-  const size_t cell_smem = sizeof(CellSmem);
+  const size_t cell_smem = sizeof(TileSmem);
   // once (thread-safe static initialisation): attribute and occupancy
   static const int per_sm = [cell_smem]() {
     int p = 0;
-    if (cudaFuncSetAttribute(k_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_cells<kCap, kCellThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)cell_smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k_cells, kCellThreads, cell_smem) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &p, k_cells<kCap, kCellThreads, true>, kCellThreads, cell_smem) !=
             cudaSuccess)
       return 0;
     return p < 1 ? 1 : p;
@@ -2293,7 +2451,7 @@ int fused_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
   const int per = (F.ctas_per_sm > 0 && F.ctas_per_sm < per_sm) ? F.ctas_per_sm : per_sm;
   const unsigned grid = (unsigned)std::min<size_t>((size_t)sms * per, tile_end - tile_begin);
   ASCI_TRACE("cells: launch grid=%u smem=%zu per_sm=%d", grid, cell_smem, per_sm);
-  k_cells<<<grid, kCellThreads, cell_smem, s>>>(CA);
+  k_cells<kCap, kCellThreads, true><<<grid, kCellThreads, cell_smem, s>>>(CA);
   ASCI_CHECK_LAUNCH();
   return ASCI_OK;
 }
@@ -2315,6 +2473,68 @@ int tile_info(const void *tiles, const std::vector<uint32_t> &list, const Spill 
   ASCI_CHECK_LAUNCH();
   ASCI_TRY_CUDA(cudaMemcpyAsync(info->data(), d_info, 5 * n * 4, cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  return ASCI_OK;
+}
+
+// Reduce oversized bucket tiles of at most kBigCap records on chip: list[i]
+// is a tile of the batch and info[5i..5i+4] its row from tile_info.  Appends
+// at most as many candidates as there are records (*nrec_out).
+int fused_big_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
+                    const uint32_t *list, const uint32_t *info, size_t nt, const Stage &st,
+                    const Spill &spill, double tau, uint64_t *cand_key, double *cand_score,
+                    unsigned long long *cand_count, unsigned long long cand_cap,
+                    unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
+                    uint64_t *nrec_out, Arena &arena) {
+  cudaStream_t s = arena.stream();
+  *nrec_out = 0;
+  if (!nt) return ASCI_OK;
+  std::vector<uint32_t> off(nt);
+  uint64_t total = 0;
+  for (size_t i = 0; i < nt; ++i) {
+    const uint32_t *r = info + 5 * i;
+    const uint64_t nrec = (uint64_t)r[1] + r[4];
+    if (nrec > (uint64_t)kBigCap || (uint64_t)r[0] + r[1] > st.cap ||
+        (uint64_t)r[3] + r[4] > spill.n)
+      return ASCI_ECUDA;
+    off[i] = (uint32_t)total;
+    total += nrec;
+  }
+  if (total >= (1ull << 32)) return ASCI_ENOMEM;
+  *nrec_out = total;
+  Arena ta(s);
+  uint32_t *d_list, *d_info, *d_off;
+  StageRec *big;
+  TileDesc *desc;
+  ASCI_TRY(ta.alloc(&d_list, nt));
+  ASCI_TRY(ta.alloc(&d_info, 5 * nt));
+  ASCI_TRY(ta.alloc(&d_off, nt));
+  ASCI_TRY(ta.alloc(&big, total));
+  ASCI_TRY(ta.alloc(&desc, nt));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(d_list, list, nt * 4, cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(d_info, info, 5 * nt * 4, cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(d_off, off.data(), nt * 4, cudaMemcpyDefault, s));
+  k_big_tile_gather<<<(unsigned)nt, 256, 0, s>>>(static_cast<const TileDesc *>(tiles), d_list,
+                                                 d_info, d_off, st.rec, spill.rec, spill.keys,
+                                                 big, desc);
+  ASCI_CHECK_LAUNCH();
+  CellArgs CA = cell_args(F, Stage{big, nullptr, total}, tau, cand_key, cand_score, cand_count,
+                          cand_cap, n_unique, n_excluded, err);
+  CA.tiles = desc;
+  CA.psi_list = psi_list;
+  CA.tile0 = 0;
+  CA.ntiles = (uint32_t)nt;
+  const size_t smem = sizeof(BigTileSmem);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      k_cells<kBigCap, kBigThreads, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)smem);
+  ASCI_TRY_CUDA(attr);
+  int dev = 0, sms = 152;
+  ASCI_TRY_CUDA(cudaGetDevice(&dev));
+  ASCI_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid = (unsigned)std::min<size_t>((size_t)sms, nt);
+  k_cells<kBigCap, kBigThreads, false><<<grid, kBigThreads, smem, s>>>(CA);
+  ASCI_CHECK_LAUNCH();
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));  // the host vector above is read by a copy
   return ASCI_OK;
 }
 

@@ -56,6 +56,12 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
                 Spill *spill_out, std::vector<uint32_t> *oversized, Arena &arena);
 int tile_info(const void *tiles, const std::vector<uint32_t> &list, const Spill &spill,
               std::vector<uint32_t> *info, cudaStream_t s);
+int fused_big_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
+                    const uint32_t *list, const uint32_t *info, size_t nt, const Stage &st,
+                    const Spill &spill, double tau, uint64_t *cand_key, double *cand_score,
+                    unsigned long long *cand_count, unsigned long long cand_cap,
+                    unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
+                    uint64_t *nrec_out, Arena &arena);
 int fused_big_tiles(const FusedCore &F, const uint32_t *info, size_t nt, const Stage &st,
                     const Spill &spill, double tau,
                     uint64_t *cand_key, double *cand_score, unsigned long long *cand_count,
@@ -69,6 +75,7 @@ int fused_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
                 unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
                 Arena &arena);
 size_t tile_capacity();
+size_t big_tile_capacity();
 int exact_scores(const FusedCore &F, const uint64_t *key, double *score, size_t n,
                  cudaStream_t s);
 int abs_min(const double *s, size_t n, double *host_min, Arena &arena);
@@ -571,7 +578,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
                        ClassQuery *cq = nullptr) {
   Arena arena(stream);
   double tl[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per-stage device milliseconds
-  uint64_t tile_launches = 0, staged_records = 0, oversized_records = 0;
+  uint64_t tile_launches = 0, staged_records = 0, oversized_records = 0, big_records = 0;
   StageTimer tm(stream), total_tm(stream), ktm(stream);
   total_tm.start();
   tm.start();
@@ -969,48 +976,69 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
         tm.start();
       }
     }
-    // buckets too large for one tile: global sorts over as many of them as
-    // the free candidate capacity allows (every record may become one)
+    // buckets too large for one tile: those of at most big_tile_capacity()
+    // records on chip in the large tile kernel, the rest by global sorts; each
+    // launch takes as many of them as the free candidate capacity allows
+    // (every record may become one)
     if (!oversized.empty()) {
       std::vector<uint32_t> info;  // 5 words per oversized tile
       ASCI_TRY(tile_info(tiles, oversized, spill, &info, stream));
-      auto recs = [&](size_t k) { return (uint64_t)info[5 * k + 1] + info[5 * k + 4]; };
-      size_t i = 0;
-      while (i < oversized.size()) {
-        if ((uint64_t)(pool_cap - pool_n) < recs(i)) {
-          tm.stop(&tl[5]);
-          tm.start();
-          ASCI_TRY(prune(ba));
-          tm.stop(&tl[6]);
-          tm.start();
-          if ((uint64_t)(pool_cap - pool_n) < recs(i)) return ASCI_ENOMEM;
+      std::vector<uint32_t> big_list, big_info, glob_info;
+      for (size_t k = 0; k < oversized.size(); ++k) {
+        const bool on_chip = (uint64_t)info[5 * k + 1] + info[5 * k + 4] <= big_tile_capacity();
+        if (on_chip) big_list.push_back(oversized[k]);
+        auto &dst = on_chip ? big_info : glob_info;
+        dst.insert(dst.end(), info.begin() + 5 * k, info.begin() + 5 * k + 5);
+      }
+      ASCI_TRACE("oversized buckets: %zu on chip, %zu by global sort", big_info.size() / 5,
+                 glob_info.size() / 5);
+      for (int pass = 0; pass < 2; ++pass) {
+        const std::vector<uint32_t> &inf = pass == 0 ? big_info : glob_info;
+        const size_t cnt = inf.size() / 5;
+        auto recs = [&](size_t k) { return (uint64_t)inf[5 * k + 1] + inf[5 * k + 4]; };
+        size_t i = 0;
+        while (i < cnt) {
+          if ((uint64_t)(pool_cap - pool_n) < recs(i)) {
+            tm.stop(&tl[5]);
+            tm.start();
+            ASCI_TRY(prune(ba));
+            tm.stop(&tl[6]);
+            tm.start();
+            if ((uint64_t)(pool_cap - pool_n) < recs(i)) return ASCI_ENOMEM;
+          }
+          uint64_t room = pool_cap - pool_n, total = 0;
+          size_t j = i;
+          while (j < cnt && total + recs(j) <= room) total += recs(j++);
+          uint64_t nrec = 0;
+          ktm.start();
+          if (pass == 0)
+            ASCI_TRY(fused_big_cells(F, tiles, psi_list, big_list.data() + i, inf.data() + 5 * i,
+                                     j - i, stg, spill, tau, pool_k[pcur], pool_s[pcur], dcount,
+                                     pool_cap, dcount + 1, dcount + 2, derr2, &nrec, ba));
+          else
+            ASCI_TRY(fused_big_tiles(F, inf.data() + 5 * i, j - i, stg, spill, tau, pool_k[pcur],
+                                     pool_s[pcur], dcount, pool_cap, dcount + 1, dcount + 2,
+                                     derr2, &nrec, ba));
+          ktm.stop(&tl[4]);
+          oversized_records += nrec;
+          if (pass == 0) big_records += nrec;
+          unsigned long long c = 0;
+          unsigned he = 0;
+          ASCI_TRY_CUDA(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDefault, stream));
+          ASCI_TRY_CUDA(cudaMemcpyAsync(&he, derr2, sizeof(he), cudaMemcpyDefault, stream));
+          ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
+          if (he) {
+            char msg[96];
+            snprintf(msg, sizeof(msg), "oversized-tile reduction check failed (flags 0x%x)", he);
+            record_error(msg, __FILE__, __LINE__);
+            return ASCI_ECUDA;
+          }
+          if (c > pool_cap) return ASCI_ECUDA;
+          ASCI_TRY(consume(c));
+          ASCI_TRACE("oversized tiles (%s): [%zu,%zu) %llu records, pool=%zu",
+                     pass == 0 ? "on chip" : "global", i, j, (unsigned long long)nrec, pool_n);
+          i = j;
         }
-        uint64_t room = pool_cap - pool_n, total = 0;
-        size_t j = i;
-        while (j < oversized.size() && total + recs(j) <= room) total += recs(j++);
-        uint64_t nrec = 0;
-        ktm.start();
-        ASCI_TRY(fused_big_tiles(F, info.data() + 5 * i, j - i, stg, spill, tau, pool_k[pcur],
-                                 pool_s[pcur], dcount, pool_cap, dcount + 1, dcount + 2, derr2,
-                                 &nrec, ba));
-        ktm.stop(&tl[4]);
-        oversized_records += nrec;
-        unsigned long long c = 0;
-        unsigned he = 0;
-        ASCI_TRY_CUDA(cudaMemcpyAsync(&c, dcount, sizeof(c), cudaMemcpyDefault, stream));
-        ASCI_TRY_CUDA(cudaMemcpyAsync(&he, derr2, sizeof(he), cudaMemcpyDefault, stream));
-        ASCI_TRY_CUDA(cudaStreamSynchronize(stream));
-        if (he) {
-          char msg[96];
-          snprintf(msg, sizeof(msg), "oversized-tile reduction check failed (flags 0x%x)", he);
-          record_error(msg, __FILE__, __LINE__);
-          return ASCI_ECUDA;
-        }
-        if (c > pool_cap) return ASCI_ECUDA;
-        ASCI_TRY(consume(c));
-        ASCI_TRACE("oversized tiles: [%zu,%zu) %llu records, pool=%zu", i, j,
-                   (unsigned long long)nrec, pool_n);
-        i = j;
       }
     }
     tm.stop(&tl[5]);
@@ -1058,6 +1086,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
       memcpy(st->t_stage, tl, sizeof(tl));
       st->tile_launches = tile_launches;
       st->oversized_records = oversized_records;
+      st->big_tile_records = big_records;
       st->tile_records = staged_records - oversized_records;
     }
     return ASCI_OK;
@@ -1114,6 +1143,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
     memcpy(st->t_stage, tl, sizeof(tl));
     st->tile_launches = tile_launches;
     st->oversized_records = oversized_records;
+    st->big_tile_records = big_records;
     st->tile_records = staged_records - oversized_records;
   }
   return ASCI_OK;

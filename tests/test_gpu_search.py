@@ -440,6 +440,36 @@ def test_search_hot_target_beyond_one_tile(torch_cuda, asci, oracle_mod):
     _check_sampled(oracle_mod, h1, eri, ec, ta, tb, c, E0, C, ga, gb, gs, 24, 2, st.diag_grid_bits)
 
 
+def test_search_hot_target_in_a_large_tile(torch_cuda, asci, oracle_mod):
+    """A hash bucket that a hot target overfills beyond one tile but not beyond
+    the large tile (between 1,024 and 4,096 records) is reduced on chip by the
+    large tile kernel; the whole candidate set matches the oracle.
+
+    psi = 2,500 of the 4,235 single and double excitations of one determinant T
+    (16 orbitals, 5 alpha + 5 beta), all in the core, T outside psi: T collects
+    2,500 contributions.
+    """
+    torch = torch_cuda
+    n, na, nb = 16, 5, 5
+    h1, eri, ec = W.random_molecular(n, 33)
+    T = (0b0000000000011111, 0b0000001111100000)
+    ints = oracle_mod.Ints(h1, eri, ec)
+    ta, tb, hv = oracle_mod.pairs(ints, [T[0]], [T[1]], [1.0])
+    rng = np.random.default_rng(5)
+    pick = np.sort(rng.choice(len(ta), 2500, replace=False))
+    ta, tb, hv = ta[pick], tb[pick], hv[pick]
+    c = 0.01 * np.where(hv >= 0, 1.0, -1.0) * (1.0 + 0.1 * rng.random(len(ta)))
+    E0 = oracle_mod.diag(ints, T) - 30.0
+    C = len(ta)
+    ref = oracle_mod.search(ints, ta, tb, c, E0, C, threads=_oracle_threads())
+    ga, gb, gs, st = _run(asci, torch, ta, tb, c, E0, h1, eri, ec, C, len(ref.a) + 100)
+    assert st.big_tile_records > 0, "no bucket went through the large tile kernel"
+    assert st.oversized_records == st.big_tile_records, "no bucket should need the global sort"
+    compare_candidates(ga, gb, gs, ref, E0, st.diag_grid_bits, label="large tile, hot target")
+    keys = dict(zip(zip(ga.tolist(), gb.tolist()), gs.tolist()))
+    assert (T[0], T[1]) in keys
+
+
 @pytest.mark.parametrize("prec", ["FP32_INT_FP64_ACC", "FP32_INT_COMP_ACC"])
 def test_search_fp32_integrals_against_fp64_oracle(torch_cuda, asci, oracle_mod, prec):
     """The precision variant (FP32-stored two-electron elements, and for the
