@@ -437,6 +437,10 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t beta, uint32_t nb) {
 
 constexpr int kRunThreads = 256;
 constexpr int kRunClaim = 4;   // runs a warp claims at a time
+// A determinant's o = 0 run (its beta singles and doubles, 10,314 pairs at
+// (24e,30o)) is emitted in pieces of at most this many pairs, so that the
+// last runs of a launch are short and its warps finish together.
+constexpr uint32_t kPiecePairs = 1024;
 constexpr int kPairTab = 496;  // C(32, 2): unranked index pairs
 constexpr int kAdThreads = 256;
 constexpr int kAdTile = 512;   // alpha-double pairs per CTA step
@@ -447,6 +451,7 @@ struct EmitArgs {
   ExcCounts E;
   FastDiv dv_va, dv_vb, dv_pa_p, dv_pb_p;
   uint32_t npd0, npd1;        // pairs per determinant for o = 0 and for an alpha single
+  uint32_t npieces;           // pieces of kPiecePairs pairs a determinant's o = 0 run is cut into
   const uint64_t *items, *Wexcl;
   const uint32_t *item_group;
   uint64_t t0, P0;
@@ -664,9 +669,12 @@ __global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
   for (uint64_t r = r0; r < r1; ++r) {
     const uint64_t run = A.runs[r];
     const uint64_t t = A.t0 + (run >> 32);
-    const uint32_t m = (uint32_t)run;
     const uint64_t it = A.items[t];
     const uint32_t k = (uint32_t)it >> A.opbits, o = (uint32_t)it & omask;
+    // determinant m of the group; for o = 0, piece number m % npieces of its run
+    const uint32_t mr = (uint32_t)run;
+    const uint32_t m = o == 0 ? mr / A.npieces : mr;
+    const uint32_t ebeg = o == 0 ? (mr - m * A.npieces) * kPiecePairs : 0u;
     const uint32_t gi = A.item_group[t] - A.gb0;
     const uint32_t kd = A.kind[gi];
     const bool big = kd == kTileBucket, packed = kd == kTilePacked;
@@ -678,6 +686,7 @@ __global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
     const uint32_t talpha = (uint32_t)(it >> 32);
     const uint32_t Ak = A.grp_alpha[k], B = A.core_beta[jdx];
     const uint32_t npd = o == 0 ? A.npd0 : A.npd1;
+    const uint32_t eend = npd < ebeg + kPiecePairs ? npd : ebeg + kPiecePairs;
     const uint64_t p0 = A.Wexcl[t] + (uint64_t)m * npd;
     // in-place staging slot of the run's first pair (classes that fit a tile)
     const uint32_t off0 = (uint32_t)(A.soff[gi] + (p0 - A.g_P0[A.gb0 + gi]));
@@ -738,7 +747,7 @@ __global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
     };
     auto decode = [&](uint32_t e0, Chunk &q) {
       const uint32_t e = e0 + lane;
-      q.valid = e < npd;
+      q.valid = e < eend;
       q.op = 0;
       q.h1 = q.h2 = q.p1 = q.p2 = 0;
       if (q.valid) {
@@ -798,10 +807,10 @@ __global__ void __launch_bounds__(kRunThreads, 4) k_emit_runs(EmitArgs A) {
     // classes) and integrals are requested before this chunk's matrix
     // elements are formed
     Chunk cur, nxt;
-    decode(0, cur);
+    decode(ebeg, cur);
 #pragma unroll 1
-    for (uint32_t e0 = 0; e0 < npd; e0 += 32) {
-      if (e0 + 32 < npd) decode(e0 + 32, nxt);  // warp-uniform
+    for (uint32_t e0 = ebeg; e0 < eend; e0 += 32) {
+      if (e0 + 32 < eend) decode(e0 + 32, nxt);  // warp-uniform
       double h = 0.0;
       int64_t dh = 0;
       {
@@ -956,14 +965,14 @@ __global__ void __launch_bounds__(kAdThreads) k_emit_ad(EmitArgs A) {
 // Per item of the batch: determinant runs (o = 0 or an alpha single) and the
 // alpha-double flag.
 __global__ void k_batch_counts(const uint64_t *items, uint64_t t0, uint64_t nt, int opbits,
-                               uint32_t sa, const uint32_t *grp_count, uint32_t *rcnt,
-                               uint32_t *adf) {
+                               uint32_t sa, uint32_t npieces, const uint32_t *grp_count,
+                               uint32_t *rcnt, uint32_t *adf) {
   const uint32_t omask = (1u << opbits) - 1u;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nt;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t lo = (uint32_t)items[t0 + i];
     const uint32_t k = lo >> opbits, o = lo & omask;
-    rcnt[i] = o <= sa ? grp_count[k] : 0u;
+    rcnt[i] = o == 0 ? grp_count[k] * npieces : (o <= sa ? grp_count[k] : 0u);
     adf[i] = o > sa ? 1u : 0u;
   }
 }
@@ -2160,8 +2169,10 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   ASCI_TRY(arena.alloc(&roff, nt));
   ASCI_TRY(arena.alloc(&adf, nt));
   ASCI_TRY(arena.alloc(&adpos, nt));
-  k_batch_counts<<<grid_for(nt), 256, 0, s>>>(F.items, t0, nt, F.opbits, F.E.sa, F.grp_count,
-                                              rcnt, adf);
+  const uint32_t npieces =
+      (uint32_t)std::max<uint64_t>(1, ((uint64_t)F.E.sb + F.E.dbb + kPiecePairs - 1) / kPiecePairs);
+  k_batch_counts<<<grid_for(nt), 256, 0, s>>>(F.items, t0, nt, F.opbits, F.E.sa, npieces,
+                                              F.grp_count, rcnt, adf);
   ASCI_CHECK_LAUNCH();
   ASCI_TRY(scan_exclusive_u32(rcnt, roff, nt, arena));
   ASCI_TRY(scan_exclusive_u32(adf, adpos, nt, arena));
@@ -2257,6 +2268,7 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   A.dv_pb_p = FastDiv(F.E.pb_p ? F.E.pb_p : 1);
   A.npd0 = (uint32_t)(F.E.sb + F.E.dbb);
   A.npd1 = 1u + F.E.sb;
+  A.npieces = npieces;
   A.items = F.items;
   A.Wexcl = F.Wexcl;
   A.item_group = F.item_group;
