@@ -1087,6 +1087,14 @@ struct CellArgs {
   unsigned long long *n_unique, *n_excluded;
   unsigned *err;
   int screened;  // records may carry the eps screen's drop marker
+  // exact sums left to k_long_sums (null: formed in the tile kernel): the
+  // values of each list, and per list (candidate slot, offset << 16 | length)
+  double *lv;
+  unsigned long long *lv_count;
+  unsigned long long lv_cap;
+  ulonglong2 *fix;
+  unsigned long long *nfix;
+  unsigned long long fix_cap;
 };
 
 __device__ __forceinline__ uint64_t mix_key(uint64_t z) {
@@ -1267,7 +1275,8 @@ __device__ __forceinline__ float abs_bound(double v) {
 // the common path's registers.
 __device__ __noinline__ double long_numerator(const StageRec *r, const uint16_t *next,
                                               uint32_t e, float tau_f, float den, int walk_max,
-                                              bool *reach, bool *deferred, unsigned *err) {
+                                              bool *reach, bool *deferred, unsigned long long *fix,
+                                              const CellArgs &C) {
   int emax = 1, len = 0;
   float sabs = 0.0f;
   for (uint32_t i = e; i != kEndList; i = next[i]) {
@@ -1284,6 +1293,24 @@ __device__ __noinline__ double long_numerator(const StageRec *r, const uint16_t 
     *reach = false;
     return 0.0;
   }
+  // The exact sum (several times the walk's cost, and one lane's work that
+  // its CTA waits for at the next barrier) is left to k_long_sums when its
+  // buffers have room: the values are copied out and the candidate is
+  // appended with the list's entry, whose slot the caller fills in.
+  if (C.lv) {
+    const unsigned long long fi = atomicAdd(C.nfix, 1ull);
+    const unsigned long long off = atomicAdd(C.lv_count, (unsigned long long)len);
+    if (fi < C.fix_cap) {
+      if (off + (unsigned long long)len <= C.lv_cap) {
+        unsigned long long j = off;
+        for (uint32_t i = e; i != kEndList; i = next[i]) C.lv[j++] = r[i].v;
+        C.fix[fi].y = (off << 16) | (unsigned long long)len;
+        *fix = fi;
+        return 0.0;
+      }
+      C.fix[fi].y = ~0ull;  // no room for the values: the entry stays unused
+    }
+  }
   const int frac = fx128_frac_for(emax);
   Fx128 acc = {0, 0};
   unsigned ovf = 0;
@@ -1291,8 +1318,38 @@ __device__ __noinline__ double long_numerator(const StageRec *r, const uint16_t 
     Fx128 x = fx128_from_double(r[i].v, frac, &ovf);
     fx128_add(acc, x);
   }
-  if (ovf) atomicOr(err, kErrAccum);
+  if (ovf) atomicOr(C.err, kErrAccum);
   return fx128_to_double(acc, frac);
+}
+
+// The exact sums left by long_numerator: one thread per list, the same
+// 128-bit fixed-point rule (so the same value bit for bit), written to the
+// candidate's score slot before its exact score is formed.
+__global__ void __launch_bounds__(256) k_long_sums(const ulonglong2 *fix,
+                                                   const unsigned long long *nfix,
+                                                   unsigned long long fix_cap, const double *lv,
+                                                   double *cand_score, unsigned *err) {
+  const unsigned long long n = *nfix < fix_cap ? *nfix : fix_cap;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const ulonglong2 f = fix[i];
+    if (f.y == ~0ull) continue;
+    const unsigned long long off = f.y >> 16, len = f.y & 0xffffull;
+    int emax = 1;
+    for (unsigned long long j = 0; j < len; ++j) {
+      const int ex = fx_exponent(lv[off + j]);
+      emax = ex > emax ? ex : emax;
+    }
+    const int frac = fx128_frac_for(emax);
+    Fx128 acc = {0, 0};
+    unsigned ovf = 0;
+    for (unsigned long long j = 0; j < len; ++j) {
+      Fx128 x = fx128_from_double(lv[off + j], frac, &ovf);
+      fx128_add(acc, x);
+    }
+    if (ovf) atomicOr(err, kErrAccum);
+    cand_score[f.x] = fx128_to_double(acc, frac);
+  }
 }
 
 // The numerator of a target with more than CAP / 32 records (a hot target),
@@ -1355,7 +1412,8 @@ __device__ __noinline__ double warp_numerator(const CellSmem<CAP, PACKED> &S, in
 template <int CAP, bool PACKED>
 __device__ __forceinline__ double list_numerator(const CellSmem<CAP, PACKED> &S, int buf, uint32_t e,
                                                  float tau_f, int walk_max, bool *reach,
-                                                 bool *deferred, unsigned *err) {
+                                                 bool *deferred, unsigned long long *fix,
+                                                 const CellArgs &C) {
   const StageRec *r = S.rec[buf];
   const uint32_t e2 = S.next[e];
   if (e2 == kEndList) return r[e].v;
@@ -1367,7 +1425,7 @@ __device__ __forceinline__ double list_numerator(const CellSmem<CAP, PACKED> &S,
   const uint32_t e4 = S.next[e3];
   if (e4 == kEndList) return sum4_ordered(0.0, r[e].v, r[e2].v, r[e3].v);
   if (S.next[e4] == kEndList) return sum4_ordered(r[e].v, r[e2].v, r[e3].v, r[e4].v);
-  return long_numerator(r, S.next, e, tau_f, r[e].den, walk_max, reach, deferred, err);
+  return long_numerator(r, S.next, e, tau_f, r[e].den, walk_max, reach, deferred, fix, C);
 }
 
 template <int CAP, int THREADS, bool PACKED>
@@ -1593,6 +1651,7 @@ __global__ void __launch_bounds__(THREADS) k_cells(CellArgs C) {
         double num = 0.0;
         float den = 0.0f;
         uint64_t key = 0;
+        unsigned long long fix = ~0ull;  // the list's k_long_sums entry, if its sum is left there
         if (idx < ntg) {
           const uint32_t h = S.targets[idx];
           const uint32_t e = S.slot[h];
@@ -1607,7 +1666,7 @@ __global__ void __launch_bounds__(THREADS) k_cells(CellArgs C) {
             live = true;
             den = S.rec[buf][e].den;
             num = list_numerator(S, buf, e, tau_f, kHotWarp ? CAP / 32 : CAP, &reach, &deferred,
-                                 C.err);
+                                 &fix, C);
           }
         }
         // hot targets: each summed by the whole warp
@@ -1626,7 +1685,7 @@ __global__ void __launch_bounds__(THREADS) k_cells(CellArgs C) {
         bool pass = false;
         if (live) {
           pass = reach;
-          if (reach && C.tau > 0.0) {
+          if (reach && C.tau > 0.0 && fix == ~0ull) {  // a deferred sum is appended untested
             bool okn;
             const float nf = abs_as_float(num, &okn);
             const float df = fabsf(den);
@@ -1644,6 +1703,9 @@ __global__ void __launch_bounds__(THREADS) k_cells(CellArgs C) {
             if (slotc < C.cand_cap) {
               C.cand_key[slotc] = key;
               C.cand_score[slotc] = sc;
+              if (fix != ~0ull) C.fix[fix].x = slotc;
+            } else if (fix != ~0ull) {
+              C.fix[fix].y = ~0ull;
             }
           }
         }
@@ -2425,6 +2487,31 @@ static CellArgs cell_args(const FusedCore &F, const Stage &st,
   return CA;
 }
 
+// Buffers of the exact sums that the tile kernels leave to k_long_sums, in a
+// scratch arena that outlives the launch and the fix-up that follows it.  A
+// launch defers a few hundred thousand lists; a list that finds no room is
+// summed in the tile kernel as before.
+static int enable_long_sums(CellArgs &CA, Arena &la) {
+  constexpr unsigned long long kLvCap = 1ull << 24, kFixCap = 1ull << 21;
+  unsigned long long *cnt;
+  ASCI_TRY(la.alloc(&CA.lv, (size_t)kLvCap));
+  ASCI_TRY(la.alloc(&CA.fix, (size_t)kFixCap));
+  ASCI_TRY(la.alloc(&cnt, 2));
+  ASCI_TRY_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), la.stream()));
+  CA.lv_count = cnt;
+  CA.nfix = cnt + 1;
+  CA.lv_cap = kLvCap;
+  CA.fix_cap = kFixCap;
+  return ASCI_OK;
+}
+
+static int run_long_sums(const CellArgs &CA, int sms, cudaStream_t s) {
+  k_long_sums<<<(unsigned)sms * 4, 256, 0, s>>>(CA.fix, CA.nfix, CA.fix_cap, CA.lv, CA.cand_score,
+                                                 CA.err);
+  ASCI_CHECK_LAUNCH();
+  return ASCI_OK;
+}
+
 // Reduce tiles [tile_begin, tile_end) of a staged batch on chip and append the
 // targets with |S| >= tau to the candidate buffer (at most kCap per tile).
 int fused_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
@@ -2463,8 +2550,11 @@ int fused_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
   const int per = (F.ctas_per_sm > 0 && F.ctas_per_sm < per_sm) ? F.ctas_per_sm : per_sm;
   const unsigned grid = (unsigned)std::min<size_t>((size_t)sms * per, tile_end - tile_begin);
   ASCI_TRACE("cells: launch grid=%u smem=%zu per_sm=%d", grid, cell_smem, per_sm);
+  Arena la(s);
+  ASCI_TRY(enable_long_sums(CA, la));
   k_cells<kCap, kCellThreads, true><<<grid, kCellThreads, cell_smem, s>>>(CA);
   ASCI_CHECK_LAUNCH();
+  ASCI_TRY(run_long_sums(CA, sms, s));
   return ASCI_OK;
 }
 
@@ -2544,8 +2634,10 @@ int fused_big_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_l
   ASCI_TRY_CUDA(cudaGetDevice(&dev));
   ASCI_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const unsigned grid = (unsigned)std::min<size_t>((size_t)sms, nt);
+  ASCI_TRY(enable_long_sums(CA, ta));
   k_cells<kBigCap, kBigThreads, false><<<grid, kBigThreads, smem, s>>>(CA);
   ASCI_CHECK_LAUNCH();
+  ASCI_TRY(run_long_sums(CA, sms, s));
   ASCI_TRY_CUDA(cudaStreamSynchronize(s));  // the host vector above is read by a copy
   return ASCI_OK;
 }
