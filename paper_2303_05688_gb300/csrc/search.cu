@@ -848,7 +848,7 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   ASCI_TRY_CUDA(cudaGetDevice(&dev));
   ASCI_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const size_t cap_extra =
-      std::max<size_t>(tile_capacity() * (size_t)sms * 16, std::min<uint64_t>(bcap, 1ull << 28));
+      std::max<size_t>(tile_capacity() * (size_t)sms * 16, std::min<uint64_t>(bcap, 1ull << 29));
   const size_t pool_cap = N + cap_extra;
   // staging: pairs of classes that fit a tile in place, kCap slots per hash
   // bucket of a big class (expected fill about 13/16)

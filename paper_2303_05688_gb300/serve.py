@@ -26,10 +26,10 @@ __all__ = ["Server", "footprint"]
 def footprint(norb: int, ndets: int, C: int, N: int, batch_pairs: int) -> int:
     """Upper estimate of one search's device bytes beyond its resident inputs:
     the staging of one constraint batch (16-byte pairs, 1.5 slots each, and the
-    alpha word), item lists, the candidate pool (two buffers of N + 2^28 entries
+    alpha word), item lists, the candidate pool (two buffers of N + 2^29 entries
     at most, 16 bytes each), the psi hash and routing, and the integral tables."""
     staging = 28 * batch_pairs
-    pool = 32 * (N + min(batch_pairs, 1 << 28))
+    pool = 32 * (N + min(batch_pairs, 1 << 29))
     psi = 48 * ndets
     tables = 40 * norb ** 4
     items = 64 * C * (1 + norb * norb)
