@@ -1164,6 +1164,10 @@ constexpr int kPsiCap = 64;                // psi markers per tile; more: global
 // record: two hash slots and eight filter bits.
 constexpr int kBigCap = 4096;
 constexpr int kBigThreads = 1024;
+// buckets of at most kMidCap records (most overfilled ones) take a middle
+// size: two CTAs of kMidThreads per SM
+constexpr int kMidCap = 2048;
+constexpr int kMidThreads = 512;
 
 template <int CAP>
 constexpr int log2_of() {
@@ -1194,6 +1198,7 @@ struct CellSmem {
 };
 using TileSmem = CellSmem<kCap, true>;
 using BigTileSmem = CellSmem<kBigCap, false>;
+using MidTileSmem = CellSmem<kMidCap, false>;
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -2578,22 +2583,67 @@ int tile_info(const void *tiles, const std::vector<uint32_t> &list, const Spill 
   return ASCI_OK;
 }
 
+// Launch the tile kernel of one size over tiles [t0, t1) of CA.tiles.
+template <int CAP, int THREADS>
+static int launch_big_cells(CellArgs CA, uint32_t t0, uint32_t t1, int sms, cudaStream_t s) {
+  if (t1 <= t0) return ASCI_OK;
+  using Smem = CellSmem<CAP, false>;
+  const size_t smem = sizeof(Smem);
+  static const int per_sm = [smem]() {
+    int p = 0;
+    if (cudaFuncSetAttribute(k_cells<CAP, THREADS, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k_cells<CAP, THREADS, false>, THREADS,
+                                                      smem) != cudaSuccess)
+      return 0;
+    return p < 1 ? 1 : p;
+  }();
+  if (!per_sm) {
+    record_error("large tile kernel: cannot set its shared memory size", __FILE__, __LINE__);
+    return ASCI_ECUDA;
+  }
+  CA.tile0 = t0;
+  CA.ntiles = t1;
+  const unsigned grid = (unsigned)std::min<size_t>((size_t)sms * per_sm, t1 - t0);
+  k_cells<CAP, THREADS, false><<<grid, THREADS, smem, s>>>(CA);
+  ASCI_CHECK_LAUNCH();
+  return ASCI_OK;
+}
+
 // Reduce oversized bucket tiles of at most kBigCap records on chip: list[i]
-// is a tile of the batch and info[5i..5i+4] its row from tile_info.  Appends
-// at most as many candidates as there are records (*nrec_out).
+// is a tile of the batch and info[5i..5i+4] its row from tile_info.  Tiles of
+// at most kMidCap records go to the middle-size kernel, the rest to the
+// kBigCap one.  Appends at most as many candidates as there are records
+// (*nrec_out).
 int fused_big_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
-                    const uint32_t *list, const uint32_t *info, size_t nt, const Stage &st,
-                    const Spill &spill, double tau, uint64_t *cand_key, double *cand_score,
-                    unsigned long long *cand_count, unsigned long long cand_cap,
-                    unsigned long long *n_unique, unsigned long long *n_excluded, unsigned *err,
-                    uint64_t *nrec_out, Arena &arena) {
+                    const uint32_t *list_in, const uint32_t *info_in, size_t nt,
+                    const Stage &st, const Spill &spill, double tau, uint64_t *cand_key,
+                    double *cand_score, unsigned long long *cand_count,
+                    unsigned long long cand_cap, unsigned long long *n_unique,
+                    unsigned long long *n_excluded, unsigned *err, uint64_t *nrec_out,
+                    Arena &arena) {
   cudaStream_t s = arena.stream();
   *nrec_out = 0;
   if (!nt) return ASCI_OK;
-  std::vector<uint32_t> off(nt);
+  // middle-size tiles first
+  std::vector<uint32_t> list(nt), info(5 * nt), off(nt);
+  size_t nmid = 0;
+  for (size_t i = 0; i < nt; ++i) {
+    const uint32_t *r = info_in + 5 * i;
+    if ((uint64_t)r[1] + r[4] <= (uint64_t)kMidCap) ++nmid;
+  }
+  {
+    size_t a = 0, b = nmid;
+    for (size_t i = 0; i < nt; ++i) {
+      const uint32_t *r = info_in + 5 * i;
+      const size_t j = ((uint64_t)r[1] + r[4] <= (uint64_t)kMidCap) ? a++ : b++;
+      list[j] = list_in[i];
+      for (int w = 0; w < 5; ++w) info[5 * j + w] = r[w];
+    }
+  }
   uint64_t total = 0;
   for (size_t i = 0; i < nt; ++i) {
-    const uint32_t *r = info + 5 * i;
+    const uint32_t *r = info.data() + 5 * i;
     const uint64_t nrec = (uint64_t)r[1] + r[4];
     if (nrec > (uint64_t)kBigCap || (uint64_t)r[0] + r[1] > st.cap ||
         (uint64_t)r[3] + r[4] > spill.n)
@@ -2612,8 +2662,8 @@ int fused_big_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_l
   ASCI_TRY(ta.alloc(&d_off, nt));
   ASCI_TRY(ta.alloc(&big, total));
   ASCI_TRY(ta.alloc(&desc, nt));
-  ASCI_TRY_CUDA(cudaMemcpyAsync(d_list, list, nt * 4, cudaMemcpyDefault, s));
-  ASCI_TRY_CUDA(cudaMemcpyAsync(d_info, info, 5 * nt * 4, cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(d_list, list.data(), nt * 4, cudaMemcpyDefault, s));
+  ASCI_TRY_CUDA(cudaMemcpyAsync(d_info, info.data(), 5 * nt * 4, cudaMemcpyDefault, s));
   ASCI_TRY_CUDA(cudaMemcpyAsync(d_off, off.data(), nt * 4, cudaMemcpyDefault, s));
   k_big_tile_gather<<<(unsigned)nt, 256, 0, s>>>(static_cast<const TileDesc *>(tiles), d_list,
                                                  d_info, d_off, st.rec, spill.rec, spill.keys,
@@ -2623,22 +2673,14 @@ int fused_big_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_l
                           cand_cap, n_unique, n_excluded, err);
   CA.tiles = desc;
   CA.psi_list = psi_list;
-  CA.tile0 = 0;
-  CA.ntiles = (uint32_t)nt;
-  const size_t smem = sizeof(BigTileSmem);
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      k_cells<kBigCap, kBigThreads, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)smem);
-  ASCI_TRY_CUDA(attr);
   int dev = 0, sms = 152;
   ASCI_TRY_CUDA(cudaGetDevice(&dev));
   ASCI_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned grid = (unsigned)std::min<size_t>((size_t)sms, nt);
   ASCI_TRY(enable_long_sums(CA, ta));
-  k_cells<kBigCap, kBigThreads, false><<<grid, kBigThreads, smem, s>>>(CA);
-  ASCI_CHECK_LAUNCH();
+  ASCI_TRY((launch_big_cells<kMidCap, kMidThreads>(CA, 0, (uint32_t)nmid, sms, s)));
+  ASCI_TRY((launch_big_cells<kBigCap, kBigThreads>(CA, (uint32_t)nmid, (uint32_t)nt, sms, s)));
   ASCI_TRY(run_long_sums(CA, sms, s));
-  ASCI_TRY_CUDA(cudaStreamSynchronize(s));  // the host vector above is read by a copy
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));  // the host vectors above are read by copies
   return ASCI_OK;
 }
 
