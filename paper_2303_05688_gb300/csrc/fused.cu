@@ -984,23 +984,39 @@ __global__ void k_batch_lists(const uint64_t *items, uint64_t t0, uint64_t nt, i
                               FastDiv dv_va, uint32_t *opinfo) {
   const uint32_t omask = (1u << opbits) - 1u;
   const uint32_t full = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nt;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t lo = (uint32_t)items[t0 + i];
-    const uint32_t k = lo >> opbits, o = lo & omask;
-    if (o <= sa) {
-      for (uint32_t m = 0; m < rcnt[i]; ++m) runs[(uint64_t)roff[i] + m] = (i << 32) | m;
-      uint32_t oi = 0;
-      if (o != 0) {
-        const uint32_t Ak = grp_alpha[k];
-        int ia, aa;
-        dec_single(Ak, ~Ak & full, o - 1, dv_va, &ia, &aa);
-        oi = (uint32_t)ia | ((uint32_t)aa << 5) | ((uint32_t)single_parity(Ak, ia, aa) << 10);
+  const int lane = (int)(threadIdx.x & 31u);
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  // warps take 32 items at a time (warp-uniform loop); the runs of the 32
+  // items are then written by the whole warp, item by item, so that an item
+  // with many runs (a big group's o = 0 item, in pieces) is not one thread's
+  for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < nt;
+       base += nwarps * 32) {
+    const uint64_t i = base + (uint64_t)lane;
+    uint32_t cnt = 0, start = 0;
+    if (i < nt) {
+      const uint32_t lo = (uint32_t)items[t0 + i];
+      const uint32_t k = lo >> opbits, o = lo & omask;
+      if (o <= sa) {
+        cnt = rcnt[i];
+        start = roff[i];
+        uint32_t oi = 0;
+        if (o != 0) {
+          const uint32_t Ak = grp_alpha[k];
+          int ia, aa;
+          dec_single(Ak, ~Ak & full, o - 1, dv_va, &ia, &aa);
+          oi = (uint32_t)ia | ((uint32_t)aa << 5) | ((uint32_t)single_parity(Ak, ia, aa) << 10);
+        }
+        opinfo[i] = oi;
+      } else {
+        adl[adpos[i]] = (uint32_t)i;
+        adw[adpos[i]] = grp_count[k];
       }
-      opinfo[i] = oi;
-    } else {
-      adl[adpos[i]] = (uint32_t)i;
-      adw[adpos[i]] = grp_count[k];
+    }
+    for (int j = 0; j < 32; ++j) {
+      const uint32_t c = __shfl_sync(0xffffffffu, cnt, j);
+      const uint32_t st = __shfl_sync(0xffffffffu, start, j);
+      const uint64_t ii = base + (uint64_t)j;
+      for (uint32_t m = (uint32_t)lane; m < c; m += 32) runs[(uint64_t)st + m] = (ii << 32) | m;
     }
   }
 }
