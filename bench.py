@@ -36,10 +36,10 @@ METRIC = "ASCI search scored excitations/s at (24e,30o)"
 # dram__bytes_write.sum over every tile launch of one search, divided by its
 # staged pairs); `traffic` is this figure scaled to one launch, and null for
 # a workload without a capture.
-TILE_DRAM_BYTES_PER_RECORD = {"random_24e30o": 17.27}
-TILE_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 42 tile launches of "
-                    "one search of the same workload at C = 1e4 with 2^25-pair batches (11.60 GB "
-                    "for 6.715e8 staged pairs)")
+TILE_DRAM_BYTES_PER_RECORD = {"random_24e30o": 17.46}
+TILE_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 42 launches of the "
+                    "1024-record tile kernel in one search of the same workload at C = 1e4 with "
+                    "2^25-pair batches (11.72 GB for 6.715e8 staged pairs)")
 UNIT = "excitations/s"
 
 
