@@ -359,6 +359,11 @@ int radix_sort_u64_u32(uint64_t **keys, uint64_t **keys_alt, uint32_t **vals, ui
                        size_t n, int begin_bit, int end_bit, Arena &arena);
 int radix_sort_u64_f64(uint64_t **keys, uint64_t **keys_alt, double **vals, double **vals_alt,
                        size_t n, int begin_bit, int end_bit, Arena &arena);
+// The same keys-only sort when the caller knows which bits vary among the
+// keys (a digit with no varying bit is skipped; varying bits outside the mask
+// would be left unsorted).
+int radix_sort_u64_varying(uint64_t **keys, uint64_t **keys_alt, size_t n, int begin_bit,
+                           int end_bit, uint64_t varying, Arena &arena);
 
 // Bits in which the keys differ (OR of key ^ keys[0]); result on the host.
 int varying_bits_u64(const uint64_t *keys, size_t n, uint64_t *host_mask, Arena &arena);

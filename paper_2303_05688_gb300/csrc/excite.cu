@@ -249,11 +249,12 @@ namespace {
 __global__ void __launch_bounds__(256)
     k_make_items(ExcCounts X, int n, const uint32_t *grp_alpha, uint32_t ngroups,
                  uint32_t o_begin, uint32_t nops, int opbits, FastDiv by_nv, FastDiv by_npp,
-                 uint64_t *items) {
+                 uint64_t *items, unsigned *t_or, unsigned *t_and) {
   __shared__ uint8_t occ[32], vir[32];
   __shared__ uint8_t pr_x[496], pr_y[496];  // pair r -> (x, y), x < y < 32
   const uint32_t per = nops - o_begin;
   const uint32_t full = full_mask(n);
+  uint32_t any_or = 0u, all_and = 0xffffffffu;
   for (int r = threadIdx.x; r < 496; r += blockDim.x) {
     int x, y;
     unrank_pair((uint32_t)r, &x, &y);
@@ -283,21 +284,42 @@ __global__ void __launch_bounds__(256)
               (1u << vir[pr_y[pp]]);
       }
       out[t] = ((uint64_t)At << 32) | lo_k | o;
+      any_or |= At;
+      all_and &= At;
     }
+  }
+  // the bits in which the target strings differ (for the sort), one atomic
+  // pair per warp
+  any_or = __reduce_or_sync(0xffffffffu, any_or);
+  all_and = __reduce_and_sync(0xffffffffu, all_and);
+  if ((threadIdx.x & 31u) == 0) {
+    atomicOr(t_or, any_or);
+    atomicAnd(t_and, all_and);
   }
 }
 
 }  // namespace
 
 int make_items(const ExcCounts &X, int n, const uint32_t *grp_alpha, uint32_t ngroups,
-               uint32_t o_begin, uint32_t nops, int opbits, uint64_t *items, Arena &arena) {
+               uint32_t o_begin, uint32_t nops, int opbits, uint64_t *items,
+               uint64_t *varying, Arena &arena) {
+  *varying = 0;
   uint64_t total = (uint64_t)ngroups * (nops - o_begin);
   if (!total) return ASCI_OK;
+  cudaStream_t s = arena.stream();
+  unsigned *bits;
+  ASCI_TRY(arena.alloc(&bits, 2));
+  const unsigned init[2] = {0u, 0xffffffffu};
+  ASCI_TRY_CUDA(cudaMemcpyAsync(bits, init, sizeof(init), cudaMemcpyHostToDevice, s));
   const unsigned blocks = (unsigned)std::min<uint64_t>(ngroups, 152 * 8);
-  k_make_items<<<blocks, 256, 0, arena.stream()>>>(X, n, grp_alpha, ngroups, o_begin, nops, opbits,
-                                                   FastDiv(X.va ? X.va : 1),
-                                                   FastDiv(X.pa_p ? X.pa_p : 1), items);
+  k_make_items<<<blocks, 256, 0, s>>>(X, n, grp_alpha, ngroups, o_begin, nops, opbits,
+                                      FastDiv(X.va ? X.va : 1), FastDiv(X.pa_p ? X.pa_p : 1),
+                                      items, bits, bits + 1);
   ASCI_CHECK_LAUNCH();
+  unsigned h[2] = {0u, 0u};
+  ASCI_TRY_CUDA(cudaMemcpyAsync(h, bits, sizeof(h), cudaMemcpyDeviceToHost, s));
+  ASCI_TRY_CUDA(cudaStreamSynchronize(s));
+  *varying = (uint64_t)(h[0] ^ h[1]) << 32;
   return ASCI_OK;
 }
 

@@ -1012,7 +1012,8 @@ __global__ void k_batch_lists(const uint64_t *items, uint64_t t0, uint64_t nt, i
         adw[adpos[i]] = grp_count[k];
       }
     }
-    for (int j = 0; j < 32; ++j) {
+    for (uint32_t have = __ballot_sync(0xffffffffu, cnt != 0); have; have &= have - 1) {
+      const int j = __ffs(have) - 1;
       const uint32_t c = __shfl_sync(0xffffffffu, cnt, j);
       const uint32_t st = __shfl_sync(0xffffffffu, start, j);
       const uint64_t ii = base + (uint64_t)j;

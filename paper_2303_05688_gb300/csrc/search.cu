@@ -32,7 +32,8 @@
 namespace asci {
 
 int make_items(const ExcCounts &X, int n, const uint32_t *grp_alpha, uint32_t ngroups,
-               uint32_t o_begin, uint32_t nops, int opbits, uint64_t *items, Arena &arena);
+               uint32_t o_begin, uint32_t nops, int opbits, uint64_t *items,
+               uint64_t *varying, Arena &arena);
 int compact_u64(const uint64_t *in, const uint32_t *keep, const uint32_t *pos, size_t n,
                 uint64_t *out, Arena &arena);
 int compact_f64(const double *in, const uint32_t *keep, const uint32_t *pos, size_t n, double *out,
@@ -716,8 +717,10 @@ static int search_impl(const asci_det *dets_in, const double *coeffs_in, size_t 
   if (T > 0) {
     ASCI_TRY(arena.alloc(&items, T));
     ASCI_TRY(arena.alloc(&items_alt, T));
-    ASCI_TRY(make_items(X, n, grp_alpha, (uint32_t)ngroups, o_begin, nops, opbits, items, arena));
-    ASCI_TRY(radix_sort_u64(&items, &items_alt, T, 32, 32 + n, arena));
+    uint64_t varying = 0;  // bits in which the target strings differ
+    ASCI_TRY(make_items(X, n, grp_alpha, (uint32_t)ngroups, o_begin, nops, opbits, items, &varying,
+                        arena));
+    ASCI_TRY(radix_sort_u64_varying(&items, &items_alt, T, 32, 32 + n, varying, arena));
     ASCI_TRY(arena.alloc(&Wexcl, T + 1));
     ASCI_TRY(scan_item_weights(items, T, opbits, grp_count, X, Wexcl, arena));
     ASCI_TRY_CUDA(cudaMemcpyAsync(&P, Wexcl + T, 8, cudaMemcpyDefault, stream));

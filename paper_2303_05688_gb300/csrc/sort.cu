@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kSortThreads, 4)
 
 template <typename V, bool kHasVals>
 int radix_sort_impl(uint64_t **keys, uint64_t **keys_alt, V **vals, V **vals_alt, size_t n,
-                    int begin_bit, int end_bit, Arena &arena) {
+                    int begin_bit, int end_bit, Arena &arena, const uint64_t *known_mask = nullptr) {
   if (n <= 1 || begin_bit >= end_bit) return ASCI_OK;
   if (n >= (1ull << 32)) return ASCI_EINVAL;
   cudaStream_t s = arena.stream();
@@ -287,7 +287,8 @@ int radix_sort_impl(uint64_t **keys, uint64_t **keys_alt, V **vals, V **vals_alt
       (int)scatter_smem<V, kHasVals>());
   ASCI_TRY_CUDA(attr);
   uint64_t mask = 0;
-  ASCI_TRY(varying_bits_u64(*keys, n, &mask, arena));
+  if (known_mask) mask = *known_mask;  // the caller knows which bits vary
+  else ASCI_TRY(varying_bits_u64(*keys, n, &mask, arena));
   for (int shift = begin_bit; shift < end_bit; shift += 8) {
     uint64_t dmask = (0xffull << shift);
     if (end_bit - shift < 8) dmask &= ((end_bit >= 64) ? ~0ull : ((1ull << end_bit) - 1));
@@ -362,6 +363,11 @@ int radix_sort_u64(uint64_t **keys, uint64_t **keys_alt, size_t n, int begin_bit
                    Arena &arena) {
   return radix_sort_impl<uint32_t, false>(keys, keys_alt, nullptr, nullptr, n, begin_bit, end_bit,
                                           arena);
+}
+int radix_sort_u64_varying(uint64_t **keys, uint64_t **keys_alt, size_t n, int begin_bit,
+                           int end_bit, uint64_t varying, Arena &arena) {
+  return radix_sort_impl<uint32_t, false>(keys, keys_alt, nullptr, nullptr, n, begin_bit, end_bit,
+                                          arena, &varying);
 }
 int radix_sort_u64_u32(uint64_t **keys, uint64_t **keys_alt, uint32_t **vals, uint32_t **vals_alt,
                        size_t n, int begin_bit, int end_bit, Arena &arena) {
