@@ -2510,11 +2510,15 @@ static CellArgs cell_args(const FusedCore &F, const Stage &st,
 }
 
 // Buffers of the exact sums that the tile kernels leave to k_long_sums, in a
-// scratch arena that outlives the launch and the fix-up that follows it.  A
-// launch defers a few hundred thousand lists; a list that finds no room is
-// summed in the tile kernel as before.
-static int enable_long_sums(CellArgs &CA, Arena &la) {
-  constexpr unsigned long long kLvCap = 1ull << 24, kFixCap = 1ull << 21;
+// scratch arena that outlives the launch and the fix-up that follows it,
+// sized from the launch's tiles (about seven lists of five or more records a
+// tile at (24e,30o), nine records long; with no threshold, as in ASCI-PT2,
+// every such list is deferred).  A list that finds no room is summed in the
+// tile kernel as before.
+static int enable_long_sums(CellArgs &CA, size_t ntiles, Arena &la) {
+  const unsigned long long kFixCap =
+      std::max<unsigned long long>(1ull << 20, (unsigned long long)ntiles * 8);
+  const unsigned long long kLvCap = kFixCap * 12;
   unsigned long long *cnt;
   ASCI_TRY(la.alloc(&CA.lv, (size_t)kLvCap));
   ASCI_TRY(la.alloc(&CA.fix, (size_t)kFixCap));
@@ -2573,7 +2577,7 @@ int fused_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_list,
   const unsigned grid = (unsigned)std::min<size_t>((size_t)sms * per, tile_end - tile_begin);
   ASCI_TRACE("cells: launch grid=%u smem=%zu per_sm=%d", grid, cell_smem, per_sm);
   Arena la(s);
-  ASCI_TRY(enable_long_sums(CA, la));
+  ASCI_TRY(enable_long_sums(CA, tile_end - tile_begin, la));
   k_cells<kCap, kCellThreads, true><<<grid, kCellThreads, cell_smem, s>>>(CA);
   ASCI_CHECK_LAUNCH();
   ASCI_TRY(run_long_sums(CA, sms, s));
@@ -2693,7 +2697,7 @@ int fused_big_cells(const FusedCore &F, const void *tiles, const uint64_t *psi_l
   int dev = 0, sms = 152;
   ASCI_TRY_CUDA(cudaGetDevice(&dev));
   ASCI_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  ASCI_TRY(enable_long_sums(CA, ta));
+  ASCI_TRY(enable_long_sums(CA, nt * 4, ta));
   ASCI_TRY((launch_big_cells<kMidCap, kMidThreads>(CA, 0, (uint32_t)nmid, sms, s)));
   ASCI_TRY((launch_big_cells<kBigCap, kBigThreads>(CA, (uint32_t)nmid, (uint32_t)nt, sms, s)));
   ASCI_TRY(run_long_sums(CA, sms, s));
