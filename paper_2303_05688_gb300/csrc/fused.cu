@@ -2828,6 +2828,7 @@ __device__ __forceinline__ int64_t warp_diag(const FxInts &X, uint32_t A, uint32
   const uint32_t lane = threadIdx.x & 31u;
   int64_t diag = 0;
   uint32_t pending = __ballot_sync(0xffffffffu, live);
+  const int nbmax = (int)__reduce_max_sync(0xffffffffu, live ? (unsigned)__popc(B) : 0u);
   for (int round = 0; pending && round < 4; ++round) {
     const uint32_t AL = __shfl_sync(0xffffffffu, A, __ffs(pending) - 1);
     int64_t part = 0, ja = 0;
@@ -2842,10 +2843,16 @@ __device__ __forceinline__ int64_t warp_diag(const FxInts &X, uint32_t A, uint32
     for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     const bool mine = live && A == AL && ((pending >> lane) & 1u);
     const uint32_t group = __ballot_sync(0xffffffffu, mine);
+    // each lane reads J_A[q] from lane q for the occupied beta orbitals q of
+    // its own B (every round is taken by the whole warp)
     int64_t cross = 0;
-    for (int q = 0; q < n; ++q) {
+    uint32_t mB = B;
+    for (int it = 0; it < nbmax; ++it) {
+      const bool has = mB != 0u;
+      const int q = has ? __ffs(mB) - 1 : 0;
+      mB &= mB - 1u;
       const int64_t t = __shfl_sync(0xffffffffu, ja, q);
-      if (mine && ((B >> q) & 1u)) cross += t;
+      if (mine && has) cross += t;
     }
     if (mine) {
       int64_t s = X.ecore_x + part + cross;
