@@ -115,8 +115,9 @@ typedef struct {
   uint64_t tile_launches;      /* launches of the on-chip tile kernel */
   uint64_t tile_records;       /* staged pairs reduced on chip (16 bytes read each) */
   uint64_t oversized_records;  /* staged pairs of hash buckets overfilled by hot
-                                  targets: reduced by the large tile kernel (up
-                                  to 4096 records a bucket) or the global sort */
+                                  targets: reduced by the larger tile kernels
+                                  (up to 2048 or 4096 records a bucket) or, in
+                                  a bigger bucket, by a global sort */
   /* The diagonal H_ii is summed exactly in 64-bit fixed point on the grid
    * 2^-diag_grid_bits: E0, ecore and each integral term of H_ii (h_pp, J - K of
    * a same-spin pair, J of an opposite-spin pair) is rounded once to the grid,
