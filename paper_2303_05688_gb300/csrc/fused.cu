@@ -287,7 +287,6 @@ __device__ __forceinline__ double flip_sign(double x, uint32_t flip) {
 
 constexpr int kCellThreads = 256;
 constexpr int kCap = 1024;                          // records per tile
-constexpr int kSlots = 2 * kCap;                    // hash slots per tile (load <= 1/2)
 constexpr uint32_t kSmallMax = kCap / 2;            // packable class size
 constexpr uint32_t kBucketTarget = kCap * 13 / 16;  // expected records per hash bucket
 
@@ -1195,7 +1194,6 @@ constexpr int log2_of() {
 
 template <int CAP, bool PACKED>
 struct CellSmem {
-  static constexpr int kRecs = CAP;
   static constexpr int kTab = 2 * CAP;           // hash slots (load <= 1/2)
   static constexpr int kFilterWords = CAP / 4;   // 8 CAP filter bits
   static constexpr int kFilterShift = 32 - (log2_of<CAP>() + 3);  // top bits pick a filter bit
@@ -2341,8 +2339,7 @@ int fused_stage(const FusedCore &F, uint64_t t0, uint64_t t1, uint64_t P0, uint6
   }
   *psi_list_out = psi_list;
 
-  EmitArgs A;
-  memset(&A, 0, sizeof(A));
+  EmitArgs A{};
   A.I = F.I;
   A.X = F.X;
   A.E = F.E;

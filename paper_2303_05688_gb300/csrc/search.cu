@@ -447,7 +447,7 @@ class Planner {
     batches_.clear();
     cur_open_ = false;
     max_level_ = L0;
-    ASCI_TRY(visit(0, G_, 0, T, 0, P, L0));
+    ASCI_TRY(visit(0, G_, T, P, L0));
     flush();
     *out = batches_;
     *max_level = max_level_;
@@ -501,8 +501,8 @@ class Planner {
     }
   }
 
-  // groups [gs, ge) = items [is, ie) = pairs [ws, we), split at level L
-  int visit(uint64_t gs, uint64_t ge, uint64_t is, uint64_t ie, uint64_t ws, uint64_t we, int L) {
+  // groups [gs, ge), whose items end at ie and pairs at we, split at level L
+  int visit(uint64_t gs, uint64_t ge, uint64_t ie, uint64_t we, int L) {
     if (L > max_level_) max_level_ = L;
     std::vector<uint64_t> gst, ist, wst;
     ASCI_TRY(query(gs, ge, L, &gst, &ist, &wst));
@@ -513,7 +513,7 @@ class Planner {
       const uint64_t w0 = wst[c], w1 = last ? we : wst[c + 1];
       if (w1 - w0 > bmax_ && L < lmax_ && g1 - g0 > 1) {
         flush();
-        ASCI_TRY(visit(g0, g1, i0, i1, w0, w1, L + 1));
+        ASCI_TRY(visit(g0, g1, i1, w1, L + 1));
       } else {
         add(i0, i1, w0, w1);
       }
