@@ -91,3 +91,35 @@ int main(void) {
     assert r.returncode == 0, r.stderr
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip() == "invalid argument"
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding passes by pointer has the header's size and
+    field offsets (a field added to asci.h without the binding, or in another
+    place, would shift everything after it)."""
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    import ctypes as ct
+    m = pytest.importorskip("paper_2303_05688_gb300")
+    pairs = [("asci_det", m._Det), ("asci_ints", m._Ints), ("asci_opts", m._Opts),
+             ("asci_select_state", m._SelectState), ("asci_problem", m._Problem),
+             ("asci_stats", m._Stats), ("asci_davidson_opts", m._DavOpts),
+             ("asci_loop_opts", m._LoopOpts), ("asci_loop_stats", m._LoopStats)]
+    lines = []
+    for cname, py in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"asci.h\"\n"
+                   "int main(void) {\n" + "\n".join(lines) + "\n  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:-1]): int(l.split()[-1]) for l in out if l.strip()}
+    for cname, py in pairs:
+        assert got[(cname, "size")] == ct.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
